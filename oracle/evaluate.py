@@ -1,0 +1,248 @@
+"""Oracle driver: one SIBFA energy + force evaluation in FP64.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and
+bench.py's CPU-baseline leg; never by the product path.
+
+Order of the steps (the method's call order): sites and frames -> real-space
+pair terms (electrostatics + penetration, exchange-repulsion, dispersion) ->
+reciprocal / self / exclusion electrostatics -> potentials on the lone pairs
+-> reduced charge transfer -> polarization solve (Jacobi-preconditioned
+conjugate gradient on T mu = E) -> polarization energy.  Forces are the exact
+gradient -dE/dx: autograd of each term, with the induced dipoles held at the
+solution (E_pol is stationary in mu there) and the charge-transfer
+dependence on the lone-pair potentials applied by the chain rule.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+import torch
+
+from synth import PARAMS
+
+from . import ewald as ew
+from . import terms as tm
+from .core import DT, build_sites, t64
+
+TERMS = ("elec", "pen", "rep", "disp", "xdisp", "pol", "ct")
+SITE_MARGIN = 2.6       # A, molecule-list margin over rc (site extents < 1.3 A)
+
+
+class _Setup:
+    def __init__(self, system, opts, P):
+        self.P = P
+        self.mp = torch.as_tensor(system.mp_local, dtype=DT)
+        self.periodic = system.box is not None
+        self.box = t64(system.box) if self.periodic else None
+        if self.periodic:
+            self.rc = float(opts["rc"])
+            self.alpha = float(opts["ewald"])
+            g = opts["grid"]
+            self.K = (g, g, g) if isinstance(g, int) else tuple(g)
+            self.order = int(opts.get("order", 5))
+            self.G = ew.influence(self.box, self.K, self.order, self.alpha, P["ke"])
+            cut = self.rc + SITE_MARGIN
+        else:
+            self.rc = None
+            self.alpha = None
+            cut = None
+        O = np.asarray(system.pos[:, 0], dtype=np.float64)
+        i, j, sh = tm.mol_pairs(O, system.box if self.periodic else None, cut)
+        self.i, self.j, self.sh = i, j, t64(sh)
+
+    def chunks(self, size):
+        n = self.i.size
+        for a in range(0, n, size):
+            b = min(n, a + size)
+            yield self.i[a:b], self.j[a:b], self.sh[a:b]
+
+
+def _grad(e, wrt):
+    return torch.autograd.grad(e, wrt, allow_unused=True)
+
+
+def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=2048,
+             P=None, mu_guess=None, pcg_log=None, per_term=False, keep_operators=False):
+    """Energies (kcal/mol) per term, forces (kcal/mol/A) on O, H1, H2, induced
+    dipoles (e.A) on O, H1, H2, PCG iteration count and final residual (D).
+
+    opts (periodic systems): rc, grid, order, ewald.  Gas phase: opts unused."""
+    P = PARAMS if P is None else P
+    opts = opts or {}
+    st = _Setup(system, opts, P)
+    x = torch.tensor(system.pos, dtype=DT, requires_grad=forces)
+    M = x.shape[0]
+    F = torch.zeros_like(x) if forces else None
+    FT = {k: torch.zeros_like(x) for k in TERMS} if (forces and per_term) else None
+    E = {k: 0.0 for k in TERMS}
+
+    def acc(e, name):
+        E[name] += float(e.detach()) if torch.is_tensor(e) else float(e)
+
+    def add_grad(e, name=None, retain=False):
+        if forces and e.requires_grad:
+            g, = torch.autograd.grad(e, [x], allow_unused=True, retain_graph=retain)
+            if g is not None:
+                F.sub_(g)
+                if FT is not None and name is not None:
+                    FT[name].sub_(g)
+
+    # ---- real-space pair terms --------------------------------------------
+    for i, j, sh in st.chunks(chunk):
+        S = build_sites(x, st.mp, P)
+        e_el, e_pen = tm.elec_pen_pairs(S, i, j, sh, P, st.rc, st.alpha)
+        e_rep = tm.rep_pairs(S, i, j, sh, P, st.rc)
+        e_d, e_xd = tm.disp_pairs(S, i, j, sh, P, st.rc)
+        acc(e_el, "elec"); acc(e_pen, "pen"); acc(e_rep, "rep"); acc(e_d, "disp"); acc(e_xd, "xdisp")
+        if FT is None:
+            add_grad(e_el + e_pen + e_rep + e_d + e_xd)
+        else:
+            for e, nm in ((e_el, "elec"), (e_pen, "pen"), (e_rep, "rep"), (e_d, "disp"), (e_xd, "xdisp")):
+                add_grad(e, nm, retain=True)
+
+    # ---- reciprocal, self and intramolecular corrections --------------------
+    Psi_perm = None
+    if st.periodic:
+        S = build_sites(x, st.mp, P)
+        e_corr, Q = tm.elec_periodic_corrections(S, P, st.alpha, st.G, st.box, st.K, st.order)
+        acc(e_corr, "elec")
+        add_grad(e_corr, "elec")
+        Psi_perm = ew.convolve(Q, st.G).detach()
+
+    # ---- potential on the lone pairs, charge transfer -----------------------
+    def lp_potential(xx, S=None):
+        S = build_sites(xx, st.mp, P) if S is None else S
+        V = torch.zeros((M, 2), dtype=DT)
+        for i, j, sh in st.chunks(chunk):
+            V = V + tm.lp_potential_pairs(S, i, j, sh, P, st.rc, st.alpha)
+        if st.periodic:
+            S2 = build_sites(xx, st.mp, P)
+            Qp = ew.spread(S2["x"].reshape(-1, 3), S2["q"].reshape(-1), S2["mu"].reshape(-1, 3),
+                           S2["th"].reshape(-1, 3, 3), st.box, st.K, st.order)
+            V = V + tm.lp_potential_periodic(S2, P, st.alpha, ew.convolve(Qp, st.G), st.box, st.K, st.order)
+        return V
+
+    with torch.no_grad():
+        V_lp = lp_potential(x.detach())
+    Vleaf = V_lp.clone().requires_grad_(True)
+    e_ct = 0.0
+    min_de = math.inf
+    lam = torch.zeros_like(V_lp)
+    for i, j, sh in st.chunks(chunk):
+        S = build_sites(x, st.mp, P)
+        Vint = tm.v_int(S, P)
+        e, mde = tm.ct_pairs(S, Vleaf, Vint, i, j, sh, P, st.rc)
+        min_de = min(min_de, mde)
+        e_ct += float(e.detach())
+        if e.requires_grad:
+            if forces:
+                gx, gv = torch.autograd.grad(e, [x, Vleaf], allow_unused=True)
+                if gx is not None:
+                    F.sub_(gx)
+                    if FT is not None:
+                        FT["ct"].sub_(gx)
+            else:
+                gv, = torch.autograd.grad(e, [Vleaf], allow_unused=True)
+            if gv is not None:
+                lam += gv
+    E["ct"] = e_ct
+    if forces and float(lam.abs().sum()) > 0:
+        add_grad((lam.detach() * lp_potential(x)).sum(), "ct")
+
+    # ---- polarization ---------------------------------------------------------
+    a_pol = tm.site_tables(P)["alpha_pol"]
+
+    def linear(xx, mu):
+        S = build_sites(xx, st.mp, P)
+        e = 0.0
+        for i, j, sh in st.chunks(chunk):
+            e = e + tm.pol_linear_pairs(S, mu, i, j, sh, P, st.rc, st.alpha)
+        if st.periodic:
+            e = e + tm.pol_periodic_linear(S, mu, P, st.alpha, Psi_perm_of(xx), st.box, st.K, st.order)
+        return e
+
+    def quadratic(xx, mu):
+        S = build_sites(xx, st.mp, P)
+        e = tm.pol_diag(mu, P)
+        for i, j, sh in st.chunks(chunk):
+            e = e + tm.pol_quadratic_pairs(S, mu, i, j, sh, P, st.rc, st.alpha)
+        if st.periodic:
+            e = e + tm.pol_periodic_quadratic(S, mu, P, st.alpha, st.G, st.box, st.K, st.order)
+        return e
+
+    def Psi_perm_of(xx):
+        if not xx.requires_grad:
+            return Psi_perm
+        S = build_sites(xx, st.mp, P)
+        Qp = ew.spread(S["x"].reshape(-1, 3), S["q"].reshape(-1), S["mu"].reshape(-1, 3),
+                       S["th"].reshape(-1, 3, 3), st.box, st.K, st.order)
+        return ew.convolve(Qp, st.G)
+
+    xd = x.detach()
+    # E_perm = -d(-mu.E)/dmu ; T p = d(1/2 p.T.p)/dp   (both divided by ke below)
+    mu0 = torch.zeros((M, 3, 3), dtype=DT, requires_grad=True)
+    Efield = -_grad(linear(xd, mu0), [mu0])[0] / P["ke"]
+
+    def matvec(p):
+        pp = p.detach().clone().requires_grad_(True)
+        return _grad(quadratic(xd, pp), [pp])[0] / P["ke"]
+
+    debye = P["debye"]
+    mu = (a_pol[None, :, None] * Efield) if mu_guess is None else torch.as_tensor(mu_guess, dtype=DT).clone()
+    r = Efield - matvec(mu)
+    z = a_pol[None, :, None] * r
+
+    def resid_D(rv):
+        return float(torch.sqrt(((a_pol[None, :, None] * rv) ** 2).sum(-1).mean())) * debye
+
+    p = z.clone()
+    rz = float((r * z).sum())
+    it = 0
+    res = resid_D(r)
+    while res > tol_D and it < max_iter:
+        Ap = matvec(p)
+        step = rz / float((p * Ap).sum())
+        mu = mu + step * p
+        r = r - step * Ap
+        z = a_pol[None, :, None] * r
+        rz_new = float((r * z).sum())
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        it += 1
+        res = resid_D(r)
+        if pcg_log is not None:
+            pcg_log.append(res)
+    E["pol"] = -0.5 * P["ke"] * float((mu * Efield).sum())
+    if forces:
+        mud = mu.detach()
+        add_grad(quadratic(x, mud) + linear(x, mud), "pol")
+
+    E["total"] = sum(E[k] for k in TERMS)
+    return {
+        "terms": E,
+        "forces": F.detach().numpy() if forces else None,
+        "forces_per_term": {k: v.numpy() for k, v in FT.items()} if FT is not None else None,
+        "mu": mu.detach().numpy(),
+        "efield": Efield.detach().numpy(),
+        "v_lp": V_lp.detach().numpy(),
+        "iters": it,
+        "resid_D": res,
+        "min_ct_denominator": min_de,
+        "pol_ops": ({"matvec": matvec, "alpha": a_pol,
+                     "functional": lambda m: float(quadratic(xd, m) + linear(xd, m)) / P["ke"]}
+                    if keep_operators else None),
+    }
+
+
+def energy_only(system, opts=None, **kw):
+    """Total energy with a tightly converged polarization (for finite differences)."""
+    out = evaluate(system, opts, forces=False, **kw)
+    return out["terms"]["total"], out
+
+
+def timed_evaluate(system, opts, **kw):
+    t0 = time.perf_counter()
+    out = evaluate(system, opts, **kw)
+    return out, time.perf_counter() - t0
