@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""SIBFA energy + force benchmark on one GB300 (or N independent replicas).
+
+Workload: the 4096-water box (12,288 atoms, 49.66 A, rc 9 A, SPME 64^3 order
+5, alpha 0.4 A^-1), mixed precision (FP32 pair and grid arithmetic, FP64
+accumulation and solver scalars), PCG tolerance 1e-6 D with warm start,
+velocity-Verlet NVE at 0.5 fs from 300 K Maxwell velocities.  A step is one
+velocity-Verlet step: one full energy + force evaluation (sites, neighbour
+list, real-space pair terms, SPME, charge transfer, polarization solve,
+forces) plus the two half kicks.  Metric: atom-steps/s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun with N ranks every rank runs its own replica (weak scaling;
+the method has no cross-replica exchange), rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom-steps/s SIBFA E+F (SPME+pol) vs FP64 GPU path; served p50/p99 latency"
+UNIT = "atom-steps/s"
+WORKLOAD = ("water4096: 4096 rigid-geometry waters (12,288 atoms), cubic box 49.66 A, rc 9 A, SPME 64^3 order 5, "
+            "alpha 0.4/A, PCG 1e-6 D warm start, velocity-Verlet NVE 0.5 fs from 300 K")
+SAMPLE = ("oracle sample: 512 waters (1,536 atoms) at the same density, rc 9 A, SPME 32^3 (1.29 points/A, as 64^3 "
+          "on 49.66 A) order 5, alpha 0.4, PCG 1e-6 D; one full energy + force evaluation per step")
+FP32_LANES_PER_SM = 128
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+
+# Algorithmic FP32 operations per unit of the real-space permanent kernel
+# (counted from the formulas).
+FLOPS_PERM_SITE_PAIR = 380      # multipole-multipole pair: erfc kernel g0..g5, field to d2, energy, gradient with d3
+FLOPS_PEN_PAIR = 190            # penetration of a pair with at least one atom site
+FLOPS_THOLE_PAIR = 130          # Thole-damped field of a site at a polarizable atom
+FLOPS_LP_PAIR = 110             # potential and gradient of a site at a lone pair
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def count_units(pos, box, rc, mp_points):
+    """Pairs evaluated by the real-space permanent kernel: (site, site),
+    (atom, site) and (lone pair, site) intermolecular pairs within rc, and the
+    number of those that carry a penetration correction."""
+    M = pos.shape[0]
+    sites = mp_points[:, :5]
+    lps = mp_points[:, 5:7]
+    O = pos[:, 0]
+    n_ss = n_pen = n_th = n_lp = 0
+    L = np.asarray(box)
+    is_atom = np.array([1, 1, 1, 0, 0], bool)
+    for i0 in range(0, M, 128):
+        i1 = min(M, i0 + 128)
+        d = O[None, :, :] - O[i0:i1, None, :]
+        d -= L * np.round(d / L)
+        near = np.einsum("ijk,ijk->ij", d, d) < (rc + 2.6) ** 2
+        for a in range(i1 - i0):
+            i = i0 + a
+            js = np.nonzero(near[a])[0]
+            js = js[js != i]
+            sh = (d[a, js] - (O[js] - O[i]))[:, None, :]
+            sj = sites[js] + sh                                   # (n,5,3)
+            r = np.linalg.norm(sites[i][:, None, None, :] - sj[None], axis=-1)   # (5,n,5)
+            inr = r < rc
+            n_ss += int(inr.sum())
+            pen = (is_atom[:, None, None] | is_atom[None, None, :])
+            n_pen += int((inr & pen).sum())
+            n_th += int(inr[:3].sum())
+            rl = np.linalg.norm(lps[i][:, None, None, :] - sj[None], axis=-1)
+            n_lp += int((rl < rc).sum())
+    return n_ss, n_pen, n_th, n_lp
+
+
+def points_from_pos(pos, P):
+    """Absolute site and lone-pair positions (for counting units only)."""
+    O, H1, H2 = pos[:, 0], pos[:, 1], pos[:, 2]
+    u1 = (H1 - O) / np.linalg.norm(H1 - O, axis=-1, keepdims=True)
+    u2 = (H2 - O) / np.linalg.norm(H2 - O, axis=-1, keepdims=True)
+    z = u1 + u2
+    z /= np.linalg.norm(z, axis=-1, keepdims=True)
+    x = (H1 - O) - ((H1 - O) * z).sum(-1, keepdims=True) * z
+    x /= np.linalg.norm(x, axis=-1, keepdims=True)
+    y = np.cross(z, x)
+    th = math.radians(P["lp_half_deg"])
+    d = P["d_lp"]
+    lp1 = O + d * (-math.cos(th) * z + math.sin(th) * y)
+    lp2 = O + d * (-math.cos(th) * z - math.sin(th) * y)
+    return np.stack([O, H1, H2, 0.5 * (O + H1), 0.5 * (O + H2), lp1, lp2], 1)
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend)
+        return dist, rank, ws
+    return None, 0, 1
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sample_system():
+    import synth
+    s = synth.make_box(8, 24.83, seed=2)
+    return s, {"rc": 9.0, "grid": 32, "order": 5, "ewald": 0.4}
+
+
+def cpu_baseline(steps=1):
+    import torch
+    import oracle
+    s, o = sample_system()
+    t = time.perf_counter()
+    for _ in range(steps):
+        oracle.evaluate(s, o, tol_D=1e-6)
+    dt = time.perf_counter() - t
+    return {"value": s.n_atoms * steps / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": SAMPLE, "seconds": dt}
+
+
+def run_reference(args, dist, rank, ws):
+    if rank != 0:
+        return
+    import torch
+    import oracle
+    s, o = sample_system()
+    for _ in range(args.warmup):
+        oracle.evaluate(s, o, tol_D=1e-6)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.evaluate(s, o, tol_D=1e-6)
+    dt = time.perf_counter() - t
+    v = s.n_atoms * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": SAMPLE},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": SAMPLE},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    dist, rank, ws = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, dist, rank, ws)
+        return
+    import torch
+
+    import synth
+    import paper_2201_00804_gb300 as pkg
+    from paper_2201_00804_gb300 import build
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    s, o = synth.make_config("water4096")
+    M = s.n_mol
+    stream = torch.cuda.current_stream()
+    ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
+                           ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"], precision=pkg.PREC_MIXED,
+                           warm_start=True, stream=stream)
+    pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
+    vel = torch.tensor(synth.maxwell_velocities(s, 300.0, seed=2).reshape(-1), dtype=torch.float64, device="cuda")
+    masses = torch.tensor(s.masses().reshape(-1), dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    dt_fs = 0.5
+
+    for _ in range(max(3, args.warmup)):
+        pkg.sibfa_md_steps(ctx, pos, vel, masses, dt_fs, 1)
+    torch.cuda.synchronize()
+    pkg.sibfa_set_profiling(ctx, True)
+    pkg.sibfa_profile_clear(ctx)
+    l0 = pkg.sibfa_kernel_launches(ctx)
+    iters = []
+    total_ms = 0.0
+    barrier(dist)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()                       # evict L2 (512 MB > 129 MB) before every timed step
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pkg.sibfa_md_steps(ctx, pos, vel, masses, dt_fs, 1)
+            b.record(stream)
+            b.synchronize()
+            total_ms += a.elapsed_time(b)
+            iters.append(pkg.sibfa_last_stats(ctx)[0])
+    torch.cuda.synchronize()
+    barrier(dist)
+    launches = pkg.sibfa_kernel_launches(ctx) - l0
+    phases = {}
+    for name in ("sites", "neighbors", "real_perm", "short", "spme_perm", "ct", "pcg", "real_tmu", "real_polforce",
+                 "spme_polforce", "finalize"):
+        ms, n = pkg.sibfa_profile_get(ctx, name)
+        phases[name] = {"ms_per_step": ms / args.steps, "launches": n}
+    pkg.sibfa_set_profiling(ctx, False)
+    step_ms = max_over_ranks(dist, total_ms) / args.steps
+    value = ws * 3 * M / (step_ms / 1000.0)
+
+    # roofline of the real-space permanent kernel (one launch per step)
+    P = synth.PARAMS
+    pos_h = pos.cpu().numpy().reshape(M, 3, 3)
+    pts = points_from_pos(pos_h, P)
+    n_ss, n_pen, n_th, n_lp = count_units(pos_h, s.box, o["rc"], pts)
+    flops = (n_ss * FLOPS_PERM_SITE_PAIR + n_pen * FLOPS_PEN_PAIR + n_th * FLOPS_THOLE_PAIR
+             + n_lp * FLOPS_LP_PAIR)
+    rp_ms = phases["real_perm"]["ms_per_step"]
+    achieved = flops / (rp_ms * 1e-3) / 1e12
+    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": "k_real_perm", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "units": {"site_pairs": n_ss, "penetration_pairs": n_pen, "thole_pairs": n_th, "lp_pairs": n_lp},
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived, not measured)"}
+
+    # end to end through the C ABI with host buffers: H2D positions, D2H forces and energies
+    pos_host = pos.cpu().numpy().copy()
+    vel_host = vel.cpu().numpy().copy()
+    inv_m = 1.0 / s.masses().reshape(-1).repeat(3)
+    F_host = np.zeros_like(pos_host)
+    pkg.sibfa_energy_forces(ctx, pos_host, F_host)
+    e2e_s = 0.0
+    conv = 4.184e-4
+    for _ in range(args.steps):
+        vel_host += 0.5 * dt_fs * F_host * inv_m * conv
+        pos_host += dt_fs * vel_host
+        t = time.perf_counter()
+        pkg.sibfa_energy_forces(ctx, pos_host, F_host)
+        e2e_s += time.perf_counter() - t
+        vel_host += 0.5 * dt_fs * F_host * inv_m * conv
+    e2e_s = max_over_ranks(dist, e2e_s)
+    e2e = {"value": ws * 3 * M * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(pos_host.nbytes),
+           "d2h_bytes_per_step": int(F_host.nbytes + 8 * 8 + 4)}
+    pkg.sibfa_destroy(ctx)
+
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "FP32 pair/grid arithmetic, FP64 accumulation",
+                   "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{ws}"},
+        "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+        "cpu_baseline": cpu, "pcg_iters_mean": float(np.mean(iters)), "phases_ms": phases,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * sibfa.h -- C ABI of the GB300 SIBFA21 water energy/force library.
+ *
+ * One call evaluates the SIBFA intermolecular potential of a set of rigid or
+ * flexible waters (Eq. 1: E_inter = E_elec+pen + E_rep + E_pol + E_ct +
+ * E_disp,xdisp) and its analytic gradient.  The terms and where they are
+ * defined:
+ *   - multipolar electrostatics to quadrupoles with the charge-charge*,
+ *     charge-dipole* and charge-quadrupole* penetration corrections (Eq. 2,
+ *     section "Multipolar Electrostatics including Short-Range Penetration");
+ *   - exchange-repulsion over bond-bond, bond-lone pair and lone pair-lone
+ *     pair overlaps (Eq. 3 and Technical Appendix, exchange-repulsion);
+ *   - many-body polarization, E_pol = 1/2 mu T mu - mu E solved by a
+ *     preconditioned conjugate gradient on T mu = E (Technical Appendix,
+ *     polarization; Computational Details);
+ *   - the reduced many-body charge transfer (Eqs. 13-16);
+ *   - C6/C8/C10 dispersion with exchange-dispersion (Technical Appendix);
+ *   - periodic systems use smooth particle mesh Ewald of order 5 for the
+ *     multipoles and the induced dipoles (Computational Details).
+ * Units: kcal/mol, Angstrom, elementary charge; dipoles in e.A, tolerances
+ * in Debye (4.80321 D per e.A).
+ *
+ * Memory and errors.  The library owns the context and every device buffer
+ * it allocates at sibfa_create.  The caller owns all input and output
+ * arrays; they may be host or device pointers (detected per call).  Device
+ * pointers are read and written on the context's stream; host pointers are
+ * staged through the context's pinned buffers and the call returns after the
+ * results are in host memory.  No call throws; every call returns a status
+ * and sibfa_last_error() gives a one-line reason for the last failure.
+ */
+#ifndef SIBFA_H
+#define SIBFA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SIBFA_OK = 0,
+    SIBFA_E_INVALID = -1,        /* bad argument or inconsistent sizes          */
+    SIBFA_E_OOM = -2,            /* device or host allocation failed            */
+    SIBFA_E_NOT_CONVERGED = -3,  /* PCG hit max_iter above the tolerance        */
+    SIBFA_E_CUTOFF = -4,         /* rc + 2 * site extent exceeds half the box   */
+    SIBFA_E_CT_DENOM = -5,       /* a charge-transfer denominator dE <= 0       */
+    SIBFA_E_TIMEOUT = -6,        /* a bounded device wait gave up               */
+    SIBFA_E_CUDA = -7,           /* a CUDA / cuFFT call failed                  */
+    SIBFA_E_BUSY = -8,           /* admission refused (serving)                 */
+    SIBFA_E_NEIGHBOR = -9        /* neighbour list overflow                     */
+} sibfa_status;
+
+/* Energy components (kcal/mol), in the order of Eq. 1; elec holds the
+ * multipolar part, pen the penetration correction. */
+typedef struct {
+    double elec, pen, rep, disp, xdisp, pol, ct, total;
+} sibfa_energy_terms;
+
+/* Force-field parameters (all scalars; see synth/water.py for the values).
+ * Layout is fixed; fields are read once at sibfa_create. */
+typedef struct {
+    double ke, debye;
+    double d_lp, lp_half_deg;
+    double alpha_o, alpha_h, alpha_m_damp, thole;
+    double z_o, z_h, b_o, b_h;
+    double cs_o, cp_o, cs_h, cp_h, cs_lp, cp_lp, g_o, g_h, nval_o, nval_h;
+    double rvdw_rep_o, rvdw_rep_h, rvdw_rep_lp, rep_alpha, rep_alpha2, rep_c1, rep_c2, rep_f;
+    double occ_bond, n_lp;
+    double rvdw_disp_o, rvdw_disp_h, rvdw_disp_lp, disp_alpha, beta_o, beta_h;
+    double c6, c8, c10, gamma6, gamma8, gamma10, disp_delta;
+    double xd_c1, xd_a1, xd_c2, xd_a2, xd_c3, xd_a3;
+    double ct_eta, ct_t, ct_m, ct_ae, ct_ah, rvdw_ct_o, rvdw_ct_h;
+} sibfa_params;
+
+/* Topology: n_mol waters; local-frame multipoles per molecule and site
+ * (sites O, H1, H2, M1 = midpoint O-H1, M2 = midpoint O-H2), 10 doubles per
+ * site: q, mu_x, mu_y, mu_z, Th_xx, Th_yy, Th_zz, Th_xy, Th_xz, Th_yz
+ * (traceless, potential convention phi = q/r + mu.r/r^3 + Th:rr/r^5).
+ * mp_local is a HOST pointer, n_mol*5*10 doubles, copied at create. */
+typedef struct {
+    int n_mol;
+    const double *mp_local;
+} sibfa_topology;
+
+enum { SIBFA_PREC_FP64 = 0, SIBFA_PREC_MIXED = 1 };
+
+/* Run options.  periodic = 0: gas phase, all pairs, no cutoff, no Ewald.
+ * periodic = 1: orthorhombic box, minimum image, real-space cutoff rc,
+ * SPME grid[3] of B-spline order 5 with Ewald parameter ewald_alpha.
+ * precision: SIBFA_PREC_FP64 (all FP64) or SIBFA_PREC_MIXED (FP32 pair and
+ * grid arithmetic, FP64 accumulation across pairs, FP64 PCG scalars,
+ * energies and influence function).  stream: a cudaStream_t or NULL for the
+ * legacy default stream.  warm_start: reuse the previous call's dipoles as
+ * the PCG initial guess. */
+typedef struct {
+    int periodic;
+    double box[3];
+    double rc;
+    int grid[3];
+    int order;
+    double ewald_alpha;
+    double pcg_tol_D;
+    int pcg_max_iter;
+    int precision;
+    int warm_start;
+    void *stream;
+} sibfa_run_opts;
+
+typedef struct sibfa_ctx sibfa_ctx;
+
+/* Create a context: validates sizes, copies the topology, builds the SPME
+ * influence function and FFT plans, allocates all device state.  *out is
+ * NULL on failure. */
+sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo,
+                          const sibfa_run_opts *opts, sibfa_ctx **out);
+
+/* One energy + force evaluation.  pos: n_mol*9 doubles (O, H1, H2 xyz per
+ * molecule, Angstrom).  box: 3 doubles or NULL to keep the current box.
+ * e: host struct, filled on success (may be NULL).  forces: n_mol*9 doubles
+ * (kcal/mol/A, = -dE/dx) or NULL.  virial: reserved, must be NULL. */
+sibfa_status sibfa_energy_forces(sibfa_ctx *ctx, const double *pos, const double *box,
+                                 sibfa_energy_terms *e, double *forces, double *virial);
+
+/* Solve T mu = E only (sites, permanent field, PCG).  mu: n_mol*9 doubles
+ * (induced dipoles on O, H1, H2, e.A) or NULL.  tol_D <= 0 uses the run
+ * option.  iters / resid_D may be NULL. */
+sibfa_status sibfa_solve_dipoles(sibfa_ctx *ctx, const double *pos, const double *box,
+                                 double tol_D, double *mu, int *iters, double *resid_D);
+
+/* Velocity-Verlet NVE steps on the device (support for the MD workloads):
+ * pos and vel (n_mol*9 doubles, A and A/fs) are updated in place; masses
+ * n_mol*3 doubles (amu).  Each step is one full energy + force evaluation.
+ * e (may be NULL) receives the energy of the last step. */
+sibfa_status sibfa_md_steps(sibfa_ctx *ctx, double *pos, double *vel, const double *masses,
+                            double dt_fs, int n_steps, sibfa_energy_terms *e);
+
+/* Statistics of the last evaluation: PCG iterations and final residual (D). */
+sibfa_status sibfa_last_stats(const sibfa_ctx *ctx, int *pcg_iters, double *pcg_resid_D);
+
+/* Number of the library's own kernel launches since the context was created
+ * (cuFFT executions are not counted). */
+uint64_t sibfa_kernel_launches(const sibfa_ctx *ctx);
+
+/* Optional phase timing with CUDA events recorded on the context stream
+ * around each phase of an evaluation: "sites", "neighbors", "real_perm"
+ * (permanent electrostatics + penetration + Thole field + lone-pair
+ * potential), "short" (repulsion, dispersion), "spme_perm", "ct", "pcg"
+ * (whole solve), "real_tmu" (real-space part of each T.mu product),
+ * "real_polforce", "spme_polforce", "finalize".  sibfa_profile_get returns
+ * the summed milliseconds and the number of spans of one phase recorded
+ * since the last get/clear of that phase, and synchronizes the stream. */
+void sibfa_set_profiling(sibfa_ctx *ctx, int on);
+sibfa_status sibfa_profile_get(sibfa_ctx *ctx, const char *name, double *ms, int *count);
+void sibfa_profile_clear(sibfa_ctx *ctx);
+
+void sibfa_destroy(sibfa_ctx *ctx);
+
+/* Text of the last error on this context (or of the last failed create when
+ * ctx is NULL).  Never NULL. */
+const char *sibfa_last_error(const sibfa_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIBFA_H */

@@ -252,7 +252,8 @@ def ct_pairs(S, V, Vint, i, j, sh, P, rc):
     ia, ja = torch.as_tensor(i), torch.as_tensor(j)
     e_ab, d1 = direction(A, B, V[ia], Vint[ja])
     e_ba, d2 = direction(B, A, V[ja], Vint[ia])
-    min_de = min(float(d1.min()) if d1.numel() else 1.0, float(d2.min()) if d2.numel() else 1.0)
+    min_de = min(float(d1.detach().min()) if d1.numel() else 1.0,
+                 float(d2.detach().min()) if d2.numel() else 1.0)
     return e_ab + e_ba, min_de
 
 

@@ -1,0 +1,660 @@
+// C ABI of the SIBFA library: context creation, one energy + force
+// evaluation (the order of the method: sites -> neighbour list -> real-space
+// pair terms -> SPME -> charge transfer -> polarization solve -> forces),
+// the dipole-only solve and device-side velocity-Verlet steps.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sibfa_internal.cuh"
+
+using namespace sibfa;
+
+static thread_local std::string g_create_error = "no error";
+
+struct sibfa_ctx {
+    int M = 0;
+    sibfa_run_opts opts{};
+    KParams kp{};
+    cudaStream_t s = nullptr;
+    int prec = SIBFA_PREC_MIXED;
+    DevState<float> df{};
+    DevState<double> dd{};
+    cufftHandle r2c1 = 0, c2r1 = 0, r2c2 = 0, c2r2 = 0;
+    bool have_fft = false;
+    int ncell[3] = {0, 0, 0};
+    double *d_forces = nullptr;   // M*9
+    double *d_energy = nullptr;   // NTERM+1
+    double *d_vel = nullptr, *d_invm = nullptr;
+    double *h_pin = nullptr;      // pinned staging, M*9*2 + 64 doubles
+    std::vector<void *> allocs;
+    std::string err = "no error";
+    uint64_t launches = 0;
+    int last_iters = 0;
+    double last_resid = 0;
+    bool have_mu = false;
+    bool md_forces_valid = false;
+    // optional per-phase timing with CUDA events on the context stream
+    bool profiling = false;
+    struct Span {
+        std::string name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Span> spans;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+struct Phase {
+    sibfa_ctx *ctx;
+    size_t idx = (size_t)-1;
+    Phase(sibfa_ctx *c, const char *name) : ctx(c) {
+        if (!ctx->profiling) return;
+        cudaEvent_t a, b;
+        if (ctx->event_pool.size() >= 2) {
+            a = ctx->event_pool.back();
+            ctx->event_pool.pop_back();
+            b = ctx->event_pool.back();
+            ctx->event_pool.pop_back();
+        } else {
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+        }
+        cudaEventRecord(a, ctx->s);
+        ctx->spans.push_back({name, a, b});
+        idx = ctx->spans.size() - 1;
+    }
+    ~Phase() {
+        if (idx != (size_t)-1) cudaEventRecord(ctx->spans[idx].b, ctx->s);
+    }
+};
+}  // namespace
+
+namespace {
+
+#define CK(call)                                                                    \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+            return SIBFA_E_CUDA;                                                    \
+        }                                                                           \
+    } while (0)
+
+#define CKF(call)                                                                   \
+    do {                                                                            \
+        cufftResult r_ = (call);                                                    \
+        if (r_ != CUFFT_SUCCESS) {                                                  \
+            ctx->err = std::string(#call) + ": cufft error " + std::to_string(r_); \
+            return SIBFA_E_CUDA;                                                    \
+        }                                                                           \
+    } while (0)
+
+template <typename T>
+sibfa_status dalloc(sibfa_ctx *ctx, T **p, size_t n) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, n * sizeof(T) + 16);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        return SIBFA_E_OOM;
+    }
+    cudaMemset(q, 0, n * sizeof(T) + 16);
+    ctx->allocs.push_back(q);
+    *p = (T *)q;
+    return SIBFA_OK;
+}
+
+#define AL(ptr, n)                                          \
+    do {                                                    \
+        sibfa_status st_ = dalloc(ctx, &(ptr), (size_t)(n)); \
+        if (st_ != SIBFA_OK) return st_;                    \
+    } while (0)
+
+template <typename R>
+sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
+    const int M = ctx->M;
+    d.M = M;
+    AL(d.pos, M * 9);
+    AL(d.mp_local, M * NS * NMP);
+    AL(d.off, M * NP * 3);
+    AL(d.gmp, M * NS * NMP);
+    AL(d.vint, M * 3);
+    AL(d.nbr, (size_t)M * MAXN);
+    AL(d.nnbr, M);
+    int ncell = std::max(1, ctx->ncell[0] * ctx->ncell[1] * ctx->ncell[2]);
+    AL(d.cell_of, M);
+    AL(d.cell_start, ncell + 1);
+    AL(d.cell_cursor, ncell);
+    AL(d.cell_mol, M);
+    AL(d.gpt, M * NP * 3);
+    AL(d.gmu, M * NS * 3);
+    AL(d.gth, M * NS * 6);
+    AL(d.efield, M * 9);
+    AL(d.d2rec, M * 18);
+    AL(d.vlp, M * 2);
+    AL(d.dvlp, M * 6);
+    AL(d.lam, M * 2);
+    AL(d.kap, M * 3);
+    AL(d.epart, M * NTERM);
+    AL(d.mu, M * 9);
+    AL(d.res, M * 9);
+    AL(d.zv, M * 9);
+    AL(d.pv, M * 9);
+    AL(d.ap, M * 9);
+    AL(d.efp, M * 9);
+    AL(d.partial, 2 * ((M * 9 + 255) / 256) + 64);
+    AL(d.scal, 32);
+    AL(d.counter, 4);
+    AL(d.flags, 4);
+    AL(d.ext, 4);
+    if (ctx->opts.periodic) {
+        const size_t ng = (size_t)ctx->kp.K[0] * ctx->kp.K[1] * ctx->kp.K[2];
+        const size_t nh = (size_t)ctx->kp.K[0] * ctx->kp.K[1] * (ctx->kp.K[2] / 2 + 1);
+        AL(d.grid, 2 * ng);
+        if (sizeof(R) == 4) {
+            cufftComplex *c;
+            AL(c, 2 * nh);
+            d.cgrid = c;
+        } else {
+            cufftDoubleComplex *c;
+            AL(c, 2 * nh);
+            d.cgrid = c;
+        }
+        AL(d.infl, nh);
+    }
+    return SIBFA_OK;
+}
+
+void fill_params(KParams &k, const sibfa_params &P, const sibfa_run_opts &o, int M) {
+    k.M = M;
+    k.periodic = o.periodic;
+    for (int i = 0; i < 3; ++i) k.box[i] = o.box[i];
+    k.rc = o.rc;
+    k.rc2 = o.rc * o.rc;
+    k.alpha = o.ewald_alpha;
+    for (int i = 0; i < 3; ++i) k.K[i] = o.grid[i];
+    k.ke = P.ke;
+    k.d_lp = P.d_lp;
+    const double th = P.lp_half_deg * M_PI / 180.0;
+    k.lp_cos = cos(th);
+    k.lp_sin = sin(th);
+    k.a_pol[0] = P.alpha_o;
+    k.a_pol[1] = k.a_pol[2] = P.alpha_h;
+    k.a_damp[0] = P.alpha_o;
+    k.a_damp[1] = k.a_damp[2] = P.alpha_h;
+    k.a_damp[3] = k.a_damp[4] = P.alpha_m_damp;
+    k.thole = P.thole;
+    k.z[0] = P.z_o;
+    k.z[1] = k.z[2] = P.z_h;
+    k.z[3] = k.z[4] = 0.0;
+    k.b[0] = P.b_o;
+    k.b[1] = k.b[2] = P.b_h;
+    k.b[3] = k.b[4] = 0.0;
+    k.cs_o = P.cs_o; k.cp_o = P.cp_o; k.cs_h = P.cs_h; k.cp_h = P.cp_h; k.cs_lp = P.cs_lp; k.cp_lp = P.cp_lp;
+    k.g_o = P.g_o; k.g_h = P.g_h; k.nval_o = P.nval_o; k.nval_h = P.nval_h;
+    k.rv_rep_o = P.rvdw_rep_o; k.rv_rep_h = P.rvdw_rep_h; k.rv_rep_lp = P.rvdw_rep_lp;
+    k.rep_a1 = P.rep_alpha; k.rep_a2 = P.rep_alpha2; k.rep_c1 = P.rep_c1; k.rep_c2 = P.rep_c2; k.rep_f = P.rep_f;
+    k.occ = P.occ_bond; k.nlp = P.n_lp;
+    k.rv_d[0] = P.rvdw_disp_o; k.rv_d[1] = k.rv_d[2] = P.rvdw_disp_h; k.rv_d[3] = k.rv_d[4] = P.rvdw_disp_lp;
+    k.beta[0] = P.beta_o; k.beta[1] = k.beta[2] = P.beta_h; k.beta[3] = k.beta[4] = P.beta_o;
+    k.disp_alpha = P.disp_alpha; k.c6 = P.c6; k.c8 = P.c8; k.c10 = P.c10;
+    k.g6 = P.gamma6; k.g8 = P.gamma8; k.g10 = P.gamma10; k.delta = P.disp_delta;
+    k.xd_c1 = P.xd_c1; k.xd_a1 = P.xd_a1; k.xd_c2 = P.xd_c2; k.xd_a2 = P.xd_a2; k.xd_c3 = P.xd_c3; k.xd_a3 = P.xd_a3;
+    k.ct_eta = P.ct_eta; k.ct_t = P.ct_t; k.ct_m = P.ct_m; k.ct_ae = P.ct_ae; k.ct_ah = P.ct_ah;
+    k.rv_ct_o = P.rvdw_ct_o; k.rv_ct_h = P.rvdw_ct_h;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename R>
+DevState<R> &state(sibfa_ctx *ctx);
+template <>
+DevState<float> &state<float>(sibfa_ctx *ctx) { return ctx->df; }
+template <>
+DevState<double> &state<double>(sibfa_ctx *ctx) { return ctx->dd; }
+
+template <typename R>
+sibfa_status fft(sibfa_ctx *ctx, DevState<R> &d, bool forward, int ngrid) {
+    if (sizeof(R) == 4) {
+        if (forward) CKF(cufftExecR2C(ngrid == 1 ? ctx->r2c1 : ctx->r2c2, (cufftReal *)d.grid, (cufftComplex *)d.cgrid));
+        else CKF(cufftExecC2R(ngrid == 1 ? ctx->c2r1 : ctx->c2r2, (cufftComplex *)d.cgrid, (cufftReal *)d.grid));
+    } else {
+        if (forward)
+            CKF(cufftExecD2Z(ngrid == 1 ? ctx->r2c1 : ctx->r2c2, (cufftDoubleReal *)d.grid, (cufftDoubleComplex *)d.cgrid));
+        else
+            CKF(cufftExecZ2D(ngrid == 1 ? ctx->c2r1 : ctx->c2r2, (cufftDoubleComplex *)d.cgrid, (cufftDoubleReal *)d.grid));
+    }
+    return SIBFA_OK;
+}
+
+// T vec (field part) into d.efp: real space + reciprocal + intramolecular
+template <typename R>
+sibfa_status matvec(sibfa_ctx *ctx, DevState<R> &d, const double *vec, Launch L) {
+    const KParams &p = ctx->kp;
+    { Phase ph(ctx, "real_tmu");  launch_real_tmu(p, d, vec, d.efp, L); }
+    if (p.periodic) {
+        const size_t ng = (size_t)p.K[0] * p.K[1] * p.K[2];
+        CK(cudaMemsetAsync(d.grid, 0, ng * sizeof(R), ctx->s));
+        launch_spread(p, d, SPREAD_DIP_PCG, vec, d.grid, L);
+        sibfa_status st = fft(ctx, d, true, 1);
+        if (st) return st;
+        launch_convolve(p, d, d.cgrid, 1, 1, L);
+        st = fft(ctx, d, false, 1);
+        if (st) return st;
+        launch_gather_field(p, d, d.efp, L);
+        launch_intra_tmu(p, d, vec, d.efp, L);
+    }
+    return SIBFA_OK;
+}
+
+template <typename R>
+sibfa_status solve(sibfa_ctx *ctx, DevState<R> &d, double tol, Launch L) {
+    const KParams &p = ctx->kp;
+    const int warm = (ctx->opts.warm_start && ctx->have_mu) ? 1 : 0;
+    launch_pcg_init(p, d, warm, L);
+    sibfa_status st = matvec(ctx, d, d.mu, L);
+    if (st) return st;
+    launch_pcg_first(p, d, L);
+    double *h = ctx->h_pin;
+    int it = 0;
+    const int maxit = ctx->opts.pcg_max_iter > 0 ? ctx->opts.pcg_max_iter : 200;
+    for (;;) {
+        CK(cudaMemcpyAsync(h, d.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        if (h[SC_DONE] != 0.0 || it >= maxit) break;
+        st = matvec(ctx, d, d.pv, L);
+        if (st) return st;
+        launch_pcg_iter_a(p, d, L);
+        launch_pcg_iter_b(p, d, tol, L);
+        ++it;
+    }
+    ctx->last_iters = (int)h[SC_IT];
+    ctx->last_resid = h[SC_RES];
+    ctx->have_mu = true;
+    if (h[SC_DONE] == 0.0) {
+        ctx->err = "PCG did not reach the tolerance within pcg_max_iter";
+        return SIBFA_E_NOT_CONVERGED;
+    }
+    return SIBFA_OK;
+}
+
+// One evaluation on the positions already in d.pos.
+template <typename R>
+sibfa_status evaluate(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, double tol) {
+    DevState<R> &d = state<R>(ctx);
+    const KParams &p = ctx->kp;
+    Launch L{ctx->s, &ctx->launches};
+    launch_begin(d.scal, d.flags, tol, L);
+    { Phase ph(ctx, "sites");  launch_sites(p, d, L); }
+    { Phase ph(ctx, "neighbors");  launch_neighbors(p, d, ctx->ncell, L); }
+    { Phase ph(ctx, "real_perm");  launch_real_perm(p, d, L); }
+    if (!dipoles_only) { Phase ph(ctx, "short");  launch_short(p, d, L); }
+    const size_t ng = (size_t)p.K[0] * p.K[1] * p.K[2];
+    sibfa_status st;
+    if (p.periodic) {
+        Phase ph(ctx, "spme_perm");
+        CK(cudaMemsetAsync(d.grid, 0, ng * sizeof(R), ctx->s));
+        launch_spread(p, d, SPREAD_PERM, nullptr, d.grid, L);
+        if ((st = fft(ctx, d, true, 1))) return st;
+        launch_convolve(p, d, d.cgrid, 1, 0, L);
+        if ((st = fft(ctx, d, false, 1))) return st;
+        launch_gather_perm(p, d, L);
+        launch_intra_perm(p, d, L);
+    }
+    if (!dipoles_only) { Phase ph(ctx, "ct");  launch_ct(p, d, L); }
+    {
+        Phase ph(ctx, "pcg");
+        st = solve(ctx, d, tol, L);
+    }
+    if (st == SIBFA_E_CUDA) return st;
+    sibfa_status st_solve = st;
+    if (dipoles_only) return st_solve;
+    launch_pol_energy(p, d, L);
+    if (want_forces) {
+        { Phase ph(ctx, "real_polforce");  launch_real_polforce(p, d, L); }
+        if (p.periodic) {
+            Phase ph(ctx, "spme_polforce");
+            CK(cudaMemsetAsync(d.grid, 0, 2 * ng * sizeof(R), ctx->s));
+            launch_spread(p, d, SPREAD_DIP, d.mu, d.grid, L);
+            launch_spread(p, d, SPREAD_LAMBDA, nullptr, d.grid + ng, L);
+            if ((st = fft(ctx, d, true, 2))) return st;
+            launch_convolve(p, d, d.cgrid, 2, 0, L);
+            if ((st = fft(ctx, d, false, 2))) return st;
+            launch_gather_polforce(p, d, L);
+            launch_intra_polforce(p, d, L);
+        }
+        { Phase ph(ctx, "finalize");  launch_finalize(p, d, ctx->d_forces, L); }
+    }
+    launch_energy_reduce(p.M, d.epart, ctx->d_energy, L);
+    return st_solve;
+}
+
+sibfa_status check_flags(sibfa_ctx *ctx, int flags) {
+    if (flags & F_CUTOFF) {
+        ctx->err = "cutoff plus twice the site extent exceeds half the box (or a site is > 1.3 A from its O)";
+        return SIBFA_E_CUTOFF;
+    }
+    if (flags & F_NEIGHBOR) {
+        ctx->err = "neighbour list overflow";
+        return SIBFA_E_NEIGHBOR;
+    }
+    if (flags & F_CTDEN) {
+        ctx->err = "charge-transfer denominator ae + V - ah <= 0";
+        return SIBFA_E_CT_DENOM;
+    }
+    return SIBFA_OK;
+}
+
+template <typename R>
+sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_energy_terms *e, double *forces,
+                 bool dipoles_only, double tol, double *mu_out, int *iters, double *resid) {
+    DevState<R> &d = state<R>(ctx);
+    const int M = ctx->M;
+    const size_t nb = (size_t)M * 9 * sizeof(double);
+    if (box) {
+        for (int k = 0; k < 3; ++k)
+            if (box[k] != ctx->kp.box[k]) {
+                ctx->err = "changing the box after create is not supported";
+                return SIBFA_E_INVALID;
+            }
+    }
+    if (pos) {
+        if (is_device_ptr(pos)) {
+            CK(cudaMemcpyAsync(d.pos, pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
+        } else {
+            CK(cudaStreamSynchronize(ctx->s));
+            std::memcpy(ctx->h_pin, pos, nb);
+            CK(cudaMemcpyAsync(d.pos, ctx->h_pin, nb, cudaMemcpyHostToDevice, ctx->s));
+        }
+    }
+    ctx->md_forces_valid = false;
+    sibfa_status st = evaluate<R>(ctx, forces != nullptr, dipoles_only, tol);
+    if (st == SIBFA_E_CUDA) return st;
+    double *h = ctx->h_pin;
+    // results: energies + flags (+ dipoles) to pinned memory
+    CK(cudaMemcpyAsync(h, ctx->d_energy, (NTERM + 1) * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaMemcpyAsync((int *)(h + 16), d.flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    if (forces) {
+        if (is_device_ptr(forces)) {
+            CK(cudaMemcpyAsync(forces, ctx->d_forces, nb, cudaMemcpyDeviceToDevice, ctx->s));
+        } else {
+            CK(cudaMemcpyAsync(h + 32, ctx->d_forces, nb, cudaMemcpyDeviceToHost, ctx->s));
+        }
+    }
+    if (mu_out) {
+        if (is_device_ptr(mu_out)) CK(cudaMemcpyAsync(mu_out, d.mu, nb, cudaMemcpyDeviceToDevice, ctx->s));
+        else CK(cudaMemcpyAsync(h + 32, d.mu, nb, cudaMemcpyDeviceToHost, ctx->s));
+    }
+    CK(cudaStreamSynchronize(ctx->s));
+    CK(cudaGetLastError());
+    if (forces && !is_device_ptr(forces)) std::memcpy(forces, h + 32, nb);
+    if (mu_out && !is_device_ptr(mu_out)) std::memcpy(mu_out, h + 32, nb);
+    sibfa_status fl = check_flags(ctx, *(int *)(h + 16));
+    if (fl) return fl;
+    if (e) {
+        e->elec = h[T_ELEC];
+        e->pen = h[T_PEN];
+        e->rep = h[T_REP];
+        e->disp = h[T_DISP];
+        e->xdisp = h[T_XDISP];
+        e->pol = h[T_POL];
+        e->ct = h[T_CT];
+        e->total = h[NTERM];
+    }
+    if (iters) *iters = ctx->last_iters;
+    if (resid) *resid = ctx->last_resid;
+    return st;
+}
+
+template <typename R>
+sibfa_status create_impl(sibfa_ctx *ctx, const sibfa_topology *topo) {
+    const int M = ctx->M;
+    sibfa_status st = alloc_state<R>(ctx, state<R>(ctx));
+    if (st) return st;
+    DevState<R> &d = state<R>(ctx);
+    CK(cudaMemcpy(d.mp_local, topo->mp_local, (size_t)M * NS * NMP * sizeof(double), cudaMemcpyHostToDevice));
+    if (ctx->opts.periodic) {
+        Launch L{ctx->s, &ctx->launches};
+        launch_influence(ctx->kp, d.infl, L);
+        int n[3] = {ctx->kp.K[0], ctx->kp.K[1], ctx->kp.K[2]};
+        const bool f32 = sizeof(R) == 4;
+        const int ng = n[0] * n[1] * n[2], nh = n[0] * n[1] * (n[2] / 2 + 1);
+        CKF(cufftPlan3d(&ctx->r2c1, n[0], n[1], n[2], f32 ? CUFFT_R2C : CUFFT_D2Z));
+        CKF(cufftPlan3d(&ctx->c2r1, n[0], n[1], n[2], f32 ? CUFFT_C2R : CUFFT_Z2D));
+        CKF(cufftPlanMany(&ctx->r2c2, 3, n, nullptr, 1, ng, nullptr, 1, nh, f32 ? CUFFT_R2C : CUFFT_D2Z, 2));
+        CKF(cufftPlanMany(&ctx->c2r2, 3, n, nullptr, 1, nh, nullptr, 1, ng, f32 ? CUFFT_C2R : CUFFT_Z2D, 2));
+        CKF(cufftSetStream(ctx->r2c1, ctx->s));
+        CKF(cufftSetStream(ctx->c2r1, ctx->s));
+        CKF(cufftSetStream(ctx->r2c2, ctx->s));
+        CKF(cufftSetStream(ctx->c2r2, ctx->s));
+        ctx->have_fft = true;
+    }
+    CK(cudaStreamSynchronize(ctx->s));
+    return SIBFA_OK;
+}
+
+}  // namespace
+
+template <typename R>
+static sibfa_status md_impl(sibfa_ctx *ctx, double *pos, double *vel, const double *masses, double dt, int n,
+                            sibfa_energy_terms *e) {
+    DevState<R> &d = state<R>(ctx);
+    const int M = ctx->M;
+    const size_t nb = (size_t)M * 9 * sizeof(double);
+    if (!is_device_ptr(pos) || !is_device_ptr(vel) || !is_device_ptr(masses)) {
+        ctx->err = "sibfa_md_steps needs device pointers for pos, vel and masses";
+        return SIBFA_E_INVALID;
+    }
+    if (!ctx->d_invm) {
+        sibfa_status st = dalloc(ctx, &ctx->d_invm, (size_t)M * 3);
+        if (st) return st;
+    }
+    std::vector<double> hm(M * 3);
+    CK(cudaMemcpy(hm.data(), masses, M * 3 * sizeof(double), cudaMemcpyDeviceToHost));
+    for (auto &v : hm) v = 1.0 / v;
+    CK(cudaMemcpyAsync(ctx->d_invm, hm.data(), M * 3 * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
+    const double tol = ctx->opts.pcg_tol_D > 0 ? ctx->opts.pcg_tol_D : 1e-6;
+    Launch L{ctx->s, &ctx->launches};
+    CK(cudaMemcpyAsync(d.pos, pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
+    sibfa_status st = SIBFA_OK;
+    if (!ctx->md_forces_valid) {
+        st = evaluate<R>(ctx, true, false, tol);
+        if (st) return st;
+    }
+    for (int k = 0; k < n; ++k) {
+        launch_md_kick(M, d.pos, vel, ctx->d_invm, ctx->d_forces, dt, 1, L);
+        st = evaluate<R>(ctx, true, false, tol);
+        if (st) return st;
+        launch_md_kick(M, d.pos, vel, ctx->d_invm, ctx->d_forces, dt, 0, L);
+    }
+    CK(cudaMemcpyAsync(pos, d.pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
+    double *h = ctx->h_pin;
+    CK(cudaMemcpyAsync(h, ctx->d_energy, (NTERM + 1) * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaMemcpyAsync((int *)(h + 16), d.flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    ctx->md_forces_valid = true;
+    sibfa_status fl = check_flags(ctx, *(int *)(h + 16));
+    if (fl) return fl;
+    if (e) {
+        e->elec = h[T_ELEC]; e->pen = h[T_PEN]; e->rep = h[T_REP]; e->disp = h[T_DISP];
+        e->xdisp = h[T_XDISP]; e->pol = h[T_POL]; e->ct = h[T_CT]; e->total = h[NTERM];
+    }
+    return SIBFA_OK;
+}
+
+extern "C" {
+
+sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo, const sibfa_run_opts *opts,
+                          sibfa_ctx **out) {
+    if (out) *out = nullptr;
+    if (!params || !topo || !opts || !out || topo->n_mol <= 0 || !topo->mp_local) {
+        g_create_error = "sibfa_create: null argument or n_mol <= 0";
+        return SIBFA_E_INVALID;
+    }
+    if (opts->precision != SIBFA_PREC_FP64 && opts->precision != SIBFA_PREC_MIXED) {
+        g_create_error = "sibfa_create: unknown precision";
+        return SIBFA_E_INVALID;
+    }
+    if (opts->periodic) {
+        if (opts->order != 5 && opts->order != 0) {
+            g_create_error = "sibfa_create: only B-spline order 5 is implemented";
+            return SIBFA_E_INVALID;
+        }
+        for (int k = 0; k < 3; ++k)
+            if (!(opts->box[k] > 0) || opts->grid[k] < 8) {
+                g_create_error = "sibfa_create: box lengths must be > 0 and grid sizes >= 8";
+                return SIBFA_E_INVALID;
+            }
+        if (!(opts->rc > 0) || !(opts->ewald_alpha > 0)) {
+            g_create_error = "sibfa_create: rc and ewald_alpha must be > 0";
+            return SIBFA_E_INVALID;
+        }
+        const double half = 0.5 * std::min(opts->box[0], std::min(opts->box[1], opts->box[2]));
+        if (opts->rc + 2.0 * 0.9572 > half) {
+            g_create_error = "sibfa_create: rc + 2 * O-H distance exceeds half the box";
+            return SIBFA_E_CUTOFF;
+        }
+    }
+    sibfa_ctx *ctx = new sibfa_ctx();
+    ctx->M = topo->n_mol;
+    ctx->opts = *opts;
+    ctx->prec = opts->precision;
+    ctx->s = (cudaStream_t)opts->stream;
+    fill_params(ctx->kp, *params, *opts, ctx->M);
+    if (opts->periodic) {
+        const double cell = opts->rc + 2.6;   // rc + 2 * maximum site extent (1.3 A)
+        for (int k = 0; k < 3; ++k) ctx->ncell[k] = (int)floor(opts->box[k] / cell);
+    }
+    sibfa_status st = SIBFA_OK;
+    do {
+        st = dalloc(ctx, &ctx->d_forces, (size_t)ctx->M * 9);
+        if (st) break;
+        st = dalloc(ctx, &ctx->d_energy, 16);
+        if (st) break;
+        if (cudaMallocHost((void **)&ctx->h_pin, ((size_t)ctx->M * 9 * 2 + 64) * sizeof(double)) != cudaSuccess) {
+            ctx->err = "cudaMallocHost failed";
+            st = SIBFA_E_OOM;
+            break;
+        }
+        st = ctx->prec == SIBFA_PREC_MIXED ? create_impl<float>(ctx, topo) : create_impl<double>(ctx, topo);
+    } while (0);
+    if (st != SIBFA_OK) {
+        g_create_error = ctx->err;
+        sibfa_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return SIBFA_OK;
+}
+
+sibfa_status sibfa_energy_forces(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_energy_terms *e,
+                                 double *forces, double *virial) {
+    if (!ctx || !pos) return SIBFA_E_INVALID;
+    if (virial) {
+        ctx->err = "virial output is not implemented";
+        return SIBFA_E_INVALID;
+    }
+    const double tol = ctx->opts.pcg_tol_D > 0 ? ctx->opts.pcg_tol_D : 1e-6;
+    return ctx->prec == SIBFA_PREC_MIXED ? run<float>(ctx, pos, box, e, forces, false, tol, nullptr, nullptr, nullptr)
+                                         : run<double>(ctx, pos, box, e, forces, false, tol, nullptr, nullptr, nullptr);
+}
+
+sibfa_status sibfa_solve_dipoles(sibfa_ctx *ctx, const double *pos, const double *box, double tol_D, double *mu,
+                                 int *iters, double *resid_D) {
+    if (!ctx || !pos) return SIBFA_E_INVALID;
+    const double tol = tol_D > 0 ? tol_D : (ctx->opts.pcg_tol_D > 0 ? ctx->opts.pcg_tol_D : 1e-6);
+    return ctx->prec == SIBFA_PREC_MIXED ? run<float>(ctx, pos, box, nullptr, nullptr, true, tol, mu, iters, resid_D)
+                                         : run<double>(ctx, pos, box, nullptr, nullptr, true, tol, mu, iters, resid_D);
+}
+
+sibfa_status sibfa_md_steps(sibfa_ctx *ctx, double *pos, double *vel, const double *masses, double dt_fs, int n_steps,
+                            sibfa_energy_terms *e) {
+    if (!ctx || !pos || !vel || !masses || n_steps < 0) return SIBFA_E_INVALID;
+    return ctx->prec == SIBFA_PREC_MIXED ? md_impl<float>(ctx, pos, vel, masses, dt_fs, n_steps, e)
+                                         : md_impl<double>(ctx, pos, vel, masses, dt_fs, n_steps, e);
+}
+
+sibfa_status sibfa_last_stats(const sibfa_ctx *ctx, int *pcg_iters, double *pcg_resid_D) {
+    if (!ctx) return SIBFA_E_INVALID;
+    if (pcg_iters) *pcg_iters = ctx->last_iters;
+    if (pcg_resid_D) *pcg_resid_D = ctx->last_resid;
+    return SIBFA_OK;
+}
+
+void sibfa_set_profiling(sibfa_ctx *ctx, int on) {
+    if (!ctx) return;
+    ctx->profiling = on != 0;
+}
+
+/* Sum of the recorded phase durations (ms) and their count for `name`; the
+ * spans are consumed (their events return to the pool).  Synchronizes the
+ * context stream. */
+sibfa_status sibfa_profile_get(sibfa_ctx *ctx, const char *name, double *ms, int *count) {
+    if (!ctx || !name) return SIBFA_E_INVALID;
+    if (cudaStreamSynchronize(ctx->s) != cudaSuccess) return SIBFA_E_CUDA;
+    double tot = 0;
+    int n = 0;
+    std::vector<sibfa_ctx::Span> keep;
+    for (auto &s : ctx->spans) {
+        if (s.name == name) {
+            float t = 0;
+            cudaEventElapsedTime(&t, s.a, s.b);
+            tot += t;
+            ++n;
+            ctx->event_pool.push_back(s.a);
+            ctx->event_pool.push_back(s.b);
+        } else {
+            keep.push_back(s);
+        }
+    }
+    ctx->spans.swap(keep);
+    if (ms) *ms = tot;
+    if (count) *count = n;
+    return SIBFA_OK;
+}
+
+void sibfa_profile_clear(sibfa_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->s);
+    for (auto &s : ctx->spans) {
+        ctx->event_pool.push_back(s.a);
+        ctx->event_pool.push_back(s.b);
+    }
+    ctx->spans.clear();
+}
+
+uint64_t sibfa_kernel_launches(const sibfa_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+void sibfa_destroy(sibfa_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->s) cudaStreamSynchronize(ctx->s);
+    else cudaDeviceSynchronize();
+    if (ctx->have_fft) {
+        cufftDestroy(ctx->r2c1);
+        cufftDestroy(ctx->c2r1);
+        cufftDestroy(ctx->r2c2);
+        cufftDestroy(ctx->c2r2);
+    }
+    for (auto &s : ctx->spans) {
+        cudaEventDestroy(s.a);
+        cudaEventDestroy(s.b);
+    }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    for (void *p : ctx->allocs) cudaFree(p);
+    if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
+    delete ctx;
+}
+
+const char *sibfa_last_error(const sibfa_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,825 @@
+// Real-space pair kernels over the full molecular neighbour list.
+//
+// Every kernel walks the neighbours of one molecule i and accumulates only
+// i's quantities (energy halves, gradients of i's points, multipole
+// sensitivities of i's sites), so no two threads write the same output and
+// no atomics are needed; the neighbour list is full, each molecule pair is
+// visited from both sides.  Pair arithmetic runs in R (float in the mixed
+// path, double in the FP64 path); per-lane partial sums are reduced across
+// the warp in double.
+#include "sibfa_internal.cuh"
+
+namespace sibfa {
+
+constexpr int TILE = 32;
+
+// shared tile of neighbour molecules
+template <typename R>
+struct Tile {
+    int j[TILE];
+    R dO[TILE][3];             // O_j - O_i (minimum image)
+    R off[TILE][NP * 3];       // point offsets of j
+    R mp[TILE][NS * NMP];      // global multipoles of j
+};
+
+template <typename R>
+__device__ inline void load_tile(const KParams &p, const DevState<R> &d, int i, int base, int nn, Tile<R> &t,
+                                 bool want_mp) {
+    for (int k = threadIdx.x; k < TILE; k += blockDim.x) {
+        int slot = base + k;
+        int j = slot < nn ? d.nbr[i * MAXN + slot] : -1;
+        t.j[k] = j;
+        if (j >= 0) {
+            double dx, dy, dz;
+            min_image(p, d.pos, i, j, dx, dy, dz);
+            t.dO[k][0] = R(dx);
+            t.dO[k][1] = R(dy);
+            t.dO[k][2] = R(dz);
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < TILE * NP * 3; k += blockDim.x) {
+        int a = k / (NP * 3), b = k % (NP * 3);
+        int j = t.j[a];
+        t.off[a][b] = j >= 0 ? d.off[j * NP * 3 + b] : R(0);
+    }
+    if (want_mp)
+        for (int k = threadIdx.x; k < TILE * NS * NMP; k += blockDim.x) {
+            int a = k / (NS * NMP), b = k % (NS * NMP);
+            int j = t.j[a];
+            t.mp[a][b] = j >= 0 ? d.gmp[j * NS * NMP + b] : R(0);
+        }
+}
+
+template <typename R>
+__device__ inline V3<R> tile_pt(const Tile<R> &t, int k, int pt) {
+    return mk(t.dO[k][0] + t.off[k][pt * 3], t.dO[k][1] + t.off[k][pt * 3 + 1], t.dO[k][2] + t.off[k][pt * 3 + 2]);
+}
+
+template <typename R>
+__device__ inline V3<R> my_pt(const DevState<R> &d, int i, int pt) {
+    const R *o = d.off + (i * NP + pt) * 3;
+    return mk(o[0], o[1], o[2]);
+}
+
+__device__ inline void add3(double *g, double s, double a, double b, double c) {
+    g[0] += s * a;
+    g[1] += s * b;
+    g[2] += s * c;
+}
+
+template <typename R>
+__device__ inline void wsum3(V3<R> v, double *dst, double scale, int lane) {
+    double a = warp_sum(double(v.x)), b = warp_sum(double(v.y)), c = warp_sum(double(v.z));
+    if (lane == 0) add3(dst, scale, a, b, c);
+}
+template <typename R>
+__device__ inline void wsum6(const Sym<R> &v, double *dst, double scale, int lane) {
+    double a[6] = {warp_sum(double(v.xx)), warp_sum(double(v.yy)), warp_sum(double(v.zz)),
+                   warp_sum(double(v.xy)), warp_sum(double(v.xz)), warp_sum(double(v.yz))};
+    if (lane == 0)
+        for (int k = 0; k < 6; ++k) dst[k] += scale * a[k];
+}
+template <typename R>
+__device__ inline void symadd(Sym<R> &a, const Sym<R> &b, R s) {
+    a.xx += s * b.xx; a.yy += s * b.yy; a.zz += s * b.zz;
+    a.xy += s * b.xy; a.xz += s * b.xz; a.yz += s * b.yz;
+}
+
+// ---------------------------------------------------------------------------
+// Permanent electrostatics + penetration (Eq. 2), Thole-damped permanent
+// field on the polarizable atoms, potential on the lone pairs.
+// Warps 0..4: target site w of molecule i.  Warps 5, 6: target lone pair.
+// ---------------------------------------------------------------------------
+template <typename R, bool PER>
+__global__ void __launch_bounds__(224) k_real_perm(KParams p, DevState<R> d) {
+    __shared__ Tile<R> tile;
+    __shared__ double s_e[7][2];
+    const int i = blockIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool is_lp = w >= NS;
+    const V3<R> ot = my_pt(d, i, w);
+    Mp<R> mt{};
+    if (!is_lp) mt = load_mp(d.gmp + (i * NS + w) * NMP);
+    const R Nt = (!is_lp) ? R(p.z[w]) - mt.q * R(w < 3) : R(0);
+    const R Nt_ = (w < 3) ? Nt : R(0);
+    const R bt = (!is_lp) ? R(p.b[w]) : R(0);
+    const R rc2 = R(p.rc2), alpha = R(p.alpha), thole = R(p.thole);
+    const R third = R(1) / R(3);
+
+    Acc<R> Ue, Up, Vl;
+    V3<R> gr = mk(R(0), R(0), R(0)), gm = gr, ef = gr;
+    Sym<R> gt{};
+    const int nn = d.nnbr[i];
+    for (int base = 0; base < nn; base += TILE) {
+        __syncthreads();
+        load_tile(p, d, i, base, nn, tile, true);
+        __syncthreads();
+        const int k = lane;
+        if (base + k >= nn) continue;
+        const V3<R> dO = mk(tile.dO[k][0], tile.dO[k][1], tile.dO[k][2]);
+#pragma unroll 1
+        for (int s = 0; s < NS; ++s) {
+            const V3<R> rs = dO + mk(tile.off[k][s * 3], tile.off[k][s * 3 + 1], tile.off[k][s * 3 + 2]);
+            const V3<R> x = ot - rs;
+            const R r2 = dot(x, x);
+            if (PER && r2 >= rc2) continue;
+            const R rinv = rsqrt_(r2);
+            const R r = r2 * rinv;
+            const Mp<R> ms = load_mp(&tile.mp[k][s * NMP]);
+            R g[6];
+            if (PER) g_erfc<R, 5>(r, rinv, alpha, g);
+            else g_bare<R, 5>(rinv, g);
+            if (is_lp) {
+                FieldTerms<R> f;
+                source_field<R, 1>(ms, x, g, f);
+                Vl.add(f.phi);
+                gr = gr + f.d1;
+                continue;
+            }
+            FieldTerms<R> f;
+            source_field<R, 3>(ms, x, g, f);
+            const R U = mt.q * f.phi + dot(mt.mu, f.d1) + third * symdd(mt.th, f.d2);
+            Ue.add(R(0.5) * U);
+            gr = gr + target_grad(mt, ms, x, g, f);
+            gm = gm + f.d1;
+            symadd(gt, f.d2, third);
+            // ---- penetration: charge-charge*, charge-dipole*, charge-quadrupole*
+            const R Ns = (s < 3) ? R(p.z[s]) - ms.q : R(0);
+            if (Nt_ != R(0) || Ns != R(0)) {
+                const R bs = R(p.b[s]);
+                R pen = R(0);
+                // q*_t q*_s - q_t q_s, with q* = q + N exp(-b r)
+                {
+                    R g1a[2], g1b[2], g1c[2];
+                    g_exp<R, 1>(r, rinv, bs, g1a);
+                    g_exp<R, 1>(r, rinv, bt, g1b);
+                    g_exp<R, 1>(r, rinv, bt + bs, g1c);
+                    const R c1 = mt.q * Ns, c2 = ms.q * Nt_, c3 = Nt_ * Ns;
+                    pen += c1 * g1a[0] + c2 * g1b[0] + c3 * g1c[0];
+                    gr = gr + (c1 * g1a[1] + c2 * g1b[1] + c3 * g1c[1]) * x;
+                }
+                if (Nt_ != R(0)) {   // valence of t in the dipole/quadrupole potential of s
+                    R ge[4];
+                    g_exp<R, 3>(r, rinv, bt, ge);
+                    Mp<R> m0 = ms;
+                    m0.q = R(0);
+                    FieldTerms<R> f2;
+                    source_field<R, 1>(m0, x, ge, f2);
+                    pen += Nt_ * f2.phi;
+                    gr = gr + Nt_ * f2.d1;
+                }
+                if (Ns != R(0)) {    // valence of s in the dipole/quadrupole potential of t
+                    R ge[4];
+                    g_exp<R, 3>(r, rinv, bs, ge);
+                    Mp<R> m0 = mt;
+                    m0.q = R(0);
+                    const V3<R> xs = -x;
+                    FieldTerms<R> f3;
+                    source_field<R, 1>(m0, xs, ge, f3);
+                    pen += Ns * f3.phi;
+                    gr = gr - Ns * f3.d1;
+                    gm = gm + (-Ns * ge[1]) * xs;
+                    const R c = Ns * third * ge[2];
+                    gt.xx += c * xs.x * xs.x; gt.yy += c * xs.y * xs.y; gt.zz += c * xs.z * xs.z;
+                    gt.xy += c * xs.x * xs.y; gt.xz += c * xs.x * xs.z; gt.yz += c * xs.y * xs.z;
+                }
+                Up.add(R(0.5) * pen);
+            }
+            // ---- Thole-damped permanent field on the polarizable atom
+            if (w < 3) {
+                const R A3 = sqrt_(R(p.a_pol[w] * p.a_damp[s]));
+                R gtol[4];
+                g_thole<R, 3>(r, rinv, R(1) / A3, thole, PER, alpha, gtol);
+                FieldTerms<R> f4;
+                source_field<R, 1>(ms, x, gtol, f4);
+                ef = ef - f4.d1;
+            }
+        }
+    }
+    const double ke = p.ke;
+    if (is_lp) {
+        const int l = w - NS;
+        double v = warp_sum(Vl.get());
+        if (lane == 0) d.vlp[i * 2 + l] += ke * v;
+        wsum3(gr, d.dvlp + (i * 2 + l) * 3, ke, lane);
+    } else {
+        wsum3(gr, d.gpt + (i * NP + w) * 3, ke, lane);
+        wsum3(gm, d.gmu + (i * NS + w) * 3, ke, lane);
+        wsum6(gt, d.gth + (i * NS + w) * 6, ke, lane);
+        if (w < 3) wsum3(ef, d.efield + i * 9 + w * 3, 1.0, lane);
+        double e0 = warp_sum(Ue.get()), e1 = warp_sum(Up.get());
+        if (lane == 0) {
+            s_e[w][0] = e0;
+            s_e[w][1] = e1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int k = 0; k < NS; ++k) a += s_e[k][0], b += s_e[k][1];
+        d.epart[i * NTERM + T_ELEC] += ke * a;
+        d.epart[i * NTERM + T_PEN] += ke * b;
+    }
+}
+
+template <typename R>
+void launch_real_perm(const KParams &p, DevState<R> &d, Launch L) {
+    if (p.periodic) k_real_perm<R, true><<<p.M, 224, 0, L.s>>>(p, d);
+    else k_real_perm<R, false><<<p.M, 224, 0, L.s>>>(p, d);
+    count(L);
+}
+
+// ---------------------------------------------------------------------------
+// Exchange-repulsion (Technical Appendix), dispersion and exchange-dispersion.
+// One lane per (i, j) molecule pair; gradients of i's points only.
+// Points: 0 = O, 1 = H1, 2 = H2, 3 = LP1, 4 = LP2 (relative to O_i).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ inline R cosv(V3<R> u, V3<R> v, V3<R> &du, V3<R> &dv) {
+    const R uu = dot(u, u), vv = dot(v, v);
+    const R iu = rsqrt_(uu), iv = rsqrt_(vv);
+    const R c = dot(u, v) * iu * iv;
+    du = (iu * iv) * v - (c / uu) * u;
+    dv = (iu * iv) * u - (c / vv) * v;
+    return c;
+}
+
+// Atom-pair overlap with each p orbital measured at its own atom:
+// O = A + B cx + C cy + D cx cy, cx = cos(ux, y - x), cy = cos(uy, x - y),
+// ux = xp - x (xp an i-side point), uy fixed (j side).
+// Adds dO/dx into gx and dO/dxp into gxp.
+template <typename R>
+__device__ inline R overlap_i(V3<R> x, V3<R> xp, V3<R> y, V3<R> uy, R A, R B, R C, R D, V3<R> &gx, V3<R> &gxp) {
+    V3<R> du, dv, du2, dv2;
+    const R cx = cosv(xp - x, y - x, du, dv);
+    const R cy = cosv(uy, x - y, du2, dv2);
+    const R ox = B + D * cy, oy = C + D * cx;
+    gxp = ox * du;
+    gx = R(-1) * ox * (du + dv) + oy * dv2;
+    return A + B * cx + C * cy + D * cx * cy;
+}
+
+template <typename R>
+struct RepAtom {
+    R cs, cp, g, cf, rv;
+};
+
+// Adds the overlap and exponential factor of one atom pair to O1/O2 and the
+// i-side gradients of O1/O2 (points ix, ixp).
+template <typename R>
+__device__ inline void rep_pair_term(V3<R> x, V3<R> xp, const RepAtom<R> &ai, V3<R> y, V3<R> uy, const RepAtom<R> &aj,
+                                     R pp, R f, R a1, R a2, R &O1, R &O2, V3<R> &g1x, V3<R> &g1xp, V3<R> &g2x,
+                                     V3<R> &g2xp) {
+    V3<R> gx, gxp;
+    const R O = overlap_i(x, xp, y, uy, ai.cs * aj.cs, aj.cs * ai.cp * f, ai.cs * aj.cp * f, pp * ai.cp * aj.cp, gx, gxp);
+    const V3<R> v = x - y;
+    const R rr = sqrt_(dot(v, v));
+    const R kr = R(1) / (R(4) * sqrt_(ai.rv * aj.rv));
+    const R M = sqrt_(ai.g * aj.g * ai.cf * aj.cf);
+    const R S1 = M * exp_(-a1 * kr * rr), S2 = M * exp_(-a2 * kr * rr);
+    O1 += O * S1;
+    O2 += O * S2;
+    const V3<R> drdx = (R(1) / rr) * v;
+    g1x = g1x + S1 * gx + (O * S1 * (-a1 * kr)) * drdx;
+    g2x = g2x + S2 * gx + (O * S2 * (-a2 * kr)) * drdx;
+    g1xp = g1xp + S1 * gxp;
+    g2xp = g2xp + S2 * gxp;
+}
+
+// E = pref (C1 O1^2 / r + C2 O2^2 / r^2): returns E and dE/dO1, dE/dO2, dE/dr.
+template <typename R>
+__device__ inline R rep_energy(R pref, R C1, R C2, R O1, R O2, R r, R &e1, R &e2, R &er) {
+    const R ri = R(1) / r;
+    e1 = pref * C1 * R(2) * O1 * ri;
+    e2 = pref * C2 * R(2) * O2 * ri * ri;
+    er = pref * (-C1 * O1 * O1 * ri * ri - R(2) * C2 * O2 * O2 * ri * ri * ri);
+    return pref * (C1 * O1 * O1 * ri + C2 * O2 * O2 * ri * ri);
+}
+
+template <typename R, bool PER>
+__global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
+    const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= p.M) return;
+    const R rc2 = R(p.rc2);
+    V3<R> P[5];
+    for (int k = 0; k < 3; ++k) P[k] = my_pt(d, i, k);
+    P[3] = my_pt(d, i, 5);
+    P[4] = my_pt(d, i, 6);
+    const R qi[3] = {d.gmp[(i * NS + 0) * NMP], d.gmp[(i * NS + 1) * NMP], d.gmp[(i * NS + 2) * NMP]};
+    const R f = R(p.rep_f), a1 = R(p.rep_a1), a2 = R(p.rep_a2), C1 = R(p.rep_c1), C2 = R(p.rep_c2);
+    const R occ = R(p.occ), nlp = R(p.nlp);
+    const R cf_lp = R(1) - nlp / R(p.nval_o);
+    V3<R> G[5];
+    for (int k = 0; k < 5; ++k) G[k] = mk(R(0), R(0), R(0));
+    Acc<R> Erep, Ed, Ex;
+    const int nn = d.nnbr[i];
+    for (int slot = lane; slot < nn; slot += 32) {
+        const int j = d.nbr[i * MAXN + slot];
+        double dx, dy, dz;
+        min_image(p, d.pos, i, j, dx, dy, dz);
+        const V3<R> dO = mk(R(dx), R(dy), R(dz));
+        V3<R> Q[5];
+        Q[0] = dO;
+        Q[1] = dO + my_pt(d, j, 1);
+        Q[2] = dO + my_pt(d, j, 2);
+        Q[3] = dO + my_pt(d, j, 5);
+        Q[4] = dO + my_pt(d, j, 6);
+        const R qj[3] = {d.gmp[(j * NS + 0) * NMP], d.gmp[(j * NS + 1) * NMP], d.gmp[(j * NS + 2) * NMP]};
+        RepAtom<R> Ai[3], Aj[3];
+        Ai[0] = {R(p.cs_o), R(p.cp_o), R(p.g_o), R(1) - qi[0] / R(p.nval_o), R(p.rv_rep_o)};
+        Aj[0] = {R(p.cs_o), R(p.cp_o), R(p.g_o), R(1) - qj[0] / R(p.nval_o), R(p.rv_rep_o)};
+        for (int k = 1; k < 3; ++k) {
+            Ai[k] = {R(p.cs_h), R(p.cp_h), R(p.g_h), R(1) - qi[k] / R(p.nval_h), R(p.rv_rep_h)};
+            Aj[k] = {R(p.cs_h), R(p.cp_h), R(p.g_h), R(1) - qj[k] / R(p.nval_h), R(p.rv_rep_h)};
+        }
+        const RepAtom<R> Alp = {R(p.cs_lp), R(p.cp_lp), R(p.g_o), cf_lp, R(p.rv_rep_lp)};
+        // ---- bond-bond
+        for (int kb = 1; kb <= 2; ++kb)
+            for (int kc = 1; kc <= 2; ++kc) {
+                const V3<R> mi = R(0.5) * (P[0] + P[kb]), mj = R(0.5) * (Q[0] + Q[kc]);
+                const V3<R> dm = mi - mj;
+                const R rm2 = dot(dm, dm);
+                if (PER && rm2 >= rc2) continue;
+                const R rm = sqrt_(rm2);
+                R O1 = 0, O2 = 0;
+                V3<R> z = mk(R(0), R(0), R(0));
+                V3<R> g1a = z, g1b = z, g2a = z, g2b = z;   // dO/d(O_i), dO/d(H_kb)
+                // x = a (O_i, partner H), x = b (H, partner O)
+                for (int u = 0; u < 2; ++u)
+                    for (int v = 0; v < 2; ++v) {
+                        const int xi = u ? kb : 0, xpi = u ? 0 : kb;
+                        const int yj = v ? kc : 0, ypj = v ? 0 : kc;
+                        V3<R> t1x = z, t1xp = z, t2x = z, t2xp = z;
+                        rep_pair_term(P[xi], P[xpi], Ai[xi], Q[yj], Q[ypj] - Q[yj], Aj[yj], R(2), f, a1, a2, O1, O2,
+                                      t1x, t1xp, t2x, t2xp);
+                        if (u == 0) { g1a = g1a + t1x; g2a = g2a + t2x; g1b = g1b + t1xp; g2b = g2b + t2xp; }
+                        else { g1b = g1b + t1x; g2b = g2b + t2x; g1a = g1a + t1xp; g2a = g2a + t2xp; }
+                    }
+                R e1, e2, er;
+                Erep.add(R(0.5) * rep_energy(occ * occ, C1, C2, O1, O2, rm, e1, e2, er));
+                const V3<R> drm = (R(0.5) / rm) * dm;
+                G[0] = G[0] + e1 * g1a + e2 * g2a + er * drm;
+                G[kb] = G[kb] + e1 * g1b + e2 * g2b + er * drm;
+            }
+        // ---- bond of i with lone pair of j
+        for (int kb = 1; kb <= 2; ++kb)
+            for (int l = 0; l < 2; ++l) {
+                const V3<R> mi = R(0.5) * (P[0] + P[kb]);
+                const V3<R> dm = mi - Q[3 + l];
+                const R r2 = dot(dm, dm);
+                if (PER && r2 >= rc2) continue;
+                const R rr = sqrt_(r2);
+                R O1 = 0, O2 = 0;
+                V3<R> z = mk(R(0), R(0), R(0));
+                V3<R> g1a = z, g1b = z, g2a = z, g2b = z;
+                for (int u = 0; u < 2; ++u) {
+                    const int xi = u ? kb : 0, xpi = u ? 0 : kb;
+                    V3<R> t1x = z, t1xp = z, t2x = z, t2xp = z;
+                    rep_pair_term(P[xi], P[xpi], Ai[xi], Q[0], Q[3 + l] - Q[0], Alp, f, f, a1, a2, O1, O2, t1x, t1xp,
+                                  t2x, t2xp);
+                    if (u == 0) { g1a = g1a + t1x; g2a = g2a + t2x; g1b = g1b + t1xp; g2b = g2b + t2xp; }
+                    else { g1b = g1b + t1x; g2b = g2b + t2x; g1a = g1a + t1xp; g2a = g2a + t2xp; }
+                }
+                R e1, e2, er;
+                Erep.add(R(0.5) * rep_energy(occ * nlp, C1, C2, O1, O2, rr, e1, e2, er));
+                const V3<R> drm = (R(0.5) / rr) * dm;
+                G[0] = G[0] + e1 * g1a + e2 * g2a + er * drm;
+                G[kb] = G[kb] + e1 * g1b + e2 * g2b + er * drm;
+            }
+        // ---- lone pair of i with bond of j (the lone pair as a pseudo-atom at its carrier)
+        for (int l = 0; l < 2; ++l)
+            for (int kc = 1; kc <= 2; ++kc) {
+                const V3<R> mj = R(0.5) * (Q[0] + Q[kc]);
+                const V3<R> dm = P[3 + l] - mj;
+                const R r2 = dot(dm, dm);
+                if (PER && r2 >= rc2) continue;
+                const R rr = sqrt_(r2);
+                R O1 = 0, O2 = 0;
+                V3<R> z = mk(R(0), R(0), R(0));
+                V3<R> g1c = z, g1l = z, g2c = z, g2l = z;
+                for (int v = 0; v < 2; ++v) {
+                    const int yj = v ? kc : 0, ypj = v ? 0 : kc;
+                    V3<R> t1x = z, t1xp = z, t2x = z, t2xp = z;
+                    rep_pair_term(P[0], P[3 + l], Alp, Q[yj], Q[ypj] - Q[yj], Aj[yj], f, f, a1, a2, O1, O2, t1x,
+                                  t1xp, t2x, t2xp);
+                    g1c = g1c + t1x; g2c = g2c + t2x; g1l = g1l + t1xp; g2l = g2l + t2xp;
+                }
+                R e1, e2, er;
+                Erep.add(R(0.5) * rep_energy(occ * nlp, C1, C2, O1, O2, rr, e1, e2, er));
+                G[0] = G[0] + e1 * g1c + e2 * g2c;
+                G[3 + l] = G[3 + l] + e1 * g1l + e2 * g2l + (er / rr) * dm;
+            }
+        // ---- lone pair - lone pair (angles toward the other lone pair's position)
+        for (int l1 = 0; l1 < 2; ++l1)
+            for (int l2 = 0; l2 < 2; ++l2) {
+                const V3<R> I = P[3 + l1], J = Q[3 + l2];
+                const V3<R> dIJ = I - J;
+                const R r2 = dot(dIJ, dIJ);
+                if (PER && r2 >= rc2) continue;
+                const R rr = sqrt_(r2);
+                V3<R> dui, dvi, duj, dvj;
+                const R ci = cosv(I - P[0], J - P[0], dui, dvi);    // depends on I and A
+                const R cj = cosv(J - Q[0], I - Q[0], duj, dvj);    // depends on I
+                const R cs = R(p.cs_lp), cp = R(p.cp_lp);
+                const R O = cs * cs + cs * cp * f * cj + cs * cp * f * ci + R(2) * cp * cp * ci * cj;
+                const R dci = cs * cp * f + R(2) * cp * cp * cj, dcj = cs * cp * f + R(2) * cp * cp * ci;
+                const V3<R> dOdI = dci * dui + dcj * dvj;
+                const V3<R> dOdA = R(-1) * dci * (dui + dvi);
+                const V3<R> dAB = P[0] - Q[0];
+                const R rab = sqrt_(dot(dAB, dAB));
+                const R kr = R(1) / (R(4) * R(p.rv_rep_lp));
+                const R M = R(p.g_o) * cf_lp;
+                const R S1 = M * exp_(-a1 * kr * rab), S2 = M * exp_(-a2 * kr * rab);
+                const R O1 = O * S1, O2 = O * S2;
+                R e1, e2, er;
+                Erep.add(R(0.5) * rep_energy(nlp * nlp, C1, C2, O1, O2, rr, e1, e2, er));
+                const V3<R> drab = (R(1) / rab) * dAB;
+                G[0] = G[0] + (e1 * S1 + e2 * S2) * dOdA + (e1 * O1 * (-a1 * kr) + e2 * O2 * (-a2 * kr)) * drab;
+                G[3 + l1] = G[3 + l1] + (e1 * S1 + e2 * S2) * dOdI + (er / rr) * dIJ;
+            }
+        // ---- dispersion and exchange-dispersion over atoms and lone pairs
+        const R cfi[5] = {R(1) - qi[0] / R(p.nval_o), R(1) - qi[1] / R(p.nval_h), R(1) - qi[2] / R(p.nval_h),
+                          R(1) - qi[0] / R(p.nval_o), R(1) - qi[0] / R(p.nval_o)};
+        const R cfj[5] = {R(1) - qj[0] / R(p.nval_o), R(1) - qj[1] / R(p.nval_h), R(1) - qj[2] / R(p.nval_h),
+                          R(1) - qj[0] / R(p.nval_o), R(1) - qj[0] / R(p.nval_o)};
+        for (int u = 0; u < 5; ++u)
+            for (int v = 0; v < 5; ++v) {
+                const V3<R> dv = P[u] - Q[v];
+                const R r2 = dot(dv, dv);
+                if (PER && r2 >= rc2) continue;
+                const R ri = rsqrt_(r2), r = r2 * ri;
+                const R rvu = R(p.rv_d[u]), rvv = R(p.rv_d[v]);
+                const R km = R(0.5) * rsqrt_(rvu * rvv);
+                const R m = r * km, mi = R(1) / m;
+                const R S = (rvu + rvv) * R(p.disp_alpha);
+                const R dd = S * ri - R(1);
+                const R m2i = mi * mi, m6i = m2i * m2i * m2i, m8i = m6i * m2i, m10i = m8i * m2i;
+                const R e6 = R(p.c6) * exp_(-R(p.g6) * dd) * m6i;
+                const R e8 = R(p.c8) * exp_(-R(p.g8) * dd) * m8i;
+                const R e10 = R(p.c10) * exp_(-R(p.g10) * dd) * m10i;
+                const R dsdr = S * ri * ri;   // -d(dd)/dr
+                const R fsum = e6 + e8 + e10;
+                const R dfdr = e6 * (R(p.g6) * dsdr - R(6) * ri) + e8 * (R(p.g8) * dsdr - R(8) * ri) +
+                               e10 * (R(p.g10) * dsdr - R(10) * ri);
+                const bool lu = u >= 3, lv = v >= 3;
+                R pref, xc, xa;
+                if (!lu && !lv) { pref = -R(p.beta[u] * p.beta[v]); xc = R(p.xd_c1); xa = R(p.xd_a1); }
+                else if (lu && lv) { pref = -nlp * nlp * R(0.25); xc = nlp * nlp * R(0.25) * R(p.xd_c2); xa = R(p.xd_a2); }
+                else { pref = -R(p.delta) * R(0.5); xc = nlp * R(0.5) * R(p.xd_c3); xa = R(p.xd_a3); }
+                const R K = R(p.beta[u] * p.beta[v]) * cfi[u] * cfj[v];
+                const R ex = xc * K * exp_(-xa * m);
+                Ed.add(R(0.5) * pref * fsum);
+                Ex.add(R(0.5) * ex);
+                const R dEdr = pref * dfdr - xa * km * ex;
+                G[u] = G[u] + (dEdr * ri) * dv;
+            }
+    }
+    // lane reduction; points 3, 4 are the lone pairs (point slots 5, 6)
+    const int slot_of[5] = {0, 1, 2, 5, 6};
+    for (int k = 0; k < 5; ++k) wsum3(G[k], d.gpt + (i * NP + slot_of[k]) * 3, 1.0, lane);
+    double er_ = warp_sum(Erep.get()), ed_ = warp_sum(Ed.get()), ex_ = warp_sum(Ex.get());
+    if (lane == 0) {
+        d.epart[i * NTERM + T_REP] += er_;
+        d.epart[i * NTERM + T_DISP] += ed_;
+        d.epart[i * NTERM + T_XDISP] += ex_;
+    }
+}
+
+template <typename R>
+void launch_short(const KParams &p, DevState<R> &d, Launch L) {
+    if (p.periodic) k_short<R, true><<<(p.M + 3) / 4, 128, 0, L.s>>>(p, d);
+    else k_short<R, false><<<(p.M + 3) / 4, 128, 0, L.s>>>(p, d);
+    count(L);
+}
+
+// ---------------------------------------------------------------------------
+// Reduced charge transfer (Eqs. 13-16).  Donors: lone pairs; acceptors: O-H
+// bonds of other molecules with carrier-O distance below rc.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct CtOut {
+    R E, dV, dVi1, dVi2;
+    V3<R> gc, glp, ga1, ga2;
+};
+
+template <typename R>
+__device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1, V3<R> a2, R V, R Vi1, R Vi2,
+                                   int *flags) {
+    CtOut<R> o;
+    const R eta = R(p.ct_eta), cs = R(p.cs_lp), cp = R(p.cp_lp), t = R(p.ct_t), mm = R(p.ct_m), n = R(p.nlp);
+    const R kc1 = R(0.5) / R(p.rv_ct_o), kc2 = R(0.5) * rsqrt_(R(p.rv_ct_o * p.rv_ct_h));
+    const V3<R> v1 = a1 - c, v2 = a2 - c, u = lp - c;
+    const R r1 = sqrt_(dot(v1, v1)), r2 = sqrt_(dot(v2, v2));
+    V3<R> du1, dv1, du2, dv2;
+    const R ca = cosv(u, v1, du1, dv1);
+    const R cb = cosv(u, v2, du2, dv2);
+    const R E1 = exp_(-eta * kc1 * r1), E2 = exp_(-eta * kc2 * r2);
+    const R K1 = cs * t + cp * mm * ca, K2 = cs * t + cp * mm * cb;
+    const R e1 = E1 * (Vi1 - V) * K1, e2 = E2 * (Vi2 - V) * K2;
+    const R D = e1 - e2;
+    const R dE = R(p.ct_ae) + V - R(p.ct_ah);
+    if (!(dE > R(0))) atomicOr(flags, F_CTDEN);
+    const R idE = R(1) / dE;
+    o.E = -n * D * D * idE;
+    const R gD = R(-2) * n * D * idE;
+    o.dV = gD * (-E1 * K1 + E2 * K2) + n * D * D * idE * idE;
+    o.dVi1 = gD * E1 * K1;
+    o.dVi2 = -gD * E2 * K2;
+    const R dr1 = gD * (-eta * kc1 * e1), dr2 = gD * (eta * kc2 * e2);
+    const R dca = gD * E1 * (Vi1 - V) * cp * mm, dcb = -gD * E2 * (Vi2 - V) * cp * mm;
+    const V3<R> n1 = (R(1) / r1) * v1, n2 = (R(1) / r2) * v2;
+    o.glp = dca * du1 + dcb * du2;
+    o.ga1 = dr1 * n1 + dca * dv1;
+    o.ga2 = dr2 * n2 + dcb * dv2;
+    o.gc = R(-1) * (o.glp + o.ga1 + o.ga2);
+    return o;
+}
+
+template <typename R, bool PER>
+__global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
+    const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= p.M) return;
+    const R rc2 = R(p.rc2);
+    V3<R> P[5];
+    for (int k = 0; k < 3; ++k) P[k] = my_pt(d, i, k);
+    P[3] = my_pt(d, i, 5);
+    P[4] = my_pt(d, i, 6);
+    const R Vi[2] = {R(d.vlp[i * 2]), R(d.vlp[i * 2 + 1])};
+    const R Vint_i[3] = {R(d.vint[i * 3]), R(d.vint[i * 3 + 1]), R(d.vint[i * 3 + 2])};
+    V3<R> G[5];
+    for (int k = 0; k < 5; ++k) G[k] = mk(R(0), R(0), R(0));
+    R lam[2] = {R(0), R(0)}, kap[3] = {R(0), R(0), R(0)};
+    Acc<R> Ect;
+    const int nn = d.nnbr[i];
+    for (int slot = lane; slot < nn; slot += 32) {
+        const int j = d.nbr[i * MAXN + slot];
+        double dx, dy, dz;
+        min_image(p, d.pos, i, j, dx, dy, dz);
+        const V3<R> dO = mk(R(dx), R(dy), R(dz));
+        if (PER && dot(dO, dO) >= rc2) continue;
+        V3<R> Q[5];
+        Q[0] = dO;
+        Q[1] = dO + my_pt(d, j, 1);
+        Q[2] = dO + my_pt(d, j, 2);
+        Q[3] = dO + my_pt(d, j, 5);
+        Q[4] = dO + my_pt(d, j, 6);
+        const R Vj[2] = {R(d.vlp[j * 2]), R(d.vlp[j * 2 + 1])};
+        const R Vint_j[3] = {R(d.vint[j * 3]), R(d.vint[j * 3 + 1]), R(d.vint[j * 3 + 2])};
+        for (int l = 0; l < 2; ++l)
+            for (int k = 1; k <= 2; ++k) {
+                // i donor (lone pair l of i), j acceptor (bond O-H_k of j)
+                CtOut<R> o = ct_pair(p, P[0], P[3 + l], Q[0], Q[k], Vi[l], Vint_j[0], Vint_j[k], d.flags);
+                Ect.add(R(0.5) * o.E);
+                G[0] = G[0] + o.gc;
+                G[3 + l] = G[3 + l] + o.glp;
+                lam[l] += o.dV;
+                // j donor (lone pair l of j), i acceptor (bond O-H_k of i)
+                CtOut<R> q = ct_pair(p, Q[0], Q[3 + l], P[0], P[k], Vj[l], Vint_i[0], Vint_i[k], d.flags);
+                Ect.add(R(0.5) * q.E);
+                G[0] = G[0] + q.ga1;
+                G[k] = G[k] + q.ga2;
+                kap[0] += q.dVi1;
+                kap[k] += q.dVi2;
+            }
+    }
+    const int slot_of[5] = {0, 1, 2, 5, 6};
+    for (int k = 0; k < 5; ++k) wsum3(G[k], d.gpt + (i * NP + slot_of[k]) * 3, 1.0, lane);
+    double e = warp_sum(Ect.get());
+    double l0 = warp_sum(double(lam[0])), l1 = warp_sum(double(lam[1]));
+    double k0 = warp_sum(double(kap[0])), k1 = warp_sum(double(kap[1])), k2 = warp_sum(double(kap[2]));
+    if (lane == 0) {
+        d.epart[i * NTERM + T_CT] += e;
+        d.lam[i * 2] += l0;
+        d.lam[i * 2 + 1] += l1;
+        d.kap[i * 3] += k0;
+        d.kap[i * 3 + 1] += k1;
+        d.kap[i * 3 + 2] += k2;
+    }
+}
+
+template <typename R>
+void launch_ct(const KParams &p, DevState<R> &d, Launch L) {
+    if (p.periodic) k_ct<R, true><<<(p.M + 3) / 4, 128, 0, L.s>>>(p, d);
+    else k_ct<R, false><<<(p.M + 3) / 4, 128, 0, L.s>>>(p, d);
+    count(L);
+}
+
+// ---------------------------------------------------------------------------
+// Polarization matrix-vector product, real-space part: field at the three
+// polarizable atoms of i from the dipoles `vec` of the other molecules
+// (Thole-damped, Ewald-screened in periodic systems).  out += field.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct DipTile {
+    int j[TILE];
+    R dO[TILE][3];
+    R off[TILE][9];
+    R v[TILE][9];
+};
+
+template <typename R, bool PER>
+__global__ void __launch_bounds__(96) k_real_tmu(KParams p, DevState<R> d, const double *vec, double *out) {
+    if (d.scal[7] != 0.0) return;   // solver already converged
+    __shared__ DipTile<R> t;
+    const int i = blockIdx.x;
+    const int a = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const V3<R> xa = my_pt(d, i, a);
+    const R rc2 = R(p.rc2), alpha = R(p.alpha), thole = R(p.thole);
+    V3<R> ef = mk(R(0), R(0), R(0));
+    const int nn = d.nnbr[i];
+    for (int base = 0; base < nn; base += TILE) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < TILE; k += blockDim.x) {
+            int slot = base + k;
+            int j = slot < nn ? d.nbr[i * MAXN + slot] : -1;
+            t.j[k] = j;
+            if (j >= 0) {
+                double dx, dy, dz;
+                min_image(p, d.pos, i, j, dx, dy, dz);
+                t.dO[k][0] = R(dx); t.dO[k][1] = R(dy); t.dO[k][2] = R(dz);
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < TILE * 9; k += blockDim.x) {
+            int s = k / 9, c = k % 9;
+            int j = t.j[s];
+            t.off[s][c] = j >= 0 ? d.off[j * NP * 3 + c] : R(0);
+            t.v[s][c] = j >= 0 ? R(vec[j * 9 + c]) : R(0);
+        }
+        __syncthreads();
+        const int k = lane;
+        if (base + k >= nn) continue;
+        const V3<R> dO = mk(t.dO[k][0], t.dO[k][1], t.dO[k][2]);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const V3<R> x = xa - (dO + mk(t.off[k][b * 3], t.off[k][b * 3 + 1], t.off[k][b * 3 + 2]));
+            const R r2 = dot(x, x);
+            if (PER && r2 >= rc2) continue;
+            const R rinv = rsqrt_(r2), r = r2 * rinv;
+            R g[4];
+            g_thole<R, 2>(r, rinv, rsqrt_(R(p.a_pol[a] * p.a_pol[b])), thole, PER, alpha, g);
+            const V3<R> mu = mk(t.v[k][b * 3], t.v[k][b * 3 + 1], t.v[k][b * 3 + 2]);
+            // field of a point dipole: E = g2 (mu.x) x + g1 mu ... d1 = -(g2 (mu.x) x + g1 mu)
+            const R s = dot(mu, x);
+            ef = ef + (g[2] * s) * x + g[1] * mu;
+        }
+    }
+    wsum3(ef, out + i * 9 + a * 3, 1.0, lane);
+}
+
+template <typename R>
+void launch_real_tmu(const KParams &p, DevState<R> &d, const double *vec, double *out, Launch L) {
+    if (p.periodic) k_real_tmu<R, true><<<p.M, 96, 0, L.s>>>(p, d, vec, out);
+    else k_real_tmu<R, false><<<p.M, 96, 0, L.s>>>(p, d, vec, out);
+    count(L);
+}
+
+// ---------------------------------------------------------------------------
+// Polarization forces, real-space part, at fixed induced dipoles mu and
+// charge-transfer sensitivities lambda (point charges on the lone pairs):
+//   target site t of i:  d/dr_t and multipole sensitivities of
+//       sum_b U(M_t, mu_b)   (Thole-damped)     + sum_l U(M_t, lambda_l) (undamped)
+//   target pol atom a of i (a = t < 3): d/dr_a of
+//       sum_s U(mu_a, M_s) + sum_b U(mu_a, mu_b)  (Thole-damped)
+// ---------------------------------------------------------------------------
+template <typename R>
+struct PfTile {
+    int j[TILE];
+    R dO[TILE][3];
+    R off[TILE][NP * 3];
+    R mp[TILE][NS * NMP];
+    R mu[TILE][9];
+    R lam[TILE][2];
+};
+
+template <typename R, bool PER>
+__global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d) {
+    __shared__ PfTile<R> t;
+    const int i = blockIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const V3<R> ot = my_pt(d, i, w);
+    const Mp<R> mt = load_mp(d.gmp + (i * NS + w) * NMP);
+    V3<R> mui = mk(R(0), R(0), R(0));
+    if (w < 3) mui = mk(R(d.mu[i * 9 + w * 3]), R(d.mu[i * 9 + w * 3 + 1]), R(d.mu[i * 9 + w * 3 + 2]));
+    const R rc2 = R(p.rc2), alpha = R(p.alpha), thole = R(p.thole), third = R(1) / R(3);
+    V3<R> gr = mk(R(0), R(0), R(0)), gm = gr;
+    Sym<R> gt{};
+    const int nn = d.nnbr[i];
+    for (int base = 0; base < nn; base += TILE) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < TILE; k += blockDim.x) {
+            int slot = base + k;
+            int j = slot < nn ? d.nbr[i * MAXN + slot] : -1;
+            t.j[k] = j;
+            if (j >= 0) {
+                double dx, dy, dz;
+                min_image(p, d.pos, i, j, dx, dy, dz);
+                t.dO[k][0] = R(dx); t.dO[k][1] = R(dy); t.dO[k][2] = R(dz);
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < TILE * NP * 3; k += blockDim.x) {
+            int s = k / (NP * 3), c = k % (NP * 3);
+            int j = t.j[s];
+            t.off[s][c] = j >= 0 ? d.off[j * NP * 3 + c] : R(0);
+        }
+        for (int k = threadIdx.x; k < TILE * NS * NMP; k += blockDim.x) {
+            int s = k / (NS * NMP), c = k % (NS * NMP);
+            int j = t.j[s];
+            t.mp[s][c] = j >= 0 ? d.gmp[j * NS * NMP + c] : R(0);
+        }
+        for (int k = threadIdx.x; k < TILE * 11; k += blockDim.x) {
+            int s = k / 11, c = k % 11;
+            int j = t.j[s];
+            if (c < 9) t.mu[s][c] = j >= 0 ? R(d.mu[j * 9 + c]) : R(0);
+            else t.lam[s][c - 9] = j >= 0 ? R(d.lam[j * 2 + c - 9]) : R(0);
+        }
+        __syncthreads();
+        const int k = lane;
+        if (base + k >= nn) continue;
+        const V3<R> dO = mk(t.dO[k][0], t.dO[k][1], t.dO[k][2]);
+        // (1) target site w, sources: induced dipoles of j
+#pragma unroll 1
+        for (int b = 0; b < 3; ++b) {
+            const V3<R> x = ot - (dO + mk(t.off[k][b * 3], t.off[k][b * 3 + 1], t.off[k][b * 3 + 2]));
+            const R r2 = dot(x, x);
+            if (PER && r2 >= rc2) continue;
+            const R rinv = rsqrt_(r2), r = r2 * rinv;
+            R g[6];
+            g_thole<R, 4>(r, rinv, rsqrt_(R(p.a_damp[w] * p.a_pol[b])), thole, PER, alpha, g);
+            g[5] = R(0);
+            Mp<R> ms{};
+            ms.mu = mk(t.mu[k][b * 3], t.mu[k][b * 3 + 1], t.mu[k][b * 3 + 2]);
+            FieldTerms<R> f;
+            source_field<R, 3>(ms, x, g, f);
+            gr = gr + target_grad(mt, ms, x, g, f);
+            gm = gm + f.d1;
+            symadd(gt, f.d2, third);
+            // induced-induced, d/dr_a of mu_a . grad phi_b: for w < 3 the site
+            // damping polarizability is the atom's, so f is the atom-atom field
+            if (w < 3) gr = gr + symv(f.d2, mui);
+        }
+        // (2) target site w, sources: lambda charges on the lone pairs of j
+#pragma unroll 1
+        for (int l = 0; l < 2; ++l) {
+            const R lq = t.lam[k][l];
+            if (lq == R(0)) continue;
+            const V3<R> x = ot - (dO + mk(t.off[k][(5 + l) * 3], t.off[k][(5 + l) * 3 + 1], t.off[k][(5 + l) * 3 + 2]));
+            const R r2 = dot(x, x);
+            if (PER && r2 >= rc2) continue;
+            const R rinv = rsqrt_(r2), r = r2 * rinv;
+            R g[6];
+            if (PER) g_erfc<R, 5>(r, rinv, alpha, g);
+            else g_bare<R, 5>(rinv, g);
+            Mp<R> ms{};
+            ms.q = lq;
+            FieldTerms<R> f;
+            source_field<R, 3>(ms, x, g, f);
+            gr = gr + target_grad(mt, ms, x, g, f);
+            gm = gm + f.d1;
+            symadd(gt, f.d2, third);
+        }
+        // (3) target pol atom a = w, sources: permanent multipoles of j
+        if (w < 3) {
+#pragma unroll 1
+            for (int s = 0; s < NS; ++s) {
+                const V3<R> x = ot - (dO + mk(t.off[k][s * 3], t.off[k][s * 3 + 1], t.off[k][s * 3 + 2]));
+                const R r2 = dot(x, x);
+                if (PER && r2 >= rc2) continue;
+                const R rinv = rsqrt_(r2), r = r2 * rinv;
+                R g[6];
+                g_thole<R, 4>(r, rinv, rsqrt_(R(p.a_pol[w] * p.a_damp[s])), thole, PER, alpha, g);
+                g[5] = R(0);
+                const Mp<R> ms = load_mp(&t.mp[k][s * NMP]);
+                FieldTerms<R> f;
+                source_field<R, 2>(ms, x, g, f);
+                gr = gr + symv(f.d2, mui);
+            }
+        }
+    }
+    const double ke = p.ke;
+    wsum3(gr, d.gpt + (i * NP + w) * 3, ke, lane);
+    wsum3(gm, d.gmu + (i * NS + w) * 3, ke, lane);
+    wsum6(gt, d.gth + (i * NS + w) * 6, ke, lane);
+}
+
+template <typename R>
+void launch_real_polforce(const KParams &p, DevState<R> &d, Launch L) {
+    if (p.periodic) k_real_polforce<R, true><<<p.M, 160, 0, L.s>>>(p, d);
+    else k_real_polforce<R, false><<<p.M, 160, 0, L.s>>>(p, d);
+    count(L);
+}
+
+#define INST(R)                                                                                    \
+    template void launch_real_perm<R>(const KParams &, DevState<R> &, Launch);                     \
+    template void launch_short<R>(const KParams &, DevState<R> &, Launch);                         \
+    template void launch_ct<R>(const KParams &, DevState<R> &, Launch);                            \
+    template void launch_real_tmu<R>(const KParams &, DevState<R> &, const double *, double *, Launch); \
+    template void launch_real_polforce<R>(const KParams &, DevState<R> &, Launch);
+INST(float)
+INST(double)
+
+}  // namespace sibfa

@@ -1,0 +1,623 @@
+// Polarization solve (Technical Appendix: T mu = E, Jacobi-preconditioned
+// conjugate gradient with FP64 vectors and dot products), intramolecular
+// Ewald corrections, the chain rule from point gradients and multipole
+// sensitivities to atom forces, energy totals and the velocity-Verlet kick.
+#include "sibfa_internal.cuh"
+
+namespace sibfa {
+
+// scal[] layout
+enum { S_RZ = 0, S_PAP = 1, S_ALPHA = 2, S_BETA = 3, S_RES = 4, S_RZN = 5, S_IT = 6, S_DONE = 7, S_TOL = 8 };
+constexpr int PB = 256;   // threads per block of the vector kernels
+
+__device__ inline double block_sum(double v, double *sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0;
+    if (w == 0) {
+        r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;   // valid in thread 0
+}
+
+// Two block partials reduced by the last block to finish, in fixed order.
+// Returns true in thread 0 of the last block, with the two totals.
+__device__ inline bool last_block_sum2(double a, double b, double *partial, unsigned *counter, double &ta,
+                                       double &tb) {
+    __shared__ double sh[32];
+    __shared__ bool s_last;
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = b;
+        __threadfence();
+        unsigned k = atomicAdd(counter, 1u);
+        s_last = (k == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double x = 0, y = 0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        x += __ldcg(&partial[2 * i]);
+        y += __ldcg(&partial[2 * i + 1]);
+    }
+    x = block_sum(x, sh);
+    y = block_sum(y, sh);
+    if (threadIdx.x == 0) {
+        ta = x;
+        tb = y;
+        *counter = 0;
+        return true;
+    }
+    return false;
+}
+
+__device__ inline double apol(const KParams &p, int k) { return p.a_pol[(k / 3) % 3]; }
+
+template <typename R>
+__global__ void k_pcg_init(KParams p, DevState<R> d, int warm) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= p.M * 9) return;
+    if (!warm) d.mu[k] = apol(p, k) * d.efield[k];
+    d.efp[k] = 0.0;
+}
+
+// r = E - T mu0, z = alpha r, p = z
+template <typename R>
+__global__ void k_pcg_first(KParams p, DevState<R> d) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double rz = 0, rr = 0;
+    if (k < p.M * 9) {
+        const double a = apol(p, k);
+        const double r = d.efield[k] - (d.mu[k] / a - d.efp[k]);
+        d.res[k] = r;
+        d.zv[k] = a * r;
+        d.pv[k] = a * r;
+        d.efp[k] = 0.0;
+        rz = r * a * r;
+        rr = a * r * a * r;
+    }
+    double trz, trr;
+    if (last_block_sum2(rz, rr, d.partial, d.counter, trz, trr)) {
+        d.scal[S_RZ] = trz;
+        const double res = sqrt(trr / (p.M * 3)) * 4.80321;
+        d.scal[S_RES] = res;
+        d.scal[S_IT] = 0;
+        d.scal[S_DONE] = (res < d.scal[S_TOL]) ? 1.0 : 0.0;
+    }
+}
+
+// ap = p / alpha - E(p); alpha_k = rz / p.ap
+template <typename R>
+__global__ void k_pcg_a(KParams p, DevState<R> d) {
+    if (d.scal[S_DONE] != 0.0) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double pap = 0;
+    if (k < p.M * 9) {
+        const double ap = d.pv[k] / apol(p, k) - d.efp[k];
+        d.ap[k] = ap;
+        pap = d.pv[k] * ap;
+    }
+    double t, u;
+    if (last_block_sum2(pap, 0.0, d.partial, d.counter, t, u)) {
+        d.scal[S_PAP] = t;
+        d.scal[S_ALPHA] = d.scal[S_RZ] / t;
+    }
+}
+
+// mu += a p, r -= a ap, z = alpha r; beta = rz_new / rz; residual check
+template <typename R>
+__global__ void k_pcg_b(KParams p, DevState<R> d) {
+    if (d.scal[S_DONE] != 0.0) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const double al = d.scal[S_ALPHA];
+    double rz = 0, rr = 0;
+    if (k < p.M * 9) {
+        const double a = apol(p, k);
+        d.mu[k] += al * d.pv[k];
+        const double r = d.res[k] - al * d.ap[k];
+        d.res[k] = r;
+        d.zv[k] = a * r;
+        rz = r * a * r;
+        rr = a * r * a * r;
+    }
+    double trz, trr;
+    if (last_block_sum2(rz, rr, d.partial, d.counter, trz, trr)) {
+        d.scal[S_BETA] = trz / d.scal[S_RZ];
+        d.scal[S_RZ] = trz;
+        const double res = sqrt(trr / (p.M * 3)) * 4.80321;
+        d.scal[S_RES] = res;
+        d.scal[S_IT] += 1.0;
+        if (res < d.scal[S_TOL]) d.scal[S_DONE] = 1.0;
+    }
+}
+
+// p = z + beta p ; clear the field accumulator for the next product
+template <typename R>
+__global__ void k_pcg_c(KParams p, DevState<R> d) {
+    if (d.scal[S_DONE] != 0.0) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= p.M * 9) return;
+    d.pv[k] = d.zv[k] + d.scal[S_BETA] * d.pv[k];
+    d.efp[k] = 0.0;
+}
+
+static inline unsigned nblk(int n) { return (unsigned)((n + PB - 1) / PB); }
+
+// start of an evaluation: clear solver scalars and error flags, set the tolerance
+__global__ void k_begin(double *scal, int *flags, double tol_D) {
+    if (threadIdx.x < 16) scal[threadIdx.x] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        scal[S_TOL] = tol_D;
+        *flags = 0;
+    }
+}
+void launch_begin(double *scal, int *flags, double tol_D, Launch L) {
+    k_begin<<<1, 32, 0, L.s>>>(scal, flags, tol_D);
+    count(L);
+}
+
+template <typename R>
+void launch_pcg_init(const KParams &p, DevState<R> &d, int warm, Launch L) {
+    k_pcg_init<R><<<nblk(p.M * 9), PB, 0, L.s>>>(p, d, warm);
+    count(L);
+}
+template <typename R>
+void launch_pcg_first(const KParams &p, DevState<R> &d, Launch L) {
+    k_pcg_first<R><<<nblk(p.M * 9), PB, 0, L.s>>>(p, d);
+    count(L);
+}
+template <typename R>
+void launch_pcg_iter_a(const KParams &p, DevState<R> &d, Launch L) {
+    k_pcg_a<R><<<nblk(p.M * 9), PB, 0, L.s>>>(p, d);
+    count(L);
+}
+template <typename R>
+void launch_pcg_iter_b(const KParams &p, DevState<R> &d, double, Launch L) {
+    k_pcg_b<R><<<nblk(p.M * 9), PB, 0, L.s>>>(p, d);
+    k_pcg_c<R><<<nblk(p.M * 9), PB, 0, L.s>>>(p, d);
+    count(L, 2);
+}
+
+// E_pol = -1/2 ke mu . E (value at the solution)
+template <typename R>
+__global__ void k_pol_energy(KParams p, DevState<R> d) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= p.M) return;
+    double e = 0;
+    for (int k = 0; k < 9; ++k) e += d.mu[m * 9 + k] * d.efield[m * 9 + k];
+    d.epart[m * NTERM + T_POL] = -0.5 * p.ke * e;
+}
+template <typename R>
+void launch_pol_energy(const KParams &p, DevState<R> &d, Launch L) {
+    k_pol_energy<R><<<(p.M + 127) / 128, 128, 0, L.s>>>(p, d);
+    count(L);
+}
+
+// ---------------------------------------------------------------------------
+// Intramolecular geometry in FP64
+// ---------------------------------------------------------------------------
+__device__ inline void frame_d2(V3<double> zv, V3<double> xv, V3<double> &ex, V3<double> &ey, V3<double> &ez) {
+    ez = (1.0 / sqrt(dot(zv, zv))) * zv;
+    V3<double> xp = xv - dot(xv, ez) * ez;
+    ex = (1.0 / sqrt(dot(xp, xp))) * xp;
+    ey = cross(ez, ex);
+}
+
+// absolute FP64 positions of the 7 points of molecule m
+template <typename R>
+__device__ inline void points_d(const KParams &p, const DevState<R> &d, int m, V3<double> *X) {
+    const double *x = d.pos + m * 9;
+    const V3<double> O = mk(x[0], x[1], x[2]), H1 = mk(x[3], x[4], x[5]), H2 = mk(x[6], x[7], x[8]);
+    const V3<double> r1 = H1 - O, r2 = H2 - O;
+    const V3<double> u1 = (1.0 / sqrt(dot(r1, r1))) * r1, u2 = (1.0 / sqrt(dot(r2, r2))) * r2;
+    V3<double> ex, ey, ez;
+    frame_d2(u1 + u2, r1, ex, ey, ez);
+    X[0] = O;
+    X[1] = H1;
+    X[2] = H2;
+    X[3] = 0.5 * (O + H1);
+    X[4] = 0.5 * (O + H2);
+    X[5] = O + p.d_lp * ((-p.lp_cos) * ez + p.lp_sin * ey);
+    X[6] = O + p.d_lp * ((-p.lp_cos) * ez - p.lp_sin * ey);
+}
+
+template <typename R>
+__device__ inline Mp<double> mp_d(const DevState<R> &d, int m, int s) {
+    const R *g = d.gmp + (m * NS + s) * NMP;
+    Mp<double> o;
+    o.q = g[0];
+    o.mu = mk((double)g[1], (double)g[2], (double)g[3]);
+    o.th = Sym<double>{g[4], g[5], g[6], g[7], g[8], g[9]};
+    return o;
+}
+
+// erf(alpha r)/r weights g_0..g_5 (1/r minus the Ewald real-space kernel)
+__device__ inline void g_erf_d(double r, double alpha, double *g) {
+    double gb[6], ge[6];
+    g_bare<double, 5>(1.0 / r, gb);
+    g_erfc<double, 5>(r, 1.0 / r, alpha, ge);
+    for (int n = 0; n < 6; ++n) g[n] = gb[n] - ge[n];
+}
+
+__device__ inline void addv(double *dst, V3<double> v, double s) {
+    dst[0] += s * v.x;
+    dst[1] += s * v.y;
+    dst[2] += s * v.z;
+}
+__device__ inline void adds(double *dst, const Sym<double> &v, double s) {
+    dst[0] += s * v.xx; dst[1] += s * v.yy; dst[2] += s * v.zz;
+    dst[3] += s * v.xy; dst[4] += s * v.xz; dst[5] += s * v.yz;
+}
+
+// Permanent pass: remove the erf part of the 10 intramolecular site pairs
+// (energy, gradients, sensitivities), add the Gaussian self energy, and
+// correct the field on O/H1/H2 and the potential on the lone pairs.
+template <typename R>
+__global__ void k_intra_perm(KParams p, DevState<R> d) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= p.M) return;
+    V3<double> X[NP];
+    points_d(p, d, m, X);
+    Mp<double> M[NS];
+    for (int s = 0; s < NS; ++s) M[s] = mp_d(d, m, s);
+    const double ke = p.ke, al = p.alpha;
+    double e = 0;
+    for (int t = 0; t < NS; ++t)
+        for (int s = t + 1; s < NS; ++s) {
+            const V3<double> x = X[t] - X[s];
+            const double r = sqrt(dot(x, x));
+            double g[6];
+            g_erf_d(r, al, g);
+            FieldTerms<double> f;
+            source_field<double, 3>(M[s], x, g, f);
+            e += M[t].q * f.phi + dot(M[t].mu, f.d1) + symdd(M[t].th, f.d2) / 3.0;
+            const V3<double> gt = target_grad(M[t], M[s], x, g, f);
+            addv(d.gpt + (m * NP + t) * 3, gt, -ke);
+            addv(d.gpt + (m * NP + s) * 3, gt, ke);
+            addv(d.gmu + (m * NS + t) * 3, f.d1, -ke);
+            adds(d.gth + (m * NS + t) * 6, f.d2, -ke / 3.0);
+            FieldTerms<double> f2;
+            source_field<double, 2>(M[t], -x, g, f2);
+            addv(d.gmu + (m * NS + s) * 3, f2.d1, -ke);
+            adds(d.gth + (m * NS + s) * 6, f2.d2, -ke / 3.0);
+        }
+    double self = 0;
+    for (int s = 0; s < NS; ++s)
+        self += M[s].q * M[s].q + (2.0 * al * al / 3.0) * dot(M[s].mu, M[s].mu) +
+                (8.0 * al * al * al * al / 45.0) * symdd(M[s].th, M[s].th);
+    self *= -ke * al / sqrt(M_PI);
+    d.epart[m * NTERM + T_ELEC] += -ke * e + self;
+    // field on the polarizable atoms: remove intramolecular erf fields, add the self term
+    const double cself = 4.0 * al * al * al / (3.0 * sqrt(M_PI));
+    for (int a = 0; a < 3; ++a) {
+        V3<double> E = cself * M[a].mu;
+        for (int s = 0; s < NS; ++s) {
+            if (s == a) continue;
+            const V3<double> x = X[a] - X[s];
+            double g[6];
+            g_erf_d(sqrt(dot(x, x)), al, g);
+            FieldTerms<double> f;
+            source_field<double, 1>(M[s], x, g, f);
+            E = E + f.d1;
+        }
+        addv(d.efield + m * 9 + a * 3, E, 1.0);
+    }
+    // lone-pair potential: remove the own molecule's erf part
+    for (int l = 0; l < 2; ++l) {
+        double V = 0;
+        V3<double> dV = mk(0.0, 0.0, 0.0);
+        for (int s = 0; s < NS; ++s) {
+            const V3<double> x = X[5 + l] - X[s];
+            double g[6];
+            g_erf_d(sqrt(dot(x, x)), al, g);
+            FieldTerms<double> f;
+            source_field<double, 1>(M[s], x, g, f);
+            V += f.phi;
+            dV = dV + f.d1;
+        }
+        d.vlp[m * 2 + l] -= ke * V;
+        addv(d.dvlp + (m * 2 + l) * 3, dV, -ke);
+    }
+}
+
+template <typename R>
+void launch_intra_perm(const KParams &p, DevState<R> &d, Launch L) {
+    k_intra_perm<R><<<(p.M + 127) / 128, 128, 0, L.s>>>(p, d);
+    count(L);
+}
+
+// PCG product, intramolecular part (periodic): out += erf-field removal and self term.
+template <typename R>
+__global__ void k_intra_tmu(KParams p, DevState<R> d, const double *vec, double *out) {
+    if (d.scal[S_DONE] != 0.0) return;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= p.M) return;
+    V3<double> X[NP];
+    points_d(p, d, m, X);
+    const double al = p.alpha;
+    const double cself = 4.0 * al * al * al / (3.0 * sqrt(M_PI));
+    for (int a = 0; a < 3; ++a) {
+        V3<double> E = cself * mk(vec[m * 9 + a * 3], vec[m * 9 + a * 3 + 1], vec[m * 9 + a * 3 + 2]);
+        for (int b = 0; b < 3; ++b) {
+            if (b == a) continue;
+            const V3<double> x = X[a] - X[b];
+            double g[6];
+            g_erf_d(sqrt(dot(x, x)), al, g);
+            Mp<double> s{};
+            s.mu = mk(vec[m * 9 + b * 3], vec[m * 9 + b * 3 + 1], vec[m * 9 + b * 3 + 2]);
+            FieldTerms<double> f;
+            source_field<double, 1>(s, x, g, f);
+            E = E + f.d1;
+        }
+        addv(out + m * 9 + a * 3, E, 1.0);
+    }
+}
+
+template <typename R>
+void launch_intra_tmu(const KParams &p, DevState<R> &d, const double *vec, double *out, Launch L) {
+    k_intra_tmu<R><<<(p.M + 127) / 128, 128, 0, L.s>>>(p, d, vec, out);
+    count(L);
+}
+
+// Force pass, intramolecular corrections (periodic) at fixed mu and lambda.
+template <typename R>
+__global__ void k_intra_polforce(KParams p, DevState<R> d) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= p.M) return;
+    V3<double> X[NP];
+    points_d(p, d, m, X);
+    Mp<double> M[NS];
+    for (int s = 0; s < NS; ++s) M[s] = mp_d(d, m, s);
+    V3<double> mu[3];
+    for (int a = 0; a < 3; ++a) mu[a] = mk(d.mu[m * 9 + a * 3], d.mu[m * 9 + a * 3 + 1], d.mu[m * 9 + a * 3 + 2]);
+    const double ke = p.ke, al = p.alpha;
+    // induced dipole a with permanent site s != a
+    for (int a = 0; a < 3; ++a)
+        for (int s = 0; s < NS; ++s) {
+            if (s == a) continue;
+            const V3<double> x = X[a] - X[s];
+            double g[6];
+            g_erf_d(sqrt(dot(x, x)), al, g);
+            FieldTerms<double> f;
+            source_field<double, 2>(M[s], x, g, f);
+            const V3<double> ga = symv(f.d2, mu[a]);
+            addv(d.gpt + (m * NP + a) * 3, ga, -ke);
+            addv(d.gpt + (m * NP + s) * 3, ga, ke);
+            Mp<double> dip{};
+            dip.mu = mu[a];
+            FieldTerms<double> f2;
+            source_field<double, 2>(dip, -x, g, f2);
+            addv(d.gmu + (m * NS + s) * 3, f2.d1, -ke);
+            adds(d.gth + (m * NS + s) * 6, f2.d2, -ke / 3.0);
+        }
+    // induced-induced
+    for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b) {
+            const V3<double> x = X[a] - X[b];
+            double g[6];
+            g_erf_d(sqrt(dot(x, x)), al, g);
+            Mp<double> dip{};
+            dip.mu = mu[b];
+            FieldTerms<double> f;
+            source_field<double, 2>(dip, x, g, f);
+            const V3<double> ga = symv(f.d2, mu[a]);
+            addv(d.gpt + (m * NP + a) * 3, ga, -ke);
+            addv(d.gpt + (m * NP + b) * 3, ga, ke);
+        }
+    // self cross term  -ke (4 a^3 / 3 sqrt(pi)) mu_ind . mu_perm : sensitivity of the permanent dipole
+    const double cself = 4.0 * al * al * al / (3.0 * sqrt(M_PI));
+    for (int a = 0; a < 3; ++a) addv(d.gmu + (m * NS + a) * 3, mu[a], -ke * cself);
+    // lambda charges on the lone pairs with the own molecule's sites
+    for (int l = 0; l < 2; ++l) {
+        const double lq = d.lam[m * 2 + l];
+        if (lq == 0.0) continue;
+        for (int s = 0; s < NS; ++s) {
+            const V3<double> x = X[s] - X[5 + l];
+            double g[6];
+            g_erf_d(sqrt(dot(x, x)), al, g);
+            Mp<double> c{};
+            c.q = lq;
+            FieldTerms<double> f;
+            source_field<double, 3>(c, x, g, f);
+            const V3<double> gs = target_grad(M[s], c, x, g, f);
+            addv(d.gpt + (m * NP + s) * 3, gs, -ke);
+            addv(d.gmu + (m * NS + s) * 3, f.d1, -ke);
+            adds(d.gth + (m * NS + s) * 6, f.d2, -ke / 3.0);
+        }
+    }
+}
+
+template <typename R>
+void launch_intra_polforce(const KParams &p, DevState<R> &d, Launch L) {
+    k_intra_polforce<R><<<(p.M + 127) / 128, 128, 0, L.s>>>(p, d);
+    count(L);
+}
+
+// ---------------------------------------------------------------------------
+// Chain rule to atom forces.  Frame construction: z along zv, x in the
+// (z, xv) plane, y = z x x; its vector-Jacobian product maps gradients of the
+// axes back to zv and xv.
+// ---------------------------------------------------------------------------
+__device__ inline void frame_vjp(V3<double> zv, V3<double> xv, V3<double> gx, V3<double> gy, V3<double> gz,
+                                 V3<double> &gzv, V3<double> &gxv) {
+    const double nz = sqrt(dot(zv, zv));
+    const V3<double> ez = (1.0 / nz) * zv;
+    const V3<double> xp = xv - dot(xv, ez) * ez;
+    const double nx = sqrt(dot(xp, xp));
+    const V3<double> ex = (1.0 / nx) * xp;
+    // y = z x x
+    gz = gz + cross(ex, gy);
+    gx = gx + cross(gy, ez);
+    // x = xp / |xp|
+    const V3<double> gxp = (1.0 / nx) * (gx - dot(gx, ex) * ex);
+    // xp = xv - (xv.z) z
+    gxv = gxp - dot(gxp, ez) * ez;
+    gz = gz - dot(xv, ez) * gxp - dot(gxp, ez) * xv;
+    // z = zv / |zv|
+    gzv = (1.0 / nz) * (gz - dot(gz, ez) * ez);
+}
+
+template <typename R>
+__global__ void k_finalize(KParams p, DevState<R> d, double *forces) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= p.M) return;
+    const double *x = d.pos + m * 9;
+    const V3<double> O = mk(x[0], x[1], x[2]), H1 = mk(x[3], x[4], x[5]), H2 = mk(x[6], x[7], x[8]);
+    V3<double> X[NP];
+    points_d(p, d, m, X);
+    V3<double> G[NP];
+    for (int k = 0; k < NP; ++k)
+        G[k] = mk(d.gpt[(m * NP + k) * 3], d.gpt[(m * NP + k) * 3 + 1], d.gpt[(m * NP + k) * 3 + 2]);
+    // lone pairs: charge-transfer dependence through their potential
+    for (int l = 0; l < 2; ++l) {
+        const double lq = d.lam[m * 2 + l];
+        G[5 + l] = G[5 + l] + lq * mk(d.dvlp[(m * 2 + l) * 3], d.dvlp[(m * 2 + l) * 3 + 1], d.dvlp[(m * 2 + l) * 3 + 2]);
+    }
+    // charge-transfer dependence through the intramolecular potentials V_int(O, H1, H2)
+    for (int a = 0; a < 3; ++a) {
+        const double k = d.kap[m * 3 + a];
+        if (k == 0.0) continue;
+        for (int s = 0; s < NS; ++s) {
+            if (s == a) continue;
+            const V3<double> dd = X[a] - X[s];
+            const double r = sqrt(dot(dd, dd));
+            const double qs = (double)d.gmp[(m * NS + s) * NMP];
+            const double c = k * p.ke * qs / (r * r * r);
+            G[a] = G[a] - c * dd;
+            G[s] = G[s] + c * dd;
+        }
+    }
+    // midpoints
+    V3<double> gO = G[0] + 0.5 * (G[3] + G[4]);
+    V3<double> gH1 = G[1] + 0.5 * G[3];
+    V3<double> gH2 = G[2] + 0.5 * G[4];
+    // frames: gradients of the axes from the multipole sensitivities
+    const V3<double> r1 = H1 - O, r2 = H2 - O;
+    const double n1 = sqrt(dot(r1, r1)), n2 = sqrt(dot(r2, r2));
+    const V3<double> u1 = (1.0 / n1) * r1, u2 = (1.0 / n2) * r2;
+    V3<double> zv[3] = {u1 + u2, O - H1, O - H2};
+    V3<double> xv[3] = {r1, H2 - H1, H1 - H2};
+    V3<double> E[3][3];
+    for (int f = 0; f < 3; ++f) frame_d2(zv[f], xv[f], E[f][0], E[f][1], E[f][2]);
+    V3<double> gE[3][3];
+    for (int f = 0; f < 3; ++f)
+        for (int k = 0; k < 3; ++k) gE[f][k] = mk(0.0, 0.0, 0.0);
+    const int fr_of[5] = {0, 1, 2, 1, 2};
+    for (int s = 0; s < NS; ++s) {
+        const int f = fr_of[s];
+        const double *ml = d.mp_local + (m * NS + s) * NMP;
+        const V3<double> gmu = mk(d.gmu[(m * NS + s) * 3], d.gmu[(m * NS + s) * 3 + 1], d.gmu[(m * NS + s) * 3 + 2]);
+        const double *gt6 = d.gth + (m * NS + s) * 6;
+        const Sym<double> D{gt6[0], gt6[1], gt6[2], gt6[3], gt6[4], gt6[5]};
+        const double tl[3][3] = {{ml[4], ml[7], ml[8]}, {ml[7], ml[5], ml[9]}, {ml[8], ml[9], ml[6]}};
+        for (int k = 0; k < 3; ++k) {
+            gE[f][k] = gE[f][k] + ml[1 + k] * gmu;
+            V3<double> acc = mk(0.0, 0.0, 0.0);
+            for (int l = 0; l < 3; ++l) acc = acc + tl[k][l] * E[f][l];
+            gE[f][k] = gE[f][k] + 2.0 * symv(D, acc);
+        }
+    }
+    // lone pairs: X = O + d (-c z_O +/- s y_O)
+    for (int l = 0; l < 2; ++l) {
+        const double sg = l == 0 ? 1.0 : -1.0;
+        gO = gO + G[5 + l];
+        gE[0][2] = gE[0][2] + (-p.d_lp * p.lp_cos) * G[5 + l];
+        gE[0][1] = gE[0][1] + (sg * p.d_lp * p.lp_sin) * G[5 + l];
+    }
+    // back through the three frames
+    for (int f = 0; f < 3; ++f) {
+        V3<double> gzv, gxv;
+        frame_vjp(zv[f], xv[f], gE[f][0], gE[f][1], gE[f][2], gzv, gxv);
+        if (f == 0) {
+            // zv = u1 + u2, u_k = r_k/|r_k|; xv = r1
+            const V3<double> gr1 = (1.0 / n1) * (gzv - dot(gzv, u1) * u1) + gxv;
+            const V3<double> gr2 = (1.0 / n2) * (gzv - dot(gzv, u2) * u2);
+            gH1 = gH1 + gr1;
+            gH2 = gH2 + gr2;
+            gO = gO - gr1 - gr2;
+        } else if (f == 1) {
+            // zv = O - H1, xv = H2 - H1
+            gO = gO + gzv;
+            gH1 = gH1 - gzv - gxv;
+            gH2 = gH2 + gxv;
+        } else {
+            // zv = O - H2, xv = H1 - H2
+            gO = gO + gzv;
+            gH2 = gH2 - gzv - gxv;
+            gH1 = gH1 + gxv;
+        }
+    }
+    if (forces) {
+        double *F = forces + m * 9;
+        F[0] = -gO.x; F[1] = -gO.y; F[2] = -gO.z;
+        F[3] = -gH1.x; F[4] = -gH1.y; F[5] = -gH1.z;
+        F[6] = -gH2.x; F[7] = -gH2.y; F[8] = -gH2.z;
+    }
+}
+
+template <typename R>
+void launch_finalize(const KParams &p, DevState<R> &d, double *forces_out, Launch L) {
+    k_finalize<R><<<(p.M + 127) / 128, 128, 0, L.s>>>(p, d, forces_out);
+    count(L);
+}
+
+// energy totals: out[k] = sum_m epart[m*NTERM + k], out[NTERM] = total (fixed order)
+__global__ void k_energy_reduce(int M, const double *epart, double *out) {
+    __shared__ double sh[32];
+    double tot = 0;
+    for (int k = 0; k < NTERM; ++k) {
+        double v = 0;
+        for (int m = threadIdx.x; m < M; m += blockDim.x) v += epart[m * NTERM + k];
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) {
+            out[k] = v;
+            tot += v;
+        }
+    }
+    if (threadIdx.x == 0) out[NTERM] = tot;
+}
+
+void launch_energy_reduce(int M, const double *epart, double *out, Launch L) {
+    k_energy_reduce<<<1, 512, 0, L.s>>>(M, epart, out);
+    count(L);
+}
+
+// velocity-Verlet half kick (and drift): v += dt/2 F/m ; x += dt v
+__global__ void k_md_kick(int M, double *pos, double *vel, const double *inv_mass, const double *F, double dt,
+                          int drift) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M * 9) return;
+    const double conv = 4.184e-4;   // (kcal/mol/A)/amu -> A/fs^2
+    double v = vel[k] + 0.5 * dt * F[k] * inv_mass[k / 3] * conv;
+    vel[k] = v;
+    if (drift) pos[k] += dt * v;
+}
+
+void launch_md_kick(int M, double *pos, double *vel, const double *inv_mass, const double *forces, double dt,
+                    int drift, Launch L) {
+    k_md_kick<<<(M * 9 + 255) / 256, 256, 0, L.s>>>(M, pos, vel, inv_mass, forces, dt, drift);
+    count(L);
+}
+
+#define INST(R)                                                                                        \
+    template void launch_pcg_init<R>(const KParams &, DevState<R> &, int, Launch);                     \
+    template void launch_pcg_first<R>(const KParams &, DevState<R> &, Launch);                         \
+    template void launch_pcg_iter_a<R>(const KParams &, DevState<R> &, Launch);                        \
+    template void launch_pcg_iter_b<R>(const KParams &, DevState<R> &, double, Launch);                \
+    template void launch_pol_energy<R>(const KParams &, DevState<R> &, Launch);                        \
+    template void launch_intra_perm<R>(const KParams &, DevState<R> &, Launch);                        \
+    template void launch_intra_tmu<R>(const KParams &, DevState<R> &, const double *, double *, Launch); \
+    template void launch_intra_polforce<R>(const KParams &, DevState<R> &, Launch);                    \
+    template void launch_finalize<R>(const KParams &, DevState<R> &, double *, Launch);
+INST(float)
+INST(double)
+
+}  // namespace sibfa

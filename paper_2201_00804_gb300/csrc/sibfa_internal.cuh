@@ -1,0 +1,441 @@
+// Internal declarations of the SIBFA CUDA library: device state, kernel
+// parameters, vector helpers, radial kernels and the multipole field
+// evaluation shared by the pair and grid kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include "../../include/sibfa.h"
+
+namespace sibfa {
+
+constexpr int NS = 5;          // multipole sites per water: O, H1, H2, M1, M2
+constexpr int NP = 7;          // points per water: 5 sites + 2 lone pairs
+constexpr int NMP = 10;        // q, mu(3), theta(6: xx yy zz xy xz yz)
+constexpr int MAXN = 384;      // neighbour slots per molecule
+constexpr int NTERM = 7;       // elec pen rep disp xdisp pol ct
+enum { T_ELEC = 0, T_PEN, T_REP, T_DISP, T_XDISP, T_POL, T_CT };
+constexpr int ORDER = 5;       // B-spline order of the SPME
+
+// error flags (bitwise, device side)
+enum { F_CUTOFF = 1, F_NEIGHBOR = 2, F_CTDEN = 4, F_NAN = 8 };
+
+// ---------------------------------------------------------------------------
+// Kernel parameters (by value).  Double values are converted to R at use.
+// ---------------------------------------------------------------------------
+struct KParams {
+    int M;
+    int periodic;
+    double box[3];
+    double rc, rc2;
+    double alpha;          // Ewald
+    int K[3];
+    double ke;
+    double d_lp, lp_cos, lp_sin;
+    double a_pol[3];       // O, H, H polarizabilities
+    double a_damp[5];      // site polarizabilities used in Thole damping
+    double thole;
+    double z[5], b[5];     // nuclear charge and valence damping per site (0 on midpoints)
+    // repulsion
+    double cs_o, cp_o, cs_h, cp_h, cs_lp, cp_lp, g_o, g_h, nval_o, nval_h;
+    double rv_rep_o, rv_rep_h, rv_rep_lp, rep_a1, rep_a2, rep_c1, rep_c2, rep_f, occ, nlp;
+    // dispersion
+    double rv_d[5];        // O, H, H, LP, LP
+    double beta[5];
+    double disp_alpha, c6, c8, c10, g6, g8, g10, delta;
+    double xd_c1, xd_a1, xd_c2, xd_a2, xd_c3, xd_a3;
+    // charge transfer
+    double ct_eta, ct_t, ct_m, ct_ae, ct_ah, rv_ct_o, rv_ct_h;
+};
+
+// ---------------------------------------------------------------------------
+// Device state.  Per-molecule arrays are SoA-by-molecule: index m*stride+k.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct DevState {
+    int M;
+    double *pos;        // M*9 working positions (O, H1, H2)
+    double *mp_local;   // M*50
+    R *off;             // M*NP*3 point offsets from own O (5 sites + 2 LPs)
+    R *gmp;             // M*NS*NMP global multipoles
+    double *vint;       // M*3 intramolecular potential on O, H1, H2 (charge-transfer V_int)
+    int *nbr;           // M*MAXN neighbour molecules (full list)
+    int *nnbr;          // M
+    // cell list
+    int *cell_of;       // M
+    int *cell_start;    // ncell+1
+    int *cell_cursor;   // ncell
+    int *cell_mol;      // M
+    // gradients dE/dx (double) and multipole sensitivities
+    double *gpt;        // M*NP*3 dE/d(point)
+    double *gmu;        // M*NS*3 dE/dmu_global
+    double *gth;        // M*NS*6 dE/dTheta_global (symmetric, components as stored)
+    double *efield;     // M*9 permanent field on O, H1, H2 (Thole-damped real + recip - excl + self)
+    double *d2rec;      // M*3*6 reciprocal Hessian of the permanent potential at O, H1, H2
+    double *vlp;        // M*2 potential on lone pairs (undamped, own molecule excluded)
+    double *dvlp;       // M*2*3 its gradient
+    double *lam;        // M*2 dE_ct/dV_lp
+    double *kap;        // M*3 dE_ct/dV_int
+    double *epart;      // M*NTERM per-molecule energy partials
+    // polarization solve
+    double *mu, *res, *zv, *pv, *ap, *efp;   // M*9 each
+    double *partial;    // reduction partials
+    double *scal;       // device scalars (see pcg kernels)
+    unsigned int *counter;
+    int *flags;         // error flags
+    float *ext;         // maximum point distance from own O (float bits, atomicMax)
+    // grids
+    R *grid;            // 2 * K0*K1*K2 (two real grids for the force pass)
+    void *cgrid;        // 2 * K0*K1*(K2/2+1) complex
+    double *infl;       // K0*K1*(K2/2+1) influence function / (K0 K1 K2)
+};
+
+// ---------------------------------------------------------------------------
+// Small vector helpers
+// ---------------------------------------------------------------------------
+template <typename R>
+struct V3 {
+    R x, y, z;
+};
+template <typename R>
+__host__ __device__ inline V3<R> mk(R a, R b, R c) { return V3<R>{a, b, c}; }
+template <typename R>
+__host__ __device__ inline V3<R> operator+(V3<R> a, V3<R> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename R>
+__host__ __device__ inline V3<R> operator-(V3<R> a, V3<R> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename R>
+__host__ __device__ inline V3<R> operator-(V3<R> a) { return {-a.x, -a.y, -a.z}; }
+template <typename R>
+__host__ __device__ inline V3<R> operator*(R s, V3<R> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <typename R>
+__host__ __device__ inline R dot(V3<R> a, V3<R> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename R>
+__host__ __device__ inline V3<R> cross(V3<R> a, V3<R> b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+template <typename R> __device__ inline R rsqrt_(R x);
+template <> __device__ inline float rsqrt_<float>(float x) { return rsqrtf(x); }
+template <> __device__ inline double rsqrt_<double>(double x) { return rsqrt(x); }
+template <typename R> __device__ inline R exp_(R x);
+template <> __device__ inline float exp_<float>(float x) { return expf(x); }
+template <> __device__ inline double exp_<double>(double x) { return exp(x); }
+template <typename R> __device__ inline R erfc_(R x);
+template <> __device__ inline float erfc_<float>(float x) { return erfcf(x); }
+template <> __device__ inline double erfc_<double>(double x) { return erfc(x); }
+template <typename R> __device__ inline R sqrt_(R x);
+template <> __device__ inline float sqrt_<float>(float x) { return sqrtf(x); }
+template <> __device__ inline double sqrt_<double>(double x) { return sqrt(x); }
+
+// Symmetric 3x3 stored as xx yy zz xy xz yz
+template <typename R>
+struct Sym {
+    R xx, yy, zz, xy, xz, yz;
+};
+template <typename R>
+__device__ inline V3<R> symv(const Sym<R> &t, V3<R> v) {
+    return {t.xx * v.x + t.xy * v.y + t.xz * v.z, t.xy * v.x + t.yy * v.y + t.yz * v.z,
+            t.xz * v.x + t.yz * v.y + t.zz * v.z};
+}
+template <typename R>
+__device__ inline R symdd(const Sym<R> &a, const Sym<R> &b) {
+    return a.xx * b.xx + a.yy * b.yy + a.zz * b.zz + R(2) * (a.xy * b.xy + a.xz * b.xz + a.yz * b.yz);
+}
+
+// A point multipole: charge, dipole, traceless quadrupole (1/3 convention:
+// phi = q g0 - mu.grad g0 + (1/3) Theta : grad grad g0).
+template <typename R>
+struct Mp {
+    R q;
+    V3<R> mu;
+    Sym<R> th;
+};
+
+// ---------------------------------------------------------------------------
+// Radial kernels: g[n+1](r) = (1/r) d g[n]/dr.
+// ---------------------------------------------------------------------------
+template <typename R, int N>
+__device__ inline void g_bare(R rinv, R *g) {
+    R r2i = rinv * rinv;
+    g[0] = rinv;
+#pragma unroll
+    for (int n = 1; n <= N; ++n) g[n] = -R(2 * n - 1) * g[n - 1] * r2i;
+}
+
+// erfc(alpha r)/r, Smith's recursion B_n = [(2n-1)B_{n-1} + (2a^2)^n e^{-a^2 r^2}/(a sqrt(pi))]/r^2,
+// g_n = (-1)^n B_n.
+template <typename R, int N>
+__device__ inline void g_erfc(R r, R rinv, R alpha, R *g) {
+    const R r2i = rinv * rinv;
+    const R ar = alpha * r;
+    const R ex = exp_(-ar * ar) * (R(0.56418958354775628695) / alpha);   // 1/(a sqrt(pi))
+    R b = erfc_(ar) * rinv;
+    g[0] = b;
+    R tw = R(2) * alpha * alpha, p = tw;
+#pragma unroll
+    for (int n = 1; n <= N; ++n) {
+        b = (R(2 * n - 1) * b + p * ex) * r2i;
+        p *= tw;
+        g[n] = (n & 1) ? -b : b;
+    }
+}
+
+// exp(-b r)/r: g_n = (-1)^n e^{-b r} theta_n(b r)/r^(2n+1), theta = reverse Bessel polynomials.
+template <typename R, int N>
+__device__ inline void g_exp(R r, R rinv, R bb, R *g) {
+    const R x = bb * r;
+    const R e = exp_(-x) * rinv;
+    R th0 = R(1), th1 = x + R(1);
+    R r2i = rinv * rinv;
+    R pw = e;
+    g[0] = e;
+    if (N >= 1) { pw *= r2i; g[1] = -th1 * pw; }
+#pragma unroll
+    for (int n = 2; n <= N; ++n) {
+        R th2 = R(2 * n - 1) * th1 + x * x * th0;
+        th0 = th1;
+        th1 = th2;
+        pw *= r2i;
+        g[n] = (n & 1) ? -th2 * pw : th2 * pw;
+    }
+}
+
+// Exponential Thole factors on top of a bare or Ewald kernel for n = 1..N.
+// gas:      g_n = lambda_{2n+1} g_n(1/r)
+// periodic: g_n = g_n(erfc) + (lambda_{2n+1} - 1) g_n(1/r)
+template <typename R, int N>
+__device__ inline void g_thole(R r, R rinv, R Ainv3, R a, bool periodic, R alpha, R *g) {
+    R gb[N + 1];
+    g_bare<R, N>(rinv, gb);
+    const R t = a * r * r * r * Ainv3;
+    const R e = exp_(-t);
+    R lam[4];
+    lam[0] = R(1) - e;
+    lam[1] = R(1) - (R(1) + t) * e;
+    lam[2] = R(1) - (R(1) + t + R(0.6) * t * t) * e;
+    lam[3] = R(1) - (R(1) + t + R(18.0 / 35.0) * t * t + R(9.0 / 35.0) * t * t * t) * e;
+    g[0] = R(0);
+    if (periodic) {
+        R ge[N + 1];
+        g_erfc<R, N>(r, rinv, alpha, ge);
+#pragma unroll
+        for (int n = 1; n <= N; ++n) g[n] = ge[n] + (lam[n - 1] - R(1)) * gb[n];
+    } else {
+#pragma unroll
+        for (int n = 1; n <= N; ++n) g[n] = lam[n - 1] * gb[n];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Potential derivatives at displacement x (target minus source) produced by a
+// source multipole s through a radial kernel with weights g[0..5]:
+//   phi, d1 = grad phi, d2 = grad grad phi (symmetric).
+// d3 is never formed: its contraction with a target multipole is returned
+// through the target-side helper below.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct FieldTerms {
+    R phi;
+    V3<R> d1;
+    Sym<R> d2;
+    // intermediates for the third-derivative contraction
+    R Rs, S;
+    V3<R> U, W, v;
+};
+
+template <typename R, int NDER>
+__device__ inline void source_field(const Mp<R> &s, V3<R> x, const R *g, FieldTerms<R> &f) {
+    const R sx = dot(s.mu, x);
+    const V3<R> v = symv(s.th, x);
+    const R w = dot(x, v);
+    const R third = R(1) / R(3), twoth = R(2) / R(3);
+    f.phi = s.q * g[0] - sx * g[1] + third * w * g[2];
+    if constexpr (NDER >= 1) {
+        const R P = s.q * g[1] - sx * g[2] + third * w * g[3];
+        const V3<R> Q = R(-g[1]) * s.mu + (twoth * g[2]) * v;
+        f.d1 = P * x + Q;
+        if constexpr (NDER >= 2) {
+            const R Rr = s.q * g[2] - sx * g[3] + third * w * g[4];
+            const V3<R> U = R(-g[2]) * s.mu + (twoth * g[3]) * v;
+            const R t2 = twoth * g[2];
+            f.d2.xx = P + x.x * x.x * Rr + R(2) * x.x * U.x + t2 * s.th.xx;
+            f.d2.yy = P + x.y * x.y * Rr + R(2) * x.y * U.y + t2 * s.th.yy;
+            f.d2.zz = P + x.z * x.z * Rr + R(2) * x.z * U.z + t2 * s.th.zz;
+            f.d2.xy = x.x * x.y * Rr + x.x * U.y + x.y * U.x + t2 * s.th.xy;
+            f.d2.xz = x.x * x.z * Rr + x.x * U.z + x.z * U.x + t2 * s.th.xz;
+            f.d2.yz = x.y * x.z * Rr + x.y * U.z + x.z * U.y + t2 * s.th.yz;
+            f.Rs = Rr;
+            f.U = U;
+            if constexpr (NDER >= 3) {
+                f.S = s.q * g[3] - sx * g[4] + third * w * g[5];
+                f.W = R(-g[3]) * s.mu + (twoth * g[4]) * v;
+                f.v = v;
+            }
+        }
+    }
+}
+
+// Target contraction.  Energy U = q phi + mu.d1 + (1/3) Th:d2; gradient of U
+// with respect to the target position (= -force) needs d3:
+//   dU/dx = q d1 + d2.mu + (1/3) Th : d3.
+// With Phi = target quadrupole (traceless), Theta = source quadrupole:
+//   (Phi:d3)_a = 2 (Phi (x R + U))_a + x_a [ (x Phi x) S + 2 x.Phi.W ]
+//               + (x Phi x) W_a + (2/3) g3 [ 2 (Theta Phi x)_a + x_a (Phi:Theta) ]
+template <typename R>
+__device__ inline V3<R> target_grad(const Mp<R> &t, const Mp<R> &s, V3<R> x, const R *g,
+                                    const FieldTerms<R> &f) {
+    V3<R> gr = t.q * f.d1 + symv(f.d2, t.mu);
+    const V3<R> px = symv(t.th, x);
+    const R xpx = dot(x, px);
+    const V3<R> a1 = f.Rs * px + symv(t.th, f.U);       // Phi (x R + U)
+    const R xpw = dot(px, f.W);
+    const V3<R> thpx = symv(s.th, px);                   // Theta Phi x
+    const R pdt = symdd(t.th, s.th);
+    const R c3 = R(2.0 / 3.0) * g[3];
+    V3<R> th3 = R(2) * a1 + (xpx * f.S + R(2) * xpw) * x + xpx * f.W + c3 * (R(2) * thpx + pdt * x);
+    return gr + R(1.0 / 3.0) * th3;
+}
+
+// ---------------------------------------------------------------------------
+// Cardinal B-spline weights of order 5 and derivatives (w.r.t. u) at
+// arguments w + j, j = 0..4, w = frac(u); grid point of j is floor(u) - j.
+// ---------------------------------------------------------------------------
+template <typename R, int NDER>
+__device__ inline void bspline5(R w, R *m0, R *m1, R *m2, R *m3) {
+    R b2[2] = {w, R(1) - w};
+    R b3[3], b4[4];
+    // order 3
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        R v = w + R(j);
+        R a = (j <= 1) ? b2[j] : R(0);
+        R b = (j >= 1) ? b2[j - 1] : R(0);
+        b3[j] = (v * a + (R(3) - v) * b) * R(0.5);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        R v = w + R(j);
+        R a = (j <= 2) ? b3[j] : R(0);
+        R b = (j >= 1) ? b3[j - 1] : R(0);
+        b4[j] = (v * a + (R(4) - v) * b) * R(1.0 / 3.0);
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        R v = w + R(j);
+        R a = (j <= 3) ? b4[j] : R(0);
+        R b = (j >= 1) ? b4[j - 1] : R(0);
+        m0[j] = (v * a + (R(5) - v) * b) * R(0.25);
+        if constexpr (NDER >= 1) m1[j] = a - b;
+        if constexpr (NDER >= 2) {
+            R c0 = (j <= 2) ? b3[j] : R(0);
+            R c1 = (j >= 1 && j <= 3) ? b3[j - 1] : R(0);
+            R c2 = (j >= 2) ? b3[j - 2] : R(0);
+            m2[j] = c0 - R(2) * c1 + c2;
+        }
+        if constexpr (NDER >= 3) {
+            R d0 = (j <= 1) ? b2[j] : R(0);
+            R d1 = (j >= 1 && j <= 2) ? b2[j - 1] : R(0);
+            R d2 = (j >= 2 && j <= 3) ? b2[j - 2] : R(0);
+            R d3 = (j >= 3) ? b2[j - 3] : R(0);
+            m3[j] = d0 - R(3) * d1 + R(3) * d2 - d3;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp reduction in double
+// ---------------------------------------------------------------------------
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Compensated (two-sum) accumulator used for per-lane energy partial sums.
+template <typename R>
+struct Acc {
+    R hi = R(0), lo = R(0);
+    __device__ inline void add(R v) {
+        R s = hi + v;
+        R bp = s - hi;
+        R err = (hi - (s - bp)) + (v - bp);
+        hi = s;
+        lo += err;
+    }
+    __device__ inline double get() const { return double(hi) + double(lo); }
+};
+
+// Minimum-image displacement of molecule j's O from molecule i's O (FP64).
+__device__ inline void min_image(const KParams &p, const double *pos, int i, int j, double &dx, double &dy,
+                                 double &dz) {
+    dx = pos[j * 9 + 0] - pos[i * 9 + 0];
+    dy = pos[j * 9 + 1] - pos[i * 9 + 1];
+    dz = pos[j * 9 + 2] - pos[i * 9 + 2];
+    if (p.periodic) {
+        dx -= p.box[0] * rint(dx / p.box[0]);
+        dy -= p.box[1] * rint(dy / p.box[1]);
+        dz -= p.box[2] * rint(dz / p.box[2]);
+    }
+}
+
+template <typename R>
+__device__ inline Mp<R> load_mp(const R *g) {
+    Mp<R> m;
+    m.q = g[0];
+    m.mu = mk(g[1], g[2], g[3]);
+    m.th = Sym<R>{g[4], g[5], g[6], g[7], g[8], g[9]};
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (explicitly instantiated for float and double)
+// ---------------------------------------------------------------------------
+struct Launch {
+    cudaStream_t s;
+    uint64_t *count;
+};
+
+template <typename R> void launch_sites(const KParams &p, DevState<R> &d, Launch L);
+template <typename R> void launch_neighbors(const KParams &p, DevState<R> &d, int ncell[3], Launch L);
+template <typename R> void launch_real_perm(const KParams &p, DevState<R> &d, Launch L);
+template <typename R> void launch_short(const KParams &p, DevState<R> &d, Launch L);
+template <typename R> void launch_ct(const KParams &p, DevState<R> &d, Launch L);
+template <typename R> void launch_intra_perm(const KParams &p, DevState<R> &d, Launch L);
+template <typename R> void launch_real_tmu(const KParams &p, DevState<R> &d, const double *vec, double *out,
+                                           Launch L);
+template <typename R> void launch_intra_tmu(const KParams &p, DevState<R> &d, const double *vec, double *out,
+                                            Launch L);
+template <typename R> void launch_real_polforce(const KParams &p, DevState<R> &d, Launch L);
+template <typename R> void launch_intra_polforce(const KParams &p, DevState<R> &d, Launch L);
+template <typename R> void launch_finalize(const KParams &p, DevState<R> &d, double *forces_out, Launch L);
+
+// SPME
+enum SpreadKind { SPREAD_PERM = 0, SPREAD_DIP = 1, SPREAD_LAMBDA = 2, SPREAD_DIP_PCG = 3 };
+template <typename R> void launch_spread(const KParams &p, DevState<R> &d, int kind, const double *vec, R *grid,
+                                         Launch L);
+template <typename R> void launch_convolve(const KParams &p, DevState<R> &d, void *cgrid, int ngrid, int check,
+                                           Launch L);
+template <typename R> void launch_gather_perm(const KParams &p, DevState<R> &d, Launch L);
+template <typename R> void launch_gather_field(const KParams &p, DevState<R> &d, double *out, Launch L);
+template <typename R> void launch_gather_polforce(const KParams &p, DevState<R> &d, Launch L);
+void launch_influence(const KParams &p, double *infl, Launch L);
+
+// PCG
+template <typename R> void launch_pcg_init(const KParams &p, DevState<R> &d, int warm, Launch L);
+template <typename R> void launch_pcg_first(const KParams &p, DevState<R> &d, Launch L);
+template <typename R> void launch_pcg_iter_a(const KParams &p, DevState<R> &d, Launch L);
+template <typename R> void launch_pcg_iter_b(const KParams &p, DevState<R> &d, double tol_D, Launch L);
+template <typename R> void launch_pol_energy(const KParams &p, DevState<R> &d, Launch L);
+void launch_energy_reduce(int M, const double *epart, double *out, Launch L);
+void launch_begin(double *scal, int *flags, double tol_D, Launch L);
+enum { SC_RZ = 0, SC_RES = 4, SC_IT = 6, SC_DONE = 7, SC_TOL = 8 };
+void launch_md_kick(int M, double *pos, double *vel, const double *inv_mass, const double *forces, double dt,
+                    int drift, Launch L);
+
+inline void count(Launch &L, int n = 1) {
+    if (L.count) *L.count += n;
+}
+
+}  // namespace sibfa

@@ -1,0 +1,215 @@
+"""Thin ctypes binding of the SIBFA C ABI (include/sibfa.h).
+
+Argument marshalling only: every step of an evaluation runs in the CUDA
+library.  Arrays may be torch tensors (host or CUDA) or numpy arrays; they
+must be float64 and contiguous.  The functions keep the C names.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsibfa.so")
+
+PARAM_FIELDS = (
+    "ke debye d_lp lp_half_deg alpha_o alpha_h alpha_m_damp thole z_o z_h b_o b_h "
+    "cs_o cp_o cs_h cp_h cs_lp cp_lp g_o g_h nval_o nval_h "
+    "rvdw_rep_o rvdw_rep_h rvdw_rep_lp rep_alpha rep_alpha2 rep_c1 rep_c2 rep_f occ_bond n_lp "
+    "rvdw_disp_o rvdw_disp_h rvdw_disp_lp disp_alpha beta_o beta_h c6 c8 c10 gamma6 gamma8 gamma10 disp_delta "
+    "xd_c1 xd_a1 xd_c2 xd_a2 xd_c3 xd_a3 ct_eta ct_t ct_m ct_ae ct_ah rvdw_ct_o rvdw_ct_h"
+).split()
+TERMS = ("elec", "pen", "rep", "disp", "xdisp", "pol", "ct", "total")
+
+SIBFA_OK = 0
+STATUS = {0: "OK", -1: "INVALID", -2: "OOM", -3: "NOT_CONVERGED", -4: "CUTOFF", -5: "CT_DENOM",
+          -6: "TIMEOUT", -7: "CUDA", -8: "BUSY", -9: "NEIGHBOR"}
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class sibfa_params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in PARAM_FIELDS]
+
+
+class sibfa_topology(C.Structure):
+    _fields_ = [("n_mol", C.c_int), ("mp_local", C.POINTER(C.c_double))]
+
+
+class sibfa_run_opts(C.Structure):
+    _fields_ = [("periodic", C.c_int), ("box", C.c_double * 3), ("rc", C.c_double), ("grid", C.c_int * 3),
+                ("order", C.c_int), ("ewald_alpha", C.c_double), ("pcg_tol_D", C.c_double),
+                ("pcg_max_iter", C.c_int), ("precision", C.c_int), ("warm_start", C.c_int),
+                ("stream", C.c_void_p)]
+
+
+class sibfa_energy_terms(C.Structure):
+    _fields_ = [(n, C.c_double) for n in TERMS]
+
+
+class SibfaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libsibfa.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it first (paper_2201_00804_gb300.build.build())")
+    lib = C.CDLL(path)
+    lib.sibfa_create.argtypes = [C.POINTER(sibfa_params), C.POINTER(sibfa_topology), C.POINTER(sibfa_run_opts),
+                                 C.POINTER(C.c_void_p)]
+    lib.sibfa_create.restype = C.c_int
+    lib.sibfa_energy_forces.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(sibfa_energy_terms),
+                                        C.c_void_p, C.c_void_p]
+    lib.sibfa_energy_forces.restype = C.c_int
+    lib.sibfa_solve_dipoles.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                        C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    lib.sibfa_solve_dipoles.restype = C.c_int
+    lib.sibfa_md_steps.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                                   C.POINTER(sibfa_energy_terms)]
+    lib.sibfa_md_steps.restype = C.c_int
+    lib.sibfa_last_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    lib.sibfa_last_stats.restype = C.c_int
+    lib.sibfa_kernel_launches.argtypes = [C.c_void_p]
+    lib.sibfa_kernel_launches.restype = C.c_uint64
+    lib.sibfa_set_profiling.argtypes = [C.c_void_p, C.c_int]
+    lib.sibfa_set_profiling.restype = None
+    lib.sibfa_profile_get.argtypes = [C.c_void_p, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    lib.sibfa_profile_get.restype = C.c_int
+    lib.sibfa_profile_clear.argtypes = [C.c_void_p]
+    lib.sibfa_profile_clear.restype = None
+    lib.sibfa_destroy.argtypes = [C.c_void_p]
+    lib.sibfa_destroy.restype = None
+    lib.sibfa_last_error.argtypes = [C.c_void_p]
+    lib.sibfa_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Raw pointer of a float64 contiguous torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("arrays must be C-contiguous float64")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(lib, ctx, st):
+    if st != SIBFA_OK:
+        raise SibfaError(st, lib.sibfa_last_error(ctx).decode())
+
+
+def sibfa_create(params: dict, mp_local: np.ndarray, *, periodic: bool, box=None, rc=9.0, grid=64, order=5,
+                 ewald_alpha=0.4, pcg_tol_D=1e-6, pcg_max_iter=200, precision=PREC_MIXED, warm_start=True,
+                 stream=None):
+    """Create a context.  mp_local: (n_mol, 5, 10) float64 host array.
+    stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+    lib = load_library()
+    P = sibfa_params(*[float(params[n]) for n in PARAM_FIELDS])
+    mp = np.ascontiguousarray(mp_local, dtype=np.float64)
+    topo = sibfa_topology(mp.shape[0], mp.ctypes.data_as(C.POINTER(C.c_double)))
+    o = sibfa_run_opts()
+    o.periodic = 1 if periodic else 0
+    if box is not None:
+        for k in range(3):
+            o.box[k] = float(box[k])
+    o.rc = float(rc)
+    g = (grid, grid, grid) if np.isscalar(grid) else tuple(grid)
+    for k in range(3):
+        o.grid[k] = int(g[k])
+    o.order = int(order)
+    o.ewald_alpha = float(ewald_alpha)
+    o.pcg_tol_D = float(pcg_tol_D)
+    o.pcg_max_iter = int(pcg_max_iter)
+    o.precision = int(precision)
+    o.warm_start = 1 if warm_start else 0
+    if stream is not None:
+        o.stream = int(getattr(stream, "cuda_stream", stream))
+    out = C.c_void_p()
+    st = lib.sibfa_create(C.byref(P), C.byref(topo), C.byref(o), C.byref(out))
+    _check(lib, None, st)
+    return out
+
+
+def sibfa_energy_forces(ctx, pos, forces=None, box=None):
+    """One evaluation; returns a dict of energy terms (kcal/mol).  forces (same
+    shape as pos) is filled in place when given."""
+    lib = load_library()
+    e = sibfa_energy_terms()
+    st = lib.sibfa_energy_forces(ctx, _ptr(pos), _ptr(box), C.byref(e), _ptr(forces), None)
+    _check(lib, ctx, st)
+    return {n: getattr(e, n) for n in TERMS}
+
+
+def sibfa_solve_dipoles(ctx, pos, mu=None, tol_D=0.0, box=None):
+    """Solve T mu = E only; returns (iterations, residual in D)."""
+    lib = load_library()
+    it = C.c_int()
+    res = C.c_double()
+    st = lib.sibfa_solve_dipoles(ctx, _ptr(pos), _ptr(box), float(tol_D), _ptr(mu), C.byref(it), C.byref(res))
+    _check(lib, ctx, st)
+    return it.value, res.value
+
+
+def sibfa_md_steps(ctx, pos, vel, masses, dt_fs, n_steps):
+    """Velocity-Verlet NVE steps on device arrays; returns the last energy terms."""
+    lib = load_library()
+    e = sibfa_energy_terms()
+    st = lib.sibfa_md_steps(ctx, _ptr(pos), _ptr(vel), _ptr(masses), float(dt_fs), int(n_steps), C.byref(e))
+    _check(lib, ctx, st)
+    return {n: getattr(e, n) for n in TERMS}
+
+
+def sibfa_last_stats(ctx):
+    lib = load_library()
+    it = C.c_int()
+    res = C.c_double()
+    _check(lib, ctx, lib.sibfa_last_stats(ctx, C.byref(it), C.byref(res)))
+    return it.value, res.value
+
+
+def sibfa_kernel_launches(ctx) -> int:
+    return int(load_library().sibfa_kernel_launches(ctx))
+
+
+def sibfa_set_profiling(ctx, on: bool):
+    load_library().sibfa_set_profiling(ctx, 1 if on else 0)
+
+
+def sibfa_profile_get(ctx, name: str):
+    """(milliseconds summed, span count) of one phase since its last read."""
+    lib = load_library()
+    ms = C.c_double()
+    n = C.c_int()
+    _check(lib, ctx, lib.sibfa_profile_get(ctx, name.encode(), C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def sibfa_profile_clear(ctx):
+    load_library().sibfa_profile_clear(ctx)
+
+
+def sibfa_destroy(ctx):
+    if ctx:
+        load_library().sibfa_destroy(ctx)
+
+
+def sibfa_last_error(ctx=None) -> str:
+    return load_library().sibfa_last_error(ctx).decode()

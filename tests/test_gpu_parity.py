@@ -1,0 +1,88 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs, in the FP64 path (tight) and the mixed path (energy
+relative error <= 1e-6, force RMS relative error <= 1e-5, induced-dipole RMS
+error <= 1e-6 D)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import (FP64_E_REL, FP64_F_RMS_REL, FP64_MU_RMS_D, MIXED_E_REL, MIXED_F_RMS_REL, MIXED_MU_RMS_D,
+                      compare, run_gpu)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_00804_gb300 import build
+    build.build()
+
+
+_cache = {}
+
+
+def _ref(key, system, opts):
+    if key not in _cache:
+        _cache[key] = oracle.evaluate(system, opts, tol_D=1e-11)
+    return _cache[key]
+
+
+def _cases():
+    return {
+        "cluster8": (synth.make_cluster(8, seed=31), None),
+        "cluster2": (synth.make_cluster(2, seed=32), None),
+        "water216": synth.make_config("water216"),
+        # 512 waters with rc 5.5: three cells per side, exercises the cell list
+        "water512": (synth.make_box(8, 24.83, seed=33), {"rc": 5.5, "grid": 32, "order": 5, "ewald": 0.55}),
+    }
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_path_matches_oracle(name):
+    import paper_2201_00804_gb300 as pkg
+    s, o = CASES[name]
+    ref = _ref(name, s, o)
+    gpu = run_gpu(s, o, pkg.PREC_FP64, 1e-11)
+    compare(gpu, ref, FP64_E_REL, FP64_F_RMS_REL, FP64_MU_RMS_D)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_path_matches_oracle(name):
+    import paper_2201_00804_gb300 as pkg
+    s, o = CASES[name]
+    ref = _ref(name, s, o)
+    gpu = run_gpu(s, o, pkg.PREC_MIXED, 1e-8)
+    compare(gpu, ref, MIXED_E_REL, MIXED_F_RMS_REL, MIXED_MU_RMS_D)
+
+
+def test_host_and_device_pointers_agree():
+    import paper_2201_00804_gb300 as pkg
+    s, o = CASES["water216"]
+    a = run_gpu(s, o, pkg.PREC_MIXED, 1e-8, device=True)
+    b = run_gpu(s, o, pkg.PREC_MIXED, 1e-8, device=False)
+    assert a["terms"]["total"] == pytest.approx(b["terms"]["total"], rel=1e-12)
+    np.testing.assert_allclose(a["forces"], b["forces"], rtol=0, atol=1e-9)
+
+
+def test_single_molecule_has_no_intermolecular_energy():
+    import paper_2201_00804_gb300 as pkg
+    s = synth.make_cluster(1, seed=5)
+    gpu = run_gpu(s, None, pkg.PREC_FP64, 1e-10)
+    for k, v in gpu["terms"].items():
+        assert abs(v) < 1e-12, (k, v)
+    assert np.abs(gpu["forces"]).max() < 1e-12
+
+
+def test_results_are_deterministic():
+    import paper_2201_00804_gb300 as pkg
+    s, o = CASES["water216"]
+    a = run_gpu(s, o, pkg.PREC_FP64, 1e-10)
+    b = run_gpu(s, o, pkg.PREC_FP64, 1e-10)
+    assert a["terms"]["total"] == pytest.approx(b["terms"]["total"], rel=1e-13)
