@@ -255,6 +255,10 @@ def main():
     masses = torch.tensor(s.masses().reshape(-1), dtype=torch.float64, device="cuda")
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     dt_fs = 0.5
+    # The jittered lattice with random orientations starts far from
+    # equilibrium (overlapping hydrogens): relax it first (untimed).
+    pkg.sibfa_minimize(ctx, pos, 20, 0.01)
+    snapshots = []
 
     for _ in range(max(3, args.warmup)):
         pkg.sibfa_md_steps(ctx, pos, vel, masses, dt_fs, 1)
@@ -277,6 +281,7 @@ def main():
             b.synchronize()
             total_ms += a.elapsed_time(b)
             iters.append(pkg.sibfa_last_stats(ctx)[0])
+            snapshots.append(pos.clone())
     torch.cuda.synchronize()
     barrier(dist)
     launches = pkg.sibfa_kernel_launches(ctx) - l0
@@ -304,24 +309,25 @@ def main():
                 "units": {"site_pairs": n_ss, "penetration_pairs": n_pen, "thole_pairs": n_th, "lp_pairs": n_lp},
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived, not measured)"}
 
-    # end to end through the C ABI with host buffers: H2D positions, D2H forces and energies
-    pos_host = pos.cpu().numpy().copy()
-    vel_host = vel.cpu().numpy().copy()
-    inv_m = 1.0 / s.masses().reshape(-1).repeat(3)
-    F_host = np.zeros_like(pos_host)
-    pkg.sibfa_energy_forces(ctx, pos_host, F_host)
+    # End to end through the C ABI with host buffers: a second context
+    # evaluates, from host memory, the positions of the trajectory that the
+    # first context advances on the device (untimed); each timed call copies
+    # the positions in and the forces and energies out.
+    api = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
+                           ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"], precision=pkg.PREC_MIXED,
+                           warm_start=True, stream=stream)
+    F_host = np.zeros(M * 9)
+    pkg.sibfa_energy_forces(api, snapshots[0].cpu().numpy(), F_host)
     e2e_s = 0.0
-    conv = 4.184e-4
-    for _ in range(args.steps):
-        vel_host += 0.5 * dt_fs * F_host * inv_m * conv
-        pos_host += dt_fs * vel_host
+    for snap in snapshots:
+        pos_host = snap.cpu().numpy()
         t = time.perf_counter()
-        pkg.sibfa_energy_forces(ctx, pos_host, F_host)
+        pkg.sibfa_energy_forces(api, pos_host, F_host)
         e2e_s += time.perf_counter() - t
-        vel_host += 0.5 * dt_fs * F_host * inv_m * conv
     e2e_s = max_over_ranks(dist, e2e_s)
     e2e = {"value": ws * 3 * M * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(pos_host.nbytes),
            "d2h_bytes_per_step": int(F_host.nbytes + 8 * 8 + 4)}
+    pkg.sibfa_destroy(api)
     pkg.sibfa_destroy(ctx)
 
     if rank != 0:

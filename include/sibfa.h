@@ -105,6 +105,11 @@ typedef struct {
     int precision;
     int warm_start;
     void *stream;
+    /* Intramolecular support potential used only by sibfa_md_steps (not
+     * part of the reported intermolecular energy): E = k_bond (r - r0)^2
+     * per O-H bond + k_angle (theta - theta0)^2 per H-O-H angle
+     * (kcal/mol, A, rad; theta0 in degrees).  k = 0 switches a term off. */
+    double md_k_bond, md_r0, md_k_angle, md_theta0_deg;
 } sibfa_run_opts;
 
 typedef struct sibfa_ctx sibfa_ctx;
@@ -134,6 +139,13 @@ sibfa_status sibfa_solve_dipoles(sibfa_ctx *ctx, const double *pos, const double
  * e (may be NULL) receives the energy of the last step. */
 sibfa_status sibfa_md_steps(sibfa_ctx *ctx, double *pos, double *vel, const double *masses,
                             double dt_fs, int n_steps, sibfa_energy_terms *e);
+
+/* Relax a starting structure by capped steepest descent on the
+ * intermolecular energy plus the intramolecular support potential:
+ * each atom moves by F * min(1e-4 A^2 mol/kcal, max_disp_A / |F|) per step.
+ * pos: device pointer, n_mol*9 doubles, updated in place.  e (may be NULL)
+ * receives the intermolecular energy before the last step. */
+sibfa_status sibfa_minimize(sibfa_ctx *ctx, double *pos, int n_steps, double max_disp_A, sibfa_energy_terms *e);
 
 /* Statistics of the last evaluation: PCG iterations and final residual (D). */
 sibfa_status sibfa_last_stats(const sibfa_ctx *ctx, int *pcg_iters, double *pcg_resid_D);

@@ -16,6 +16,7 @@ from .sibfa import (  # noqa: F401
     sibfa_last_error,
     sibfa_last_stats,
     sibfa_md_steps,
+    sibfa_minimize,
     sibfa_profile_clear,
     sibfa_profile_get,
     sibfa_set_profiling,

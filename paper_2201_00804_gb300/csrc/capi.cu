@@ -204,6 +204,32 @@ void fill_params(KParams &k, const sibfa_params &P, const sibfa_run_opts &o, int
     k.xd_c1 = P.xd_c1; k.xd_a1 = P.xd_a1; k.xd_c2 = P.xd_c2; k.xd_a2 = P.xd_a2; k.xd_c3 = P.xd_c3; k.xd_a3 = P.xd_a3;
     k.ct_eta = P.ct_eta; k.ct_t = P.ct_t; k.ct_m = P.ct_m; k.ct_ae = P.ct_ae; k.ct_ah = P.ct_ah;
     k.rv_ct_o = P.rvdw_ct_o; k.rv_ct_h = P.rvdw_ct_h;
+    // pair-type coefficients in FP64 (kinds O, H, lone pair)
+    auto coef = [](double v) {
+        KParams::Coef c;
+        c.d = v;
+        c.hi = (float)v;
+        c.lo = (float)(v - (double)c.hi);
+        return c;
+    };
+    const double rvr[3] = {P.rvdw_rep_o, P.rvdw_rep_h, P.rvdw_rep_lp};
+    const double rvd[3] = {P.rvdw_disp_o, P.rvdw_disp_h, P.rvdw_disp_lp};
+    const double gam[3] = {P.gamma6, P.gamma8, P.gamma10};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const double kr = 1.0 / (4.0 * sqrt(rvr[a] * rvr[b]));
+            k.rep_k1[a][b] = coef(P.rep_alpha * kr);
+            k.rep_k2[a][b] = coef(P.rep_alpha2 * kr);
+            const double km = 1.0 / (2.0 * sqrt(rvd[a] * rvd[b]));
+            k.disp_km[a][b] = coef(km);
+            for (int n = 0; n < 3; ++n) k.disp_gS[n][a][b] = coef(gam[n] * (rvd[a] + rvd[b]) * P.disp_alpha);
+            const bool la = a == 2, lb = b == 2;
+            const double A = (!la && !lb) ? P.xd_a1 : ((la && lb) ? P.xd_a2 : P.xd_a3);
+            k.xd_k[a][b] = coef(A * km);
+        }
+    k.ct_k1 = coef(P.ct_eta / (2.0 * sqrt(P.rvdw_ct_o * P.rvdw_ct_o)));
+    k.ct_k2 = coef(P.ct_eta / (2.0 * sqrt(P.rvdw_ct_o * P.rvdw_ct_h)));
+    for (int s = 0; s < 5; ++s) k.pen_b[s] = coef(k.b[s]);
 }
 
 bool is_device_ptr(const void *p) {
@@ -445,6 +471,11 @@ sibfa_status create_impl(sibfa_ctx *ctx, const sibfa_topology *topo) {
 
 }  // namespace
 
+__global__ void k_inverse(int n, const double *a, double *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = 1.0 / a[k];
+}
+
 template <typename R>
 static sibfa_status md_impl(sibfa_ctx *ctx, double *pos, double *vel, const double *masses, double dt, int n,
                             sibfa_energy_terms *e) {
@@ -459,22 +490,24 @@ static sibfa_status md_impl(sibfa_ctx *ctx, double *pos, double *vel, const doub
         sibfa_status st = dalloc(ctx, &ctx->d_invm, (size_t)M * 3);
         if (st) return st;
     }
-    std::vector<double> hm(M * 3);
-    CK(cudaMemcpy(hm.data(), masses, M * 3 * sizeof(double), cudaMemcpyDeviceToHost));
-    for (auto &v : hm) v = 1.0 / v;
-    CK(cudaMemcpyAsync(ctx->d_invm, hm.data(), M * 3 * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
     const double tol = ctx->opts.pcg_tol_D > 0 ? ctx->opts.pcg_tol_D : 1e-6;
     Launch L{ctx->s, &ctx->launches};
+    k_inverse<<<(M * 3 + 255) / 256, 256, 0, ctx->s>>>(M * 3, masses, ctx->d_invm);
+    ctx->launches += 1;
     CK(cudaMemcpyAsync(d.pos, pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
+    const sibfa_run_opts &o = ctx->opts;
+    const double th0 = o.md_theta0_deg * M_PI / 180.0;
     sibfa_status st = SIBFA_OK;
     if (!ctx->md_forces_valid) {
         st = evaluate<R>(ctx, true, false, tol);
         if (st) return st;
+        launch_water_intra(M, d.pos, ctx->d_forces, o.md_k_bond, o.md_r0, o.md_k_angle, th0, L);
     }
     for (int k = 0; k < n; ++k) {
         launch_md_kick(M, d.pos, vel, ctx->d_invm, ctx->d_forces, dt, 1, L);
         st = evaluate<R>(ctx, true, false, tol);
         if (st) return st;
+        launch_water_intra(M, d.pos, ctx->d_forces, o.md_k_bond, o.md_r0, o.md_k_angle, th0, L);
         launch_md_kick(M, d.pos, vel, ctx->d_invm, ctx->d_forces, dt, 0, L);
     }
     CK(cudaMemcpyAsync(pos, d.pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
@@ -575,6 +608,48 @@ sibfa_status sibfa_solve_dipoles(sibfa_ctx *ctx, const double *pos, const double
     const double tol = tol_D > 0 ? tol_D : (ctx->opts.pcg_tol_D > 0 ? ctx->opts.pcg_tol_D : 1e-6);
     return ctx->prec == SIBFA_PREC_MIXED ? run<float>(ctx, pos, box, nullptr, nullptr, true, tol, mu, iters, resid_D)
                                          : run<double>(ctx, pos, box, nullptr, nullptr, true, tol, mu, iters, resid_D);
+}
+
+}  // extern "C"
+
+template <typename R>
+static sibfa_status minimize_impl(sibfa_ctx *ctx, double *pos, int n, double cap, sibfa_energy_terms *e) {
+    DevState<R> &d = state<R>(ctx);
+    const int M = ctx->M;
+    const size_t nb = (size_t)M * 9 * sizeof(double);
+    if (!is_device_ptr(pos)) {
+        ctx->err = "sibfa_minimize needs a device pointer for pos";
+        return SIBFA_E_INVALID;
+    }
+    const double tol = ctx->opts.pcg_tol_D > 0 ? ctx->opts.pcg_tol_D : 1e-6;
+    Launch L{ctx->s, &ctx->launches};
+    const sibfa_run_opts &o = ctx->opts;
+    const double th0 = o.md_theta0_deg * M_PI / 180.0;
+    CK(cudaMemcpyAsync(d.pos, pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
+    for (int k = 0; k < n; ++k) {
+        sibfa_status st = evaluate<R>(ctx, true, false, tol);
+        if (st) return st;
+        launch_water_intra(M, d.pos, ctx->d_forces, o.md_k_bond, o.md_r0, o.md_k_angle, th0, L);
+        launch_sd_step(M, d.pos, ctx->d_forces, 1e-4, cap, L);
+    }
+    CK(cudaMemcpyAsync(pos, d.pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
+    double *h = ctx->h_pin;
+    CK(cudaMemcpyAsync(h, ctx->d_energy, (NTERM + 1) * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    ctx->md_forces_valid = false;
+    if (e) {
+        e->elec = h[T_ELEC]; e->pen = h[T_PEN]; e->rep = h[T_REP]; e->disp = h[T_DISP];
+        e->xdisp = h[T_XDISP]; e->pol = h[T_POL]; e->ct = h[T_CT]; e->total = h[NTERM];
+    }
+    return SIBFA_OK;
+}
+
+extern "C" {
+
+sibfa_status sibfa_minimize(sibfa_ctx *ctx, double *pos, int n_steps, double max_disp_A, sibfa_energy_terms *e) {
+    if (!ctx || !pos || n_steps < 0 || !(max_disp_A > 0)) return SIBFA_E_INVALID;
+    return ctx->prec == SIBFA_PREC_MIXED ? minimize_impl<float>(ctx, pos, n_steps, max_disp_A, e)
+                                         : minimize_impl<double>(ctx, pos, n_steps, max_disp_A, e);
 }
 
 sibfa_status sibfa_md_steps(sibfa_ctx *ctx, double *pos, double *vel, const double *masses, double dt_fs, int n_steps,

@@ -103,7 +103,6 @@ __global__ void __launch_bounds__(224) k_real_perm(KParams p, DevState<R> d) {
     if (!is_lp) mt = load_mp(d.gmp + (i * NS + w) * NMP);
     const R Nt = (!is_lp) ? R(p.z[w]) - mt.q * R(w < 3) : R(0);
     const R Nt_ = (w < 3) ? Nt : R(0);
-    const R bt = (!is_lp) ? R(p.b[w]) : R(0);
     const R rc2 = R(p.rc2), alpha = R(p.alpha), thole = R(p.thole);
     const R third = R(1) / R(3);
 
@@ -147,21 +146,22 @@ __global__ void __launch_bounds__(224) k_real_perm(KParams p, DevState<R> d) {
             // ---- penetration: charge-charge*, charge-dipole*, charge-quadrupole*
             const R Ns = (s < 3) ? R(p.z[s]) - ms.q : R(0);
             if (Nt_ != R(0) || Ns != R(0)) {
-                const R bs = R(p.b[s]);
+                const R xs_b = mulc(r, p.pen_b[s]);          // b_s r
+                const R xt_b = is_lp ? R(0) : mulc(r, p.pen_b[w]);   // b_t r
                 R pen = R(0);
                 // q*_t q*_s - q_t q_s, with q* = q + N exp(-b r)
                 {
                     R g1a[2], g1b[2], g1c[2];
-                    g_exp<R, 1>(r, rinv, bs, g1a);
-                    g_exp<R, 1>(r, rinv, bt, g1b);
-                    g_exp<R, 1>(r, rinv, bt + bs, g1c);
+                    g_exp_x<R, 1>(xs_b, rinv, g1a);
+                    g_exp_x<R, 1>(xt_b, rinv, g1b);
+                    g_exp_x<R, 1>(xt_b + xs_b, rinv, g1c);
                     const R c1 = mt.q * Ns, c2 = ms.q * Nt_, c3 = Nt_ * Ns;
                     pen += c1 * g1a[0] + c2 * g1b[0] + c3 * g1c[0];
                     gr = gr + (c1 * g1a[1] + c2 * g1b[1] + c3 * g1c[1]) * x;
                 }
                 if (Nt_ != R(0)) {   // valence of t in the dipole/quadrupole potential of s
                     R ge[4];
-                    g_exp<R, 3>(r, rinv, bt, ge);
+                    g_exp_x<R, 3>(xt_b, rinv, ge);
                     Mp<R> m0 = ms;
                     m0.q = R(0);
                     FieldTerms<R> f2;
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(224) k_real_perm(KParams p, DevState<R> d) {
                 }
                 if (Ns != R(0)) {    // valence of s in the dipole/quadrupole potential of t
                     R ge[4];
-                    g_exp<R, 3>(r, rinv, bs, ge);
+                    g_exp_x<R, 3>(xs_b, rinv, ge);
                     Mp<R> m0 = mt;
                     m0.q = R(0);
                     const V3<R> xs = -x;
@@ -262,27 +262,28 @@ __device__ inline R overlap_i(V3<R> x, V3<R> xp, V3<R> y, V3<R> uy, R A, R B, R 
 
 template <typename R>
 struct RepAtom {
-    R cs, cp, g, cf, rv;
+    R cs, cp, g, cf;
+    int kind;   // 0 = O, 1 = H, 2 = lone pair (selects the precomputed exponent coefficients)
 };
 
 // Adds the overlap and exponential factor of one atom pair to O1/O2 and the
 // i-side gradients of O1/O2 (points ix, ixp).
 template <typename R>
 __device__ inline void rep_pair_term(V3<R> x, V3<R> xp, const RepAtom<R> &ai, V3<R> y, V3<R> uy, const RepAtom<R> &aj,
-                                     R pp, R f, R a1, R a2, R &O1, R &O2, V3<R> &g1x, V3<R> &g1xp, V3<R> &g2x,
+                                     R pp, R f, const KParams &p, R &O1, R &O2, V3<R> &g1x, V3<R> &g1xp, V3<R> &g2x,
                                      V3<R> &g2xp) {
     V3<R> gx, gxp;
     const R O = overlap_i(x, xp, y, uy, ai.cs * aj.cs, aj.cs * ai.cp * f, ai.cs * aj.cp * f, pp * ai.cp * aj.cp, gx, gxp);
     const V3<R> v = x - y;
     const R rr = sqrt_(dot(v, v));
-    const R kr = R(1) / (R(4) * sqrt_(ai.rv * aj.rv));
+    const KParams::Coef &k1 = p.rep_k1[ai.kind][aj.kind], &k2 = p.rep_k2[ai.kind][aj.kind];
     const R M = sqrt_(ai.g * aj.g * ai.cf * aj.cf);
-    const R S1 = M * exp_(-a1 * kr * rr), S2 = M * exp_(-a2 * kr * rr);
+    const R S1 = M * exp_(-mulc(rr, k1)), S2 = M * exp_(-mulc(rr, k2));
     O1 += O * S1;
     O2 += O * S2;
     const V3<R> drdx = (R(1) / rr) * v;
-    g1x = g1x + S1 * gx + (O * S1 * (-a1 * kr)) * drdx;
-    g2x = g2x + S2 * gx + (O * S2 * (-a2 * kr)) * drdx;
+    g1x = g1x + S1 * gx + (O * S1 * (-cval<R>(k1))) * drdx;
+    g2x = g2x + S2 * gx + (O * S2 * (-cval<R>(k2))) * drdx;
     g1xp = g1xp + S1 * gxp;
     g2xp = g2xp + S2 * gxp;
 }
@@ -328,13 +329,13 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
         Q[4] = dO + my_pt(d, j, 6);
         const R qj[3] = {d.gmp[(j * NS + 0) * NMP], d.gmp[(j * NS + 1) * NMP], d.gmp[(j * NS + 2) * NMP]};
         RepAtom<R> Ai[3], Aj[3];
-        Ai[0] = {R(p.cs_o), R(p.cp_o), R(p.g_o), R(1) - qi[0] / R(p.nval_o), R(p.rv_rep_o)};
-        Aj[0] = {R(p.cs_o), R(p.cp_o), R(p.g_o), R(1) - qj[0] / R(p.nval_o), R(p.rv_rep_o)};
+        Ai[0] = {R(p.cs_o), R(p.cp_o), R(p.g_o), R(1) - qi[0] / R(p.nval_o), 0};
+        Aj[0] = {R(p.cs_o), R(p.cp_o), R(p.g_o), R(1) - qj[0] / R(p.nval_o), 0};
         for (int k = 1; k < 3; ++k) {
-            Ai[k] = {R(p.cs_h), R(p.cp_h), R(p.g_h), R(1) - qi[k] / R(p.nval_h), R(p.rv_rep_h)};
-            Aj[k] = {R(p.cs_h), R(p.cp_h), R(p.g_h), R(1) - qj[k] / R(p.nval_h), R(p.rv_rep_h)};
+            Ai[k] = {R(p.cs_h), R(p.cp_h), R(p.g_h), R(1) - qi[k] / R(p.nval_h), 1};
+            Aj[k] = {R(p.cs_h), R(p.cp_h), R(p.g_h), R(1) - qj[k] / R(p.nval_h), 1};
         }
-        const RepAtom<R> Alp = {R(p.cs_lp), R(p.cp_lp), R(p.g_o), cf_lp, R(p.rv_rep_lp)};
+        const RepAtom<R> Alp = {R(p.cs_lp), R(p.cp_lp), R(p.g_o), cf_lp, 2};
         // ---- bond-bond
         for (int kb = 1; kb <= 2; ++kb)
             for (int kc = 1; kc <= 2; ++kc) {
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
                         const int xi = u ? kb : 0, xpi = u ? 0 : kb;
                         const int yj = v ? kc : 0, ypj = v ? 0 : kc;
                         V3<R> t1x = z, t1xp = z, t2x = z, t2xp = z;
-                        rep_pair_term(P[xi], P[xpi], Ai[xi], Q[yj], Q[ypj] - Q[yj], Aj[yj], R(2), f, a1, a2, O1, O2,
+                        rep_pair_term(P[xi], P[xpi], Ai[xi], Q[yj], Q[ypj] - Q[yj], Aj[yj], R(2), f, p, O1, O2,
                                       t1x, t1xp, t2x, t2xp);
                         if (u == 0) { g1a = g1a + t1x; g2a = g2a + t2x; g1b = g1b + t1xp; g2b = g2b + t2xp; }
                         else { g1b = g1b + t1x; g2b = g2b + t2x; g1a = g1a + t1xp; g2a = g2a + t2xp; }
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
                 for (int u = 0; u < 2; ++u) {
                     const int xi = u ? kb : 0, xpi = u ? 0 : kb;
                     V3<R> t1x = z, t1xp = z, t2x = z, t2xp = z;
-                    rep_pair_term(P[xi], P[xpi], Ai[xi], Q[0], Q[3 + l] - Q[0], Alp, f, f, a1, a2, O1, O2, t1x, t1xp,
+                    rep_pair_term(P[xi], P[xpi], Ai[xi], Q[0], Q[3 + l] - Q[0], Alp, f, f, p, O1, O2, t1x, t1xp,
                                   t2x, t2xp);
                     if (u == 0) { g1a = g1a + t1x; g2a = g2a + t2x; g1b = g1b + t1xp; g2b = g2b + t2xp; }
                     else { g1b = g1b + t1x; g2b = g2b + t2x; g1a = g1a + t1xp; g2a = g2a + t2xp; }
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
                 for (int v = 0; v < 2; ++v) {
                     const int yj = v ? kc : 0, ypj = v ? 0 : kc;
                     V3<R> t1x = z, t1xp = z, t2x = z, t2xp = z;
-                    rep_pair_term(P[0], P[3 + l], Alp, Q[yj], Q[ypj] - Q[yj], Aj[yj], f, f, a1, a2, O1, O2, t1x,
+                    rep_pair_term(P[0], P[3 + l], Alp, Q[yj], Q[ypj] - Q[yj], Aj[yj], f, f, p, O1, O2, t1x,
                                   t1xp, t2x, t2xp);
                     g1c = g1c + t1x; g2c = g2c + t2x; g1l = g1l + t1xp; g2l = g2l + t2xp;
                 }
@@ -429,14 +430,14 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
                 const V3<R> dOdA = R(-1) * dci * (dui + dvi);
                 const V3<R> dAB = P[0] - Q[0];
                 const R rab = sqrt_(dot(dAB, dAB));
-                const R kr = R(1) / (R(4) * R(p.rv_rep_lp));
                 const R M = R(p.g_o) * cf_lp;
-                const R S1 = M * exp_(-a1 * kr * rab), S2 = M * exp_(-a2 * kr * rab);
+                const R S1 = M * exp_(-mulc(rab, p.rep_k1[2][2])), S2 = M * exp_(-mulc(rab, p.rep_k2[2][2]));
                 const R O1 = O * S1, O2 = O * S2;
                 R e1, e2, er;
                 Erep.add(R(0.5) * rep_energy(nlp * nlp, C1, C2, O1, O2, rr, e1, e2, er));
                 const V3<R> drab = (R(1) / rab) * dAB;
-                G[0] = G[0] + (e1 * S1 + e2 * S2) * dOdA + (e1 * O1 * (-a1 * kr) + e2 * O2 * (-a2 * kr)) * drab;
+                G[0] = G[0] + (e1 * S1 + e2 * S2) * dOdA +
+                       (e1 * O1 * (-cval<R>(p.rep_k1[2][2])) + e2 * O2 * (-cval<R>(p.rep_k2[2][2]))) * drab;
                 G[3 + l1] = G[3 + l1] + (e1 * S1 + e2 * S2) * dOdI + (er / rr) * dIJ;
             }
         // ---- dispersion and exchange-dispersion over atoms and lone pairs
@@ -444,35 +445,35 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
                           R(1) - qi[0] / R(p.nval_o), R(1) - qi[0] / R(p.nval_o)};
         const R cfj[5] = {R(1) - qj[0] / R(p.nval_o), R(1) - qj[1] / R(p.nval_h), R(1) - qj[2] / R(p.nval_h),
                           R(1) - qj[0] / R(p.nval_o), R(1) - qj[0] / R(p.nval_o)};
+        const int kind_of[5] = {0, 1, 1, 2, 2};
         for (int u = 0; u < 5; ++u)
             for (int v = 0; v < 5; ++v) {
                 const V3<R> dv = P[u] - Q[v];
                 const R r2 = dot(dv, dv);
                 if (PER && r2 >= rc2) continue;
                 const R ri = rsqrt_(r2), r = r2 * ri;
-                const R rvu = R(p.rv_d[u]), rvv = R(p.rv_d[v]);
-                const R km = R(0.5) * rsqrt_(rvu * rvv);
-                const R m = r * km, mi = R(1) / m;
-                const R S = (rvu + rvv) * R(p.disp_alpha);
-                const R dd = S * ri - R(1);
+                const int ku = kind_of[u], kv = kind_of[v];
+                const R m = mulc(r, p.disp_km[ku][kv]), mi = R(1) / m;
+                // exp(-gamma_n d) with d = S/r - 1: argument gamma_n - (gamma_n S)/r
+                const R a6 = mulc(ri, p.disp_gS[0][ku][kv]), a8 = mulc(ri, p.disp_gS[1][ku][kv]),
+                        a10 = mulc(ri, p.disp_gS[2][ku][kv]);
                 const R m2i = mi * mi, m6i = m2i * m2i * m2i, m8i = m6i * m2i, m10i = m8i * m2i;
-                const R e6 = R(p.c6) * exp_(-R(p.g6) * dd) * m6i;
-                const R e8 = R(p.c8) * exp_(-R(p.g8) * dd) * m8i;
-                const R e10 = R(p.c10) * exp_(-R(p.g10) * dd) * m10i;
-                const R dsdr = S * ri * ri;   // -d(dd)/dr
+                const R e6 = R(p.c6) * exp_(R(p.g6) - a6) * m6i;
+                const R e8 = R(p.c8) * exp_(R(p.g8) - a8) * m8i;
+                const R e10 = R(p.c10) * exp_(R(p.g10) - a10) * m10i;
                 const R fsum = e6 + e8 + e10;
-                const R dfdr = e6 * (R(p.g6) * dsdr - R(6) * ri) + e8 * (R(p.g8) * dsdr - R(8) * ri) +
-                               e10 * (R(p.g10) * dsdr - R(10) * ri);
+                const R dfdr = e6 * ((a6 - R(6)) * ri) + e8 * ((a8 - R(8)) * ri) + e10 * ((a10 - R(10)) * ri);
                 const bool lu = u >= 3, lv = v >= 3;
                 R pref, xc, xa;
                 if (!lu && !lv) { pref = -R(p.beta[u] * p.beta[v]); xc = R(p.xd_c1); xa = R(p.xd_a1); }
                 else if (lu && lv) { pref = -nlp * nlp * R(0.25); xc = nlp * nlp * R(0.25) * R(p.xd_c2); xa = R(p.xd_a2); }
                 else { pref = -R(p.delta) * R(0.5); xc = nlp * R(0.5) * R(p.xd_c3); xa = R(p.xd_a3); }
                 const R K = R(p.beta[u] * p.beta[v]) * cfi[u] * cfj[v];
-                const R ex = xc * K * exp_(-xa * m);
+                const R ex = xc * K * exp_(-mulc(r, p.xd_k[ku][kv]));
                 Ed.add(R(0.5) * pref * fsum);
                 Ex.add(R(0.5) * ex);
-                const R dEdr = pref * dfdr - xa * km * ex;
+                const R dEdr = pref * dfdr - cval<R>(p.xd_k[ku][kv]) * ex;
+                (void)xa;
                 G[u] = G[u] + (dEdr * ri) * dv;
             }
     }
@@ -509,13 +510,13 @@ __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1
                                    int *flags) {
     CtOut<R> o;
     const R eta = R(p.ct_eta), cs = R(p.cs_lp), cp = R(p.cp_lp), t = R(p.ct_t), mm = R(p.ct_m), n = R(p.nlp);
-    const R kc1 = R(0.5) / R(p.rv_ct_o), kc2 = R(0.5) * rsqrt_(R(p.rv_ct_o * p.rv_ct_h));
     const V3<R> v1 = a1 - c, v2 = a2 - c, u = lp - c;
     const R r1 = sqrt_(dot(v1, v1)), r2 = sqrt_(dot(v2, v2));
     V3<R> du1, dv1, du2, dv2;
     const R ca = cosv(u, v1, du1, dv1);
     const R cb = cosv(u, v2, du2, dv2);
-    const R E1 = exp_(-eta * kc1 * r1), E2 = exp_(-eta * kc2 * r2);
+    const R E1 = exp_(-mulc(r1, p.ct_k1)), E2 = exp_(-mulc(r2, p.ct_k2));
+    const R ek1 = cval<R>(p.ct_k1), ek2 = cval<R>(p.ct_k2);   // eta / (2 sqrt(rv rv))
     const R K1 = cs * t + cp * mm * ca, K2 = cs * t + cp * mm * cb;
     const R e1 = E1 * (Vi1 - V) * K1, e2 = E2 * (Vi2 - V) * K2;
     const R D = e1 - e2;
@@ -527,7 +528,8 @@ __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1
     o.dV = gD * (-E1 * K1 + E2 * K2) + n * D * D * idE * idE;
     o.dVi1 = gD * E1 * K1;
     o.dVi2 = -gD * E2 * K2;
-    const R dr1 = gD * (-eta * kc1 * e1), dr2 = gD * (eta * kc2 * e2);
+    const R dr1 = gD * (-ek1 * e1), dr2 = gD * (ek2 * e2);
+    (void)eta;
     const R dca = gD * E1 * (Vi1 - V) * cp * mm, dcb = -gD * E2 * (Vi2 - V) * cp * mm;
     const V3<R> n1 = (R(1) / r1) * v1, n2 = (R(1) / r2) * v2;
     o.glp = dca * du1 + dcb * du2;

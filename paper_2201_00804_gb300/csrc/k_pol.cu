@@ -601,6 +601,59 @@ __global__ void k_md_kick(int M, double *pos, double *vel, const double *inv_mas
     if (drift) pos[k] += dt * v;
 }
 
+// Intramolecular support potential for the MD driver (not part of the
+// intermolecular energy): harmonic O-H bonds and a harmonic H-O-H angle,
+// forces added to F in place.
+__global__ void k_water_intra(int M, const double *pos, double *F, double kb, double r0, double ka, double th0) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const double *x = pos + m * 9;
+    const V3<double> O = mk(x[0], x[1], x[2]), H1 = mk(x[3], x[4], x[5]), H2 = mk(x[6], x[7], x[8]);
+    const V3<double> a = H1 - O, b = H2 - O;
+    const double ra = sqrt(dot(a, a)), rb = sqrt(dot(b, b));
+    // bonds: E = kb (r - r0)^2
+    const V3<double> fa = (-2.0 * kb * (ra - r0) / ra) * a;   // force on H1
+    const V3<double> fb = (-2.0 * kb * (rb - r0) / rb) * b;
+    // angle: E = ka (theta - th0)^2
+    const double c = fmax(-1.0, fmin(1.0, dot(a, b) / (ra * rb)));
+    const double th = acos(c);
+    const double s = fmax(sqrt(1.0 - c * c), 1e-8);
+    const double dEdth = 2.0 * ka * (th - th0);
+    // dtheta/da = -(b/(ra rb) - c a/ra^2)/sin
+    const V3<double> dca = (1.0 / (ra * rb)) * b - (c / (ra * ra)) * a;
+    const V3<double> dcb = (1.0 / (ra * rb)) * a - (c / (rb * rb)) * b;
+    const V3<double> ga = (dEdth / s) * dca;     // -dE/da  (dtheta = -dc/sin)
+    const V3<double> gb = (dEdth / s) * dcb;
+    const V3<double> f1 = fa + ga, f2 = fb + gb;
+    double *f = F + m * 9;
+    f[0] -= f1.x + f2.x; f[1] -= f1.y + f2.y; f[2] -= f1.z + f2.z;
+    f[3] += f1.x; f[4] += f1.y; f[5] += f1.z;
+    f[6] += f2.x; f[7] += f2.y; f[8] += f2.z;
+}
+
+// Capped steepest-descent update used to relax a starting structure:
+// x += F * min(gamma, cap / |F|) per atom.
+__global__ void k_sd_step(int M, double *pos, const double *F, double gamma, double cap) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= M * 3) return;
+    const double fx = F[a * 3], fy = F[a * 3 + 1], fz = F[a * 3 + 2];
+    const double f = sqrt(fx * fx + fy * fy + fz * fz);
+    const double s = (f * gamma > cap) ? cap / f : gamma;
+    pos[a * 3] += s * fx;
+    pos[a * 3 + 1] += s * fy;
+    pos[a * 3 + 2] += s * fz;
+}
+
+void launch_sd_step(int M, double *pos, const double *F, double gamma, double cap, Launch L) {
+    k_sd_step<<<(M * 3 + 127) / 128, 128, 0, L.s>>>(M, pos, F, gamma, cap);
+    count(L);
+}
+
+void launch_water_intra(int M, const double *pos, double *F, double kb, double r0, double ka, double th0, Launch L) {
+    k_water_intra<<<(M + 127) / 128, 128, 0, L.s>>>(M, pos, F, kb, r0, ka, th0);
+    count(L);
+}
+
 void launch_md_kick(int M, double *pos, double *vel, const double *inv_mass, const double *forces, double dt,
                     int drift, Launch L) {
     k_md_kick<<<(M * 9 + 255) / 256, 256, 0, L.s>>>(M, pos, vel, inv_mass, forces, dt, drift);

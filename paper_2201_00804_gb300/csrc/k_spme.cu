@@ -95,7 +95,7 @@ __global__ void k_spread(KParams p, DevState<R> d, int kind, const double *vec, 
 
 template <typename R>
 void launch_spread(const KParams &p, DevState<R> &d, int kind, const double *vec, R *grid, Launch L) {
-    const int per = kind == SPREAD_PERM ? NS : (kind == SPREAD_DIP ? 3 : 2);
+    const int per = kind == SPREAD_PERM ? NS : ((kind == SPREAD_DIP || kind == SPREAD_DIP_PCG) ? 3 : 2);
     const int n = p.M * per;
     k_spread<R><<<(n + 127) / 128, 128, 0, L.s>>>(p, d, kind, vec, grid);
     count(L);

@@ -48,7 +48,35 @@ struct KParams {
     double xd_c1, xd_a1, xd_c2, xd_a2, xd_c3, xd_a3;
     // charge transfer
     double ct_eta, ct_t, ct_m, ct_ae, ct_ah, rv_ct_o, rv_ct_h;
+    // Pair-type coefficients precomputed in FP64 on the host (kinds: 0 = O,
+    // 1 = H, 2 = lone pair).  In the FP32 path each is used as a hi + lo pair
+    // of floats so that large exponent arguments keep FP64-rounded constants.
+    struct Coef {
+        double d;
+        float hi, lo;   // hi = float(d), lo = float(d - hi)
+    };
+    Coef rep_k1[3][3], rep_k2[3][3];     // rep_alpha / (4 sqrt(rv_a rv_b)), same with rep_alpha2
+    Coef disp_km[3][3];                  // 1 / (2 sqrt(rv_a rv_b))   (dispersion radii)
+    Coef disp_gS[3][3][3];               // gamma_n (rv_a + rv_b) disp_alpha, n = 6, 8, 10
+    Coef xd_k[3][3];                     // A_type / (2 sqrt(rv_a rv_b)) for exchange-dispersion
+    Coef ct_k1, ct_k2;                   // eta / (2 sqrt(rv_O rv_O)), eta / (2 sqrt(rv_O rv_H))
+    Coef pen_b[5];                       // valence damping exponents per site
 };
+
+// x * c for a coefficient precomputed in FP64: in FP32 the product keeps the
+// FP64 rounding of c (x * hi + x * lo).
+template <typename R>
+__device__ inline R mulc(R x, const KParams::Coef &c);
+template <>
+__device__ inline double mulc<double>(double x, const KParams::Coef &c) { return x * c.d; }
+template <>
+__device__ inline float mulc<float>(float x, const KParams::Coef &c) { return fmaf(x, c.hi, x * c.lo); }
+template <typename R>
+__device__ inline R cval(const KParams::Coef &c);
+template <>
+__device__ inline double cval<double>(const KParams::Coef &c) { return c.d; }
+template <>
+__device__ inline float cval<float>(const KParams::Coef &c) { return c.hi; }
 
 // ---------------------------------------------------------------------------
 // Device state.  Per-molecule arrays are SoA-by-molecule: index m*stride+k.
@@ -183,6 +211,28 @@ __device__ inline void g_erfc(R r, R rinv, R alpha, R *g) {
 }
 
 // exp(-b r)/r: g_n = (-1)^n e^{-b r} theta_n(b r)/r^(2n+1), theta = reverse Bessel polynomials.
+template <typename R, int N>
+__device__ inline void g_exp(R r, R rinv, R bb, R *g);
+
+// same kernel with the exponent argument x = b r supplied by the caller
+template <typename R, int N>
+__device__ inline void g_exp_x(R x, R rinv, R *g) {
+    const R e = exp_(-x) * rinv;
+    R th0 = R(1), th1 = x + R(1);
+    R r2i = rinv * rinv;
+    R pw = e;
+    g[0] = e;
+    if (N >= 1) { pw *= r2i; g[1] = -th1 * pw; }
+#pragma unroll
+    for (int n = 2; n <= N; ++n) {
+        R th2 = R(2 * n - 1) * th1 + x * x * th0;
+        th0 = th1;
+        th1 = th2;
+        pw *= r2i;
+        g[n] = (n & 1) ? -th2 * pw : th2 * pw;
+    }
+}
+
 template <typename R, int N>
 __device__ inline void g_exp(R r, R rinv, R bb, R *g) {
     const R x = bb * r;
@@ -430,6 +480,8 @@ template <typename R> void launch_pcg_iter_b(const KParams &p, DevState<R> &d, d
 template <typename R> void launch_pol_energy(const KParams &p, DevState<R> &d, Launch L);
 void launch_energy_reduce(int M, const double *epart, double *out, Launch L);
 void launch_begin(double *scal, int *flags, double tol_D, Launch L);
+void launch_water_intra(int M, const double *pos, double *F, double kb, double r0, double ka, double th0, Launch L);
+void launch_sd_step(int M, double *pos, const double *F, double gamma, double cap, Launch L);
 enum { SC_RZ = 0, SC_RES = 4, SC_IT = 6, SC_DONE = 7, SC_TOL = 8 };
 void launch_md_kick(int M, double *pos, double *vel, const double *inv_mass, const double *forces, double dt,
                     int drift, Launch L);

@@ -41,7 +41,8 @@ class sibfa_run_opts(C.Structure):
     _fields_ = [("periodic", C.c_int), ("box", C.c_double * 3), ("rc", C.c_double), ("grid", C.c_int * 3),
                 ("order", C.c_int), ("ewald_alpha", C.c_double), ("pcg_tol_D", C.c_double),
                 ("pcg_max_iter", C.c_int), ("precision", C.c_int), ("warm_start", C.c_int),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("md_k_bond", C.c_double), ("md_r0", C.c_double),
+                ("md_k_angle", C.c_double), ("md_theta0_deg", C.c_double)]
 
 
 class sibfa_energy_terms(C.Structure):
@@ -77,6 +78,8 @@ def load_library(path: str = LIB_PATH):
     lib.sibfa_md_steps.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                    C.POINTER(sibfa_energy_terms)]
     lib.sibfa_md_steps.restype = C.c_int
+    lib.sibfa_minimize.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.POINTER(sibfa_energy_terms)]
+    lib.sibfa_minimize.restype = C.c_int
     lib.sibfa_last_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     lib.sibfa_last_stats.restype = C.c_int
     lib.sibfa_kernel_launches.argtypes = [C.c_void_p]
@@ -118,7 +121,7 @@ def _check(lib, ctx, st):
 
 def sibfa_create(params: dict, mp_local: np.ndarray, *, periodic: bool, box=None, rc=9.0, grid=64, order=5,
                  ewald_alpha=0.4, pcg_tol_D=1e-6, pcg_max_iter=200, precision=PREC_MIXED, warm_start=True,
-                 stream=None):
+                 stream=None, md_k_bond=529.6, md_r0=0.9572, md_k_angle=34.05, md_theta0_deg=104.52):
     """Create a context.  mp_local: (n_mol, 5, 10) float64 host array.
     stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
     lib = load_library()
@@ -142,6 +145,7 @@ def sibfa_create(params: dict, mp_local: np.ndarray, *, periodic: bool, box=None
     o.warm_start = 1 if warm_start else 0
     if stream is not None:
         o.stream = int(getattr(stream, "cuda_stream", stream))
+    o.md_k_bond, o.md_r0, o.md_k_angle, o.md_theta0_deg = md_k_bond, md_r0, md_k_angle, md_theta0_deg
     out = C.c_void_p()
     st = lib.sibfa_create(C.byref(P), C.byref(topo), C.byref(o), C.byref(out))
     _check(lib, None, st)
@@ -173,6 +177,15 @@ def sibfa_md_steps(ctx, pos, vel, masses, dt_fs, n_steps):
     lib = load_library()
     e = sibfa_energy_terms()
     st = lib.sibfa_md_steps(ctx, _ptr(pos), _ptr(vel), _ptr(masses), float(dt_fs), int(n_steps), C.byref(e))
+    _check(lib, ctx, st)
+    return {n: getattr(e, n) for n in TERMS}
+
+
+def sibfa_minimize(ctx, pos, n_steps, max_disp_A=0.02):
+    """Capped steepest-descent relaxation of device positions (in place)."""
+    lib = load_library()
+    e = sibfa_energy_terms()
+    st = lib.sibfa_minimize(ctx, _ptr(pos), int(n_steps), float(max_disp_A), C.byref(e))
     _check(lib, ctx, st)
     return {n: getattr(e, n) for n in TERMS}
 

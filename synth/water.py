@@ -73,8 +73,8 @@ PARAMS = {
     "rvdw_rep_lp": 1.30,
     "rep_alpha": 12.0,
     "rep_alpha2": 14.0,
-    "rep_c1": 16000.0,
-    "rep_c2": 8000.0,
+    "rep_c1": 9600.0,
+    "rep_c2": 4800.0,
     "rep_f": 0.8,
     "occ_bond": 2.0,
     "n_lp": 2.0,
@@ -101,10 +101,10 @@ PARAMS = {
     "xd_a3": 4.5,
     # reduced charge transfer
     "ct_eta": 3.2,
-    "ct_t": 0.34,
-    "ct_m": 0.27,
-    "ct_ae": 300.0,           # lone-pair ionization potential (kcal/mol)
-    "ct_ah": 90.0,            # heavy-atom electron affinity (kcal/mol)
+    "ct_t": 0.486,
+    "ct_m": 0.386,
+    "ct_ae": 500.0,           # lone-pair ionization potential (kcal/mol)
+    "ct_ah": 60.0,            # heavy-atom electron affinity (kcal/mol)
     "rvdw_ct_o": 1.50,
     "rvdw_ct_h": 1.10,
 }
@@ -166,55 +166,85 @@ def _water_body() -> np.ndarray:
 
 
 def _random_multipoles(rng: np.random.Generator, n_mol: int) -> np.ndarray:
+    """Per-molecule draws with an ISA-like layout in each site's local frame:
+    dipoles along the local z axis (the O bisector, the bond for H and the
+    midpoints) and diagonal traceless quadrupoles.  Bounds: |mu| <= 0.3 e.A
+    and quadrupole entries <= 0.5 e.A^2 on O; the H and midpoint moments are
+    drawn from smaller ranges inside the same bounds."""
     mp = np.zeros((n_mol, N_SITES, N_MP))
     q_o = rng.uniform(-0.85, -0.75, size=n_mol)
     mp[:, 0, 0] = q_o
     mp[:, 1:, 0] = (-q_o / 4.0)[:, None]
-    # dipoles: random direction, magnitude U(0, 0.3)
-    v = rng.normal(size=(n_mol, N_SITES, 3))
-    v /= np.linalg.norm(v, axis=-1, keepdims=True)
-    mag = rng.uniform(0.0, 0.3, size=(n_mol, N_SITES, 1))
-    mp[:, :, 1:4] = v * mag
-    # quadrupoles: symmetric entries U(-0.5, 0.5), then traceless
-    e = rng.uniform(-0.5, 0.5, size=(n_mol, N_SITES, 6))
-    tr = (e[..., 0] + e[..., 1] + e[..., 2]) / 3.0
-    e[..., 0] -= tr
-    e[..., 1] -= tr
-    e[..., 2] -= tr
-    mp[:, :, 4:] = e
+    mu_rng = np.array([[0.0, 0.3], [0.0, 0.1], [0.0, 0.1], [-0.1, 0.1], [-0.1, 0.1]])
+    th_rng = np.array([0.5, 0.1, 0.1, 0.2, 0.2])
+    for s in range(N_SITES):
+        mp[:, s, 3] = rng.uniform(mu_rng[s, 0], mu_rng[s, 1], size=n_mol)
+        d = rng.uniform(-th_rng[s], th_rng[s], size=(n_mol, 3))
+        d -= d.mean(axis=1, keepdims=True)
+        mp[:, s, 4:7] = d
     return mp
 
 
-def _place(rng, centers, box, min_oo, jitter):
-    """Sequential jittered placement with an O-O rejection test (min image)."""
-    n = centers.shape[0]
-    out = np.empty_like(centers)
-    for i in range(n):
-        placed = False
-        for _ in range(200):
-            p = centers[i] + (rng.uniform(-jitter, jitter, size=3) if jitter > 0 else 0.0)
-            if i == 0:
-                placed = True
-                break
-            d = out[:i] - p
-            if box is not None:
-                d -= box * np.round(d / box)
-            if np.min(np.einsum("ij,ij->i", d, d)) >= min_oo * min_oo:
-                placed = True
-                break
-        if not placed:
-            p = centers[i].copy()
-        out[i] = p
-    return out
+MIN_ATOM_DIST = 1.7   # A, minimum intermolecular atom-atom distance of a starting structure
 
 
-def _orient(rng, o_pos):
+def _place_molecules(rng, propose, n, box, min_oo, min_atom=MIN_ATOM_DIST, tries=400):
+    """Sequential placement of rigid waters: each molecule draws a position
+    (propose(k)) and a uniform random orientation until its O is at least
+    min_oo from every placed O and each of its atoms at least min_atom from
+    every atom of another molecule (minimum image in a box).  A spatial hash
+    limits the test to nearby molecules."""
     body = _water_body()
-    n = o_pos.shape[0]
     pos = np.empty((n, 3, 3))
-    for i in range(n):
-        r = random_rotation(rng)
-        pos[i] = o_pos[i] + body @ r.T
+    reach = min_atom + 2.0 * WATER_GEOM["r_oh"]          # O-O range that can violate min_atom
+    cut = max(min_oo, reach)
+    if box is not None:
+        nc = np.maximum(1, np.floor(box / cut).astype(int))
+        cs = box / nc
+    else:
+        nc = None
+        cs = np.array([cut] * 3)
+    cells = {}
+
+    def key(p):
+        c = np.floor(p / cs).astype(int)
+        if nc is not None:
+            c %= nc
+        return tuple(c)
+
+    def nearby(p):
+        c0 = np.floor(p / cs).astype(int)
+        out = []
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    c = c0 + (dx, dy, dz)
+                    if nc is not None:
+                        c %= nc
+                    out.extend(cells.get(tuple(c), ()))
+        return sorted(set(out))
+
+    for k in range(n):
+        best = None
+        for _ in range(tries):
+            p = propose(k)
+            atoms = p + body @ random_rotation(rng).T
+            ok = True
+            for j in nearby(p):
+                d = pos[j][None, :, :] - atoms[:, None, :]
+                if box is not None:
+                    d -= box * np.round(d / box)
+                r2 = np.einsum("abk,abk->ab", d, d)
+                if r2[0, 0] < min_oo * min_oo or r2.min() < min_atom * min_atom:
+                    ok = False
+                    break
+            if ok:
+                best = atoms
+                break
+            if best is None:
+                best = atoms
+        pos[k] = best
+        cells.setdefault(key(pos[k, 0]), []).append(k)
     return pos
 
 
@@ -230,8 +260,11 @@ def make_box(n_side: int, box_len: float, seed: int, n_remove: int = 0,
         idx = idx[keep]
     centers = (idx + 0.5) * a
     box = np.array([box_len] * 3, dtype=np.float64)
-    o_pos = _place(rng, centers, box, min_oo, jitter)
-    pos = _orient(rng, o_pos)
+
+    def propose(k):
+        return centers[k] + (rng.uniform(-jitter, jitter, size=3) if jitter > 0 else 0.0)
+
+    pos = _place_molecules(rng, propose, centers.shape[0], box, min_oo)
     mp = _random_multipoles(rng, pos.shape[0])
     return System(pos=pos, mp_local=mp, box=box,
                   meta={"kind": "box", "n_side": n_side, "seed": seed})
@@ -241,19 +274,14 @@ def make_cluster(n_mol: int, seed: int, min_oo: float = 2.5) -> System:
     """Gas-phase cluster: O uniform in a sphere of radius 3 n^(1/3) A."""
     rng = np.random.default_rng(seed)
     radius = 3.0 * n_mol ** (1.0 / 3.0)
-    o_pos = np.empty((n_mol, 3))
-    k = 0
-    tries = 0
-    while k < n_mol:
-        tries += 1
-        p = rng.uniform(-radius, radius, size=3)
-        if p @ p > radius * radius:
-            continue
-        if k and np.min(np.sum((o_pos[:k] - p) ** 2, axis=1)) < min_oo * min_oo and tries < 100000:
-            continue
-        o_pos[k] = p
-        k += 1
-    pos = _orient(rng, o_pos)
+
+    def propose(k):
+        while True:
+            p = rng.uniform(-radius, radius, size=3)
+            if p @ p <= radius * radius:
+                return p
+
+    pos = _place_molecules(rng, propose, n_mol, None, min_oo)
     mp = _random_multipoles(rng, n_mol)
     return System(pos=pos, mp_local=mp, box=None,
                   meta={"kind": "cluster", "n_mol": n_mol, "seed": seed})
