@@ -166,6 +166,33 @@ void sibfa_set_profiling(sibfa_ctx *ctx, int on);
 sibfa_status sibfa_profile_get(sibfa_ctx *ctx, const char *name, double *ms, int *count);
 void sibfa_profile_clear(sibfa_ctx *ctx);
 
+/* Allocation-free electrostatics of a gas-phase cluster.  (The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate.)
+ *
+ * Some callers must not allocate device memory during a step: code running
+ * under a memory pool or arena that owns all device memory, plugins of host
+ * MD engines that forbid cudaMalloc/cudaFree inside their force callback
+ * (an allocation can synchronize the device and stall other streams), and
+ * code that records its launches into a CUDA graph.  This call computes, on
+ * `stream`, the same multipole (elec) and penetration (pen) energies that
+ * sibfa_energy_forces reports for a gas-phase cluster, using only a fixed
+ * file-scope device array as scratch (about 270 KB, held by every GPU that
+ * loads the library until the process exits).
+ *
+ * n_mol: 1..512 waters (larger clusters are rejected with SIBFA_E_INVALID).
+ * pos: DEVICE pointer, n_mol*9 doubles (O, H1, H2).  mp_local: DEVICE
+ * pointer, n_mol*5*10 doubles (local-frame multipoles as in sibfa_topology).
+ * elec_pen: DEVICE pointer to 2 doubles receiving elec and pen (kcal/mol).
+ * params: host struct.  The call is asynchronous on `stream` and does not
+ * synchronize.  The first call on each device looks up the scratch array's
+ * device address with that device current; make that first call before any
+ * stream capture.  All calls on a device share the scratch array: calls whose
+ * kernels overlap on the GPU (different streams, no ordering) race.  Errors
+ * are described by sibfa_noalloc_last_error(). */
+sibfa_status sibfa_cluster_elec_noalloc(const sibfa_params *params, int n_mol, const double *pos,
+                                        const double *mp_local, double *elec_pen, void *stream);
+const char *sibfa_noalloc_last_error(void);
+
 void sibfa_destroy(sibfa_ctx *ctx);
 
 /* Text of the last error on this context (or of the last failed create when

@@ -90,6 +90,11 @@ def load_library(path: str = LIB_PATH):
     lib.sibfa_profile_get.restype = C.c_int
     lib.sibfa_profile_clear.argtypes = [C.c_void_p]
     lib.sibfa_profile_clear.restype = None
+    lib.sibfa_cluster_elec_noalloc.argtypes = [C.POINTER(sibfa_params), C.c_int, C.c_void_p, C.c_void_p,
+                                               C.c_void_p, C.c_void_p]
+    lib.sibfa_cluster_elec_noalloc.restype = C.c_int
+    lib.sibfa_noalloc_last_error.argtypes = []
+    lib.sibfa_noalloc_last_error.restype = C.c_char_p
     lib.sibfa_destroy.argtypes = [C.c_void_p]
     lib.sibfa_destroy.restype = None
     lib.sibfa_last_error.argtypes = [C.c_void_p]
@@ -188,6 +193,20 @@ def sibfa_minimize(ctx, pos, n_steps, max_disp_A=0.02):
     st = lib.sibfa_minimize(ctx, _ptr(pos), int(n_steps), float(max_disp_A), C.byref(e))
     _check(lib, ctx, st)
     return {n: getattr(e, n) for n in TERMS}
+
+
+def sibfa_cluster_elec_noalloc(params: dict, pos, mp_local, elec_pen, stream=None):
+    """Allocation-free cluster electrostatics: pos (n_mol*9), mp_local
+    (n_mol*50) and elec_pen (2) are float64 CUDA tensors.  Asynchronous on
+    `stream` (a torch.cuda.Stream, raw handle, or None for the legacy default
+    stream)."""
+    lib = load_library()
+    P = sibfa_params(*[float(params[n]) for n in PARAM_FIELDS])
+    n_mol = int(pos.numel() // 9)
+    s = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    st = lib.sibfa_cluster_elec_noalloc(C.byref(P), n_mol, _ptr(pos), _ptr(mp_local), _ptr(elec_pen), s)
+    if st != SIBFA_OK:
+        raise SibfaError(st, lib.sibfa_noalloc_last_error().decode())
 
 
 def sibfa_last_stats(ctx):
