@@ -122,6 +122,8 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.gmp, M * NS * NMP);
     AL(d.vint, M * 3);
     AL(d.nbr, (size_t)M * MAXN);
+    AL(d.ndo, (size_t)M * MAXN * 3);
+    AL(d.ofw, (size_t)M * 3);
     AL(d.nnbr, M);
     int ncell = std::max(1, ctx->ncell[0] * ctx->ncell[1] * ctx->ncell[2]);
     AL(d.cell_of, M);
@@ -230,6 +232,14 @@ void fill_params(KParams &k, const sibfa_params &P, const sibfa_run_opts &o, int
     k.ct_k1 = coef(P.ct_eta / (2.0 * sqrt(P.rvdw_ct_o * P.rvdw_ct_o)));
     k.ct_k2 = coef(P.ct_eta / (2.0 * sqrt(P.rvdw_ct_o * P.rvdw_ct_h)));
     for (int s = 0; s < 5; ++s) k.pen_b[s] = coef(k.b[s]);
+    for (int s = 0; s < 5; ++s) {
+        k.zf[s] = (float)k.z[s];
+        k.betaf[s] = (float)k.beta[s];
+        for (int t = 0; t < 5; ++t) {
+            k.ainv3[s][t] = 1.0 / sqrt(k.a_damp[s] * k.a_damp[t]);
+            k.ainv3f[s][t] = (float)k.ainv3[s][t];
+        }
+    }
 }
 
 bool is_device_ptr(const void *p) {

@@ -30,8 +30,8 @@ __device__ inline void load_tile(const KParams &p, const DevState<R> &d, int i, 
         int j = slot < nn ? d.nbr[i * MAXN + slot] : -1;
         t.j[k] = j;
         if (j >= 0) {
-            double dx, dy, dz;
-            min_image(p, d.pos, i, j, dx, dy, dz);
+            const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
+                const double dx = dp_[0], dy = dp_[1], dz = dp_[2];
             t.dO[k][0] = R(dx);
             t.dO[k][1] = R(dy);
             t.dO[k][2] = R(dz);
@@ -92,8 +92,7 @@ __device__ inline void symadd(Sym<R> &a, const Sym<R> &b, R s) {
 // Warps 0..4: target site w of molecule i.  Warps 5, 6: target lone pair.
 // ---------------------------------------------------------------------------
 template <typename R, bool PER>
-__global__ void __launch_bounds__(224) k_real_perm(KParams p, DevState<R> d) {
-    __shared__ Tile<R> tile;
+__global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) {
     __shared__ double s_e[7][2];
     const int i = blockIdx.x;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -101,7 +100,7 @@ __global__ void __launch_bounds__(224) k_real_perm(KParams p, DevState<R> d) {
     const V3<R> ot = my_pt(d, i, w);
     Mp<R> mt{};
     if (!is_lp) mt = load_mp(d.gmp + (i * NS + w) * NMP);
-    const R Nt = (!is_lp) ? R(p.z[w]) - mt.q * R(w < 3) : R(0);
+    const R Nt = (!is_lp) ? zsite<R>(p, w) - mt.q * R(w < 3) : R(0);
     const R Nt_ = (w < 3) ? Nt : R(0);
     const R rc2 = R(p.rc2), alpha = R(p.alpha), thole = R(p.thole);
     const R third = R(1) / R(3);
@@ -110,22 +109,21 @@ __global__ void __launch_bounds__(224) k_real_perm(KParams p, DevState<R> d) {
     V3<R> gr = mk(R(0), R(0), R(0)), gm = gr, ef = gr;
     Sym<R> gt{};
     const int nn = d.nnbr[i];
-    for (int base = 0; base < nn; base += TILE) {
-        __syncthreads();
-        load_tile(p, d, i, base, nn, tile, true);
-        __syncthreads();
-        const int k = lane;
-        if (base + k >= nn) continue;
-        const V3<R> dO = mk(tile.dO[k][0], tile.dO[k][1], tile.dO[k][2]);
+    for (int slot = lane; slot < nn; slot += 32) {
+        const int j = d.nbr[i * MAXN + slot];
+        const R *dp = d.ndo + ((size_t)i * MAXN + slot) * 3;
+        const V3<R> dO = mk(dp[0], dp[1], dp[2]);
+        const R *offj = d.off + j * NP * 3;
+        const R *mpj = d.gmp + j * NS * NMP;
 #pragma unroll 1
         for (int s = 0; s < NS; ++s) {
-            const V3<R> rs = dO + mk(tile.off[k][s * 3], tile.off[k][s * 3 + 1], tile.off[k][s * 3 + 2]);
+            const V3<R> rs = dO + mk(__ldg(offj + s * 3), __ldg(offj + s * 3 + 1), __ldg(offj + s * 3 + 2));
             const V3<R> x = ot - rs;
             const R r2 = dot(x, x);
             if (PER && r2 >= rc2) continue;
             const R rinv = rsqrt_(r2);
             const R r = r2 * rinv;
-            const Mp<R> ms = load_mp(&tile.mp[k][s * NMP]);
+            const Mp<R> ms = load_mp_g(mpj + s * NMP);
             R g[6];
             if (PER) g_erfc<R, 5>(r, rinv, alpha, g);
             else g_bare<R, 5>(rinv, g);
@@ -144,7 +142,7 @@ __global__ void __launch_bounds__(224) k_real_perm(KParams p, DevState<R> d) {
             gm = gm + f.d1;
             symadd(gt, f.d2, third);
             // ---- penetration: charge-charge*, charge-dipole*, charge-quadrupole*
-            const R Ns = (s < 3) ? R(p.z[s]) - ms.q : R(0);
+            const R Ns = (s < 3) ? zsite<R>(p, s) - ms.q : R(0);
             if (Nt_ != R(0) || Ns != R(0)) {
                 const R xs_b = mulc(r, p.pen_b[s]);          // b_s r
                 const R xt_b = is_lp ? R(0) : mulc(r, p.pen_b[w]);   // b_t r
@@ -188,9 +186,8 @@ __global__ void __launch_bounds__(224) k_real_perm(KParams p, DevState<R> d) {
             }
             // ---- Thole-damped permanent field on the polarizable atom
             if (w < 3) {
-                const R A3 = sqrt_(R(p.a_pol[w] * p.a_damp[s]));
                 R gtol[4];
-                g_thole<R, 3>(r, rinv, R(1) / A3, thole, PER, alpha, gtol);
+                g_thole<R, 3>(r, rinv, ainv3<R>(p, w, s), thole, PER, alpha, gtol);
                 FieldTerms<R> f4;
                 source_field<R, 1>(ms, x, gtol, f4);
                 ef = ef - f4.d1;
@@ -318,8 +315,8 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
     const int nn = d.nnbr[i];
     for (int slot = lane; slot < nn; slot += 32) {
         const int j = d.nbr[i * MAXN + slot];
-        double dx, dy, dz;
-        min_image(p, d.pos, i, j, dx, dy, dz);
+        const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
+                const double dx = dp_[0], dy = dp_[1], dz = dp_[2];
         const V3<R> dO = mk(R(dx), R(dy), R(dz));
         V3<R> Q[5];
         Q[0] = dO;
@@ -465,10 +462,10 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
                 const R dfdr = e6 * ((a6 - R(6)) * ri) + e8 * ((a8 - R(8)) * ri) + e10 * ((a10 - R(10)) * ri);
                 const bool lu = u >= 3, lv = v >= 3;
                 R pref, xc, xa;
-                if (!lu && !lv) { pref = -R(p.beta[u] * p.beta[v]); xc = R(p.xd_c1); xa = R(p.xd_a1); }
+                if (!lu && !lv) { pref = -betap<R>(p, u) * betap<R>(p, v); xc = R(p.xd_c1); xa = R(p.xd_a1); }
                 else if (lu && lv) { pref = -nlp * nlp * R(0.25); xc = nlp * nlp * R(0.25) * R(p.xd_c2); xa = R(p.xd_a2); }
                 else { pref = -R(p.delta) * R(0.5); xc = nlp * R(0.5) * R(p.xd_c3); xa = R(p.xd_a3); }
-                const R K = R(p.beta[u] * p.beta[v]) * cfi[u] * cfj[v];
+                const R K = betap<R>(p, u) * betap<R>(p, v) * cfi[u] * cfj[v];
                 const R ex = xc * K * exp_(-mulc(r, p.xd_k[ku][kv]));
                 Ed.add(R(0.5) * pref * fsum);
                 Ex.add(R(0.5) * ex);
@@ -558,8 +555,8 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
     const int nn = d.nnbr[i];
     for (int slot = lane; slot < nn; slot += 32) {
         const int j = d.nbr[i * MAXN + slot];
-        double dx, dy, dz;
-        min_image(p, d.pos, i, j, dx, dy, dz);
+        const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
+                const double dx = dp_[0], dy = dp_[1], dz = dp_[2];
         const V3<R> dO = mk(R(dx), R(dy), R(dz));
         if (PER && dot(dO, dO) >= rc2) continue;
         V3<R> Q[5];
@@ -639,8 +636,8 @@ __global__ void __launch_bounds__(96) k_real_tmu(KParams p, DevState<R> d, const
             int j = slot < nn ? d.nbr[i * MAXN + slot] : -1;
             t.j[k] = j;
             if (j >= 0) {
-                double dx, dy, dz;
-                min_image(p, d.pos, i, j, dx, dy, dz);
+                const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
+                const double dx = dp_[0], dy = dp_[1], dz = dp_[2];
                 t.dO[k][0] = R(dx); t.dO[k][1] = R(dy); t.dO[k][2] = R(dz);
             }
         }
@@ -662,7 +659,7 @@ __global__ void __launch_bounds__(96) k_real_tmu(KParams p, DevState<R> d, const
             if (PER && r2 >= rc2) continue;
             const R rinv = rsqrt_(r2), r = r2 * rinv;
             R g[4];
-            g_thole<R, 2>(r, rinv, rsqrt_(R(p.a_pol[a] * p.a_pol[b])), thole, PER, alpha, g);
+            g_thole<R, 2>(r, rinv, ainv3<R>(p, a, b), thole, PER, alpha, g);
             const V3<R> mu = mk(t.v[k][b * 3], t.v[k][b * 3 + 1], t.v[k][b * 3 + 2]);
             // field of a point dipole: E = g2 (mu.x) x + g1 mu ... d1 = -(g2 (mu.x) x + g1 mu)
             const R s = dot(mu, x);
@@ -717,8 +714,8 @@ __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d)
             int j = slot < nn ? d.nbr[i * MAXN + slot] : -1;
             t.j[k] = j;
             if (j >= 0) {
-                double dx, dy, dz;
-                min_image(p, d.pos, i, j, dx, dy, dz);
+                const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
+                const double dx = dp_[0], dy = dp_[1], dz = dp_[2];
                 t.dO[k][0] = R(dx); t.dO[k][1] = R(dy); t.dO[k][2] = R(dz);
             }
         }
@@ -751,7 +748,7 @@ __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d)
             if (PER && r2 >= rc2) continue;
             const R rinv = rsqrt_(r2), r = r2 * rinv;
             R g[6];
-            g_thole<R, 4>(r, rinv, rsqrt_(R(p.a_damp[w] * p.a_pol[b])), thole, PER, alpha, g);
+            g_thole<R, 4>(r, rinv, ainv3<R>(p, w, b), thole, PER, alpha, g);
             g[5] = R(0);
             Mp<R> ms{};
             ms.mu = mk(t.mu[k][b * 3], t.mu[k][b * 3 + 1], t.mu[k][b * 3 + 2]);
@@ -793,7 +790,7 @@ __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d)
                 if (PER && r2 >= rc2) continue;
                 const R rinv = rsqrt_(r2), r = r2 * rinv;
                 R g[6];
-                g_thole<R, 4>(r, rinv, rsqrt_(R(p.a_pol[w] * p.a_damp[s])), thole, PER, alpha, g);
+                g_thole<R, 4>(r, rinv, ainv3<R>(p, w, s), thole, PER, alpha, g);
                 g[5] = R(0);
                 const Mp<R> ms = load_mp(&t.mp[k][s * NMP]);
                 FieldTerms<R> f;

@@ -43,6 +43,12 @@ __global__ void k_sites(KParams p, DevState<R> d) {
         ext = fmaxf(ext, (float)sqrt(dot(offs[k], offs[k])));
     }
     atomicMax((int *)d.ext, __float_as_int(ext));
+    // O wrapped into the box in single precision (candidate tests of the list build)
+    for (int k = 0; k < 3; ++k) {
+        double v = x[k];
+        if (p.periodic) v -= p.box[k] * floor(v / p.box[k]);
+        d.ofw[m * 3 + k] = (float)v;
+    }
     const double *ml = d.mp_local + m * NS * NMP;
     double qs[NS];
     for (int s = 0; s < NS; ++s) {
@@ -111,8 +117,11 @@ void launch_sites(const KParams &p, DevState<R> &d, Launch L) {
 // ---------------------------------------------------------------------------
 // Neighbour list: molecule pairs whose O-O distance (minimum image) is below
 // rc + 2 * ext, ext = largest point distance from its own O this step.  The
-// list is full (both orders), sorted by cell and molecule index, so every
-// pair sum over it has a fixed order.
+// list is full (both orders), ordered by cell and molecule index, so every
+// pair sum over it has a fixed order.  Each entry stores the minimum-image
+// displacement O_j - O_i (computed in FP64, stored in R), so the pair
+// kernels do no FP64 work.  Candidates are tested in FP32 with a small
+// margin; only accepted pairs pay the FP64 displacement.
 // ---------------------------------------------------------------------------
 __device__ inline double list_cut(const KParams &p, const float *ext) {
     return p.periodic ? p.rc + 2.0 * (double)(*ext) : 1e300;
@@ -126,27 +135,44 @@ __global__ void k_check_ext(KParams p, DevState<R> d) {
     if (cut > half || *d.ext > 1.3f) atomicOr(d.flags, F_CUTOFF);
 }
 
+// FP32 candidate test on wrapped O positions
+template <typename R>
+__device__ inline bool near_f(const KParams &p, const DevState<R> &d, int i, int j, float cut2f) {
+    float dx = d.ofw[j * 3] - d.ofw[i * 3], dy = d.ofw[j * 3 + 1] - d.ofw[i * 3 + 1], dz = d.ofw[j * 3 + 2] - d.ofw[i * 3 + 2];
+    if (p.periodic) {
+        const float L0 = (float)p.box[0], L1 = (float)p.box[1], L2 = (float)p.box[2];
+        dx -= L0 * rintf(dx / L0);
+        dy -= L1 * rintf(dy / L1);
+        dz -= L2 * rintf(dz / L2);
+    }
+    return dx * dx + dy * dy + dz * dz < cut2f;
+}
+
+template <typename R>
+__device__ inline void store_entry(const KParams &p, DevState<R> &d, int i, int slot, int j) {
+    if (slot >= MAXN) return;
+    double dx, dy, dz;
+    min_image(p, d.pos, i, j, dx, dy, dz);
+    d.nbr[i * MAXN + slot] = j;
+    R *o = d.ndo + ((size_t)i * MAXN + slot) * 3;
+    o[0] = R(dx);
+    o[1] = R(dy);
+    o[2] = R(dz);
+}
+
 template <typename R>
 __global__ void k_nbr_all(KParams p, DevState<R> d) {
     const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (i >= p.M) return;
-    const double cut = list_cut(p, d.ext);
-    const double cut2 = cut * cut;
+    const double cut = list_cut(p, d.ext) + 1e-3;
+    const float cut2f = p.periodic ? (float)(cut * cut) : 3.0e38f;
     int n = 0;
     for (int j0 = 0; j0 < p.M; j0 += 32) {
-        int j = j0 + lane;
-        bool ok = false;
-        if (j < p.M && j != i) {
-            double dx, dy, dz;
-            min_image(p, d.pos, i, j, dx, dy, dz);
-            ok = dx * dx + dy * dy + dz * dz < cut2;
-        }
-        unsigned b = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            int slot = n + __popc(b & ((1u << lane) - 1u));
-            if (slot < MAXN) d.nbr[i * MAXN + slot] = j;
-        }
+        const int j = j0 + lane;
+        const bool ok = (j < p.M && j != i) && near_f(p, d, i, j, cut2f);
+        const unsigned b = __ballot_sync(0xffffffffu, ok);
+        if (ok) store_entry(p, d, i, n + __popc(b & ((1u << lane) - 1u)), j);
         n += __popc(b);
     }
     if (lane == 0) {
@@ -155,12 +181,11 @@ __global__ void k_nbr_all(KParams p, DevState<R> d) {
     }
 }
 
-__device__ inline int cell_index(const KParams &p, const int nc[3], double x, double y, double z) {
-    double f[3] = {x / p.box[0], y / p.box[1], z / p.box[2]};
+__device__ inline int cell_index(const KParams &p, const int nc[3], float x, float y, float z) {
+    const float f[3] = {x / (float)p.box[0], y / (float)p.box[1], z / (float)p.box[2]};
     int c[3];
     for (int k = 0; k < 3; ++k) {
-        double u = f[k] - floor(f[k]);
-        int ci = (int)(u * nc[k]);
+        int ci = (int)(f[k] * nc[k]);
         c[k] = min(max(ci, 0), nc[k] - 1);
     }
     return (c[0] * nc[1] + c[1]) * nc[2] + c[2];
@@ -171,7 +196,7 @@ __global__ void k_cell_count(KParams p, DevState<R> d, int nc0, int nc1, int nc2
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= p.M) return;
     const int nc[3] = {nc0, nc1, nc2};
-    int c = cell_index(p, nc, d.pos[m * 9], d.pos[m * 9 + 1], d.pos[m * 9 + 2]);
+    const int c = cell_index(p, nc, d.ofw[m * 3], d.ofw[m * 3 + 1], d.ofw[m * 3 + 2]);
     d.cell_of[m] = c;
     atomicAdd(&d.cell_cursor[c], 1);
 }
@@ -215,19 +240,34 @@ __global__ void k_cell_fill(KParams p, DevState<R> d) {
     d.cell_mol[d.cell_start[c] + k] = m;
 }
 
+// Order the members of every cell by molecule index: one warp per cell, each
+// member's rank is the number of smaller members (indices are distinct).
+constexpr int SORT_CAP = 256;
 template <typename R>
 __global__ void k_cell_sort(DevState<R> d, int ncell) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ int buf[4][SORT_CAP];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 4 + w;
     if (c >= ncell) return;
-    int a = d.cell_start[c], b = d.cell_start[c + 1];
-    for (int k = a + 1; k < b; ++k) {
-        int v = d.cell_mol[k];
-        int j = k - 1;
-        while (j >= a && d.cell_mol[j] > v) {
-            d.cell_mol[j + 1] = d.cell_mol[j];
-            --j;
+    const int a = d.cell_start[c], n = d.cell_start[c + 1] - a;
+    if (n <= SORT_CAP) {
+        for (int k = lane; k < n; k += 32) buf[w][k] = d.cell_mol[a + k];
+        __syncwarp();
+        for (int k = lane; k < n; k += 32) {
+            const int v = buf[w][k];
+            int r = 0;
+            for (int q = 0; q < n; ++q) r += buf[w][q] < v;
+            d.cell_mol[a + r] = v;
         }
-        d.cell_mol[j + 1] = v;
+    } else if (lane == 0) {
+        for (int k = a + 1; k < a + n; ++k) {
+            int v = d.cell_mol[k], j = k - 1;
+            while (j >= a && d.cell_mol[j] > v) {
+                d.cell_mol[j + 1] = d.cell_mol[j];
+                --j;
+            }
+            d.cell_mol[j + 1] = v;
+        }
     }
 }
 
@@ -236,32 +276,25 @@ __global__ void k_nbr_cell(KParams p, DevState<R> d, int nc0, int nc1, int nc2) 
     const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (i >= p.M) return;
-    const double cut = list_cut(p, d.ext);
-    const double cut2 = cut * cut;
+    const double cut = list_cut(p, d.ext) + 1e-3;
+    const float cut2f = (float)(cut * cut);
     const int ci = d.cell_of[i];
     const int cz = ci % nc2, cy = (ci / nc2) % nc1, cx = ci / (nc1 * nc2);
     int n = 0;
     for (int o = 0; o < 27; ++o) {
-        int ox = o / 9 - 1, oy = (o / 3) % 3 - 1, oz = o % 3 - 1;
-        int c = (((cx + ox + nc0) % nc0) * nc1 + (cy + oy + nc1) % nc1) * nc2 + (cz + oz + nc2) % nc2;
-        int a = d.cell_start[c], b = d.cell_start[c + 1];
+        const int ox = o / 9 - 1, oy = (o / 3) % 3 - 1, oz = o % 3 - 1;
+        const int c = (((cx + ox + nc0) % nc0) * nc1 + (cy + oy + nc1) % nc1) * nc2 + (cz + oz + nc2) % nc2;
+        const int a = d.cell_start[c], b = d.cell_start[c + 1];
         for (int k0 = a; k0 < b; k0 += 32) {
-            int k = k0 + lane;
-            bool ok = false;
+            const int k = k0 + lane;
             int j = -1;
+            bool ok = false;
             if (k < b) {
                 j = d.cell_mol[k];
-                if (j != i) {
-                    double dx, dy, dz;
-                    min_image(p, d.pos, i, j, dx, dy, dz);
-                    ok = dx * dx + dy * dy + dz * dz < cut2;
-                }
+                ok = (j != i) && near_f(p, d, i, j, cut2f);
             }
-            unsigned bl = __ballot_sync(0xffffffffu, ok);
-            if (ok) {
-                int slot = n + __popc(bl & ((1u << lane) - 1u));
-                if (slot < MAXN) d.nbr[i * MAXN + slot] = j;
-            }
+            const unsigned bl = __ballot_sync(0xffffffffu, ok);
+            if (ok) store_entry(p, d, i, n + __popc(bl & ((1u << lane) - 1u)), j);
             n += __popc(bl);
         }
     }
@@ -286,7 +319,7 @@ void launch_neighbors(const KParams &p, DevState<R> &d, int nc[3], Launch L) {
     k_cell_count<R><<<(p.M + 255) / 256, 256, 0, L.s>>>(p, d, nc[0], nc[1], nc[2]);
     k_cell_scan<R><<<1, 1024, 0, L.s>>>(d, ncell);
     k_cell_fill<R><<<(p.M + 255) / 256, 256, 0, L.s>>>(p, d);
-    k_cell_sort<R><<<(ncell + 127) / 128, 128, 0, L.s>>>(d, ncell);
+    k_cell_sort<R><<<(ncell + 3) / 4, 128, 0, L.s>>>(d, ncell);
     k_nbr_cell<R><<<(p.M + wpb - 1) / wpb, 32 * wpb, 0, L.s>>>(p, d, nc[0], nc[1], nc[2]);
     count(L, 5);
 }

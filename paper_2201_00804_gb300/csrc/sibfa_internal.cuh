@@ -61,7 +61,32 @@ struct KParams {
     Coef xd_k[3][3];                     // A_type / (2 sqrt(rv_a rv_b)) for exchange-dispersion
     Coef ct_k1, ct_k2;                   // eta / (2 sqrt(rv_O rv_O)), eta / (2 sqrt(rv_O rv_H))
     Coef pen_b[5];                       // valence damping exponents per site
+    // Single-precision copies of per-pair indexed constants (no FP64 work in
+    // the FP32 inner loops); the FP64 path uses the double tables.
+    float zf[5];                         // nuclear charge per site
+    float ainv3f[5][5];                  // Thole 1 / sqrt(alpha_s alpha_t) over the site damping polarizabilities
+    double ainv3[5][5];
+    float betaf[5];                      // dispersion beta per point (O, H, H, LP, LP)
 };
+
+template <typename R>
+__device__ inline R zsite(const KParams &p, int s);
+template <>
+__device__ inline float zsite<float>(const KParams &p, int s) { return p.zf[s]; }
+template <>
+__device__ inline double zsite<double>(const KParams &p, int s) { return p.z[s]; }
+template <typename R>
+__device__ inline R ainv3(const KParams &p, int a, int b);
+template <>
+__device__ inline float ainv3<float>(const KParams &p, int a, int b) { return p.ainv3f[a][b]; }
+template <>
+__device__ inline double ainv3<double>(const KParams &p, int a, int b) { return p.ainv3[a][b]; }
+template <typename R>
+__device__ inline R betap(const KParams &p, int a);
+template <>
+__device__ inline float betap<float>(const KParams &p, int a) { return p.betaf[a]; }
+template <>
+__device__ inline double betap<double>(const KParams &p, int a) { return p.beta[a]; }
 
 // x * c for a coefficient precomputed in FP64: in FP32 the product keeps the
 // FP64 rounding of c (x * hi + x * lo).
@@ -90,7 +115,9 @@ struct DevState {
     R *gmp;             // M*NS*NMP global multipoles
     double *vint;       // M*3 intramolecular potential on O, H1, H2 (charge-transfer V_int)
     int *nbr;           // M*MAXN neighbour molecules (full list)
+    R *ndo;             // M*MAXN*3 minimum-image displacement O_j - O_i of each entry
     int *nnbr;          // M
+    float *ofw;         // M*3 O positions wrapped into the box (single precision, list build only)
     // cell list
     int *cell_of;       // M
     int *cell_start;    // ncell+1
@@ -428,6 +455,15 @@ __device__ inline void min_image(const KParams &p, const double *pos, int i, int
         dy -= p.box[1] * rint(dy / p.box[1]);
         dz -= p.box[2] * rint(dz / p.box[2]);
     }
+}
+
+template <typename R>
+__device__ inline Mp<R> load_mp_g(const R *g) {
+    Mp<R> m;
+    m.q = __ldg(g);
+    m.mu = mk(__ldg(g + 1), __ldg(g + 2), __ldg(g + 3));
+    m.th = Sym<R>{__ldg(g + 4), __ldg(g + 5), __ldg(g + 6), __ldg(g + 7), __ldg(g + 8), __ldg(g + 9)};
+    return m;
 }
 
 template <typename R>
