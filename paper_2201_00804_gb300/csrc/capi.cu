@@ -18,7 +18,14 @@ struct sibfa_ctx {
     int M = 0;
     sibfa_run_opts opts{};
     KParams kp{};
-    cudaStream_t s = nullptr;
+    cudaStream_t s = nullptr;    // the library's own work stream (non-blocking)
+    cudaStream_t us = nullptr;   // the caller's stream (ordering only)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // polarization iterations as one CUDA graph with a device-side while loop
+    cudaGraphExec_t pcg_exec = nullptr;
+    int pcg_graph_state = 0;     // 0 untried, 1 in use, -1 unavailable (host loop)
+    uint64_t pcg_iter_launches = 0;
+    bool capturing = false;
     int prec = SIBFA_PREC_MIXED;
     DevState<float> df{};
     DevState<double> dd{};
@@ -51,7 +58,7 @@ struct Phase {
     sibfa_ctx *ctx;
     size_t idx = (size_t)-1;
     Phase(sibfa_ctx *c, const char *name) : ctx(c) {
-        if (!ctx->profiling) return;
+        if (!ctx->profiling || ctx->capturing) return;
         cudaEvent_t a, b;
         if (ctx->event_pool.size() >= 2) {
             a = ctx->event_pool.back();
@@ -100,7 +107,7 @@ sibfa_status dalloc(sibfa_ctx *ctx, T **p, size_t n) {
         ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
         return SIBFA_E_OOM;
     }
-    cudaMemset(q, 0, n * sizeof(T) + 16);
+    cudaMemsetAsync(q, 0, n * sizeof(T) + 16, ctx->s);   // ordered before any later work on the stream
     ctx->allocs.push_back(q);
     *p = (T *)q;
     return SIBFA_OK;
@@ -172,7 +179,10 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
 void fill_params(KParams &k, const sibfa_params &P, const sibfa_run_opts &o, int M) {
     k.M = M;
     k.periodic = o.periodic;
-    for (int i = 0; i < 3; ++i) k.box[i] = o.box[i];
+    for (int i = 0; i < 3; ++i) {
+        k.box[i] = o.box[i];
+        k.ibox[i] = o.box[i] > 0 ? 1.0 / o.box[i] : 0.0;
+    }
     k.rc = o.rc;
     k.rc2 = o.rc * o.rc;
     k.alpha = o.ewald_alpha;
@@ -242,6 +252,19 @@ void fill_params(KParams &k, const sibfa_params &P, const sibfa_run_opts &o, int
     }
 }
 
+// Order the work stream after the caller's stream at entry, and the caller's
+// stream after the work stream at exit.
+sibfa_status enter(sibfa_ctx *ctx) {
+    CK(cudaEventRecord(ctx->ev_in, ctx->us));
+    CK(cudaStreamWaitEvent(ctx->s, ctx->ev_in, 0));
+    return SIBFA_OK;
+}
+sibfa_status leave(sibfa_ctx *ctx) {
+    CK(cudaEventRecord(ctx->ev_out, ctx->s));
+    CK(cudaStreamWaitEvent(ctx->us, ctx->ev_out, 0));
+    return SIBFA_OK;
+}
+
 bool is_device_ptr(const void *p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -293,6 +316,56 @@ sibfa_status matvec(sibfa_ctx *ctx, DevState<R> &d, const double *vec, Launch L)
     return SIBFA_OK;
 }
 
+// Continue the device-side PCG loop while not converged and below maxit.
+__global__ void k_pcg_cond(cudaGraphConditionalHandle h, const double *scal, int maxit) {
+    const bool more = scal[SC_DONE] == 0.0 && scal[SC_IT] < (double)maxit;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// One PCG iteration (T p product, step, residual, direction update) captured
+// as the body of a graph while-node; the loop runs on the device and the host
+// waits once per solve.
+template <typename R>
+sibfa_status build_pcg_graph(sibfa_ctx *ctx, DevState<R> &d, int maxit) {
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return SIBFA_E_CUDA;
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    cudaGraph_t out = nullptr;
+    uint64_t before = ctx->launches;
+    sibfa_status st = SIBFA_E_CUDA;
+    do {
+        if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) break;
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(ctx->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+            cudaSuccess)
+            break;
+        ctx->capturing = true;
+        Launch L{ctx->s, &ctx->launches};
+        sibfa_status sm = matvec(ctx, d, d.pv, L);
+        launch_pcg_iter_a(ctx->kp, d, L);
+        launch_pcg_iter_b(ctx->kp, d, 0.0, L);
+        k_pcg_cond<<<1, 1, 0, ctx->s>>>(h, d.scal, maxit);
+        ctx->capturing = false;
+        const cudaError_t ec = cudaStreamEndCapture(ctx->s, &out);
+        if (sm != SIBFA_OK || ec != cudaSuccess) break;
+        if (cudaGraphInstantiate(&ctx->pcg_exec, g, 0) != cudaSuccess) break;
+        st = SIBFA_OK;
+    } while (0);
+    ctx->capturing = false;
+    ctx->pcg_iter_launches = ctx->launches - before + 1;
+    ctx->launches = before;     // counted per executed iteration instead
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st;
+}
+
 template <typename R>
 sibfa_status solve(sibfa_ctx *ctx, DevState<R> &d, double tol, Launch L) {
     const KParams &p = ctx->kp;
@@ -304,6 +377,14 @@ sibfa_status solve(sibfa_ctx *ctx, DevState<R> &d, double tol, Launch L) {
     double *h = ctx->h_pin;
     int it = 0;
     const int maxit = ctx->opts.pcg_max_iter > 0 ? ctx->opts.pcg_max_iter : 200;
+    if (ctx->pcg_graph_state == 0) ctx->pcg_graph_state = build_pcg_graph(ctx, d, maxit) == SIBFA_OK ? 1 : -1;
+    if (ctx->pcg_graph_state == 1) {
+        CK(cudaGraphLaunch(ctx->pcg_exec, ctx->s));
+        CK(cudaMemcpyAsync(h, d.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+        CK(cudaStreamSynchronize(ctx->s));
+        ctx->launches += (uint64_t)h[SC_IT] * ctx->pcg_iter_launches;
+        it = maxit;   // the device loop has finished
+    }
     for (;;) {
         CK(cudaMemcpyAsync(h, d.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
         CK(cudaStreamSynchronize(ctx->s));
@@ -404,6 +485,8 @@ sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_ene
                 return SIBFA_E_INVALID;
             }
     }
+    sibfa_status st0 = enter(ctx);
+    if (st0) return st0;
     if (pos) {
         if (is_device_ptr(pos)) {
             CK(cudaMemcpyAsync(d.pos, pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
@@ -431,6 +514,8 @@ sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_ene
         if (is_device_ptr(mu_out)) CK(cudaMemcpyAsync(mu_out, d.mu, nb, cudaMemcpyDeviceToDevice, ctx->s));
         else CK(cudaMemcpyAsync(h + 32, d.mu, nb, cudaMemcpyDeviceToHost, ctx->s));
     }
+    st0 = leave(ctx);
+    if (st0) return st0;
     CK(cudaStreamSynchronize(ctx->s));
     CK(cudaGetLastError());
     if (forces && !is_device_ptr(forces)) std::memcpy(forces, h + 32, nb);
@@ -458,7 +543,9 @@ sibfa_status create_impl(sibfa_ctx *ctx, const sibfa_topology *topo) {
     sibfa_status st = alloc_state<R>(ctx, state<R>(ctx));
     if (st) return st;
     DevState<R> &d = state<R>(ctx);
-    CK(cudaMemcpy(d.mp_local, topo->mp_local, (size_t)M * NS * NMP * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(d.mp_local, topo->mp_local, (size_t)M * NS * NMP * sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
     if (ctx->opts.periodic) {
         Launch L{ctx->s, &ctx->launches};
         launch_influence(ctx->kp, d.infl, L);
@@ -502,6 +589,8 @@ static sibfa_status md_impl(sibfa_ctx *ctx, double *pos, double *vel, const doub
     }
     const double tol = ctx->opts.pcg_tol_D > 0 ? ctx->opts.pcg_tol_D : 1e-6;
     Launch L{ctx->s, &ctx->launches};
+    sibfa_status st_e = enter(ctx);
+    if (st_e) return st_e;
     k_inverse<<<(M * 3 + 255) / 256, 256, 0, ctx->s>>>(M * 3, masses, ctx->d_invm);
     ctx->launches += 1;
     CK(cudaMemcpyAsync(d.pos, pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
@@ -524,6 +613,8 @@ static sibfa_status md_impl(sibfa_ctx *ctx, double *pos, double *vel, const doub
     double *h = ctx->h_pin;
     CK(cudaMemcpyAsync(h, ctx->d_energy, (NTERM + 1) * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaMemcpyAsync((int *)(h + 16), d.flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    st_e = leave(ctx);
+    if (st_e) return st_e;
     CK(cudaStreamSynchronize(ctx->s));
     ctx->md_forces_valid = true;
     sibfa_status fl = check_flags(ctx, *(int *)(h + 16));
@@ -572,7 +663,14 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
     ctx->M = topo->n_mol;
     ctx->opts = *opts;
     ctx->prec = opts->precision;
-    ctx->s = (cudaStream_t)opts->stream;
+    ctx->us = (cudaStream_t)opts->stream;
+    if (cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        g_create_error = "sibfa_create: could not create the work stream";
+        delete ctx;
+        return SIBFA_E_CUDA;
+    }
     fill_params(ctx->kp, *params, *opts, ctx->M);
     if (opts->periodic) {
         const double cell = opts->rc + 2.6;   // rc + 2 * maximum site extent (1.3 A)
@@ -635,6 +733,8 @@ static sibfa_status minimize_impl(sibfa_ctx *ctx, double *pos, int n, double cap
     Launch L{ctx->s, &ctx->launches};
     const sibfa_run_opts &o = ctx->opts;
     const double th0 = o.md_theta0_deg * M_PI / 180.0;
+    sibfa_status st_e = enter(ctx);
+    if (st_e) return st_e;
     CK(cudaMemcpyAsync(d.pos, pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
     for (int k = 0; k < n; ++k) {
         sibfa_status st = evaluate<R>(ctx, true, false, tol);
@@ -645,6 +745,8 @@ static sibfa_status minimize_impl(sibfa_ctx *ctx, double *pos, int n, double cap
     CK(cudaMemcpyAsync(pos, d.pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
     double *h = ctx->h_pin;
     CK(cudaMemcpyAsync(h, ctx->d_energy, (NTERM + 1) * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    st_e = leave(ctx);
+    if (st_e) return st_e;
     CK(cudaStreamSynchronize(ctx->s));
     ctx->md_forces_valid = false;
     if (e) {
@@ -723,6 +825,9 @@ uint64_t sibfa_kernel_launches(const sibfa_ctx *ctx) { return ctx ? ctx->launche
 void sibfa_destroy(sibfa_ctx *ctx) {
     if (!ctx) return;
     if (ctx->s) cudaStreamSynchronize(ctx->s);
+    if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     else cudaDeviceSynchronize();
     if (ctx->have_fft) {
         cufftDestroy(ctx->r2c1);
@@ -737,6 +842,7 @@ void sibfa_destroy(sibfa_ctx *ctx) {
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     for (void *p : ctx->allocs) cudaFree(p);
     if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
+    if (ctx->s) cudaStreamDestroy(ctx->s);
     delete ctx;
 }
 

@@ -202,246 +202,6 @@ void launch_pol_energy(const KParams &p, DevState<R> &d, Launch L) {
 }
 
 // ---------------------------------------------------------------------------
-// Intramolecular geometry in FP64
-// ---------------------------------------------------------------------------
-__device__ inline void frame_d2(V3<double> zv, V3<double> xv, V3<double> &ex, V3<double> &ey, V3<double> &ez) {
-    ez = (1.0 / sqrt(dot(zv, zv))) * zv;
-    V3<double> xp = xv - dot(xv, ez) * ez;
-    ex = (1.0 / sqrt(dot(xp, xp))) * xp;
-    ey = cross(ez, ex);
-}
-
-// absolute FP64 positions of the 7 points of molecule m
-template <typename R>
-__device__ inline void points_d(const KParams &p, const DevState<R> &d, int m, V3<double> *X) {
-    const double *x = d.pos + m * 9;
-    const V3<double> O = mk(x[0], x[1], x[2]), H1 = mk(x[3], x[4], x[5]), H2 = mk(x[6], x[7], x[8]);
-    const V3<double> r1 = H1 - O, r2 = H2 - O;
-    const V3<double> u1 = (1.0 / sqrt(dot(r1, r1))) * r1, u2 = (1.0 / sqrt(dot(r2, r2))) * r2;
-    V3<double> ex, ey, ez;
-    frame_d2(u1 + u2, r1, ex, ey, ez);
-    X[0] = O;
-    X[1] = H1;
-    X[2] = H2;
-    X[3] = 0.5 * (O + H1);
-    X[4] = 0.5 * (O + H2);
-    X[5] = O + p.d_lp * ((-p.lp_cos) * ez + p.lp_sin * ey);
-    X[6] = O + p.d_lp * ((-p.lp_cos) * ez - p.lp_sin * ey);
-}
-
-template <typename R>
-__device__ inline Mp<double> mp_d(const DevState<R> &d, int m, int s) {
-    const R *g = d.gmp + (m * NS + s) * NMP;
-    Mp<double> o;
-    o.q = g[0];
-    o.mu = mk((double)g[1], (double)g[2], (double)g[3]);
-    o.th = Sym<double>{g[4], g[5], g[6], g[7], g[8], g[9]};
-    return o;
-}
-
-// erf(alpha r)/r weights g_0..g_5 (1/r minus the Ewald real-space kernel)
-__device__ inline void g_erf_d(double r, double alpha, double *g) {
-    double gb[6], ge[6];
-    g_bare<double, 5>(1.0 / r, gb);
-    g_erfc<double, 5>(r, 1.0 / r, alpha, ge);
-    for (int n = 0; n < 6; ++n) g[n] = gb[n] - ge[n];
-}
-
-__device__ inline void addv(double *dst, V3<double> v, double s) {
-    dst[0] += s * v.x;
-    dst[1] += s * v.y;
-    dst[2] += s * v.z;
-}
-__device__ inline void adds(double *dst, const Sym<double> &v, double s) {
-    dst[0] += s * v.xx; dst[1] += s * v.yy; dst[2] += s * v.zz;
-    dst[3] += s * v.xy; dst[4] += s * v.xz; dst[5] += s * v.yz;
-}
-
-// Permanent pass: remove the erf part of the 10 intramolecular site pairs
-// (energy, gradients, sensitivities), add the Gaussian self energy, and
-// correct the field on O/H1/H2 and the potential on the lone pairs.
-template <typename R>
-__global__ void k_intra_perm(KParams p, DevState<R> d) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= p.M) return;
-    V3<double> X[NP];
-    points_d(p, d, m, X);
-    Mp<double> M[NS];
-    for (int s = 0; s < NS; ++s) M[s] = mp_d(d, m, s);
-    const double ke = p.ke, al = p.alpha;
-    double e = 0;
-    for (int t = 0; t < NS; ++t)
-        for (int s = t + 1; s < NS; ++s) {
-            const V3<double> x = X[t] - X[s];
-            const double r = sqrt(dot(x, x));
-            double g[6];
-            g_erf_d(r, al, g);
-            FieldTerms<double> f;
-            source_field<double, 3>(M[s], x, g, f);
-            e += M[t].q * f.phi + dot(M[t].mu, f.d1) + symdd(M[t].th, f.d2) / 3.0;
-            const V3<double> gt = target_grad(M[t], M[s], x, g, f);
-            addv(d.gpt + (m * NP + t) * 3, gt, -ke);
-            addv(d.gpt + (m * NP + s) * 3, gt, ke);
-            addv(d.gmu + (m * NS + t) * 3, f.d1, -ke);
-            adds(d.gth + (m * NS + t) * 6, f.d2, -ke / 3.0);
-            FieldTerms<double> f2;
-            source_field<double, 2>(M[t], -x, g, f2);
-            addv(d.gmu + (m * NS + s) * 3, f2.d1, -ke);
-            adds(d.gth + (m * NS + s) * 6, f2.d2, -ke / 3.0);
-        }
-    double self = 0;
-    for (int s = 0; s < NS; ++s)
-        self += M[s].q * M[s].q + (2.0 * al * al / 3.0) * dot(M[s].mu, M[s].mu) +
-                (8.0 * al * al * al * al / 45.0) * symdd(M[s].th, M[s].th);
-    self *= -ke * al / sqrt(M_PI);
-    d.epart[m * NTERM + T_ELEC] += -ke * e + self;
-    // field on the polarizable atoms: remove intramolecular erf fields, add the self term
-    const double cself = 4.0 * al * al * al / (3.0 * sqrt(M_PI));
-    for (int a = 0; a < 3; ++a) {
-        V3<double> E = cself * M[a].mu;
-        for (int s = 0; s < NS; ++s) {
-            if (s == a) continue;
-            const V3<double> x = X[a] - X[s];
-            double g[6];
-            g_erf_d(sqrt(dot(x, x)), al, g);
-            FieldTerms<double> f;
-            source_field<double, 1>(M[s], x, g, f);
-            E = E + f.d1;
-        }
-        addv(d.efield + m * 9 + a * 3, E, 1.0);
-    }
-    // lone-pair potential: remove the own molecule's erf part
-    for (int l = 0; l < 2; ++l) {
-        double V = 0;
-        V3<double> dV = mk(0.0, 0.0, 0.0);
-        for (int s = 0; s < NS; ++s) {
-            const V3<double> x = X[5 + l] - X[s];
-            double g[6];
-            g_erf_d(sqrt(dot(x, x)), al, g);
-            FieldTerms<double> f;
-            source_field<double, 1>(M[s], x, g, f);
-            V += f.phi;
-            dV = dV + f.d1;
-        }
-        d.vlp[m * 2 + l] -= ke * V;
-        addv(d.dvlp + (m * 2 + l) * 3, dV, -ke);
-    }
-}
-
-template <typename R>
-void launch_intra_perm(const KParams &p, DevState<R> &d, Launch L) {
-    k_intra_perm<R><<<(p.M + 127) / 128, 128, 0, L.s>>>(p, d);
-    count(L);
-}
-
-// PCG product, intramolecular part (periodic): out += erf-field removal and self term.
-template <typename R>
-__global__ void k_intra_tmu(KParams p, DevState<R> d, const double *vec, double *out) {
-    if (d.scal[S_DONE] != 0.0) return;
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= p.M) return;
-    V3<double> X[NP];
-    points_d(p, d, m, X);
-    const double al = p.alpha;
-    const double cself = 4.0 * al * al * al / (3.0 * sqrt(M_PI));
-    for (int a = 0; a < 3; ++a) {
-        V3<double> E = cself * mk(vec[m * 9 + a * 3], vec[m * 9 + a * 3 + 1], vec[m * 9 + a * 3 + 2]);
-        for (int b = 0; b < 3; ++b) {
-            if (b == a) continue;
-            const V3<double> x = X[a] - X[b];
-            double g[6];
-            g_erf_d(sqrt(dot(x, x)), al, g);
-            Mp<double> s{};
-            s.mu = mk(vec[m * 9 + b * 3], vec[m * 9 + b * 3 + 1], vec[m * 9 + b * 3 + 2]);
-            FieldTerms<double> f;
-            source_field<double, 1>(s, x, g, f);
-            E = E + f.d1;
-        }
-        addv(out + m * 9 + a * 3, E, 1.0);
-    }
-}
-
-template <typename R>
-void launch_intra_tmu(const KParams &p, DevState<R> &d, const double *vec, double *out, Launch L) {
-    k_intra_tmu<R><<<(p.M + 127) / 128, 128, 0, L.s>>>(p, d, vec, out);
-    count(L);
-}
-
-// Force pass, intramolecular corrections (periodic) at fixed mu and lambda.
-template <typename R>
-__global__ void k_intra_polforce(KParams p, DevState<R> d) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= p.M) return;
-    V3<double> X[NP];
-    points_d(p, d, m, X);
-    Mp<double> M[NS];
-    for (int s = 0; s < NS; ++s) M[s] = mp_d(d, m, s);
-    V3<double> mu[3];
-    for (int a = 0; a < 3; ++a) mu[a] = mk(d.mu[m * 9 + a * 3], d.mu[m * 9 + a * 3 + 1], d.mu[m * 9 + a * 3 + 2]);
-    const double ke = p.ke, al = p.alpha;
-    // induced dipole a with permanent site s != a
-    for (int a = 0; a < 3; ++a)
-        for (int s = 0; s < NS; ++s) {
-            if (s == a) continue;
-            const V3<double> x = X[a] - X[s];
-            double g[6];
-            g_erf_d(sqrt(dot(x, x)), al, g);
-            FieldTerms<double> f;
-            source_field<double, 2>(M[s], x, g, f);
-            const V3<double> ga = symv(f.d2, mu[a]);
-            addv(d.gpt + (m * NP + a) * 3, ga, -ke);
-            addv(d.gpt + (m * NP + s) * 3, ga, ke);
-            Mp<double> dip{};
-            dip.mu = mu[a];
-            FieldTerms<double> f2;
-            source_field<double, 2>(dip, -x, g, f2);
-            addv(d.gmu + (m * NS + s) * 3, f2.d1, -ke);
-            adds(d.gth + (m * NS + s) * 6, f2.d2, -ke / 3.0);
-        }
-    // induced-induced
-    for (int a = 0; a < 3; ++a)
-        for (int b = a + 1; b < 3; ++b) {
-            const V3<double> x = X[a] - X[b];
-            double g[6];
-            g_erf_d(sqrt(dot(x, x)), al, g);
-            Mp<double> dip{};
-            dip.mu = mu[b];
-            FieldTerms<double> f;
-            source_field<double, 2>(dip, x, g, f);
-            const V3<double> ga = symv(f.d2, mu[a]);
-            addv(d.gpt + (m * NP + a) * 3, ga, -ke);
-            addv(d.gpt + (m * NP + b) * 3, ga, ke);
-        }
-    // self cross term  -ke (4 a^3 / 3 sqrt(pi)) mu_ind . mu_perm : sensitivity of the permanent dipole
-    const double cself = 4.0 * al * al * al / (3.0 * sqrt(M_PI));
-    for (int a = 0; a < 3; ++a) addv(d.gmu + (m * NS + a) * 3, mu[a], -ke * cself);
-    // lambda charges on the lone pairs with the own molecule's sites
-    for (int l = 0; l < 2; ++l) {
-        const double lq = d.lam[m * 2 + l];
-        if (lq == 0.0) continue;
-        for (int s = 0; s < NS; ++s) {
-            const V3<double> x = X[s] - X[5 + l];
-            double g[6];
-            g_erf_d(sqrt(dot(x, x)), al, g);
-            Mp<double> c{};
-            c.q = lq;
-            FieldTerms<double> f;
-            source_field<double, 3>(c, x, g, f);
-            const V3<double> gs = target_grad(M[s], c, x, g, f);
-            addv(d.gpt + (m * NP + s) * 3, gs, -ke);
-            addv(d.gmu + (m * NS + s) * 3, f.d1, -ke);
-            adds(d.gth + (m * NS + s) * 6, f.d2, -ke / 3.0);
-        }
-    }
-}
-
-template <typename R>
-void launch_intra_polforce(const KParams &p, DevState<R> &d, Launch L) {
-    k_intra_polforce<R><<<(p.M + 127) / 128, 128, 0, L.s>>>(p, d);
-    count(L);
-}
-
-// ---------------------------------------------------------------------------
 // Chain rule to atom forces.  Frame construction: z along zv, x in the
 // (z, xv) plane, y = z x x; its vector-Jacobian product maps gradients of the
 // axes back to zv and xv.
@@ -666,9 +426,6 @@ void launch_md_kick(int M, double *pos, double *vel, const double *inv_mass, con
     template void launch_pcg_iter_a<R>(const KParams &, DevState<R> &, Launch);                        \
     template void launch_pcg_iter_b<R>(const KParams &, DevState<R> &, double, Launch);                \
     template void launch_pol_energy<R>(const KParams &, DevState<R> &, Launch);                        \
-    template void launch_intra_perm<R>(const KParams &, DevState<R> &, Launch);                        \
-    template void launch_intra_tmu<R>(const KParams &, DevState<R> &, const double *, double *, Launch); \
-    template void launch_intra_polforce<R>(const KParams &, DevState<R> &, Launch);                    \
     template void launch_finalize<R>(const KParams &, DevState<R> &, double *, Launch);
 INST(float)
 INST(double)

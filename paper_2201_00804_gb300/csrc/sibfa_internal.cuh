@@ -29,6 +29,7 @@ struct KParams {
     int M;
     int periodic;
     double box[3];
+    double ibox[3];        // 1 / box
     double rc, rc2;
     double alpha;          // Ewald
     int K[3];
@@ -451,9 +452,9 @@ __device__ inline void min_image(const KParams &p, const double *pos, int i, int
     dy = pos[j * 9 + 1] - pos[i * 9 + 1];
     dz = pos[j * 9 + 2] - pos[i * 9 + 2];
     if (p.periodic) {
-        dx -= p.box[0] * rint(dx / p.box[0]);
-        dy -= p.box[1] * rint(dy / p.box[1]);
-        dz -= p.box[2] * rint(dz / p.box[2]);
+        dx -= p.box[0] * rint(dx * p.ibox[0]);
+        dy -= p.box[1] * rint(dy * p.ibox[1]);
+        dz -= p.box[2] * rint(dz * p.ibox[2]);
     }
 }
 
@@ -473,6 +474,62 @@ __device__ inline Mp<R> load_mp(const R *g) {
     m.mu = mk(g[1], g[2], g[3]);
     m.th = Sym<R>{g[4], g[5], g[6], g[7], g[8], g[9]};
     return m;
+}
+
+// ---------------------------------------------------------------------------
+// Intramolecular geometry in FP64 (shared by the intramolecular and chain-rule kernels)
+// ---------------------------------------------------------------------------
+__device__ inline void frame_d2(V3<double> zv, V3<double> xv, V3<double> &ex, V3<double> &ey, V3<double> &ez) {
+    ez = (1.0 / sqrt(dot(zv, zv))) * zv;
+    V3<double> xp = xv - dot(xv, ez) * ez;
+    ex = (1.0 / sqrt(dot(xp, xp))) * xp;
+    ey = cross(ez, ex);
+}
+
+// absolute FP64 positions of the 7 points of molecule m
+template <typename R>
+__device__ inline void points_d(const KParams &p, const DevState<R> &d, int m, V3<double> *X) {
+    const double *x = d.pos + m * 9;
+    const V3<double> O = mk(x[0], x[1], x[2]), H1 = mk(x[3], x[4], x[5]), H2 = mk(x[6], x[7], x[8]);
+    const V3<double> r1 = H1 - O, r2 = H2 - O;
+    const V3<double> u1 = (1.0 / sqrt(dot(r1, r1))) * r1, u2 = (1.0 / sqrt(dot(r2, r2))) * r2;
+    V3<double> ex, ey, ez;
+    frame_d2(u1 + u2, r1, ex, ey, ez);
+    X[0] = O;
+    X[1] = H1;
+    X[2] = H2;
+    X[3] = 0.5 * (O + H1);
+    X[4] = 0.5 * (O + H2);
+    X[5] = O + p.d_lp * ((-p.lp_cos) * ez + p.lp_sin * ey);
+    X[6] = O + p.d_lp * ((-p.lp_cos) * ez - p.lp_sin * ey);
+}
+
+template <typename R>
+__device__ inline Mp<double> mp_d(const DevState<R> &d, int m, int s) {
+    const R *g = d.gmp + (m * NS + s) * NMP;
+    Mp<double> o;
+    o.q = g[0];
+    o.mu = mk((double)g[1], (double)g[2], (double)g[3]);
+    o.th = Sym<double>{g[4], g[5], g[6], g[7], g[8], g[9]};
+    return o;
+}
+
+// erf(alpha r)/r weights g_0..g_5 (1/r minus the Ewald real-space kernel)
+__device__ inline void g_erf_d(double r, double alpha, double *g) {
+    double gb[6], ge[6];
+    g_bare<double, 5>(1.0 / r, gb);
+    g_erfc<double, 5>(r, 1.0 / r, alpha, ge);
+    for (int n = 0; n < 6; ++n) g[n] = gb[n] - ge[n];
+}
+
+__device__ inline void addv(double *dst, V3<double> v, double s) {
+    dst[0] += s * v.x;
+    dst[1] += s * v.y;
+    dst[2] += s * v.z;
+}
+__device__ inline void adds(double *dst, const Sym<double> &v, double s) {
+    dst[0] += s * v.xx; dst[1] += s * v.yy; dst[2] += s * v.zz;
+    dst[3] += s * v.xy; dst[4] += s * v.xz; dst[5] += s * v.yz;
 }
 
 // ---------------------------------------------------------------------------
