@@ -41,12 +41,17 @@ FP32_LANES_PER_SM = 128
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 
-# Algorithmic FP32 operations per unit of the real-space permanent kernel
-# (counted from the formulas).
-FLOPS_PERM_SITE_PAIR = 380      # multipole-multipole pair: erfc kernel g0..g5, field to d2, energy, gradient with d3
-FLOPS_PEN_PAIR = 190            # penetration of a pair with at least one atom site
-FLOPS_THOLE_PAIR = 130          # Thole-damped field of a site at a polarizable atom
-FLOPS_LP_PAIR = 110             # potential and gradient of a site at a lone pair
+# Algorithmic FP32 operations per unit of the real-space permanent kernel,
+# counted by hand from its formulas (fused multiply-add = 2, each
+# transcendental or reciprocal square root = 1).
+FLOPS_PERM_SITE_PAIR = 364      # multipole pair: erfc kernel g0..g5, field to d2, energy, gradient with d3, sensitivities
+FLOPS_PEN_ATOM_ATOM = 236       # penetration, both sites atoms (charge-charge*, both dipole/quadrupole* sides)
+FLOPS_PEN_ATOM_MID = 129        # penetration, atom target and midpoint source
+FLOPS_PEN_MID_ATOM = 156        # penetration, midpoint target and atom source (incl. sensitivity terms)
+FLOPS_THOLE_PAIR = 119          # Thole-damped field of a site at a polarizable atom
+FLOPS_LP_PAIR = 101             # potential and gradient of a site at a lone pair
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_real_perm_traffic.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2201_00804_gb300", "csrc", f) for f in ("k_pair.cu", "sibfa_internal.cuh")]
 
 
 def parse():
@@ -114,16 +119,20 @@ class Clocks:
 
 
 def count_units(pos, box, rc, mp_points):
-    """Pairs evaluated by the real-space permanent kernel: (site, site),
-    (atom, site) and (lone pair, site) intermolecular pairs within rc, and the
-    number of those that carry a penetration correction."""
+    """Pairs evaluated by the real-space permanent kernel: intermolecular
+    (site, site) pairs within rc split by which side carries a valence
+    (penetration), (polarizable atom, site) pairs and (lone pair, site)
+    pairs within rc."""
     M = pos.shape[0]
     sites = mp_points[:, :5]
     lps = mp_points[:, 5:7]
     O = pos[:, 0]
-    n_ss = n_pen = n_th = n_lp = 0
+    n = dict(site_pairs=0, pen_atom_atom=0, pen_atom_mid=0, pen_mid_atom=0, thole_pairs=0, lp_pairs=0)
     L = np.asarray(box)
-    is_atom = np.array([1, 1, 1, 0, 0], bool)
+    atom = np.array([1, 1, 1, 0, 0], bool)
+    aa = atom[:, None, None] & atom[None, None, :]
+    am = atom[:, None, None] & ~atom[None, None, :]
+    ma = ~atom[:, None, None] & atom[None, None, :]
     for i0 in range(0, M, 128):
         i1 = min(M, i0 + 128)
         d = O[None, :, :] - O[i0:i1, None, :]
@@ -137,13 +146,38 @@ def count_units(pos, box, rc, mp_points):
             sj = sites[js] + sh                                   # (n,5,3)
             r = np.linalg.norm(sites[i][:, None, None, :] - sj[None], axis=-1)   # (5,n,5)
             inr = r < rc
-            n_ss += int(inr.sum())
-            pen = (is_atom[:, None, None] | is_atom[None, None, :])
-            n_pen += int((inr & pen).sum())
-            n_th += int(inr[:3].sum())
+            n["site_pairs"] += int(inr.sum())
+            n["pen_atom_atom"] += int((inr & aa).sum())
+            n["pen_atom_mid"] += int((inr & am).sum())
+            n["pen_mid_atom"] += int((inr & ma).sum())
+            n["thole_pairs"] += int(inr[:3].sum())
             rl = np.linalg.norm(lps[i][:, None, None, :] - sj[None], axis=-1)
-            n_lp += int((rl < rc).sum())
-    return n_ss, n_pen, n_th, n_lp
+            n["lp_pairs"] += int((rl < rc).sum())
+    return n
+
+
+def unit_flops(n):
+    return (n["site_pairs"] * FLOPS_PERM_SITE_PAIR + n["pen_atom_atom"] * FLOPS_PEN_ATOM_ATOM
+            + n["pen_atom_mid"] * FLOPS_PEN_ATOM_MID + n["pen_mid_atom"] * FLOPS_PEN_MID_ATOM
+            + n["thole_pairs"] * FLOPS_THOLE_PAIR + n["lp_pairs"] * FLOPS_LP_PAIR)
+
+
+def measured_traffic():
+    """DRAM bytes per launch of k_real_perm from the committed ncu summary,
+    or None when the kernel source changed after those counters were taken."""
+    import hashlib
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    if rec.get("source_sha256") != h.hexdigest():
+        return None
+    return rec.get("dram_bytes_per_launch_scaled", rec.get("dram_bytes_per_launch"))
 
 
 def points_from_pos(pos, P):
@@ -298,16 +332,14 @@ def main():
     P = synth.PARAMS
     pos_h = pos.cpu().numpy().reshape(M, 3, 3)
     pts = points_from_pos(pos_h, P)
-    n_ss, n_pen, n_th, n_lp = count_units(pos_h, s.box, o["rc"], pts)
-    flops = (n_ss * FLOPS_PERM_SITE_PAIR + n_pen * FLOPS_PEN_PAIR + n_th * FLOPS_THOLE_PAIR
-             + n_lp * FLOPS_LP_PAIR)
+    units = count_units(pos_h, s.box, o["rc"], pts)
+    flops = unit_flops(units)
     rp_ms = phases["real_perm"]["ms_per_step"]
     achieved = flops / (rp_ms * 1e-3) / 1e12
     peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "kernel": "k_real_perm", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "units": {"site_pairs": n_ss, "penetration_pairs": n_pen, "thole_pairs": n_th, "lp_pairs": n_lp},
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived, not measured)"}
+                "frac": achieved / peak, "traffic": measured_traffic(), "flops_per_launch": flops, "units": units,
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived from unit counts and max clock)"}
 
     # End to end through the C ABI with host buffers: a second context
     # evaluates, from host memory, the positions of the trajectory that the

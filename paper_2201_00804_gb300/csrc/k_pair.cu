@@ -13,49 +13,6 @@ namespace sibfa {
 
 constexpr int TILE = 32;
 
-// shared tile of neighbour molecules
-template <typename R>
-struct Tile {
-    int j[TILE];
-    R dO[TILE][3];             // O_j - O_i (minimum image)
-    R off[TILE][NP * 3];       // point offsets of j
-    R mp[TILE][NS * NMP];      // global multipoles of j
-};
-
-template <typename R>
-__device__ inline void load_tile(const KParams &p, const DevState<R> &d, int i, int base, int nn, Tile<R> &t,
-                                 bool want_mp) {
-    for (int k = threadIdx.x; k < TILE; k += blockDim.x) {
-        int slot = base + k;
-        int j = slot < nn ? d.nbr[i * MAXN + slot] : -1;
-        t.j[k] = j;
-        if (j >= 0) {
-            const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
-                const double dx = dp_[0], dy = dp_[1], dz = dp_[2];
-            t.dO[k][0] = R(dx);
-            t.dO[k][1] = R(dy);
-            t.dO[k][2] = R(dz);
-        }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < TILE * NP * 3; k += blockDim.x) {
-        int a = k / (NP * 3), b = k % (NP * 3);
-        int j = t.j[a];
-        t.off[a][b] = j >= 0 ? d.off[j * NP * 3 + b] : R(0);
-    }
-    if (want_mp)
-        for (int k = threadIdx.x; k < TILE * NS * NMP; k += blockDim.x) {
-            int a = k / (NS * NMP), b = k % (NS * NMP);
-            int j = t.j[a];
-            t.mp[a][b] = j >= 0 ? d.gmp[j * NS * NMP + b] : R(0);
-        }
-}
-
-template <typename R>
-__device__ inline V3<R> tile_pt(const Tile<R> &t, int k, int pt) {
-    return mk(t.dO[k][0] + t.off[k][pt * 3], t.dO[k][1] + t.off[k][pt * 3 + 1], t.dO[k][2] + t.off[k][pt * 3 + 2]);
-}
-
 template <typename R>
 __device__ inline V3<R> my_pt(const DevState<R> &d, int i, int pt) {
     const R *o = d.off + (i * NP + pt) * 3;
