@@ -116,7 +116,11 @@ typedef struct sibfa_ctx sibfa_ctx;
 
 /* Create a context: validates sizes, copies the topology, builds the SPME
  * influence function and FFT plans, allocates all device state.  *out is
- * NULL on failure. */
+ * NULL on failure.  The PCG loop normally runs on the device as a CUDA graph
+ * with a conditional while-node; with the environment variable
+ * SIBFA_PCG_HOST_LOOP=1 at creation it is driven from the host instead (one
+ * launch per kernel and iteration, same arithmetic), which kernel profilers
+ * can follow. */
 sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo,
                           const sibfa_run_opts *opts, sibfa_ctx **out);
 

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <cstdlib>
+
 #include "sibfa_internal.cuh"
 
 using namespace sibfa;
@@ -176,6 +178,18 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     return SIBFA_OK;
 }
 
+template <typename R>
+void fill_scal(Scal<R> &s, const KParams &k) {
+    s.rc2 = R(k.rc2); s.alpha = R(k.alpha); s.thole = R(k.thole);
+    s.cs_o = R(k.cs_o); s.cp_o = R(k.cp_o); s.cs_h = R(k.cs_h); s.cp_h = R(k.cp_h);
+    s.cs_lp = R(k.cs_lp); s.cp_lp = R(k.cp_lp); s.g_o = R(k.g_o); s.g_h = R(k.g_h);
+    s.inv_nval_o = R(1.0 / k.nval_o); s.inv_nval_h = R(1.0 / k.nval_h);
+    s.rep_f = R(k.rep_f); s.rep_c1 = R(k.rep_c1); s.rep_c2 = R(k.rep_c2); s.occ = R(k.occ); s.nlp = R(k.nlp);
+    s.c6 = R(k.c6); s.c8 = R(k.c8); s.c10 = R(k.c10); s.g6 = R(k.g6); s.g8 = R(k.g8); s.g10 = R(k.g10);
+    s.delta = R(k.delta); s.xd_c1 = R(k.xd_c1); s.xd_c2 = R(k.xd_c2); s.xd_c3 = R(k.xd_c3);
+    s.ct_t = R(k.ct_t); s.ct_m = R(k.ct_m); s.ct_ae = R(k.ct_ae); s.ct_ah = R(k.ct_ah);
+}
+
 void fill_params(KParams &k, const sibfa_params &P, const sibfa_run_opts &o, int M) {
     k.M = M;
     k.periodic = o.periodic;
@@ -242,6 +256,8 @@ void fill_params(KParams &k, const sibfa_params &P, const sibfa_run_opts &o, int
     k.ct_k1 = coef(P.ct_eta / (2.0 * sqrt(P.rvdw_ct_o * P.rvdw_ct_o)));
     k.ct_k2 = coef(P.ct_eta / (2.0 * sqrt(P.rvdw_ct_o * P.rvdw_ct_h)));
     for (int s = 0; s < 5; ++s) k.pen_b[s] = coef(k.b[s]);
+    fill_scal(k.sd, k);
+    fill_scal(k.sf, k);
     for (int s = 0; s < 5; ++s) {
         k.zf[s] = (float)k.z[s];
         k.betaf[s] = (float)k.beta[s];
@@ -672,6 +688,10 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
         return SIBFA_E_CUDA;
     }
     fill_params(ctx->kp, *params, *opts, ctx->M);
+    {
+        const char *e = getenv("SIBFA_PCG_HOST_LOOP");
+        if (e && e[0] == '1') ctx->pcg_graph_state = -1;
+    }
     if (opts->periodic) {
         const double cell = opts->rc + 2.6;   // rc + 2 * maximum site extent (1.3 A)
         for (int k = 0; k < 3; ++k) ctx->ncell[k] = (int)floor(opts->box[k] / cell);

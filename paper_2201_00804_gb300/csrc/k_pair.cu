@@ -19,24 +19,6 @@ __device__ inline V3<R> my_pt(const DevState<R> &d, int i, int pt) {
     return mk(o[0], o[1], o[2]);
 }
 
-__device__ inline void add3(double *g, double s, double a, double b, double c) {
-    g[0] += s * a;
-    g[1] += s * b;
-    g[2] += s * c;
-}
-
-template <typename R>
-__device__ inline void wsum3(V3<R> v, double *dst, double scale, int lane) {
-    double a = warp_sum(double(v.x)), b = warp_sum(double(v.y)), c = warp_sum(double(v.z));
-    if (lane == 0) add3(dst, scale, a, b, c);
-}
-template <typename R>
-__device__ inline void wsum6(const Sym<R> &v, double *dst, double scale, int lane) {
-    double a[6] = {warp_sum(double(v.xx)), warp_sum(double(v.yy)), warp_sum(double(v.zz)),
-                   warp_sum(double(v.xy)), warp_sum(double(v.xz)), warp_sum(double(v.yz))};
-    if (lane == 0)
-        for (int k = 0; k < 6; ++k) dst[k] += scale * a[k];
-}
 template <typename R>
 __device__ inline void symadd(Sym<R> &a, const Sym<R> &b, R s) {
     a.xx += s * b.xx; a.yy += s * b.yy; a.zz += s * b.zz;
@@ -44,125 +26,230 @@ __device__ inline void symadd(Sym<R> &a, const Sym<R> &b, R s) {
 }
 
 // ---------------------------------------------------------------------------
+// Work queues.  A warp walks its molecule's neighbour list 32 entries at a
+// time, tests each (neighbour, source site) pair against the cutoff and
+// appends the pairs inside it to a per-warp ring queue in shared memory
+// (source position relative to O_i, neighbour index and site).  Pairs are
+// evaluated in rounds of 32 only while the queue holds a full round, so
+// lanes stay busy whatever the cutoff rejects; the tail is flushed at the
+// end.  Atom and midpoint sources go to separate queues because only atom
+// sources carry a valence (penetration), which keeps every round uniform.
+// ---------------------------------------------------------------------------
+constexpr int QCAP_A = 128;   // >= 31 carried + 3 atom sites x 32 new entries
+constexpr int QCAP_M = 96;    // >= 31 carried + 2 midpoints x 32 new entries
+
+template <typename R>
+struct PairQueue {
+    int js[QCAP_A + QCAP_M];   // j * 8 + s
+    R rx[QCAP_A + QCAP_M], ry[QCAP_A + QCAP_M], rz[QCAP_A + QCAP_M];
+};
+
+__device__ inline int warp_excl_scan(int c, int lane, int &total) {
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    total = __shfl_sync(0xffffffffu, incl, 31);
+    return incl - c;
+}
+
+// ---------------------------------------------------------------------------
 // Permanent electrostatics + penetration (Eq. 2), Thole-damped permanent
 // field on the polarizable atoms, potential on the lone pairs.
 // Warps 0..4: target site w of molecule i.  Warps 5, 6: target lone pair.
 // ---------------------------------------------------------------------------
+template <typename R>
+struct PermAcc {
+    Acc<R> Ue, Up, Vl;
+    V3<R> gr, gm, ef;
+    Sym<R> gt;
+};
+
+template <typename R, bool PER, bool ATOM_SRC>
+__device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d, int w, bool is_lp, V3<R> ot,
+                                          const Mp<R> &mt, R Nt_, int js, V3<R> rs, PermAcc<R> &A) {
+    const Scal<R> &S = sc<R>(p);
+    const R third = R(1) / R(3);
+    const int j = js >> 3, s = js & 7;
+    const V3<R> x = ot - rs;
+    const R r2 = dot(x, x);
+    const R rinv = rsqrt_(r2);
+    const R r = r2 * rinv;
+    const Mp<R> ms = load_mp_g(d.gmp + (j * NS + s) * NMP);
+    R g[6];
+    if (PER) g_erfc<R, 5>(r, rinv, S.alpha, g);
+    else g_bare<R, 5>(rinv, g);
+    if (is_lp) {
+        FieldTerms<R> f;
+        source_field<R, 1>(ms, x, g, f);
+        A.Vl.add(f.phi);
+        A.gr = A.gr + f.d1;
+        return;
+    }
+    FieldTerms<R> f;
+    source_field<R, 3>(ms, x, g, f);
+    const R U = mt.q * f.phi + dot(mt.mu, f.d1) + third * symdd(mt.th, f.d2);
+    A.Ue.add(R(0.5) * U);
+    A.gr = A.gr + target_grad(mt, ms, x, g, f);
+    A.gm = A.gm + f.d1;
+    symadd(A.gt, f.d2, third);
+    // ---- penetration: charge-charge*, charge-dipole*, charge-quadrupole*
+    // Kernels exp(-b r)/r of the source (es) and target (et) valence; the
+    // product kernel exp(-(b_s + b_t) r)/r of the N_t N_s term is es0 et0 r.
+    if (ATOM_SRC || Nt_ != R(0)) {
+        R pen = R(0), gq = R(0);
+        R et[4];
+        const R xt_b = mulc(r, p.pen_b[w]);   // b_t r
+        if (Nt_ != R(0)) {
+            g_exp_x<R, 3>(xt_b, rinv, et);
+            const R c2 = ms.q * Nt_;            // q_s N_t exp(-b_t r)/r
+            pen += c2 * et[0];
+            gq += c2 * et[1];
+        }
+        if (ATOM_SRC) {
+            const R Ns = zsite<R>(p, s) - ms.q;
+            const R xs_b = mulc(r, p.pen_b[s]);   // b_s r
+            R es[4];
+            g_exp_x<R, 3>(xs_b, rinv, es);
+            const R c1 = mt.q * Ns;                // q_t N_s exp(-b_s r)/r
+            pen += c1 * es[0];
+            gq += c1 * es[1];
+            if (Nt_ != R(0)) {                     // N_t N_s exp(-(b_t + b_s) r)/r
+                const R c3 = Nt_ * Ns;
+                const R ec = es[0] * et[0] * r;
+                pen += c3 * ec;
+                gq -= c3 * (xt_b + xs_b + R(1)) * ec * (rinv * rinv);
+            }
+            // valence of s in the dipole/quadrupole potential of t
+            Mp<R> m0 = mt;
+            m0.q = R(0);
+            const V3<R> xs = -x;
+            FieldTerms<R> f3;
+            source_field<R, 1>(m0, xs, es, f3);
+            pen += Ns * f3.phi;
+            A.gr = A.gr - Ns * f3.d1;
+            A.gm = A.gm + (-Ns * es[1]) * xs;
+            const R c = Ns * third * es[2];
+            A.gt.xx += c * xs.x * xs.x; A.gt.yy += c * xs.y * xs.y; A.gt.zz += c * xs.z * xs.z;
+            A.gt.xy += c * xs.x * xs.y; A.gt.xz += c * xs.x * xs.z; A.gt.yz += c * xs.y * xs.z;
+        }
+        A.gr = A.gr + gq * x;
+        if (Nt_ != R(0)) {   // valence of t in the dipole/quadrupole potential of s
+            Mp<R> m0 = ms;
+            m0.q = R(0);
+            FieldTerms<R> f2;
+            source_field<R, 1>(m0, x, et, f2);
+            pen += Nt_ * f2.phi;
+            A.gr = A.gr + Nt_ * f2.d1;
+        }
+        A.Up.add(R(0.5) * pen);
+    }
+    // ---- Thole-damped permanent field on the polarizable atom (same base kernel g)
+    if (w < 3) {
+        R gtol[4];
+        g_thole_on<R, 3>(r, rinv, ainv3<R>(p, w, s), S.thole, PER, g, gtol);
+        FieldTerms<R> f4;
+        source_field<R, 1>(ms, x, gtol, f4);
+        A.ef = A.ef - f4.d1;
+    }
+}
+
 template <typename R, bool PER>
 __global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) {
     __shared__ double s_e[7][2];
+    __shared__ PairQueue<R> qs[7];
+    static_assert(sizeof(PairQueue<R>) >= 15 * 33 * sizeof(R), "reduction buffer aliases the queue");
     const int i = blockIdx.x;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool is_lp = w >= NS;
+    PairQueue<R> &q = qs[w];
     const V3<R> ot = my_pt(d, i, w);
     Mp<R> mt{};
     if (!is_lp) mt = load_mp(d.gmp + (i * NS + w) * NMP);
     const R Nt = (!is_lp) ? zsite<R>(p, w) - mt.q * R(w < 3) : R(0);
     const R Nt_ = (w < 3) ? Nt : R(0);
-    const R rc2 = R(p.rc2), alpha = R(p.alpha), thole = R(p.thole);
-    const R third = R(1) / R(3);
+    const R rc2 = sc<R>(p).rc2;
 
-    Acc<R> Ue, Up, Vl;
-    V3<R> gr = mk(R(0), R(0), R(0)), gm = gr, ef = gr;
-    Sym<R> gt{};
+    PermAcc<R> A;
+    A.gr = mk(R(0), R(0), R(0));
+    A.gm = A.gr;
+    A.ef = A.gr;
+    A.gt = Sym<R>{};
+    int ha = 0, ta = 0, hm = 0, tm = 0;   // queue heads and tails (warp-uniform, monotone)
     const int nn = d.nnbr[i];
-    for (int slot = lane; slot < nn; slot += 32) {
-        const int j = d.nbr[i * MAXN + slot];
-        const R *dp = d.ndo + ((size_t)i * MAXN + slot) * 3;
-        const V3<R> dO = mk(dp[0], dp[1], dp[2]);
-        const R *offj = d.off + j * NP * 3;
-        const R *mpj = d.gmp + j * NS * NMP;
-#pragma unroll 1
-        for (int s = 0; s < NS; ++s) {
-            const V3<R> rs = dO + mk(__ldg(offj + s * 3), __ldg(offj + s * 3 + 1), __ldg(offj + s * 3 + 2));
-            const V3<R> x = ot - rs;
-            const R r2 = dot(x, x);
-            if (PER && r2 >= rc2) continue;
-            const R rinv = rsqrt_(r2);
-            const R r = r2 * rinv;
-            const Mp<R> ms = load_mp_g(mpj + s * NMP);
-            R g[6];
-            if (PER) g_erfc<R, 5>(r, rinv, alpha, g);
-            else g_bare<R, 5>(rinv, g);
-            if (is_lp) {
-                FieldTerms<R> f;
-                source_field<R, 1>(ms, x, g, f);
-                Vl.add(f.phi);
-                gr = gr + f.d1;
-                continue;
-            }
-            FieldTerms<R> f;
-            source_field<R, 3>(ms, x, g, f);
-            const R U = mt.q * f.phi + dot(mt.mu, f.d1) + third * symdd(mt.th, f.d2);
-            Ue.add(R(0.5) * U);
-            gr = gr + target_grad(mt, ms, x, g, f);
-            gm = gm + f.d1;
-            symadd(gt, f.d2, third);
-            // ---- penetration: charge-charge*, charge-dipole*, charge-quadrupole*
-            const R Ns = (s < 3) ? zsite<R>(p, s) - ms.q : R(0);
-            if (Nt_ != R(0) || Ns != R(0)) {
-                const R xs_b = mulc(r, p.pen_b[s]);          // b_s r
-                const R xt_b = is_lp ? R(0) : mulc(r, p.pen_b[w]);   // b_t r
-                R pen = R(0);
-                // q*_t q*_s - q_t q_s, with q* = q + N exp(-b r)
-                {
-                    R g1a[2], g1b[2], g1c[2];
-                    g_exp_x<R, 1>(xs_b, rinv, g1a);
-                    g_exp_x<R, 1>(xt_b, rinv, g1b);
-                    g_exp_x<R, 1>(xt_b + xs_b, rinv, g1c);
-                    const R c1 = mt.q * Ns, c2 = ms.q * Nt_, c3 = Nt_ * Ns;
-                    pen += c1 * g1a[0] + c2 * g1b[0] + c3 * g1c[0];
-                    gr = gr + (c1 * g1a[1] + c2 * g1b[1] + c3 * g1c[1]) * x;
-                }
-                if (Nt_ != R(0)) {   // valence of t in the dipole/quadrupole potential of s
-                    R ge[4];
-                    g_exp_x<R, 3>(xt_b, rinv, ge);
-                    Mp<R> m0 = ms;
-                    m0.q = R(0);
-                    FieldTerms<R> f2;
-                    source_field<R, 1>(m0, x, ge, f2);
-                    pen += Nt_ * f2.phi;
-                    gr = gr + Nt_ * f2.d1;
-                }
-                if (Ns != R(0)) {    // valence of s in the dipole/quadrupole potential of t
-                    R ge[4];
-                    g_exp_x<R, 3>(xs_b, rinv, ge);
-                    Mp<R> m0 = mt;
-                    m0.q = R(0);
-                    const V3<R> xs = -x;
-                    FieldTerms<R> f3;
-                    source_field<R, 1>(m0, xs, ge, f3);
-                    pen += Ns * f3.phi;
-                    gr = gr - Ns * f3.d1;
-                    gm = gm + (-Ns * ge[1]) * xs;
-                    const R c = Ns * third * ge[2];
-                    gt.xx += c * xs.x * xs.x; gt.yy += c * xs.y * xs.y; gt.zz += c * xs.z * xs.z;
-                    gt.xy += c * xs.x * xs.y; gt.xz += c * xs.x * xs.z; gt.yz += c * xs.y * xs.z;
-                }
-                Up.add(R(0.5) * pen);
-            }
-            // ---- Thole-damped permanent field on the polarizable atom
-            if (w < 3) {
-                R gtol[4];
-                g_thole<R, 3>(r, rinv, ainv3<R>(p, w, s), thole, PER, alpha, gtol);
-                FieldTerms<R> f4;
-                source_field<R, 1>(ms, x, gtol, f4);
-                ef = ef - f4.d1;
+    for (int base = 0;; base += 32) {
+        const bool flush = base >= nn;   // list exhausted: evaluate what is left in the queues
+        const int slot = base + lane;
+        unsigned bits = 0;
+        int j = 0;
+        V3<R> rs[NS];
+        if (slot < nn) {
+            j = d.nbr[i * MAXN + slot];
+            const R *dp = d.ndo + ((size_t)i * MAXN + slot) * 3;
+            const V3<R> dO = mk(dp[0], dp[1], dp[2]);
+            const R *offj = d.off + j * NP * 3;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                rs[s] = dO + mk(__ldg(offj + s * 3), __ldg(offj + s * 3 + 1), __ldg(offj + s * 3 + 2));
+                const V3<R> x = ot - rs[s];
+                if (!PER || dot(x, x) < rc2) bits |= 1u << s;
             }
         }
+        int na, nm;
+        int pa = warp_excl_scan(__popc(bits & 7u), lane, na);
+        int pm = warp_excl_scan(__popc(bits >> 3), lane, nm);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            if (!((bits >> s) & 1u)) continue;
+            int e;
+            if (s < 3) e = (ta + pa++) % QCAP_A;
+            else e = QCAP_A + (tm + pm++) % QCAP_M;
+            q.js[e] = j * 8 + s;
+            q.rx[e] = rs[s].x;
+            q.ry[e] = rs[s].y;
+            q.rz[e] = rs[s].z;
+        }
+        ta += na;
+        tm += nm;
+        __syncwarp();
+        while (ta - ha >= 32 || (flush && ta > ha)) {
+            if (lane < ta - ha) {
+                const int e = (ha + lane) % QCAP_A;
+                perm_pair<R, PER, true>(p, d, w, is_lp, ot, mt, Nt_, q.js[e], mk(q.rx[e], q.ry[e], q.rz[e]), A);
+            }
+            ha += min(32, ta - ha);
+        }
+        while (tm - hm >= 32 || (flush && tm > hm)) {
+            if (lane < tm - hm) {
+                const int e = QCAP_A + (hm + lane) % QCAP_M;
+                perm_pair<R, PER, false>(p, d, w, is_lp, ot, mt, Nt_, q.js[e], mk(q.rx[e], q.ry[e], q.rz[e]), A);
+            }
+            hm += min(32, tm - hm);
+        }
+        __syncwarp();
+        if (flush) break;
     }
+
     const double ke = p.ke;
+    R *buf = reinterpret_cast<R *>(&q);
     if (is_lp) {
         const int l = w - NS;
-        double v = warp_sum(Vl.get());
+        const double v = warp_sum_acc(A.Vl);
+        const R vals[3] = {A.gr.x, A.gr.y, A.gr.z};
+        const R t = warp_transpose_sum<R, 3>(vals, buf, lane);
+        if (lane < 3) d.dvlp[(i * 2 + l) * 3 + lane] += ke * double(t);
         if (lane == 0) d.vlp[i * 2 + l] += ke * v;
-        wsum3(gr, d.dvlp + (i * 2 + l) * 3, ke, lane);
     } else {
-        wsum3(gr, d.gpt + (i * NP + w) * 3, ke, lane);
-        wsum3(gm, d.gmu + (i * NS + w) * 3, ke, lane);
-        wsum6(gt, d.gth + (i * NS + w) * 6, ke, lane);
-        if (w < 3) wsum3(ef, d.efield + i * 9 + w * 3, 1.0, lane);
-        double e0 = warp_sum(Ue.get()), e1 = warp_sum(Up.get());
+        const R vals[15] = {A.gr.x, A.gr.y, A.gr.z, A.gm.x, A.gm.y, A.gm.z, A.gt.xx, A.gt.yy, A.gt.zz,
+                            A.gt.xy, A.gt.xz, A.gt.yz, A.ef.x, A.ef.y, A.ef.z};
+        const R t = warp_transpose_sum<R, 15>(vals, buf, lane);
+        if (lane < 3) d.gpt[(i * NP + w) * 3 + lane] += ke * double(t);
+        else if (lane < 6) d.gmu[(i * NS + w) * 3 + lane - 3] += ke * double(t);
+        else if (lane < 12) d.gth[(i * NS + w) * 6 + lane - 6] += ke * double(t);
+        else if (lane < 15 && w < 3) d.efield[i * 9 + w * 3 + lane - 12] += double(t);
+        const double e0 = warp_sum_acc(A.Ue), e1 = warp_sum_acc(A.Up);
         if (lane == 0) {
             s_e[w][0] = e0;
             s_e[w][1] = e1;
@@ -254,18 +341,20 @@ __device__ inline R rep_energy(R pref, R C1, R C2, R O1, R O2, R r, R &e1, R &e2
 
 template <typename R, bool PER>
 __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
+    __shared__ R red[4][15 * 33];
     const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= p.M) return;
-    const R rc2 = R(p.rc2);
+    const Scal<R> &S = sc<R>(p);
+    const R rc2 = S.rc2;
     V3<R> P[5];
     for (int k = 0; k < 3; ++k) P[k] = my_pt(d, i, k);
     P[3] = my_pt(d, i, 5);
     P[4] = my_pt(d, i, 6);
     const R qi[3] = {d.gmp[(i * NS + 0) * NMP], d.gmp[(i * NS + 1) * NMP], d.gmp[(i * NS + 2) * NMP]};
-    const R f = R(p.rep_f), a1 = R(p.rep_a1), a2 = R(p.rep_a2), C1 = R(p.rep_c1), C2 = R(p.rep_c2);
-    const R occ = R(p.occ), nlp = R(p.nlp);
-    const R cf_lp = R(1) - nlp / R(p.nval_o);
+    const R f = S.rep_f, C1 = S.rep_c1, C2 = S.rep_c2;
+    const R occ = S.occ, nlp = S.nlp;
+    const R cf_lp = R(1) - nlp * S.inv_nval_o;
     V3<R> G[5];
     for (int k = 0; k < 5; ++k) G[k] = mk(R(0), R(0), R(0));
     Acc<R> Erep, Ed, Ex;
@@ -273,8 +362,7 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
     for (int slot = lane; slot < nn; slot += 32) {
         const int j = d.nbr[i * MAXN + slot];
         const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
-                const double dx = dp_[0], dy = dp_[1], dz = dp_[2];
-        const V3<R> dO = mk(R(dx), R(dy), R(dz));
+        const V3<R> dO = mk(dp_[0], dp_[1], dp_[2]);
         V3<R> Q[5];
         Q[0] = dO;
         Q[1] = dO + my_pt(d, j, 1);
@@ -283,13 +371,13 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
         Q[4] = dO + my_pt(d, j, 6);
         const R qj[3] = {d.gmp[(j * NS + 0) * NMP], d.gmp[(j * NS + 1) * NMP], d.gmp[(j * NS + 2) * NMP]};
         RepAtom<R> Ai[3], Aj[3];
-        Ai[0] = {R(p.cs_o), R(p.cp_o), R(p.g_o), R(1) - qi[0] / R(p.nval_o), 0};
-        Aj[0] = {R(p.cs_o), R(p.cp_o), R(p.g_o), R(1) - qj[0] / R(p.nval_o), 0};
+        Ai[0] = {S.cs_o, S.cp_o, S.g_o, R(1) - qi[0] * S.inv_nval_o, 0};
+        Aj[0] = {S.cs_o, S.cp_o, S.g_o, R(1) - qj[0] * S.inv_nval_o, 0};
         for (int k = 1; k < 3; ++k) {
-            Ai[k] = {R(p.cs_h), R(p.cp_h), R(p.g_h), R(1) - qi[k] / R(p.nval_h), 1};
-            Aj[k] = {R(p.cs_h), R(p.cp_h), R(p.g_h), R(1) - qj[k] / R(p.nval_h), 1};
+            Ai[k] = {S.cs_h, S.cp_h, S.g_h, R(1) - qi[k] * S.inv_nval_h, 1};
+            Aj[k] = {S.cs_h, S.cp_h, S.g_h, R(1) - qj[k] * S.inv_nval_h, 1};
         }
-        const RepAtom<R> Alp = {R(p.cs_lp), R(p.cp_lp), R(p.g_o), cf_lp, 2};
+        const RepAtom<R> Alp = {S.cs_lp, S.cp_lp, S.g_o, cf_lp, 2};
         // ---- bond-bond
         for (int kb = 1; kb <= 2; ++kb)
             for (int kc = 1; kc <= 2; ++kc) {
@@ -377,14 +465,14 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
                 V3<R> dui, dvi, duj, dvj;
                 const R ci = cosv(I - P[0], J - P[0], dui, dvi);    // depends on I and A
                 const R cj = cosv(J - Q[0], I - Q[0], duj, dvj);    // depends on I
-                const R cs = R(p.cs_lp), cp = R(p.cp_lp);
+                const R cs = S.cs_lp, cp = S.cp_lp;
                 const R O = cs * cs + cs * cp * f * cj + cs * cp * f * ci + R(2) * cp * cp * ci * cj;
                 const R dci = cs * cp * f + R(2) * cp * cp * cj, dcj = cs * cp * f + R(2) * cp * cp * ci;
                 const V3<R> dOdI = dci * dui + dcj * dvj;
                 const V3<R> dOdA = R(-1) * dci * (dui + dvi);
                 const V3<R> dAB = P[0] - Q[0];
                 const R rab = sqrt_(dot(dAB, dAB));
-                const R M = R(p.g_o) * cf_lp;
+                const R M = S.g_o * cf_lp;
                 const R S1 = M * exp_(-mulc(rab, p.rep_k1[2][2])), S2 = M * exp_(-mulc(rab, p.rep_k2[2][2]));
                 const R O1 = O * S1, O2 = O * S2;
                 R e1, e2, er;
@@ -395,10 +483,10 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
                 G[3 + l1] = G[3 + l1] + (e1 * S1 + e2 * S2) * dOdI + (er / rr) * dIJ;
             }
         // ---- dispersion and exchange-dispersion over atoms and lone pairs
-        const R cfi[5] = {R(1) - qi[0] / R(p.nval_o), R(1) - qi[1] / R(p.nval_h), R(1) - qi[2] / R(p.nval_h),
-                          R(1) - qi[0] / R(p.nval_o), R(1) - qi[0] / R(p.nval_o)};
-        const R cfj[5] = {R(1) - qj[0] / R(p.nval_o), R(1) - qj[1] / R(p.nval_h), R(1) - qj[2] / R(p.nval_h),
-                          R(1) - qj[0] / R(p.nval_o), R(1) - qj[0] / R(p.nval_o)};
+        const R cfi[5] = {R(1) - qi[0] * S.inv_nval_o, R(1) - qi[1] * S.inv_nval_h, R(1) - qi[2] * S.inv_nval_h,
+                          R(1) - qi[0] * S.inv_nval_o, R(1) - qi[0] * S.inv_nval_o};
+        const R cfj[5] = {R(1) - qj[0] * S.inv_nval_o, R(1) - qj[1] * S.inv_nval_h, R(1) - qj[2] * S.inv_nval_h,
+                          R(1) - qj[0] * S.inv_nval_o, R(1) - qj[0] * S.inv_nval_o};
         const int kind_of[5] = {0, 1, 1, 2, 2};
         for (int u = 0; u < 5; ++u)
             for (int v = 0; v < 5; ++v) {
@@ -412,29 +500,33 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
                 const R a6 = mulc(ri, p.disp_gS[0][ku][kv]), a8 = mulc(ri, p.disp_gS[1][ku][kv]),
                         a10 = mulc(ri, p.disp_gS[2][ku][kv]);
                 const R m2i = mi * mi, m6i = m2i * m2i * m2i, m8i = m6i * m2i, m10i = m8i * m2i;
-                const R e6 = R(p.c6) * exp_(R(p.g6) - a6) * m6i;
-                const R e8 = R(p.c8) * exp_(R(p.g8) - a8) * m8i;
-                const R e10 = R(p.c10) * exp_(R(p.g10) - a10) * m10i;
+                const R e6 = S.c6 * exp_(S.g6 - a6) * m6i;
+                const R e8 = S.c8 * exp_(S.g8 - a8) * m8i;
+                const R e10 = S.c10 * exp_(S.g10 - a10) * m10i;
                 const R fsum = e6 + e8 + e10;
                 const R dfdr = e6 * ((a6 - R(6)) * ri) + e8 * ((a8 - R(8)) * ri) + e10 * ((a10 - R(10)) * ri);
                 const bool lu = u >= 3, lv = v >= 3;
-                R pref, xc, xa;
-                if (!lu && !lv) { pref = -betap<R>(p, u) * betap<R>(p, v); xc = R(p.xd_c1); xa = R(p.xd_a1); }
-                else if (lu && lv) { pref = -nlp * nlp * R(0.25); xc = nlp * nlp * R(0.25) * R(p.xd_c2); xa = R(p.xd_a2); }
-                else { pref = -R(p.delta) * R(0.5); xc = nlp * R(0.5) * R(p.xd_c3); xa = R(p.xd_a3); }
+                R pref, xc;
+                if (!lu && !lv) { pref = -betap<R>(p, u) * betap<R>(p, v); xc = S.xd_c1; }
+                else if (lu && lv) { pref = -nlp * nlp * R(0.25); xc = nlp * nlp * R(0.25) * S.xd_c2; }
+                else { pref = -S.delta * R(0.5); xc = nlp * R(0.5) * S.xd_c3; }
                 const R K = betap<R>(p, u) * betap<R>(p, v) * cfi[u] * cfj[v];
                 const R ex = xc * K * exp_(-mulc(r, p.xd_k[ku][kv]));
                 Ed.add(R(0.5) * pref * fsum);
                 Ex.add(R(0.5) * ex);
                 const R dEdr = pref * dfdr - cval<R>(p.xd_k[ku][kv]) * ex;
-                (void)xa;
                 G[u] = G[u] + (dEdr * ri) * dv;
             }
     }
     // lane reduction; points 3, 4 are the lone pairs (point slots 5, 6)
-    const int slot_of[5] = {0, 1, 2, 5, 6};
-    for (int k = 0; k < 5; ++k) wsum3(G[k], d.gpt + (i * NP + slot_of[k]) * 3, 1.0, lane);
-    double er_ = warp_sum(Erep.get()), ed_ = warp_sum(Ed.get()), ex_ = warp_sum(Ex.get());
+    {
+        const R vals[15] = {G[0].x, G[0].y, G[0].z, G[1].x, G[1].y, G[1].z, G[2].x, G[2].y, G[2].z,
+                            G[3].x, G[3].y, G[3].z, G[4].x, G[4].y, G[4].z};
+        const R t = warp_transpose_sum<R, 15>(vals, red[threadIdx.x >> 5], lane);
+        const int pt = lane / 3;
+        if (lane < 15) d.gpt[(i * NP + (pt < 3 ? pt : pt + 2)) * 3 + lane % 3] += double(t);
+    }
+    const double er_ = warp_sum_acc(Erep), ed_ = warp_sum_acc(Ed), ex_ = warp_sum_acc(Ex);
     if (lane == 0) {
         d.epart[i * NTERM + T_REP] += er_;
         d.epart[i * NTERM + T_DISP] += ed_;
@@ -463,7 +555,8 @@ template <typename R>
 __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1, V3<R> a2, R V, R Vi1, R Vi2,
                                    int *flags) {
     CtOut<R> o;
-    const R eta = R(p.ct_eta), cs = R(p.cs_lp), cp = R(p.cp_lp), t = R(p.ct_t), mm = R(p.ct_m), n = R(p.nlp);
+    const Scal<R> &S = sc<R>(p);
+    const R cs = S.cs_lp, cp = S.cp_lp, t = S.ct_t, mm = S.ct_m, n = S.nlp;
     const V3<R> v1 = a1 - c, v2 = a2 - c, u = lp - c;
     const R r1 = sqrt_(dot(v1, v1)), r2 = sqrt_(dot(v2, v2));
     V3<R> du1, dv1, du2, dv2;
@@ -474,7 +567,7 @@ __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1
     const R K1 = cs * t + cp * mm * ca, K2 = cs * t + cp * mm * cb;
     const R e1 = E1 * (Vi1 - V) * K1, e2 = E2 * (Vi2 - V) * K2;
     const R D = e1 - e2;
-    const R dE = R(p.ct_ae) + V - R(p.ct_ah);
+    const R dE = S.ct_ae + V - S.ct_ah;
     if (!(dE > R(0))) atomicOr(flags, F_CTDEN);
     const R idE = R(1) / dE;
     o.E = -n * D * D * idE;
@@ -483,7 +576,6 @@ __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1
     o.dVi1 = gD * E1 * K1;
     o.dVi2 = -gD * E2 * K2;
     const R dr1 = gD * (-ek1 * e1), dr2 = gD * (ek2 * e2);
-    (void)eta;
     const R dca = gD * E1 * (Vi1 - V) * cp * mm, dcb = -gD * E2 * (Vi2 - V) * cp * mm;
     const V3<R> n1 = (R(1) / r1) * v1, n2 = (R(1) / r2) * v2;
     o.glp = dca * du1 + dcb * du2;
@@ -495,10 +587,11 @@ __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1
 
 template <typename R, bool PER>
 __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
+    __shared__ R red[4][20 * 33];
     const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= p.M) return;
-    const R rc2 = R(p.rc2);
+    const R rc2 = sc<R>(p).rc2;
     V3<R> P[5];
     for (int k = 0; k < 3; ++k) P[k] = my_pt(d, i, k);
     P[3] = my_pt(d, i, 5);
@@ -513,8 +606,7 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
     for (int slot = lane; slot < nn; slot += 32) {
         const int j = d.nbr[i * MAXN + slot];
         const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
-                const double dx = dp_[0], dy = dp_[1], dz = dp_[2];
-        const V3<R> dO = mk(R(dx), R(dy), R(dz));
+        const V3<R> dO = mk(dp_[0], dp_[1], dp_[2]);
         if (PER && dot(dO, dO) >= rc2) continue;
         V3<R> Q[5];
         Q[0] = dO;
@@ -541,19 +633,15 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
                 kap[k] += q.dVi2;
             }
     }
-    const int slot_of[5] = {0, 1, 2, 5, 6};
-    for (int k = 0; k < 5; ++k) wsum3(G[k], d.gpt + (i * NP + slot_of[k]) * 3, 1.0, lane);
-    double e = warp_sum(Ect.get());
-    double l0 = warp_sum(double(lam[0])), l1 = warp_sum(double(lam[1]));
-    double k0 = warp_sum(double(kap[0])), k1 = warp_sum(double(kap[1])), k2 = warp_sum(double(kap[2]));
-    if (lane == 0) {
-        d.epart[i * NTERM + T_CT] += e;
-        d.lam[i * 2] += l0;
-        d.lam[i * 2 + 1] += l1;
-        d.kap[i * 3] += k0;
-        d.kap[i * 3 + 1] += k1;
-        d.kap[i * 3 + 2] += k2;
-    }
+    const R vals[20] = {G[0].x, G[0].y, G[0].z, G[1].x, G[1].y, G[1].z, G[2].x, G[2].y, G[2].z,
+                        G[3].x, G[3].y, G[3].z, G[4].x, G[4].y, G[4].z, lam[0], lam[1], kap[0], kap[1], kap[2]};
+    const R t = warp_transpose_sum<R, 20>(vals, red[threadIdx.x >> 5], lane);
+    const int pt = lane / 3;
+    if (lane < 15) d.gpt[(i * NP + (pt < 3 ? pt : pt + 2)) * 3 + lane % 3] += double(t);
+    else if (lane < 17) d.lam[i * 2 + lane - 15] += double(t);
+    else if (lane < 20) d.kap[i * 3 + lane - 17] += double(t);
+    const double e = warp_sum_acc(Ect);
+    if (lane == 0) d.epart[i * NTERM + T_CT] += e;
 }
 
 template <typename R>
@@ -580,10 +668,12 @@ template <typename R, bool PER>
 __global__ void __launch_bounds__(96) k_real_tmu(KParams p, DevState<R> d, const double *vec, double *out) {
     if (d.scal[7] != 0.0) return;   // solver already converged
     __shared__ DipTile<R> t;
+    __shared__ R red[3][3 * 33];
     const int i = blockIdx.x;
     const int a = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const V3<R> xa = my_pt(d, i, a);
-    const R rc2 = R(p.rc2), alpha = R(p.alpha), thole = R(p.thole);
+    const Scal<R> &S = sc<R>(p);
+    const R rc2 = S.rc2, alpha = S.alpha, thole = S.thole;
     V3<R> ef = mk(R(0), R(0), R(0));
     const int nn = d.nnbr[i];
     for (int base = 0; base < nn; base += TILE) {
@@ -594,8 +684,7 @@ __global__ void __launch_bounds__(96) k_real_tmu(KParams p, DevState<R> d, const
             t.j[k] = j;
             if (j >= 0) {
                 const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
-                const double dx = dp_[0], dy = dp_[1], dz = dp_[2];
-                t.dO[k][0] = R(dx); t.dO[k][1] = R(dy); t.dO[k][2] = R(dz);
+                t.dO[k][0] = dp_[0]; t.dO[k][1] = dp_[1]; t.dO[k][2] = dp_[2];
             }
         }
         __syncthreads();
@@ -623,7 +712,9 @@ __global__ void __launch_bounds__(96) k_real_tmu(KParams p, DevState<R> d, const
             ef = ef + (g[2] * s) * x + g[1] * mu;
         }
     }
-    wsum3(ef, out + i * 9 + a * 3, 1.0, lane);
+    const R vals[3] = {ef.x, ef.y, ef.z};
+    const R s = warp_transpose_sum<R, 3>(vals, red[a], lane);
+    if (lane < 3) out[i * 9 + a * 3 + lane] += double(s);
 }
 
 template <typename R>
@@ -654,13 +745,15 @@ struct PfTile {
 template <typename R, bool PER>
 __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d) {
     __shared__ PfTile<R> t;
+    __shared__ R red[5][12 * 33];
     const int i = blockIdx.x;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const Scal<R> &S = sc<R>(p);
     const V3<R> ot = my_pt(d, i, w);
     const Mp<R> mt = load_mp(d.gmp + (i * NS + w) * NMP);
     V3<R> mui = mk(R(0), R(0), R(0));
     if (w < 3) mui = mk(R(d.mu[i * 9 + w * 3]), R(d.mu[i * 9 + w * 3 + 1]), R(d.mu[i * 9 + w * 3 + 2]));
-    const R rc2 = R(p.rc2), alpha = R(p.alpha), thole = R(p.thole), third = R(1) / R(3);
+    const R rc2 = S.rc2, alpha = S.alpha, thole = S.thole, third = R(1) / R(3);
     V3<R> gr = mk(R(0), R(0), R(0)), gm = gr;
     Sym<R> gt{};
     const int nn = d.nnbr[i];
@@ -672,8 +765,7 @@ __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d)
             t.j[k] = j;
             if (j >= 0) {
                 const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
-                const double dx = dp_[0], dy = dp_[1], dz = dp_[2];
-                t.dO[k][0] = R(dx); t.dO[k][1] = R(dy); t.dO[k][2] = R(dz);
+                t.dO[k][0] = dp_[0]; t.dO[k][1] = dp_[1]; t.dO[k][2] = dp_[2];
             }
         }
         __syncthreads();
@@ -757,9 +849,11 @@ __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d)
         }
     }
     const double ke = p.ke;
-    wsum3(gr, d.gpt + (i * NP + w) * 3, ke, lane);
-    wsum3(gm, d.gmu + (i * NS + w) * 3, ke, lane);
-    wsum6(gt, d.gth + (i * NS + w) * 6, ke, lane);
+    const R vals[12] = {gr.x, gr.y, gr.z, gm.x, gm.y, gm.z, gt.xx, gt.yy, gt.zz, gt.xy, gt.xz, gt.yz};
+    const R s = warp_transpose_sum<R, 12>(vals, red[w], lane);
+    if (lane < 3) d.gpt[(i * NP + w) * 3 + lane] += ke * double(s);
+    else if (lane < 6) d.gmu[(i * NS + w) * 3 + lane - 3] += ke * double(s);
+    else if (lane < 12) d.gth[(i * NS + w) * 6 + lane - 6] += ke * double(s);
 }
 
 template <typename R>

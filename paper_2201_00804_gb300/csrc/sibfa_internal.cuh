@@ -22,8 +22,19 @@ constexpr int ORDER = 5;       // B-spline order of the SPME
 // error flags (bitwise, device side)
 enum { F_CUTOFF = 1, F_NEIGHBOR = 2, F_CTDEN = 4, F_NAN = 8 };
 
+// Scalars read inside pair loops, rounded once per precision on the host so
+// that the FP32 kernels do no FP64 conversion in their loops.
+template <typename R>
+struct Scal {
+    R rc2, alpha, thole;
+    R cs_o, cp_o, cs_h, cp_h, cs_lp, cp_lp, g_o, g_h, inv_nval_o, inv_nval_h;
+    R rep_f, rep_c1, rep_c2, occ, nlp;
+    R c6, c8, c10, g6, g8, g10, delta, xd_c1, xd_c2, xd_c3;
+    R ct_t, ct_m, ct_ae, ct_ah;
+};
+
 // ---------------------------------------------------------------------------
-// Kernel parameters (by value).  Double values are converted to R at use.
+// Kernel parameters (by value).
 // ---------------------------------------------------------------------------
 struct KParams {
     int M;
@@ -68,7 +79,16 @@ struct KParams {
     float ainv3f[5][5];                  // Thole 1 / sqrt(alpha_s alpha_t) over the site damping polarizabilities
     double ainv3[5][5];
     float betaf[5];                      // dispersion beta per point (O, H, H, LP, LP)
+    Scal<float> sf;
+    Scal<double> sd;
 };
+
+template <typename R>
+__device__ inline const Scal<R> &sc(const KParams &p);
+template <>
+__device__ inline const Scal<float> &sc<float>(const KParams &p) { return p.sf; }
+template <>
+__device__ inline const Scal<double> &sc<double>(const KParams &p) { return p.sd; }
 
 template <typename R>
 __device__ inline R zsite(const KParams &p, int s);
@@ -280,13 +300,54 @@ __device__ inline void g_exp(R r, R rinv, R bb, R *g) {
     }
 }
 
+// erf(alpha r)/r and its radial derivatives g_0..g_N (intramolecular Ewald
+// exclusions), free of the cancellation in 1/r - erfc(alpha r)/r at small r.
+// With y = (alpha r)^2 and B_n = (-1)^n g_n, term-wise differentiation of the
+// Maclaurin series of erf gives
+//   B_N = (2 alpha / sqrt(pi)) (2 alpha^2)^N sum_j (-y)^j / (j! (2j + 2N + 1)),
+// and the erf form of the Ewald recursion runs downward without loss:
+//   B_{n-1} = (r^2 B_n + (2 alpha^2)^n e^{-y} / (alpha sqrt(pi))) / (2n - 1).
+// For y > 2 (no cancellation left) the difference of the two kernels is used.
+template <typename R, int N>
+__device__ inline void g_erf_s(R r2, R alpha, R *g) {
+    const R a2 = alpha * alpha, y = a2 * r2;
+    if (y > R(2)) {
+        const R rinv = rsqrt_(r2);
+        R gb[N + 1];
+        g_bare<R, N>(rinv, gb);
+        g_erfc<R, N>(r2 * rinv, rinv, alpha, g);
+#pragma unroll
+        for (int n = 0; n <= N; ++n) g[n] = gb[n] - g[n];
+        return;
+    }
+    R term = R(1), s = R(1) / R(2 * N + 1);
+#pragma unroll
+    for (int j = 1; j <= 22; ++j) {
+        term *= -y * R(1.0 / j);
+        s += term * R(1.0 / (2 * j + 2 * N + 1));
+    }
+    const R tw = R(2) * a2, itw = R(1) / tw;
+    R pw = R(1);
+#pragma unroll
+    for (int n = 0; n < N; ++n) pw *= tw;
+    R B = R(1.12837916709551257390) * alpha * pw * s;                   // 2 alpha / sqrt(pi)
+    const R ex = exp_(-y) * (R(0.56418958354775628695) / alpha);        // e^{-y} / (alpha sqrt(pi))
+    g[N] = (N & 1) ? -B : B;
+#pragma unroll
+    for (int n = N; n >= 1; --n) {
+        B = (r2 * B + pw * ex) * R(1.0 / (2 * n - 1));
+        pw *= itw;
+        g[n - 1] = ((n - 1) & 1) ? -B : B;
+    }
+}
+
 // Exponential Thole factors on top of a bare or Ewald kernel for n = 1..N.
 // gas:      g_n = lambda_{2n+1} g_n(1/r)
 // periodic: g_n = g_n(erfc) + (lambda_{2n+1} - 1) g_n(1/r)
+// gbase holds the base kernel already evaluated at r (erfc in periodic
+// systems, bare in the gas phase).
 template <typename R, int N>
-__device__ inline void g_thole(R r, R rinv, R Ainv3, R a, bool periodic, R alpha, R *g) {
-    R gb[N + 1];
-    g_bare<R, N>(rinv, gb);
+__device__ inline void g_thole_on(R r, R rinv, R Ainv3, R a, bool periodic, const R *gbase, R *g) {
     const R t = a * r * r * r * Ainv3;
     const R e = exp_(-t);
     R lam[4];
@@ -296,14 +357,22 @@ __device__ inline void g_thole(R r, R rinv, R Ainv3, R a, bool periodic, R alpha
     lam[3] = R(1) - (R(1) + t + R(18.0 / 35.0) * t * t + R(9.0 / 35.0) * t * t * t) * e;
     g[0] = R(0);
     if (periodic) {
-        R ge[N + 1];
-        g_erfc<R, N>(r, rinv, alpha, ge);
+        R gb[N + 1];
+        g_bare<R, N>(rinv, gb);
 #pragma unroll
-        for (int n = 1; n <= N; ++n) g[n] = ge[n] + (lam[n - 1] - R(1)) * gb[n];
+        for (int n = 1; n <= N; ++n) g[n] = gbase[n] + (lam[n - 1] - R(1)) * gb[n];
     } else {
 #pragma unroll
-        for (int n = 1; n <= N; ++n) g[n] = lam[n - 1] * gb[n];
+        for (int n = 1; n <= N; ++n) g[n] = lam[n - 1] * gbase[n];
     }
+}
+
+template <typename R, int N>
+__device__ inline void g_thole(R r, R rinv, R Ainv3, R a, bool periodic, R alpha, R *g) {
+    R gbase[N + 1];
+    if (periodic) g_erfc<R, N>(r, rinv, alpha, gbase);
+    else g_bare<R, N>(rinv, gbase);
+    g_thole_on<R, N>(r, rinv, Ainv3, a, periodic, gbase, g);
 }
 
 // ---------------------------------------------------------------------------
@@ -431,6 +500,29 @@ __device__ inline double warp_sum(double v) {
     return v;
 }
 
+// Sums NV per-lane values over the warp, transposed: on return lane k < NV
+// holds the sum of value k over the 32 lanes (other lanes hold 0).  The
+// values pass through buf (NV * 33 elements of this warp's shared memory,
+// padded so that both the writes and the column sums are conflict-free);
+// the caller then needs one FP64 operation per value instead of a shuffle
+// tree per value.
+template <typename R, int NV>
+__device__ inline R warp_transpose_sum(const R (&v)[NV], R *buf, int lane) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) buf[k * 33 + lane] = v[k];
+    __syncwarp();
+    R s0 = R(0), s1 = R(0);
+    if (lane < NV) {
+#pragma unroll 8
+        for (int j = 0; j < 32; j += 2) {
+            s0 += buf[lane * 33 + j];
+            s1 += buf[lane * 33 + j + 1];
+        }
+    }
+    __syncwarp();
+    return s0 + s1;
+}
+
 // Compensated (two-sum) accumulator used for per-lane energy partial sums.
 template <typename R>
 struct Acc {
@@ -444,6 +536,22 @@ struct Acc {
     }
     __device__ inline double get() const { return double(hi) + double(lo); }
 };
+
+// Warp sum of compensated partials.  FP32: a two-sum butterfly on (hi, lo)
+// pairs, so the only FP64 work is the final conversion; FP64: plain tree.
+__device__ inline double warp_sum_acc(const Acc<float> &a) {
+    float hi = a.hi, lo = a.lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float s = hi + h2, bp = s - hi;
+        const float err = (hi - (s - bp)) + (h2 - bp);
+        hi = s;
+        lo = lo + l2 + err;
+    }
+    return double(hi) + double(lo);
+}
+__device__ inline double warp_sum_acc(const Acc<double> &a) { return warp_sum(a.get()); }
 
 // Minimum-image displacement of molecule j's O from molecule i's O (FP64).
 __device__ inline void min_image(const KParams &p, const double *pos, int i, int j, double &dx, double &dy,

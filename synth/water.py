@@ -5,10 +5,12 @@ rigid waters (O-H 0.9572 A, HOH 104.52 deg) with uniform random orientations
 on a jittered cubic lattice (minimum O-O 2.5 A), or compact gas-phase
 clusters.  Each molecule draws its own local-frame multipoles: q_O uniform in
 [-0.85, -0.75], the four other sites (H1, H2 and the two O-H bond midpoints)
-carry -q_O/4 so the molecule is neutral, every site gets a dipole of random
-direction with |mu| uniform in [0, 0.3] e.A and a traceless quadrupole whose
-symmetric entries start uniform in [-0.5, 0.5] e.A^2 before the trace is
-removed.
+carry -q_O/4 so the molecule is neutral; in each site's local frame the
+dipole lies along z (O: uniform in [0, 0.3] e.A; H: [0, 0.1]; midpoints:
+[-0.1, 0.1]) and the quadrupole is diagonal and traceless (diagonal entries
+uniform in [-0.5, 0.5] e.A^2 on O, [-0.1, 0.1] on H, [-0.2, 0.2] on the
+midpoints, then the mean removed).  This mimics the axial layout of
+ISA-derived water multipoles.
 
 Site order inside a molecule: 0 = O, 1 = H1, 2 = H2, 3 = M1 (midpoint O-H1),
 4 = M2 (midpoint O-H2).  Lone pairs: 0, 1.  Local multipole layout per site:
