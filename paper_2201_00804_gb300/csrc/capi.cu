@@ -155,6 +155,14 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.pv, M * 9);
     AL(d.ap, M * 9);
     AL(d.efp, M * 9);
+    AL(d.vecR, M * 9);
+    AL(d.tl_n, M * 3);
+    AL(d.tl_j, (size_t)M * 3 * TLS);
+    AL(d.tl_x, (size_t)M * 3 * TLS);
+    AL(d.tl_y, (size_t)M * 3 * TLS);
+    AL(d.tl_z, (size_t)M * 3 * TLS);
+    AL(d.tl_g1, (size_t)M * 3 * TLS);
+    AL(d.tl_g2, (size_t)M * 3 * TLS);
     AL(d.partial, 2 * ((M * 9 + 255) / 256) + 64);
     AL(d.scal, 32);
     AL(d.counter, 4);
@@ -316,7 +324,7 @@ sibfa_status fft(sibfa_ctx *ctx, DevState<R> &d, bool forward, int ngrid) {
 template <typename R>
 sibfa_status matvec(sibfa_ctx *ctx, DevState<R> &d, const double *vec, Launch L) {
     const KParams &p = ctx->kp;
-    { Phase ph(ctx, "real_tmu");  launch_real_tmu(p, d, vec, d.efp, L); }
+    { Phase ph(ctx, "real_tmu");  launch_tmu_list(p, d, d.efp, L); }
     if (p.periodic) {
         const size_t ng = (size_t)p.K[0] * p.K[1] * p.K[2];
         CK(cudaMemsetAsync(d.grid, 0, ng * sizeof(R), ctx->s));

@@ -38,10 +38,17 @@ __device__ inline void symadd(Sym<R> &a, const Sym<R> &b, R s) {
 constexpr int QCAP_A = 128;   // >= 31 carried + 3 atom sites x 32 new entries
 constexpr int QCAP_M = 96;    // >= 31 carried + 2 midpoints x 32 new entries
 
-template <typename R>
+template <typename R, int CAP = QCAP_A + QCAP_M>
 struct PairQueue {
-    int js[QCAP_A + QCAP_M];   // j * 8 + s
-    R rx[QCAP_A + QCAP_M], ry[QCAP_A + QCAP_M], rz[QCAP_A + QCAP_M];
+    int js[CAP];   // j * 8 + s
+    R rx[CAP], ry[CAP], rz[CAP];
+    __device__ inline void put(int e, int j, int s, V3<R> r) {
+        js[e] = j * 8 + s;
+        rx[e] = r.x;
+        ry[e] = r.y;
+        rz[e] = r.z;
+    }
+    __device__ inline V3<R> at(int e) const { return mk(rx[e], ry[e], rz[e]); }
 };
 
 __device__ inline int warp_excl_scan(int c, int lane, int &total) {
@@ -69,7 +76,7 @@ struct PermAcc {
 
 template <typename R, bool PER, bool ATOM_SRC>
 __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d, int w, bool is_lp, V3<R> ot,
-                                          const Mp<R> &mt, R Nt_, int js, V3<R> rs, PermAcc<R> &A) {
+                                          const Mp<R> &mt, R Nt_, int js, V3<R> rs, size_t te, PermAcc<R> &A) {
     const Scal<R> &S = sc<R>(p);
     const R third = R(1) / R(3);
     const int j = js >> 3, s = js & 7;
@@ -153,6 +160,14 @@ __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d
         FieldTerms<R> f4;
         source_field<R, 1>(ms, x, gtol, f4);
         A.ef = A.ef - f4.d1;
+        if (ATOM_SRC) {   // the same atom pair in the polarization matrix T
+            d.tl_j[te] = j * 3 + s;
+            d.tl_x[te] = x.x;
+            d.tl_y[te] = x.y;
+            d.tl_z[te] = x.z;
+            d.tl_g1[te] = gtol[1];
+            d.tl_g2[te] = gtol[2];
+        }
     }
 }
 
@@ -171,6 +186,7 @@ __global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) 
     const R Nt = (!is_lp) ? zsite<R>(p, w) - mt.q * R(w < 3) : R(0);
     const R Nt_ = (w < 3) ? Nt : R(0);
     const R rc2 = sc<R>(p).rc2;
+    const size_t tbase = (size_t)(i * 3 + (w < 3 ? w : 0)) * TLS;
 
     PermAcc<R> A;
     A.gr = mk(R(0), R(0), R(0));
@@ -217,14 +233,14 @@ __global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) 
         while (ta - ha >= 32 || (flush && ta > ha)) {
             if (lane < ta - ha) {
                 const int e = (ha + lane) % QCAP_A;
-                perm_pair<R, PER, true>(p, d, w, is_lp, ot, mt, Nt_, q.js[e], mk(q.rx[e], q.ry[e], q.rz[e]), A);
+                perm_pair<R, PER, true>(p, d, w, is_lp, ot, mt, Nt_, q.js[e], q.at(e), tbase + ha + lane, A);
             }
             ha += min(32, ta - ha);
         }
         while (tm - hm >= 32 || (flush && tm > hm)) {
             if (lane < tm - hm) {
                 const int e = QCAP_A + (hm + lane) % QCAP_M;
-                perm_pair<R, PER, false>(p, d, w, is_lp, ot, mt, Nt_, q.js[e], mk(q.rx[e], q.ry[e], q.rz[e]), A);
+                perm_pair<R, PER, false>(p, d, w, is_lp, ot, mt, Nt_, q.js[e], q.at(e), 0, A);
             }
             hm += min(32, tm - hm);
         }
@@ -232,6 +248,7 @@ __global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) 
         if (flush) break;
     }
 
+    if (w < 3 && lane == 0) d.tl_n[i * 3 + w] = ta;
     const double ke = p.ke;
     R *buf = reinterpret_cast<R *>(&q);
     if (is_lp) {
@@ -652,75 +669,36 @@ void launch_ct(const KParams &p, DevState<R> &d, Launch L) {
 }
 
 // ---------------------------------------------------------------------------
-// Polarization matrix-vector product, real-space part: field at the three
-// polarizable atoms of i from the dipoles `vec` of the other molecules
-// (Thole-damped, Ewald-screened in periodic systems).  out += field.
+// Polarization matrix-vector product, real-space part: field at each
+// polarizable atom from the dipoles vecR of the atoms of other molecules
+// within rc (Thole-damped, Ewald-screened in periodic systems), streamed
+// from the pair list that the permanent pass recorded.  out += field.
+// One warp per polarizable atom.
 // ---------------------------------------------------------------------------
 template <typename R>
-struct DipTile {
-    int j[TILE];
-    R dO[TILE][3];
-    R off[TILE][9];
-    R v[TILE][9];
-};
-
-template <typename R, bool PER>
-__global__ void __launch_bounds__(96) k_real_tmu(KParams p, DevState<R> d, const double *vec, double *out) {
+__global__ void __launch_bounds__(128) k_tmu_list(int M, DevState<R> d, double *out) {
+    __shared__ R red[4][3 * 33];
     if (d.scal[7] != 0.0) return;   // solver already converged
-    __shared__ DipTile<R> t;
-    __shared__ R red[3][3 * 33];
-    const int i = blockIdx.x;
-    const int a = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const V3<R> xa = my_pt(d, i, a);
-    const Scal<R> &S = sc<R>(p);
-    const R rc2 = S.rc2, alpha = S.alpha, thole = S.thole;
+    const int t = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (t >= M * 3) return;
+    const int n = d.tl_n[t];
+    const size_t base = (size_t)t * TLS;
     V3<R> ef = mk(R(0), R(0), R(0));
-    const int nn = d.nnbr[i];
-    for (int base = 0; base < nn; base += TILE) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < TILE; k += blockDim.x) {
-            int slot = base + k;
-            int j = slot < nn ? d.nbr[i * MAXN + slot] : -1;
-            t.j[k] = j;
-            if (j >= 0) {
-                const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
-                t.dO[k][0] = dp_[0]; t.dO[k][1] = dp_[1]; t.dO[k][2] = dp_[2];
-            }
-        }
-        __syncthreads();
-        for (int k = threadIdx.x; k < TILE * 9; k += blockDim.x) {
-            int s = k / 9, c = k % 9;
-            int j = t.j[s];
-            t.off[s][c] = j >= 0 ? d.off[j * NP * 3 + c] : R(0);
-            t.v[s][c] = j >= 0 ? R(vec[j * 9 + c]) : R(0);
-        }
-        __syncthreads();
-        const int k = lane;
-        if (base + k >= nn) continue;
-        const V3<R> dO = mk(t.dO[k][0], t.dO[k][1], t.dO[k][2]);
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            const V3<R> x = xa - (dO + mk(t.off[k][b * 3], t.off[k][b * 3 + 1], t.off[k][b * 3 + 2]));
-            const R r2 = dot(x, x);
-            if (PER && r2 >= rc2) continue;
-            const R rinv = rsqrt_(r2), r = r2 * rinv;
-            R g[4];
-            g_thole<R, 2>(r, rinv, ainv3<R>(p, a, b), thole, PER, alpha, g);
-            const V3<R> mu = mk(t.v[k][b * 3], t.v[k][b * 3 + 1], t.v[k][b * 3 + 2]);
-            // field of a point dipole: E = g2 (mu.x) x + g1 mu ... d1 = -(g2 (mu.x) x + g1 mu)
-            const R s = dot(mu, x);
-            ef = ef + (g[2] * s) * x + g[1] * mu;
-        }
+    for (int e = lane; e < n; e += 32) {
+        const size_t k = base + e;
+        const R *mv = d.vecR + d.tl_j[k] * 3;
+        const V3<R> mu = mk(mv[0], mv[1], mv[2]);
+        const V3<R> x = mk(d.tl_x[k], d.tl_y[k], d.tl_z[k]);
+        ef = ef + (d.tl_g2[k] * dot(mu, x)) * x + d.tl_g1[k] * mu;
     }
     const R vals[3] = {ef.x, ef.y, ef.z};
-    const R s = warp_transpose_sum<R, 3>(vals, red[a], lane);
-    if (lane < 3) out[i * 9 + a * 3 + lane] += double(s);
+    const R s = warp_transpose_sum<R, 3>(vals, red[threadIdx.x >> 5], lane);
+    if (lane < 3) out[t * 3 + lane] += double(s);
 }
 
 template <typename R>
-void launch_real_tmu(const KParams &p, DevState<R> &d, const double *vec, double *out, Launch L) {
-    if (p.periodic) k_real_tmu<R, true><<<p.M, 96, 0, L.s>>>(p, d, vec, out);
-    else k_real_tmu<R, false><<<p.M, 96, 0, L.s>>>(p, d, vec, out);
+void launch_tmu_list(const KParams &p, DevState<R> &d, double *out, Launch L) {
+    k_tmu_list<R><<<(p.M * 3 + 3) / 4, 128, 0, L.s>>>(p.M, d, out);
     count(L);
 }
 
@@ -731,126 +709,148 @@ void launch_real_tmu(const KParams &p, DevState<R> &d, const double *vec, double
 //       sum_b U(M_t, mu_b)   (Thole-damped)     + sum_l U(M_t, lambda_l) (undamped)
 //   target pol atom a of i (a = t < 3): d/dr_a of
 //       sum_s U(mu_a, M_s) + sum_b U(mu_a, mu_b)  (Thole-damped)
+// One warp per target site; work queues as in the permanent kernel with
+// three classes: atom sources (induced dipole and, for a polarizable target,
+// permanent multipole, sharing one Thole kernel), midpoint sources
+// (permanent multipole, polarizable targets only) and lambda charges.
 // ---------------------------------------------------------------------------
+constexpr int PQ_A = 128, PQ_M = 96, PQ_L = 96;
+
 template <typename R>
-struct PfTile {
-    int j[TILE];
-    R dO[TILE][3];
-    R off[TILE][NP * 3];
-    R mp[TILE][NS * NMP];
-    R mu[TILE][9];
-    R lam[TILE][2];
+struct PfAcc {
+    V3<R> gr, gm;
+    Sym<R> gt;
 };
+
+template <typename R, bool PER, int KIND>   // KIND 0: atom source, 1: midpoint source, 2: lambda charge
+__device__ __forceinline__ void polf_pair(const KParams &p, const DevState<R> &d, int w, V3<R> ot, const Mp<R> &mt,
+                                          V3<R> mui, int js, V3<R> rs, PfAcc<R> &A) {
+    const Scal<R> &S = sc<R>(p);
+    const R third = R(1) / R(3);
+    const int j = js >> 3, s = js & 7;
+    const V3<R> x = ot - rs;
+    const R r2 = dot(x, x);
+    const R rinv = rsqrt_(r2), r = r2 * rinv;
+    if (KIND == 2) {
+        R g[6];
+        if (PER) g_erfc<R, 5>(r, rinv, S.alpha, g);
+        else g_bare<R, 5>(rinv, g);
+        Mp<R> ms{};
+        ms.q = R(d.lam[j * 2 + s]);
+        FieldTerms<R> f;
+        source_field<R, 3>(ms, x, g, f);
+        A.gr = A.gr + target_grad(mt, ms, x, g, f);
+        A.gm = A.gm + f.d1;
+        symadd(A.gt, f.d2, third);
+        return;
+    }
+    R gb[5], g[6];
+    if (PER) g_erfc<R, 4>(r, rinv, S.alpha, gb);
+    else g_bare<R, 4>(rinv, gb);
+    g_thole_on<R, 4>(r, rinv, ainv3<R>(p, w, s), S.thole, PER, gb, g);
+    g[5] = R(0);
+    if (KIND == 0) {   // induced dipole of atom s of j at target site w
+        Mp<R> ms{};
+        const double *mj = d.mu + j * 9 + s * 3;
+        ms.mu = mk(R(mj[0]), R(mj[1]), R(mj[2]));
+        FieldTerms<R> f;
+        source_field<R, 3>(ms, x, g, f);
+        A.gr = A.gr + target_grad(mt, ms, x, g, f);
+        A.gm = A.gm + f.d1;
+        symadd(A.gt, f.d2, third);
+        // induced-induced, d/dr_a of mu_a . grad phi_b: for w < 3 the site
+        // damping polarizability is the atom's, so f is the atom-atom field
+        if (w < 3) A.gr = A.gr + symv(f.d2, mui);
+    }
+    if (w < 3) {       // permanent multipoles of site s of j at polarizable atom w
+        const Mp<R> ms = load_mp_g(d.gmp + (j * NS + s) * NMP);
+        FieldTerms<R> f;
+        source_field<R, 2>(ms, x, g, f);
+        A.gr = A.gr + symv(f.d2, mui);
+    }
+}
 
 template <typename R, bool PER>
 __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d) {
-    __shared__ PfTile<R> t;
-    __shared__ R red[5][12 * 33];
+    __shared__ PairQueue<R, PQ_A + PQ_M + PQ_L> qs[5];
+    static_assert(sizeof(PairQueue<R, PQ_A + PQ_M + PQ_L>) >= 12 * 33 * sizeof(R), "reduction buffer");
     const int i = blockIdx.x;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const Scal<R> &S = sc<R>(p);
+    PairQueue<R, PQ_A + PQ_M + PQ_L> &q = qs[w];
     const V3<R> ot = my_pt(d, i, w);
     const Mp<R> mt = load_mp(d.gmp + (i * NS + w) * NMP);
     V3<R> mui = mk(R(0), R(0), R(0));
     if (w < 3) mui = mk(R(d.mu[i * 9 + w * 3]), R(d.mu[i * 9 + w * 3 + 1]), R(d.mu[i * 9 + w * 3 + 2]));
-    const R rc2 = S.rc2, alpha = S.alpha, thole = S.thole, third = R(1) / R(3);
-    V3<R> gr = mk(R(0), R(0), R(0)), gm = gr;
-    Sym<R> gt{};
+    const R rc2 = sc<R>(p).rc2;
+    PfAcc<R> A;
+    A.gr = mk(R(0), R(0), R(0));
+    A.gm = A.gr;
+    A.gt = Sym<R>{};
+    int ha = 0, ta = 0, hm = 0, tm = 0, hl = 0, tl = 0;
     const int nn = d.nnbr[i];
-    for (int base = 0; base < nn; base += TILE) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < TILE; k += blockDim.x) {
-            int slot = base + k;
-            int j = slot < nn ? d.nbr[i * MAXN + slot] : -1;
-            t.j[k] = j;
-            if (j >= 0) {
-                const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
-                t.dO[k][0] = dp_[0]; t.dO[k][1] = dp_[1]; t.dO[k][2] = dp_[2];
+    for (int base = 0;; base += 32) {
+        const bool flush = base >= nn;
+        const int slot = base + lane;
+        unsigned bits = 0;   // bits 0-4 sites, 5-6 lone pairs
+        int j = 0;
+        V3<R> rs[NP];
+        if (slot < nn) {
+            j = d.nbr[i * MAXN + slot];
+            const R *dp = d.ndo + ((size_t)i * MAXN + slot) * 3;
+            const V3<R> dO = mk(dp[0], dp[1], dp[2]);
+            const R *offj = d.off + j * NP * 3;
+#pragma unroll
+            for (int s = 0; s < NP; ++s) {
+                rs[s] = dO + mk(__ldg(offj + s * 3), __ldg(offj + s * 3 + 1), __ldg(offj + s * 3 + 2));
+                const V3<R> x = ot - rs[s];
+                const bool in = !PER || dot(x, x) < rc2;
+                const bool want = s < 3 || (s < NS ? w < 3 : d.lam[j * 2 + s - NS] != 0.0);
+                if (in && want) bits |= 1u << s;
             }
         }
-        __syncthreads();
-        for (int k = threadIdx.x; k < TILE * NP * 3; k += blockDim.x) {
-            int s = k / (NP * 3), c = k % (NP * 3);
-            int j = t.j[s];
-            t.off[s][c] = j >= 0 ? d.off[j * NP * 3 + c] : R(0);
+        int na, nm, nl;
+        int pa = warp_excl_scan(__popc(bits & 7u), lane, na);
+        int pm = warp_excl_scan(__popc((bits >> 3) & 3u), lane, nm);
+        int pl = warp_excl_scan(__popc(bits >> 5), lane, nl);
+#pragma unroll
+        for (int s = 0; s < NP; ++s) {
+            if (!((bits >> s) & 1u)) continue;
+            if (s < 3) q.put((ta + pa++) % PQ_A, j, s, rs[s]);
+            else if (s < NS) q.put(PQ_A + (tm + pm++) % PQ_M, j, s, rs[s]);
+            else q.put(PQ_A + PQ_M + (tl + pl++) % PQ_L, j, s - NS, rs[s]);
         }
-        for (int k = threadIdx.x; k < TILE * NS * NMP; k += blockDim.x) {
-            int s = k / (NS * NMP), c = k % (NS * NMP);
-            int j = t.j[s];
-            t.mp[s][c] = j >= 0 ? d.gmp[j * NS * NMP + c] : R(0);
-        }
-        for (int k = threadIdx.x; k < TILE * 11; k += blockDim.x) {
-            int s = k / 11, c = k % 11;
-            int j = t.j[s];
-            if (c < 9) t.mu[s][c] = j >= 0 ? R(d.mu[j * 9 + c]) : R(0);
-            else t.lam[s][c - 9] = j >= 0 ? R(d.lam[j * 2 + c - 9]) : R(0);
-        }
-        __syncthreads();
-        const int k = lane;
-        if (base + k >= nn) continue;
-        const V3<R> dO = mk(t.dO[k][0], t.dO[k][1], t.dO[k][2]);
-        // (1) target site w, sources: induced dipoles of j
-#pragma unroll 1
-        for (int b = 0; b < 3; ++b) {
-            const V3<R> x = ot - (dO + mk(t.off[k][b * 3], t.off[k][b * 3 + 1], t.off[k][b * 3 + 2]));
-            const R r2 = dot(x, x);
-            if (PER && r2 >= rc2) continue;
-            const R rinv = rsqrt_(r2), r = r2 * rinv;
-            R g[6];
-            g_thole<R, 4>(r, rinv, ainv3<R>(p, w, b), thole, PER, alpha, g);
-            g[5] = R(0);
-            Mp<R> ms{};
-            ms.mu = mk(t.mu[k][b * 3], t.mu[k][b * 3 + 1], t.mu[k][b * 3 + 2]);
-            FieldTerms<R> f;
-            source_field<R, 3>(ms, x, g, f);
-            gr = gr + target_grad(mt, ms, x, g, f);
-            gm = gm + f.d1;
-            symadd(gt, f.d2, third);
-            // induced-induced, d/dr_a of mu_a . grad phi_b: for w < 3 the site
-            // damping polarizability is the atom's, so f is the atom-atom field
-            if (w < 3) gr = gr + symv(f.d2, mui);
-        }
-        // (2) target site w, sources: lambda charges on the lone pairs of j
-#pragma unroll 1
-        for (int l = 0; l < 2; ++l) {
-            const R lq = t.lam[k][l];
-            if (lq == R(0)) continue;
-            const V3<R> x = ot - (dO + mk(t.off[k][(5 + l) * 3], t.off[k][(5 + l) * 3 + 1], t.off[k][(5 + l) * 3 + 2]));
-            const R r2 = dot(x, x);
-            if (PER && r2 >= rc2) continue;
-            const R rinv = rsqrt_(r2), r = r2 * rinv;
-            R g[6];
-            if (PER) g_erfc<R, 5>(r, rinv, alpha, g);
-            else g_bare<R, 5>(rinv, g);
-            Mp<R> ms{};
-            ms.q = lq;
-            FieldTerms<R> f;
-            source_field<R, 3>(ms, x, g, f);
-            gr = gr + target_grad(mt, ms, x, g, f);
-            gm = gm + f.d1;
-            symadd(gt, f.d2, third);
-        }
-        // (3) target pol atom a = w, sources: permanent multipoles of j
-        if (w < 3) {
-#pragma unroll 1
-            for (int s = 0; s < NS; ++s) {
-                const V3<R> x = ot - (dO + mk(t.off[k][s * 3], t.off[k][s * 3 + 1], t.off[k][s * 3 + 2]));
-                const R r2 = dot(x, x);
-                if (PER && r2 >= rc2) continue;
-                const R rinv = rsqrt_(r2), r = r2 * rinv;
-                R g[6];
-                g_thole<R, 4>(r, rinv, ainv3<R>(p, w, s), thole, PER, alpha, g);
-                g[5] = R(0);
-                const Mp<R> ms = load_mp(&t.mp[k][s * NMP]);
-                FieldTerms<R> f;
-                source_field<R, 2>(ms, x, g, f);
-                gr = gr + symv(f.d2, mui);
+        ta += na;
+        tm += nm;
+        tl += nl;
+        __syncwarp();
+        while (ta - ha >= 32 || (flush && ta > ha)) {
+            if (lane < ta - ha) {
+                const int e = (ha + lane) % PQ_A;
+                polf_pair<R, PER, 0>(p, d, w, ot, mt, mui, q.js[e], q.at(e), A);
             }
+            ha += min(32, ta - ha);
         }
+        while (tm - hm >= 32 || (flush && tm > hm)) {
+            if (lane < tm - hm) {
+                const int e = PQ_A + (hm + lane) % PQ_M;
+                polf_pair<R, PER, 1>(p, d, w, ot, mt, mui, q.js[e], q.at(e), A);
+            }
+            hm += min(32, tm - hm);
+        }
+        while (tl - hl >= 32 || (flush && tl > hl)) {
+            if (lane < tl - hl) {
+                const int e = PQ_A + PQ_M + (hl + lane) % PQ_L;
+                polf_pair<R, PER, 2>(p, d, w, ot, mt, mui, q.js[e], q.at(e), A);
+            }
+            hl += min(32, tl - hl);
+        }
+        __syncwarp();
+        if (flush) break;
     }
     const double ke = p.ke;
-    const R vals[12] = {gr.x, gr.y, gr.z, gm.x, gm.y, gm.z, gt.xx, gt.yy, gt.zz, gt.xy, gt.xz, gt.yz};
-    const R s = warp_transpose_sum<R, 12>(vals, red[w], lane);
+    const R vals[12] = {A.gr.x, A.gr.y, A.gr.z, A.gm.x, A.gm.y, A.gm.z,
+                        A.gt.xx, A.gt.yy, A.gt.zz, A.gt.xy, A.gt.xz, A.gt.yz};
+    const R s = warp_transpose_sum<R, 12>(vals, reinterpret_cast<R *>(&q), lane);
     if (lane < 3) d.gpt[(i * NP + w) * 3 + lane] += ke * double(s);
     else if (lane < 6) d.gmu[(i * NS + w) * 3 + lane - 3] += ke * double(s);
     else if (lane < 12) d.gth[(i * NS + w) * 6 + lane - 6] += ke * double(s);
@@ -867,7 +867,7 @@ void launch_real_polforce(const KParams &p, DevState<R> &d, Launch L) {
     template void launch_real_perm<R>(const KParams &, DevState<R> &, Launch);                     \
     template void launch_short<R>(const KParams &, DevState<R> &, Launch);                         \
     template void launch_ct<R>(const KParams &, DevState<R> &, Launch);                            \
-    template void launch_real_tmu<R>(const KParams &, DevState<R> &, const double *, double *, Launch); \
+    template void launch_tmu_list<R>(const KParams &, DevState<R> &, double *, Launch);             \
     template void launch_real_polforce<R>(const KParams &, DevState<R> &, Launch);
 INST(float)
 INST(double)

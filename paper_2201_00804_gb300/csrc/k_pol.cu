@@ -65,6 +65,7 @@ __global__ void k_pcg_init(KParams p, DevState<R> d, int warm) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= p.M * 9) return;
     if (!warm) d.mu[k] = apol(p, k) * d.efield[k];
+    d.vecR[k] = R(d.mu[k]);
     d.efp[k] = 0.0;
 }
 
@@ -79,6 +80,7 @@ __global__ void k_pcg_first(KParams p, DevState<R> d) {
         d.res[k] = r;
         d.zv[k] = a * r;
         d.pv[k] = a * r;
+        d.vecR[k] = R(a * r);
         d.efp[k] = 0.0;
         rz = r * a * r;
         rr = a * r * a * r;
@@ -144,7 +146,9 @@ __global__ void k_pcg_c(KParams p, DevState<R> d) {
     if (d.scal[S_DONE] != 0.0) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= p.M * 9) return;
-    d.pv[k] = d.zv[k] + d.scal[S_BETA] * d.pv[k];
+    const double pk = d.zv[k] + d.scal[S_BETA] * d.pv[k];
+    d.pv[k] = pk;
+    d.vecR[k] = R(pk);
     d.efp[k] = 0.0;
 }
 

@@ -18,6 +18,7 @@ constexpr int MAXN = 384;      // neighbour slots per molecule
 constexpr int NTERM = 7;       // elec pen rep disp xdisp pol ct
 enum { T_ELEC = 0, T_PEN, T_REP, T_DISP, T_XDISP, T_POL, T_CT };
 constexpr int ORDER = 5;       // B-spline order of the SPME
+constexpr int TLS = 3 * MAXN;  // T-pair list slots per polarizable atom
 
 // error flags (bitwise, device side)
 enum { F_CUTOFF = 1, F_NEIGHBOR = 2, F_CTDEN = 4, F_NAN = 8 };
@@ -157,6 +158,13 @@ struct DevState {
     double *epart;      // M*NTERM per-molecule energy partials
     // polarization solve
     double *mu, *res, *zv, *pv, *ap, *efp;   // M*9 each
+    R *vecR;            // M*9 the vector of the current T product in the working precision
+    // Real-space T pairs recorded by the permanent pass: for polarizable atom
+    // t = 3 m + a, entries [t*TLS, t*TLS + tl_n[t]) hold the partner atom
+    // (3 j + b), the displacement x = r_t - r_jb and the Thole-damped kernel
+    // weights g1, g2 of the dipole field (E = g2 (mu.x) x + g1 mu).
+    int *tl_n, *tl_j;
+    R *tl_x, *tl_y, *tl_z, *tl_g1, *tl_g2;
     double *partial;    // reduction partials
     double *scal;       // device scalars (see pcg kernels)
     unsigned int *counter;
@@ -654,7 +662,7 @@ template <typename R> void launch_real_perm(const KParams &p, DevState<R> &d, La
 template <typename R> void launch_short(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_ct(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_intra_perm(const KParams &p, DevState<R> &d, Launch L);
-template <typename R> void launch_real_tmu(const KParams &p, DevState<R> &d, const double *vec, double *out,
+template <typename R> void launch_tmu_list(const KParams &p, DevState<R> &d, double *out,
                                            Launch L);
 template <typename R> void launch_intra_tmu(const KParams &p, DevState<R> &d, const double *vec, double *out,
                                             Launch L);
