@@ -133,6 +133,9 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.nbr, (size_t)M * MAXN);
     AL(d.ndo, (size_t)M * MAXN * 3);
     AL(d.ofw, (size_t)M * 3);
+    AL(d.ufx, (size_t)M * 3);
+    AL(d.sbase, (size_t)M * NP * 3);
+    AL(d.sfrac, (size_t)M * NP * 3);
     AL(d.nnbr, M);
     int ncell = std::max(1, ctx->ncell[0] * ctx->ncell[1] * ctx->ncell[2]);
     AL(d.cell_of, M);
@@ -182,6 +185,7 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
             d.cgrid = c;
         }
         AL(d.infl, nh);
+        AL(d.inflR, nh);
     }
     return SIBFA_OK;
 }
@@ -196,6 +200,8 @@ void fill_scal(Scal<R> &s, const KParams &k) {
     s.c6 = R(k.c6); s.c8 = R(k.c8); s.c10 = R(k.c10); s.g6 = R(k.g6); s.g8 = R(k.g8); s.g10 = R(k.g10);
     s.delta = R(k.delta); s.xd_c1 = R(k.xd_c1); s.xd_c2 = R(k.xd_c2); s.xd_c3 = R(k.xd_c3);
     s.ct_t = R(k.ct_t); s.ct_m = R(k.ct_m); s.ct_ae = R(k.ct_ae); s.ct_ah = R(k.ct_ah);
+    for (int c = 0; c < 3; ++c) s.kl[c] = k.box[c] > 0 ? R((double)k.K[c] / k.box[c]) : R(0);
+    s.ike = R(1.0 / k.ke);
 }
 
 void fill_params(KParams &k, const sibfa_params &P, const sibfa_run_opts &o, int M) {
@@ -264,6 +270,7 @@ void fill_params(KParams &k, const sibfa_params &P, const sibfa_run_opts &o, int
     k.ct_k1 = coef(P.ct_eta / (2.0 * sqrt(P.rvdw_ct_o * P.rvdw_ct_o)));
     k.ct_k2 = coef(P.ct_eta / (2.0 * sqrt(P.rvdw_ct_o * P.rvdw_ct_h)));
     for (int s = 0; s < 5; ++s) k.pen_b[s] = coef(k.b[s]);
+    for (int i = 0; i < 3; ++i) k.fxs[i] = (float)(o.box[i] / 4294967296.0);
     fill_scal(k.sd, k);
     fill_scal(k.sf, k);
     for (int s = 0; s < 5; ++s) {
@@ -324,7 +331,7 @@ sibfa_status fft(sibfa_ctx *ctx, DevState<R> &d, bool forward, int ngrid) {
 template <typename R>
 sibfa_status matvec(sibfa_ctx *ctx, DevState<R> &d, const double *vec, Launch L) {
     const KParams &p = ctx->kp;
-    { Phase ph(ctx, "real_tmu");  launch_tmu_list(p, d, d.efp, L); }
+    { Phase ph(ctx, "real_tmu");  launch_real_tmu(p, d, d.efp, L); }
     if (p.periodic) {
         const size_t ng = (size_t)p.K[0] * p.K[1] * p.K[2];
         CK(cudaMemsetAsync(d.grid, 0, ng * sizeof(R), ctx->s));
@@ -335,7 +342,7 @@ sibfa_status matvec(sibfa_ctx *ctx, DevState<R> &d, const double *vec, Launch L)
         st = fft(ctx, d, false, 1);
         if (st) return st;
         launch_gather_field(p, d, d.efp, L);
-        launch_intra_tmu(p, d, vec, d.efp, L);
+        launch_intra_tmu(p, d, d.efp, L);
     }
     return SIBFA_OK;
 }
@@ -573,6 +580,7 @@ sibfa_status create_impl(sibfa_ctx *ctx, const sibfa_topology *topo) {
     if (ctx->opts.periodic) {
         Launch L{ctx->s, &ctx->launches};
         launch_influence(ctx->kp, d.infl, L);
+        launch_influence_copy(ctx->kp, d, L);
         int n[3] = {ctx->kp.K[0], ctx->kp.K[1], ctx->kp.K[2]};
         const bool f32 = sizeof(R) == 4;
         const int ng = n[0] * n[1] * n[2], nh = n[0] * n[1] * (n[2] / 2 + 1);

@@ -145,18 +145,18 @@ void launch_intra_perm(const KParams &p, DevState<R> &d, Launch L) {
 
 // PCG product, intramolecular part: one thread per polarizable atom, out +=
 // minus the erf part of the field from the other two atoms' dipoles, plus the
-// self term of its own dipole.
+// self term of its own dipole (dipoles: the working-precision PCG vector).
 template <typename R>
-__global__ void k_intra_tmu(KParams p, DevState<R> d, const double *vec, double *out) {
-    if (d.scal[7] != 0.0) return;   // solver already converged
+__global__ void k_intra_tmu(KParams p, DevState<R> d, double *out) {
+    if (d.flags[1]) return;   // solver already converged
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= p.M * 3) return;
     const int m = t / 3, a = t % 3;
     const R al = sc<R>(p).alpha;
     const R cself = R(4.0 / 3.0) * al * al * al * R(0.56418958354775628695);
-    const double *v = vec + m * 9;
+    const R *v = d.vecR + m * 9;
     const V3<R> Xa = opt(d, m, a);
-    V3<R> E = cself * mk(R(v[a * 3]), R(v[a * 3 + 1]), R(v[a * 3 + 2]));
+    V3<R> E = cself * mk(v[a * 3], v[a * 3 + 1], v[a * 3 + 2]);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
         if (b == a) continue;
@@ -164,7 +164,7 @@ __global__ void k_intra_tmu(KParams p, DevState<R> d, const double *vec, double 
         R g[4];
         g_erf_s<R, 3>(dot(xv, xv), al, g);
         Mp<R> s{};
-        s.mu = mk(R(v[b * 3]), R(v[b * 3 + 1]), R(v[b * 3 + 2]));
+        s.mu = mk(v[b * 3], v[b * 3 + 1], v[b * 3 + 2]);
         FieldTerms<R> f;
         source_field<R, 1>(s, xv, g, f);
         E = E + f.d1;
@@ -175,9 +175,9 @@ __global__ void k_intra_tmu(KParams p, DevState<R> d, const double *vec, double 
 }
 
 template <typename R>
-void launch_intra_tmu(const KParams &p, DevState<R> &d, const double *vec, double *out, Launch L) {
+void launch_intra_tmu(const KParams &p, DevState<R> &d, double *out, Launch L) {
     const int n = p.M * 3;
-    k_intra_tmu<R><<<(n + 127) / 128, 128, 0, L.s>>>(p, d, vec, out);
+    k_intra_tmu<R><<<(n + 127) / 128, 128, 0, L.s>>>(p, d, out);
     count(L);
 }
 
@@ -266,7 +266,7 @@ void launch_intra_polforce(const KParams &p, DevState<R> &d, Launch L) {
 
 #define INST(R)                                                                                         \
     template void launch_intra_perm<R>(const KParams &, DevState<R> &, Launch);                         \
-    template void launch_intra_tmu<R>(const KParams &, DevState<R> &, const double *, double *, Launch); \
+    template void launch_intra_tmu<R>(const KParams &, DevState<R> &, double *, Launch);                \
     template void launch_intra_polforce<R>(const KParams &, DevState<R> &, Launch);
 INST(float)
 INST(double)

@@ -14,12 +14,6 @@ namespace sibfa {
 constexpr int TILE = 32;
 
 template <typename R>
-__device__ inline V3<R> my_pt(const DevState<R> &d, int i, int pt) {
-    const R *o = d.off + (i * NP + pt) * 3;
-    return mk(o[0], o[1], o[2]);
-}
-
-template <typename R>
 __device__ inline void symadd(Sym<R> &a, const Sym<R> &b, R s) {
     a.xx += s * b.xx; a.yy += s * b.yy; a.zz += s * b.zz;
     a.xy += s * b.xy; a.xz += s * b.xz; a.yz += s * b.yz;
@@ -50,17 +44,6 @@ struct PairQueue {
     }
     __device__ inline V3<R> at(int e) const { return mk(rx[e], ry[e], rz[e]); }
 };
-
-__device__ inline int warp_excl_scan(int c, int lane, int &total) {
-    int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    total = __shfl_sync(0xffffffffu, incl, 31);
-    return incl - c;
-}
 
 // ---------------------------------------------------------------------------
 // Permanent electrostatics + penetration (Eq. 2), Thole-damped permanent
@@ -186,7 +169,7 @@ __global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) 
     const R Nt = (!is_lp) ? zsite<R>(p, w) - mt.q * R(w < 3) : R(0);
     const R Nt_ = (w < 3) ? Nt : R(0);
     const R rc2 = sc<R>(p).rc2;
-    const size_t tbase = (size_t)(i * 3 + (w < 3 ? w : 0)) * TLS;
+    const size_t tbase = (size_t)(i * 3 + (w < 3 ? w : 0)) * TLS;   // T-pair list of target atom w
 
     PermAcc<R> A;
     A.gr = mk(R(0), R(0), R(0));
@@ -285,276 +268,6 @@ template <typename R>
 void launch_real_perm(const KParams &p, DevState<R> &d, Launch L) {
     if (p.periodic) k_real_perm<R, true><<<p.M, 224, 0, L.s>>>(p, d);
     else k_real_perm<R, false><<<p.M, 224, 0, L.s>>>(p, d);
-    count(L);
-}
-
-// ---------------------------------------------------------------------------
-// Exchange-repulsion (Technical Appendix), dispersion and exchange-dispersion.
-// One lane per (i, j) molecule pair; gradients of i's points only.
-// Points: 0 = O, 1 = H1, 2 = H2, 3 = LP1, 4 = LP2 (relative to O_i).
-// ---------------------------------------------------------------------------
-template <typename R>
-__device__ inline R cosv(V3<R> u, V3<R> v, V3<R> &du, V3<R> &dv) {
-    const R uu = dot(u, u), vv = dot(v, v);
-    const R iu = rsqrt_(uu), iv = rsqrt_(vv);
-    const R c = dot(u, v) * iu * iv;
-    du = (iu * iv) * v - (c / uu) * u;
-    dv = (iu * iv) * u - (c / vv) * v;
-    return c;
-}
-
-// Atom-pair overlap with each p orbital measured at its own atom:
-// O = A + B cx + C cy + D cx cy, cx = cos(ux, y - x), cy = cos(uy, x - y),
-// ux = xp - x (xp an i-side point), uy fixed (j side).
-// Adds dO/dx into gx and dO/dxp into gxp.
-template <typename R>
-__device__ inline R overlap_i(V3<R> x, V3<R> xp, V3<R> y, V3<R> uy, R A, R B, R C, R D, V3<R> &gx, V3<R> &gxp) {
-    V3<R> du, dv, du2, dv2;
-    const R cx = cosv(xp - x, y - x, du, dv);
-    const R cy = cosv(uy, x - y, du2, dv2);
-    const R ox = B + D * cy, oy = C + D * cx;
-    gxp = ox * du;
-    gx = R(-1) * ox * (du + dv) + oy * dv2;
-    return A + B * cx + C * cy + D * cx * cy;
-}
-
-template <typename R>
-struct RepAtom {
-    R cs, cp, g, cf;
-    int kind;   // 0 = O, 1 = H, 2 = lone pair (selects the precomputed exponent coefficients)
-};
-
-// Adds the overlap and exponential factor of one atom pair to O1/O2 and the
-// i-side gradients of O1/O2 (points ix, ixp).
-template <typename R>
-__device__ inline void rep_pair_term(V3<R> x, V3<R> xp, const RepAtom<R> &ai, V3<R> y, V3<R> uy, const RepAtom<R> &aj,
-                                     R pp, R f, const KParams &p, R &O1, R &O2, V3<R> &g1x, V3<R> &g1xp, V3<R> &g2x,
-                                     V3<R> &g2xp) {
-    V3<R> gx, gxp;
-    const R O = overlap_i(x, xp, y, uy, ai.cs * aj.cs, aj.cs * ai.cp * f, ai.cs * aj.cp * f, pp * ai.cp * aj.cp, gx, gxp);
-    const V3<R> v = x - y;
-    const R rr = sqrt_(dot(v, v));
-    const KParams::Coef &k1 = p.rep_k1[ai.kind][aj.kind], &k2 = p.rep_k2[ai.kind][aj.kind];
-    const R M = sqrt_(ai.g * aj.g * ai.cf * aj.cf);
-    const R S1 = M * exp_(-mulc(rr, k1)), S2 = M * exp_(-mulc(rr, k2));
-    O1 += O * S1;
-    O2 += O * S2;
-    const V3<R> drdx = (R(1) / rr) * v;
-    g1x = g1x + S1 * gx + (O * S1 * (-cval<R>(k1))) * drdx;
-    g2x = g2x + S2 * gx + (O * S2 * (-cval<R>(k2))) * drdx;
-    g1xp = g1xp + S1 * gxp;
-    g2xp = g2xp + S2 * gxp;
-}
-
-// E = pref (C1 O1^2 / r + C2 O2^2 / r^2): returns E and dE/dO1, dE/dO2, dE/dr.
-template <typename R>
-__device__ inline R rep_energy(R pref, R C1, R C2, R O1, R O2, R r, R &e1, R &e2, R &er) {
-    const R ri = R(1) / r;
-    e1 = pref * C1 * R(2) * O1 * ri;
-    e2 = pref * C2 * R(2) * O2 * ri * ri;
-    er = pref * (-C1 * O1 * O1 * ri * ri - R(2) * C2 * O2 * O2 * ri * ri * ri);
-    return pref * (C1 * O1 * O1 * ri + C2 * O2 * O2 * ri * ri);
-}
-
-template <typename R, bool PER>
-__global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
-    __shared__ R red[4][15 * 33];
-    const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= p.M) return;
-    const Scal<R> &S = sc<R>(p);
-    const R rc2 = S.rc2;
-    V3<R> P[5];
-    for (int k = 0; k < 3; ++k) P[k] = my_pt(d, i, k);
-    P[3] = my_pt(d, i, 5);
-    P[4] = my_pt(d, i, 6);
-    const R qi[3] = {d.gmp[(i * NS + 0) * NMP], d.gmp[(i * NS + 1) * NMP], d.gmp[(i * NS + 2) * NMP]};
-    const R f = S.rep_f, C1 = S.rep_c1, C2 = S.rep_c2;
-    const R occ = S.occ, nlp = S.nlp;
-    const R cf_lp = R(1) - nlp * S.inv_nval_o;
-    V3<R> G[5];
-    for (int k = 0; k < 5; ++k) G[k] = mk(R(0), R(0), R(0));
-    Acc<R> Erep, Ed, Ex;
-    const int nn = d.nnbr[i];
-    for (int slot = lane; slot < nn; slot += 32) {
-        const int j = d.nbr[i * MAXN + slot];
-        const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
-        const V3<R> dO = mk(dp_[0], dp_[1], dp_[2]);
-        V3<R> Q[5];
-        Q[0] = dO;
-        Q[1] = dO + my_pt(d, j, 1);
-        Q[2] = dO + my_pt(d, j, 2);
-        Q[3] = dO + my_pt(d, j, 5);
-        Q[4] = dO + my_pt(d, j, 6);
-        const R qj[3] = {d.gmp[(j * NS + 0) * NMP], d.gmp[(j * NS + 1) * NMP], d.gmp[(j * NS + 2) * NMP]};
-        RepAtom<R> Ai[3], Aj[3];
-        Ai[0] = {S.cs_o, S.cp_o, S.g_o, R(1) - qi[0] * S.inv_nval_o, 0};
-        Aj[0] = {S.cs_o, S.cp_o, S.g_o, R(1) - qj[0] * S.inv_nval_o, 0};
-        for (int k = 1; k < 3; ++k) {
-            Ai[k] = {S.cs_h, S.cp_h, S.g_h, R(1) - qi[k] * S.inv_nval_h, 1};
-            Aj[k] = {S.cs_h, S.cp_h, S.g_h, R(1) - qj[k] * S.inv_nval_h, 1};
-        }
-        const RepAtom<R> Alp = {S.cs_lp, S.cp_lp, S.g_o, cf_lp, 2};
-        // ---- bond-bond
-        for (int kb = 1; kb <= 2; ++kb)
-            for (int kc = 1; kc <= 2; ++kc) {
-                const V3<R> mi = R(0.5) * (P[0] + P[kb]), mj = R(0.5) * (Q[0] + Q[kc]);
-                const V3<R> dm = mi - mj;
-                const R rm2 = dot(dm, dm);
-                if (PER && rm2 >= rc2) continue;
-                const R rm = sqrt_(rm2);
-                R O1 = 0, O2 = 0;
-                V3<R> z = mk(R(0), R(0), R(0));
-                V3<R> g1a = z, g1b = z, g2a = z, g2b = z;   // dO/d(O_i), dO/d(H_kb)
-                // x = a (O_i, partner H), x = b (H, partner O)
-                for (int u = 0; u < 2; ++u)
-                    for (int v = 0; v < 2; ++v) {
-                        const int xi = u ? kb : 0, xpi = u ? 0 : kb;
-                        const int yj = v ? kc : 0, ypj = v ? 0 : kc;
-                        V3<R> t1x = z, t1xp = z, t2x = z, t2xp = z;
-                        rep_pair_term(P[xi], P[xpi], Ai[xi], Q[yj], Q[ypj] - Q[yj], Aj[yj], R(2), f, p, O1, O2,
-                                      t1x, t1xp, t2x, t2xp);
-                        if (u == 0) { g1a = g1a + t1x; g2a = g2a + t2x; g1b = g1b + t1xp; g2b = g2b + t2xp; }
-                        else { g1b = g1b + t1x; g2b = g2b + t2x; g1a = g1a + t1xp; g2a = g2a + t2xp; }
-                    }
-                R e1, e2, er;
-                Erep.add(R(0.5) * rep_energy(occ * occ, C1, C2, O1, O2, rm, e1, e2, er));
-                const V3<R> drm = (R(0.5) / rm) * dm;
-                G[0] = G[0] + e1 * g1a + e2 * g2a + er * drm;
-                G[kb] = G[kb] + e1 * g1b + e2 * g2b + er * drm;
-            }
-        // ---- bond of i with lone pair of j
-        for (int kb = 1; kb <= 2; ++kb)
-            for (int l = 0; l < 2; ++l) {
-                const V3<R> mi = R(0.5) * (P[0] + P[kb]);
-                const V3<R> dm = mi - Q[3 + l];
-                const R r2 = dot(dm, dm);
-                if (PER && r2 >= rc2) continue;
-                const R rr = sqrt_(r2);
-                R O1 = 0, O2 = 0;
-                V3<R> z = mk(R(0), R(0), R(0));
-                V3<R> g1a = z, g1b = z, g2a = z, g2b = z;
-                for (int u = 0; u < 2; ++u) {
-                    const int xi = u ? kb : 0, xpi = u ? 0 : kb;
-                    V3<R> t1x = z, t1xp = z, t2x = z, t2xp = z;
-                    rep_pair_term(P[xi], P[xpi], Ai[xi], Q[0], Q[3 + l] - Q[0], Alp, f, f, p, O1, O2, t1x, t1xp,
-                                  t2x, t2xp);
-                    if (u == 0) { g1a = g1a + t1x; g2a = g2a + t2x; g1b = g1b + t1xp; g2b = g2b + t2xp; }
-                    else { g1b = g1b + t1x; g2b = g2b + t2x; g1a = g1a + t1xp; g2a = g2a + t2xp; }
-                }
-                R e1, e2, er;
-                Erep.add(R(0.5) * rep_energy(occ * nlp, C1, C2, O1, O2, rr, e1, e2, er));
-                const V3<R> drm = (R(0.5) / rr) * dm;
-                G[0] = G[0] + e1 * g1a + e2 * g2a + er * drm;
-                G[kb] = G[kb] + e1 * g1b + e2 * g2b + er * drm;
-            }
-        // ---- lone pair of i with bond of j (the lone pair as a pseudo-atom at its carrier)
-        for (int l = 0; l < 2; ++l)
-            for (int kc = 1; kc <= 2; ++kc) {
-                const V3<R> mj = R(0.5) * (Q[0] + Q[kc]);
-                const V3<R> dm = P[3 + l] - mj;
-                const R r2 = dot(dm, dm);
-                if (PER && r2 >= rc2) continue;
-                const R rr = sqrt_(r2);
-                R O1 = 0, O2 = 0;
-                V3<R> z = mk(R(0), R(0), R(0));
-                V3<R> g1c = z, g1l = z, g2c = z, g2l = z;
-                for (int v = 0; v < 2; ++v) {
-                    const int yj = v ? kc : 0, ypj = v ? 0 : kc;
-                    V3<R> t1x = z, t1xp = z, t2x = z, t2xp = z;
-                    rep_pair_term(P[0], P[3 + l], Alp, Q[yj], Q[ypj] - Q[yj], Aj[yj], f, f, p, O1, O2, t1x,
-                                  t1xp, t2x, t2xp);
-                    g1c = g1c + t1x; g2c = g2c + t2x; g1l = g1l + t1xp; g2l = g2l + t2xp;
-                }
-                R e1, e2, er;
-                Erep.add(R(0.5) * rep_energy(occ * nlp, C1, C2, O1, O2, rr, e1, e2, er));
-                G[0] = G[0] + e1 * g1c + e2 * g2c;
-                G[3 + l] = G[3 + l] + e1 * g1l + e2 * g2l + (er / rr) * dm;
-            }
-        // ---- lone pair - lone pair (angles toward the other lone pair's position)
-        for (int l1 = 0; l1 < 2; ++l1)
-            for (int l2 = 0; l2 < 2; ++l2) {
-                const V3<R> I = P[3 + l1], J = Q[3 + l2];
-                const V3<R> dIJ = I - J;
-                const R r2 = dot(dIJ, dIJ);
-                if (PER && r2 >= rc2) continue;
-                const R rr = sqrt_(r2);
-                V3<R> dui, dvi, duj, dvj;
-                const R ci = cosv(I - P[0], J - P[0], dui, dvi);    // depends on I and A
-                const R cj = cosv(J - Q[0], I - Q[0], duj, dvj);    // depends on I
-                const R cs = S.cs_lp, cp = S.cp_lp;
-                const R O = cs * cs + cs * cp * f * cj + cs * cp * f * ci + R(2) * cp * cp * ci * cj;
-                const R dci = cs * cp * f + R(2) * cp * cp * cj, dcj = cs * cp * f + R(2) * cp * cp * ci;
-                const V3<R> dOdI = dci * dui + dcj * dvj;
-                const V3<R> dOdA = R(-1) * dci * (dui + dvi);
-                const V3<R> dAB = P[0] - Q[0];
-                const R rab = sqrt_(dot(dAB, dAB));
-                const R M = S.g_o * cf_lp;
-                const R S1 = M * exp_(-mulc(rab, p.rep_k1[2][2])), S2 = M * exp_(-mulc(rab, p.rep_k2[2][2]));
-                const R O1 = O * S1, O2 = O * S2;
-                R e1, e2, er;
-                Erep.add(R(0.5) * rep_energy(nlp * nlp, C1, C2, O1, O2, rr, e1, e2, er));
-                const V3<R> drab = (R(1) / rab) * dAB;
-                G[0] = G[0] + (e1 * S1 + e2 * S2) * dOdA +
-                       (e1 * O1 * (-cval<R>(p.rep_k1[2][2])) + e2 * O2 * (-cval<R>(p.rep_k2[2][2]))) * drab;
-                G[3 + l1] = G[3 + l1] + (e1 * S1 + e2 * S2) * dOdI + (er / rr) * dIJ;
-            }
-        // ---- dispersion and exchange-dispersion over atoms and lone pairs
-        const R cfi[5] = {R(1) - qi[0] * S.inv_nval_o, R(1) - qi[1] * S.inv_nval_h, R(1) - qi[2] * S.inv_nval_h,
-                          R(1) - qi[0] * S.inv_nval_o, R(1) - qi[0] * S.inv_nval_o};
-        const R cfj[5] = {R(1) - qj[0] * S.inv_nval_o, R(1) - qj[1] * S.inv_nval_h, R(1) - qj[2] * S.inv_nval_h,
-                          R(1) - qj[0] * S.inv_nval_o, R(1) - qj[0] * S.inv_nval_o};
-        const int kind_of[5] = {0, 1, 1, 2, 2};
-        for (int u = 0; u < 5; ++u)
-            for (int v = 0; v < 5; ++v) {
-                const V3<R> dv = P[u] - Q[v];
-                const R r2 = dot(dv, dv);
-                if (PER && r2 >= rc2) continue;
-                const R ri = rsqrt_(r2), r = r2 * ri;
-                const int ku = kind_of[u], kv = kind_of[v];
-                const R m = mulc(r, p.disp_km[ku][kv]), mi = R(1) / m;
-                // exp(-gamma_n d) with d = S/r - 1: argument gamma_n - (gamma_n S)/r
-                const R a6 = mulc(ri, p.disp_gS[0][ku][kv]), a8 = mulc(ri, p.disp_gS[1][ku][kv]),
-                        a10 = mulc(ri, p.disp_gS[2][ku][kv]);
-                const R m2i = mi * mi, m6i = m2i * m2i * m2i, m8i = m6i * m2i, m10i = m8i * m2i;
-                const R e6 = S.c6 * exp_(S.g6 - a6) * m6i;
-                const R e8 = S.c8 * exp_(S.g8 - a8) * m8i;
-                const R e10 = S.c10 * exp_(S.g10 - a10) * m10i;
-                const R fsum = e6 + e8 + e10;
-                const R dfdr = e6 * ((a6 - R(6)) * ri) + e8 * ((a8 - R(8)) * ri) + e10 * ((a10 - R(10)) * ri);
-                const bool lu = u >= 3, lv = v >= 3;
-                R pref, xc;
-                if (!lu && !lv) { pref = -betap<R>(p, u) * betap<R>(p, v); xc = S.xd_c1; }
-                else if (lu && lv) { pref = -nlp * nlp * R(0.25); xc = nlp * nlp * R(0.25) * S.xd_c2; }
-                else { pref = -S.delta * R(0.5); xc = nlp * R(0.5) * S.xd_c3; }
-                const R K = betap<R>(p, u) * betap<R>(p, v) * cfi[u] * cfj[v];
-                const R ex = xc * K * exp_(-mulc(r, p.xd_k[ku][kv]));
-                Ed.add(R(0.5) * pref * fsum);
-                Ex.add(R(0.5) * ex);
-                const R dEdr = pref * dfdr - cval<R>(p.xd_k[ku][kv]) * ex;
-                G[u] = G[u] + (dEdr * ri) * dv;
-            }
-    }
-    // lane reduction; points 3, 4 are the lone pairs (point slots 5, 6)
-    {
-        const R vals[15] = {G[0].x, G[0].y, G[0].z, G[1].x, G[1].y, G[1].z, G[2].x, G[2].y, G[2].z,
-                            G[3].x, G[3].y, G[3].z, G[4].x, G[4].y, G[4].z};
-        const R t = warp_transpose_sum<R, 15>(vals, red[threadIdx.x >> 5], lane);
-        const int pt = lane / 3;
-        if (lane < 15) d.gpt[(i * NP + (pt < 3 ? pt : pt + 2)) * 3 + lane % 3] += double(t);
-    }
-    const double er_ = warp_sum_acc(Erep), ed_ = warp_sum_acc(Ed), ex_ = warp_sum_acc(Ex);
-    if (lane == 0) {
-        d.epart[i * NTERM + T_REP] += er_;
-        d.epart[i * NTERM + T_DISP] += ed_;
-        d.epart[i * NTERM + T_XDISP] += ex_;
-    }
-}
-
-template <typename R>
-void launch_short(const KParams &p, DevState<R> &d, Launch L) {
-    if (p.periodic) k_short<R, true><<<(p.M + 3) / 4, 128, 0, L.s>>>(p, d);
-    else k_short<R, false><<<(p.M + 3) / 4, 128, 0, L.s>>>(p, d);
     count(L);
 }
 
@@ -671,34 +384,47 @@ void launch_ct(const KParams &p, DevState<R> &d, Launch L) {
 // ---------------------------------------------------------------------------
 // Polarization matrix-vector product, real-space part: field at each
 // polarizable atom from the dipoles vecR of the atoms of other molecules
-// within rc (Thole-damped, Ewald-screened in periodic systems), streamed
-// from the pair list that the permanent pass recorded.  out += field.
-// One warp per polarizable atom.
+// within rc (Thole-damped, Ewald-screened in periodic systems), streamed from
+// the pair list that the permanent pass recorded.  out += field.  One warp
+// per polarizable atom; each lane keeps four entries in flight.
 // ---------------------------------------------------------------------------
+constexpr int TW = 8;   // warps per block
+
 template <typename R>
-__global__ void __launch_bounds__(128) k_tmu_list(int M, DevState<R> d, double *out) {
-    __shared__ R red[4][3 * 33];
-    if (d.scal[7] != 0.0) return;   // solver already converged
-    const int t = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+__device__ inline void tmu_entry(const DevState<R> &d, size_t k, int jb, V3<R> &ef) {
+    const R *mv = d.vecR + jb * 3;
+    const V3<R> mu = mk(mv[0], mv[1], mv[2]);
+    const V3<R> x = mk(d.tl_x[k], d.tl_y[k], d.tl_z[k]);
+    ef = ef + (d.tl_g2[k] * dot(mu, x)) * x + d.tl_g1[k] * mu;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(32 * TW) k_real_tmu(int M, DevState<R> d, double *out) {
+    __shared__ R red[TW][3 * 33];
+    if (d.flags[1]) return;   // solver already converged
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * TW + w;
     if (t >= M * 3) return;
     const int n = d.tl_n[t];
     const size_t base = (size_t)t * TLS;
     V3<R> ef = mk(R(0), R(0), R(0));
-    for (int e = lane; e < n; e += 32) {
-        const size_t k = base + e;
-        const R *mv = d.vecR + d.tl_j[k] * 3;
-        const V3<R> mu = mk(mv[0], mv[1], mv[2]);
-        const V3<R> x = mk(d.tl_x[k], d.tl_y[k], d.tl_z[k]);
-        ef = ef + (d.tl_g2[k] * dot(mu, x)) * x + d.tl_g1[k] * mu;
+    int e = lane;
+    for (; e + 96 < n; e += 128) {
+        int jb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) jb[u] = d.tl_j[base + e + 32 * u];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) tmu_entry(d, base + e + 32 * u, jb[u], ef);
     }
+    for (; e < n; e += 32) tmu_entry(d, base + e, d.tl_j[base + e], ef);
     const R vals[3] = {ef.x, ef.y, ef.z};
-    const R s = warp_transpose_sum<R, 3>(vals, red[threadIdx.x >> 5], lane);
+    const R s = warp_transpose_sum<R, 3>(vals, red[w], lane);
     if (lane < 3) out[t * 3 + lane] += double(s);
 }
 
 template <typename R>
-void launch_tmu_list(const KParams &p, DevState<R> &d, double *out, Launch L) {
-    k_tmu_list<R><<<(p.M * 3 + 3) / 4, 128, 0, L.s>>>(p.M, d, out);
+void launch_real_tmu(const KParams &p, DevState<R> &d, double *out, Launch L) {
+    k_real_tmu<R><<<(p.M * 3 + TW - 1) / TW, 32 * TW, 0, L.s>>>(p.M, d, out);
     count(L);
 }
 
@@ -865,9 +591,8 @@ void launch_real_polforce(const KParams &p, DevState<R> &d, Launch L) {
 
 #define INST(R)                                                                                    \
     template void launch_real_perm<R>(const KParams &, DevState<R> &, Launch);                     \
-    template void launch_short<R>(const KParams &, DevState<R> &, Launch);                         \
     template void launch_ct<R>(const KParams &, DevState<R> &, Launch);                            \
-    template void launch_tmu_list<R>(const KParams &, DevState<R> &, double *, Launch);             \
+    template void launch_real_tmu<R>(const KParams &, DevState<R> &, double *, Launch);             \
     template void launch_real_polforce<R>(const KParams &, DevState<R> &, Launch);
 INST(float)
 INST(double)

@@ -92,13 +92,14 @@ __global__ void k_pcg_first(KParams p, DevState<R> d) {
         d.scal[S_RES] = res;
         d.scal[S_IT] = 0;
         d.scal[S_DONE] = (res < d.scal[S_TOL]) ? 1.0 : 0.0;
+        d.flags[1] = res < d.scal[S_TOL];
     }
 }
 
 // ap = p / alpha - E(p); alpha_k = rz / p.ap
 template <typename R>
 __global__ void k_pcg_a(KParams p, DevState<R> d) {
-    if (d.scal[S_DONE] != 0.0) return;
+    if (d.flags[1]) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     double pap = 0;
     if (k < p.M * 9) {
@@ -116,7 +117,7 @@ __global__ void k_pcg_a(KParams p, DevState<R> d) {
 // mu += a p, r -= a ap, z = alpha r; beta = rz_new / rz; residual check
 template <typename R>
 __global__ void k_pcg_b(KParams p, DevState<R> d) {
-    if (d.scal[S_DONE] != 0.0) return;
+    if (d.flags[1]) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const double al = d.scal[S_ALPHA];
     double rz = 0, rr = 0;
@@ -136,14 +137,17 @@ __global__ void k_pcg_b(KParams p, DevState<R> d) {
         const double res = sqrt(trr / (p.M * 3)) * 4.80321;
         d.scal[S_RES] = res;
         d.scal[S_IT] += 1.0;
-        if (res < d.scal[S_TOL]) d.scal[S_DONE] = 1.0;
+        if (res < d.scal[S_TOL]) {
+            d.scal[S_DONE] = 1.0;
+            d.flags[1] = 1;
+        }
     }
 }
 
 // p = z + beta p ; clear the field accumulator for the next product
 template <typename R>
 __global__ void k_pcg_c(KParams p, DevState<R> d) {
-    if (d.scal[S_DONE] != 0.0) return;
+    if (d.flags[1]) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= p.M * 9) return;
     const double pk = d.zv[k] + d.scal[S_BETA] * d.pv[k];
@@ -160,7 +164,8 @@ __global__ void k_begin(double *scal, int *flags, double tol_D) {
     __syncthreads();
     if (threadIdx.x == 0) {
         scal[S_TOL] = tol_D;
-        *flags = 0;
+        flags[0] = 0;   // error flags
+        flags[1] = 0;   // PCG converged (integer copy of scal[S_DONE] for the loop kernels)
     }
 }
 void launch_begin(double *scal, int *flags, double tol_D, Launch L) {
@@ -229,107 +234,123 @@ __device__ inline void frame_vjp(V3<double> zv, V3<double> xv, V3<double> gx, V3
     gzv = (1.0 / nz) * (gz - dot(gz, ez) * ez);
 }
 
+// Four lanes per molecule.  Lane f < 3 carries the multipole sensitivities
+// of the sites in frame f (frame 0: O and the lone pairs; frame 1: H1, M1;
+// frame 2: H2, M2) back through that frame's construction; lane 3 takes the
+// point gradients (lone-pair charge-transfer term, V_int chain rule,
+// midpoints, lone-pair carrier).  The four partial atom gradients are summed
+// with shuffles.
 template <typename R>
-__global__ void k_finalize(KParams p, DevState<R> d, double *forces) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= p.M) return;
-    const double *x = d.pos + m * 9;
-    const V3<double> O = mk(x[0], x[1], x[2]), H1 = mk(x[3], x[4], x[5]), H2 = mk(x[6], x[7], x[8]);
-    V3<double> X[NP];
-    points_d(p, d, m, X);
-    V3<double> G[NP];
-    for (int k = 0; k < NP; ++k)
-        G[k] = mk(d.gpt[(m * NP + k) * 3], d.gpt[(m * NP + k) * 3 + 1], d.gpt[(m * NP + k) * 3 + 2]);
-    // lone pairs: charge-transfer dependence through their potential
-    for (int l = 0; l < 2; ++l) {
-        const double lq = d.lam[m * 2 + l];
-        G[5 + l] = G[5 + l] + lq * mk(d.dvlp[(m * 2 + l) * 3], d.dvlp[(m * 2 + l) * 3 + 1], d.dvlp[(m * 2 + l) * 3 + 2]);
-    }
-    // charge-transfer dependence through the intramolecular potentials V_int(O, H1, H2)
-    for (int a = 0; a < 3; ++a) {
-        const double k = d.kap[m * 3 + a];
-        if (k == 0.0) continue;
-        for (int s = 0; s < NS; ++s) {
-            if (s == a) continue;
-            const V3<double> dd = X[a] - X[s];
-            const double r = sqrt(dot(dd, dd));
-            const double qs = (double)d.gmp[(m * NS + s) * NMP];
-            const double c = k * p.ke * qs / (r * r * r);
-            G[a] = G[a] - c * dd;
-            G[s] = G[s] + c * dd;
-        }
-    }
-    // midpoints
-    V3<double> gO = G[0] + 0.5 * (G[3] + G[4]);
-    V3<double> gH1 = G[1] + 0.5 * G[3];
-    V3<double> gH2 = G[2] + 0.5 * G[4];
-    // frames: gradients of the axes from the multipole sensitivities
-    const V3<double> r1 = H1 - O, r2 = H2 - O;
-    const double n1 = sqrt(dot(r1, r1)), n2 = sqrt(dot(r2, r2));
-    const V3<double> u1 = (1.0 / n1) * r1, u2 = (1.0 / n2) * r2;
-    V3<double> zv[3] = {u1 + u2, O - H1, O - H2};
-    V3<double> xv[3] = {r1, H2 - H1, H1 - H2};
-    V3<double> E[3][3];
-    for (int f = 0; f < 3; ++f) frame_d2(zv[f], xv[f], E[f][0], E[f][1], E[f][2]);
-    V3<double> gE[3][3];
-    for (int f = 0; f < 3; ++f)
-        for (int k = 0; k < 3; ++k) gE[f][k] = mk(0.0, 0.0, 0.0);
-    const int fr_of[5] = {0, 1, 2, 1, 2};
-    for (int s = 0; s < NS; ++s) {
-        const int f = fr_of[s];
-        const double *ml = d.mp_local + (m * NS + s) * NMP;
-        const V3<double> gmu = mk(d.gmu[(m * NS + s) * 3], d.gmu[(m * NS + s) * 3 + 1], d.gmu[(m * NS + s) * 3 + 2]);
-        const double *gt6 = d.gth + (m * NS + s) * 6;
-        const Sym<double> D{gt6[0], gt6[1], gt6[2], gt6[3], gt6[4], gt6[5]};
-        const double tl[3][3] = {{ml[4], ml[7], ml[8]}, {ml[7], ml[5], ml[9]}, {ml[8], ml[9], ml[6]}};
-        for (int k = 0; k < 3; ++k) {
-            gE[f][k] = gE[f][k] + ml[1 + k] * gmu;
-            V3<double> acc = mk(0.0, 0.0, 0.0);
-            for (int l = 0; l < 3; ++l) acc = acc + tl[k][l] * E[f][l];
-            gE[f][k] = gE[f][k] + 2.0 * symv(D, acc);
-        }
-    }
-    // lone pairs: X = O + d (-c z_O +/- s y_O)
-    for (int l = 0; l < 2; ++l) {
-        const double sg = l == 0 ? 1.0 : -1.0;
-        gO = gO + G[5 + l];
-        gE[0][2] = gE[0][2] + (-p.d_lp * p.lp_cos) * G[5 + l];
-        gE[0][1] = gE[0][1] + (sg * p.d_lp * p.lp_sin) * G[5 + l];
-    }
-    // back through the three frames
-    for (int f = 0; f < 3; ++f) {
-        V3<double> gzv, gxv;
-        frame_vjp(zv[f], xv[f], gE[f][0], gE[f][1], gE[f][2], gzv, gxv);
-        if (f == 0) {
-            // zv = u1 + u2, u_k = r_k/|r_k|; xv = r1
-            const V3<double> gr1 = (1.0 / n1) * (gzv - dot(gzv, u1) * u1) + gxv;
-            const V3<double> gr2 = (1.0 / n2) * (gzv - dot(gzv, u2) * u2);
-            gH1 = gH1 + gr1;
-            gH2 = gH2 + gr2;
-            gO = gO - gr1 - gr2;
-        } else if (f == 1) {
-            // zv = O - H1, xv = H2 - H1
-            gO = gO + gzv;
-            gH1 = gH1 - gzv - gxv;
-            gH2 = gH2 + gxv;
+__global__ void __launch_bounds__(128) k_finalize(KParams p, DevState<R> d, double *forces) {
+    const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = gidx >> 2, t = gidx & 3;
+    const bool live = m < p.M;
+    V3<double> gO = mk(0.0, 0.0, 0.0), gH1 = gO, gH2 = gO;
+    if (live) {
+        const double *x = d.pos + m * 9;
+        const V3<double> O = mk(x[0], x[1], x[2]), H1 = mk(x[3], x[4], x[5]), H2 = mk(x[6], x[7], x[8]);
+        const V3<double> r1 = H1 - O, r2 = H2 - O;
+        const double n1 = sqrt(dot(r1, r1)), n2 = sqrt(dot(r2, r2));
+        const V3<double> u1 = (1.0 / n1) * r1, u2 = (1.0 / n2) * r2;
+        auto gpt = [&](int k) {
+            return mk(d.gpt[(m * NP + k) * 3], d.gpt[(m * NP + k) * 3 + 1], d.gpt[(m * NP + k) * 3 + 2]);
+        };
+        // lone-pair point gradient including the charge-transfer dependence through its potential
+        auto glp = [&](int l) {
+            const double lq = d.lam[m * 2 + l];
+            return gpt(5 + l) +
+                   lq * mk(d.dvlp[(m * 2 + l) * 3], d.dvlp[(m * 2 + l) * 3 + 1], d.dvlp[(m * 2 + l) * 3 + 2]);
+        };
+        if (t < 3) {
+            const int f = t;
+            const V3<double> zv = f == 0 ? u1 + u2 : (f == 1 ? O - H1 : O - H2);
+            const V3<double> xv = f == 0 ? r1 : (f == 1 ? H2 - H1 : H1 - H2);
+            V3<double> E[3];
+            frame_d2(zv, xv, E[0], E[1], E[2]);
+            V3<double> gE[3] = {mk(0.0, 0.0, 0.0), mk(0.0, 0.0, 0.0), mk(0.0, 0.0, 0.0)};
+            for (int s = 0; s < NS; ++s) {
+                const int fs = s == 0 ? 0 : (s == 1 || s == 3 ? 1 : 2);
+                if (fs != f) continue;
+                const double *ml = d.mp_local + (m * NS + s) * NMP;
+                const V3<double> gmu = mk(d.gmu[(m * NS + s) * 3], d.gmu[(m * NS + s) * 3 + 1], d.gmu[(m * NS + s) * 3 + 2]);
+                const double *gt6 = d.gth + (m * NS + s) * 6;
+                const Sym<double> D{gt6[0], gt6[1], gt6[2], gt6[3], gt6[4], gt6[5]};
+                const double tl[3][3] = {{ml[4], ml[7], ml[8]}, {ml[7], ml[5], ml[9]}, {ml[8], ml[9], ml[6]}};
+                for (int k = 0; k < 3; ++k) {
+                    gE[k] = gE[k] + ml[1 + k] * gmu;
+                    V3<double> acc = mk(0.0, 0.0, 0.0);
+                    for (int l = 0; l < 3; ++l) acc = acc + tl[k][l] * E[l];
+                    gE[k] = gE[k] + 2.0 * symv(D, acc);
+                }
+            }
+            if (f == 0)   // lone pairs: X = O + d (-c z_O +/- s y_O)
+                for (int l = 0; l < 2; ++l) {
+                    const double sg = l == 0 ? 1.0 : -1.0;
+                    const V3<double> G = glp(l);
+                    gE[2] = gE[2] + (-p.d_lp * p.lp_cos) * G;
+                    gE[1] = gE[1] + (sg * p.d_lp * p.lp_sin) * G;
+                }
+            V3<double> gzv, gxv;
+            frame_vjp(zv, xv, gE[0], gE[1], gE[2], gzv, gxv);
+            if (f == 0) {
+                // zv = u1 + u2, u_k = r_k/|r_k|; xv = r1
+                const V3<double> gr1 = (1.0 / n1) * (gzv - dot(gzv, u1) * u1) + gxv;
+                const V3<double> gr2 = (1.0 / n2) * (gzv - dot(gzv, u2) * u2);
+                gH1 = gr1;
+                gH2 = gr2;
+                gO = -1.0 * (gr1 + gr2);
+            } else if (f == 1) {
+                // zv = O - H1, xv = H2 - H1
+                gO = gzv;
+                gH1 = -1.0 * (gzv + gxv);
+                gH2 = gxv;
+            } else {
+                // zv = O - H2, xv = H1 - H2
+                gO = gzv;
+                gH2 = -1.0 * (gzv + gxv);
+                gH1 = gxv;
+            }
         } else {
-            // zv = O - H2, xv = H1 - H2
-            gO = gO + gzv;
-            gH2 = gH2 - gzv - gxv;
-            gH1 = gH1 + gxv;
+            V3<double> X[NP];
+            points_d(p, d, m, X);
+            V3<double> G[NS];
+            for (int k = 0; k < NS; ++k) G[k] = gpt(k);
+            // charge-transfer dependence through the intramolecular potentials V_int(O, H1, H2)
+            for (int a = 0; a < 3; ++a) {
+                const double k = d.kap[m * 3 + a];
+                if (k == 0.0) continue;
+                for (int s = 0; s < NS; ++s) {
+                    if (s == a) continue;
+                    const V3<double> dd = X[a] - X[s];
+                    const double r = sqrt(dot(dd, dd));
+                    const double qs = (double)d.gmp[(m * NS + s) * NMP];
+                    const double c = k * p.ke * qs / (r * r * r);
+                    G[a] = G[a] - c * dd;
+                    G[s] = G[s] + c * dd;
+                }
+            }
+            // midpoints and the lone pairs' carrier
+            gO = G[0] + 0.5 * (G[3] + G[4]) + glp(0) + glp(1);
+            gH1 = G[1] + 0.5 * G[3];
+            gH2 = G[2] + 0.5 * G[4];
         }
     }
-    if (forces) {
+    double v[9] = {gO.x, gO.y, gO.z, gH1.x, gH1.y, gH1.z, gH2.x, gH2.y, gH2.z};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        v[k] += __shfl_xor_sync(0xffffffffu, v[k], 1, 4);
+        v[k] += __shfl_xor_sync(0xffffffffu, v[k], 2, 4);
+    }
+    if (live && t == 0 && forces) {
         double *F = forces + m * 9;
-        F[0] = -gO.x; F[1] = -gO.y; F[2] = -gO.z;
-        F[3] = -gH1.x; F[4] = -gH1.y; F[5] = -gH1.z;
-        F[6] = -gH2.x; F[7] = -gH2.y; F[8] = -gH2.z;
+        for (int k = 0; k < 9; ++k) F[k] = -v[k];
     }
 }
 
 template <typename R>
 void launch_finalize(const KParams &p, DevState<R> &d, double *forces_out, Launch L) {
-    k_finalize<R><<<(p.M + 127) / 128, 128, 0, L.s>>>(p, d, forces_out);
+    const long long n = (long long)p.M * 4;
+    k_finalize<R><<<(unsigned)((n + 127) / 128), 128, 0, L.s>>>(p, d, forces_out);
     count(L);
 }
 

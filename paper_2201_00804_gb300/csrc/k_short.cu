@@ -1,0 +1,463 @@
+// Exchange-repulsion (Technical Appendix: S^2/R and S^2/R^2 overlap terms
+// over bond-bond, bond-lone pair and lone pair-lone pair pairs), dispersion
+// (C6/C8/C10 with damping) and exchange-dispersion.
+//
+// One warp per molecule i walks its neighbour list 32 entries at a time.
+// Every molecule pair (i, j) expands into 41 items:
+//   BB  bond O-H_kb of i with bond O-H_kc of j          4
+//   BL  bond of i with lone pair l of j                 4
+//   LB  lone pair l of i with bond of j                 4
+//   LL  lone pair of i with lone pair of j              4
+//   D   point u of i with point v of j                 25   (O, H1, H2, LP1, LP2)
+// Items inside the cutoff (per item, on the distance of its radial factor)
+// are appended to one ring queue per class in shared memory and evaluated in
+// full 32-lane rounds, so all lanes of a round do the same work.  Dispersion
+// items are pushed per point u of i to bound the queue.  Gradients go to i's
+// points only (the full list visits each pair from both sides).
+#include <cstddef>
+
+#include "sibfa_internal.cuh"
+
+namespace sibfa {
+
+// Atom-pair overlap with each p orbital measured at its own atom:
+// O = A + B cx + C cy + D cx cy, cx = cos(ux, y - x), cy = cos(uy, x - y),
+// ux = xp - x (xp an i-side point), uy fixed (j side).
+// Returns O; gx = dO/dx and gxp = dO/dxp.
+template <typename R>
+__device__ inline R overlap_i(V3<R> x, V3<R> xp, V3<R> y, V3<R> uy, R A, R B, R C, R D, V3<R> &gx, V3<R> &gxp) {
+    V3<R> du, dv, du2, dv2;
+    const R cx = cosv(xp - x, y - x, du, dv);
+    const R cy = cosv(uy, x - y, du2, dv2);
+    const R ox = B + D * cy, oy = C + D * cx;
+    gxp = ox * du;
+    gx = R(-1) * ox * (du + dv) + oy * dv2;
+    return A + B * cx + C * cy + D * cx * cy;
+}
+
+template <typename R>
+struct RepAtom {
+    R cs, cp, g, cf;
+    int kind;   // 0 = O, 1 = H, 2 = lone pair (selects the pair-type exponent coefficients)
+};
+
+// Pair-type coefficient tables copied to shared memory: items of one round
+// mix pair types, and divergent indices into the parameter bank serialise.
+struct ShortTables {
+    KParams::Coef rep_k1[3][3], rep_k2[3][3], disp_km[3][3], disp_gS[3][3][3], xd_k[3][3];
+};
+
+// Adds the overlap and exponential factor of one atom pair to O1/O2 and the
+// i-side gradients dO1/dx, dO1/dxp, dO2/dx, dO2/dxp.
+template <typename R>
+__device__ inline void rep_pair_term(V3<R> x, V3<R> xp, const RepAtom<R> &ai, V3<R> y, V3<R> uy, const RepAtom<R> &aj,
+                                     R pp, R f, const ShortTables &T, R &O1, R &O2, V3<R> &g1x, V3<R> &g1xp,
+                                     V3<R> &g2x, V3<R> &g2xp) {
+    V3<R> gx, gxp;
+    const R O = overlap_i(x, xp, y, uy, ai.cs * aj.cs, aj.cs * ai.cp * f, ai.cs * aj.cp * f, pp * ai.cp * aj.cp, gx, gxp);
+    const V3<R> v = x - y;
+    const R rr = sqrt_(dot(v, v));
+    const KParams::Coef &k1 = T.rep_k1[ai.kind][aj.kind], &k2 = T.rep_k2[ai.kind][aj.kind];
+    const R M = sqrt_(ai.g * aj.g * ai.cf * aj.cf);
+    const R S1 = M * exp_(-mulc(rr, k1)), S2 = M * exp_(-mulc(rr, k2));
+    O1 += O * S1;
+    O2 += O * S2;
+    const V3<R> drdx = (R(1) / rr) * v;
+    g1x = S1 * gx + (O * S1 * (-cval<R>(k1))) * drdx;
+    g2x = S2 * gx + (O * S2 * (-cval<R>(k2))) * drdx;
+    g1xp = S1 * gxp;
+    g2xp = S2 * gxp;
+}
+
+// E = pref (C1 O1^2 / r + C2 O2^2 / r^2): returns E and dE/dO1, dE/dO2, dE/dr.
+template <typename R>
+__device__ inline R rep_energy(R pref, R C1, R C2, R O1, R O2, R r, R &e1, R &e2, R &er) {
+    const R ri = R(1) / r;
+    e1 = pref * C1 * R(2) * O1 * ri;
+    e2 = pref * C2 * R(2) * O2 * ri * ri;
+    er = pref * (-C1 * O1 * O1 * ri * ri - R(2) * C2 * O2 * O2 * ri * ri * ri);
+    return pref * (C1 * O1 * O1 * ri + C2 * O2 * O2 * ri * ri);
+}
+
+// Queue layout (words: slot * 32 + item code)
+constexpr int SQ_BB = 0, SQ_BL = 160, SQ_LB = 320, SQ_LL = 480, SQ_D = 640;
+constexpr int SQ_CAP = 160;    // >= 31 carried + 32 lanes x 4 items
+constexpr int SQ_CAPD = 192;   // >= 31 carried + 32 lanes x 5 items (one point u of i)
+constexpr int SQ_WORDS = 1024; // also holds the FP64 reduction buffer (15 x 33 doubles)
+
+// i-side state of one warp
+template <typename R>
+struct ShortI {
+    V3<R> P[5];            // O, H1, H2, LP1, LP2 relative to O_i
+    RepAtom<R> A[3];       // O, H1, H2 of i
+    R cf[5];               // valence factors 1 - q/N of O, H1, H2 and (O's) for the lone pairs
+};
+
+template <typename R>
+struct ShortAcc {
+    V3<R> G[5];
+    Acc<R> Erep, Ed, Ex;
+};
+
+template <typename R>
+__device__ inline void addG(ShortAcc<R> &a, int k, V3<R> v) {
+#pragma unroll
+    for (int t = 0; t < 5; ++t)
+        if (t == k) a.G[t] = a.G[t] + v;
+}
+template <typename R>
+__device__ inline V3<R> selP(const ShortI<R> &I, int k) {
+    V3<R> r = I.P[0];
+#pragma unroll
+    for (int t = 1; t < 5; ++t)
+        if (t == k) r = I.P[t];
+    return r;
+}
+
+// point k (0 O, 1 H1, 2 H2, 3 LP1, 4 LP2) of neighbour j relative to O_i
+template <typename R>
+__device__ inline V3<R> qpt(const DevState<R> &d, int j, V3<R> dO, int k) {
+    const int s = k < 3 ? k : k + 2;
+    const R *o = d.off + (j * NP + s) * 3;
+    return dO + mk(o[0], o[1], o[2]);
+}
+
+template <typename R>
+__device__ inline R qcharge(const DevState<R> &d, int j, int k) { return d.gmp[(j * NS + k) * NMP]; }
+
+template <typename R>
+__device__ inline RepAtom<R> atom_j(const Scal<R> &S, const DevState<R> &d, int j, int k) {
+    const R q = qcharge(d, j, k);
+    if (k == 0) return {S.cs_o, S.cp_o, S.g_o, R(1) - q * S.inv_nval_o, 0};
+    return {S.cs_h, S.cp_h, S.g_h, R(1) - q * S.inv_nval_h, 1};
+}
+
+template <typename R>
+__device__ inline void neighbour(const DevState<R> &d, int i, int slot, int &j, V3<R> &dO) {
+    j = d.nbr[i * MAXN + slot];
+    const R *dp = d.ndo + ((size_t)i * MAXN + slot) * 3;
+    dO = mk(dp[0], dp[1], dp[2]);
+}
+
+// ---- item evaluation -------------------------------------------------------
+
+template <typename R>
+__device__ void item_bb(const Scal<R> &S, const ShortTables &T, const DevState<R> &d, const ShortI<R> &I, int i,
+                        int word, ShortAcc<R> &a) {
+    const int slot = word >> 5, c = word & 31;
+    const int kb = 1 + (c >> 1), kc = 1 + (c & 1);
+    int j;
+    V3<R> dO;
+    neighbour(d, i, slot, j, dO);
+    const V3<R> P0 = I.P[0], Pb = kb == 1 ? I.P[1] : I.P[2];
+    const RepAtom<R> Ab = kb == 1 ? I.A[1] : I.A[2];
+    const V3<R> Q0 = dO, Qc = qpt(d, j, dO, kc);
+    const RepAtom<R> AjO = atom_j(S, d, j, 0), Ajc = atom_j(S, d, j, kc);
+    const V3<R> dm = R(0.5) * (P0 + Pb) - R(0.5) * (Q0 + Qc);
+    const R rm = sqrt_(dot(dm, dm));
+    R O1 = 0, O2 = 0;
+    const V3<R> z = mk(R(0), R(0), R(0));
+    V3<R> g1a = z, g1b = z, g2a = z, g2b = z;   // gradients at O_i (a) and H_kb (b)
+#pragma unroll 1
+    for (int uv = 0; uv < 4; ++uv) {
+        const bool u = uv >> 1, v = uv & 1;
+        V3<R> t1x, t1xp, t2x, t2xp;
+        rep_pair_term(u ? Pb : P0, u ? P0 : Pb, u ? Ab : I.A[0], v ? Qc : Q0, v ? Q0 - Qc : Qc - Q0, v ? Ajc : AjO,
+                      R(2), S.rep_f, T, O1, O2, t1x, t1xp, t2x, t2xp);
+        if (!u) { g1a = g1a + t1x; g2a = g2a + t2x; g1b = g1b + t1xp; g2b = g2b + t2xp; }
+        else { g1b = g1b + t1x; g2b = g2b + t2x; g1a = g1a + t1xp; g2a = g2a + t2xp; }
+    }
+    R e1, e2, er;
+    a.Erep.add(R(0.5) * rep_energy(S.occ * S.occ, S.rep_c1, S.rep_c2, O1, O2, rm, e1, e2, er));
+    const V3<R> drm = (R(0.5) / rm) * dm;
+    a.G[0] = a.G[0] + e1 * g1a + e2 * g2a + er * drm;
+    addG(a, kb, e1 * g1b + e2 * g2b + er * drm);
+}
+
+template <typename R>
+__device__ void item_bl(const Scal<R> &S, const ShortTables &T, const DevState<R> &d, const ShortI<R> &I, int i,
+                        int word, ShortAcc<R> &a) {
+    const int slot = word >> 5, c = word & 31;
+    const int kb = 1 + (c >> 1), l = c & 1;
+    int j;
+    V3<R> dO;
+    neighbour(d, i, slot, j, dO);
+    const V3<R> P0 = I.P[0], Pb = kb == 1 ? I.P[1] : I.P[2];
+    const RepAtom<R> Ab = kb == 1 ? I.A[1] : I.A[2];
+    const V3<R> Ql = qpt(d, j, dO, 3 + l);
+    const RepAtom<R> Alp = {S.cs_lp, S.cp_lp, S.g_o, R(1) - S.nlp * S.inv_nval_o, 2};
+    const V3<R> dm = R(0.5) * (P0 + Pb) - Ql;
+    const R rr = sqrt_(dot(dm, dm));
+    R O1 = 0, O2 = 0;
+    const V3<R> z = mk(R(0), R(0), R(0));
+    V3<R> g1a = z, g1b = z, g2a = z, g2b = z;
+#pragma unroll 1
+    for (int u = 0; u < 2; ++u) {
+        V3<R> t1x, t1xp, t2x, t2xp;
+        rep_pair_term(u ? Pb : P0, u ? P0 : Pb, u ? Ab : I.A[0], dO, Ql - dO, Alp, S.rep_f, S.rep_f, T, O1, O2, t1x,
+                      t1xp, t2x, t2xp);
+        if (!u) { g1a = g1a + t1x; g2a = g2a + t2x; g1b = g1b + t1xp; g2b = g2b + t2xp; }
+        else { g1b = g1b + t1x; g2b = g2b + t2x; g1a = g1a + t1xp; g2a = g2a + t2xp; }
+    }
+    R e1, e2, er;
+    a.Erep.add(R(0.5) * rep_energy(S.occ * S.nlp, S.rep_c1, S.rep_c2, O1, O2, rr, e1, e2, er));
+    const V3<R> drm = (R(0.5) / rr) * dm;
+    a.G[0] = a.G[0] + e1 * g1a + e2 * g2a + er * drm;
+    addG(a, kb, e1 * g1b + e2 * g2b + er * drm);
+}
+
+// lone pair of i (a pseudo-atom at its carrier O_i) with a bond of j
+template <typename R>
+__device__ void item_lb(const Scal<R> &S, const ShortTables &T, const DevState<R> &d, const ShortI<R> &I, int i,
+                        int word, ShortAcc<R> &a) {
+    const int slot = word >> 5, c = word & 31;
+    const int l = c >> 1, kc = 1 + (c & 1);
+    int j;
+    V3<R> dO;
+    neighbour(d, i, slot, j, dO);
+    const V3<R> P0 = I.P[0], Pl = l ? I.P[4] : I.P[3];
+    const V3<R> Q0 = dO, Qc = qpt(d, j, dO, kc);
+    const RepAtom<R> AjO = atom_j(S, d, j, 0), Ajc = atom_j(S, d, j, kc);
+    const RepAtom<R> Alp = {S.cs_lp, S.cp_lp, S.g_o, R(1) - S.nlp * S.inv_nval_o, 2};
+    const V3<R> dm = Pl - R(0.5) * (Q0 + Qc);
+    const R rr = sqrt_(dot(dm, dm));
+    R O1 = 0, O2 = 0;
+    const V3<R> z = mk(R(0), R(0), R(0));
+    V3<R> g1c = z, g1l = z, g2c = z, g2l = z;
+#pragma unroll 1
+    for (int v = 0; v < 2; ++v) {
+        V3<R> t1x, t1xp, t2x, t2xp;
+        rep_pair_term(P0, Pl, Alp, v ? Qc : Q0, v ? Q0 - Qc : Qc - Q0, v ? Ajc : AjO, S.rep_f, S.rep_f, T, O1, O2,
+                      t1x, t1xp, t2x, t2xp);
+        g1c = g1c + t1x; g2c = g2c + t2x; g1l = g1l + t1xp; g2l = g2l + t2xp;
+    }
+    R e1, e2, er;
+    a.Erep.add(R(0.5) * rep_energy(S.occ * S.nlp, S.rep_c1, S.rep_c2, O1, O2, rr, e1, e2, er));
+    a.G[0] = a.G[0] + e1 * g1c + e2 * g2c;
+    addG(a, 3 + l, e1 * g1l + e2 * g2l + (er / rr) * dm);
+}
+
+// lone pair - lone pair, angles toward the other lone pair's position
+template <typename R>
+__device__ void item_ll(const Scal<R> &S, const ShortTables &T, const DevState<R> &d, const ShortI<R> &I, int i,
+                        int word, ShortAcc<R> &a) {
+    const int slot = word >> 5, c = word & 31;
+    const int l1 = c >> 1, l2 = c & 1;
+    int j;
+    V3<R> dO;
+    neighbour(d, i, slot, j, dO);
+    const V3<R> P0 = I.P[0], Ip = l1 ? I.P[4] : I.P[3];
+    const V3<R> Jp = qpt(d, j, dO, 3 + l2);
+    const V3<R> dIJ = Ip - Jp;
+    const R rr = sqrt_(dot(dIJ, dIJ));
+    V3<R> dui, dvi, duj, dvj;
+    const R ci = cosv(Ip - P0, Jp - P0, dui, dvi);   // depends on I and A
+    const R cj = cosv(Jp - dO, Ip - dO, duj, dvj);   // depends on I
+    const R cs = S.cs_lp, cp = S.cp_lp, f = S.rep_f;
+    const R O = cs * cs + cs * cp * f * cj + cs * cp * f * ci + R(2) * cp * cp * ci * cj;
+    const R dci = cs * cp * f + R(2) * cp * cp * cj, dcj = cs * cp * f + R(2) * cp * cp * ci;
+    const V3<R> dOdI = dci * dui + dcj * dvj;
+    const V3<R> dOdA = R(-1) * dci * (dui + dvi);
+    const V3<R> dAB = P0 - dO;
+    const R rab = sqrt_(dot(dAB, dAB));
+    const R M = S.g_o * (R(1) - S.nlp * S.inv_nval_o);
+    const R S1 = M * exp_(-mulc(rab, T.rep_k1[2][2])), S2 = M * exp_(-mulc(rab, T.rep_k2[2][2]));
+    const R O1 = O * S1, O2 = O * S2;
+    R e1, e2, er;
+    a.Erep.add(R(0.5) * rep_energy(S.nlp * S.nlp, S.rep_c1, S.rep_c2, O1, O2, rr, e1, e2, er));
+    const V3<R> drab = (R(1) / rab) * dAB;
+    a.G[0] = a.G[0] + (e1 * S1 + e2 * S2) * dOdA +
+             (e1 * O1 * (-cval<R>(T.rep_k1[2][2])) + e2 * O2 * (-cval<R>(T.rep_k2[2][2]))) * drab;
+    addG(a, 3 + l1, (e1 * S1 + e2 * S2) * dOdI + (er / rr) * dIJ);
+}
+
+// dispersion and exchange-dispersion of point u of i with point v of j
+template <typename R>
+__device__ void item_d(const KParams &p, const Scal<R> &S, const ShortTables &T, const DevState<R> &d,
+                       const ShortI<R> &I, int i, int word, ShortAcc<R> &a) {
+    const int slot = word >> 5, c = word & 31;
+    const int u = c / 5, v = c % 5;
+    int j;
+    V3<R> dO;
+    neighbour(d, i, slot, j, dO);
+    const V3<R> dv = selP(I, u) - qpt(d, j, dO, v);
+    const R r2 = dot(dv, dv);
+    const R ri = rsqrt_(r2), r = r2 * ri;
+    const int ku = u == 0 ? 0 : (u < 3 ? 1 : 2), kv = v == 0 ? 0 : (v < 3 ? 1 : 2);
+    const R m = mulc(r, T.disp_km[ku][kv]), mi = R(1) / m;
+    // exp(-gamma_n d) with d = S/r - 1: argument gamma_n - (gamma_n S)/r
+    const R a6 = mulc(ri, T.disp_gS[0][ku][kv]), a8 = mulc(ri, T.disp_gS[1][ku][kv]),
+            a10 = mulc(ri, T.disp_gS[2][ku][kv]);
+    const R m2i = mi * mi, m6i = m2i * m2i * m2i, m8i = m6i * m2i, m10i = m8i * m2i;
+    const R e6 = S.c6 * exp_(S.g6 - a6) * m6i;
+    const R e8 = S.c8 * exp_(S.g8 - a8) * m8i;
+    const R e10 = S.c10 * exp_(S.g10 - a10) * m10i;
+    const R fsum = e6 + e8 + e10;
+    const R dfdr = e6 * ((a6 - R(6)) * ri) + e8 * ((a8 - R(8)) * ri) + e10 * ((a10 - R(10)) * ri);
+    const bool lu = u >= 3, lv = v >= 3;
+    const R bu = betap<R>(p, u), bv = betap<R>(p, v);
+    const R nlp = S.nlp;
+    R pref, xc;
+    if (!lu && !lv) { pref = -bu * bv; xc = S.xd_c1; }
+    else if (lu && lv) { pref = -nlp * nlp * R(0.25); xc = nlp * nlp * R(0.25) * S.xd_c2; }
+    else { pref = -S.delta * R(0.5); xc = nlp * R(0.5) * S.xd_c3; }
+    const R cfj = R(1) - qcharge(d, j, v < 3 ? v : 0) * (v == 1 || v == 2 ? S.inv_nval_h : S.inv_nval_o);
+    R cfi = I.cf[0];
+#pragma unroll
+    for (int t = 1; t < 5; ++t)
+        if (t == u) cfi = I.cf[t];
+    const R K = bu * bv * cfi * cfj;
+    const R ex = xc * K * exp_(-mulc(r, T.xd_k[ku][kv]));
+    a.Ed.add(R(0.5) * pref * fsum);
+    a.Ex.add(R(0.5) * ex);
+    const R dEdr = pref * dfdr - cval<R>(T.xd_k[ku][kv]) * ex;
+    addG(a, u, (dEdr * ri) * dv);
+}
+
+// ---- kernel ------------------------------------------------------------------
+
+template <typename R, bool PER>
+__global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
+    __shared__ ShortTables T;
+    __shared__ int qbuf[4][SQ_WORDS];
+    static_assert(SQ_D + SQ_CAPD <= SQ_WORDS && 15 * 33 * sizeof(R) <= SQ_WORDS * sizeof(int), "queue layout");
+    static_assert(offsetof(KParams, xd_k) - offsetof(KParams, rep_k1) == offsetof(ShortTables, xd_k) &&
+                      sizeof(ShortTables) == sizeof(KParams::Coef) * (9 * 4 + 27),
+                  "coefficient tables are copied as one block");
+    {
+        const KParams::Coef *src = &p.rep_k1[0][0];
+        KParams::Coef *dst = &T.rep_k1[0][0];
+        for (int k = threadIdx.x; k < (int)(sizeof(ShortTables) / sizeof(KParams::Coef)); k += blockDim.x) {
+            // rep_k1, rep_k2, disp_km, disp_gS, xd_k are consecutive in KParams and in ShortTables
+            dst[k] = src[k];
+        }
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 4 + w;
+    if (i >= p.M) return;
+    int *q = qbuf[w];
+    const Scal<R> &S = sc<R>(p);
+    const R rc2 = S.rc2;
+    ShortI<R> I;
+    for (int k = 0; k < 3; ++k) I.P[k] = my_pt(d, i, k);
+    I.P[3] = my_pt(d, i, 5);
+    I.P[4] = my_pt(d, i, 6);
+    {
+        const R q0 = d.gmp[(i * NS) * NMP], q1 = d.gmp[(i * NS + 1) * NMP], q2 = d.gmp[(i * NS + 2) * NMP];
+        I.A[0] = {S.cs_o, S.cp_o, S.g_o, R(1) - q0 * S.inv_nval_o, 0};
+        I.A[1] = {S.cs_h, S.cp_h, S.g_h, R(1) - q1 * S.inv_nval_h, 1};
+        I.A[2] = {S.cs_h, S.cp_h, S.g_h, R(1) - q2 * S.inv_nval_h, 1};
+        I.cf[0] = I.A[0].cf;
+        I.cf[1] = I.A[1].cf;
+        I.cf[2] = I.A[2].cf;
+        I.cf[3] = I.A[0].cf;
+        I.cf[4] = I.A[0].cf;
+    }
+    ShortAcc<R> acc;
+    for (int k = 0; k < 5; ++k) acc.G[k] = mk(R(0), R(0), R(0));
+    int h[5] = {0, 0, 0, 0, 0}, t[5] = {0, 0, 0, 0, 0};   // heads and tails: BB, BL, LB, LL, D
+    const int nn = d.nnbr[i];
+    for (int base = 0;; base += 32) {
+        const bool flush = base >= nn;
+        const int slot = base + lane;
+        const bool live = slot < nn;
+        int j = 0;
+        V3<R> dO = mk(R(0), R(0), R(0));
+        if (live) neighbour(d, i, slot, j, dO);
+        // stage 0: repulsion items; stages 1-5: dispersion items of point u = stage - 1
+        for (int stage = 0; stage < 6; ++stage) {
+            if (stage == 0) {
+                unsigned bb = 0, bl = 0, lb = 0, ll = 0;
+                if (live) {
+                    const V3<R> Q1 = qpt(d, j, dO, 1), Q2 = qpt(d, j, dO, 2);
+                    const V3<R> L1 = qpt(d, j, dO, 3), L2 = qpt(d, j, dO, 4);
+                    const V3<R> mi1 = R(0.5) * (I.P[0] + I.P[1]), mi2 = R(0.5) * (I.P[0] + I.P[2]);
+                    const V3<R> mj1 = R(0.5) * (dO + Q1), mj2 = R(0.5) * (dO + Q2);
+                    auto in = [&](V3<R> x) { return !PER || dot(x, x) < rc2; };
+                    bb = in(mi1 - mj1) | in(mi1 - mj2) << 1 | in(mi2 - mj1) << 2 | in(mi2 - mj2) << 3;
+                    bl = in(mi1 - L1) | in(mi1 - L2) << 1 | in(mi2 - L1) << 2 | in(mi2 - L2) << 3;
+                    lb = in(I.P[3] - mj1) | in(I.P[3] - mj2) << 1 | in(I.P[4] - mj1) << 2 | in(I.P[4] - mj2) << 3;
+                    ll = in(I.P[3] - L1) | in(I.P[3] - L2) << 1 | in(I.P[4] - L1) << 2 | in(I.P[4] - L2) << 3;
+                }
+                const unsigned bits[4] = {bb, bl, lb, ll};
+                const int off[4] = {SQ_BB, SQ_BL, SQ_LB, SQ_LL};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    int n;
+                    int pos = warp_excl_scan(__popc(bits[c]), lane, n);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if ((bits[c] >> k) & 1u) q[off[c] + (t[c] + pos++) % SQ_CAP] = slot * 32 + k;
+                    t[c] += n;
+                }
+            } else {
+                const int u = stage - 1;
+                unsigned bits = 0;
+                if (live) {
+                    const V3<R> Pu = selP(I, u);
+#pragma unroll
+                    for (int v = 0; v < 5; ++v) {
+                        const V3<R> x = Pu - qpt(d, j, dO, v);
+                        if (!PER || dot(x, x) < rc2) bits |= 1u << v;
+                    }
+                }
+                int n;
+                int pos = warp_excl_scan(__popc(bits), lane, n);
+#pragma unroll
+                for (int v = 0; v < 5; ++v)
+                    if ((bits >> v) & 1u) q[SQ_D + (t[4] + pos++) % SQ_CAPD] = slot * 32 + u * 5 + v;
+                t[4] += n;
+            }
+            __syncwarp();
+            const bool last = flush && stage == 5;
+            while (t[0] - h[0] >= 32 || (last && t[0] > h[0])) {
+                if (lane < t[0] - h[0]) item_bb(S, T, d, I, i, q[SQ_BB + (h[0] + lane) % SQ_CAP], acc);
+                h[0] += min(32, t[0] - h[0]);
+            }
+            while (t[1] - h[1] >= 32 || (last && t[1] > h[1])) {
+                if (lane < t[1] - h[1]) item_bl(S, T, d, I, i, q[SQ_BL + (h[1] + lane) % SQ_CAP], acc);
+                h[1] += min(32, t[1] - h[1]);
+            }
+            while (t[2] - h[2] >= 32 || (last && t[2] > h[2])) {
+                if (lane < t[2] - h[2]) item_lb(S, T, d, I, i, q[SQ_LB + (h[2] + lane) % SQ_CAP], acc);
+                h[2] += min(32, t[2] - h[2]);
+            }
+            while (t[3] - h[3] >= 32 || (last && t[3] > h[3])) {
+                if (lane < t[3] - h[3]) item_ll(S, T, d, I, i, q[SQ_LL + (h[3] + lane) % SQ_CAP], acc);
+                h[3] += min(32, t[3] - h[3]);
+            }
+            while (t[4] - h[4] >= 32 || (last && t[4] > h[4])) {
+                if (lane < t[4] - h[4]) item_d(p, S, T, d, I, i, q[SQ_D + (h[4] + lane) % SQ_CAPD], acc);
+                h[4] += min(32, t[4] - h[4]);
+            }
+            __syncwarp();
+        }
+        if (flush) break;
+    }
+    // lane reduction; points 3, 4 are the lone pairs (point slots 5, 6)
+    const R vals[15] = {acc.G[0].x, acc.G[0].y, acc.G[0].z, acc.G[1].x, acc.G[1].y, acc.G[1].z,
+                        acc.G[2].x, acc.G[2].y, acc.G[2].z, acc.G[3].x, acc.G[3].y, acc.G[3].z,
+                        acc.G[4].x, acc.G[4].y, acc.G[4].z};
+    const R s = warp_transpose_sum<R, 15>(vals, reinterpret_cast<R *>(q), lane);
+    const int pt = lane / 3;
+    if (lane < 15) d.gpt[(i * NP + (pt < 3 ? pt : pt + 2)) * 3 + lane % 3] += double(s);
+    const double er_ = warp_sum_acc(acc.Erep), ed_ = warp_sum_acc(acc.Ed), ex_ = warp_sum_acc(acc.Ex);
+    if (lane == 0) {
+        d.epart[i * NTERM + T_REP] += er_;
+        d.epart[i * NTERM + T_DISP] += ed_;
+        d.epart[i * NTERM + T_XDISP] += ex_;
+    }
+}
+
+template <typename R>
+void launch_short(const KParams &p, DevState<R> &d, Launch L) {
+    if (p.periodic) k_short<R, true><<<(p.M + 3) / 4, 128, 0, L.s>>>(p, d);
+    else k_short<R, false><<<(p.M + 3) / 4, 128, 0, L.s>>>(p, d);
+    count(L);
+}
+
+template void launch_short<float>(const KParams &, DevState<float> &, Launch);
+template void launch_short<double>(const KParams &, DevState<double> &, Launch);
+
+}  // namespace sibfa

@@ -14,103 +14,141 @@ __device__ inline void frame_d(V3<double> zv, V3<double> xv, V3<double> &ex, V3<
     ey = cross(ez, ex);
 }
 
+// Eight lanes per molecule: every lane builds the three frames (FP64); lane
+// t < 7 owns point t (offset, SPME grid coordinates), lane t < 5 rotates the
+// multipoles of site t, lane t < 3 forms V_int of atom t, lane 7 wraps O, and
+// the lanes share the clearing of the per-molecule accumulators.
 template <typename R>
-__global__ void k_sites(KParams p, DevState<R> d) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= p.M) return;
-    const double *x = d.pos + m * 9;
-    V3<double> O = mk(x[0], x[1], x[2]), H1 = mk(x[3], x[4], x[5]), H2 = mk(x[6], x[7], x[8]);
-    V3<double> r1 = H1 - O, r2 = H2 - O;
-    V3<double> u1 = (1.0 / sqrt(dot(r1, r1))) * r1, u2 = (1.0 / sqrt(dot(r2, r2))) * r2;
-    V3<double> F[3][3];  // frames: [frame][axis]
-    frame_d(u1 + u2, r1, F[0][0], F[0][1], F[0][2]);
-    frame_d(O - H1, H2 - H1, F[1][0], F[1][1], F[1][2]);
-    frame_d(O - H2, H1 - H2, F[2][0], F[2][1], F[2][2]);
-    const int fr_of[5] = {0, 1, 2, 1, 2};
-    V3<double> offs[NP];
-    offs[0] = mk(0.0, 0.0, 0.0);
-    offs[1] = r1;
-    offs[2] = r2;
-    offs[3] = 0.5 * r1;
-    offs[4] = 0.5 * r2;
-    offs[5] = p.d_lp * ((-p.lp_cos) * F[0][2] + p.lp_sin * F[0][1]);
-    offs[6] = p.d_lp * ((-p.lp_cos) * F[0][2] - p.lp_sin * F[0][1]);
+__global__ void __launch_bounds__(128) k_sites(KParams p, DevState<R> d) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = g >> 3, t = g & 7;
+    const bool live = m < p.M;
     float ext = 0.f;
-    for (int k = 0; k < NP; ++k) {
-        d.off[(m * NP + k) * 3 + 0] = R(offs[k].x);
-        d.off[(m * NP + k) * 3 + 1] = R(offs[k].y);
-        d.off[(m * NP + k) * 3 + 2] = R(offs[k].z);
-        ext = fmaxf(ext, (float)sqrt(dot(offs[k], offs[k])));
-    }
-    atomicMax((int *)d.ext, __float_as_int(ext));
-    // O wrapped into the box in single precision (candidate tests of the list build)
-    for (int k = 0; k < 3; ++k) {
-        double v = x[k];
-        if (p.periodic) v -= p.box[k] * floor(v / p.box[k]);
-        d.ofw[m * 3 + k] = (float)v;
-    }
-    const double *ml = d.mp_local + m * NS * NMP;
-    double qs[NS];
-    for (int s = 0; s < NS; ++s) {
-        const double *l = ml + s * NMP;
-        const V3<double> *e = F[fr_of[s]];
-        V3<double> mu = l[1] * e[0] + l[2] * e[1] + l[3] * e[2];
-        // Theta = R Th_l R^T ; Th_l symmetric (xx yy zz xy xz yz)
-        double tl[3][3] = {{l[4], l[7], l[8]}, {l[7], l[5], l[9]}, {l[8], l[9], l[6]}};
-        double Rm[3][3] = {{e[0].x, e[1].x, e[2].x}, {e[0].y, e[1].y, e[2].y}, {e[0].z, e[1].z, e[2].z}};
-        double A[3][3];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) {
-                double acc = 0;
-                for (int c = 0; c < 3; ++c) acc += Rm[a][c] * tl[c][b];
-                A[a][b] = acc;
+    if (live) {
+        const double *x = d.pos + m * 9;
+        V3<double> O = mk(x[0], x[1], x[2]), H1 = mk(x[3], x[4], x[5]), H2 = mk(x[6], x[7], x[8]);
+        V3<double> r1 = H1 - O, r2 = H2 - O;
+        V3<double> u1 = (1.0 / sqrt(dot(r1, r1))) * r1, u2 = (1.0 / sqrt(dot(r2, r2))) * r2;
+        V3<double> F[3][3];  // frames: [frame][axis]
+        frame_d(u1 + u2, r1, F[0][0], F[0][1], F[0][2]);
+        frame_d(O - H1, H2 - H1, F[1][0], F[1][1], F[1][2]);
+        frame_d(O - H2, H1 - H2, F[2][0], F[2][1], F[2][2]);
+        V3<double> offs[NP];
+        offs[0] = mk(0.0, 0.0, 0.0);
+        offs[1] = r1;
+        offs[2] = r2;
+        offs[3] = 0.5 * r1;
+        offs[4] = 0.5 * r2;
+        offs[5] = p.d_lp * ((-p.lp_cos) * F[0][2] + p.lp_sin * F[0][1]);
+        offs[6] = p.d_lp * ((-p.lp_cos) * F[0][2] - p.lp_sin * F[0][1]);
+        const double *ml = d.mp_local + m * NS * NMP;
+        if (t < NP) {
+            V3<double> o = offs[0];
+#pragma unroll
+            for (int k = 1; k < NP; ++k)
+                if (k == t) o = offs[k];
+            d.off[(m * NP + t) * 3 + 0] = R(o.x);
+            d.off[(m * NP + t) * 3 + 1] = R(o.y);
+            d.off[(m * NP + t) * 3 + 2] = R(o.z);
+            ext = (float)sqrt(dot(o, o));
+            // SPME grid coordinates of the point (FP64 once per step; the spread
+            // and gather kernels build their B-spline weights from the fraction)
+            if (p.periodic) {
+                const double pk[3] = {O.x + o.x, O.y + o.y, O.z + o.z};
+                for (int c = 0; c < 3; ++c) {
+                    const double u = pk[c] * p.ibox[c] * (double)p.K[c];
+                    const double fl = floor(u);
+                    int b = (int)fl % p.K[c];
+                    if (b < 0) b += p.K[c];
+                    d.sbase[(m * NP + t) * 3 + c] = b;
+                    d.sfrac[(m * NP + t) * 3 + c] = R(u - fl);
+                }
             }
-        double T[3][3];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) {
-                double acc = 0;
-                for (int c = 0; c < 3; ++c) acc += A[a][c] * Rm[b][c];
-                T[a][b] = acc;
-            }
-        R *g = d.gmp + (m * NS + s) * NMP;
-        g[0] = R(l[0]);
-        g[1] = R(mu.x);
-        g[2] = R(mu.y);
-        g[3] = R(mu.z);
-        g[4] = R(T[0][0]);
-        g[5] = R(T[1][1]);
-        g[6] = R(T[2][2]);
-        g[7] = R(T[0][1]);
-        g[8] = R(T[0][2]);
-        g[9] = R(T[1][2]);
-        qs[s] = l[0];
-    }
-    // intramolecular potential on O, H1, H2 from the charges of the other sites
-    for (int a = 0; a < 3; ++a) {
-        double v = 0;
-        for (int s = 0; s < NS; ++s) {
-            if (s == a) continue;
-            V3<double> dd = offs[a] - offs[s];
-            v += qs[s] / sqrt(dot(dd, dd));
         }
-        d.vint[m * 3 + a] = p.ke * v;
+        if (t < NS) {
+            const double *l = ml + t * NMP;
+            const int fr = t == 0 ? 0 : (t == 1 || t == 3 ? 1 : 2);
+            V3<double> e[3];
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+                if (f == fr) e[0] = F[f][0], e[1] = F[f][1], e[2] = F[f][2];
+            const V3<double> mu = l[1] * e[0] + l[2] * e[1] + l[3] * e[2];
+            // Theta = R Th_l R^T ; Th_l symmetric (xx yy zz xy xz yz), R columns = frame axes
+            const double tl[3][3] = {{l[4], l[7], l[8]}, {l[7], l[5], l[9]}, {l[8], l[9], l[6]}};
+            const double Rm[3][3] = {{e[0].x, e[1].x, e[2].x}, {e[0].y, e[1].y, e[2].y}, {e[0].z, e[1].z, e[2].z}};
+            double A[3][3];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double acc = 0;
+                    for (int c = 0; c < 3; ++c) acc += Rm[a][c] * tl[c][b];
+                    A[a][b] = acc;
+                }
+            double T[3][3];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double acc = 0;
+                    for (int c = 0; c < 3; ++c) acc += A[a][c] * Rm[b][c];
+                    T[a][b] = acc;
+                }
+            R *gm = d.gmp + (m * NS + t) * NMP;
+            gm[0] = R(l[0]);
+            gm[1] = R(mu.x);
+            gm[2] = R(mu.y);
+            gm[3] = R(mu.z);
+            gm[4] = R(T[0][0]);
+            gm[5] = R(T[1][1]);
+            gm[6] = R(T[2][2]);
+            gm[7] = R(T[0][1]);
+            gm[8] = R(T[0][2]);
+            gm[9] = R(T[1][2]);
+        }
+        if (t < 3) {
+            // intramolecular potential on atom t from the charges of the other sites
+            double v = 0;
+            for (int s = 0; s < NS; ++s) {
+                if (s == t) continue;
+                const V3<double> dd = offs[t] - offs[s];
+                v += ml[s * NMP] / sqrt(dot(dd, dd));
+            }
+            d.vint[m * 3 + t] = p.ke * v;
+        }
+        if (t == 7) {
+            // O wrapped into the box in single precision (cell binning) and as
+            // 32-bit fixed-point fractional coordinates: the difference of two
+            // of those, read as a signed integer, is the minimum-image
+            // displacement in units of box / 2^32.
+            for (int k = 0; k < 3; ++k) {
+                double v = x[k];
+                if (p.periodic) {
+                    const double f = v * p.ibox[k];
+                    const double fr = f - floor(f);
+                    d.ufx[m * 3 + k] = (unsigned)(long long)(fr * 4294967296.0);   // fr -> 1 wraps to 0
+                    v = fr * p.box[k];
+                }
+                d.ofw[m * 3 + k] = (float)v;
+            }
+        }
+        // clear the per-molecule accumulators of this evaluation
+        for (int k = t; k < NP * 3; k += 8) d.gpt[m * NP * 3 + k] = 0.0;
+        for (int k = t; k < NS * 3; k += 8) d.gmu[m * NS * 3 + k] = 0.0;
+        for (int k = t; k < NS * 6; k += 8) d.gth[m * NS * 6 + k] = 0.0;
+        for (int k = t; k < 9; k += 8) d.efield[m * 9 + k] = 0.0;
+        for (int k = t; k < 18; k += 8) d.d2rec[m * 18 + k] = 0.0;
+        if (t < 2) d.vlp[m * 2 + t] = 0.0, d.lam[m * 2 + t] = 0.0;
+        if (t < 6) d.dvlp[m * 6 + t] = 0.0;
+        if (t < 3) d.kap[m * 3 + t] = 0.0;
+        if (t < NTERM) d.epart[m * NTERM + t] = 0.0;
     }
-    // clear the per-molecule accumulators of this evaluation
-    for (int k = 0; k < NP * 3; ++k) d.gpt[m * NP * 3 + k] = 0.0;
-    for (int k = 0; k < NS * 3; ++k) d.gmu[m * NS * 3 + k] = 0.0;
-    for (int k = 0; k < NS * 6; ++k) d.gth[m * NS * 6 + k] = 0.0;
-    for (int k = 0; k < 9; ++k) d.efield[m * 9 + k] = 0.0;
-    for (int k = 0; k < 18; ++k) d.d2rec[m * 18 + k] = 0.0;
-    for (int k = 0; k < 2; ++k) d.vlp[m * 2 + k] = 0.0, d.lam[m * 2 + k] = 0.0;
-    for (int k = 0; k < 6; ++k) d.dvlp[m * 6 + k] = 0.0;
-    for (int k = 0; k < 3; ++k) d.kap[m * 3 + k] = 0.0;
-    for (int k = 0; k < NTERM; ++k) d.epart[m * NTERM + k] = 0.0;
+    // largest point distance from its O (list margin): one atomic per warp
+    const int e = __reduce_max_sync(0xffffffffu, __float_as_int(ext));
+    if ((threadIdx.x & 31) == 0) atomicMax((int *)d.ext, e);
 }
 
 template <typename R>
 void launch_sites(const KParams &p, DevState<R> &d, Launch L) {
     cudaMemsetAsync(d.ext, 0, sizeof(float), L.s);
-    k_sites<R><<<(p.M + 127) / 128, 128, 0, L.s>>>(p, d);
+    const long long n = (long long)p.M * 8;
+    k_sites<R><<<(unsigned)((n + 127) / 128), 128, 0, L.s>>>(p, d);
     count(L);
 }
 
@@ -135,26 +173,44 @@ __global__ void k_check_ext(KParams p, DevState<R> d) {
     if (cut > half || *d.ext > 1.3f) atomicOr(d.flags, F_CUTOFF);
 }
 
-// FP32 candidate test on wrapped O positions
+// Minimum-image O_j - O_i from the fixed-point fractional coordinates (FP32).
 template <typename R>
-__device__ inline bool near_f(const KParams &p, const DevState<R> &d, int i, int j, float cut2f) {
-    float dx = d.ofw[j * 3] - d.ofw[i * 3], dy = d.ofw[j * 3 + 1] - d.ofw[i * 3 + 1], dz = d.ofw[j * 3 + 2] - d.ofw[i * 3 + 2];
-    if (p.periodic) {
-        const float L0 = (float)p.box[0], L1 = (float)p.box[1], L2 = (float)p.box[2];
-        dx -= L0 * rintf(dx / L0);
-        dy -= L1 * rintf(dy / L1);
-        dz -= L2 * rintf(dz / L2);
-    }
-    return dx * dx + dy * dy + dz * dz < cut2f;
+__device__ inline V3<float> fx_disp(const KParams &p, const DevState<R> &d, int i, int j) {
+    const int ax = (int)(d.ufx[j * 3] - d.ufx[i * 3]);
+    const int ay = (int)(d.ufx[j * 3 + 1] - d.ufx[i * 3 + 1]);
+    const int az = (int)(d.ufx[j * 3 + 2] - d.ufx[i * 3 + 2]);
+    return mk((float)ax * p.fxs[0], (float)ay * p.fxs[1], (float)az * p.fxs[2]);
 }
 
+// FP32 candidate test
+template <typename R>
+__device__ inline bool near_f(const KParams &p, const DevState<R> &d, int i, int j, float cut2f) {
+    if (!p.periodic) {
+        const float dx = d.ofw[j * 3] - d.ofw[i * 3], dy = d.ofw[j * 3 + 1] - d.ofw[i * 3 + 1],
+                    dz = d.ofw[j * 3 + 2] - d.ofw[i * 3 + 2];
+        return dx * dx + dy * dy + dz * dz < cut2f;
+    }
+    const V3<float> v = fx_disp(p, d, i, j);
+    return dot(v, v) < cut2f;
+}
+
+// Stored displacement: FP32 path in a periodic box from the fixed-point
+// coordinates (relative error ~1e-7, like rounding an exact value to FP32);
+// otherwise the FP64 minimum image.
 template <typename R>
 __device__ inline void store_entry(const KParams &p, DevState<R> &d, int i, int slot, int j) {
     if (slot >= MAXN) return;
-    double dx, dy, dz;
-    min_image(p, d.pos, i, j, dx, dy, dz);
     d.nbr[i * MAXN + slot] = j;
     R *o = d.ndo + ((size_t)i * MAXN + slot) * 3;
+    if (sizeof(R) == 4 && p.periodic) {
+        const V3<float> v = fx_disp(p, d, i, j);
+        o[0] = R(v.x);
+        o[1] = R(v.y);
+        o[2] = R(v.z);
+        return;
+    }
+    double dx, dy, dz;
+    min_image(p, d.pos, i, j, dx, dy, dz);
     o[0] = R(dx);
     o[1] = R(dy);
     o[2] = R(dz);

@@ -8,111 +8,125 @@
 
 namespace sibfa {
 
-// Per-dimension spline data of one point: grid indices and weights with
-// Cartesian derivatives up to NDER.
+// B-spline weights of one point along one axis at the 5 grid lines
+// base - j (j = 0..4), with Cartesian derivatives up to NDER (scaled by K/L).
 template <typename R, int NDER>
-struct Spl {
-    int idx[3][ORDER];
-    R w[NDER + 1][3][ORDER];
+struct Axis {
+    int g[ORDER];
+    R w[NDER + 1][ORDER];
 };
 
 template <typename R, int NDER>
-__device__ inline void spline_point(const KParams &p, double x, double y, double z, Spl<R, NDER> &s) {
-    const double xyz[3] = {x, y, z};
+__device__ inline void axis_weights(const KParams &p, const DevState<R> &d, int m, int pt, int c, Axis<R, NDER> &A) {
+    const int K = p.K[c];
+    const int b = d.sbase[(m * NP + pt) * 3 + c];
+    const R u = d.sfrac[(m * NP + pt) * 3 + c];
+    R m0[ORDER], m1[ORDER], m2[ORDER], m3[ORDER];
+    bspline5<R, NDER>(u, m0, m1, m2, m3);
+    const R scl = sc<R>(p).kl[c];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const double u = xyz[d] * (double)p.K[d] / p.box[d];
-        const double fl = floor(u);
-        const R w = R(u - fl);
-        int base = (int)fl;
-        base %= p.K[d];
-        if (base < 0) base += p.K[d];
-        R m0[ORDER], m1[ORDER], m2[ORDER], m3[ORDER];
-        bspline5<R, NDER>(w, m0, m1, m2, m3);
-        const R sc = R((double)p.K[d] / p.box[d]);
-#pragma unroll
-        for (int j = 0; j < ORDER; ++j) {
-            int g = base - j;
-            if (g < 0) g += p.K[d];
-            s.idx[d][j] = g;
-            s.w[0][d][j] = m0[j];
-            if constexpr (NDER >= 1) s.w[1][d][j] = m1[j] * sc;
-            if constexpr (NDER >= 2) s.w[2][d][j] = m2[j] * sc * sc;
-            if constexpr (NDER >= 3) s.w[3][d][j] = m3[j] * sc * sc * sc;
-        }
+    for (int j = 0; j < ORDER; ++j) {
+        const int g = b - j;
+        A.g[j] = g < 0 ? g + K : g;
+        A.w[0][j] = m0[j];
+        if constexpr (NDER >= 1) A.w[1][j] = m1[j] * scl;
+        if constexpr (NDER >= 2) A.w[2][j] = m2[j] * scl * scl;
+        if constexpr (NDER >= 3) A.w[3][j] = m3[j] * scl * scl * scl;
     }
 }
 
-// absolute position of point pt of molecule m
-template <typename R>
-__device__ inline void abs_point(const DevState<R> &d, int m, int pt, double &x, double &y, double &z) {
-    x = d.pos[m * 9 + 0] + (double)d.off[(m * NP + pt) * 3 + 0];
-    y = d.pos[m * 9 + 1] + (double)d.off[(m * NP + pt) * 3 + 1];
-    z = d.pos[m * 9 + 2] + (double)d.off[(m * NP + pt) * 3 + 2];
+// weights of stencil line i only (x or y axis of a lane's row)
+template <typename R, int NDER>
+__device__ inline void line_weight(const Axis<R, NDER> &A, int i, int &g, R (&w)[NDER + 1]) {
+    g = A.g[0];
+#pragma unroll
+    for (int n = 0; n <= NDER; ++n) w[n] = A.w[n][0];
+#pragma unroll
+    for (int j = 1; j < ORDER; ++j)
+        if (j == i) {
+            g = A.g[j];
+#pragma unroll
+            for (int n = 0; n <= NDER; ++n) w[n] = A.w[n][j];
+        }
 }
 
+// Spread one point per warp: lanes 0-24 own the stencil rows (i, j) and add
+// the multipole operator q + mu.grad + (1/3) Theta:grad grad applied to the
+// B-spline weights at the 5 grid points of their row.
 // kind PERM: 5 sites per molecule with their multipoles;
 // kind DIP: 3 polarizable atoms with dipoles vec[m*9 + a*3 + c];
+// kind DIP_PCG: the same from the working-precision PCG vector;
 // kind LAMBDA: 2 lone pairs with charges d.lam.
 template <typename R>
-__global__ void k_spread(KParams p, DevState<R> d, int kind, const double *vec, R *grid) {
-    if (kind == SPREAD_DIP_PCG) {
-        if (d.scal[7] != 0.0) return;   // solver already converged
+__global__ void __launch_bounds__(256) k_spread(KParams p, DevState<R> d, int kind, const double *vec, R *grid) {
+    const bool pcg = kind == SPREAD_DIP_PCG;
+    if (pcg) {
+        if (d.flags[1]) return;   // solver already converged
         kind = SPREAD_DIP;
     }
     const int per = kind == SPREAD_PERM ? NS : (kind == SPREAD_DIP ? 3 : 2);
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= p.M * per) return;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (t >= p.M * per || lane >= 25) return;
     const int m = t / per, a = t % per;
     const int pt = kind == SPREAD_LAMBDA ? 5 + a : a;
     Mp<R> mp{};
     if (kind == SPREAD_PERM) mp = load_mp(d.gmp + (m * NS + a) * NMP);
-    else if (kind == SPREAD_DIP) mp.mu = mk(R(vec[m * 9 + a * 3]), R(vec[m * 9 + a * 3 + 1]), R(vec[m * 9 + a * 3 + 2]));
-    else mp.q = R(d.lam[m * 2 + a]);
-    double x, y, z;
-    abs_point(d, m, pt, x, y, z);
-    Spl<R, 2> s;
-    spline_point<R, 2>(p, x, y, z, s);
+    else if (kind == SPREAD_DIP) {
+        if (pcg) mp.mu = mk(d.vecR[m * 9 + a * 3], d.vecR[m * 9 + a * 3 + 1], d.vecR[m * 9 + a * 3 + 2]);
+        else mp.mu = mk(R(vec[m * 9 + a * 3]), R(vec[m * 9 + a * 3 + 1]), R(vec[m * 9 + a * 3 + 2]));
+    } else mp.q = R(d.lam[m * 2 + a]);
+    Axis<R, 2> X, Y, Z;
+    axis_weights<R, 2>(p, d, m, pt, 0, X);
+    axis_weights<R, 2>(p, d, m, pt, 1, Y);
+    axis_weights<R, 2>(p, d, m, pt, 2, Z);
+    int gx, gy;
+    R wx[3], wy[3];
+    line_weight<R, 2>(X, lane / 5, gx, wx);
+    line_weight<R, 2>(Y, lane % 5, gy, wy);
     const R third = R(1) / R(3);
-    const int K1 = p.K[1], K2 = p.K[2];
-    for (int i = 0; i < ORDER; ++i) {
-        const R wx0 = s.w[0][0][i], wx1 = s.w[1][0][i], wx2 = s.w[2][0][i];
-        for (int j = 0; j < ORDER; ++j) {
-            const R wy0 = s.w[0][1][j], wy1 = s.w[1][1][j], wy2 = s.w[2][1][j];
-            // coefficients of the z weights (0th, 1st, 2nd derivative)
-            const R c0 = mp.q * wx0 * wy0 + mp.mu.x * wx1 * wy0 + mp.mu.y * wx0 * wy1 +
-                         third * (mp.th.xx * wx2 * wy0 + mp.th.yy * wx0 * wy2 + R(2) * mp.th.xy * wx1 * wy1);
-            const R c1 = mp.mu.z * wx0 * wy0 + third * R(2) * (mp.th.xz * wx1 * wy0 + mp.th.yz * wx0 * wy1);
-            const R c2 = third * mp.th.zz * wx0 * wy0;
-            const size_t row = ((size_t)s.idx[0][i] * K1 + s.idx[1][j]) * K2;
-            for (int k = 0; k < ORDER; ++k) {
-                const R v = c0 * s.w[0][2][k] + c1 * s.w[1][2][k] + c2 * s.w[2][2][k];
-                atomicAdd(&grid[row + s.idx[2][k]], v);
-            }
-        }
-    }
+    // coefficients of the z weights (0th, 1st, 2nd derivative)
+    const R c0 = mp.q * wx[0] * wy[0] + mp.mu.x * wx[1] * wy[0] + mp.mu.y * wx[0] * wy[1] +
+                 third * (mp.th.xx * wx[2] * wy[0] + mp.th.yy * wx[0] * wy[2] + R(2) * mp.th.xy * wx[1] * wy[1]);
+    const R c1 = mp.mu.z * wx[0] * wy[0] + third * R(2) * (mp.th.xz * wx[1] * wy[0] + mp.th.yz * wx[0] * wy[1]);
+    const R c2 = third * mp.th.zz * wx[0] * wy[0];
+    const size_t row = ((size_t)gx * p.K[1] + gy) * p.K[2];
+#pragma unroll
+    for (int k = 0; k < ORDER; ++k) atomicAdd(&grid[row + Z.g[k]], c0 * Z.w[0][k] + c1 * Z.w[1][k] + c2 * Z.w[2][k]);
 }
 
 template <typename R>
 void launch_spread(const KParams &p, DevState<R> &d, int kind, const double *vec, R *grid, Launch L) {
     const int per = kind == SPREAD_PERM ? NS : ((kind == SPREAD_DIP || kind == SPREAD_DIP_PCG) ? 3 : 2);
-    const int n = p.M * per;
-    k_spread<R><<<(n + 127) / 128, 128, 0, L.s>>>(p, d, kind, vec, grid);
+    const long long threads = (long long)p.M * per * 32;
+    k_spread<R><<<(unsigned)((threads + 255) / 256), 256, 0, L.s>>>(p, d, kind, vec, grid);
     count(L);
 }
 
 // multiply the half-complex spectrum (ngrid grids back to back) by the influence function
 template <typename R, typename C>
-__global__ void k_convolve(KParams p, const double *infl, C *cg, int ngrid, const double *scal, int check) {
-    if (check && scal[7] != 0.0) return;
+__global__ void k_convolve(KParams p, const R *infl, C *cg, int ngrid, const int *done, int check) {
+    if (check && *done) return;
     const size_t nh = (size_t)p.K[0] * p.K[1] * (p.K[2] / 2 + 1);
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nh * ngrid) return;
-    const double g = infl[t % nh];
+    const R g = infl[t % nh];
     C c = cg[t];
-    c.x = R(double(c.x) * g);
-    c.y = R(double(c.y) * g);
+    c.x *= g;
+    c.y *= g;
     cg[t] = c;
+}
+
+// working-precision copy of the FP64 influence function
+template <typename R>
+__global__ void k_infl_copy(size_t n, const double *infl, R *out) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = R(infl[t]);
+}
+template <typename R>
+void launch_influence_copy(const KParams &p, DevState<R> &d, Launch L) {
+    const size_t nh = (size_t)p.K[0] * p.K[1] * (p.K[2] / 2 + 1);
+    k_infl_copy<R><<<(unsigned)((nh + 255) / 256), 256, 0, L.s>>>(nh, d.infl, d.inflR);
+    count(L);
 }
 
 template <typename R>
@@ -120,11 +134,11 @@ void launch_convolve(const KParams &p, DevState<R> &d, void *cgrid, int ngrid, i
     const size_t nh = (size_t)p.K[0] * p.K[1] * (p.K[2] / 2 + 1);
     const size_t n = nh * ngrid;
     if (sizeof(R) == 4)
-        k_convolve<float, cufftComplex><<<(unsigned)((n + 255) / 256), 256, 0, L.s>>>(p, d.infl, (cufftComplex *)cgrid,
-                                                                                    ngrid, d.scal, check);
+        k_convolve<float, cufftComplex><<<(unsigned)((n + 255) / 256), 256, 0, L.s>>>(
+            p, (const float *)d.inflR, (cufftComplex *)cgrid, ngrid, d.flags + 1, check);
     else
         k_convolve<double, cufftDoubleComplex><<<(unsigned)((n + 255) / 256), 256, 0, L.s>>>(
-            p, d.infl, (cufftDoubleComplex *)cgrid, ngrid, d.scal, check);
+            p, (const double *)d.inflR, (cufftDoubleComplex *)cgrid, ngrid, d.flags + 1, check);
     count(L);
 }
 
@@ -175,7 +189,8 @@ void launch_influence(const KParams &p, double *infl, Launch L) {
 }
 
 // ---------------------------------------------------------------------------
-// Gather: potential derivatives at a point from a convolved grid.
+// Gather: potential derivatives at a point from a convolved grid, one warp
+// per point; lane (i, j) < 25 sums its stencil row, the warp reduces.
 // ---------------------------------------------------------------------------
 template <typename R>
 struct Derivs {
@@ -184,54 +199,77 @@ struct Derivs {
     R d2[6];    // xx yy zz xy xz yz
     R d3[10];   // xxx yyy zzz xxy xxz xyy yyz xzz yzz xyz
 };
+constexpr int ND_VALS = 20;
 
+// this lane's row contribution to the derivatives up to NDER, packed as
+// phi, d1[3], d2[6], d3[10]
 template <typename R, int NDER>
-__device__ inline void gather_point(const KParams &p, const R *grid, const Spl<R, NDER> &s, Derivs<R> &D) {
-    D = Derivs<R>{};
-    const int K1 = p.K[1], K2 = p.K[2];
-    for (int i = 0; i < ORDER; ++i) {
-        for (int j = 0; j < ORDER; ++j) {
-            const size_t row = ((size_t)s.idx[0][i] * K1 + s.idx[1][j]) * K2;
-            R t0 = 0, t1 = 0, t2 = 0, t3 = 0;   // sums over z with z-derivative order 0..3
-            for (int k = 0; k < ORDER; ++k) {
-                const R g = grid[row + s.idx[2][k]];
-                t0 += g * s.w[0][2][k];
-                if constexpr (NDER >= 1) t1 += g * s.w[1][2][k];
-                if constexpr (NDER >= 2) t2 += g * s.w[2][2][k];
-                if constexpr (NDER >= 3) t3 += g * s.w[3][2][k];
-            }
-            const R x0 = s.w[0][0][i], y0 = s.w[0][1][j];
-            D.phi += x0 * y0 * t0;
-            if constexpr (NDER >= 1) {
-                const R x1 = s.w[1][0][i], y1 = s.w[1][1][j];
-                D.d1[0] += x1 * y0 * t0;
-                D.d1[1] += x0 * y1 * t0;
-                D.d1[2] += x0 * y0 * t1;
-                if constexpr (NDER >= 2) {
-                    const R x2 = s.w[2][0][i], y2 = s.w[2][1][j];
-                    D.d2[0] += x2 * y0 * t0;
-                    D.d2[1] += x0 * y2 * t0;
-                    D.d2[2] += x0 * y0 * t2;
-                    D.d2[3] += x1 * y1 * t0;
-                    D.d2[4] += x1 * y0 * t1;
-                    D.d2[5] += x0 * y1 * t1;
-                    if constexpr (NDER >= 3) {
-                        const R x3 = s.w[3][0][i], y3 = s.w[3][1][j];
-                        D.d3[0] += x3 * y0 * t0;
-                        D.d3[1] += x0 * y3 * t0;
-                        D.d3[2] += x0 * y0 * t3;
-                        D.d3[3] += x2 * y1 * t0;
-                        D.d3[4] += x2 * y0 * t1;
-                        D.d3[5] += x1 * y2 * t0;
-                        D.d3[6] += x0 * y2 * t1;
-                        D.d3[7] += x1 * y0 * t2;
-                        D.d3[8] += x0 * y1 * t2;
-                        D.d3[9] += x1 * y1 * t1;
-                    }
-                }
-            }
-        }
+__device__ inline void gather_row(const KParams &p, const R *grid, const Axis<R, NDER> &X, const Axis<R, NDER> &Y,
+                                  const Axis<R, NDER> &Z, int lane, R *v) {
+    int gx, gy;
+    R x[NDER + 1], y[NDER + 1];
+    line_weight<R, NDER>(X, lane / 5, gx, x);
+    line_weight<R, NDER>(Y, lane % 5, gy, y);
+    const size_t row = ((size_t)gx * p.K[1] + gy) * p.K[2];
+    R t[4] = {R(0), R(0), R(0), R(0)};   // sums over z with z-derivative order 0..3
+#pragma unroll
+    for (int k = 0; k < ORDER; ++k) {
+        const R g = grid[row + Z.g[k]];
+#pragma unroll
+        for (int n = 0; n <= NDER; ++n) t[n] += g * Z.w[n][k];
     }
+    v[0] = x[0] * y[0] * t[0];
+    if constexpr (NDER >= 1) {
+        v[1] = x[1] * y[0] * t[0];
+        v[2] = x[0] * y[1] * t[0];
+        v[3] = x[0] * y[0] * t[1];
+    }
+    if constexpr (NDER >= 2) {
+        v[4] = x[2] * y[0] * t[0];
+        v[5] = x[0] * y[2] * t[0];
+        v[6] = x[0] * y[0] * t[2];
+        v[7] = x[1] * y[1] * t[0];
+        v[8] = x[1] * y[0] * t[1];
+        v[9] = x[0] * y[1] * t[1];
+    }
+    if constexpr (NDER >= 3) {
+        v[10] = x[3] * y[0] * t[0];
+        v[11] = x[0] * y[3] * t[0];
+        v[12] = x[0] * y[0] * t[3];
+        v[13] = x[2] * y[1] * t[0];
+        v[14] = x[2] * y[0] * t[1];
+        v[15] = x[1] * y[2] * t[0];
+        v[16] = x[0] * y[2] * t[1];
+        v[17] = x[1] * y[0] * t[2];
+        v[18] = x[0] * y[1] * t[2];
+        v[19] = x[1] * y[1] * t[1];
+    }
+}
+
+// Warp gather of one point: returns the derivatives in shared memory (buf,
+// ND_VALS * 33 elements of this warp), valid in all lanes after the call.
+template <typename R, int NDER>
+__device__ inline void warp_gather(const KParams &p, const DevState<R> &d, const R *grid, int m, int pt, int lane,
+                                   R *buf, Derivs<R> &D) {
+    constexpr int NV = NDER >= 3 ? 20 : (NDER == 2 ? 10 : (NDER == 1 ? 4 : 1));
+    Axis<R, NDER> X, Y, Z;
+    axis_weights<R, NDER>(p, d, m, pt, 0, X);
+    axis_weights<R, NDER>(p, d, m, pt, 1, Y);
+    axis_weights<R, NDER>(p, d, m, pt, 2, Z);
+    R v[ND_VALS];
+#pragma unroll
+    for (int k = 0; k < ND_VALS; ++k) v[k] = R(0);
+    if (lane < 25) gather_row<R, NDER>(p, grid, X, Y, Z, lane, v);
+    R vv[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) vv[k] = v[k];
+    const R s = warp_transpose_sum<R, NV>(vv, buf, lane);
+    if (lane < NV) buf[lane] = s;
+    __syncwarp();
+    R *o = reinterpret_cast<R *>(&D);
+#pragma unroll
+    for (int k = 0; k < ND_VALS; ++k) o[k] = k < NV ? buf[k] : R(0);
+    __syncwarp();
 }
 
 // full third-derivative tensor entry (a, b, c) from the 10 unique components
@@ -258,20 +296,18 @@ __device__ inline R sym_at(const R *s6, int a, int b) {
     return s6[2 + k];
 }
 
-// dU/dr for a multipole sitting in the gathered potential:
+// dU/dr component a for a multipole sitting in the gathered potential:
 // q d1 + d2 . mu + (1/3) Theta : d3
 template <typename R>
-__device__ inline void mp_grad(const Mp<R> &m, const Derivs<R> &D, R out[3]) {
+__device__ inline R mp_grad(const Mp<R> &m, const Derivs<R> &D, int a) {
     const R th[6] = {m.th.xx, m.th.yy, m.th.zz, m.th.xy, m.th.xz, m.th.yz};
     const R mu[3] = {m.mu.x, m.mu.y, m.mu.z};
-    for (int a = 0; a < 3; ++a) {
-        R v = m.q * D.d1[a];
-        for (int b = 0; b < 3; ++b) v += sym_at(D.d2, a, b) * mu[b];
-        R t = 0;
-        for (int b = 0; b < 3; ++b)
-            for (int c = 0; c < 3; ++c) t += sym_at(th, b, c) * d3at(D, a, b, c);
-        out[a] = v + t / R(3);
-    }
+    R v = m.q * D.d1[a];
+    for (int b = 0; b < 3; ++b) v += sym_at(D.d2, a, b) * mu[b];
+    R t = 0;
+    for (int b = 0; b < 3; ++b)
+        for (int c = 0; c < 3; ++c) t += sym_at(th, b, c) * d3at(D, a, b, c);
+    return v + t / R(3);
 }
 
 template <typename R>
@@ -280,79 +316,71 @@ __device__ inline R mp_energy(const Mp<R> &m, const Derivs<R> &D) {
     return m.q * D.phi + m.mu.x * D.d1[0] + m.mu.y * D.d1[1] + m.mu.z * D.d1[2] + symdd(m.th, d2) / R(3);
 }
 
-// Permanent pass: 8 threads per molecule (points 0..6 used).  Sites: energy,
+constexpr int GW = 8;   // warps (points) per block of the gather kernels
+
+// Permanent pass: one warp per point (7 per molecule).  Sites: energy,
 // gradient, multipole sensitivities; O/H1/H2 also their field and Hessian;
 // lone pairs: potential and its gradient.
 template <typename R>
-__global__ void k_gather_perm(KParams p, DevState<R> d) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int m = t >> 3, pt = t & 7;
-    double e = 0.0;
-    if (m < p.M && pt < NP) {
-        double x, y, z;
-        abs_point(d, m, pt, x, y, z);
-        Derivs<R> D;
-        if (pt < NS) {
-            Spl<R, 3> s;
-            spline_point<R, 3>(p, x, y, z, s);
-            gather_point<R, 3>(p, d.grid, s, D);
-            const Mp<R> mp = load_mp(d.gmp + (m * NS + pt) * NMP);
-            e = 0.5 * (double)mp_energy(mp, D);
-            R g[3];
-            mp_grad(mp, D, g);
-            double *gp = d.gpt + (m * NP + pt) * 3;
-            double *gm = d.gmu + (m * NS + pt) * 3;
-            double *gt = d.gth + (m * NS + pt) * 6;
-            for (int a = 0; a < 3; ++a) {
-                gp[a] += (double)g[a];
-                gm[a] += (double)D.d1[a];
-            }
-            for (int k = 0; k < 6; ++k) gt[k] += (double)D.d2[k] / 3.0;
-            if (pt < 3) {
-                for (int a = 0; a < 3; ++a) d.efield[m * 9 + pt * 3 + a] -= (double)D.d1[a] / p.ke;
-                for (int k = 0; k < 6; ++k) d.d2rec[m * 18 + pt * 6 + k] = (double)D.d2[k];
-            }
-        } else {
-            Spl<R, 1> s;
-            spline_point<R, 1>(p, x, y, z, s);
-            gather_point<R, 1>(p, d.grid, s, D);
-            const int l = pt - NS;
-            d.vlp[m * 2 + l] += (double)D.phi;
-            for (int a = 0; a < 3; ++a) d.dvlp[(m * 2 + l) * 3 + a] += (double)D.d1[a];
+__global__ void __launch_bounds__(32 * GW) k_gather_perm(KParams p, DevState<R> d) {
+    __shared__ R buf[GW][ND_VALS * 33];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * GW + w;
+    if (t >= p.M * NP) return;
+    const int m = t / NP, pt = t % NP;
+    Derivs<R> D;
+    if (pt < NS) {
+        warp_gather<R, 3>(p, d, d.grid, m, pt, lane, buf[w], D);
+        const Mp<R> mp = load_mp(d.gmp + (m * NS + pt) * NMP);
+        if (lane < 3) {
+            d.gpt[(m * NP + pt) * 3 + lane] += (double)mp_grad(mp, D, lane);
+            d.gmu[(m * NS + pt) * 3 + lane] += (double)D.d1[lane];
+            if (pt < 3) d.efield[m * 9 + pt * 3 + lane] -= (double)D.d1[lane] / p.ke;
+        } else if (lane < 9) {
+            d.gth[(m * NS + pt) * 6 + lane - 3] += (double)D.d2[lane - 3] / 3.0;
+            if (pt < 3) d.d2rec[m * 18 + pt * 6 + lane - 3] = (double)D.d2[lane - 3];
+        } else if (lane == 9) {
+            atomicAdd(&d.epart[m * NTERM + T_ELEC], 0.5 * (double)mp_energy(mp, D));
         }
+    } else {
+        warp_gather<R, 1>(p, d, d.grid, m, pt, lane, buf[w], D);
+        const int l = pt - NS;
+        if (lane < 3) d.dvlp[(m * 2 + l) * 3 + lane] += (double)D.d1[lane];
+        else if (lane == 3) d.vlp[m * 2 + l] += (double)D.phi;
     }
-    // sum the 8 lanes of this molecule
-    for (int o = 4; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o, 8);
-    if (m < p.M && pt == 0) d.epart[m * NTERM + T_ELEC] += e;
 }
 
 template <typename R>
 void launch_gather_perm(const KParams &p, DevState<R> &d, Launch L) {
-    const int n = p.M * 8;
-    k_gather_perm<R><<<(n + 127) / 128, 128, 0, L.s>>>(p, d);
+    const int n = p.M * NP;
+    k_gather_perm<R><<<(n + GW - 1) / GW, 32 * GW, 0, L.s>>>(p, d);
     count(L);
 }
 
 // Field on the polarizable atoms from the dipole grid: out += -grad phi / ke.
 template <typename R>
-__global__ void k_gather_field(KParams p, DevState<R> d, double *out) {
-    if (d.scal[7] != 0.0) return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32 * GW) k_gather_field(KParams p, DevState<R> d, double *out) {
+    __shared__ R buf[GW][4 * 33];
+    if (d.flags[1]) return;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * GW + w;
     if (t >= p.M * 3) return;
     const int m = t / 3, a = t % 3;
-    double x, y, z;
-    abs_point(d, m, a, x, y, z);
-    Spl<R, 1> s;
-    spline_point<R, 1>(p, x, y, z, s);
-    Derivs<R> D;
-    gather_point<R, 1>(p, d.grid, s, D);
-    for (int c = 0; c < 3; ++c) out[m * 9 + a * 3 + c] -= (double)D.d1[c] / p.ke;
+    Axis<R, 1> X, Y, Z;
+    axis_weights<R, 1>(p, d, m, a, 0, X);
+    axis_weights<R, 1>(p, d, m, a, 1, Y);
+    axis_weights<R, 1>(p, d, m, a, 2, Z);
+    R v[4] = {R(0), R(0), R(0), R(0)};
+    if (lane < 25) gather_row<R, 1>(p, d.grid, X, Y, Z, lane, v);
+    const R vals[3] = {v[1], v[2], v[3]};
+    const R s = warp_transpose_sum<R, 3>(vals, buf[w], lane);
+    if (lane < 3) out[m * 9 + a * 3 + lane] -= (double)(s * sc<R>(p).ike);
 }
 
 template <typename R>
 void launch_gather_field(const KParams &p, DevState<R> &d, double *out, Launch L) {
     const int n = p.M * 3;
-    k_gather_field<R><<<(n + 127) / 128, 128, 0, L.s>>>(p, d, out);
+    k_gather_field<R><<<(n + GW - 1) / GW, 32 * GW, 0, L.s>>>(p, d, out);
     count(L);
 }
 
@@ -361,55 +389,48 @@ void launch_gather_field(const KParams &p, DevState<R> &d, double *out, Launch L
 // both potentials.  O/H1/H2: gradient of the induced dipole in the induced
 // (grid 0) and permanent (stored Hessian) reciprocal potentials.
 template <typename R>
-__global__ void k_gather_polforce(KParams p, DevState<R> d) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32 * GW) k_gather_polforce(KParams p, DevState<R> d) {
+    __shared__ R buf[GW][ND_VALS * 33];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * GW + w;
     if (t >= p.M * NS) return;
     const int m = t / NS, pt = t % NS;
     const size_t ng = (size_t)p.K[0] * p.K[1] * p.K[2];
-    double x, y, z;
-    abs_point(d, m, pt, x, y, z);
-    Spl<R, 3> s;
-    spline_point<R, 3>(p, x, y, z, s);
     Derivs<R> A, B;
-    gather_point<R, 3>(p, d.grid, s, A);
-    gather_point<R, 3>(p, d.grid + ng, s, B);
+    warp_gather<R, 3>(p, d, d.grid, m, pt, lane, buf[w], A);
+    warp_gather<R, 3>(p, d, d.grid + ng, m, pt, lane, buf[w], B);
     Derivs<R> S;
     S.phi = A.phi + B.phi;
     for (int k = 0; k < 3; ++k) S.d1[k] = A.d1[k] + B.d1[k];
     for (int k = 0; k < 6; ++k) S.d2[k] = A.d2[k] + B.d2[k];
     for (int k = 0; k < 10; ++k) S.d3[k] = A.d3[k] + B.d3[k];
     const Mp<R> mp = load_mp(d.gmp + (m * NS + pt) * NMP);
-    R g[3];
-    mp_grad(mp, S, g);
-    double *gp = d.gpt + (m * NP + pt) * 3;
-    double *gm = d.gmu + (m * NS + pt) * 3;
-    double *gt = d.gth + (m * NS + pt) * 6;
-    for (int a = 0; a < 3; ++a) {
-        gp[a] += (double)g[a];
-        gm[a] += (double)S.d1[a];
-    }
-    for (int k = 0; k < 6; ++k) gt[k] += (double)S.d2[k] / 3.0;
-    if (pt < 3) {
-        const double mu[3] = {d.mu[m * 9 + pt * 3], d.mu[m * 9 + pt * 3 + 1], d.mu[m * 9 + pt * 3 + 2]};
-        const double *h = d.d2rec + m * 18 + pt * 6;
-        for (int a = 0; a < 3; ++a) {
-            double v = 0;
-            for (int b = 0; b < 3; ++b) v += ((double)sym_at(A.d2, a, b) + sym_at(h, a, b)) * mu[b];
-            gp[a] += v;
+    if (lane < 3) {
+        double g = (double)mp_grad(mp, S, lane);
+        if (pt < 3) {
+            // induced dipole in the induced (grid 0) and permanent (stored Hessian) potentials
+            const double *mu = d.mu + m * 9 + pt * 3;
+            const double *h = d.d2rec + m * 18 + pt * 6;
+            for (int b = 0; b < 3; ++b) g += ((double)sym_at(A.d2, lane, b) + sym_at(h, lane, b)) * mu[b];
         }
+        d.gpt[(m * NP + pt) * 3 + lane] += g;
+        d.gmu[(m * NS + pt) * 3 + lane] += (double)S.d1[lane];
+    } else if (lane < 9) {
+        d.gth[(m * NS + pt) * 6 + lane - 3] += (double)S.d2[lane - 3] / 3.0;
     }
 }
 
 template <typename R>
 void launch_gather_polforce(const KParams &p, DevState<R> &d, Launch L) {
     const int n = p.M * NS;
-    k_gather_polforce<R><<<(n + 127) / 128, 128, 0, L.s>>>(p, d);
+    k_gather_polforce<R><<<(n + GW - 1) / GW, 32 * GW, 0, L.s>>>(p, d);
     count(L);
 }
 
 #define INST(R)                                                                                         \
     template void launch_spread<R>(const KParams &, DevState<R> &, int, const double *, R *, Launch);    \
     template void launch_convolve<R>(const KParams &, DevState<R> &, void *, int, int, Launch);               \
+    template void launch_influence_copy<R>(const KParams &, DevState<R> &, Launch);                      \
     template void launch_gather_perm<R>(const KParams &, DevState<R> &, Launch);                         \
     template void launch_gather_field<R>(const KParams &, DevState<R> &, double *, Launch);              \
     template void launch_gather_polforce<R>(const KParams &, DevState<R> &, Launch);

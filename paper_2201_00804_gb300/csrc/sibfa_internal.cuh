@@ -32,6 +32,8 @@ struct Scal {
     R rep_f, rep_c1, rep_c2, occ, nlp;
     R c6, c8, c10, g6, g8, g10, delta, xd_c1, xd_c2, xd_c3;
     R ct_t, ct_m, ct_ae, ct_ah;
+    R kl[3];   // SPME grid points per unit length, K / L
+    R ike;     // 1 / ke
 };
 
 // ---------------------------------------------------------------------------
@@ -82,6 +84,7 @@ struct KParams {
     float betaf[5];                      // dispersion beta per point (O, H, H, LP, LP)
     Scal<float> sf;
     Scal<double> sd;
+    float fxs[3];                        // box / 2^32: length of one fixed-point unit per axis
 };
 
 template <typename R>
@@ -139,7 +142,10 @@ struct DevState {
     int *nbr;           // M*MAXN neighbour molecules (full list)
     R *ndo;             // M*MAXN*3 minimum-image displacement O_j - O_i of each entry
     int *nnbr;          // M
-    float *ofw;         // M*3 O positions wrapped into the box (single precision, list build only)
+    float *ofw;         // M*3 O positions wrapped into the box (single precision, cell binning)
+    unsigned *ufx;      // M*3 O fractional coordinates in units of 2^-32 of the box (periodic list build)
+    int *sbase;         // M*NP*3 SPME: floor(u) mod K of every point (u = fractional coordinate x K)
+    R *sfrac;           // M*NP*3 SPME: u - floor(u)
     // cell list
     int *cell_of;       // M
     int *cell_start;    // ncell+1
@@ -168,12 +174,13 @@ struct DevState {
     double *partial;    // reduction partials
     double *scal;       // device scalars (see pcg kernels)
     unsigned int *counter;
-    int *flags;         // error flags
+    int *flags;         // [0] error flags, [1] PCG converged
     float *ext;         // maximum point distance from own O (float bits, atomicMax)
     // grids
     R *grid;            // 2 * K0*K1*K2 (two real grids for the force pass)
     void *cgrid;        // 2 * K0*K1*(K2/2+1) complex
     double *infl;       // K0*K1*(K2/2+1) influence function / (K0 K1 K2)
+    R *inflR;           // the same in the working precision
 };
 
 // ---------------------------------------------------------------------------
@@ -531,6 +538,36 @@ __device__ inline R warp_transpose_sum(const R (&v)[NV], R *buf, int lane) {
     return s0 + s1;
 }
 
+// position of point k of molecule m relative to its O (points: 5 sites, 2 lone pairs)
+template <typename R>
+__device__ inline V3<R> my_pt(const DevState<R> &d, int i, int pt) {
+    const R *o = d.off + (i * NP + pt) * 3;
+    return mk(o[0], o[1], o[2]);
+}
+
+// cos(u, v) and its gradients with respect to u and v
+template <typename R>
+__device__ inline R cosv(V3<R> u, V3<R> v, V3<R> &du, V3<R> &dv) {
+    const R uu = dot(u, u), vv = dot(v, v);
+    const R iu = rsqrt_(uu), iv = rsqrt_(vv);
+    const R c = dot(u, v) * iu * iv;
+    du = (iu * iv) * v - (c / uu) * u;
+    dv = (iu * iv) * u - (c / vv) * v;
+    return c;
+}
+
+// exclusive prefix sum of c over the lanes of a warp; total = sum over all lanes
+__device__ inline int warp_excl_scan(int c, int lane, int &total) {
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    total = __shfl_sync(0xffffffffu, incl, 31);
+    return incl - c;
+}
+
 // Compensated (two-sum) accumulator used for per-lane energy partial sums.
 template <typename R>
 struct Acc {
@@ -662,9 +699,9 @@ template <typename R> void launch_real_perm(const KParams &p, DevState<R> &d, La
 template <typename R> void launch_short(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_ct(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_intra_perm(const KParams &p, DevState<R> &d, Launch L);
-template <typename R> void launch_tmu_list(const KParams &p, DevState<R> &d, double *out,
+template <typename R> void launch_real_tmu(const KParams &p, DevState<R> &d, double *out,
                                            Launch L);
-template <typename R> void launch_intra_tmu(const KParams &p, DevState<R> &d, const double *vec, double *out,
+template <typename R> void launch_intra_tmu(const KParams &p, DevState<R> &d, double *out,
                                             Launch L);
 template <typename R> void launch_real_polforce(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_intra_polforce(const KParams &p, DevState<R> &d, Launch L);
@@ -680,6 +717,7 @@ template <typename R> void launch_gather_perm(const KParams &p, DevState<R> &d, 
 template <typename R> void launch_gather_field(const KParams &p, DevState<R> &d, double *out, Launch L);
 template <typename R> void launch_gather_polforce(const KParams &p, DevState<R> &d, Launch L);
 void launch_influence(const KParams &p, double *infl, Launch L);
+template <typename R> void launch_influence_copy(const KParams &p, DevState<R> &d, Launch L);
 
 // PCG
 template <typename R> void launch_pcg_init(const KParams &p, DevState<R> &d, int warm, Launch L);
