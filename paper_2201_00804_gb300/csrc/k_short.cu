@@ -316,7 +316,9 @@ __device__ void item_d(const KParams &p, const Scal<R> &S, const ShortTables &T,
 
 // ---- kernel ------------------------------------------------------------------
 
-template <typename R, bool PER>
+// PART 0: exchange-repulsion items (BB, BL, LB, LL); PART 1: dispersion and
+// exchange-dispersion items (D).  Two launches keep each kernel's code small.
+template <typename R, bool PER, int PART>
 __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
     __shared__ ShortTables T;
     __shared__ int qbuf[4][SQ_WORDS];
@@ -365,9 +367,10 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
         int j = 0;
         V3<R> dO = mk(R(0), R(0), R(0));
         if (live) neighbour(d, i, slot, j, dO);
-        // stage 0: repulsion items; stages 1-5: dispersion items of point u = stage - 1
-        for (int stage = 0; stage < 6; ++stage) {
-            if (stage == 0) {
+        // PART 0, stage 0: repulsion items; PART 1, stages 1-5: dispersion items of point u = stage - 1
+        const int s0 = PART == 0 ? 0 : 1, s1 = PART == 0 ? 1 : 6;
+        for (int stage = s0; stage < s1; ++stage) {
+            if (PART == 0) {
                 unsigned bb = 0, bl = 0, lb = 0, ll = 0;
                 if (live) {
                     const V3<R> Q1 = qpt(d, j, dO, 1), Q2 = qpt(d, j, dO, 2);
@@ -410,7 +413,15 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
                 t[4] += n;
             }
             __syncwarp();
-            const bool last = flush && stage == 5;
+            const bool last = flush && stage == s1 - 1;
+            if (PART == 1) {
+                while (t[4] - h[4] >= 32 || (last && t[4] > h[4])) {
+                    if (lane < t[4] - h[4]) item_d(p, S, T, d, I, i, q[SQ_D + (h[4] + lane) % SQ_CAPD], acc);
+                    h[4] += min(32, t[4] - h[4]);
+                }
+                __syncwarp();
+                continue;
+            }
             while (t[0] - h[0] >= 32 || (last && t[0] > h[0])) {
                 if (lane < t[0] - h[0]) item_bb(S, T, d, I, i, q[SQ_BB + (h[0] + lane) % SQ_CAP], acc);
                 h[0] += min(32, t[0] - h[0]);
@@ -427,10 +438,6 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
                 if (lane < t[3] - h[3]) item_ll(S, T, d, I, i, q[SQ_LL + (h[3] + lane) % SQ_CAP], acc);
                 h[3] += min(32, t[3] - h[3]);
             }
-            while (t[4] - h[4] >= 32 || (last && t[4] > h[4])) {
-                if (lane < t[4] - h[4]) item_d(p, S, T, d, I, i, q[SQ_D + (h[4] + lane) % SQ_CAPD], acc);
-                h[4] += min(32, t[4] - h[4]);
-            }
             __syncwarp();
         }
         if (flush) break;
@@ -442,19 +449,29 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
     const R s = warp_transpose_sum<R, 15>(vals, reinterpret_cast<R *>(q), lane);
     const int pt = lane / 3;
     if (lane < 15) d.gpt[(i * NP + (pt < 3 ? pt : pt + 2)) * 3 + lane % 3] += double(s);
-    const double er_ = warp_sum_acc(acc.Erep), ed_ = warp_sum_acc(acc.Ed), ex_ = warp_sum_acc(acc.Ex);
-    if (lane == 0) {
-        d.epart[i * NTERM + T_REP] += er_;
-        d.epart[i * NTERM + T_DISP] += ed_;
-        d.epart[i * NTERM + T_XDISP] += ex_;
+    if (PART == 0) {
+        const double er_ = warp_sum_acc(acc.Erep);
+        if (lane == 0) d.epart[i * NTERM + T_REP] += er_;
+    } else {
+        const double ed_ = warp_sum_acc(acc.Ed), ex_ = warp_sum_acc(acc.Ex);
+        if (lane == 0) {
+            d.epart[i * NTERM + T_DISP] += ed_;
+            d.epart[i * NTERM + T_XDISP] += ex_;
+        }
     }
 }
 
 template <typename R>
 void launch_short(const KParams &p, DevState<R> &d, Launch L) {
-    if (p.periodic) k_short<R, true><<<(p.M + 3) / 4, 128, 0, L.s>>>(p, d);
-    else k_short<R, false><<<(p.M + 3) / 4, 128, 0, L.s>>>(p, d);
-    count(L);
+    const unsigned nb = (p.M + 3) / 4;
+    if (p.periodic) {
+        k_short<R, true, 0><<<nb, 128, 0, L.s>>>(p, d);
+        k_short<R, true, 1><<<nb, 128, 0, L.s>>>(p, d);
+    } else {
+        k_short<R, false, 0><<<nb, 128, 0, L.s>>>(p, d);
+        k_short<R, false, 1><<<nb, 128, 0, L.s>>>(p, d);
+    }
+    count(L, 2);
 }
 
 template void launch_short<float>(const KParams &, DevState<float> &, Launch);
