@@ -21,6 +21,8 @@ struct sibfa_ctx {
     sibfa_run_opts opts{};
     KParams kp{};
     cudaStream_t s = nullptr;    // the library's own work stream (non-blocking)
+    cudaStream_t s2 = nullptr;   // reciprocal-space chain, forked from s and joined back
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t us = nullptr;   // the caller's stream (ordering only)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     // polarization iterations as one CUDA graph with a device-side while loop
@@ -59,7 +61,8 @@ namespace {
 struct Phase {
     sibfa_ctx *ctx;
     size_t idx = (size_t)-1;
-    Phase(sibfa_ctx *c, const char *name) : ctx(c) {
+    cudaStream_t st;
+    Phase(sibfa_ctx *c, const char *name, cudaStream_t stream = nullptr) : ctx(c), st(stream ? stream : c->s) {
         if (!ctx->profiling || ctx->capturing) return;
         cudaEvent_t a, b;
         if (ctx->event_pool.size() >= 2) {
@@ -71,12 +74,12 @@ struct Phase {
             cudaEventCreate(&a);
             cudaEventCreate(&b);
         }
-        cudaEventRecord(a, ctx->s);
+        cudaEventRecord(a, st);
         ctx->spans.push_back({name, a, b});
         idx = ctx->spans.size() - 1;
     }
     ~Phase() {
-        if (idx != (size_t)-1) cudaEventRecord(ctx->spans[idx].b, ctx->s);
+        if (idx != (size_t)-1) cudaEventRecord(ctx->spans[idx].b, st);
     }
 };
 }  // namespace
@@ -152,6 +155,14 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.lam, M * 2);
     AL(d.kap, M * 3);
     AL(d.epart, M * NTERM);
+    AL(d.gpt_r, M * NP * 3);
+    AL(d.gmu_r, M * NS * 3);
+    AL(d.gth_r, M * NS * 6);
+    AL(d.efield_r, M * 9);
+    AL(d.vlp_r, M * 2);
+    AL(d.dvlp_r, M * 6);
+    AL(d.epart_r, M * NTERM);
+    AL(d.efp_r, M * 9);
     AL(d.mu, M * 9);
     AL(d.res, M * 9);
     AL(d.zv, M * 9);
@@ -296,6 +307,19 @@ sibfa_status leave(sibfa_ctx *ctx) {
     return SIBFA_OK;
 }
 
+// Fork the reciprocal-space chain onto s2 after the work queued on s so
+// far, and join it back into s.
+sibfa_status fork_rec(sibfa_ctx *ctx) {
+    CK(cudaEventRecord(ctx->ev_fork, ctx->s));
+    CK(cudaStreamWaitEvent(ctx->s2, ctx->ev_fork, 0));
+    return SIBFA_OK;
+}
+sibfa_status join_rec(sibfa_ctx *ctx) {
+    CK(cudaEventRecord(ctx->ev_join, ctx->s2));
+    CK(cudaStreamWaitEvent(ctx->s, ctx->ev_join, 0));
+    return SIBFA_OK;
+}
+
 bool is_device_ptr(const void *p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -327,23 +351,29 @@ sibfa_status fft(sibfa_ctx *ctx, DevState<R> &d, bool forward, int ngrid) {
     return SIBFA_OK;
 }
 
-// T vec (field part) into d.efp: real space + reciprocal + intramolecular
+// T vec (field part): real space into d.efp on s, reciprocal and
+// intramolecular into d.efp_r on s2, concurrently; vec is the PCG vector
+// already copied to d.vecR.
 template <typename R>
 sibfa_status matvec(sibfa_ctx *ctx, DevState<R> &d, const double *vec, Launch L) {
     const KParams &p = ctx->kp;
-    { Phase ph(ctx, "real_tmu");  launch_real_tmu(p, d, d.efp, L); }
     if (p.periodic) {
-        const size_t ng = (size_t)p.K[0] * p.K[1] * p.K[2];
-        CK(cudaMemsetAsync(d.grid, 0, ng * sizeof(R), ctx->s));
-        launch_spread(p, d, SPREAD_DIP_PCG, vec, d.grid, L);
-        sibfa_status st = fft(ctx, d, true, 1);
+        sibfa_status st = fork_rec(ctx);
         if (st) return st;
-        launch_convolve(p, d, d.cgrid, 1, 1, L);
+        Launch L2{ctx->s2, L.count};
+        const size_t ng = (size_t)p.K[0] * p.K[1] * p.K[2];
+        CK(cudaMemsetAsync(d.grid, 0, ng * sizeof(R), ctx->s2));
+        launch_spread(p, d, SPREAD_DIP_PCG, vec, d.grid, L2);
+        st = fft(ctx, d, true, 1);
+        if (st) return st;
+        launch_convolve(p, d, d.cgrid, 1, 1, L2);
         st = fft(ctx, d, false, 1);
         if (st) return st;
-        launch_gather_field(p, d, d.efp, L);
-        launch_intra_tmu(p, d, d.efp, L);
+        launch_gather_field(p, d, d.efp_r, L2);
+        launch_intra_tmu(p, d, d.efp_r, L2);
     }
+    { Phase ph(ctx, "real_tmu");  launch_real_tmu(p, d, d.efp, L); }
+    if (p.periodic) return join_rec(ctx);
     return SIBFA_OK;
 }
 
@@ -440,24 +470,33 @@ sibfa_status solve(sibfa_ctx *ctx, DevState<R> &d, double tol, Launch L) {
 template <typename R>
 sibfa_status evaluate(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, double tol) {
     DevState<R> &d = state<R>(ctx);
+    DevState<R> dr = rec_view(d);   // accumulators of the reciprocal chain
     const KParams &p = ctx->kp;
     Launch L{ctx->s, &ctx->launches};
+    Launch L2{ctx->s2, &ctx->launches};
     launch_begin(d.scal, d.flags, tol, L);
     { Phase ph(ctx, "sites");  launch_sites(p, d, L); }
-    { Phase ph(ctx, "neighbors");  launch_neighbors(p, d, ctx->ncell, L); }
-    { Phase ph(ctx, "real_perm");  launch_real_perm(p, d, L); }
-    if (!dipoles_only) { Phase ph(ctx, "short");  launch_short(p, d, L); }
     const size_t ng = (size_t)p.K[0] * p.K[1] * p.K[2];
     sibfa_status st;
     if (p.periodic) {
-        Phase ph(ctx, "spme_perm");
-        CK(cudaMemsetAsync(d.grid, 0, ng * sizeof(R), ctx->s));
-        launch_spread(p, d, SPREAD_PERM, nullptr, d.grid, L);
+        // permanent multipoles in reciprocal space, concurrent with the
+        // neighbour list and the real-space pair kernels
+        if ((st = fork_rec(ctx))) return st;
+        Phase ph(ctx, "spme_perm", ctx->s2);
+        CK(cudaMemsetAsync(d.grid, 0, ng * sizeof(R), ctx->s2));
+        launch_spread(p, d, SPREAD_PERM, nullptr, d.grid, L2);
         if ((st = fft(ctx, d, true, 1))) return st;
-        launch_convolve(p, d, d.cgrid, 1, 0, L);
+        launch_convolve(p, d, d.cgrid, 1, 0, L2);
         if ((st = fft(ctx, d, false, 1))) return st;
-        launch_gather_perm(p, d, L);
-        launch_intra_perm(p, d, L);
+        launch_gather_perm(p, dr, L2);
+        launch_intra_perm(p, dr, L2);
+    }
+    { Phase ph(ctx, "neighbors");  launch_neighbors(p, d, ctx->ncell, L); }
+    { Phase ph(ctx, "real_perm");  launch_real_perm(p, d, L); }
+    if (!dipoles_only) { Phase ph(ctx, "short");  launch_short(p, d, L); }
+    if (p.periodic) {
+        if ((st = join_rec(ctx))) return st;
+        launch_merge_rec(p, d, L);
     }
     if (!dipoles_only) { Phase ph(ctx, "ct");  launch_ct(p, d, L); }
     {
@@ -469,21 +508,29 @@ sibfa_status evaluate(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, doubl
     if (dipoles_only) return st_solve;
     launch_pol_energy(p, d, L);
     if (want_forces) {
+        if (p.periodic) {
+            // induced dipoles and charge-transfer lambdas in reciprocal space,
+            // concurrent with the real-space force kernel
+            sibfa_status sf = fork_rec(ctx);
+            if (sf) return sf;
+            Phase ph(ctx, "spme_polforce", ctx->s2);
+            CK(cudaMemsetAsync(d.grid, 0, 2 * ng * sizeof(R), ctx->s2));
+            launch_spread(p, d, SPREAD_DIP, d.mu, d.grid, L2);
+            launch_spread(p, d, SPREAD_LAMBDA, nullptr, d.grid + ng, L2);
+            if ((sf = fft(ctx, d, true, 2))) return sf;
+            launch_convolve(p, d, d.cgrid, 2, 0, L2);
+            if ((sf = fft(ctx, d, false, 2))) return sf;
+            launch_gather_polforce(p, dr, L2);
+            launch_intra_polforce(p, dr, L2);
+        }
         { Phase ph(ctx, "real_polforce");  launch_real_polforce(p, d, L); }
         if (p.periodic) {
-            Phase ph(ctx, "spme_polforce");
-            CK(cudaMemsetAsync(d.grid, 0, 2 * ng * sizeof(R), ctx->s));
-            launch_spread(p, d, SPREAD_DIP, d.mu, d.grid, L);
-            launch_spread(p, d, SPREAD_LAMBDA, nullptr, d.grid + ng, L);
-            if ((st = fft(ctx, d, true, 2))) return st;
-            launch_convolve(p, d, d.cgrid, 2, 0, L);
-            if ((st = fft(ctx, d, false, 2))) return st;
-            launch_gather_polforce(p, d, L);
-            launch_intra_polforce(p, d, L);
+            sibfa_status sj = join_rec(ctx);
+            if (sj) return sj;
         }
         { Phase ph(ctx, "finalize");  launch_finalize(p, d, ctx->d_forces, L); }
     }
-    launch_energy_reduce(p.M, d.epart, ctx->d_energy, L);
+    launch_energy_reduce(p.M, d.epart, d.epart_r, ctx->d_energy, L);
     return st_solve;
 }
 
@@ -588,10 +635,10 @@ sibfa_status create_impl(sibfa_ctx *ctx, const sibfa_topology *topo) {
         CKF(cufftPlan3d(&ctx->c2r1, n[0], n[1], n[2], f32 ? CUFFT_C2R : CUFFT_Z2D));
         CKF(cufftPlanMany(&ctx->r2c2, 3, n, nullptr, 1, ng, nullptr, 1, nh, f32 ? CUFFT_R2C : CUFFT_D2Z, 2));
         CKF(cufftPlanMany(&ctx->c2r2, 3, n, nullptr, 1, nh, nullptr, 1, ng, f32 ? CUFFT_C2R : CUFFT_Z2D, 2));
-        CKF(cufftSetStream(ctx->r2c1, ctx->s));
-        CKF(cufftSetStream(ctx->c2r1, ctx->s));
-        CKF(cufftSetStream(ctx->r2c2, ctx->s));
-        CKF(cufftSetStream(ctx->c2r2, ctx->s));
+        CKF(cufftSetStream(ctx->r2c1, ctx->s2));
+        CKF(cufftSetStream(ctx->c2r1, ctx->s2));
+        CKF(cufftSetStream(ctx->r2c2, ctx->s2));
+        CKF(cufftSetStream(ctx->c2r2, ctx->s2));
         ctx->have_fft = true;
     }
     CK(cudaStreamSynchronize(ctx->s));
@@ -697,8 +744,11 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
     ctx->prec = opts->precision;
     ctx->us = (cudaStream_t)opts->stream;
     if (cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->s2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         g_create_error = "sibfa_create: could not create the work stream";
         delete ctx;
         return SIBFA_E_CUDA;
@@ -861,9 +911,12 @@ uint64_t sibfa_kernel_launches(const sibfa_ctx *ctx) { return ctx ? ctx->launche
 void sibfa_destroy(sibfa_ctx *ctx) {
     if (!ctx) return;
     if (ctx->s) cudaStreamSynchronize(ctx->s);
+    if (ctx->s2) cudaStreamSynchronize(ctx->s2);
     if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     else cudaDeviceSynchronize();
     if (ctx->have_fft) {
         cufftDestroy(ctx->r2c1);
@@ -879,6 +932,7 @@ void sibfa_destroy(sibfa_ctx *ctx) {
     for (void *p : ctx->allocs) cudaFree(p);
     if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
     if (ctx->s) cudaStreamDestroy(ctx->s);
+    if (ctx->s2) cudaStreamDestroy(ctx->s2);
     delete ctx;
 }
 

@@ -67,6 +67,7 @@ __global__ void k_pcg_init(KParams p, DevState<R> d, int warm) {
     if (!warm) d.mu[k] = apol(p, k) * d.efield[k];
     d.vecR[k] = R(d.mu[k]);
     d.efp[k] = 0.0;
+    d.efp_r[k] = 0.0;
 }
 
 // r = E - T mu0, z = alpha r, p = z
@@ -76,12 +77,13 @@ __global__ void k_pcg_first(KParams p, DevState<R> d) {
     double rz = 0, rr = 0;
     if (k < p.M * 9) {
         const double a = apol(p, k);
-        const double r = d.efield[k] - (d.mu[k] / a - d.efp[k]);
+        const double r = d.efield[k] - (d.mu[k] / a - (d.efp[k] + d.efp_r[k]));
         d.res[k] = r;
         d.zv[k] = a * r;
         d.pv[k] = a * r;
         d.vecR[k] = R(a * r);
         d.efp[k] = 0.0;
+        d.efp_r[k] = 0.0;
         rz = r * a * r;
         rr = a * r * a * r;
     }
@@ -103,7 +105,7 @@ __global__ void k_pcg_a(KParams p, DevState<R> d) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     double pap = 0;
     if (k < p.M * 9) {
-        const double ap = d.pv[k] / apol(p, k) - d.efp[k];
+        const double ap = d.pv[k] / apol(p, k) - (d.efp[k] + d.efp_r[k]);
         d.ap[k] = ap;
         pap = d.pv[k] * ap;
     }
@@ -154,6 +156,7 @@ __global__ void k_pcg_c(KParams p, DevState<R> d) {
     d.pv[k] = pk;
     d.vecR[k] = R(pk);
     d.efp[k] = 0.0;
+    d.efp_r[k] = 0.0;
 }
 
 static inline unsigned nblk(int n) { return (unsigned)((n + PB - 1) / PB); }
@@ -253,13 +256,15 @@ __global__ void __launch_bounds__(128) k_finalize(KParams p, DevState<R> d, doub
         const double n1 = sqrt(dot(r1, r1)), n2 = sqrt(dot(r2, r2));
         const V3<double> u1 = (1.0 / n1) * r1, u2 = (1.0 / n2) * r2;
         auto gpt = [&](int k) {
-            return mk(d.gpt[(m * NP + k) * 3], d.gpt[(m * NP + k) * 3 + 1], d.gpt[(m * NP + k) * 3 + 2]);
+            const int o = (m * NP + k) * 3;
+            return mk(d.gpt[o] + d.gpt_r[o], d.gpt[o + 1] + d.gpt_r[o + 1], d.gpt[o + 2] + d.gpt_r[o + 2]);
         };
         // lone-pair point gradient including the charge-transfer dependence through its potential
         auto glp = [&](int l) {
             const double lq = d.lam[m * 2 + l];
+            const int o = (m * 2 + l) * 3;
             return gpt(5 + l) +
-                   lq * mk(d.dvlp[(m * 2 + l) * 3], d.dvlp[(m * 2 + l) * 3 + 1], d.dvlp[(m * 2 + l) * 3 + 2]);
+                   lq * mk(d.dvlp[o] + d.dvlp_r[o], d.dvlp[o + 1] + d.dvlp_r[o + 1], d.dvlp[o + 2] + d.dvlp_r[o + 2]);
         };
         if (t < 3) {
             const int f = t;
@@ -272,9 +277,12 @@ __global__ void __launch_bounds__(128) k_finalize(KParams p, DevState<R> d, doub
                 const int fs = s == 0 ? 0 : (s == 1 || s == 3 ? 1 : 2);
                 if (fs != f) continue;
                 const double *ml = d.mp_local + (m * NS + s) * NMP;
-                const V3<double> gmu = mk(d.gmu[(m * NS + s) * 3], d.gmu[(m * NS + s) * 3 + 1], d.gmu[(m * NS + s) * 3 + 2]);
-                const double *gt6 = d.gth + (m * NS + s) * 6;
-                const Sym<double> D{gt6[0], gt6[1], gt6[2], gt6[3], gt6[4], gt6[5]};
+                const int om = (m * NS + s) * 3, ot = (m * NS + s) * 6;
+                const V3<double> gmu = mk(d.gmu[om] + d.gmu_r[om], d.gmu[om + 1] + d.gmu_r[om + 1],
+                                          d.gmu[om + 2] + d.gmu_r[om + 2]);
+                const double *gt6 = d.gth + ot, *gr6 = d.gth_r + ot;
+                const Sym<double> D{gt6[0] + gr6[0], gt6[1] + gr6[1], gt6[2] + gr6[2],
+                                    gt6[3] + gr6[3], gt6[4] + gr6[4], gt6[5] + gr6[5]};
                 const double tl[3][3] = {{ml[4], ml[7], ml[8]}, {ml[7], ml[5], ml[9]}, {ml[8], ml[9], ml[6]}};
                 for (int k = 0; k < 3; ++k) {
                     gE[k] = gE[k] + ml[1 + k] * gmu;
@@ -347,6 +355,20 @@ __global__ void __launch_bounds__(128) k_finalize(KParams p, DevState<R> d, doub
     }
 }
 
+// Join of the reciprocal chain into the arrays read by the charge transfer
+// and the polarization solve: permanent field and lone-pair potentials.
+template <typename R>
+__global__ void k_merge_rec(int M, DevState<R> d) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < M * 9) d.efield[k] += d.efield_r[k];
+    if (k < M * 2) d.vlp[k] += d.vlp_r[k];
+}
+template <typename R>
+void launch_merge_rec(const KParams &p, DevState<R> &d, Launch L) {
+    k_merge_rec<R><<<(p.M * 9 + 255) / 256, 256, 0, L.s>>>(p.M, d);
+    count(L);
+}
+
 template <typename R>
 void launch_finalize(const KParams &p, DevState<R> &d, double *forces_out, Launch L) {
     const long long n = (long long)p.M * 4;
@@ -355,12 +377,12 @@ void launch_finalize(const KParams &p, DevState<R> &d, double *forces_out, Launc
 }
 
 // energy totals: out[k] = sum_m epart[m*NTERM + k], out[NTERM] = total (fixed order)
-__global__ void k_energy_reduce(int M, const double *epart, double *out) {
+__global__ void k_energy_reduce(int M, const double *epart, const double *epart_r, double *out) {
     __shared__ double sh[32];
     double tot = 0;
     for (int k = 0; k < NTERM; ++k) {
         double v = 0;
-        for (int m = threadIdx.x; m < M; m += blockDim.x) v += epart[m * NTERM + k];
+        for (int m = threadIdx.x; m < M; m += blockDim.x) v += epart[m * NTERM + k] + epart_r[m * NTERM + k];
         v = block_sum(v, sh);
         if (threadIdx.x == 0) {
             out[k] = v;
@@ -370,8 +392,8 @@ __global__ void k_energy_reduce(int M, const double *epart, double *out) {
     if (threadIdx.x == 0) out[NTERM] = tot;
 }
 
-void launch_energy_reduce(int M, const double *epart, double *out, Launch L) {
-    k_energy_reduce<<<1, 512, 0, L.s>>>(M, epart, out);
+void launch_energy_reduce(int M, const double *epart, const double *epart_r, double *out, Launch L) {
+    k_energy_reduce<<<1, 512, 0, L.s>>>(M, epart, epart_r, out);
     count(L);
 }
 
@@ -451,7 +473,8 @@ void launch_md_kick(int M, double *pos, double *vel, const double *inv_mass, con
     template void launch_pcg_iter_a<R>(const KParams &, DevState<R> &, Launch);                        \
     template void launch_pcg_iter_b<R>(const KParams &, DevState<R> &, double, Launch);                \
     template void launch_pol_energy<R>(const KParams &, DevState<R> &, Launch);                        \
-    template void launch_finalize<R>(const KParams &, DevState<R> &, double *, Launch);
+    template void launch_finalize<R>(const KParams &, DevState<R> &, double *, Launch);                \
+    template void launch_merge_rec<R>(const KParams &, DevState<R> &, Launch);
 INST(float)
 INST(double)
 

@@ -129,15 +129,15 @@ __global__ void __launch_bounds__(128) k_sites(KParams p, DevState<R> d) {
             }
         }
         // clear the per-molecule accumulators of this evaluation
-        for (int k = t; k < NP * 3; k += 8) d.gpt[m * NP * 3 + k] = 0.0;
-        for (int k = t; k < NS * 3; k += 8) d.gmu[m * NS * 3 + k] = 0.0;
-        for (int k = t; k < NS * 6; k += 8) d.gth[m * NS * 6 + k] = 0.0;
-        for (int k = t; k < 9; k += 8) d.efield[m * 9 + k] = 0.0;
+        for (int k = t; k < NP * 3; k += 8) d.gpt[m * NP * 3 + k] = 0.0, d.gpt_r[m * NP * 3 + k] = 0.0;
+        for (int k = t; k < NS * 3; k += 8) d.gmu[m * NS * 3 + k] = 0.0, d.gmu_r[m * NS * 3 + k] = 0.0;
+        for (int k = t; k < NS * 6; k += 8) d.gth[m * NS * 6 + k] = 0.0, d.gth_r[m * NS * 6 + k] = 0.0;
+        for (int k = t; k < 9; k += 8) d.efield[m * 9 + k] = 0.0, d.efield_r[m * 9 + k] = 0.0;
         for (int k = t; k < 18; k += 8) d.d2rec[m * 18 + k] = 0.0;
-        if (t < 2) d.vlp[m * 2 + t] = 0.0, d.lam[m * 2 + t] = 0.0;
-        if (t < 6) d.dvlp[m * 6 + t] = 0.0;
+        if (t < 2) d.vlp[m * 2 + t] = 0.0, d.vlp_r[m * 2 + t] = 0.0, d.lam[m * 2 + t] = 0.0;
+        if (t < 6) d.dvlp[m * 6 + t] = 0.0, d.dvlp_r[m * 6 + t] = 0.0;
         if (t < 3) d.kap[m * 3 + t] = 0.0;
-        if (t < NTERM) d.epart[m * NTERM + t] = 0.0;
+        if (t < NTERM) d.epart[m * NTERM + t] = 0.0, d.epart_r[m * NTERM + t] = 0.0;
     }
     // largest point distance from its O (list margin): one atomic per warp
     const int e = __reduce_max_sync(0xffffffffu, __float_as_int(ext));

@@ -162,6 +162,10 @@ struct DevState {
     double *lam;        // M*2 dE_ct/dV_lp
     double *kap;        // M*3 dE_ct/dV_int
     double *epart;      // M*NTERM per-molecule energy partials
+    // Accumulators of the reciprocal-space chain (SPME and intramolecular
+    // Ewald corrections), which runs on a second stream concurrently with the
+    // real-space kernels; same layouts as the arrays above, merged where used.
+    double *gpt_r, *gmu_r, *gth_r, *efield_r, *vlp_r, *dvlp_r, *epart_r, *efp_r;
     // polarization solve
     double *mu, *res, *zv, *pv, *ap, *efp;   // M*9 each
     R *vecR;            // M*9 the vector of the current T product in the working precision
@@ -706,6 +710,21 @@ template <typename R> void launch_intra_tmu(const KParams &p, DevState<R> &d, do
 template <typename R> void launch_real_polforce(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_intra_polforce(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_finalize(const KParams &p, DevState<R> &d, double *forces_out, Launch L);
+template <typename R> void launch_merge_rec(const KParams &p, DevState<R> &d, Launch L);
+
+// The view of a state whose accumulators are the reciprocal-chain set.
+template <typename R>
+inline DevState<R> rec_view(const DevState<R> &d) {
+    DevState<R> r = d;
+    r.gpt = d.gpt_r;
+    r.gmu = d.gmu_r;
+    r.gth = d.gth_r;
+    r.efield = d.efield_r;
+    r.vlp = d.vlp_r;
+    r.dvlp = d.dvlp_r;
+    r.epart = d.epart_r;
+    return r;
+}
 
 // SPME
 enum SpreadKind { SPREAD_PERM = 0, SPREAD_DIP = 1, SPREAD_LAMBDA = 2, SPREAD_DIP_PCG = 3 };
@@ -725,7 +744,7 @@ template <typename R> void launch_pcg_first(const KParams &p, DevState<R> &d, La
 template <typename R> void launch_pcg_iter_a(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_pcg_iter_b(const KParams &p, DevState<R> &d, double tol_D, Launch L);
 template <typename R> void launch_pol_energy(const KParams &p, DevState<R> &d, Launch L);
-void launch_energy_reduce(int M, const double *epart, double *out, Launch L);
+void launch_energy_reduce(int M, const double *epart, const double *epart_r, double *out, Launch L);
 void launch_begin(double *scal, int *flags, double tol_D, Launch L);
 void launch_water_intra(int M, const double *pos, double *F, double kb, double r0, double ka, double th0, Launch L);
 void launch_sd_step(int M, double *pos, const double *F, double gamma, double cap, Launch L);
