@@ -29,6 +29,7 @@ struct sibfa_ctx {
     cudaGraphExec_t pcg_exec = nullptr;
     int pcg_graph_state = 0;     // 0 untried, 1 in use, -1 unavailable (host loop)
     uint64_t pcg_iter_launches = 0;
+    uint64_t pcg_graph_solves = 0;   // graph solves whose iteration count is not yet folded into launches
     bool capturing = false;
     int prec = SIBFA_PREC_MIXED;
     DevState<float> df{};
@@ -40,6 +41,7 @@ struct sibfa_ctx {
     double *d_energy = nullptr;   // NTERM+1
     double *d_vel = nullptr, *d_invm = nullptr;
     double *h_pin = nullptr;      // pinned staging, M*9*2 + 64 doubles
+    double *h_scal = nullptr;     // pinned copy of the solver scalars of the last solve
     std::vector<void *> allocs;
     std::string err = "no error";
     uint64_t launches = 0;
@@ -177,7 +179,7 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.tl_z, (size_t)M * 3 * TLS);
     AL(d.tl_g1, (size_t)M * 3 * TLS);
     AL(d.tl_g2, (size_t)M * 3 * TLS);
-    AL(d.partial, 2 * ((M * 9 + 255) / 256) + 64);
+    AL(d.partial, 4 * ((M * 9 + 255) / 256) + 64);
     AL(d.scal, 32);
     AL(d.counter, 4);
     AL(d.flags, 4);
@@ -320,6 +322,17 @@ sibfa_status join_rec(sibfa_ctx *ctx) {
     return SIBFA_OK;
 }
 
+// Statistics of the last solve (valid after the call's final synchronisation).
+void solve_stats(sibfa_ctx *ctx) {
+    ctx->last_iters = (int)ctx->h_scal[SC_IT];
+    ctx->last_resid = ctx->h_scal[SC_RES];
+    if (ctx->pcg_graph_solves) {
+        // kernel launches inside the device loop, counted per executed iteration
+        ctx->launches += (uint64_t)ctx->last_iters * ctx->pcg_iter_launches * ctx->pcg_graph_solves;
+        ctx->pcg_graph_solves = 0;
+    }
+}
+
 bool is_device_ptr(const void *p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -361,16 +374,14 @@ sibfa_status matvec(sibfa_ctx *ctx, DevState<R> &d, const double *vec, Launch L)
         sibfa_status st = fork_rec(ctx);
         if (st) return st;
         Launch L2{ctx->s2, L.count};
-        const size_t ng = (size_t)p.K[0] * p.K[1] * p.K[2];
-        CK(cudaMemsetAsync(d.grid, 0, ng * sizeof(R), ctx->s2));
+        // the grid was cleared by the PCG vector kernel that preceded this product
         launch_spread(p, d, SPREAD_DIP_PCG, vec, d.grid, L2);
         st = fft(ctx, d, true, 1);
         if (st) return st;
         launch_convolve(p, d, d.cgrid, 1, 1, L2);
         st = fft(ctx, d, false, 1);
         if (st) return st;
-        launch_gather_field(p, d, d.efp_r, L2);
-        launch_intra_tmu(p, d, d.efp_r, L2);
+        launch_gather_field(p, d, d.efp_r, L2);   // includes the intramolecular part
     }
     { Phase ph(ctx, "real_tmu");  launch_real_tmu(p, d, d.efp, L); }
     if (p.periodic) return join_rec(ctx);
@@ -410,13 +421,12 @@ sibfa_status build_pcg_graph(sibfa_ctx *ctx, DevState<R> &d, int maxit) {
         ctx->capturing = true;
         Launch L{ctx->s, &ctx->launches};
         sibfa_status sm = matvec(ctx, d, d.pv, L);
-        launch_pcg_iter_a(ctx->kp, d, L);
-        launch_pcg_iter_b(ctx->kp, d, 0.0, L);
+        launch_pcg_step(ctx->kp, d, L);
         k_pcg_cond<<<1, 1, 0, ctx->s>>>(h, d.scal, maxit);
         ctx->capturing = false;
         const cudaError_t ec = cudaStreamEndCapture(ctx->s, &out);
         if (sm != SIBFA_OK || ec != cudaSuccess) break;
-        if (cudaGraphInstantiate(&ctx->pcg_exec, g, 0) != cudaSuccess) break;
+        if (cudaGraphInstantiate(&ctx->pcg_exec, g, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) break;
         st = SIBFA_OK;
     } while (0);
     ctx->capturing = false;
@@ -440,11 +450,14 @@ sibfa_status solve(sibfa_ctx *ctx, DevState<R> &d, double tol, Launch L) {
     const int maxit = ctx->opts.pcg_max_iter > 0 ? ctx->opts.pcg_max_iter : 200;
     if (ctx->pcg_graph_state == 0) ctx->pcg_graph_state = build_pcg_graph(ctx, d, maxit) == SIBFA_OK ? 1 : -1;
     if (ctx->pcg_graph_state == 1) {
+        // device-side loop; no host synchronisation: the convergence check is a
+        // flag and the statistics are read at the end of the call
         CK(cudaGraphLaunch(ctx->pcg_exec, ctx->s));
-        CK(cudaMemcpyAsync(h, d.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
-        CK(cudaStreamSynchronize(ctx->s));
-        ctx->launches += (uint64_t)h[SC_IT] * ctx->pcg_iter_launches;
-        it = maxit;   // the device loop has finished
+        launch_pcg_check(d.scal, d.flags, L);
+        CK(cudaMemcpyAsync(ctx->h_scal, d.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+        ctx->pcg_graph_solves += 1;
+        ctx->have_mu = true;
+        return SIBFA_OK;
     }
     for (;;) {
         CK(cudaMemcpyAsync(h, d.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
@@ -452,17 +465,12 @@ sibfa_status solve(sibfa_ctx *ctx, DevState<R> &d, double tol, Launch L) {
         if (h[SC_DONE] != 0.0 || it >= maxit) break;
         st = matvec(ctx, d, d.pv, L);
         if (st) return st;
-        launch_pcg_iter_a(p, d, L);
-        launch_pcg_iter_b(p, d, tol, L);
+        launch_pcg_step(p, d, L);
         ++it;
     }
-    ctx->last_iters = (int)h[SC_IT];
-    ctx->last_resid = h[SC_RES];
+    std::memcpy(ctx->h_scal, h, 16 * sizeof(double));
     ctx->have_mu = true;
-    if (h[SC_DONE] == 0.0) {
-        ctx->err = "PCG did not reach the tolerance within pcg_max_iter";
-        return SIBFA_E_NOT_CONVERGED;
-    }
+    launch_pcg_check(d.scal, d.flags, L);
     return SIBFA_OK;
 }
 
@@ -547,6 +555,10 @@ sibfa_status check_flags(sibfa_ctx *ctx, int flags) {
         ctx->err = "charge-transfer denominator ae + V - ah <= 0";
         return SIBFA_E_CT_DENOM;
     }
+    if (flags & F_NOCONV) {
+        ctx->err = "PCG did not reach the tolerance within pcg_max_iter";
+        return SIBFA_E_NOT_CONVERGED;
+    }
     return SIBFA_OK;
 }
 
@@ -565,6 +577,7 @@ sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_ene
     }
     sibfa_status st0 = enter(ctx);
     if (st0) return st0;
+    CK(cudaMemsetAsync(d.flags, 0, sizeof(int), ctx->s));
     if (pos) {
         if (is_device_ptr(pos)) {
             CK(cudaMemcpyAsync(d.pos, pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
@@ -598,8 +611,10 @@ sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_ene
     CK(cudaGetLastError());
     if (forces && !is_device_ptr(forces)) std::memcpy(forces, h + 32, nb);
     if (mu_out && !is_device_ptr(mu_out)) std::memcpy(mu_out, h + 32, nb);
+    solve_stats(ctx);
     sibfa_status fl = check_flags(ctx, *(int *)(h + 16));
-    if (fl) return fl;
+    if (fl && fl != SIBFA_E_NOT_CONVERGED) return fl;
+    if (fl) st = fl;
     if (e) {
         e->elec = h[T_ELEC];
         e->pen = h[T_PEN];
@@ -672,6 +687,7 @@ static sibfa_status md_impl(sibfa_ctx *ctx, double *pos, double *vel, const doub
     if (st_e) return st_e;
     k_inverse<<<(M * 3 + 255) / 256, 256, 0, ctx->s>>>(M * 3, masses, ctx->d_invm);
     ctx->launches += 1;
+    CK(cudaMemsetAsync(d.flags, 0, sizeof(int), ctx->s));
     CK(cudaMemcpyAsync(d.pos, pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
     const sibfa_run_opts &o = ctx->opts;
     const double th0 = o.md_theta0_deg * M_PI / 180.0;
@@ -696,6 +712,7 @@ static sibfa_status md_impl(sibfa_ctx *ctx, double *pos, double *vel, const doub
     if (st_e) return st_e;
     CK(cudaStreamSynchronize(ctx->s));
     ctx->md_forces_valid = true;
+    solve_stats(ctx);
     sibfa_status fl = check_flags(ctx, *(int *)(h + 16));
     if (fl) return fl;
     if (e) {
@@ -743,8 +760,13 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
     ctx->opts = *opts;
     ctx->prec = opts->precision;
     ctx->us = (cudaStream_t)opts->stream;
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    // the reciprocal chain is a sequence of small latency-bound kernels: it
+    // gets the higher priority so that its blocks start ahead of the large
+    // real-space grids that run beside it
     if (cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctx->s2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ctx->s2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -768,7 +790,8 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
         if (st) break;
         st = dalloc(ctx, &ctx->d_energy, 16);
         if (st) break;
-        if (cudaMallocHost((void **)&ctx->h_pin, ((size_t)ctx->M * 9 * 2 + 64) * sizeof(double)) != cudaSuccess) {
+        if (cudaMallocHost((void **)&ctx->h_pin, ((size_t)ctx->M * 9 * 2 + 64) * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost((void **)&ctx->h_scal, 16 * sizeof(double)) != cudaSuccess) {
             ctx->err = "cudaMallocHost failed";
             st = SIBFA_E_OOM;
             break;
@@ -821,6 +844,7 @@ static sibfa_status minimize_impl(sibfa_ctx *ctx, double *pos, int n, double cap
     const double th0 = o.md_theta0_deg * M_PI / 180.0;
     sibfa_status st_e = enter(ctx);
     if (st_e) return st_e;
+    CK(cudaMemsetAsync(d.flags, 0, sizeof(int), ctx->s));
     CK(cudaMemcpyAsync(d.pos, pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
     for (int k = 0; k < n; ++k) {
         sibfa_status st = evaluate<R>(ctx, true, false, tol);
@@ -831,10 +855,16 @@ static sibfa_status minimize_impl(sibfa_ctx *ctx, double *pos, int n, double cap
     CK(cudaMemcpyAsync(pos, d.pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
     double *h = ctx->h_pin;
     CK(cudaMemcpyAsync(h, ctx->d_energy, (NTERM + 1) * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaMemcpyAsync((int *)(h + 16), d.flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
     st_e = leave(ctx);
     if (st_e) return st_e;
     CK(cudaStreamSynchronize(ctx->s));
     ctx->md_forces_valid = false;
+    solve_stats(ctx);
+    {
+        sibfa_status fl = check_flags(ctx, *(int *)(h + 16));
+        if (fl) return fl;
+    }
     if (e) {
         e->elec = h[T_ELEC]; e->pen = h[T_PEN]; e->rep = h[T_REP]; e->disp = h[T_DISP];
         e->xdisp = h[T_XDISP]; e->pol = h[T_POL]; e->ct = h[T_CT]; e->total = h[NTERM];
@@ -931,6 +961,7 @@ void sibfa_destroy(sibfa_ctx *ctx) {
     for (auto e : ctx->event_pool) cudaEventDestroy(e);
     for (void *p : ctx->allocs) cudaFree(p);
     if (ctx->h_pin) cudaFreeHost(ctx->h_pin);
+    if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     if (ctx->s) cudaStreamDestroy(ctx->s);
     if (ctx->s2) cudaStreamDestroy(ctx->s2);
     delete ctx;

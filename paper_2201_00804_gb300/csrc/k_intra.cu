@@ -143,44 +143,6 @@ void launch_intra_perm(const KParams &p, DevState<R> &d, Launch L) {
     count(L);
 }
 
-// PCG product, intramolecular part: one thread per polarizable atom, out +=
-// minus the erf part of the field from the other two atoms' dipoles, plus the
-// self term of its own dipole (dipoles: the working-precision PCG vector).
-template <typename R>
-__global__ void k_intra_tmu(KParams p, DevState<R> d, double *out) {
-    if (d.flags[1]) return;   // solver already converged
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= p.M * 3) return;
-    const int m = t / 3, a = t % 3;
-    const R al = sc<R>(p).alpha;
-    const R cself = R(4.0 / 3.0) * al * al * al * R(0.56418958354775628695);
-    const R *v = d.vecR + m * 9;
-    const V3<R> Xa = opt(d, m, a);
-    V3<R> E = cself * mk(v[a * 3], v[a * 3 + 1], v[a * 3 + 2]);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        if (b == a) continue;
-        const V3<R> xv = Xa - opt(d, m, b);
-        R g[4];
-        g_erf_s<R, 3>(dot(xv, xv), al, g);
-        Mp<R> s{};
-        s.mu = mk(v[b * 3], v[b * 3 + 1], v[b * 3 + 2]);
-        FieldTerms<R> f;
-        source_field<R, 1>(s, xv, g, f);
-        E = E + f.d1;
-    }
-    out[m * 9 + a * 3] += double(E.x);
-    out[m * 9 + a * 3 + 1] += double(E.y);
-    out[m * 9 + a * 3 + 2] += double(E.z);
-}
-
-template <typename R>
-void launch_intra_tmu(const KParams &p, DevState<R> &d, double *out, Launch L) {
-    const int n = p.M * 3;
-    k_intra_tmu<R><<<(n + 127) / 128, 128, 0, L.s>>>(p, d, out);
-    count(L);
-}
-
 __constant__ int c_pair3[3][2] = {{0, 1}, {0, 2}, {1, 2}};
 
 // Force pass at fixed induced dipoles and lambda charges.  Lanes 0-11:
@@ -266,7 +228,6 @@ void launch_intra_polforce(const KParams &p, DevState<R> &d, Launch L) {
 
 #define INST(R)                                                                                         \
     template void launch_intra_perm<R>(const KParams &, DevState<R> &, Launch);                         \
-    template void launch_intra_tmu<R>(const KParams &, DevState<R> &, double *, Launch);                \
     template void launch_intra_polforce<R>(const KParams &, DevState<R> &, Launch);
 INST(float)
 INST(double)

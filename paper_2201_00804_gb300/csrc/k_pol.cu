@@ -2,6 +2,10 @@
 // conjugate gradient with FP64 vectors and dot products), intramolecular
 // Ewald corrections, the chain rule from point gradients and multipole
 // sensitivities to atom forces, energy totals and the velocity-Verlet kick.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "sibfa_internal.cuh"
 
 namespace sibfa {
@@ -60,9 +64,18 @@ __device__ inline bool last_block_sum2(double a, double b, double *partial, unsi
 
 __device__ inline double apol(const KParams &p, int k) { return p.a_pol[(k / 3) % 3]; }
 
+// Zero the real SPME grid (input of the next spread of the PCG product).
+template <typename R>
+__device__ inline void zero_grid(const KParams &p, const DevState<R> &d, size_t tid, size_t nth) {
+    if (!p.periodic) return;
+    const size_t ng = (size_t)p.K[0] * p.K[1] * p.K[2];
+    for (size_t k = tid; k < ng; k += nth) d.grid[k] = R(0);
+}
+
 template <typename R>
 __global__ void k_pcg_init(KParams p, DevState<R> d, int warm) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    zero_grid(p, d, k, (size_t)gridDim.x * blockDim.x);
     if (k >= p.M * 9) return;
     if (!warm) d.mu[k] = apol(p, k) * d.efield[k];
     d.vecR[k] = R(d.mu[k]);
@@ -74,6 +87,7 @@ __global__ void k_pcg_init(KParams p, DevState<R> d, int warm) {
 template <typename R>
 __global__ void k_pcg_first(KParams p, DevState<R> d) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    zero_grid(p, d, k, (size_t)gridDim.x * blockDim.x);
     double rz = 0, rr = 0;
     if (k < p.M * 9) {
         const double a = apol(p, k);
@@ -98,79 +112,115 @@ __global__ void k_pcg_first(KParams p, DevState<R> d) {
     }
 }
 
-// ap = p / alpha - E(p); alpha_k = rz / p.ap
-template <typename R>
-__global__ void k_pcg_a(KParams p, DevState<R> d) {
-    if (d.flags[1]) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    double pap = 0;
-    if (k < p.M * 9) {
-        const double ap = d.pv[k] / apol(p, k) - (d.efp[k] + d.efp_r[k]);
-        d.ap[k] = ap;
-        pap = d.pv[k] * ap;
+// Sum of the nb block partials at part[0], part[stride], ... in a fixed
+// order (lane l takes l, l+32, ...; then a fixed tree): every block obtains
+// the bit-identical total.
+__device__ inline double sum_partials(const double *part, int nb, int stride, double *sh) {
+    if (threadIdx.x < 32) {
+        double v = 0;
+        for (int b = threadIdx.x; b < nb; b += 32) v += __ldcg(part + (size_t)b * stride);
+        v = warp_sum(v);
+        if (threadIdx.x == 0) sh[0] = v;
     }
-    double t, u;
-    if (last_block_sum2(pap, 0.0, d.partial, d.counter, t, u)) {
-        d.scal[S_PAP] = t;
-        d.scal[S_ALPHA] = d.scal[S_RZ] / t;
-    }
+    __syncthreads();
+    const double t = sh[0];
+    __syncthreads();
+    return t;
 }
 
-// mu += a p, r -= a ap, z = alpha r; beta = rz_new / rz; residual check
+// One PCG iteration after the product T p (cooperative launch, grid-stride):
+//   (a) ap = p / alpha - E(p), alpha_k = rz / p.ap
+//   (b) mu += alpha_k p, r -= alpha_k ap, z = alpha r, beta = rz_new / rz,
+//       residual check
+//   (c) p = z + beta p, working-precision copy of p, clear the field
+//       accumulators and the SPME grid for the next product.
 template <typename R>
-__global__ void k_pcg_b(KParams p, DevState<R> d) {
-    if (d.flags[1]) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const double al = d.scal[S_ALPHA];
+__global__ void __launch_bounds__(PB) k_pcg_step(KParams p, DevState<R> d) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    __shared__ double sh[32];
+    if (d.flags[1]) return;   // converged before this launch: uniform over the grid
+    const int n = p.M * 9;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    const int nb = gridDim.x;
+    const double rz_old = d.scal[S_RZ], tol = d.scal[S_TOL];
+    double pap = 0;
+    for (int k = tid; k < n; k += nth) {
+        const double ap = d.pv[k] / apol(p, k) - (d.efp[k] + d.efp_r[k]);
+        d.ap[k] = ap;
+        pap += d.pv[k] * ap;
+    }
+    pap = block_sum(pap, sh);
+    if (threadIdx.x == 0) d.partial[blockIdx.x] = pap;
+    grid.sync();
+    const double tpap = sum_partials(d.partial, nb, 1, sh);
+    const double al = rz_old / tpap;
     double rz = 0, rr = 0;
-    if (k < p.M * 9) {
+    for (int k = tid; k < n; k += nth) {
         const double a = apol(p, k);
         d.mu[k] += al * d.pv[k];
         const double r = d.res[k] - al * d.ap[k];
         d.res[k] = r;
         d.zv[k] = a * r;
-        rz = r * a * r;
-        rr = a * r * a * r;
+        rz += r * a * r;
+        rr += a * r * a * r;
     }
-    double trz, trr;
-    if (last_block_sum2(rz, rr, d.partial, d.counter, trz, trr)) {
-        d.scal[S_BETA] = trz / d.scal[S_RZ];
+    rz = block_sum(rz, sh);
+    rr = block_sum(rr, sh);
+    if (threadIdx.x == 0) {
+        d.partial[nb + 2 * blockIdx.x] = rz;
+        d.partial[nb + 2 * blockIdx.x + 1] = rr;
+    }
+    grid.sync();
+    const double trz = sum_partials(d.partial + nb, nb, 2, sh);
+    const double trr = sum_partials(d.partial + nb + 1, nb, 2, sh);
+    const double beta = trz / rz_old;
+    const double res = sqrt(trr / (p.M * 3)) * 4.80321;
+    const bool done = res < tol;
+    if (tid == 0) {
+        d.scal[S_PAP] = tpap;
+        d.scal[S_ALPHA] = al;
+        d.scal[S_BETA] = beta;
         d.scal[S_RZ] = trz;
-        const double res = sqrt(trr / (p.M * 3)) * 4.80321;
         d.scal[S_RES] = res;
         d.scal[S_IT] += 1.0;
-        if (res < d.scal[S_TOL]) {
+        if (done) {
             d.scal[S_DONE] = 1.0;
             d.flags[1] = 1;
         }
     }
-}
-
-// p = z + beta p ; clear the field accumulator for the next product
-template <typename R>
-__global__ void k_pcg_c(KParams p, DevState<R> d) {
-    if (d.flags[1]) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= p.M * 9) return;
-    const double pk = d.zv[k] + d.scal[S_BETA] * d.pv[k];
-    d.pv[k] = pk;
-    d.vecR[k] = R(pk);
-    d.efp[k] = 0.0;
-    d.efp_r[k] = 0.0;
+    if (done) return;   // uniform: every block computed the same residual
+    for (int k = tid; k < n; k += nth) {
+        const double pk = d.zv[k] + beta * d.pv[k];
+        d.pv[k] = pk;
+        d.vecR[k] = R(pk);
+        d.efp[k] = 0.0;
+        d.efp_r[k] = 0.0;
+    }
+    zero_grid(p, d, tid, nth);
 }
 
 static inline unsigned nblk(int n) { return (unsigned)((n + PB - 1) / PB); }
 
-// start of an evaluation: clear solver scalars and error flags, set the tolerance
+// start of an evaluation: clear the solver scalars and the converged flag,
+// set the tolerance (error flags accumulate over the evaluations of one call)
 __global__ void k_begin(double *scal, int *flags, double tol_D) {
     if (threadIdx.x < 16) scal[threadIdx.x] = 0.0;
     __syncthreads();
     if (threadIdx.x == 0) {
         scal[S_TOL] = tol_D;
-        flags[0] = 0;   // error flags
         flags[1] = 0;   // PCG converged (integer copy of scal[S_DONE] for the loop kernels)
     }
 }
+// after the solve: record a solve that stopped at the iteration limit
+__global__ void k_pcg_check(const double *scal, int *flags) {
+    if (scal[S_DONE] == 0.0) atomicOr(flags, F_NOCONV);
+}
+void launch_pcg_check(const double *scal, int *flags, Launch L) {
+    k_pcg_check<<<1, 1, 0, L.s>>>(scal, flags);
+    count(L);
+}
+
 void launch_begin(double *scal, int *flags, double tol_D, Launch L) {
     k_begin<<<1, 32, 0, L.s>>>(scal, flags, tol_D);
     count(L);
@@ -186,16 +236,31 @@ void launch_pcg_first(const KParams &p, DevState<R> &d, Launch L) {
     k_pcg_first<R><<<nblk(p.M * 9), PB, 0, L.s>>>(p, d);
     count(L);
 }
+// Cooperative launch of the PCG step: a grid-stride kernel with as many
+// blocks as can be resident at once (at most one per 256 vector entries).
 template <typename R>
-void launch_pcg_iter_a(const KParams &p, DevState<R> &d, Launch L) {
-    k_pcg_a<R><<<nblk(p.M * 9), PB, 0, L.s>>>(p, d);
+void launch_pcg_step(const KParams &p, DevState<R> &d, Launch L) {
+    static int per_sm[2] = {0, 0}, n_sm = 0;
+    int &ps = per_sm[sizeof(R) == 8];
+    if (ps == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_pcg_step<R>, PB, 0);
+        if (ps < 1) ps = 1;
+    }
+    const unsigned grid = (unsigned)std::min<long long>(nblk(p.M * 9), (long long)ps * n_sm);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(PB);
+    cfg.stream = L.s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_pcg_step<R>, p, d);
     count(L);
-}
-template <typename R>
-void launch_pcg_iter_b(const KParams &p, DevState<R> &d, double, Launch L) {
-    k_pcg_b<R><<<nblk(p.M * 9), PB, 0, L.s>>>(p, d);
-    k_pcg_c<R><<<nblk(p.M * 9), PB, 0, L.s>>>(p, d);
-    count(L, 2);
 }
 
 // E_pol = -1/2 ke mu . E (value at the solution)
@@ -470,8 +535,7 @@ void launch_md_kick(int M, double *pos, double *vel, const double *inv_mass, con
 #define INST(R)                                                                                        \
     template void launch_pcg_init<R>(const KParams &, DevState<R> &, int, Launch);                     \
     template void launch_pcg_first<R>(const KParams &, DevState<R> &, Launch);                         \
-    template void launch_pcg_iter_a<R>(const KParams &, DevState<R> &, Launch);                        \
-    template void launch_pcg_iter_b<R>(const KParams &, DevState<R> &, double, Launch);                \
+    template void launch_pcg_step<R>(const KParams &, DevState<R> &, Launch);                          \
     template void launch_pol_energy<R>(const KParams &, DevState<R> &, Launch);                        \
     template void launch_finalize<R>(const KParams &, DevState<R> &, double *, Launch);                \
     template void launch_merge_rec<R>(const KParams &, DevState<R> &, Launch);

@@ -357,7 +357,11 @@ void launch_gather_perm(const KParams &p, DevState<R> &d, Launch L) {
     count(L);
 }
 
-// Field on the polarizable atoms from the dipole grid: out += -grad phi / ke.
+// PCG product, reciprocal and intramolecular part at each polarizable atom:
+// out += -grad phi / ke from the dipole grid (lanes 0-24, one stencil row
+// each) plus, from lane 25, the self term of the atom's own dipole minus the
+// erf part of the field of the other two atoms' dipoles (dipoles: the
+// working-precision PCG vector).
 template <typename R>
 __global__ void __launch_bounds__(32 * GW) k_gather_field(KParams p, DevState<R> d, double *out) {
     __shared__ R buf[GW][4 * 33];
@@ -366,15 +370,42 @@ __global__ void __launch_bounds__(32 * GW) k_gather_field(KParams p, DevState<R>
     const int t = blockIdx.x * GW + w;
     if (t >= p.M * 3) return;
     const int m = t / 3, a = t % 3;
+    const Scal<R> &S = sc<R>(p);
     Axis<R, 1> X, Y, Z;
     axis_weights<R, 1>(p, d, m, a, 0, X);
     axis_weights<R, 1>(p, d, m, a, 1, Y);
     axis_weights<R, 1>(p, d, m, a, 2, Z);
-    R v[4] = {R(0), R(0), R(0), R(0)};
-    if (lane < 25) gather_row<R, 1>(p, d.grid, X, Y, Z, lane, v);
-    const R vals[3] = {v[1], v[2], v[3]};
+    R vals[3] = {R(0), R(0), R(0)};
+    if (lane < 25) {
+        R v[4];
+        gather_row<R, 1>(p, d.grid, X, Y, Z, lane, v);
+        vals[0] = -v[1] * S.ike;
+        vals[1] = -v[2] * S.ike;
+        vals[2] = -v[3] * S.ike;
+    } else if (lane == 25) {
+        const R al = S.alpha;
+        const R cself = R(4.0 / 3.0) * al * al * al * R(0.56418958354775628695);
+        const R *v = d.vecR + m * 9;
+        const V3<R> Xa = my_pt(d, m, a);
+        V3<R> E = cself * mk(v[a * 3], v[a * 3 + 1], v[a * 3 + 2]);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (b == a) continue;
+            const V3<R> xv = Xa - my_pt(d, m, b);
+            R g[4];
+            g_erf_s<R, 3>(dot(xv, xv), al, g);
+            Mp<R> s{};
+            s.mu = mk(v[b * 3], v[b * 3 + 1], v[b * 3 + 2]);
+            FieldTerms<R> f;
+            source_field<R, 1>(s, xv, g, f);
+            E = E + f.d1;
+        }
+        vals[0] = E.x;
+        vals[1] = E.y;
+        vals[2] = E.z;
+    }
     const R s = warp_transpose_sum<R, 3>(vals, buf[w], lane);
-    if (lane < 3) out[m * 9 + a * 3 + lane] -= (double)(s * sc<R>(p).ike);
+    if (lane < 3) out[m * 9 + a * 3 + lane] += (double)s;
 }
 
 template <typename R>

@@ -21,7 +21,7 @@ constexpr int ORDER = 5;       // B-spline order of the SPME
 constexpr int TLS = 3 * MAXN;  // T-pair list slots per polarizable atom
 
 // error flags (bitwise, device side)
-enum { F_CUTOFF = 1, F_NEIGHBOR = 2, F_CTDEN = 4, F_NAN = 8 };
+enum { F_CUTOFF = 1, F_NEIGHBOR = 2, F_CTDEN = 4, F_NAN = 8, F_NOCONV = 16 };
 
 // Scalars read inside pair loops, rounded once per precision on the host so
 // that the FP32 kernels do no FP64 conversion in their loops.
@@ -705,8 +705,6 @@ template <typename R> void launch_ct(const KParams &p, DevState<R> &d, Launch L)
 template <typename R> void launch_intra_perm(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_real_tmu(const KParams &p, DevState<R> &d, double *out,
                                            Launch L);
-template <typename R> void launch_intra_tmu(const KParams &p, DevState<R> &d, double *out,
-                                            Launch L);
 template <typename R> void launch_real_polforce(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_intra_polforce(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_finalize(const KParams &p, DevState<R> &d, double *forces_out, Launch L);
@@ -741,11 +739,11 @@ template <typename R> void launch_influence_copy(const KParams &p, DevState<R> &
 // PCG
 template <typename R> void launch_pcg_init(const KParams &p, DevState<R> &d, int warm, Launch L);
 template <typename R> void launch_pcg_first(const KParams &p, DevState<R> &d, Launch L);
-template <typename R> void launch_pcg_iter_a(const KParams &p, DevState<R> &d, Launch L);
-template <typename R> void launch_pcg_iter_b(const KParams &p, DevState<R> &d, double tol_D, Launch L);
+template <typename R> void launch_pcg_step(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_pol_energy(const KParams &p, DevState<R> &d, Launch L);
 void launch_energy_reduce(int M, const double *epart, const double *epart_r, double *out, Launch L);
 void launch_begin(double *scal, int *flags, double tol_D, Launch L);
+void launch_pcg_check(const double *scal, int *flags, Launch L);
 void launch_water_intra(int M, const double *pos, double *F, double kb, double r0, double ka, double th0, Launch L);
 void launch_sd_step(int M, double *pos, const double *F, double gamma, double cap, Launch L);
 enum { SC_RZ = 0, SC_RES = 4, SC_IT = 6, SC_DONE = 7, SC_TOL = 8 };

@@ -89,3 +89,22 @@ def test_results_are_deterministic():
     a = run_gpu(s, o, pkg.PREC_FP64, 1e-10)
     b = run_gpu(s, o, pkg.PREC_FP64, 1e-10)
     assert a["terms"]["total"] == pytest.approx(b["terms"]["total"], rel=1e-13)
+
+
+def test_solver_limit_reports_not_converged():
+    """A solve stopped by pcg_max_iter returns NOT_CONVERGED (status -3) from
+    the device-side loop, and the statistics show the one iteration done."""
+    import paper_2201_00804_gb300 as pkg
+    s, o = _cases()["water216"]
+    ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
+                           ewald_alpha=o["ewald"], pcg_tol_D=1e-12, pcg_max_iter=1, precision=pkg.PREC_FP64,
+                           warm_start=False)
+    F = np.zeros(s.n_mol * 9)
+    try:
+        with pytest.raises(pkg.SibfaError) as ei:
+            pkg.sibfa_energy_forces(ctx, s.pos.reshape(-1), F)
+        assert ei.value.status == -3
+        it, _ = pkg.sibfa_last_stats(ctx)
+        assert it == 1
+    finally:
+        pkg.sibfa_destroy(ctx)
