@@ -172,6 +172,8 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.ap, M * 9);
     AL(d.efp, M * 9);
     AL(d.vecR, M * 9);
+    AL(d.muR, M * 9);
+    AL(d.lamR, M * 2);
     AL(d.tl_n, M * 3);
     AL(d.tl_j, (size_t)M * 3 * TLS);
     AL(d.tl_x, (size_t)M * 3 * TLS);
@@ -523,7 +525,7 @@ sibfa_status evaluate(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, doubl
             if (sf) return sf;
             Phase ph(ctx, "spme_polforce", ctx->s2);
             CK(cudaMemsetAsync(d.grid, 0, 2 * ng * sizeof(R), ctx->s2));
-            launch_spread(p, d, SPREAD_DIP, d.mu, d.grid, L2);
+            launch_spread(p, d, SPREAD_DIP, nullptr, d.grid, L2);
             launch_spread(p, d, SPREAD_LAMBDA, nullptr, d.grid + ng, L2);
             if ((sf = fft(ctx, d, true, 2))) return sf;
             launch_convolve(p, d, d.cgrid, 2, 0, L2);

@@ -462,7 +462,7 @@ __device__ __forceinline__ void polf_pair(const KParams &p, const DevState<R> &d
         if (PER) g_erfc<R, 5>(r, rinv, S.alpha, g);
         else g_bare<R, 5>(rinv, g);
         Mp<R> ms{};
-        ms.q = R(d.lam[j * 2 + s]);
+        ms.q = d.lamR[j * 2 + s];
         FieldTerms<R> f;
         source_field<R, 3>(ms, x, g, f);
         A.gr = A.gr + target_grad(mt, ms, x, g, f);
@@ -477,8 +477,8 @@ __device__ __forceinline__ void polf_pair(const KParams &p, const DevState<R> &d
     g[5] = R(0);
     if (KIND == 0) {   // induced dipole of atom s of j at target site w
         Mp<R> ms{};
-        const double *mj = d.mu + j * 9 + s * 3;
-        ms.mu = mk(R(mj[0]), R(mj[1]), R(mj[2]));
+        const R *mj = d.muR + j * 9 + s * 3;
+        ms.mu = mk(mj[0], mj[1], mj[2]);
         FieldTerms<R> f;
         source_field<R, 3>(ms, x, g, f);
         A.gr = A.gr + target_grad(mt, ms, x, g, f);
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d)
     const V3<R> ot = my_pt(d, i, w);
     const Mp<R> mt = load_mp(d.gmp + (i * NS + w) * NMP);
     V3<R> mui = mk(R(0), R(0), R(0));
-    if (w < 3) mui = mk(R(d.mu[i * 9 + w * 3]), R(d.mu[i * 9 + w * 3 + 1]), R(d.mu[i * 9 + w * 3 + 2]));
+    if (w < 3) mui = mk(d.muR[i * 9 + w * 3], d.muR[i * 9 + w * 3 + 1], d.muR[i * 9 + w * 3 + 2]);
     const R rc2 = sc<R>(p).rc2;
     PfAcc<R> A;
     A.gr = mk(R(0), R(0), R(0));
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d)
                 rs[s] = dO + mk(__ldg(offj + s * 3), __ldg(offj + s * 3 + 1), __ldg(offj + s * 3 + 2));
                 const V3<R> x = ot - rs[s];
                 const bool in = !PER || dot(x, x) < rc2;
-                const bool want = s < 3 || (s < NS ? w < 3 : d.lam[j * 2 + s - NS] != 0.0);
+                const bool want = s < 3 || (s < NS ? w < 3 : d.lamR[j * 2 + s - NS] != R(0));
                 if (in && want) bits |= 1u << s;
             }
         }

@@ -263,13 +263,19 @@ void launch_pcg_step(const KParams &p, DevState<R> &d, Launch L) {
     count(L);
 }
 
-// E_pol = -1/2 ke mu . E (value at the solution)
+// E_pol = -1/2 ke mu . E (value at the solution); working-precision copies
+// of mu and of the CT lambdas for the force pass
 template <typename R>
 __global__ void k_pol_energy(KParams p, DevState<R> d) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= p.M) return;
     double e = 0;
-    for (int k = 0; k < 9; ++k) e += d.mu[m * 9 + k] * d.efield[m * 9 + k];
+    for (int k = 0; k < 9; ++k) {
+        e += d.mu[m * 9 + k] * d.efield[m * 9 + k];
+        d.muR[m * 9 + k] = R(d.mu[m * 9 + k]);
+    }
+    d.lamR[m * 2] = R(d.lam[m * 2]);
+    d.lamR[m * 2 + 1] = R(d.lam[m * 2 + 1]);
     d.epart[m * NTERM + T_POL] = -0.5 * p.ke * e;
 }
 template <typename R>

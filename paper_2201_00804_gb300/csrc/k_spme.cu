@@ -54,9 +54,9 @@ __device__ inline void line_weight(const Axis<R, NDER> &A, int i, int &g, R (&w)
 // the multipole operator q + mu.grad + (1/3) Theta:grad grad applied to the
 // B-spline weights at the 5 grid points of their row.
 // kind PERM: 5 sites per molecule with their multipoles;
-// kind DIP: 3 polarizable atoms with dipoles vec[m*9 + a*3 + c];
+// kind DIP: 3 polarizable atoms with the induced dipoles (d.muR);
 // kind DIP_PCG: the same from the working-precision PCG vector;
-// kind LAMBDA: 2 lone pairs with charges d.lam.
+// kind LAMBDA: 2 lone pairs with the charge-transfer lambdas (d.lamR).
 template <typename R>
 __global__ void __launch_bounds__(256) k_spread(KParams p, DevState<R> d, int kind, const double *vec, R *grid) {
     const bool pcg = kind == SPREAD_DIP_PCG;
@@ -72,9 +72,9 @@ __global__ void __launch_bounds__(256) k_spread(KParams p, DevState<R> d, int ki
     Mp<R> mp{};
     if (kind == SPREAD_PERM) mp = load_mp(d.gmp + (m * NS + a) * NMP);
     else if (kind == SPREAD_DIP) {
-        if (pcg) mp.mu = mk(d.vecR[m * 9 + a * 3], d.vecR[m * 9 + a * 3 + 1], d.vecR[m * 9 + a * 3 + 2]);
-        else mp.mu = mk(R(vec[m * 9 + a * 3]), R(vec[m * 9 + a * 3 + 1]), R(vec[m * 9 + a * 3 + 2]));
-    } else mp.q = R(d.lam[m * 2 + a]);
+        const R *v = pcg ? d.vecR : d.muR;
+        mp.mu = mk(v[m * 9 + a * 3], v[m * 9 + a * 3 + 1], v[m * 9 + a * 3 + 2]);
+    } else mp.q = d.lamR[m * 2 + a];
     Axis<R, 2> X, Y, Z;
     axis_weights<R, 2>(p, d, m, pt, 0, X);
     axis_weights<R, 2>(p, d, m, pt, 1, Y);

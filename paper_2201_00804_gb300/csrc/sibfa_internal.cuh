@@ -169,6 +169,7 @@ struct DevState {
     // polarization solve
     double *mu, *res, *zv, *pv, *ap, *efp;   // M*9 each
     R *vecR;            // M*9 the vector of the current T product in the working precision
+    R *muR, *lamR;      // M*9, M*2 induced dipoles and CT lambdas in the working precision (force pass)
     // Real-space T pairs recorded by the permanent pass: for polarizable atom
     // t = 3 m + a, entries [t*TLS, t*TLS + tl_n[t]) hold the partner atom
     // (3 j + b), the displacement x = r_t - r_jb and the Thole-damped kernel
