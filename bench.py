@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the FP64 GPU path")
+    ap.add_argument("--workload", default="water4096", choices=["water4096", "clusters4096"])
     return ap.parse_args()
 
 
@@ -263,6 +265,69 @@ def run_reference(args, dist, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+WORKLOADS = {
+    "water4096": WORKLOAD,
+    "clusters4096": ("clusters4096: 4096 independent gas-phase water clusters, sizes uniform in 2-32 (70,240 waters, "
+                     "210,720 atoms), all pairs within each cluster, no cutoff or Ewald, one context and one launch "
+                     "per kernel, PCG 1e-6 D per cluster with warm start, velocity-Verlet NVE 0.5 fs from 300 K"),
+}
+
+
+def setup(name, pkg, synth, precision, stream):
+    """Context, device arrays and unit counts of a workload."""
+    import torch
+    if name == "water4096":
+        s, o = synth.make_config("water4096")
+        ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
+                               ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"], precision=precision,
+                               warm_start=True, stream=stream)
+        make_api = lambda: pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"],  # noqa: E731
+                                            grid=o["grid"], ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"],
+                                            precision=precision, warm_start=True, stream=stream)
+        seed = 2
+    else:
+        s, start, _ = synth.make_cluster_batch(4096, seed=4)
+        o = {"rc": None, "cluster_start": start}
+        ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=False, pcg_tol_D=1e-6, precision=precision,
+                               warm_start=True, stream=stream, cluster_start=start)
+        make_api = lambda: pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=False, pcg_tol_D=1e-6,  # noqa: E731
+                                            precision=precision, warm_start=True, stream=stream,
+                                            cluster_start=start)
+        seed = 4
+    pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
+    vel = torch.tensor(synth.maxwell_velocities(s, 300.0, seed=seed).reshape(-1), dtype=torch.float64, device="cuda")
+    masses = torch.tensor(s.masses().reshape(-1), dtype=torch.float64, device="cuda")
+    return s, o, ctx, make_api, pos, vel, masses
+
+
+def count_units_clusters(start, M):
+    """Unit counts of the permanent kernel for all intramolecular-free pairs inside clusters."""
+    n = np.diff(np.asarray(start, dtype=np.int64))
+    pairs = int((n * (n - 1)).sum())          # ordered molecule pairs (full list)
+    return dict(site_pairs=25 * pairs, pen_atom_atom=9 * pairs, pen_atom_mid=6 * pairs, pen_mid_atom=6 * pairs,
+                thole_pairs=15 * pairs, lp_pairs=10 * pairs)
+
+
+def timed_steps(pkg, ctx, pos, vel, masses, steps, stream, flush, dt_fs=0.5, keep=False):
+    """steps velocity-Verlet steps, each timed with CUDA events on the
+    caller's stream after an L2 flush; returns (ms total, iterations, snapshots)."""
+    import torch
+    total, iters, snaps = 0.0, [], []
+    for _ in range(steps):
+        flush.zero_()                       # evict L2 (512 MB > 129 MB) before every timed step
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pkg.sibfa_md_steps(ctx, pos, vel, masses, dt_fs, 1)
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b)
+        iters.append(pkg.sibfa_last_stats(ctx)[0])
+        if keep:
+            snaps.append(pos.clone())
+    return total, iters, snaps
+
+
 def main():
     args = parse()
     dist, rank, ws = dist_setup()
@@ -278,44 +343,24 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     build.build()
-    s, o = synth.make_config("water4096")
-    M = s.n_mol
     stream = torch.cuda.current_stream()
-    ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
-                           ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"], precision=pkg.PREC_MIXED,
-                           warm_start=True, stream=stream)
-    pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
-    vel = torch.tensor(synth.maxwell_velocities(s, 300.0, seed=2).reshape(-1), dtype=torch.float64, device="cuda")
-    masses = torch.tensor(s.masses().reshape(-1), dtype=torch.float64, device="cuda")
+    s, o, ctx, make_api, pos, vel, masses = setup(args.workload, pkg, synth, pkg.PREC_MIXED, stream)
+    M = s.n_mol
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    dt_fs = 0.5
-    # The jittered lattice with random orientations starts far from
-    # equilibrium (overlapping hydrogens): relax it first (untimed).
+    # The random starting structures are far from equilibrium (close
+    # hydrogens): relax them first (untimed), then warm up.
     pkg.sibfa_minimize(ctx, pos, 20, 0.01)
-    snapshots = []
-
+    pos0, vel0 = pos.clone(), vel.clone()
     for _ in range(max(3, args.warmup)):
-        pkg.sibfa_md_steps(ctx, pos, vel, masses, dt_fs, 1)
+        pkg.sibfa_md_steps(ctx, pos, vel, masses, 0.5, 1)
     torch.cuda.synchronize()
     pkg.sibfa_set_profiling(ctx, True)
     pkg.sibfa_profile_clear(ctx)
     l0 = pkg.sibfa_kernel_launches(ctx)
-    iters = []
-    total_ms = 0.0
     barrier(dist)
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        for _ in range(args.steps):
-            flush.zero_()                       # evict L2 (512 MB > 129 MB) before every timed step
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            pkg.sibfa_md_steps(ctx, pos, vel, masses, dt_fs, 1)
-            b.record(stream)
-            b.synchronize()
-            total_ms += a.elapsed_time(b)
-            iters.append(pkg.sibfa_last_stats(ctx)[0])
-            snapshots.append(pos.clone())
+        total_ms, iters, snapshots = timed_steps(pkg, ctx, pos, vel, masses, args.steps, stream, flush, keep=True)
     torch.cuda.synchronize()
     barrier(dist)
     launches = pkg.sibfa_kernel_launches(ctx) - l0
@@ -331,23 +376,26 @@ def main():
     # roofline of the real-space permanent kernel (one launch per step)
     P = synth.PARAMS
     pos_h = pos.cpu().numpy().reshape(M, 3, 3)
-    pts = points_from_pos(pos_h, P)
-    units = count_units(pos_h, s.box, o["rc"], pts)
+    if args.workload == "water4096":
+        units = count_units(pos_h, s.box, o["rc"], points_from_pos(pos_h, P))
+    else:
+        units = count_units_clusters(o["cluster_start"], M)
     flops = unit_flops(units)
     rp_ms = phases["real_perm"]["ms_per_step"]
     achieved = flops / (rp_ms * 1e-3) / 1e12
     peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    roofline = {"bound": "alu", "kernel": "k_real_perm", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": measured_traffic(), "flops_per_launch": flops, "units": units,
+    kname = "k_real_perm<float, 1>" if args.workload == "water4096" else "k_real_perm<float, 0>"
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "traffic": measured_traffic() if args.workload == "water4096" else None,
+                "flops_per_launch": flops, "units": units,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived from unit counts and max clock)"}
 
     # End to end through the C ABI with host buffers: a second context
     # evaluates, from host memory, the positions of the trajectory that the
     # first context advances on the device (untimed); each timed call copies
     # the positions in and the forces and energies out.
-    api = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
-                           ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"], precision=pkg.PREC_MIXED,
-                           warm_start=True, stream=stream)
+    api = make_api()
     F_host = np.zeros(M * 9)
     pkg.sibfa_energy_forces(api, snapshots[0].cpu().numpy(), F_host)
     e2e_s = 0.0
@@ -362,19 +410,36 @@ def main():
     pkg.sibfa_destroy(api)
     pkg.sibfa_destroy(ctx)
 
+    # The plain FP64 GPU path on the same workload and starting state (the
+    # comparison the metric names): a few steps, same timing method.
+    fp64 = None
+    if not args.no_fp64_path:
+        _, _, c64, _, p64, v64, m64 = setup(args.workload, pkg, synth, pkg.PREC_FP64, stream)
+        p64.copy_(pos0)
+        v64.copy_(vel0)
+        for _ in range(2):
+            pkg.sibfa_md_steps(c64, p64, v64, m64, 0.5, 1)
+        torch.cuda.synchronize()
+        n64 = 3
+        ms64, it64, _ = timed_steps(pkg, c64, p64, v64, m64, n64, stream, flush)
+        ms64 = max_over_ranks(dist, ms64) / n64
+        pkg.sibfa_destroy(c64)
+        fp64 = {"value": ws * 3 * M / (ms64 / 1000.0), "unit": UNIT, "ms_per_step": ms64, "steps": n64,
+                "pcg_iters_mean": float(np.mean(it64)), "speedup_of_mixed": ms64 / step_ms}
+
     if rank != 0:
         return
     cpu = None
-    if ws == 1 and not args.no_cpu_baseline:
+    if ws == 1 and not args.no_cpu_baseline and args.workload == "water4096":
         cpu = cpu_baseline()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "FP32 pair/grid arithmetic, FP64 accumulation",
+        "config": {"workload": WORKLOADS[args.workload], "precision": "FP32 pair/grid arithmetic, FP64 accumulation",
                    "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{ws}"},
         "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
-        "cpu_baseline": cpu, "pcg_iters_mean": float(np.mean(iters)), "phases_ms": phases,
+        "cpu_baseline": cpu, "fp64_gpu_path": fp64, "pcg_iters_mean": float(np.mean(iters)), "phases_ms": phases,
     }
     print(json.dumps(line), flush=True)
 

@@ -81,6 +81,18 @@ typedef struct {
 typedef struct {
     int n_mol;
     const double *mp_local;
+    /* Optional batch of independent gas-phase clusters (periodic = 0 only).
+     * n_clusters > 1 splits the molecules into consecutive clusters: cluster
+     * c holds molecules cluster_start[c] .. cluster_start[c+1]-1 (HOST
+     * pointer, n_clusters+1 ints, cluster_start[0] = 0, cluster_start
+     * [n_clusters] = n_mol, increasing; copied at create).  Molecules of
+     * different clusters do not interact; each call evaluates every cluster
+     * with one launch per kernel, the polarization solve stops when the RMS
+     * residual of every cluster is below pcg_tol_D, sibfa_cluster_terms
+     * returns the terms per cluster and the terms of sibfa_energy_forces are
+     * their sums.  n_clusters = 0 or 1: one system (cluster_start unused). */
+    int n_clusters;
+    const int *cluster_start;
 } sibfa_topology;
 
 enum { SIBFA_PREC_FP64 = 0, SIBFA_PREC_MIXED = 1 };
@@ -151,8 +163,13 @@ sibfa_status sibfa_md_steps(sibfa_ctx *ctx, double *pos, double *vel, const doub
  * receives the intermolecular energy before the last step. */
 sibfa_status sibfa_minimize(sibfa_ctx *ctx, double *pos, int n_steps, double max_disp_A, sibfa_energy_terms *e);
 
-/* Statistics of the last evaluation: PCG iterations and final residual (D). */
+/* Statistics of the last evaluation: PCG iterations and final residual (D;
+ * for a cluster batch, the largest per-cluster residual). */
 sibfa_status sibfa_last_stats(const sibfa_ctx *ctx, int *pcg_iters, double *pcg_resid_D);
+
+/* Energy terms per cluster of the last evaluation (cluster batches; one
+ * entry for a single system).  terms: HOST pointer, n_clusters entries. */
+sibfa_status sibfa_cluster_terms(sibfa_ctx *ctx, sibfa_energy_terms *terms);
 
 /* Number of the library's own kernel launches since the context was created
  * (cuFFT executions are not counted). */

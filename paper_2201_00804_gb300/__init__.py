@@ -9,6 +9,7 @@ from .sibfa import (  # noqa: F401
     PREC_MIXED,
     SibfaError,
     load_library,
+    sibfa_cluster_terms,
     sibfa_create,
     sibfa_destroy,
     sibfa_energy_forces,

@@ -142,6 +142,10 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.sbase, (size_t)M * NP * 3);
     AL(d.sfrac, (size_t)M * NP * 3);
     AL(d.nnbr, M);
+    AL(d.cl_of, M);
+    AL(d.cl_start, ctx->kp.n_cl + 1);
+    AL(d.cl_rr, ctx->kp.n_cl);
+    AL(d.cl_energy, (size_t)ctx->kp.n_cl * (NTERM + 1));
     int ncell = std::max(1, ctx->ncell[0] * ctx->ncell[1] * ctx->ncell[2]);
     AL(d.cell_of, M);
     AL(d.cell_start, ncell + 1);
@@ -540,7 +544,8 @@ sibfa_status evaluate(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, doubl
         }
         { Phase ph(ctx, "finalize");  launch_finalize(p, d, ctx->d_forces, L); }
     }
-    launch_energy_reduce(p.M, d.epart, d.epart_r, ctx->d_energy, L);
+    if (p.n_cl > 1) launch_cluster_energy(p, d, ctx->d_energy, L);
+    else launch_energy_reduce(p.M, d.epart, d.epart_r, ctx->d_energy, L);
     return st_solve;
 }
 
@@ -640,6 +645,16 @@ sibfa_status create_impl(sibfa_ctx *ctx, const sibfa_topology *topo) {
     DevState<R> &d = state<R>(ctx);
     CK(cudaMemcpyAsync(d.mp_local, topo->mp_local, (size_t)M * NS * NMP * sizeof(double), cudaMemcpyHostToDevice,
                        ctx->s));
+    {
+        const int nc = ctx->kp.n_cl;
+        std::vector<int> start(nc + 1), of(M);
+        if (nc > 1) std::memcpy(start.data(), topo->cluster_start, (nc + 1) * sizeof(int));
+        else start[0] = 0, start[1] = M;
+        for (int c = 0; c < nc; ++c)
+            for (int m = start[c]; m < start[c + 1]; ++m) of[m] = c;
+        CK(cudaMemcpyAsync(d.cl_start, start.data(), (nc + 1) * sizeof(int), cudaMemcpyHostToDevice, ctx->s));
+        CK(cudaMemcpyAsync(d.cl_of, of.data(), M * sizeof(int), cudaMemcpyHostToDevice, ctx->s));
+    }
     CK(cudaStreamSynchronize(ctx->s));
     if (ctx->opts.periodic) {
         Launch L{ctx->s, &ctx->launches};
@@ -733,6 +748,19 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
         g_create_error = "sibfa_create: null argument or n_mol <= 0";
         return SIBFA_E_INVALID;
     }
+    if (topo->n_clusters > 1) {
+        bool ok = !opts->periodic && topo->cluster_start && topo->cluster_start[0] == 0 &&
+                  topo->cluster_start[topo->n_clusters] == topo->n_mol;
+        for (int c = 0; ok && c < topo->n_clusters; ++c) {
+            const int n = topo->cluster_start[c + 1] - topo->cluster_start[c];
+            ok = n >= 1 && n <= MAXN + 1;
+        }
+        if (!ok) {
+            g_create_error = "sibfa_create: cluster batches need periodic = 0 and increasing cluster_start from 0 to "
+                             "n_mol with 1..385 molecules per cluster";
+            return SIBFA_E_INVALID;
+        }
+    }
     if (opts->precision != SIBFA_PREC_FP64 && opts->precision != SIBFA_PREC_MIXED) {
         g_create_error = "sibfa_create: unknown precision";
         return SIBFA_E_INVALID;
@@ -778,6 +806,7 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
         return SIBFA_E_CUDA;
     }
     fill_params(ctx->kp, *params, *opts, ctx->M);
+    ctx->kp.n_cl = topo->n_clusters > 1 ? topo->n_clusters : 1;
     {
         const char *e = getenv("SIBFA_PCG_HOST_LOOP");
         if (e && e[0] == '1') ctx->pcg_graph_state = -1;
@@ -887,6 +916,23 @@ sibfa_status sibfa_md_steps(sibfa_ctx *ctx, double *pos, double *vel, const doub
     if (!ctx || !pos || !vel || !masses || n_steps < 0) return SIBFA_E_INVALID;
     return ctx->prec == SIBFA_PREC_MIXED ? md_impl<float>(ctx, pos, vel, masses, dt_fs, n_steps, e)
                                          : md_impl<double>(ctx, pos, vel, masses, dt_fs, n_steps, e);
+}
+
+sibfa_status sibfa_cluster_terms(sibfa_ctx *ctx, sibfa_energy_terms *terms) {
+    if (!ctx || !terms) return SIBFA_E_INVALID;
+    const int nc = ctx->kp.n_cl;
+    std::vector<double> h((size_t)nc * (NTERM + 1));
+    const double *src = ctx->d_energy;
+    if (nc > 1) src = ctx->prec == SIBFA_PREC_MIXED ? ctx->df.cl_energy : ctx->dd.cl_energy;
+    CK(cudaMemcpyAsync(h.data(), src, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    for (int c = 0; c < nc; ++c) {
+        const double *v = h.data() + (size_t)c * (NTERM + 1);
+        sibfa_energy_terms &e = terms[c];
+        e.elec = v[T_ELEC]; e.pen = v[T_PEN]; e.rep = v[T_REP]; e.disp = v[T_DISP];
+        e.xdisp = v[T_XDISP]; e.pol = v[T_POL]; e.ct = v[T_CT]; e.total = v[NTERM];
+    }
+    return SIBFA_OK;
 }
 
 sibfa_status sibfa_last_stats(const sibfa_ctx *ctx, int *pcg_iters, double *pcg_resid_D) {

@@ -76,6 +76,7 @@ template <typename R>
 __global__ void k_pcg_init(KParams p, DevState<R> d, int warm) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     zero_grid(p, d, k, (size_t)gridDim.x * blockDim.x);
+    if (p.n_cl > 1 && k < p.n_cl) d.cl_rr[k] = 0.0;
     if (k >= p.M * 9) return;
     if (!warm) d.mu[k] = apol(p, k) * d.efield[k];
     d.vecR[k] = R(d.mu[k]);
@@ -101,14 +102,58 @@ __global__ void k_pcg_first(KParams p, DevState<R> d) {
         rz = r * a * r;
         rr = a * r * a * r;
     }
+    if (p.n_cl > 1) cluster_rr_add(d, k, k < p.M * 9, rr);
     double trz, trr;
     if (last_block_sum2(rz, rr, d.partial, d.counter, trz, trr)) {
         d.scal[S_RZ] = trz;
-        const double res = sqrt(trr / (p.M * 3)) * 4.80321;
+        double res = sqrt(trr / (p.M * 3)) * 4.80321;
+        if (p.n_cl > 1) {   // one thread here: the last block's thread 0
+            double mx = 0;
+            for (int c = 0; c < p.n_cl; ++c)
+                mx = fmax(mx, __ldcg(d.cl_rr + c) / (3.0 * (d.cl_start[c + 1] - d.cl_start[c])));
+            res = sqrt(mx) * 4.80321;
+        }
         d.scal[S_RES] = res;
         d.scal[S_IT] = 0;
         d.scal[S_DONE] = (res < d.scal[S_TOL]) ? 1.0 : 0.0;
         d.flags[1] = res < d.scal[S_TOL];
+    }
+}
+
+// Cluster batches: the largest per-cluster RMS preconditioned residual (D)
+// from the per-cluster sums of squares.  Block-wide (all threads call it);
+// every block gets the same value (a maximum does not depend on order).
+template <typename R>
+__device__ inline double cluster_res_max(const KParams &p, const DevState<R> &d) {
+    __shared__ double smx[32];
+    double mx = 0;
+    for (int c = threadIdx.x; c < p.n_cl; c += blockDim.x) {
+        const int n = d.cl_start[c + 1] - d.cl_start[c];
+        mx = fmax(mx, __ldcg(d.cl_rr + c) / (3.0 * n));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) smx[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    double r = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, smx[w]);
+    __syncthreads();
+    return sqrt(r) * 4.80321;
+}
+
+// Cluster batches: add v (element k of the PCG vectors, valid or not) to the
+// sum of squares of its cluster.  Warp-collective: a warp whose elements lie
+// in one cluster adds its total with one atomic.
+template <typename R>
+__device__ inline void cluster_rr_add(const DevState<R> &d, int k, bool valid, double v) {
+    const int c = valid ? d.cl_of[k / 9] : -1;
+    const int c0 = __shfl_sync(0xffffffffu, c, 0);
+    if (__all_sync(0xffffffffu, c == c0 || c < 0)) {
+        const double s = warp_sum(valid ? v : 0.0);
+        if ((threadIdx.x & 31) == 0 && c0 >= 0) atomicAdd(d.cl_rr + c0, s);
+    } else if (valid) {
+        atomicAdd(d.cl_rr + c, v);
     }
 }
 
@@ -145,6 +190,8 @@ __global__ void __launch_bounds__(PB) k_pcg_step(KParams p, DevState<R> d) {
     const int nb = gridDim.x;
     const double rz_old = d.scal[S_RZ], tol = d.scal[S_TOL];
     double pap = 0;
+    if (p.n_cl > 1)
+        for (int c = tid; c < p.n_cl; c += nth) d.cl_rr[c] = 0.0;
     for (int k = tid; k < n; k += nth) {
         const double ap = d.pv[k] / apol(p, k) - (d.efp[k] + d.efp_r[k]);
         d.ap[k] = ap;
@@ -156,14 +203,20 @@ __global__ void __launch_bounds__(PB) k_pcg_step(KParams p, DevState<R> d) {
     const double tpap = sum_partials(d.partial, nb, 1, sh);
     const double al = rz_old / tpap;
     double rz = 0, rr = 0;
-    for (int k = tid; k < n; k += nth) {
-        const double a = apol(p, k);
-        d.mu[k] += al * d.pv[k];
-        const double r = d.res[k] - al * d.ap[k];
-        d.res[k] = r;
-        d.zv[k] = a * r;
-        rz += r * a * r;
-        rr += a * r * a * r;
+    for (int k0 = tid - (threadIdx.x & 31); k0 < n; k0 += nth) {   // warp-uniform trip count
+        const int k = k0 + (threadIdx.x & 31);
+        double q = 0;
+        if (k < n) {
+            const double a = apol(p, k);
+            d.mu[k] += al * d.pv[k];
+            const double r = d.res[k] - al * d.ap[k];
+            d.res[k] = r;
+            d.zv[k] = a * r;
+            rz += r * a * r;
+            q = a * r * a * r;
+            rr += q;
+        }
+        if (p.n_cl > 1) cluster_rr_add(d, k, k < n, q);
     }
     rz = block_sum(rz, sh);
     rr = block_sum(rr, sh);
@@ -175,7 +228,7 @@ __global__ void __launch_bounds__(PB) k_pcg_step(KParams p, DevState<R> d) {
     const double trz = sum_partials(d.partial + nb, nb, 2, sh);
     const double trr = sum_partials(d.partial + nb + 1, nb, 2, sh);
     const double beta = trz / rz_old;
-    const double res = sqrt(trr / (p.M * 3)) * 4.80321;
+    const double res = p.n_cl > 1 ? cluster_res_max(p, d) : sqrt(trr / (p.M * 3)) * 4.80321;
     const bool done = res < tol;
     if (tid == 0) {
         d.scal[S_PAP] = tpap;
@@ -468,6 +521,41 @@ void launch_energy_reduce(int M, const double *epart, const double *epart_r, dou
     count(L);
 }
 
+// Cluster batches: terms per cluster (one block per cluster, fixed order),
+// then their sums over the clusters into out (NTERM terms and the total).
+template <typename R>
+__global__ void k_cluster_energy(KParams p, DevState<R> d) {
+    __shared__ double sh[32];
+    const int c = blockIdx.x;
+    const int m0 = d.cl_start[c], m1 = d.cl_start[c + 1];
+    double tot = 0;
+    for (int k = 0; k < NTERM; ++k) {
+        double v = 0;
+        for (int m = m0 + threadIdx.x; m < m1; m += blockDim.x) v += d.epart[m * NTERM + k] + d.epart_r[m * NTERM + k];
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) {
+            d.cl_energy[c * (NTERM + 1) + k] = v;
+            tot += v;
+        }
+    }
+    if (threadIdx.x == 0) d.cl_energy[c * (NTERM + 1) + NTERM] = tot;
+}
+__global__ void k_cluster_total(int n_cl, const double *cl_energy, double *out) {
+    __shared__ double sh[32];
+    for (int k = 0; k <= NTERM; ++k) {
+        double v = 0;
+        for (int c = threadIdx.x; c < n_cl; c += blockDim.x) v += cl_energy[c * (NTERM + 1) + k];
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) out[k] = v;
+    }
+}
+template <typename R>
+void launch_cluster_energy(const KParams &p, DevState<R> &d, double *out, Launch L) {
+    k_cluster_energy<R><<<p.n_cl, 64, 0, L.s>>>(p, d);
+    k_cluster_total<<<1, 512, 0, L.s>>>(p.n_cl, d.cl_energy, out);
+    count(L, 2);
+}
+
 // velocity-Verlet half kick (and drift): v += dt/2 F/m ; x += dt v
 __global__ void k_md_kick(int M, double *pos, double *vel, const double *inv_mass, const double *F, double dt,
                           int drift) {
@@ -544,7 +632,8 @@ void launch_md_kick(int M, double *pos, double *vel, const double *inv_mass, con
     template void launch_pcg_step<R>(const KParams &, DevState<R> &, Launch);                          \
     template void launch_pol_energy<R>(const KParams &, DevState<R> &, Launch);                        \
     template void launch_finalize<R>(const KParams &, DevState<R> &, double *, Launch);                \
-    template void launch_merge_rec<R>(const KParams &, DevState<R> &, Launch);
+    template void launch_merge_rec<R>(const KParams &, DevState<R> &, Launch);                         \
+    template void launch_cluster_energy<R>(const KParams &, DevState<R> &, double *, Launch);
 INST(float)
 INST(double)
 

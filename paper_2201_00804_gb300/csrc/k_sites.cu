@@ -223,10 +223,12 @@ __global__ void k_nbr_all(KParams p, DevState<R> d) {
     if (i >= p.M) return;
     const double cut = list_cut(p, d.ext) + 1e-3;
     const float cut2f = p.periodic ? (float)(cut * cut) : 3.0e38f;
+    // partners: the molecules of i's own cluster (the whole system when n_cl = 1)
+    const int c = d.cl_of[i], j_lo = d.cl_start[c], j_hi = d.cl_start[c + 1];
     int n = 0;
-    for (int j0 = 0; j0 < p.M; j0 += 32) {
+    for (int j0 = j_lo; j0 < j_hi; j0 += 32) {
         const int j = j0 + lane;
-        const bool ok = (j < p.M && j != i) && near_f(p, d, i, j, cut2f);
+        const bool ok = (j < j_hi && j != i) && near_f(p, d, i, j, cut2f);
         const unsigned b = __ballot_sync(0xffffffffu, ok);
         if (ok) store_entry(p, d, i, n + __popc(b & ((1u << lane) - 1u)), j);
         n += __popc(b);

@@ -42,6 +42,7 @@ struct Scal {
 struct KParams {
     int M;
     int periodic;
+    int n_cl;              // clusters (1: one system)
     double box[3];
     double ibox[3];        // 1 / box
     double rc, rc2;
@@ -142,6 +143,10 @@ struct DevState {
     int *nbr;           // M*MAXN neighbour molecules (full list)
     R *ndo;             // M*MAXN*3 minimum-image displacement O_j - O_i of each entry
     int *nnbr;          // M
+    int *cl_of;         // M    cluster of each molecule
+    int *cl_start;      // n_cl+1 first molecule of each cluster
+    double *cl_rr;      // n_cl  PCG: sum of squared preconditioned residuals per cluster
+    double *cl_energy;  // n_cl*(NTERM+1) energy terms and total per cluster
     float *ofw;         // M*3 O positions wrapped into the box (single precision, cell binning)
     unsigned *ufx;      // M*3 O fractional coordinates in units of 2^-32 of the box (periodic list build)
     int *sbase;         // M*NP*3 SPME: floor(u) mod K of every point (u = fractional coordinate x K)
@@ -213,7 +218,14 @@ __host__ __device__ inline V3<R> cross(V3<R> a, V3<R> b) {
 }
 
 template <typename R> __device__ inline R rsqrt_(R x);
-template <> __device__ inline float rsqrt_<float>(float x) { return rsqrtf(x); }
+// FP32: the hardware reciprocal square root refined by one Newton step
+// (y <- y (3 - x y^2) / 2), which brings it to about one ulp; the radial
+// kernels of every multipole order start from it.
+template <> __device__ inline float rsqrt_<float>(float x) {
+    const float y = rsqrtf(x);
+    const float h = fmaf(-0.5f * x * y, y, 0.5f);   // (1 - x y^2) / 2
+    return fmaf(y, h, y);
+}
 template <> __device__ inline double rsqrt_<double>(double x) { return rsqrt(x); }
 template <typename R> __device__ inline R exp_(R x);
 template <> __device__ inline float exp_<float>(float x) { return expf(x); }
@@ -743,6 +755,7 @@ template <typename R> void launch_pcg_first(const KParams &p, DevState<R> &d, La
 template <typename R> void launch_pcg_step(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_pol_energy(const KParams &p, DevState<R> &d, Launch L);
 void launch_energy_reduce(int M, const double *epart, const double *epart_r, double *out, Launch L);
+template <typename R> void launch_cluster_energy(const KParams &p, DevState<R> &d, double *out, Launch L);
 void launch_begin(double *scal, int *flags, double tol_D, Launch L);
 void launch_pcg_check(const double *scal, int *flags, Launch L);
 void launch_water_intra(int M, const double *pos, double *F, double kb, double r0, double ka, double th0, Launch L);

@@ -34,7 +34,8 @@ class sibfa_params(C.Structure):
 
 
 class sibfa_topology(C.Structure):
-    _fields_ = [("n_mol", C.c_int), ("mp_local", C.POINTER(C.c_double))]
+    _fields_ = [("n_mol", C.c_int), ("mp_local", C.POINTER(C.c_double)), ("n_clusters", C.c_int),
+                ("cluster_start", C.POINTER(C.c_int))]
 
 
 class sibfa_run_opts(C.Structure):
@@ -82,6 +83,8 @@ def load_library(path: str = LIB_PATH):
     lib.sibfa_minimize.restype = C.c_int
     lib.sibfa_last_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     lib.sibfa_last_stats.restype = C.c_int
+    lib.sibfa_cluster_terms.argtypes = [C.c_void_p, C.POINTER(sibfa_energy_terms)]
+    lib.sibfa_cluster_terms.restype = C.c_int
     lib.sibfa_kernel_launches.argtypes = [C.c_void_p]
     lib.sibfa_kernel_launches.restype = C.c_uint64
     lib.sibfa_set_profiling.argtypes = [C.c_void_p, C.c_int]
@@ -126,13 +129,20 @@ def _check(lib, ctx, st):
 
 def sibfa_create(params: dict, mp_local: np.ndarray, *, periodic: bool, box=None, rc=9.0, grid=64, order=5,
                  ewald_alpha=0.4, pcg_tol_D=1e-6, pcg_max_iter=200, precision=PREC_MIXED, warm_start=True,
-                 stream=None, md_k_bond=529.6, md_r0=0.9572, md_k_angle=34.05, md_theta0_deg=104.52):
+                 stream=None, md_k_bond=529.6, md_r0=0.9572, md_k_angle=34.05, md_theta0_deg=104.52,
+                 cluster_start=None):
     """Create a context.  mp_local: (n_mol, 5, 10) float64 host array.
-    stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+    stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None.
+    cluster_start: optional (n_clusters + 1) ints splitting a gas-phase batch
+    into independent clusters of consecutive molecules."""
     lib = load_library()
     P = sibfa_params(*[float(params[n]) for n in PARAM_FIELDS])
     mp = np.ascontiguousarray(mp_local, dtype=np.float64)
-    topo = sibfa_topology(mp.shape[0], mp.ctypes.data_as(C.POINTER(C.c_double)))
+    topo = sibfa_topology(mp.shape[0], mp.ctypes.data_as(C.POINTER(C.c_double)), 0, None)
+    if cluster_start is not None:
+        cs = np.ascontiguousarray(cluster_start, dtype=np.int32)
+        topo.n_clusters = int(cs.size - 1)
+        topo.cluster_start = cs.ctypes.data_as(C.POINTER(C.c_int))
     o = sibfa_run_opts()
     o.periodic = 1 if periodic else 0
     if box is not None:
@@ -207,6 +217,14 @@ def sibfa_cluster_elec_noalloc(params: dict, pos, mp_local, elec_pen, stream=Non
     st = lib.sibfa_cluster_elec_noalloc(C.byref(P), n_mol, _ptr(pos), _ptr(mp_local), _ptr(elec_pen), s)
     if st != SIBFA_OK:
         raise SibfaError(st, lib.sibfa_noalloc_last_error().decode())
+
+
+def sibfa_cluster_terms(ctx, n_clusters: int):
+    """Energy terms per cluster of the last evaluation: list of dicts."""
+    lib = load_library()
+    arr = (sibfa_energy_terms * max(1, int(n_clusters)))()
+    _check(lib, ctx, lib.sibfa_cluster_terms(ctx, arr))
+    return [{k: getattr(t, k) for k, _ in sibfa_energy_terms._fields_} for t in arr]
 
 
 def sibfa_last_stats(ctx):

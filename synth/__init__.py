@@ -13,6 +13,7 @@ from .water import (  # noqa: F401
     System,
     make_box,
     make_cluster,
+    make_cluster_batch,
     make_dimer,
     make_config,
     maxwell_velocities,

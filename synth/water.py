@@ -355,3 +355,19 @@ def make_config(name: str):
     opts = {"rc": c["rc"], "grid": c["grid"], "order": 5, "ewald": c["ewald"],
             "pcg_tol": c["pcg_tol"]}
     return sysm, opts
+
+
+def make_cluster_batch(n_clusters: int, seed: int, n_min: int = 2, n_max: int = 32):
+    """A batch of independent gas-phase clusters, sizes uniform in
+    [n_min, n_max]; each cluster is make_cluster with its own seed drawn from
+    the batch seed.  Returns (System of all molecules, cluster_start array of
+    n_clusters + 1 ints, list of the per-cluster Systems)."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(n_min, n_max + 1, size=n_clusters)
+    seeds = rng.integers(0, 2**31 - 1, size=n_clusters)
+    parts = [make_cluster(int(n), seed=int(s)) for n, s in zip(sizes, seeds)]
+    start = np.zeros(n_clusters + 1, dtype=np.int32)
+    start[1:] = np.cumsum(sizes)
+    allsys = System(pos=np.concatenate([c.pos for c in parts]), mp_local=np.concatenate([c.mp_local for c in parts]),
+                    box=None, meta={"kind": "cluster_batch", "n_clusters": n_clusters, "seed": seed})
+    return allsys, start, parts
