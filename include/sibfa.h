@@ -216,6 +216,80 @@ const char *sibfa_noalloc_last_error(void);
 
 void sibfa_destroy(sibfa_ctx *ctx);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop for energy/force jobs that arrive over time.
+ *
+ * Jobs are MD runs (n_steps velocity-Verlet steps; n_steps = 0 is one energy
+ * and force evaluation) of a periodic water box or a gas-phase cluster.
+ * Box jobs run in `slots` concurrent workers, each with its own stream and a
+ * context kept between jobs of the same shape.  Gas-phase clusters of at most
+ * `batch_max_cluster` waters are batched continuously: one resident batch
+ * context advances every admitted cluster by one step per tick, finished jobs
+ * leave and newly arrived ones join at the next tick, and each cluster keeps
+ * its induced dipoles on the device as the warm start of its next solve.
+ * Jobs are admitted while the device memory they need (estimated from their
+ * size) fits under `device_mem_bytes`; the others wait in the queue.
+ * The scheme follows the serving form of the hot path; the paper itself has
+ * no request loop.
+ * ------------------------------------------------------------------------- */
+typedef struct sibfa_server sibfa_server;
+
+typedef struct {
+    const sibfa_params *params;  /* force-field parameters (copied)                       */
+    int slots;                   /* concurrent box workers, >= 1                           */
+    size_t device_mem_bytes;     /* admission cap on the server's device memory            */
+    int max_pending;             /* queued jobs beyond which sibfa_submit returns BUSY     */
+    int batch_waters;            /* capacity of the cluster batch (waters); 0 = no batch   */
+    int batch_max_cluster;       /* largest cluster that joins the batch (<= 385)          */
+    double batch_dt_fs;          /* time step of batched cluster jobs (fs)                 */
+    int precision;               /* SIBFA_PREC_MIXED or SIBFA_PREC_FP64                    */
+    double pcg_tol_D;            /* PCG tolerance of every job (D)                         */
+} sibfa_server_opts;
+
+typedef struct {
+    int n_mol;
+    const double *pos;           /* HOST n_mol*9 (A), copied at submit                    */
+    const double *vel;           /* HOST n_mol*9 (A/fs) or NULL (zero), copied             */
+    const double *mp_local;      /* HOST n_mol*50 local multipoles, copied                 */
+    int periodic;                /* 1: box job (box, rc, grid, ewald_alpha used)           */
+    double box[3];
+    double rc;
+    int grid[3];
+    double ewald_alpha;
+    int n_steps;                 /* velocity-Verlet steps; 0: one evaluation               */
+    double dt_fs;                /* time step (a batched cluster uses batch_dt_fs)         */
+} sibfa_job;
+
+typedef struct {
+    sibfa_energy_terms terms;    /* intermolecular terms at the final positions (kcal/mol) */
+    double *forces;              /* HOST n_mol*9 or NULL: filled by sibfa_poll; MD jobs:   */
+                                 /* the integrator's forces (with the intramolecular        */
+                                 /* support potential), evaluations: intermolecular         */
+    double *pos;                 /* HOST n_mol*9 or NULL: final positions                  */
+    int status;                  /* sibfa_status of the job                                */
+    int pcg_iters;               /* iterations of the last solve                           */
+    double queue_ms;             /* submit -> start of the job on the device               */
+    double latency_ms;           /* submit -> completion                                   */
+    int batched;                 /* 1 if the job ran in the cluster batch                  */
+} sibfa_result;
+
+/* Create a server on the current device; worker threads start at once. */
+sibfa_status sibfa_server_create(const sibfa_server_opts *opts, sibfa_server **out);
+
+/* Queue a job (its arrays are copied before the call returns) and return its
+ * ticket.  SIBFA_E_BUSY: max_pending jobs already wait; SIBFA_E_INVALID: bad
+ * sizes or a job that can never fit the memory cap.  Never blocks on the GPU. */
+sibfa_status sibfa_submit(sibfa_server *srv, const sibfa_job *job, uint64_t *ticket);
+
+/* *done = 1 when the job has finished: out receives its result (forces and
+ * positions copied to the caller's buffers when non-NULL) and the ticket is
+ * released; *done = 0 while it waits or runs.  Unknown ticket: INVALID. */
+sibfa_status sibfa_poll(sibfa_server *srv, uint64_t ticket, sibfa_result *out, int *done);
+
+/* Stop accepting jobs, finish the running ones, free everything. */
+void sibfa_server_destroy(sibfa_server *srv);
+
+
 /* Text of the last error on this context (or of the last failed create when
  * ctx is NULL).  Never NULL. */
 const char *sibfa_last_error(const sibfa_ctx *ctx);

@@ -7,6 +7,7 @@ CPU fallback: the binding raises if the library is missing.
 from .sibfa import (  # noqa: F401
     PREC_FP64,
     PREC_MIXED,
+    Server,
     SibfaError,
     load_library,
     sibfa_cluster_terms,

@@ -8,9 +8,11 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
 #include <cstdlib>
 
 #include "sibfa_internal.cuh"
+#include "server_internal.h"
 
 using namespace sibfa;
 
@@ -18,6 +20,7 @@ static thread_local std::string g_create_error = "no error";
 
 struct sibfa_ctx {
     int M = 0;
+    int capacity = 0;             // molecules the device arrays hold (M <= capacity)
     sibfa_run_opts opts{};
     KParams kp{};
     cudaStream_t s = nullptr;    // the library's own work stream (non-blocking)
@@ -45,6 +48,7 @@ struct sibfa_ctx {
     std::vector<void *> allocs;
     std::string err = "no error";
     uint64_t launches = 0;
+    size_t dev_bytes = 0;         // device memory allocated by the context
     int last_iters = 0;
     double last_resid = 0;
     bool have_mu = false;
@@ -116,6 +120,7 @@ sibfa_status dalloc(sibfa_ctx *ctx, T **p, size_t n) {
     }
     cudaMemsetAsync(q, 0, n * sizeof(T) + 16, ctx->s);   // ordered before any later work on the stream
     ctx->allocs.push_back(q);
+    ctx->dev_bytes += n * sizeof(T) + 16;
     *p = (T *)q;
     return SIBFA_OK;
 }
@@ -142,10 +147,12 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.sbase, (size_t)M * NP * 3);
     AL(d.sfrac, (size_t)M * NP * 3);
     AL(d.nnbr, M);
+    // cluster arrays sized for up to one cluster per molecule, so that a
+    // batch context can be regrouped in place (ctx_set_batch)
     AL(d.cl_of, M);
-    AL(d.cl_start, ctx->kp.n_cl + 1);
-    AL(d.cl_rr, ctx->kp.n_cl);
-    AL(d.cl_energy, (size_t)ctx->kp.n_cl * (NTERM + 1));
+    AL(d.cl_start, M + 1);
+    AL(d.cl_rr, M);
+    AL(d.cl_energy, (size_t)M * (NTERM + 1));
     int ncell = std::max(1, ctx->ncell[0] * ctx->ncell[1] * ctx->ncell[2]);
     AL(d.cell_of, M);
     AL(d.cell_start, ncell + 1);
@@ -179,12 +186,13 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.muR, M * 9);
     AL(d.lamR, M * 2);
     AL(d.tl_n, M * 3);
-    AL(d.tl_j, (size_t)M * 3 * TLS);
-    AL(d.tl_x, (size_t)M * 3 * TLS);
-    AL(d.tl_y, (size_t)M * 3 * TLS);
-    AL(d.tl_z, (size_t)M * 3 * TLS);
-    AL(d.tl_g1, (size_t)M * 3 * TLS);
-    AL(d.tl_g2, (size_t)M * 3 * TLS);
+    const size_t nt = (size_t)M * 3 * ctx->kp.tls;
+    AL(d.tl_j, nt);
+    AL(d.tl_x, nt);
+    AL(d.tl_y, nt);
+    AL(d.tl_z, nt);
+    AL(d.tl_g1, nt);
+    AL(d.tl_g2, nt);
     AL(d.partial, 4 * ((M * 9 + 255) / 256) + 64);
     AL(d.scal, 32);
     AL(d.counter, 4);
@@ -787,6 +795,7 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
     }
     sibfa_ctx *ctx = new sibfa_ctx();
     ctx->M = topo->n_mol;
+    ctx->capacity = topo->n_mol;
     ctx->opts = *opts;
     ctx->prec = opts->precision;
     ctx->us = (cudaStream_t)opts->stream;
@@ -807,6 +816,21 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
     }
     fill_params(ctx->kp, *params, *opts, ctx->M);
     ctx->kp.n_cl = topo->n_clusters > 1 ? topo->n_clusters : 1;
+    {
+        // the most neighbours a molecule can have: the list capacity in a box,
+        // the largest cluster minus one in the gas phase
+        int nmax = MAXN;
+        if (!opts->periodic) {
+            int big = topo->n_mol;
+            if (topo->n_clusters > 1) {
+                big = 0;
+                for (int c = 0; c < topo->n_clusters; ++c)
+                    big = std::max(big, topo->cluster_start[c + 1] - topo->cluster_start[c]);
+            }
+            nmax = std::min(MAXN, std::max(1, big - 1));
+        }
+        ctx->kp.tls = 3 * nmax;
+    }
     {
         const char *e = getenv("SIBFA_PCG_HOST_LOOP");
         if (e && e[0] == '1') ctx->pcg_graph_state = -1;
@@ -1018,3 +1042,64 @@ void sibfa_destroy(sibfa_ctx *ctx) {
 const char *sibfa_last_error(const sibfa_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Hooks for the request server (server.cu): regrouping a gas-phase batch
+// context in place and reading its device arrays.
+// ---------------------------------------------------------------------------
+namespace sibfa {
+
+template <typename R>
+static sibfa_status set_batch_impl(sibfa_ctx *ctx, int M, int n_cl, const int *cluster_start) {
+    DevState<R> &d = state<R>(ctx);
+    std::vector<int> start(n_cl + 1), of(M);
+    for (int c = 0; c <= n_cl; ++c) start[c] = cluster_start[c];
+    for (int c = 0; c < n_cl; ++c)
+        for (int m = start[c]; m < start[c + 1]; ++m) of[m] = c;
+    CK(cudaStreamSynchronize(ctx->s));
+    CK(cudaMemcpyAsync(d.cl_start, start.data(), (n_cl + 1) * sizeof(int), cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaMemcpyAsync(d.cl_of, of.data(), M * sizeof(int), cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));   // the host vectors are freed on return
+    return SIBFA_OK;
+}
+
+sibfa_status ctx_set_batch(sibfa_ctx *ctx, int M, int n_cl, const int *cluster_start) {
+    if (!ctx || M < 1 || M > ctx->capacity || n_cl < 1 || n_cl > M || ctx->opts.periodic) return SIBFA_E_INVALID;
+    if (cluster_start[0] != 0 || cluster_start[n_cl] != M) return SIBFA_E_INVALID;
+    for (int c = 0; c < n_cl; ++c) {
+        const int n = cluster_start[c + 1] - cluster_start[c];
+        if (n < 1 || n > ctx->kp.tls / 3 + 1) return SIBFA_E_INVALID;
+    }
+    sibfa_status st = ctx->prec == SIBFA_PREC_MIXED ? set_batch_impl<float>(ctx, M, n_cl, cluster_start)
+                                                     : set_batch_impl<double>(ctx, M, n_cl, cluster_start);
+    if (st) return st;
+    ctx->M = M;
+    ctx->kp.M = M;
+    ctx->kp.n_cl = n_cl;
+    ctx->md_forces_valid = false;
+    // the device-side PCG loop is captured for one size: drive the loop from the host
+    if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+    ctx->pcg_exec = nullptr;
+    ctx->pcg_graph_state = -1;
+    return SIBFA_OK;
+}
+
+BatchArrays ctx_batch_arrays(sibfa_ctx *ctx) {
+    BatchArrays b{};
+    if (!ctx) return b;
+    if (ctx->prec == SIBFA_PREC_MIXED) {
+        b.mp_local = ctx->df.mp_local;
+        b.mu = ctx->df.mu;
+    } else {
+        b.mp_local = ctx->dd.mp_local;
+        b.mu = ctx->dd.mu;
+    }
+    b.forces = ctx->d_forces;
+    b.capacity = ctx->capacity;
+    return b;
+}
+
+cudaStream_t ctx_stream(sibfa_ctx *ctx) { return ctx ? ctx->s : nullptr; }
+size_t ctx_device_bytes(const sibfa_ctx *ctx) { return ctx ? ctx->dev_bytes : 0; }
+
+}  // namespace sibfa

@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) 
     const R Nt = (!is_lp) ? zsite<R>(p, w) - mt.q * R(w < 3) : R(0);
     const R Nt_ = (w < 3) ? Nt : R(0);
     const R rc2 = sc<R>(p).rc2;
-    const size_t tbase = (size_t)(i * 3 + (w < 3 ? w : 0)) * TLS;   // T-pair list of target atom w
+    const size_t tbase = (size_t)(i * 3 + (w < 3 ? w : 0)) * p.tls;   // T-pair list of target atom w
 
     PermAcc<R> A;
     A.gr = mk(R(0), R(0), R(0));
@@ -399,14 +399,14 @@ __device__ inline void tmu_entry(const DevState<R> &d, size_t k, int jb, V3<R> &
 }
 
 template <typename R>
-__global__ void __launch_bounds__(32 * TW) k_real_tmu(int M, DevState<R> d, double *out) {
+__global__ void __launch_bounds__(32 * TW) k_real_tmu(int M, int tls, DevState<R> d, double *out) {
     __shared__ R red[TW][3 * 33];
     if (d.flags[1]) return;   // solver already converged
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * TW + w;
     if (t >= M * 3) return;
     const int n = d.tl_n[t];
-    const size_t base = (size_t)t * TLS;
+    const size_t base = (size_t)t * tls;
     V3<R> ef = mk(R(0), R(0), R(0));
     int e = lane;
     for (; e + 96 < n; e += 128) {
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(32 * TW) k_real_tmu(int M, DevState<R> d, doub
 
 template <typename R>
 void launch_real_tmu(const KParams &p, DevState<R> &d, double *out, Launch L) {
-    k_real_tmu<R><<<(p.M * 3 + TW - 1) / TW, 32 * TW, 0, L.s>>>(p.M, d, out);
+    k_real_tmu<R><<<(p.M * 3 + TW - 1) / TW, 32 * TW, 0, L.s>>>(p.M, p.tls, d, out);
     count(L);
 }
 

@@ -18,7 +18,6 @@ constexpr int MAXN = 384;      // neighbour slots per molecule
 constexpr int NTERM = 7;       // elec pen rep disp xdisp pol ct
 enum { T_ELEC = 0, T_PEN, T_REP, T_DISP, T_XDISP, T_POL, T_CT };
 constexpr int ORDER = 5;       // B-spline order of the SPME
-constexpr int TLS = 3 * MAXN;  // T-pair list slots per polarizable atom
 
 // error flags (bitwise, device side)
 enum { F_CUTOFF = 1, F_NEIGHBOR = 2, F_CTDEN = 4, F_NAN = 8, F_NOCONV = 16 };
@@ -43,6 +42,7 @@ struct KParams {
     int M;
     int periodic;
     int n_cl;              // clusters (1: one system)
+    int tls;               // T-pair list slots per polarizable atom: 3 x the most neighbours a molecule can have
     double box[3];
     double ibox[3];        // 1 / box
     double rc, rc2;
@@ -176,7 +176,7 @@ struct DevState {
     R *vecR;            // M*9 the vector of the current T product in the working precision
     R *muR, *lamR;      // M*9, M*2 induced dipoles and CT lambdas in the working precision (force pass)
     // Real-space T pairs recorded by the permanent pass: for polarizable atom
-    // t = 3 m + a, entries [t*TLS, t*TLS + tl_n[t]) hold the partner atom
+    // t = 3 m + a, entries [t*tls, t*tls + tl_n[t]) hold the partner atom
     // (3 j + b), the displacement x = r_t - r_jb and the Thole-damped kernel
     // weights g1, g2 of the dipole field (E = g2 (mu.x) x + g1 mu).
     int *tl_n, *tl_j;

@@ -50,6 +50,25 @@ class sibfa_energy_terms(C.Structure):
     _fields_ = [(n, C.c_double) for n in TERMS]
 
 
+class sibfa_server_opts(C.Structure):
+    _fields_ = [("params", C.POINTER(sibfa_params)), ("slots", C.c_int), ("device_mem_bytes", C.c_size_t),
+                ("max_pending", C.c_int), ("batch_waters", C.c_int), ("batch_max_cluster", C.c_int),
+                ("batch_dt_fs", C.c_double), ("precision", C.c_int), ("pcg_tol_D", C.c_double)]
+
+
+class sibfa_job(C.Structure):
+    _fields_ = [("n_mol", C.c_int), ("pos", C.POINTER(C.c_double)), ("vel", C.POINTER(C.c_double)),
+                ("mp_local", C.POINTER(C.c_double)), ("periodic", C.c_int), ("box", C.c_double * 3),
+                ("rc", C.c_double), ("grid", C.c_int * 3), ("ewald_alpha", C.c_double), ("n_steps", C.c_int),
+                ("dt_fs", C.c_double)]
+
+
+class sibfa_result(C.Structure):
+    _fields_ = [("terms", sibfa_energy_terms), ("forces", C.POINTER(C.c_double)), ("pos", C.POINTER(C.c_double)),
+                ("status", C.c_int), ("pcg_iters", C.c_int), ("queue_ms", C.c_double), ("latency_ms", C.c_double),
+                ("batched", C.c_int)]
+
+
 class SibfaError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -85,6 +104,14 @@ def load_library(path: str = LIB_PATH):
     lib.sibfa_last_stats.restype = C.c_int
     lib.sibfa_cluster_terms.argtypes = [C.c_void_p, C.POINTER(sibfa_energy_terms)]
     lib.sibfa_cluster_terms.restype = C.c_int
+    lib.sibfa_server_create.argtypes = [C.POINTER(sibfa_server_opts), C.POINTER(C.c_void_p)]
+    lib.sibfa_server_create.restype = C.c_int
+    lib.sibfa_submit.argtypes = [C.c_void_p, C.POINTER(sibfa_job), C.POINTER(C.c_uint64)]
+    lib.sibfa_submit.restype = C.c_int
+    lib.sibfa_poll.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(sibfa_result), C.POINTER(C.c_int)]
+    lib.sibfa_poll.restype = C.c_int
+    lib.sibfa_server_destroy.argtypes = [C.c_void_p]
+    lib.sibfa_server_destroy.restype = None
     lib.sibfa_kernel_launches.argtypes = [C.c_void_p]
     lib.sibfa_kernel_launches.restype = C.c_uint64
     lib.sibfa_set_profiling.argtypes = [C.c_void_p, C.c_int]
@@ -263,3 +290,90 @@ def sibfa_destroy(ctx):
 
 def sibfa_last_error(ctx=None) -> str:
     return load_library().sibfa_last_error(ctx).decode()
+
+
+# ---------------------------------------------------------------------------
+# Serving
+# ---------------------------------------------------------------------------
+SIBFA_E_BUSY = -8
+
+
+class Server:
+    """Request server (sibfa_server_*): submit MD/energy jobs, poll results."""
+
+    def __init__(self, params: dict, *, slots=2, device_mem_bytes=8 << 30, max_pending=4096, batch_waters=8192,
+                 batch_max_cluster=32, batch_dt_fs=0.5, precision=PREC_MIXED, pcg_tol_D=1e-6):
+        self._lib = load_library()
+        self._h = None
+        self._P = sibfa_params(*[float(params[n]) for n in PARAM_FIELDS])
+        o = sibfa_server_opts(C.pointer(self._P), int(slots), int(device_mem_bytes), int(max_pending),
+                              int(batch_waters), int(batch_max_cluster), float(batch_dt_fs), int(precision),
+                              float(pcg_tol_D))
+        h = C.c_void_p()
+        st = self._lib.sibfa_server_create(C.byref(o), C.byref(h))
+        if st != SIBFA_OK:
+            raise SibfaError(st, "sibfa_server_create failed")
+        self._h = h
+        self._n = {}
+
+    def submit(self, pos, mp_local, *, vel=None, periodic=False, box=None, rc=9.0, grid=64, ewald_alpha=0.4,
+               n_steps=0, dt_fs=0.5):
+        """Queue a job; returns its ticket, or None when the server is busy."""
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1)
+        mp = np.ascontiguousarray(mp_local, dtype=np.float64).reshape(-1)
+        n = pos.size // 9
+        j = sibfa_job()
+        j.n_mol = n
+        j.pos = pos.ctypes.data_as(C.POINTER(C.c_double))
+        v = None
+        if vel is not None:
+            v = np.ascontiguousarray(vel, dtype=np.float64).reshape(-1)
+            j.vel = v.ctypes.data_as(C.POINTER(C.c_double))
+        j.mp_local = mp.ctypes.data_as(C.POINTER(C.c_double))
+        j.periodic = 1 if periodic else 0
+        if box is not None:
+            for k in range(3):
+                j.box[k] = float(box[k])
+        g = (grid, grid, grid) if np.isscalar(grid) else tuple(grid)
+        for k in range(3):
+            j.grid[k] = int(g[k])
+        j.rc, j.ewald_alpha, j.n_steps, j.dt_fs = float(rc), float(ewald_alpha), int(n_steps), float(dt_fs)
+        t = C.c_uint64()
+        st = self._lib.sibfa_submit(self._h, C.byref(j), C.byref(t))
+        if st == SIBFA_E_BUSY:
+            return None
+        if st != SIBFA_OK:
+            raise SibfaError(st, "sibfa_submit refused the job")
+        self._n[t.value] = n
+        return t.value
+
+    def poll(self, ticket):
+        """None while the job waits or runs; then a dict with terms, forces,
+        final positions, status, pcg_iters, queue_ms, latency_ms, batched."""
+        n = self._n[ticket]
+        F = np.zeros(n * 9)
+        X = np.zeros(n * 9)
+        r = sibfa_result()
+        r.forces = F.ctypes.data_as(C.POINTER(C.c_double))
+        r.pos = X.ctypes.data_as(C.POINTER(C.c_double))
+        done = C.c_int()
+        st = self._lib.sibfa_poll(self._h, C.c_uint64(ticket), C.byref(r), C.byref(done))
+        if st != SIBFA_OK:
+            raise SibfaError(st, "sibfa_poll: unknown ticket")
+        if not done.value:
+            return None
+        del self._n[ticket]
+        return {"terms": {k: getattr(r.terms, k) for k in TERMS}, "forces": F, "pos": X, "status": r.status,
+                "pcg_iters": r.pcg_iters, "queue_ms": r.queue_ms, "latency_ms": r.latency_ms,
+                "batched": bool(r.batched)}
+
+    def close(self):
+        if self._h:
+            self._lib.sibfa_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
