@@ -703,7 +703,8 @@ static sibfa_status md_impl(sibfa_ctx *ctx, double *pos, double *vel, const doub
         return SIBFA_E_INVALID;
     }
     if (!ctx->d_invm) {
-        sibfa_status st = dalloc(ctx, &ctx->d_invm, (size_t)M * 3);
+        // sized for the capacity: a batch context grows after its first MD call
+        sibfa_status st = dalloc(ctx, &ctx->d_invm, (size_t)ctx->capacity * 3);
         if (st) return st;
     }
     const double tol = ctx->opts.pcg_tol_D > 0 ? ctx->opts.pcg_tol_D : 1e-6;

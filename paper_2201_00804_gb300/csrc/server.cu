@@ -442,12 +442,15 @@ void batch_worker(sibfa_server *S) {
         offset = keep_off;
     }
     if (!ok) {
-        // the batch failed: finish its jobs with an error rather than leave them waiting
+        // the batch failed: finish its jobs with an error, and send the queued
+        // cluster jobs to the slots rather than leave them waiting
         std::lock_guard<std::mutex> lk(S->m);
         for (Job *j : active) {
             j->status = SIBFA_E_CUDA;
             S->finish(j);
         }
+        for (Job *j : S->queue) j->batch = false;
+        S->o.batch_waters = 0;
     }
     S->cv.notify_all();
     if (ctx) sibfa_destroy(ctx);

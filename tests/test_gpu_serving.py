@@ -63,9 +63,11 @@ def _wait(srv, tickets, timeout=300.0):
 def test_results_alone_equal_in_the_mix():
     import paper_2201_00804_gb300 as pkg
     jobs = []
-    for k, n in enumerate((3, 7, 12, 20, 31, 5)):
+    # the first cluster runs alone in the batch for a while; the others join
+    # later, so the batch grows between steps
+    for k, n in enumerate((2, 7, 12, 20, 31, 5)):
         s = synth.make_cluster(n, seed=300 + k)
-        jobs.append(dict(sys=s, periodic=False, n_steps=0 if k == 5 else 3 + k % 3,
+        jobs.append(dict(sys=s, periodic=False, n_steps=40 if k == 0 else (0 if k == 5 else 3 + k % 3),
                          vel=synth.maxwell_velocities(s, 300.0, seed=k)))
     s, o = synth.make_config("water216")
     jobs.append(dict(sys=s, periodic=True, rc=o["rc"], grid=o["grid"], alpha=o["ewald"], n_steps=3,
@@ -75,7 +77,9 @@ def test_results_alone_equal_in_the_mix():
     srv = pkg.Server(synth.PARAMS, slots=2, batch_waters=512, precision=pkg.PREC_MIXED)
     try:
         tickets = []
-        for j in jobs:
+        for n, j in enumerate(jobs):
+            if n == 1:
+                time.sleep(0.3)
             s = j["sys"]
             kw = dict(periodic=j["periodic"], n_steps=j["n_steps"], vel=j["vel"], dt_fs=0.5)
             if j["periodic"]:
