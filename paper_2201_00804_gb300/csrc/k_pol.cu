@@ -30,8 +30,9 @@ __device__ inline double block_sum(double v, double *sh) {
 
 // Two block partials reduced by the last block to finish, in fixed order.
 // Returns true in thread 0 of the last block, with the two totals.
+// *is_last (optional) tells every thread of the block whether it is the last one.
 __device__ inline bool last_block_sum2(double a, double b, double *partial, unsigned *counter, double &ta,
-                                       double &tb) {
+                                       double &tb, bool *is_last = nullptr) {
     __shared__ double sh[32];
     __shared__ bool s_last;
     a = block_sum(a, sh);
@@ -44,6 +45,7 @@ __device__ inline bool last_block_sum2(double a, double b, double *partial, unsi
         s_last = (k == gridDim.x - 1);
     }
     __syncthreads();
+    if (is_last) *is_last = s_last;
     if (!s_last) return false;
     __threadfence();
     double x = 0, y = 0;
@@ -104,15 +106,13 @@ __global__ void k_pcg_first(KParams p, DevState<R> d) {
     }
     if (p.n_cl > 1) cluster_rr_add(d, k, k < p.M * 9, rr);
     double trz, trr;
-    if (last_block_sum2(rz, rr, d.partial, d.counter, trz, trr)) {
+    bool last = false;
+    const bool lead = last_block_sum2(rz, rr, d.partial, d.counter, trz, trr, &last);
+    double cres = 0;
+    if (last && p.n_cl > 1) cres = cluster_res_max(p, d);   // the whole last block
+    if (lead) {
         d.scal[S_RZ] = trz;
-        double res = sqrt(trr / (p.M * 3)) * 4.80321;
-        if (p.n_cl > 1) {   // one thread here: the last block's thread 0
-            double mx = 0;
-            for (int c = 0; c < p.n_cl; ++c)
-                mx = fmax(mx, __ldcg(d.cl_rr + c) / (3.0 * (d.cl_start[c + 1] - d.cl_start[c])));
-            res = sqrt(mx) * 4.80321;
-        }
+        const double res = p.n_cl > 1 ? cres : sqrt(trr / (p.M * 3)) * 4.80321;
         d.scal[S_RES] = res;
         d.scal[S_IT] = 0;
         d.scal[S_DONE] = (res < d.scal[S_TOL]) ? 1.0 : 0.0;
@@ -190,8 +190,11 @@ __global__ void __launch_bounds__(PB) k_pcg_step(KParams p, DevState<R> d) {
     const int nb = gridDim.x;
     const double rz_old = d.scal[S_RZ], tol = d.scal[S_TOL];
     double pap = 0;
-    if (p.n_cl > 1)
+    unsigned long long *rmax = reinterpret_cast<unsigned long long *>(d.partial + 3 * nb);   // cluster max slot
+    if (p.n_cl > 1) {
         for (int c = tid; c < p.n_cl; c += nth) d.cl_rr[c] = 0.0;
+        if (tid == 0) *rmax = 0ull;
+    }
     for (int k = tid; k < n; k += nth) {
         const double ap = d.pv[k] / apol(p, k) - (d.efp[k] + d.efp_r[k]);
         d.ap[k] = ap;
@@ -228,7 +231,19 @@ __global__ void __launch_bounds__(PB) k_pcg_step(KParams p, DevState<R> d) {
     const double trz = sum_partials(d.partial + nb, nb, 2, sh);
     const double trr = sum_partials(d.partial + nb + 1, nb, 2, sh);
     const double beta = trz / rz_old;
-    const double res = p.n_cl > 1 ? cluster_res_max(p, d) : sqrt(trr / (p.M * 3)) * 4.80321;
+    double res = sqrt(trr / (p.M * 3)) * 4.80321;
+    if (p.n_cl > 1) {
+        // largest per-cluster mean square: each block a slice, combined by an
+        // atomic maximum (non-negative doubles order like their bit patterns)
+        double mx = 0;
+        for (int c = tid; c < p.n_cl; c += nth)
+            mx = fmax(mx, __ldcg(d.cl_rr + c) / (3.0 * (d.cl_start[c + 1] - d.cl_start[c])));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(rmax, (unsigned long long)__double_as_longlong(mx));
+        grid.sync();
+        res = sqrt(__longlong_as_double((long long)__ldcg(rmax))) * 4.80321;
+    }
     const bool done = res < tol;
     if (tid == 0) {
         d.scal[S_PAP] = tpap;
