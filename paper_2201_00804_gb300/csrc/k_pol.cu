@@ -357,23 +357,23 @@ void launch_pol_energy(const KParams &p, DevState<R> &d, Launch L) {
 // (z, xv) plane, y = z x x; its vector-Jacobian product maps gradients of the
 // axes back to zv and xv.
 // ---------------------------------------------------------------------------
-__device__ inline void frame_vjp(V3<double> zv, V3<double> xv, V3<double> gx, V3<double> gy, V3<double> gz,
-                                 V3<double> &gzv, V3<double> &gxv) {
-    const double nz = sqrt(dot(zv, zv));
-    const V3<double> ez = (1.0 / nz) * zv;
-    const V3<double> xp = xv - dot(xv, ez) * ez;
-    const double nx = sqrt(dot(xp, xp));
-    const V3<double> ex = (1.0 / nx) * xp;
+template <typename W>
+__device__ inline void frame_vjp(V3<W> zv, V3<W> xv, V3<W> gx, V3<W> gy, V3<W> gz, V3<W> &gzv, V3<W> &gxv) {
+    const W iz = rsqrt_<W>(dot(zv, zv));
+    const V3<W> ez = iz * zv;
+    const V3<W> xp = xv - dot(xv, ez) * ez;
+    const W ix = rsqrt_<W>(dot(xp, xp));
+    const V3<W> ex = ix * xp;
     // y = z x x
     gz = gz + cross(ex, gy);
     gx = gx + cross(gy, ez);
     // x = xp / |xp|
-    const V3<double> gxp = (1.0 / nx) * (gx - dot(gx, ex) * ex);
+    const V3<W> gxp = ix * (gx - dot(gx, ex) * ex);
     // xp = xv - (xv.z) z
     gxv = gxp - dot(gxp, ez) * ez;
     gz = gz - dot(xv, ez) * gxp - dot(gxp, ez) * xv;
     // z = zv / |zv|
-    gzv = (1.0 / nz) * (gz - dot(gz, ez) * ez);
+    gzv = iz * (gz - dot(gz, ez) * ez);
 }
 
 // Four lanes per molecule.  Lane f < 3 carries the multipole sensitivities
@@ -381,108 +381,103 @@ __device__ inline void frame_vjp(V3<double> zv, V3<double> xv, V3<double> gx, V3
 // frame 2: H2, M2) back through that frame's construction; lane 3 takes the
 // point gradients (lone-pair charge-transfer term, V_int chain rule,
 // midpoints, lone-pair carrier).  The four partial atom gradients are summed
-// with shuffles.
+// with shuffles.  The accumulated gradients are summed in FP64 and the chain
+// rule runs in the working precision R, on the same frames as the site
+// kernel.
 template <typename R>
 __global__ void __launch_bounds__(128) k_finalize(KParams p, DevState<R> d, double *forces) {
     const int gidx = blockIdx.x * blockDim.x + threadIdx.x;
     const int m = gidx >> 2, t = gidx & 3;
     const bool live = m < p.M;
-    V3<double> gO = mk(0.0, 0.0, 0.0), gH1 = gO, gH2 = gO;
+    V3<R> gO = mk(R(0), R(0), R(0)), gH1 = gO, gH2 = gO;
     if (live) {
-        const double *x = d.pos + m * 9;
-        const V3<double> O = mk(x[0], x[1], x[2]), H1 = mk(x[3], x[4], x[5]), H2 = mk(x[6], x[7], x[8]);
-        const V3<double> r1 = H1 - O, r2 = H2 - O;
-        const double n1 = sqrt(dot(r1, r1)), n2 = sqrt(dot(r2, r2));
-        const V3<double> u1 = (1.0 / n1) * r1, u2 = (1.0 / n2) * r2;
-        auto gpt = [&](int k) {
-            const int o = (m * NP + k) * 3;
-            return mk(d.gpt[o] + d.gpt_r[o], d.gpt[o + 1] + d.gpt_r[o + 1], d.gpt[o + 2] + d.gpt_r[o + 2]);
+        V3<R> r1, r2;
+        bond_vectors(d.pos + m * 9, r1, r2);
+        const R s1 = rsqrt_<R>(dot(r1, r1)), s2 = rsqrt_<R>(dot(r2, r2));
+        auto sum2 = [&](const double *a, const double *b, int o) {
+            return mk(R(a[o] + b[o]), R(a[o + 1] + b[o + 1]), R(a[o + 2] + b[o + 2]));
         };
+        auto gpt = [&](int k) { return sum2(d.gpt, d.gpt_r, (m * NP + k) * 3); };
         // lone-pair point gradient including the charge-transfer dependence through its potential
         auto glp = [&](int l) {
-            const double lq = d.lam[m * 2 + l];
-            const int o = (m * 2 + l) * 3;
-            return gpt(5 + l) +
-                   lq * mk(d.dvlp[o] + d.dvlp_r[o], d.dvlp[o + 1] + d.dvlp_r[o + 1], d.dvlp[o + 2] + d.dvlp_r[o + 2]);
+            return gpt(5 + l) + R(d.lam[m * 2 + l]) * sum2(d.dvlp, d.dvlp_r, (m * 2 + l) * 3);
         };
         if (t < 3) {
             const int f = t;
-            const V3<double> zv = f == 0 ? u1 + u2 : (f == 1 ? O - H1 : O - H2);
-            const V3<double> xv = f == 0 ? r1 : (f == 1 ? H2 - H1 : H1 - H2);
-            V3<double> E[3];
-            frame_d2(zv, xv, E[0], E[1], E[2]);
-            V3<double> gE[3] = {mk(0.0, 0.0, 0.0), mk(0.0, 0.0, 0.0), mk(0.0, 0.0, 0.0)};
+            V3<R> zv, xv, E[3];
+            frame_generators(f, r1, r2, s1, s2, zv, xv);
+            frame_axes(zv, xv, E[0], E[1], E[2]);
+            V3<R> gE[3] = {mk(R(0), R(0), R(0)), mk(R(0), R(0), R(0)), mk(R(0), R(0), R(0))};
             for (int s = 0; s < NS; ++s) {
-                const int fs = s == 0 ? 0 : (s == 1 || s == 3 ? 1 : 2);
-                if (fs != f) continue;
+                if (site_frame(s) != f) continue;
                 const double *ml = d.mp_local + (m * NS + s) * NMP;
-                const int om = (m * NS + s) * 3, ot = (m * NS + s) * 6;
-                const V3<double> gmu = mk(d.gmu[om] + d.gmu_r[om], d.gmu[om + 1] + d.gmu_r[om + 1],
-                                          d.gmu[om + 2] + d.gmu_r[om + 2]);
+                const int ot = (m * NS + s) * 6;
+                const V3<R> gmu = sum2(d.gmu, d.gmu_r, (m * NS + s) * 3);
                 const double *gt6 = d.gth + ot, *gr6 = d.gth_r + ot;
-                const Sym<double> D{gt6[0] + gr6[0], gt6[1] + gr6[1], gt6[2] + gr6[2],
-                                    gt6[3] + gr6[3], gt6[4] + gr6[4], gt6[5] + gr6[5]};
-                const double tl[3][3] = {{ml[4], ml[7], ml[8]}, {ml[7], ml[5], ml[9]}, {ml[8], ml[9], ml[6]}};
+                const Sym<R> D{R(gt6[0] + gr6[0]), R(gt6[1] + gr6[1]), R(gt6[2] + gr6[2]),
+                               R(gt6[3] + gr6[3]), R(gt6[4] + gr6[4]), R(gt6[5] + gr6[5])};
+                const R tl[3][3] = {{R(ml[4]), R(ml[7]), R(ml[8])}, {R(ml[7]), R(ml[5]), R(ml[9])},
+                                    {R(ml[8]), R(ml[9]), R(ml[6])}};
                 for (int k = 0; k < 3; ++k) {
-                    gE[k] = gE[k] + ml[1 + k] * gmu;
-                    V3<double> acc = mk(0.0, 0.0, 0.0);
-                    for (int l = 0; l < 3; ++l) acc = acc + tl[k][l] * E[l];
-                    gE[k] = gE[k] + 2.0 * symv(D, acc);
+                    const V3<R> acc = tl[k][0] * E[0] + tl[k][1] * E[1] + tl[k][2] * E[2];
+                    gE[k] = gE[k] + R(ml[1 + k]) * gmu + R(2) * symv(D, acc);
                 }
             }
             if (f == 0)   // lone pairs: X = O + d (-c z_O +/- s y_O)
                 for (int l = 0; l < 2; ++l) {
-                    const double sg = l == 0 ? 1.0 : -1.0;
-                    const V3<double> G = glp(l);
-                    gE[2] = gE[2] + (-p.d_lp * p.lp_cos) * G;
-                    gE[1] = gE[1] + (sg * p.d_lp * p.lp_sin) * G;
+                    const V3<R> G = glp(l);
+                    gE[2] = gE[2] + R(-p.d_lp * p.lp_cos) * G;
+                    gE[1] = gE[1] + R(l == 0 ? p.d_lp * p.lp_sin : -p.d_lp * p.lp_sin) * G;
                 }
-            V3<double> gzv, gxv;
+            V3<R> gzv, gxv;
             frame_vjp(zv, xv, gE[0], gE[1], gE[2], gzv, gxv);
             if (f == 0) {
                 // zv = u1 + u2, u_k = r_k/|r_k|; xv = r1
-                const V3<double> gr1 = (1.0 / n1) * (gzv - dot(gzv, u1) * u1) + gxv;
-                const V3<double> gr2 = (1.0 / n2) * (gzv - dot(gzv, u2) * u2);
+                const V3<R> u1 = s1 * r1, u2 = s2 * r2;
+                const V3<R> gr1 = s1 * (gzv - dot(gzv, u1) * u1) + gxv;
+                const V3<R> gr2 = s2 * (gzv - dot(gzv, u2) * u2);
                 gH1 = gr1;
                 gH2 = gr2;
-                gO = -1.0 * (gr1 + gr2);
+                gO = -(gr1 + gr2);
             } else if (f == 1) {
                 // zv = O - H1, xv = H2 - H1
                 gO = gzv;
-                gH1 = -1.0 * (gzv + gxv);
+                gH1 = -(gzv + gxv);
                 gH2 = gxv;
             } else {
                 // zv = O - H2, xv = H1 - H2
                 gO = gzv;
-                gH2 = -1.0 * (gzv + gxv);
+                gH2 = -(gzv + gxv);
                 gH1 = gxv;
             }
         } else {
-            V3<double> X[NP];
-            points_d(p, d, m, X);
-            V3<double> G[NS];
-            for (int k = 0; k < NS; ++k) G[k] = gpt(k);
+            V3<R> G[NS], X[NS];
+            for (int k = 0; k < NS; ++k) {
+                G[k] = gpt(k);
+                const R *o = d.off + (m * NP + k) * 3;
+                X[k] = mk(o[0], o[1], o[2]);
+            }
             // charge-transfer dependence through the intramolecular potentials V_int(O, H1, H2)
             for (int a = 0; a < 3; ++a) {
                 const double k = d.kap[m * 3 + a];
                 if (k == 0.0) continue;
+                const R kk = R(k * p.ke);
                 for (int s = 0; s < NS; ++s) {
                     if (s == a) continue;
-                    const V3<double> dd = X[a] - X[s];
-                    const double r = sqrt(dot(dd, dd));
-                    const double qs = (double)d.gmp[(m * NS + s) * NMP];
-                    const double c = k * p.ke * qs / (r * r * r);
+                    const V3<R> dd = X[a] - X[s];
+                    const R ir = rsqrt_<R>(dot(dd, dd));
+                    const R c = kk * d.gmp[(m * NS + s) * NMP] * ir * ir * ir;
                     G[a] = G[a] - c * dd;
                     G[s] = G[s] + c * dd;
                 }
             }
             // midpoints and the lone pairs' carrier
-            gO = G[0] + 0.5 * (G[3] + G[4]) + glp(0) + glp(1);
-            gH1 = G[1] + 0.5 * G[3];
-            gH2 = G[2] + 0.5 * G[4];
+            gO = G[0] + R(0.5) * (G[3] + G[4]) + glp(0) + glp(1);
+            gH1 = G[1] + R(0.5) * G[3];
+            gH2 = G[2] + R(0.5) * G[4];
         }
     }
-    double v[9] = {gO.x, gO.y, gO.z, gH1.x, gH1.y, gH1.z, gH2.x, gH2.y, gH2.z};
+    R v[9] = {gO.x, gO.y, gO.z, gH1.x, gH1.y, gH1.z, gH2.x, gH2.y, gH2.z};
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         v[k] += __shfl_xor_sync(0xffffffffu, v[k], 1, 4);
@@ -490,7 +485,7 @@ __global__ void __launch_bounds__(128) k_finalize(KParams p, DevState<R> d, doub
     }
     if (live && t == 0 && forces) {
         double *F = forces + m * 9;
-        for (int k = 0; k < 9; ++k) F[k] = -v[k];
+        for (int k = 0; k < 9; ++k) F[k] = -(double)v[k];
     }
 }
 

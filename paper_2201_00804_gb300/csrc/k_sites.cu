@@ -6,18 +6,13 @@
 
 namespace sibfa {
 
-// Orthonormal frame with z along zv and x in the (z, xv) plane; y = z x x.
-__device__ inline void frame_d(V3<double> zv, V3<double> xv, V3<double> &ex, V3<double> &ey, V3<double> &ez) {
-    ez = (1.0 / sqrt(dot(zv, zv))) * zv;
-    V3<double> xp = xv - dot(xv, ez) * ez;
-    ex = (1.0 / sqrt(dot(xp, xp))) * xp;
-    ey = cross(ez, ex);
-}
-
-// Eight lanes per molecule: every lane builds the three frames (FP64); lane
-// t < 7 owns point t (offset, SPME grid coordinates), lane t < 5 rotates the
-// multipoles of site t, lane t < 3 forms V_int of atom t, lane 7 wraps O, and
-// the lanes share the clearing of the per-molecule accumulators.
+// Eight lanes per molecule.  Lane t < 7 owns point t (offset from O, SPME
+// grid coordinates) and builds the one local frame it needs (points 5 and 6,
+// the lone pairs, hang on frame 0); lane t < 5 rotates the multipoles of site
+// t into the global frame; lane t < 3 forms V_int of atom t; lane 7 wraps O;
+// the lanes share the clearing of the per-molecule accumulators.  Geometry
+// and rotation in the working precision R (the results are stored in R);
+// the SPME grid coordinates and the wrap in FP64.
 template <typename R>
 __global__ void __launch_bounds__(128) k_sites(KParams p, DevState<R> d) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -26,35 +21,31 @@ __global__ void __launch_bounds__(128) k_sites(KParams p, DevState<R> d) {
     float ext = 0.f;
     if (live) {
         const double *x = d.pos + m * 9;
-        V3<double> O = mk(x[0], x[1], x[2]), H1 = mk(x[3], x[4], x[5]), H2 = mk(x[6], x[7], x[8]);
-        V3<double> r1 = H1 - O, r2 = H2 - O;
-        V3<double> u1 = (1.0 / sqrt(dot(r1, r1))) * r1, u2 = (1.0 / sqrt(dot(r2, r2))) * r2;
-        V3<double> F[3][3];  // frames: [frame][axis]
-        frame_d(u1 + u2, r1, F[0][0], F[0][1], F[0][2]);
-        frame_d(O - H1, H2 - H1, F[1][0], F[1][1], F[1][2]);
-        frame_d(O - H2, H1 - H2, F[2][0], F[2][1], F[2][2]);
-        V3<double> offs[NP];
-        offs[0] = mk(0.0, 0.0, 0.0);
-        offs[1] = r1;
-        offs[2] = r2;
-        offs[3] = 0.5 * r1;
-        offs[4] = 0.5 * r2;
-        offs[5] = p.d_lp * ((-p.lp_cos) * F[0][2] + p.lp_sin * F[0][1]);
-        offs[6] = p.d_lp * ((-p.lp_cos) * F[0][2] - p.lp_sin * F[0][1]);
+        V3<R> r1, r2;
+        bond_vectors(x, r1, r2);
+        const R s1 = rsqrt_<R>(dot(r1, r1)), s2 = rsqrt_<R>(dot(r2, r2));
+        const int f = t < NS ? site_frame(t) : 0;
+        V3<R> zv, xv, ex, ey, ez;
+        frame_generators(f, r1, r2, s1, s2, zv, xv);
+        frame_axes(zv, xv, ex, ey, ez);
+        const R hz = R(-p.d_lp * p.lp_cos), hy = R(p.d_lp * p.lp_sin);
+        // offsets of the sites O, H1, H2, M1, M2 (needed by every V_int lane)
+        const V3<R> so[NS] = {mk(R(0), R(0), R(0)), r1, r2, R(0.5) * r1, R(0.5) * r2};
         const double *ml = d.mp_local + m * NS * NMP;
         if (t < NP) {
-            V3<double> o = offs[0];
+            V3<R> o = hz * ez + (t == 5 ? hy : -hy) * ey;
 #pragma unroll
-            for (int k = 1; k < NP; ++k)
-                if (k == t) o = offs[k];
-            d.off[(m * NP + t) * 3 + 0] = R(o.x);
-            d.off[(m * NP + t) * 3 + 1] = R(o.y);
-            d.off[(m * NP + t) * 3 + 2] = R(o.z);
-            ext = (float)sqrt(dot(o, o));
-            // SPME grid coordinates of the point (FP64 once per step; the spread
-            // and gather kernels build their B-spline weights from the fraction)
+            for (int k = 0; k < NS; ++k)
+                if (k == t) o = so[k];
+            d.off[(m * NP + t) * 3 + 0] = o.x;
+            d.off[(m * NP + t) * 3 + 1] = o.y;
+            d.off[(m * NP + t) * 3 + 2] = o.z;
+            ext = (float)sqrt_<R>(dot(o, o));
+            // SPME grid coordinates of the point, from the FP64 O position
+            // and the stored offset (the spread and gather kernels build their
+            // B-spline weights from the fraction)
             if (p.periodic) {
-                const double pk[3] = {O.x + o.x, O.y + o.y, O.z + o.z};
+                const double pk[3] = {x[0] + (double)o.x, x[1] + (double)o.y, x[2] + (double)o.z};
                 for (int c = 0; c < 3; ++c) {
                     const double u = pk[c] * p.ibox[c] * (double)p.K[c];
                     const double fl = floor(u);
@@ -67,50 +58,47 @@ __global__ void __launch_bounds__(128) k_sites(KParams p, DevState<R> d) {
         }
         if (t < NS) {
             const double *l = ml + t * NMP;
-            const int fr = t == 0 ? 0 : (t == 1 || t == 3 ? 1 : 2);
-            V3<double> e[3];
+            const R q = R(l[0]), m1 = R(l[1]), m2 = R(l[2]), m3 = R(l[3]);
+            const V3<R> mu = m1 * ex + m2 * ey + m3 * ez;
+            // Theta = Rm Th_l Rm^T; Th_l symmetric (xx yy zz xy xz yz), Rm columns = frame axes
+            const R tl[3][3] = {{R(l[4]), R(l[7]), R(l[8])}, {R(l[7]), R(l[5]), R(l[9])}, {R(l[8]), R(l[9]), R(l[6])}};
+            const V3<R> e[3] = {ex, ey, ez};
+            // A_k = sum_c Th_l[k][c] e_c (column k of Rm Th_l); Theta = sum_k e_k A_k^T
+            V3<R> A[3];
 #pragma unroll
-            for (int f = 0; f < 3; ++f)
-                if (f == fr) e[0] = F[f][0], e[1] = F[f][1], e[2] = F[f][2];
-            const V3<double> mu = l[1] * e[0] + l[2] * e[1] + l[3] * e[2];
-            // Theta = R Th_l R^T ; Th_l symmetric (xx yy zz xy xz yz), R columns = frame axes
-            const double tl[3][3] = {{l[4], l[7], l[8]}, {l[7], l[5], l[9]}, {l[8], l[9], l[6]}};
-            const double Rm[3][3] = {{e[0].x, e[1].x, e[2].x}, {e[0].y, e[1].y, e[2].y}, {e[0].z, e[1].z, e[2].z}};
-            double A[3][3];
-            for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) {
-                    double acc = 0;
-                    for (int c = 0; c < 3; ++c) acc += Rm[a][c] * tl[c][b];
-                    A[a][b] = acc;
-                }
-            double T[3][3];
-            for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) {
-                    double acc = 0;
-                    for (int c = 0; c < 3; ++c) acc += A[a][c] * Rm[b][c];
-                    T[a][b] = acc;
-                }
+            for (int k = 0; k < 3; ++k) A[k] = tl[k][0] * e[0] + tl[k][1] * e[1] + tl[k][2] * e[2];
+            R T[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                T[0] += e[k].x * A[k].x;
+                T[1] += e[k].y * A[k].y;
+                T[2] += e[k].z * A[k].z;
+                T[3] += e[k].x * A[k].y;
+                T[4] += e[k].x * A[k].z;
+                T[5] += e[k].y * A[k].z;
+            }
             R *gm = d.gmp + (m * NS + t) * NMP;
-            gm[0] = R(l[0]);
-            gm[1] = R(mu.x);
-            gm[2] = R(mu.y);
-            gm[3] = R(mu.z);
-            gm[4] = R(T[0][0]);
-            gm[5] = R(T[1][1]);
-            gm[6] = R(T[2][2]);
-            gm[7] = R(T[0][1]);
-            gm[8] = R(T[0][2]);
-            gm[9] = R(T[1][2]);
+            gm[0] = q;
+            gm[1] = mu.x;
+            gm[2] = mu.y;
+            gm[3] = mu.z;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) gm[4 + k] = T[k];
         }
         if (t < 3) {
             // intramolecular potential on atom t from the charges of the other sites
-            double v = 0;
+            V3<R> ot = so[0];
+#pragma unroll
+            for (int k = 1; k < 3; ++k)
+                if (k == t) ot = so[k];
+            R v = R(0);
+#pragma unroll
             for (int s = 0; s < NS; ++s) {
                 if (s == t) continue;
-                const V3<double> dd = offs[t] - offs[s];
-                v += ml[s * NMP] / sqrt(dot(dd, dd));
+                const V3<R> dd = ot - so[s];
+                v += R(ml[s * NMP]) * rsqrt_<R>(dot(dd, dd));
             }
-            d.vint[m * 3 + t] = p.ke * v;
+            d.vint[m * 3 + t] = p.ke * (double)v;
         }
         if (t == 7) {
             // O wrapped into the box in single precision (cell binning) and as

@@ -647,32 +647,40 @@ __device__ inline Mp<R> load_mp(const R *g) {
 }
 
 // ---------------------------------------------------------------------------
-// Intramolecular geometry in FP64 (shared by the intramolecular and chain-rule kernels)
+// Local frames of a water (shared by the site kernel and the chain rule, so
+// both see the same axes).  W is the arithmetic type: FP64 on the FP64 path,
+// FP32 on the mixed path, where the rotated multipoles and point offsets are
+// stored in FP32 anyway.
 // ---------------------------------------------------------------------------
-__device__ inline void frame_d2(V3<double> zv, V3<double> xv, V3<double> &ex, V3<double> &ey, V3<double> &ez) {
-    ez = (1.0 / sqrt(dot(zv, zv))) * zv;
-    V3<double> xp = xv - dot(xv, ez) * ez;
-    ex = (1.0 / sqrt(dot(xp, xp))) * xp;
+// Bond vectors r1 = H1 - O, r2 = H2 - O: FP64 differences, rounded once to W.
+template <typename W>
+__device__ inline void bond_vectors(const double *x, V3<W> &r1, V3<W> &r2) {
+    r1 = mk(W(x[3] - x[0]), W(x[4] - x[1]), W(x[5] - x[2]));
+    r2 = mk(W(x[6] - x[0]), W(x[7] - x[1]), W(x[8] - x[2]));
+}
+
+// Axis generators of frame f: frame 0 (O, lone pairs) has z along the
+// bisector u1 + u2 (u = r / |r|) and x toward H1; frame 1 (H1, O-H1
+// midpoint) has z along O - H1 and x toward H2; frame 2 (H2, O-H2 midpoint)
+// has z along O - H2 and x toward H1.  s1 = 1/|r1|, s2 = 1/|r2|.
+template <typename W>
+__device__ inline void frame_generators(int f, V3<W> r1, V3<W> r2, W s1, W s2, V3<W> &zv, V3<W> &xv) {
+    const V3<W> b = s1 * r1 + s2 * r2;
+    zv = f == 0 ? b : (f == 1 ? -r1 : -r2);
+    xv = f == 0 ? r1 : (f == 1 ? r2 - r1 : r1 - r2);
+}
+
+// Orthonormal frame with z along zv and x in the (z, xv) plane; y = z x x.
+template <typename W>
+__device__ inline void frame_axes(V3<W> zv, V3<W> xv, V3<W> &ex, V3<W> &ey, V3<W> &ez) {
+    ez = rsqrt_<W>(dot(zv, zv)) * zv;
+    const V3<W> xp = xv - dot(xv, ez) * ez;
+    ex = rsqrt_<W>(dot(xp, xp)) * xp;
     ey = cross(ez, ex);
 }
 
-// absolute FP64 positions of the 7 points of molecule m
-template <typename R>
-__device__ inline void points_d(const KParams &p, const DevState<R> &d, int m, V3<double> *X) {
-    const double *x = d.pos + m * 9;
-    const V3<double> O = mk(x[0], x[1], x[2]), H1 = mk(x[3], x[4], x[5]), H2 = mk(x[6], x[7], x[8]);
-    const V3<double> r1 = H1 - O, r2 = H2 - O;
-    const V3<double> u1 = (1.0 / sqrt(dot(r1, r1))) * r1, u2 = (1.0 / sqrt(dot(r2, r2))) * r2;
-    V3<double> ex, ey, ez;
-    frame_d2(u1 + u2, r1, ex, ey, ez);
-    X[0] = O;
-    X[1] = H1;
-    X[2] = H2;
-    X[3] = 0.5 * (O + H1);
-    X[4] = 0.5 * (O + H2);
-    X[5] = O + p.d_lp * ((-p.lp_cos) * ez + p.lp_sin * ey);
-    X[6] = O + p.d_lp * ((-p.lp_cos) * ez - p.lp_sin * ey);
-}
+// frame carrying site s: O -> 0, H1 and the O-H1 midpoint -> 1, H2 and the O-H2 midpoint -> 2
+__device__ inline int site_frame(int s) { return s == 0 ? 0 : (s == 1 || s == 3 ? 1 : 2); }
 
 template <typename R>
 __device__ inline Mp<double> mp_d(const DevState<R> &d, int m, int s) {
