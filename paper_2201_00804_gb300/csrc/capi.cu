@@ -138,7 +138,7 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.pos, M * 9);
     AL(d.mp_local, M * NS * NMP);
     AL(d.off, M * NP * 3);
-    AL(d.gmp, M * NS * NMP);
+    AL(d.gmp, M * NS * GMP);
     AL(d.vint, M * 3);
     AL(d.nbr, (size_t)M * MAXN);
     AL(d.ndo, (size_t)M * MAXN * 3);
@@ -249,6 +249,7 @@ void fill_params(KParams &k, const sibfa_params &P, const sibfa_run_opts &o, int
     k.lp_sin = sin(th);
     k.a_pol[0] = P.alpha_o;
     k.a_pol[1] = k.a_pol[2] = P.alpha_h;
+    for (int a = 0; a < 3; ++a) k.a_pol_inv[a] = 1.0 / k.a_pol[a];
     k.a_damp[0] = P.alpha_o;
     k.a_damp[1] = k.a_damp[2] = P.alpha_h;
     k.a_damp[3] = k.a_damp[4] = P.alpha_m_damp;

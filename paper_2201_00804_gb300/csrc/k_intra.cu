@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(128) k_intra_perm(KParams p, DevState<R> d) {
     R e = R(0), vl = R(0);
     if (lane < 10) {
         const int t = c_pair10[lane][0], s = c_pair10[lane][1];
-        const Mp<R> Mt = load_mp(d.gmp + (m * NS + t) * NMP), Ms = load_mp(d.gmp + (m * NS + s) * NMP);
+        const Mp<R> Mt = load_mp(d.gmp + (m * NS + t) * GMP), Ms = load_mp(d.gmp + (m * NS + s) * GMP);
         const V3<R> x = opt(d, m, t) - opt(d, m, s);
         R g[6];
         g_erf_s<R, 5>(dot(x, x), al, g);
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(128) k_intra_perm(KParams p, DevState<R> d) {
     } else if (lane < 22) {
         const int a = (lane - 10) / 4, k = (lane - 10) % 4;
         const int s = k < a ? k : k + 1;
-        const Mp<R> Ms = load_mp(d.gmp + (m * NS + s) * NMP);
+        const Mp<R> Ms = load_mp(d.gmp + (m * NS + s) * GMP);
         const V3<R> x = opt(d, m, a) - opt(d, m, s);
         R g[4];
         g_erf_s<R, 3>(dot(x, x), al, g);
@@ -98,13 +98,13 @@ __global__ void __launch_bounds__(128) k_intra_perm(KParams p, DevState<R> d) {
         source_field<R, 1>(Ms, x, g, f);
         V3<R> E = f.d1;
         if (k == 0) {
-            const Mp<R> Ma = load_mp(d.gmp + (m * NS + a) * NMP);
+            const Mp<R> Ma = load_mp(d.gmp + (m * NS + a) * GMP);
             E = E + cself * Ma.mu;
         }
         sadd3(A.ef[a], E, R(1));
     } else {
         const int l = (lane - 22) / 5, s = (lane - 22) % 5;
-        const Mp<R> Ms = load_mp(d.gmp + (m * NS + s) * NMP);
+        const Mp<R> Ms = load_mp(d.gmp + (m * NS + s) * GMP);
         const V3<R> x = opt(d, m, 5 + l) - opt(d, m, s);
         R g[4];
         g_erf_s<R, 3>(dot(x, x), al, g);
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(128) k_intra_perm(KParams p, DevState<R> d) {
         sadd3(A.dvlp[l], f.d1, R(-1));
     }
     if (lane < NS) {
-        const Mp<R> M = load_mp(d.gmp + (m * NS + lane) * NMP);
+        const Mp<R> M = load_mp(d.gmp + (m * NS + lane) * GMP);
         const R self = M.q * M.q + (R(2.0 / 3.0) * al * al) * dot(M.mu, M.mu) +
                        (R(8.0 / 45.0) * al * al * al * al) * symdd(M.th, M.th);
         e -= self * al * spi;
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(128) k_intra_polforce(KParams p, DevState<R> d
     if (lane < 12) {
         const int a = lane / 4, k = lane % 4;
         const int s = k < a ? k : k + 1;
-        const Mp<R> Ms = load_mp(d.gmp + (m * NS + s) * NMP);
+        const Mp<R> Ms = load_mp(d.gmp + (m * NS + s) * GMP);
         const V3<R> mua = mu_of(a);
         const V3<R> x = opt(d, m, a) - opt(d, m, s);
         R g[5];
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(128) k_intra_polforce(KParams p, DevState<R> d
         const int l = (lane - 15) / 5, s = (lane - 15) % 5;
         const double lq = d.lam[m * 2 + l];
         if (lq != 0.0) {
-            const Mp<R> Ms = load_mp(d.gmp + (m * NS + s) * NMP);
+            const Mp<R> Ms = load_mp(d.gmp + (m * NS + s) * GMP);
             const V3<R> x = opt(d, m, s) - opt(d, m, 5 + l);
             R g[6];
             g_erf_s<R, 5>(dot(x, x), al, g);

@@ -67,7 +67,7 @@ __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d
     const R r2 = dot(x, x);
     const R rinv = rsqrt_(r2);
     const R r = r2 * rinv;
-    const Mp<R> ms = load_mp_g(d.gmp + (j * NS + s) * NMP);
+    const Mp<R> ms = load_mp_g(d.gmp + (j * NS + s) * GMP);
     R g[6];
     if (PER) g_erfc<R, 5>(r, rinv, S.alpha, g);
     else g_bare<R, 5>(rinv, g);
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) 
     PairQueue<R> &q = qs[w];
     const V3<R> ot = my_pt(d, i, w);
     Mp<R> mt{};
-    if (!is_lp) mt = load_mp(d.gmp + (i * NS + w) * NMP);
+    if (!is_lp) mt = load_mp(d.gmp + (i * NS + w) * GMP);
     const R Nt = (!is_lp) ? zsite<R>(p, w) - mt.q * R(w < 3) : R(0);
     const R Nt_ = (w < 3) ? Nt : R(0);
     const R rc2 = sc<R>(p).rc2;
@@ -245,10 +245,13 @@ __global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) 
         const R vals[15] = {A.gr.x, A.gr.y, A.gr.z, A.gm.x, A.gm.y, A.gm.z, A.gt.xx, A.gt.yy, A.gt.zz,
                             A.gt.xy, A.gt.xz, A.gt.yz, A.ef.x, A.ef.y, A.ef.z};
         const R t = warp_transpose_sum<R, 15>(vals, buf, lane);
-        if (lane < 3) d.gpt[(i * NP + w) * 3 + lane] += ke * double(t);
-        else if (lane < 6) d.gmu[(i * NS + w) * 3 + lane - 3] += ke * double(t);
-        else if (lane < 12) d.gth[(i * NS + w) * 6 + lane - 6] += ke * double(t);
-        else if (lane < 15 && w < 3) d.efield[i * 9 + w * 3 + lane - 12] += double(t);
+        // one destination per lane, so the FP64 update is a single warp instruction
+        double *dst = nullptr;
+        if (lane < 3) dst = d.gpt + (i * NP + w) * 3 + lane;
+        else if (lane < 6) dst = d.gmu + (i * NS + w) * 3 + lane - 3;
+        else if (lane < 12) dst = d.gth + (i * NS + w) * 6 + lane - 6;
+        else if (lane < 15 && w < 3) dst = d.efield + i * 9 + w * 3 + lane - 12;
+        if (dst) *dst += (lane < 12 ? ke : 1.0) * double(t);
         const double e0 = warp_sum_acc(A.Ue), e1 = warp_sum_acc(A.Up);
         if (lane == 0) {
             s_e[w][0] = e0;
@@ -367,9 +370,11 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
                         G[3].x, G[3].y, G[3].z, G[4].x, G[4].y, G[4].z, lam[0], lam[1], kap[0], kap[1], kap[2]};
     const R t = warp_transpose_sum<R, 20>(vals, red[threadIdx.x >> 5], lane);
     const int pt = lane / 3;
-    if (lane < 15) d.gpt[(i * NP + (pt < 3 ? pt : pt + 2)) * 3 + lane % 3] += double(t);
-    else if (lane < 17) d.lam[i * 2 + lane - 15] += double(t);
-    else if (lane < 20) d.kap[i * 3 + lane - 17] += double(t);
+    double *dst = nullptr;
+    if (lane < 15) dst = d.gpt + (i * NP + (pt < 3 ? pt : pt + 2)) * 3 + lane % 3;
+    else if (lane < 17) dst = d.lam + i * 2 + lane - 15;
+    else if (lane < 20) dst = d.kap + i * 3 + lane - 17;
+    if (dst) *dst += double(t);
     const double e = warp_sum_acc(Ect);
     if (lane == 0) d.epart[i * NTERM + T_CT] += e;
 }
@@ -489,7 +494,7 @@ __device__ __forceinline__ void polf_pair(const KParams &p, const DevState<R> &d
         if (w < 3) A.gr = A.gr + symv(f.d2, mui);
     }
     if (w < 3) {       // permanent multipoles of site s of j at polarizable atom w
-        const Mp<R> ms = load_mp_g(d.gmp + (j * NS + s) * NMP);
+        const Mp<R> ms = load_mp_g(d.gmp + (j * NS + s) * GMP);
         FieldTerms<R> f;
         source_field<R, 2>(ms, x, g, f);
         A.gr = A.gr + symv(f.d2, mui);
@@ -504,7 +509,7 @@ __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d)
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     PairQueue<R, PQ_A + PQ_M + PQ_L> &q = qs[w];
     const V3<R> ot = my_pt(d, i, w);
-    const Mp<R> mt = load_mp(d.gmp + (i * NS + w) * NMP);
+    const Mp<R> mt = load_mp(d.gmp + (i * NS + w) * GMP);
     V3<R> mui = mk(R(0), R(0), R(0));
     if (w < 3) mui = mk(d.muR[i * 9 + w * 3], d.muR[i * 9 + w * 3 + 1], d.muR[i * 9 + w * 3 + 2]);
     const R rc2 = sc<R>(p).rc2;
@@ -577,9 +582,11 @@ __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d)
     const R vals[12] = {A.gr.x, A.gr.y, A.gr.z, A.gm.x, A.gm.y, A.gm.z,
                         A.gt.xx, A.gt.yy, A.gt.zz, A.gt.xy, A.gt.xz, A.gt.yz};
     const R s = warp_transpose_sum<R, 12>(vals, reinterpret_cast<R *>(&q), lane);
-    if (lane < 3) d.gpt[(i * NP + w) * 3 + lane] += ke * double(s);
-    else if (lane < 6) d.gmu[(i * NS + w) * 3 + lane - 3] += ke * double(s);
-    else if (lane < 12) d.gth[(i * NS + w) * 6 + lane - 6] += ke * double(s);
+    double *dst = nullptr;
+    if (lane < 3) dst = d.gpt + (i * NP + w) * 3 + lane;
+    else if (lane < 6) dst = d.gmu + (i * NS + w) * 3 + lane - 3;
+    else if (lane < 12) dst = d.gth + (i * NS + w) * 6 + lane - 6;
+    if (dst) *dst += ke * double(s);
 }
 
 template <typename R>

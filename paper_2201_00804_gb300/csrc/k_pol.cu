@@ -65,6 +65,7 @@ __device__ inline bool last_block_sum2(double a, double b, double *partial, unsi
 }
 
 __device__ inline double apol(const KParams &p, int k) { return p.a_pol[(k / 3) % 3]; }
+__device__ inline double apol_inv(const KParams &p, int k) { return p.a_pol_inv[(k / 3) % 3]; }
 
 // Zero the real SPME grid (input of the next spread of the PCG product).
 template <typename R>
@@ -94,7 +95,7 @@ __global__ void k_pcg_first(KParams p, DevState<R> d) {
     double rz = 0, rr = 0;
     if (k < p.M * 9) {
         const double a = apol(p, k);
-        const double r = d.efield[k] - (d.mu[k] / a - (d.efp[k] + d.efp_r[k]));
+        const double r = d.efield[k] - (d.mu[k] * apol_inv(p, k) - (d.efp[k] + d.efp_r[k]));
         d.res[k] = r;
         d.zv[k] = a * r;
         d.pv[k] = a * r;
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(PB) k_pcg_step(KParams p, DevState<R> d) {
         if (tid == 0) *rmax = 0ull;
     }
     for (int k = tid; k < n; k += nth) {
-        const double ap = d.pv[k] / apol(p, k) - (d.efp[k] + d.efp_r[k]);
+        const double ap = d.pv[k] * apol_inv(p, k) - (d.efp[k] + d.efp_r[k]);
         d.ap[k] = ap;
         pap += d.pv[k] * ap;
     }
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(128) k_finalize(KParams p, DevState<R> d, doub
                     if (s == a) continue;
                     const V3<R> dd = X[a] - X[s];
                     const R ir = rsqrt_<R>(dot(dd, dd));
-                    const R c = kk * d.gmp[(m * NS + s) * NMP] * ir * ir * ir;
+                    const R c = kk * d.gmp[(m * NS + s) * GMP] * ir * ir * ir;
                     G[a] = G[a] - c * dd;
                     G[s] = G[s] + c * dd;
                 }

@@ -123,7 +123,7 @@ __device__ inline V3<R> qpt(const DevState<R> &d, int j, V3<R> dO, int k) {
 }
 
 template <typename R>
-__device__ inline R qcharge(const DevState<R> &d, int j, int k) { return d.gmp[(j * NS + k) * NMP]; }
+__device__ inline R qcharge(const DevState<R> &d, int j, int k) { return d.gmp[(j * NS + k) * GMP]; }
 
 template <typename R>
 __device__ inline RepAtom<R> atom_j(const Scal<R> &S, const DevState<R> &d, int j, int k) {
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
     I.P[3] = my_pt(d, i, 5);
     I.P[4] = my_pt(d, i, 6);
     {
-        const R q0 = d.gmp[(i * NS) * NMP], q1 = d.gmp[(i * NS + 1) * NMP], q2 = d.gmp[(i * NS + 2) * NMP];
+        const R q0 = d.gmp[(i * NS) * GMP], q1 = d.gmp[(i * NS + 1) * GMP], q2 = d.gmp[(i * NS + 2) * GMP];
         I.A[0] = {S.cs_o, S.cp_o, S.g_o, R(1) - q0 * S.inv_nval_o, 0};
         I.A[1] = {S.cs_h, S.cp_h, S.g_h, R(1) - q1 * S.inv_nval_h, 1};
         I.A[2] = {S.cs_h, S.cp_h, S.g_h, R(1) - q2 * S.inv_nval_h, 1};

@@ -77,13 +77,15 @@ __global__ void __launch_bounds__(128) k_sites(KParams p, DevState<R> d) {
                 T[4] += e[k].x * A[k].z;
                 T[5] += e[k].y * A[k].z;
             }
-            R *gm = d.gmp + (m * NS + t) * NMP;
+            R *gm = d.gmp + (m * NS + t) * GMP;
             gm[0] = q;
             gm[1] = mu.x;
             gm[2] = mu.y;
             gm[3] = mu.z;
 #pragma unroll
             for (int k = 0; k < 6; ++k) gm[4 + k] = T[k];
+            gm[10] = R(0);
+            gm[11] = R(0);
         }
         if (t < 3) {
             // intramolecular potential on atom t from the charges of the other sites

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) k_spread(KParams p, DevState<R> d, int ki
     const int m = t / per, a = t % per;
     const int pt = kind == SPREAD_LAMBDA ? 5 + a : a;
     Mp<R> mp{};
-    if (kind == SPREAD_PERM) mp = load_mp(d.gmp + (m * NS + a) * NMP);
+    if (kind == SPREAD_PERM) mp = load_mp(d.gmp + (m * NS + a) * GMP);
     else if (kind == SPREAD_DIP) {
         const R *v = pcg ? d.vecR : d.muR;
         mp.mu = mk(v[m * 9 + a * 3], v[m * 9 + a * 3 + 1], v[m * 9 + a * 3 + 2]);
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(32 * GW) k_gather_perm(KParams p, DevState<R> 
     Derivs<R> D;
     if (pt < NS) {
         warp_gather<R, 3>(p, d, d.grid, m, pt, lane, buf[w], D);
-        const Mp<R> mp = load_mp(d.gmp + (m * NS + pt) * NMP);
+        const Mp<R> mp = load_mp(d.gmp + (m * NS + pt) * GMP);
         if (lane < 3) {
             d.gpt[(m * NP + pt) * 3 + lane] += (double)mp_grad(mp, D, lane);
             d.gmu[(m * NS + pt) * 3 + lane] += (double)D.d1[lane];
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(32 * GW) k_gather_polforce(KParams p, DevState
     for (int k = 0; k < 3; ++k) S.d1[k] = A.d1[k] + B.d1[k];
     for (int k = 0; k < 6; ++k) S.d2[k] = A.d2[k] + B.d2[k];
     for (int k = 0; k < 10; ++k) S.d3[k] = A.d3[k] + B.d3[k];
-    const Mp<R> mp = load_mp(d.gmp + (m * NS + pt) * NMP);
+    const Mp<R> mp = load_mp(d.gmp + (m * NS + pt) * GMP);
     if (lane < 3) {
         double g = (double)mp_grad(mp, S, lane);
         if (pt < 3) {

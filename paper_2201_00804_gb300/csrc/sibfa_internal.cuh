@@ -14,6 +14,7 @@ namespace sibfa {
 constexpr int NS = 5;          // multipole sites per water: O, H1, H2, M1, M2
 constexpr int NP = 7;          // points per water: 5 sites + 2 lone pairs
 constexpr int NMP = 10;        // q, mu(3), theta(6: xx yy zz xy xz yz)
+constexpr int GMP = 12;        // row stride of the global multipoles: NMP values + 2 pad (48-byte FP32 rows)
 constexpr int MAXN = 384;      // neighbour slots per molecule
 constexpr int NTERM = 7;       // elec pen rep disp xdisp pol ct
 enum { T_ELEC = 0, T_PEN, T_REP, T_DISP, T_XDISP, T_POL, T_CT };
@@ -51,6 +52,7 @@ struct KParams {
     double ke;
     double d_lp, lp_cos, lp_sin;
     double a_pol[3];       // O, H, H polarizabilities
+    double a_pol_inv[3];   // their reciprocals
     double a_damp[5];      // site polarizabilities used in Thole damping
     double thole;
     double z[5], b[5];     // nuclear charge and valence damping per site (0 on midpoints)
@@ -138,7 +140,7 @@ struct DevState {
     double *pos;        // M*9 working positions (O, H1, H2)
     double *mp_local;   // M*50
     R *off;             // M*NP*3 point offsets from own O (5 sites + 2 LPs)
-    R *gmp;             // M*NS*NMP global multipoles
+    R *gmp;             // M*NS*GMP global multipoles (rows of NMP values, padded)
     double *vint;       // M*3 intramolecular potential on O, H1, H2 (charge-transfer V_int)
     int *nbr;           // M*MAXN neighbour molecules (full list)
     R *ndo;             // M*MAXN*3 minimum-image displacement O_j - O_i of each entry
@@ -628,12 +630,29 @@ __device__ inline void min_image(const KParams &p, const double *pos, int i, int
     }
 }
 
+// source multipole row through the read-only path with vector loads (rows
+// are GMP values long, so every row starts on a 16-byte boundary)
 template <typename R>
-__device__ inline Mp<R> load_mp_g(const R *g) {
-    Mp<R> m;
-    m.q = __ldg(g);
-    m.mu = mk(__ldg(g + 1), __ldg(g + 2), __ldg(g + 3));
-    m.th = Sym<R>{__ldg(g + 4), __ldg(g + 5), __ldg(g + 6), __ldg(g + 7), __ldg(g + 8), __ldg(g + 9)};
+__device__ inline Mp<R> load_mp_g(const R *g);
+template <>
+__device__ inline Mp<float> load_mp_g<float>(const float *g) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(g));
+    const float4 b = __ldg(reinterpret_cast<const float4 *>(g) + 1);
+    const float2 c = __ldg(reinterpret_cast<const float2 *>(g) + 4);
+    Mp<float> m;
+    m.q = a.x;
+    m.mu = mk(a.y, a.z, a.w);
+    m.th = Sym<float>{b.x, b.y, b.z, b.w, c.x, c.y};
+    return m;
+}
+template <>
+__device__ inline Mp<double> load_mp_g<double>(const double *g) {
+    const double2 *v = reinterpret_cast<const double2 *>(g);
+    const double2 a = __ldg(v), b = __ldg(v + 1), c = __ldg(v + 2), e = __ldg(v + 3), f = __ldg(v + 4);
+    Mp<double> m;
+    m.q = a.x;
+    m.mu = mk(a.y, b.x, b.y);
+    m.th = Sym<double>{c.x, c.y, e.x, e.y, f.x, f.y};
     return m;
 }
 
@@ -684,7 +703,7 @@ __device__ inline int site_frame(int s) { return s == 0 ? 0 : (s == 1 || s == 3 
 
 template <typename R>
 __device__ inline Mp<double> mp_d(const DevState<R> &d, int m, int s) {
-    const R *g = d.gmp + (m * NS + s) * NMP;
+    const R *g = d.gmp + (m * NS + s) * GMP;
     Mp<double> o;
     o.q = g[0];
     o.mu = mk((double)g[1], (double)g[2], (double)g[3]);
