@@ -35,6 +35,7 @@ class _Setup:
         self.P = P
         self.mp = torch.as_tensor(system.mp_local, dtype=DT)
         self.periodic = system.box is not None
+        # edge lengths of an orthorhombic box, or a 3x3 cell (columns = cell vectors)
         self.box = t64(system.box) if self.periodic else None
         if self.periodic:
             self.rc = float(opts["rc"])
@@ -56,26 +57,48 @@ class _Setup:
         n = self.i.size
         for a in range(0, n, size):
             b = min(n, a + size)
-            yield self.i[a:b], self.j[a:b], self.sh[a:b]
+            sh = self.sh[a:b]
+            yield self.i[a:b], self.j[a:b], (sh if self.strain is None else sh @ self.strain.T)
+
+    strain = None   # (I + eps) in virial mode: image shifts are lattice vectors and deform with the cell
 
 
-def _grad(e, wrt):
-    return torch.autograd.grad(e, wrt, allow_unused=True)
+def _grad(e, wrt, retain=False):
+    return torch.autograd.grad(e, wrt, allow_unused=True, retain_graph=retain)
 
 
 def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=2048,
-             P=None, mu_guess=None, pcg_log=None, per_term=False, keep_operators=False):
+             P=None, mu_guess=None, pcg_log=None, per_term=False, keep_operators=False, virial=False):
     """Energies (kcal/mol) per term, forces (kcal/mol/A) on O, H1, H2, induced
     dipoles (e.A) on O, H1, H2, PCG iteration count and final residual (D).
 
-    opts (periodic systems): rc, grid, order, ewald.  Gas phase: opts unused."""
+    opts (periodic systems): rc, grid, order, ewald.  Gas phase: opts unused.
+
+    virial=True: instead of forces, the virial W_ab = -dE/d eps_ab (kcal/mol)
+    for the affine strain x -> (I + eps) x of every atom and of the periodic
+    cell (the image shifts and the reciprocal lattice deform with it), by the
+    same chain rule as the forces, with eps as the variable.  For a gas-phase
+    system it equals sum_atoms F_a x_b."""
     P = PARAMS if P is None else P
     opts = opts or {}
     st = _Setup(system, opts, P)
-    x = torch.tensor(system.pos, dtype=DT, requires_grad=forces)
+    if virial:
+        forces = True
+        eps = torch.zeros((3, 3), dtype=DT, requires_grad=True)
+        Fm = torch.eye(3, dtype=DT) + eps
+        x = t64(system.pos) @ Fm.T
+        wrt = eps
+        st.strain = Fm
+        if st.periodic:
+            cell0 = st.box if ew.is_cell(st.box) else torch.diag(st.box)
+            st.box = Fm @ cell0                       # cell matrix, columns = cell vectors
+            st.G = ew.influence(st.box, st.K, st.order, st.alpha, P["ke"])
+    else:
+        x = torch.tensor(system.pos, dtype=DT, requires_grad=forces)
+        wrt = x
     M = x.shape[0]
-    F = torch.zeros_like(x) if forces else None
-    FT = {k: torch.zeros_like(x) for k in TERMS} if (forces and per_term) else None
+    F = torch.zeros_like(wrt) if forces else None
+    FT = {k: torch.zeros_like(wrt) for k in TERMS} if (forces and per_term) else None
     E = {k: 0.0 for k in TERMS}
 
     def acc(e, name):
@@ -83,7 +106,7 @@ def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=20
 
     def add_grad(e, name=None, retain=False):
         if forces and e.requires_grad:
-            g, = torch.autograd.grad(e, [x], allow_unused=True, retain_graph=retain)
+            g, = torch.autograd.grad(e, [wrt], allow_unused=True, retain_graph=retain or virial)
             if g is not None:
                 F.sub_(g)
                 if FT is not None and name is not None:
@@ -138,13 +161,13 @@ def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=20
         e_ct += float(e.detach())
         if e.requires_grad:
             if forces:
-                gx, gv = torch.autograd.grad(e, [x, Vleaf], allow_unused=True)
+                gx, gv = torch.autograd.grad(e, [wrt, Vleaf], allow_unused=True, retain_graph=virial)
                 if gx is not None:
                     F.sub_(gx)
                     if FT is not None:
                         FT["ct"].sub_(gx)
             else:
-                gv, = torch.autograd.grad(e, [Vleaf], allow_unused=True)
+                gv, = torch.autograd.grad(e, [Vleaf], allow_unused=True, retain_graph=virial)
             if gv is not None:
                 lam += gv
     E["ct"] = e_ct
@@ -183,11 +206,11 @@ def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=20
     xd = x.detach()
     # E_perm = -d(-mu.E)/dmu ; T p = d(1/2 p.T.p)/dp   (both divided by ke below)
     mu0 = torch.zeros((M, 3, 3), dtype=DT, requires_grad=True)
-    Efield = -_grad(linear(xd, mu0), [mu0])[0] / P["ke"]
+    Efield = -_grad(linear(xd, mu0), [mu0], virial)[0] / P["ke"]
 
     def matvec(p):
         pp = p.detach().clone().requires_grad_(True)
-        return _grad(quadratic(xd, pp), [pp])[0] / P["ke"]
+        return _grad(quadratic(xd, pp), [pp], virial)[0] / P["ke"]
 
     debye = P["debye"]
     mu = (a_pol[None, :, None] * Efield) if mu_guess is None else torch.as_tensor(mu_guess, dtype=DT).clone()
@@ -222,7 +245,8 @@ def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=20
     E["total"] = sum(E[k] for k in TERMS)
     return {
         "terms": E,
-        "forces": F.detach().numpy() if forces else None,
+        "forces": F.detach().numpy() if (forces and not virial) else None,
+        "virial": F.detach().numpy() if virial else None,
         "forces_per_term": {k: v.numpy() for k, v in FT.items()} if FT is not None else None,
         "mu": mu.detach().numpy(),
         "efield": Efield.detach().numpy(),

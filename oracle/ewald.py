@@ -83,9 +83,103 @@ def _mi(*axes):
     return tuple(a)
 
 
+# ---------------------------------------------------------------------------
+# General (triclinic) cells.  `box` is either the three edge lengths of an
+# orthorhombic box or a 3x3 cell matrix h whose columns are the cell vectors
+# (x = h s, s the fractional coordinates).  The grid coordinate of x is
+# u = A x with A = diag(K) h^-1, so a Cartesian gradient is A^T times the
+# gradient in u: multipoles are mapped to grid coordinates before the spread
+# (mu_u = A mu, Theta_u = A Theta A^T) and potential derivatives back after
+# the gather.  The virial (strain derivative) is taken through h.
+# ---------------------------------------------------------------------------
+
+def is_cell(box):
+    return torch.is_tensor(box) and box.dim() == 2
+
+
+def grid_map(cell, K):
+    """A = diag(K) h^-1."""
+    return t64(K)[:, None] * torch.linalg.inv(cell)
+
+
+def _cell_weights(x, cell, K, order, nderiv):
+    """Spline indices and weights in grid coordinates (derivatives with respect to u)."""
+    A = grid_map(cell, K)
+    u = x @ A.T
+    fl = torch.floor(u.detach())
+    w = u - fl
+    j = torch.arange(order, dtype=DT)
+    v = w[..., None] + j
+    idx = (fl[..., None].long() - torch.arange(order)) % torch.as_tensor(K)[None, :, None]
+    W = [bspline_deriv(order, v, k) for k in range(nderiv + 1)]
+    return idx, W, A
+
+
+def _spread_cell(x, q, mu, th, cell, K, order):
+    N = x.shape[0]
+    idx, W, A = _cell_weights(x, cell, K, order, 2)
+    coef = q[:, None, None, None] * _dir_product(W, N, order, (0, 0, 0))
+    if mu is not None:
+        mu_u = mu @ A.T
+        for a in range(3):
+            coef = coef + mu_u[:, a, None, None, None] * _dir_product(W, N, order, D1[a])
+    if th is not None:
+        th_u = A @ th @ A.T
+        for a in range(3):
+            for b in range(3):
+                coef = coef + (th_u[:, a, b] / 3.0)[:, None, None, None] * _dir_product(W, N, order, _mi(a, b))
+    flat = _flat_index(idx, K).reshape(-1)
+    Q = torch.zeros(K[0] * K[1] * K[2], dtype=DT).index_add(0, flat, coef.reshape(-1))
+    return Q.reshape(K[0], K[1], K[2])
+
+
+def _potential_derivs_cell(x, Psi, cell, K, order, nderiv):
+    N = x.shape[0]
+    idx, W, A = _cell_weights(x, cell, K, order, nderiv)
+    flat = _flat_index(idx, K)
+    vals = Psi.reshape(-1)[flat.reshape(-1)].reshape(N, order, order, order)
+
+    def contract(a):
+        return (_dir_product(W, N, order, a) * vals).sum((1, 2, 3))
+
+    out = {"phi": contract((0, 0, 0))}
+    if nderiv >= 1:
+        d1 = torch.stack([contract(D1[a]) for a in range(3)], -1)
+        out["d1"] = d1 @ A
+    if nderiv >= 2:
+        d2 = torch.stack([torch.stack([contract(_mi(a, b)) for b in range(3)], -1) for a in range(3)], -2)
+        out["d2"] = A.T @ d2 @ A
+    if nderiv >= 3:
+        d3 = torch.stack([torch.stack([torch.stack([contract(_mi(a, b, c)) for c in range(3)], -1)
+                                       for b in range(3)], -2) for a in range(3)], -3)
+        out["d3"] = torch.einsum("ndef,da,eb,fc->nabc", d3, A, A, A)
+    return out
+
+
+def _influence_cell(cell, K, order, alpha, ke):
+    """G on the grid for a general cell: reciprocal vectors m = h^-T k."""
+    V = torch.abs(torch.linalg.det(cell))
+    ks = []
+    for d in range(3):
+        k = torch.arange(K[d], dtype=DT)
+        ks.append(torch.where(k > K[d] // 2, k - K[d], k))
+    kx, ky, kz = torch.meshgrid(*ks, indexing="ij")
+    kk = torch.stack([kx, ky, kz], -1).reshape(-1, 3)
+    m = kk @ torch.linalg.inv(cell)            # rows: m^T = k^T h^-1
+    m2 = (m * m).sum(-1).reshape(K[0], K[1], K[2])
+    B = (bspline_moduli(K[0], order)[:, None, None] * bspline_moduli(K[1], order)[None, :, None]
+         * bspline_moduli(K[2], order)[None, None, :])
+    safe = torch.where(m2 > 0, m2, torch.ones_like(m2))
+    G = torch.where(m2 > 0, torch.exp(-math.pi ** 2 * m2 / alpha ** 2) * B / (math.pi * V * safe),
+                    torch.zeros_like(m2))
+    return G * (K[0] * K[1] * K[2]) * ke
+
+
 def spread(x, q, mu, th, box, K, order):
     """Grid Q(k) = sum_i [q_i + mu_i . grad_i + (1/3) Theta_i : grad_i grad_i] W_i(k)."""
     N = x.shape[0]
+    if is_cell(box):
+        return _spread_cell(x, q, mu, th, box, K, order)
     idx, W = spline_weights(x, box, K, order, 2)
     coef = q[:, None, None, None] * _dir_product(W, N, order, (0, 0, 0))
     if mu is not None:
@@ -123,6 +217,8 @@ def influence(box, K, order, alpha, ke):
     """G(m) such that E_rec = 1/2 sum_k Q(k) Psi(k), Psi = IFFT(G FFT(Q)):
     G(m) = K1 K2 K3 ke exp(-pi^2 |m~|^2/alpha^2) B(m) / (pi V |m~|^2), G(0) = 0,
     with m~ = (m1/L1, m2/L2, m3/L3) and folded integer frequencies m."""
+    if is_cell(box):
+        return _influence_cell(box, K, order, alpha, ke)
     box = t64(box)
     V = float(box[0] * box[1] * box[2])
     freqs = []
@@ -152,6 +248,8 @@ def potential_derivs(x, Psi, box, K, order, nderiv):
     """phi and its Cartesian derivatives up to nderiv at points x from the
     convolved grid Psi.  Returns dict: 'phi' (N,), 'd1' (N,3), 'd2' (N,3,3),
     'd3' (N,3,3,3)."""
+    if is_cell(box):
+        return _potential_derivs_cell(x, Psi, box, K, order, nderiv)
     N = x.shape[0]
     idx, W = spline_weights(x, box, K, order, nderiv)
     flat = _flat_index(idx, K)
@@ -178,13 +276,18 @@ def potential_derivs(x, Psi, box, K, order, nderiv):
 
 def exact_recip_energy(x, q, mu, th, box, alpha, ke, mmax):
     """(ke / 2 pi V) sum_{m != 0} exp(-pi^2 m~^2/alpha^2)/m~^2 |S(m)|^2 with
-    S(m) = sum_j [q_j + 2 pi i m~.mu_j - (4 pi^2/3) m~.Theta_j.m~] exp(2 pi i m~.r_j)."""
-    box = t64(box)
-    V = float(box[0] * box[1] * box[2])
+    S(m) = sum_j [q_j + 2 pi i m~.mu_j - (4 pi^2/3) m~.Theta_j.m~] exp(2 pi i m~.r_j).
+    For a 3x3 cell h (columns = cell vectors), m~ = h^-T m and V = |det h|."""
     rng = torch.arange(-mmax, mmax + 1, dtype=DT)
     mm = torch.stack(torch.meshgrid(rng, rng, rng, indexing="ij"), -1).reshape(-1, 3)
     mm = mm[(mm != 0).any(-1)]
-    mt = mm / box
+    if is_cell(box):
+        V = float(torch.abs(torch.linalg.det(box)))
+        mt = mm @ torch.linalg.inv(box)
+    else:
+        box = t64(box)
+        V = float(box[0] * box[1] * box[2])
+        mt = mm / box
     m2 = (mt * mt).sum(-1)
     E = x.new_zeros(())
     for chunk in torch.split(torch.arange(mt.shape[0]), 4096):

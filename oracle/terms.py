@@ -52,17 +52,23 @@ def valence(S, P):
 
 def mol_pairs(O, box, cut):
     """Pairs i<j whose O-O distance is below `cut`, with the image shift that
-    must be added to molecule j.  O: (M, 3) numpy."""
+    must be added to molecule j.  O: (M, 3) numpy.  box: edge lengths, or a
+    3x3 cell matrix (columns = cell vectors; nearest image in fractional
+    coordinates, exact for the nearly orthogonal cells used here)."""
     M = O.shape[0]
     if box is None:
         i, j = np.triu_indices(M, 1)
         return i, j, np.zeros((i.size, 3))
     box = np.asarray(box, dtype=np.float64)
+    cell = box if box.ndim == 2 else None
     Is, Js, Ss = [], [], []
     for i0 in range(0, M, 256):
         i1 = min(M, i0 + 256)
         d = O[None, :, :] - O[i0:i1, None, :]
-        sh = -box * np.round(d / box)
+        if cell is None:
+            sh = -box * np.round(d / box)
+        else:
+            sh = -np.round(d @ np.linalg.inv(cell).T) @ cell.T
         d = d + sh
         r2 = np.einsum("ijk,ijk->ij", d, d)
         ii, jj = np.nonzero(r2 < cut * cut)
