@@ -139,7 +139,16 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
 /* One energy + force evaluation.  pos: n_mol*9 doubles (O, H1, H2 xyz per
  * molecule, Angstrom).  box: 3 doubles or NULL to keep the current box.
  * e: host struct, filled on success (may be NULL).  forces: n_mol*9 doubles
- * (kcal/mol/A, = -dE/dx) or NULL.  virial: reserved, must be NULL. */
+ * (kcal/mol/A, = -dE/dx) or NULL.  virial: 9 host doubles (row-major 3x3,
+ * kcal/mol) or NULL: W_ab = -dE/d eps_ab for the affine strain x -> (I + eps) x
+ * applied to every atom and to the periodic cell, the quantity a barostat
+ * needs (pressure tensor P = (sum m v v + W) / V); in the gas phase it
+ * equals sum over atoms of F_a x_b.  It is a sum of pair terms (real space),
+ * the reciprocal-space strain derivative (k-space sums and the k-dependence of
+ * the multipole structure factor) and the frame terms of the rotating
+ * multipoles and lone pairs; a cluster batch returns the sum over clusters.
+ * Requesting it runs the force pass and selects kernel variants that also
+ * accumulate it. */
 sibfa_status sibfa_energy_forces(sibfa_ctx *ctx, const double *pos, const double *box,
                                  sibfa_energy_terms *e, double *forces, double *virial);
 

@@ -41,7 +41,7 @@ struct sibfa_ctx {
     bool have_fft = false;
     int ncell[3] = {0, 0, 0};
     double *d_forces = nullptr;   // M*9
-    double *d_energy = nullptr;   // NTERM+1
+    double *d_energy = nullptr;   // NTERM+1 energies; [16, 25) the virial
     double *d_vel = nullptr, *d_invm = nullptr;
     double *h_pin = nullptr;      // pinned staging, M*9*2 + 64 doubles
     double *h_scal = nullptr;     // pinned copy of the solver scalars of the last solve
@@ -168,6 +168,9 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.lam, M * 2);
     AL(d.kap, M * 3);
     AL(d.epart, M * NTERM);
+    AL(d.vir, M * 9);
+    AL(d.vir_r, M * 9);
+    AL(d.vphi, M * 9);
     AL(d.gpt_r, M * NP * 3);
     AL(d.gmu_r, M * NS * 3);
     AL(d.gth_r, M * NS * 6);
@@ -213,6 +216,16 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
         }
         AL(d.infl, nh);
         AL(d.inflR, nh);
+        AL(d.virk, (size_t)2 * VK_BLOCKS * 8);
+        if (sizeof(R) == 4) {
+            cufftComplex *c;
+            AL(c, nh);
+            d.qhat_p = c;
+        } else {
+            cufftDoubleComplex *c;
+            AL(c, nh);
+            d.qhat_p = c;
+        }
     }
     return SIBFA_OK;
 }
@@ -509,7 +522,8 @@ sibfa_status evaluate(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, doubl
         CK(cudaMemsetAsync(d.grid, 0, ng * sizeof(R), ctx->s2));
         launch_spread(p, d, SPREAD_PERM, nullptr, d.grid, L2);
         if ((st = fft(ctx, d, true, 1))) return st;
-        launch_convolve(p, d, d.cgrid, 1, 0, L2);
+        if (p.vir) launch_convolve_vir(p, d, 0, L2);
+        else launch_convolve(p, d, d.cgrid, 1, 0, L2);
         if ((st = fft(ctx, d, false, 1))) return st;
         launch_gather_perm(p, dr, L2);
         launch_intra_perm(p, dr, L2);
@@ -541,7 +555,8 @@ sibfa_status evaluate(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, doubl
             launch_spread(p, d, SPREAD_DIP, nullptr, d.grid, L2);
             launch_spread(p, d, SPREAD_LAMBDA, nullptr, d.grid + ng, L2);
             if ((sf = fft(ctx, d, true, 2))) return sf;
-            launch_convolve(p, d, d.cgrid, 2, 0, L2);
+            if (p.vir) launch_convolve_vir(p, d, 1, L2);
+            else launch_convolve(p, d, d.cgrid, 2, 0, L2);
             if ((sf = fft(ctx, d, false, 2))) return sf;
             launch_gather_polforce(p, dr, L2);
             launch_intra_polforce(p, dr, L2);
@@ -580,7 +595,7 @@ sibfa_status check_flags(sibfa_ctx *ctx, int flags) {
 
 template <typename R>
 sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_energy_terms *e, double *forces,
-                 bool dipoles_only, double tol, double *mu_out, int *iters, double *resid) {
+                 bool dipoles_only, double tol, double *mu_out, int *iters, double *resid, double *virial = nullptr) {
     DevState<R> &d = state<R>(ctx);
     const int M = ctx->M;
     const size_t nb = (size_t)M * 9 * sizeof(double);
@@ -604,9 +619,18 @@ sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_ene
         }
     }
     ctx->md_forces_valid = false;
-    sibfa_status st = evaluate<R>(ctx, forces != nullptr, dipoles_only, tol);
+    // the virial needs the force pass; kernels read the switch from their parameters
+    ctx->kp.vir = virial != nullptr;
+    sibfa_status st = evaluate<R>(ctx, forces != nullptr || virial != nullptr, dipoles_only, tol);
+    ctx->kp.vir = 0;
     if (st == SIBFA_E_CUDA) return st;
     double *h = ctx->h_pin;
+    if (virial) {
+        KParams pv = ctx->kp;
+        pv.vir = 1;
+        launch_virial_total(pv, d, ctx->d_energy + 16, Launch{ctx->s, &ctx->launches});
+        CK(cudaMemcpyAsync(h + 20, ctx->d_energy + 16, 9 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    }
     // results: energies + flags (+ dipoles) to pinned memory
     CK(cudaMemcpyAsync(h, ctx->d_energy, (NTERM + 1) * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaMemcpyAsync((int *)(h + 16), d.flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
@@ -626,6 +650,7 @@ sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_ene
     CK(cudaStreamSynchronize(ctx->s));
     CK(cudaGetLastError());
     if (forces && !is_device_ptr(forces)) std::memcpy(forces, h + 32, nb);
+    if (virial) std::memcpy(virial, h + 20, 9 * sizeof(double));
     if (mu_out && !is_device_ptr(mu_out)) std::memcpy(mu_out, h + 32, nb);
     solve_stats(ctx);
     sibfa_status fl = check_flags(ctx, *(int *)(h + 16));
@@ -845,7 +870,7 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
     do {
         st = dalloc(ctx, &ctx->d_forces, (size_t)ctx->M * 9);
         if (st) break;
-        st = dalloc(ctx, &ctx->d_energy, 16);
+        st = dalloc(ctx, &ctx->d_energy, 32);
         if (st) break;
         if (cudaMallocHost((void **)&ctx->h_pin, ((size_t)ctx->M * 9 * 2 + 64) * sizeof(double)) != cudaSuccess ||
             cudaMallocHost((void **)&ctx->h_scal, 16 * sizeof(double)) != cudaSuccess) {
@@ -867,13 +892,10 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
 sibfa_status sibfa_energy_forces(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_energy_terms *e,
                                  double *forces, double *virial) {
     if (!ctx || !pos) return SIBFA_E_INVALID;
-    if (virial) {
-        ctx->err = "virial output is not implemented";
-        return SIBFA_E_INVALID;
-    }
     const double tol = ctx->opts.pcg_tol_D > 0 ? ctx->opts.pcg_tol_D : 1e-6;
-    return ctx->prec == SIBFA_PREC_MIXED ? run<float>(ctx, pos, box, e, forces, false, tol, nullptr, nullptr, nullptr)
-                                         : run<double>(ctx, pos, box, e, forces, false, tol, nullptr, nullptr, nullptr);
+    return ctx->prec == SIBFA_PREC_MIXED
+               ? run<float>(ctx, pos, box, e, forces, false, tol, nullptr, nullptr, nullptr, virial)
+               : run<double>(ctx, pos, box, e, forces, false, tol, nullptr, nullptr, nullptr, virial);
 }
 
 sibfa_status sibfa_solve_dipoles(sibfa_ctx *ctx, const double *pos, const double *box, double tol_D, double *mu,

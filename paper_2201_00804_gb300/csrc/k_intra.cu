@@ -51,6 +51,25 @@ __device__ inline V3<R> opt(const DevState<R> &d, int m, int k) {
     return mk(o[0], o[1], o[2]);
 }
 
+// warp sum of the per-lane virials into vir[m] (scaled by ke)
+template <typename R>
+__device__ inline void vir_warp_out(const DevState<R> &d, int m, R (&W)[9], double ke, int lane) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        R v = W[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        W[k] = v;
+    }
+    if (lane < 9) {
+        R v = W[0];
+#pragma unroll
+        for (int k = 1; k < 9; ++k)
+            if (k == lane) v = W[k];
+        d.vir[m * 9 + lane] += ke * double(v);
+    }
+}
+
 __constant__ int c_pair10[10][2] = {{0, 1}, {0, 2}, {0, 3}, {0, 4}, {1, 2}, {1, 3}, {1, 4}, {2, 3}, {2, 4}, {3, 4}};
 
 // Permanent pass.  Lanes 0-9: the 10 site pairs (energy, gradients and
@@ -69,6 +88,7 @@ __global__ void __launch_bounds__(128) k_intra_perm(KParams p, DevState<R> d) {
     const R spi = R(0.56418958354775628695);   // 1 / sqrt(pi)
     const R cself = R(4.0 / 3.0) * al * al * al * spi;
     R e = R(0), vl = R(0);
+    R W[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};   // virial (p.vir)
     if (lane < 10) {
         const int t = c_pair10[lane][0], s = c_pair10[lane][1];
         const Mp<R> Mt = load_mp(d.gmp + (m * NS + t) * GMP), Ms = load_mp(d.gmp + (m * NS + s) * GMP);
@@ -81,6 +101,7 @@ __global__ void __launch_bounds__(128) k_intra_perm(KParams p, DevState<R> d) {
         const V3<R> gt = target_grad(Mt, Ms, x, g, f);
         sadd3(A.gpt[t], gt, R(-1));
         sadd3(A.gpt[s], gt, R(1));
+        if (p.vir) vir_add(W, gt, x, R(-1));
         sadd3(A.gmu[t], f.d1, R(-1));
         sadd6(A.gth[t], f.d2, R(-1.0 / 3.0));
         FieldTerms<R> f2;
@@ -135,6 +156,8 @@ __global__ void __launch_bounds__(128) k_intra_perm(KParams p, DevState<R> d) {
         d.vlp[m * 2 + 1] += ke * v1;
         d.epart[m * NTERM + T_ELEC] += ke * esum;
     }
+    // the lone pairs' share of the lambda-weighted virial is taken in the force pass
+    if (p.vir) vir_warp_out(d, m, W, ke, lane);
 }
 
 template <typename R>
@@ -158,6 +181,7 @@ __global__ void __launch_bounds__(128) k_intra_polforce(KParams p, DevState<R> d
     IntraAcc<R> &A = acc[w];
     zero_acc(A, lane);
     const R al = sc<R>(p).alpha;
+    R W[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};   // virial (p.vir)
     auto mu_of = [&](int a) {
         return mk(R(d.mu[m * 9 + a * 3]), R(d.mu[m * 9 + a * 3 + 1]), R(d.mu[m * 9 + a * 3 + 2]));
     };
@@ -174,6 +198,7 @@ __global__ void __launch_bounds__(128) k_intra_polforce(KParams p, DevState<R> d
         const V3<R> ga = symv(f.d2, mua);
         sadd3(A.gpt[a], ga, R(-1));
         sadd3(A.gpt[s], ga, R(1));
+        if (p.vir) vir_add(W, ga, x, R(-1));
         Mp<R> dip{};
         dip.mu = mua;
         FieldTerms<R> f2;
@@ -192,6 +217,7 @@ __global__ void __launch_bounds__(128) k_intra_polforce(KParams p, DevState<R> d
         const V3<R> ga = symv(f.d2, mu_of(a));
         sadd3(A.gpt[a], ga, R(-1));
         sadd3(A.gpt[b], ga, R(1));
+        if (p.vir) vir_add(W, ga, x, R(-1));
     } else if (lane < 25) {
         const int l = (lane - 15) / 5, s = (lane - 15) % 5;
         const double lq = d.lam[m * 2 + l];
@@ -204,7 +230,9 @@ __global__ void __launch_bounds__(128) k_intra_polforce(KParams p, DevState<R> d
             c.q = R(lq);
             FieldTerms<R> f;
             source_field<R, 3>(c, x, g, f);
-            sadd3(A.gpt[s], target_grad(Ms, c, x, g, f), R(-1));
+            const V3<R> tg = target_grad(Ms, c, x, g, f);
+            sadd3(A.gpt[s], tg, R(-1));
+            if (p.vir) vir_add(W, tg, x, R(-1));   // the whole (site, lambda) pair
             sadd3(A.gmu[s], f.d1, R(-1));
             sadd6(A.gth[s], f.d2, R(-1.0 / 3.0));
         }
@@ -218,6 +246,7 @@ __global__ void __launch_bounds__(128) k_intra_polforce(KParams p, DevState<R> d
     for (int k = lane; k < NS * 3; k += 32) d.gpt[m * NP * 3 + k] += ke * double((&A.gpt[0][0])[k]);
     for (int k = lane; k < NS * 3; k += 32) d.gmu[m * NS * 3 + k] += ke * double((&A.gmu[0][0])[k]);
     for (int k = lane; k < NS * 6; k += 32) d.gth[m * NS * 6 + k] += ke * double((&A.gth[0][0])[k]);
+    if (p.vir) vir_warp_out(d, m, W, ke, lane);
 }
 
 template <typename R>

@@ -55,9 +55,13 @@ struct PermAcc {
     Acc<R> Ue, Up, Vl;
     V3<R> gr, gm, ef;
     Sym<R> gt;
+    R W[9];   // virial (VIR kernels only)
 };
 
-template <typename R, bool PER, bool ATOM_SRC>
+// VIR: also accumulate the pair virial 1/2 g (x) x of the target's gradient g
+// (both molecules of a pair see it, so each adds half); the lone-pair
+// potential's share is taken with the lambda charges in the force pass.
+template <typename R, bool PER, bool ATOM_SRC, bool VIR>
 __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d, int w, bool is_lp, V3<R> ot,
                                           const Mp<R> &mt, R Nt_, int js, V3<R> rs, size_t te, PermAcc<R> &A) {
     const Scal<R> &S = sc<R>(p);
@@ -82,7 +86,9 @@ __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d
     source_field<R, 3>(ms, x, g, f);
     const R U = mt.q * f.phi + dot(mt.mu, f.d1) + third * symdd(mt.th, f.d2);
     A.Ue.add(R(0.5) * U);
-    A.gr = A.gr + target_grad(mt, ms, x, g, f);
+    const V3<R> gel = target_grad(mt, ms, x, g, f);
+    A.gr = A.gr + gel;
+    V3<R> gv = gel;   // this pair's gradient (virial)
     A.gm = A.gm + f.d1;
     symadd(A.gt, f.d2, third);
     // ---- penetration: charge-charge*, charge-dipole*, charge-quadrupole*
@@ -120,12 +126,14 @@ __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d
             source_field<R, 1>(m0, xs, es, f3);
             pen += Ns * f3.phi;
             A.gr = A.gr - Ns * f3.d1;
+            if (VIR) gv = gv - Ns * f3.d1;
             A.gm = A.gm + (-Ns * es[1]) * xs;
             const R c = Ns * third * es[2];
             A.gt.xx += c * xs.x * xs.x; A.gt.yy += c * xs.y * xs.y; A.gt.zz += c * xs.z * xs.z;
             A.gt.xy += c * xs.x * xs.y; A.gt.xz += c * xs.x * xs.z; A.gt.yz += c * xs.y * xs.z;
         }
         A.gr = A.gr + gq * x;
+        if (VIR) gv = gv + gq * x;
         if (Nt_ != R(0)) {   // valence of t in the dipole/quadrupole potential of s
             Mp<R> m0 = ms;
             m0.q = R(0);
@@ -133,9 +141,11 @@ __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d
             source_field<R, 1>(m0, x, et, f2);
             pen += Nt_ * f2.phi;
             A.gr = A.gr + Nt_ * f2.d1;
+            if (VIR) gv = gv + Nt_ * f2.d1;
         }
         A.Up.add(R(0.5) * pen);
     }
+    if (VIR) vir_add(A.W, gv, x, R(0.5));
     // ---- Thole-damped permanent field on the polarizable atom (same base kernel g)
     if (w < 3) {
         R gtol[4];
@@ -154,9 +164,10 @@ __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d
     }
 }
 
-template <typename R, bool PER>
+template <typename R, bool PER, bool VIR>
 __global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) {
     __shared__ double s_e[7][2];
+    __shared__ double s_w[VIR ? NS : 1][9];
     __shared__ PairQueue<R> qs[7];
     static_assert(sizeof(PairQueue<R>) >= 15 * 33 * sizeof(R), "reduction buffer aliases the queue");
     const int i = blockIdx.x;
@@ -176,6 +187,8 @@ __global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) 
     A.gm = A.gr;
     A.ef = A.gr;
     A.gt = Sym<R>{};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) A.W[k] = R(0);
     int ha = 0, ta = 0, hm = 0, tm = 0;   // queue heads and tails (warp-uniform, monotone)
     const int nn = d.nnbr[i];
     for (int base = 0;; base += 32) {
@@ -216,14 +229,14 @@ __global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) 
         while (ta - ha >= 32 || (flush && ta > ha)) {
             if (lane < ta - ha) {
                 const int e = (ha + lane) % QCAP_A;
-                perm_pair<R, PER, true>(p, d, w, is_lp, ot, mt, Nt_, q.js[e], q.at(e), tbase + ha + lane, A);
+                perm_pair<R, PER, true, VIR>(p, d, w, is_lp, ot, mt, Nt_, q.js[e], q.at(e), tbase + ha + lane, A);
             }
             ha += min(32, ta - ha);
         }
         while (tm - hm >= 32 || (flush && tm > hm)) {
             if (lane < tm - hm) {
                 const int e = QCAP_A + (hm + lane) % QCAP_M;
-                perm_pair<R, PER, false>(p, d, w, is_lp, ot, mt, Nt_, q.js[e], q.at(e), 0, A);
+                perm_pair<R, PER, false, VIR>(p, d, w, is_lp, ot, mt, Nt_, q.js[e], q.at(e), 0, A);
             }
             hm += min(32, tm - hm);
         }
@@ -252,6 +265,10 @@ __global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) 
         else if (lane < 12) dst = d.gth + (i * NS + w) * 6 + lane - 6;
         else if (lane < 15 && w < 3) dst = d.efield + i * 9 + w * 3 + lane - 12;
         if (dst) *dst += (lane < 12 ? ke : 1.0) * double(t);
+        if (VIR) {
+            const R wv = warp_transpose_sum<R, 9>(A.W, buf, lane);
+            if (lane < 9) s_w[w][lane] = double(wv);
+        }
         const double e0 = warp_sum_acc(A.Ue), e1 = warp_sum_acc(A.Up);
         if (lane == 0) {
             s_e[w][0] = e0;
@@ -265,12 +282,22 @@ __global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) 
         d.epart[i * NTERM + T_ELEC] += ke * a;
         d.epart[i * NTERM + T_PEN] += ke * b;
     }
+    if (VIR && threadIdx.x < 9) {   // the site warps' virials in a fixed order
+        double v = 0;
+        for (int k = 0; k < NS; ++k) v += s_w[k][threadIdx.x];
+        d.vir[i * 9 + threadIdx.x] += ke * v;
+    }
 }
 
 template <typename R>
 void launch_real_perm(const KParams &p, DevState<R> &d, Launch L) {
-    if (p.periodic) k_real_perm<R, true><<<p.M, 224, 0, L.s>>>(p, d);
-    else k_real_perm<R, false><<<p.M, 224, 0, L.s>>>(p, d);
+    if (p.vir) {
+        if (p.periodic) k_real_perm<R, true, true><<<p.M, 224, 0, L.s>>>(p, d);
+        else k_real_perm<R, false, true><<<p.M, 224, 0, L.s>>>(p, d);
+    } else {
+        if (p.periodic) k_real_perm<R, true, false><<<p.M, 224, 0, L.s>>>(p, d);
+        else k_real_perm<R, false, false><<<p.M, 224, 0, L.s>>>(p, d);
+    }
     count(L);
 }
 
@@ -318,7 +345,12 @@ __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1
     return o;
 }
 
-template <typename R, bool PER>
+// VIR: the virial of the pair terms by translation invariance: with X_p =
+// O_i + off_p, sum over a molecule pair of g_p (x) X_p = sum_{p of i} g_p (x)
+// off_p + sum_{p of j} g_p (x) off_p - G_{i<-j} (x) dO_ij, where G_{i<-j} is
+// the total gradient on i's points and dO_ij = O_j - O_i; each side adds
+// its own offsets term and half of the last one.
+template <typename R, bool PER, bool VIR>
 __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
     __shared__ R red[4][20 * 33];
     const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -334,6 +366,9 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
     V3<R> G[5];
     for (int k = 0; k < 5; ++k) G[k] = mk(R(0), R(0), R(0));
     R lam[2] = {R(0), R(0)}, kap[3] = {R(0), R(0), R(0)};
+    R W[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) W[k] = R(0);
     Acc<R> Ect;
     const int nn = d.nnbr[i];
     for (int slot = lane; slot < nn; slot += 32) {
@@ -349,6 +384,7 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
         Q[4] = dO + my_pt(d, j, 6);
         const R Vj[2] = {R(d.vlp[j * 2]), R(d.vlp[j * 2 + 1])};
         const R Vint_j[3] = {R(d.vint[j * 3]), R(d.vint[j * 3 + 1]), R(d.vint[j * 3 + 2])};
+        V3<R> Gj = mk(R(0), R(0), R(0));   // gradient on i's points from j (virial)
         for (int l = 0; l < 2; ++l)
             for (int k = 1; k <= 2; ++k) {
                 // i donor (lone pair l of i), j acceptor (bond O-H_k of j)
@@ -364,7 +400,9 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
                 G[k] = G[k] + q.ga2;
                 kap[0] += q.dVi1;
                 kap[k] += q.dVi2;
+                if (VIR) Gj = Gj + o.gc + o.glp + q.ga1 + q.ga2;
             }
+        if (VIR) vir_add(W, Gj, dO, R(-0.5));
     }
     const R vals[20] = {G[0].x, G[0].y, G[0].z, G[1].x, G[1].y, G[1].z, G[2].x, G[2].y, G[2].z,
                         G[3].x, G[3].y, G[3].z, G[4].x, G[4].y, G[4].z, lam[0], lam[1], kap[0], kap[1], kap[2]};
@@ -375,14 +413,21 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
     else if (lane < 17) dst = d.lam + i * 2 + lane - 15;
     else if (lane < 20) dst = d.kap + i * 3 + lane - 17;
     if (dst) *dst += double(t);
+    if (VIR) vir_points_out(d, i, P, t, W, red[threadIdx.x >> 5], lane);
     const double e = warp_sum_acc(Ect);
     if (lane == 0) d.epart[i * NTERM + T_CT] += e;
 }
 
 template <typename R>
 void launch_ct(const KParams &p, DevState<R> &d, Launch L) {
-    if (p.periodic) k_ct<R, true><<<(p.M + 3) / 4, 128, 0, L.s>>>(p, d);
-    else k_ct<R, false><<<(p.M + 3) / 4, 128, 0, L.s>>>(p, d);
+    const unsigned nb = (p.M + 3) / 4;
+    if (p.vir) {
+        if (p.periodic) k_ct<R, true, true><<<nb, 128, 0, L.s>>>(p, d);
+        else k_ct<R, false, true><<<nb, 128, 0, L.s>>>(p, d);
+    } else {
+        if (p.periodic) k_ct<R, true, false><<<nb, 128, 0, L.s>>>(p, d);
+        else k_ct<R, false, false><<<nb, 128, 0, L.s>>>(p, d);
+    }
     count(L);
 }
 
@@ -451,9 +496,13 @@ template <typename R>
 struct PfAcc {
     V3<R> gr, gm;
     Sym<R> gt;
+    R W[9];   // virial (VIR kernels only)
 };
 
-template <typename R, bool PER, int KIND>   // KIND 0: atom source, 1: midpoint source, 2: lambda charge
+// VIR: also accumulate the pair virial g (x) x of the target's gradient g:
+// half of it for dipole and multipole sources (the partner adds the other
+// half), all of it for lambda charges (whose lone-pair side adds none).
+template <typename R, bool PER, int KIND, bool VIR>   // KIND 0: atom source, 1: midpoint source, 2: lambda charge
 __device__ __forceinline__ void polf_pair(const KParams &p, const DevState<R> &d, int w, V3<R> ot, const Mp<R> &mt,
                                           V3<R> mui, int js, V3<R> rs, PfAcc<R> &A) {
     const Scal<R> &S = sc<R>(p);
@@ -470,11 +519,14 @@ __device__ __forceinline__ void polf_pair(const KParams &p, const DevState<R> &d
         ms.q = d.lamR[j * 2 + s];
         FieldTerms<R> f;
         source_field<R, 3>(ms, x, g, f);
-        A.gr = A.gr + target_grad(mt, ms, x, g, f);
+        const V3<R> gl = target_grad(mt, ms, x, g, f);
+        A.gr = A.gr + gl;
         A.gm = A.gm + f.d1;
         symadd(A.gt, f.d2, third);
+        if (VIR) vir_add(A.W, gl, x, R(1));
         return;
     }
+    V3<R> gv = mk(R(0), R(0), R(0));   // this pair's gradient (virial)
     R gb[5], g[6];
     if (PER) g_erfc<R, 4>(r, rinv, S.alpha, gb);
     else g_bare<R, 4>(rinv, gb);
@@ -486,22 +538,31 @@ __device__ __forceinline__ void polf_pair(const KParams &p, const DevState<R> &d
         ms.mu = mk(mj[0], mj[1], mj[2]);
         FieldTerms<R> f;
         source_field<R, 3>(ms, x, g, f);
-        A.gr = A.gr + target_grad(mt, ms, x, g, f);
+        const V3<R> gm = target_grad(mt, ms, x, g, f);
+        A.gr = A.gr + gm;
         A.gm = A.gm + f.d1;
         symadd(A.gt, f.d2, third);
+        if (VIR) gv = gm;
         // induced-induced, d/dr_a of mu_a . grad phi_b: for w < 3 the site
         // damping polarizability is the atom's, so f is the atom-atom field
-        if (w < 3) A.gr = A.gr + symv(f.d2, mui);
+        if (w < 3) {
+            const V3<R> gi = symv(f.d2, mui);
+            A.gr = A.gr + gi;
+            if (VIR) gv = gv + gi;
+        }
     }
     if (w < 3) {       // permanent multipoles of site s of j at polarizable atom w
         const Mp<R> ms = load_mp_g(d.gmp + (j * NS + s) * GMP);
         FieldTerms<R> f;
         source_field<R, 2>(ms, x, g, f);
-        A.gr = A.gr + symv(f.d2, mui);
+        const V3<R> gp = symv(f.d2, mui);
+        A.gr = A.gr + gp;
+        if (VIR) gv = gv + gp;
     }
+    if (VIR) vir_add(A.W, gv, x, R(0.5));
 }
 
-template <typename R, bool PER>
+template <typename R, bool PER, bool VIR>
 __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d) {
     __shared__ PairQueue<R, PQ_A + PQ_M + PQ_L> qs[5];
     static_assert(sizeof(PairQueue<R, PQ_A + PQ_M + PQ_L>) >= 12 * 33 * sizeof(R), "reduction buffer");
@@ -517,6 +578,8 @@ __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d)
     A.gr = mk(R(0), R(0), R(0));
     A.gm = A.gr;
     A.gt = Sym<R>{};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) A.W[k] = R(0);
     int ha = 0, ta = 0, hm = 0, tm = 0, hl = 0, tl = 0;
     const int nn = d.nnbr[i];
     for (int base = 0;; base += 32) {
@@ -557,21 +620,21 @@ __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d)
         while (ta - ha >= 32 || (flush && ta > ha)) {
             if (lane < ta - ha) {
                 const int e = (ha + lane) % PQ_A;
-                polf_pair<R, PER, 0>(p, d, w, ot, mt, mui, q.js[e], q.at(e), A);
+                polf_pair<R, PER, 0, VIR>(p, d, w, ot, mt, mui, q.js[e], q.at(e), A);
             }
             ha += min(32, ta - ha);
         }
         while (tm - hm >= 32 || (flush && tm > hm)) {
             if (lane < tm - hm) {
                 const int e = PQ_A + (hm + lane) % PQ_M;
-                polf_pair<R, PER, 1>(p, d, w, ot, mt, mui, q.js[e], q.at(e), A);
+                polf_pair<R, PER, 1, VIR>(p, d, w, ot, mt, mui, q.js[e], q.at(e), A);
             }
             hm += min(32, tm - hm);
         }
         while (tl - hl >= 32 || (flush && tl > hl)) {
             if (lane < tl - hl) {
                 const int e = PQ_A + PQ_M + (hl + lane) % PQ_L;
-                polf_pair<R, PER, 2>(p, d, w, ot, mt, mui, q.js[e], q.at(e), A);
+                polf_pair<R, PER, 2, VIR>(p, d, w, ot, mt, mui, q.js[e], q.at(e), A);
             }
             hl += min(32, tl - hl);
         }
@@ -587,12 +650,28 @@ __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d)
     else if (lane < 6) dst = d.gmu + (i * NS + w) * 3 + lane - 3;
     else if (lane < 12) dst = d.gth + (i * NS + w) * 6 + lane - 6;
     if (dst) *dst += ke * double(s);
+    if (VIR) {   // the five warps' virials summed in a fixed order
+        __shared__ double s_w[NS][9];
+        const R wv = warp_transpose_sum<R, 9>(A.W, reinterpret_cast<R *>(&q), lane);
+        if (lane < 9) s_w[w][lane] = double(wv);
+        __syncthreads();
+        if (threadIdx.x < 9) {
+            double v = 0;
+            for (int k = 0; k < NS; ++k) v += s_w[k][threadIdx.x];
+            d.vir[i * 9 + threadIdx.x] += ke * v;
+        }
+    }
 }
 
 template <typename R>
 void launch_real_polforce(const KParams &p, DevState<R> &d, Launch L) {
-    if (p.periodic) k_real_polforce<R, true><<<p.M, 160, 0, L.s>>>(p, d);
-    else k_real_polforce<R, false><<<p.M, 160, 0, L.s>>>(p, d);
+    if (p.vir) {
+        if (p.periodic) k_real_polforce<R, true, true><<<p.M, 160, 0, L.s>>>(p, d);
+        else k_real_polforce<R, false, true><<<p.M, 160, 0, L.s>>>(p, d);
+    } else {
+        if (p.periodic) k_real_polforce<R, true, false><<<p.M, 160, 0, L.s>>>(p, d);
+        else k_real_polforce<R, false, false><<<p.M, 160, 0, L.s>>>(p, d);
+    }
     count(L);
 }
 

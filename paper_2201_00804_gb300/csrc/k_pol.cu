@@ -391,6 +391,7 @@ __global__ void __launch_bounds__(128) k_finalize(KParams p, DevState<R> d, doub
     const int m = gidx >> 2, t = gidx & 3;
     const bool live = m < p.M;
     V3<R> gO = mk(R(0), R(0), R(0)), gH1 = gO, gH2 = gO;
+    R W[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};   // virial (p.vir)
     if (live) {
         V3<R> r1, r2;
         bond_vectors(d.pos + m * 9, r1, r2);
@@ -451,6 +452,10 @@ __global__ void __launch_bounds__(128) k_finalize(KParams p, DevState<R> d, doub
                 gH2 = -(gzv + gxv);
                 gH1 = gxv;
             }
+            if (p.vir) {   // the frame's atoms move affinely: sum_a g_a (x) (x_a - O)
+                vir_add(W, gH1, r1, R(1));
+                vir_add(W, gH2, r2, R(1));
+            }
         } else {
             V3<R> G[NS], X[NS];
             for (int k = 0; k < NS; ++k) {
@@ -470,8 +475,17 @@ __global__ void __launch_bounds__(128) k_finalize(KParams p, DevState<R> d, doub
                     const R c = kk * d.gmp[(m * NS + s) * GMP] * ir * ir * ir;
                     G[a] = G[a] - c * dd;
                     G[s] = G[s] + c * dd;
+                    if (p.vir) vir_add(W, dd, dd, -c);   // the (a, s) pair's gradient on a is -c dd
                 }
             }
+            // The pair kernels counted the lone pairs as points moving with
+            // the strain; they follow the frame of O instead, which lane 0's
+            // chain rule has taken: remove their point share g_lp (x) off_lp.
+            if (p.vir)
+                for (int l = 0; l < 2; ++l) {
+                    const R *o = d.off + (m * NP + 5 + l) * 3;
+                    vir_add(W, glp(l), mk(o[0], o[1], o[2]), R(-1));
+                }
             // midpoints and the lone pairs' carrier
             gO = G[0] + R(0.5) * (G[3] + G[4]) + glp(0) + glp(1);
             gH1 = G[1] + R(0.5) * G[3];
@@ -488,6 +502,57 @@ __global__ void __launch_bounds__(128) k_finalize(KParams p, DevState<R> d, doub
         double *F = forces + m * 9;
         for (int k = 0; k < 9; ++k) F[k] = -(double)v[k];
     }
+    if (p.vir) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            W[k] += __shfl_xor_sync(0xffffffffu, W[k], 1, 4);
+            W[k] += __shfl_xor_sync(0xffffffffu, W[k], 2, 4);
+        }
+        if (live && t == 0)
+            for (int k = 0; k < 9; ++k) d.vir[m * 9 + k] += (double)W[k];
+    }
+}
+
+// Virial total: out[3a + b] = -dE/d eps_ab = -(sum over molecules of both
+// chains' dE/d eps + the k-space sums of npass convolution passes), summed
+// in a fixed order by one block.
+template <typename R>
+__global__ void __launch_bounds__(256) k_virial_total(int M, DevState<R> d, int npass, double *out) {
+    __shared__ double sh[8][9];
+    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int m = threadIdx.x; m < M; m += blockDim.x)
+        for (int k = 0; k < 9; ++k) v[k] += d.vir[m * 9 + k] + d.vir_r[m * 9 + k];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = 0; k < 9; ++k) {
+        double x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[w][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[9];
+        for (int k = 0; k < 9; ++k) {
+            t[k] = 0;
+            for (int j = 0; j < 8; ++j) t[k] += sh[j][k];
+        }
+        double ks[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int b = 0; b < npass * VK_BLOCKS; ++b)
+            for (int k = 0; k < 7; ++k) ks[k] += d.virk[(size_t)b * 8 + k];
+        // dE/d eps_ab from the k-space sums: -delta_ab sum e + sum e f m_a m_b
+        const int ia[6] = {0, 4, 8, 1, 2, 5}, ib[6] = {0, 4, 8, 3, 6, 7};
+        for (int k = 0; k < 3; ++k) t[4 * k] -= ks[0];
+        for (int k = 0; k < 6; ++k) {
+            t[ia[k]] += ks[1 + k];
+            if (ib[k] != ia[k]) t[ib[k]] += ks[1 + k];
+        }
+        for (int k = 0; k < 9; ++k) out[k] = -t[k];
+    }
+}
+
+template <typename R>
+void launch_virial_total(const KParams &p, DevState<R> &d, double *out, Launch L) {
+    k_virial_total<R><<<1, 256, 0, L.s>>>(p.M, d, p.periodic ? 2 : 0, out);
+    count(L);
 }
 
 // Join of the reciprocal chain into the arrays read by the charge transfer
@@ -644,7 +709,8 @@ void launch_md_kick(int M, double *pos, double *vel, const double *inv_mass, con
     template void launch_pol_energy<R>(const KParams &, DevState<R> &, Launch);                        \
     template void launch_finalize<R>(const KParams &, DevState<R> &, double *, Launch);                \
     template void launch_merge_rec<R>(const KParams &, DevState<R> &, Launch);                         \
-    template void launch_cluster_energy<R>(const KParams &, DevState<R> &, double *, Launch);
+    template void launch_cluster_energy<R>(const KParams &, DevState<R> &, double *, Launch);           \
+    template void launch_virial_total<R>(const KParams &, DevState<R> &, double *, Launch);
 INST(float)
 INST(double)
 

@@ -97,6 +97,7 @@ template <typename R>
 struct ShortAcc {
     V3<R> G[5];
     Acc<R> Erep, Ed, Ex;
+    R W[9];   // virial: -1/2 sum over items of (gradient on i's points) (x) dO_ij (VIR kernels only)
 };
 
 template <typename R>
@@ -141,7 +142,7 @@ __device__ inline void neighbour(const DevState<R> &d, int i, int slot, int &j, 
 
 // ---- item evaluation -------------------------------------------------------
 
-template <typename R>
+template <typename R, bool VIR>
 __device__ void item_bb(const Scal<R> &S, const ShortTables &T, const DevState<R> &d, const ShortI<R> &I, int i,
                         int word, ShortAcc<R> &a) {
     const int slot = word >> 5, c = word & 31;
@@ -170,11 +171,13 @@ __device__ void item_bb(const Scal<R> &S, const ShortTables &T, const DevState<R
     R e1, e2, er;
     a.Erep.add(R(0.5) * rep_energy(S.occ * S.occ, S.rep_c1, S.rep_c2, O1, O2, rm, e1, e2, er));
     const V3<R> drm = (R(0.5) / rm) * dm;
-    a.G[0] = a.G[0] + e1 * g1a + e2 * g2a + er * drm;
-    addG(a, kb, e1 * g1b + e2 * g2b + er * drm);
+    const V3<R> ga = e1 * g1a + e2 * g2a + er * drm, gb = e1 * g1b + e2 * g2b + er * drm;
+    a.G[0] = a.G[0] + ga;
+    addG(a, kb, gb);
+    if (VIR) vir_add(a.W, ga + gb, dO, R(-0.5));
 }
 
-template <typename R>
+template <typename R, bool VIR>
 __device__ void item_bl(const Scal<R> &S, const ShortTables &T, const DevState<R> &d, const ShortI<R> &I, int i,
                         int word, ShortAcc<R> &a) {
     const int slot = word >> 5, c = word & 31;
@@ -202,12 +205,14 @@ __device__ void item_bl(const Scal<R> &S, const ShortTables &T, const DevState<R
     R e1, e2, er;
     a.Erep.add(R(0.5) * rep_energy(S.occ * S.nlp, S.rep_c1, S.rep_c2, O1, O2, rr, e1, e2, er));
     const V3<R> drm = (R(0.5) / rr) * dm;
-    a.G[0] = a.G[0] + e1 * g1a + e2 * g2a + er * drm;
-    addG(a, kb, e1 * g1b + e2 * g2b + er * drm);
+    const V3<R> ga = e1 * g1a + e2 * g2a + er * drm, gb = e1 * g1b + e2 * g2b + er * drm;
+    a.G[0] = a.G[0] + ga;
+    addG(a, kb, gb);
+    if (VIR) vir_add(a.W, ga + gb, dO, R(-0.5));
 }
 
 // lone pair of i (a pseudo-atom at its carrier O_i) with a bond of j
-template <typename R>
+template <typename R, bool VIR>
 __device__ void item_lb(const Scal<R> &S, const ShortTables &T, const DevState<R> &d, const ShortI<R> &I, int i,
                         int word, ShortAcc<R> &a) {
     const int slot = word >> 5, c = word & 31;
@@ -233,12 +238,14 @@ __device__ void item_lb(const Scal<R> &S, const ShortTables &T, const DevState<R
     }
     R e1, e2, er;
     a.Erep.add(R(0.5) * rep_energy(S.occ * S.nlp, S.rep_c1, S.rep_c2, O1, O2, rr, e1, e2, er));
-    a.G[0] = a.G[0] + e1 * g1c + e2 * g2c;
-    addG(a, 3 + l, e1 * g1l + e2 * g2l + (er / rr) * dm);
+    const V3<R> gc = e1 * g1c + e2 * g2c, gl = e1 * g1l + e2 * g2l + (er / rr) * dm;
+    a.G[0] = a.G[0] + gc;
+    addG(a, 3 + l, gl);
+    if (VIR) vir_add(a.W, gc + gl, dO, R(-0.5));
 }
 
 // lone pair - lone pair, angles toward the other lone pair's position
-template <typename R>
+template <typename R, bool VIR>
 __device__ void item_ll(const Scal<R> &S, const ShortTables &T, const DevState<R> &d, const ShortI<R> &I, int i,
                         int word, ShortAcc<R> &a) {
     const int slot = word >> 5, c = word & 31;
@@ -266,13 +273,16 @@ __device__ void item_ll(const Scal<R> &S, const ShortTables &T, const DevState<R
     R e1, e2, er;
     a.Erep.add(R(0.5) * rep_energy(S.nlp * S.nlp, S.rep_c1, S.rep_c2, O1, O2, rr, e1, e2, er));
     const V3<R> drab = (R(1) / rab) * dAB;
-    a.G[0] = a.G[0] + (e1 * S1 + e2 * S2) * dOdA +
-             (e1 * O1 * (-cval<R>(T.rep_k1[2][2])) + e2 * O2 * (-cval<R>(T.rep_k2[2][2]))) * drab;
-    addG(a, 3 + l1, (e1 * S1 + e2 * S2) * dOdI + (er / rr) * dIJ);
+    const V3<R> go = (e1 * S1 + e2 * S2) * dOdA +
+                     (e1 * O1 * (-cval<R>(T.rep_k1[2][2])) + e2 * O2 * (-cval<R>(T.rep_k2[2][2]))) * drab;
+    const V3<R> gl = (e1 * S1 + e2 * S2) * dOdI + (er / rr) * dIJ;
+    a.G[0] = a.G[0] + go;
+    addG(a, 3 + l1, gl);
+    if (VIR) vir_add(a.W, go + gl, dO, R(-0.5));
 }
 
 // dispersion and exchange-dispersion of point u of i with point v of j
-template <typename R>
+template <typename R, bool VIR>
 __device__ void item_d(const KParams &p, const Scal<R> &S, const ShortTables &T, const DevState<R> &d,
                        const ShortI<R> &I, int i, int word, ShortAcc<R> &a) {
     const int slot = word >> 5, c = word & 31;
@@ -311,14 +321,19 @@ __device__ void item_d(const KParams &p, const Scal<R> &S, const ShortTables &T,
     a.Ed.add(R(0.5) * pref * fsum);
     a.Ex.add(R(0.5) * ex);
     const R dEdr = pref * dfdr - cval<R>(T.xd_k[ku][kv]) * ex;
-    addG(a, u, (dEdr * ri) * dv);
+    const V3<R> gu = (dEdr * ri) * dv;
+    addG(a, u, gu);
+    if (VIR) vir_add(a.W, gu, dO, R(-0.5));
 }
 
 // ---- kernel ------------------------------------------------------------------
 
 // PART 0: exchange-repulsion items (BB, BL, LB, LL); PART 1: dispersion and
 // exchange-dispersion items (D).  Two launches keep each kernel's code small.
-template <typename R, bool PER, int PART>
+// VIR: also the virial, in the translation-invariance form of the pair
+// kernels (see vir_points_out): per item -1/2 (gradient on i's points) (x)
+// dO_ij, plus sum_p G_p (x) off_p at the end.
+template <typename R, bool PER, int PART, bool VIR>
 __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
     __shared__ ShortTables T;
     __shared__ int qbuf[4][SQ_WORDS];
@@ -358,6 +373,8 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
     }
     ShortAcc<R> acc;
     for (int k = 0; k < 5; ++k) acc.G[k] = mk(R(0), R(0), R(0));
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc.W[k] = R(0);
     int h[5] = {0, 0, 0, 0, 0}, t[5] = {0, 0, 0, 0, 0};   // heads and tails: BB, BL, LB, LL, D
     const int nn = d.nnbr[i];
     for (int base = 0;; base += 32) {
@@ -416,26 +433,26 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
             const bool last = flush && stage == s1 - 1;
             if (PART == 1) {
                 while (t[4] - h[4] >= 32 || (last && t[4] > h[4])) {
-                    if (lane < t[4] - h[4]) item_d(p, S, T, d, I, i, q[SQ_D + (h[4] + lane) % SQ_CAPD], acc);
+                    if (lane < t[4] - h[4]) item_d<R, VIR>(p, S, T, d, I, i, q[SQ_D + (h[4] + lane) % SQ_CAPD], acc);
                     h[4] += min(32, t[4] - h[4]);
                 }
                 __syncwarp();
                 continue;
             }
             while (t[0] - h[0] >= 32 || (last && t[0] > h[0])) {
-                if (lane < t[0] - h[0]) item_bb(S, T, d, I, i, q[SQ_BB + (h[0] + lane) % SQ_CAP], acc);
+                if (lane < t[0] - h[0]) item_bb<R, VIR>(S, T, d, I, i, q[SQ_BB + (h[0] + lane) % SQ_CAP], acc);
                 h[0] += min(32, t[0] - h[0]);
             }
             while (t[1] - h[1] >= 32 || (last && t[1] > h[1])) {
-                if (lane < t[1] - h[1]) item_bl(S, T, d, I, i, q[SQ_BL + (h[1] + lane) % SQ_CAP], acc);
+                if (lane < t[1] - h[1]) item_bl<R, VIR>(S, T, d, I, i, q[SQ_BL + (h[1] + lane) % SQ_CAP], acc);
                 h[1] += min(32, t[1] - h[1]);
             }
             while (t[2] - h[2] >= 32 || (last && t[2] > h[2])) {
-                if (lane < t[2] - h[2]) item_lb(S, T, d, I, i, q[SQ_LB + (h[2] + lane) % SQ_CAP], acc);
+                if (lane < t[2] - h[2]) item_lb<R, VIR>(S, T, d, I, i, q[SQ_LB + (h[2] + lane) % SQ_CAP], acc);
                 h[2] += min(32, t[2] - h[2]);
             }
             while (t[3] - h[3] >= 32 || (last && t[3] > h[3])) {
-                if (lane < t[3] - h[3]) item_ll(S, T, d, I, i, q[SQ_LL + (h[3] + lane) % SQ_CAP], acc);
+                if (lane < t[3] - h[3]) item_ll<R, VIR>(S, T, d, I, i, q[SQ_LL + (h[3] + lane) % SQ_CAP], acc);
                 h[3] += min(32, t[3] - h[3]);
             }
             __syncwarp();
@@ -449,6 +466,7 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
     const R s = warp_transpose_sum<R, 15>(vals, reinterpret_cast<R *>(q), lane);
     const int pt = lane / 3;
     if (lane < 15) d.gpt[(i * NP + (pt < 3 ? pt : pt + 2)) * 3 + lane % 3] += double(s);
+    if (VIR) vir_points_out(d, i, I.P, s, acc.W, reinterpret_cast<R *>(q), lane);
     if (PART == 0) {
         const double er_ = warp_sum_acc(acc.Erep);
         if (lane == 0) d.epart[i * NTERM + T_REP] += er_;
@@ -464,12 +482,20 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
 template <typename R>
 void launch_short(const KParams &p, DevState<R> &d, Launch L) {
     const unsigned nb = (p.M + 3) / 4;
-    if (p.periodic) {
-        k_short<R, true, 0><<<nb, 128, 0, L.s>>>(p, d);
-        k_short<R, true, 1><<<nb, 128, 0, L.s>>>(p, d);
+    if (p.vir) {
+        if (p.periodic) {
+            k_short<R, true, 0, true><<<nb, 128, 0, L.s>>>(p, d);
+            k_short<R, true, 1, true><<<nb, 128, 0, L.s>>>(p, d);
+        } else {
+            k_short<R, false, 0, true><<<nb, 128, 0, L.s>>>(p, d);
+            k_short<R, false, 1, true><<<nb, 128, 0, L.s>>>(p, d);
+        }
+    } else if (p.periodic) {
+        k_short<R, true, 0, false><<<nb, 128, 0, L.s>>>(p, d);
+        k_short<R, true, 1, false><<<nb, 128, 0, L.s>>>(p, d);
     } else {
-        k_short<R, false, 0><<<nb, 128, 0, L.s>>>(p, d);
-        k_short<R, false, 1><<<nb, 128, 0, L.s>>>(p, d);
+        k_short<R, false, 0, false><<<nb, 128, 0, L.s>>>(p, d);
+        k_short<R, false, 1, false><<<nb, 128, 0, L.s>>>(p, d);
     }
     count(L, 2);
 }

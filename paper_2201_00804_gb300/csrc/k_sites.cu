@@ -128,6 +128,8 @@ __global__ void __launch_bounds__(128) k_sites(KParams p, DevState<R> d) {
         if (t < 6) d.dvlp[m * 6 + t] = 0.0, d.dvlp_r[m * 6 + t] = 0.0;
         if (t < 3) d.kap[m * 3 + t] = 0.0;
         if (t < NTERM) d.epart[m * NTERM + t] = 0.0, d.epart_r[m * NTERM + t] = 0.0;
+        if (p.vir)
+            for (int k = t; k < 9; k += 8) d.vir[m * 9 + k] = 0.0, d.vir_r[m * 9 + k] = 0.0;
     }
     // largest point distance from its O (list margin): one atomic per warp
     const int e = __reduce_max_sync(0xffffffffu, __float_as_int(ext));

@@ -142,6 +142,97 @@ void launch_convolve(const KParams &p, DevState<R> &d, void *cgrid, int ngrid, i
     count(L);
 }
 
+// Convolution with the k-space virial sums.  E_rec = sum over the full
+// spectrum of e(k) = G(k) (...); a half-spectrum point with 0 < kz < K2/2
+// also stands for its conjugate -k (same e, folded vector below).  Under the
+// strain the reciprocal vectors m and the volume change, dG/d eps_ab =
+// G [-delta_ab + 2 (1/m^2 + pi^2/alpha^2) m_a m_b].  Per block: sum e, and
+// sum e f m_a m_b (xx yy zz xy xz yz), f = 2 (1/m^2 + pi^2/alpha^2).
+// pass 0: the permanent spectrum, e = 1/2 |Q_p|^2 G; it is kept in qp.
+// pass 1: grids of the induced dipoles (Q_m) and the lambda charges (Q_l),
+//         e = G [Re(Q_p^* (Q_m + Q_l)) + 1/2 |Q_m|^2].
+template <typename R, typename C>
+__global__ void __launch_bounds__(256) k_convolve_vir(KParams p, const R *infl, C *cg, C *qp, double *part, int pass) {
+    const int K0 = p.K[0], K1 = p.K[1], K2 = p.K[2], nz = K2 / 2 + 1;
+    const size_t nh = (size_t)K0 * K1 * nz;
+    const double pa2 = M_PI * M_PI / (p.alpha * p.alpha);
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < nh; t += (size_t)gridDim.x * blockDim.x) {
+        const int kz = (int)(t % nz), ky = (int)((t / nz) % K1), kx = (int)(t / ((size_t)nz * K1));
+        const double fx = (kx <= K0 / 2 ? kx : kx - K0) * p.ibox[0];
+        const double fy = (ky <= K1 / 2 ? ky : ky - K1) * p.ibox[1];
+        const double fz = kz * p.ibox[2];
+        const double m2 = fx * fx + fy * fy + fz * fz;
+        const R g = infl[t];
+        C a = cg[t];
+        double e;
+        if (pass == 0) {
+            e = 0.5 * (double)g * ((double)a.x * a.x + (double)a.y * a.y);
+            qp[t] = a;
+        } else {
+            C b = cg[t + nh];
+            const C q = qp[t];
+            e = (double)g * ((double)q.x * ((double)a.x + b.x) + (double)q.y * ((double)a.y + b.y) +
+                             0.5 * ((double)a.x * a.x + (double)a.y * a.y));
+            b.x *= g;
+            b.y *= g;
+            cg[t + nh] = b;
+        }
+        a.x *= g;
+        a.y *= g;
+        cg[t] = a;
+        if (m2 > 0.0) {
+            const double f = 2.0 * (1.0 / m2 + pa2) * e;
+            acc[0] += e;
+            acc[1] += f * fx * fx;
+            acc[2] += f * fy * fy;
+            acc[3] += f * fz * fz;
+            acc[4] += f * fx * fy;
+            acc[5] += f * fx * fz;
+            acc[6] += f * fy * fz;
+            if (!(kz == 0 || (K2 % 2 == 0 && kz == K2 / 2))) {
+                // the conjugate point -k of the full spectrum, same e; its
+                // folded vector flips every component except on a Nyquist
+                // row (k = K/2 folds onto itself)
+                const double gx = 2 * kx == K0 ? fx : -fx, gy = 2 * ky == K1 ? fy : -fy, gz = -fz;
+                acc[0] += e;
+                acc[1] += f * gx * gx;
+                acc[2] += f * gy * gy;
+                acc[3] += f * gz * gz;
+                acc[4] += f * gx * gy;
+                acc[5] += f * gx * gz;
+                acc[6] += f * gy * gz;
+            }
+        }
+    }
+    __shared__ double sh[8][7];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[wp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        double v = 0;
+        for (int k = 0; k < 8; ++k) v += sh[k][threadIdx.x];
+        part[((size_t)pass * VK_BLOCKS + blockIdx.x) * 8 + threadIdx.x] = v;
+    }
+}
+
+template <typename R>
+void launch_convolve_vir(const KParams &p, DevState<R> &d, int pass, Launch L) {
+    if (sizeof(R) == 4)
+        k_convolve_vir<float, cufftComplex><<<VK_BLOCKS, 256, 0, L.s>>>(
+            p, (const float *)d.inflR, (cufftComplex *)d.cgrid, (cufftComplex *)d.qhat_p, d.virk, pass);
+    else
+        k_convolve_vir<double, cufftDoubleComplex><<<VK_BLOCKS, 256, 0, L.s>>>(
+            p, (const double *)d.inflR, (cufftDoubleComplex *)d.cgrid, (cufftDoubleComplex *)d.qhat_p, d.virk, pass);
+    count(L);
+}
+
 // Influence function G(m) = ke exp(-pi^2 m~^2/alpha^2) B(m) / (pi V m~^2), G(0) = 0, with the
 // Euler-spline moduli B(m) = prod_d |b_d(m_d)|^2; a vanishing modulus denominator
 // (m = K/2 for odd orders) takes the mean of its neighbours.
@@ -316,6 +407,20 @@ __device__ inline R mp_energy(const Mp<R> &m, const Derivs<R> &D) {
     return m.q * D.phi + m.mu.x * D.d1[0] + m.mu.y * D.d1[1] + m.mu.z * D.d1[2] + symdd(m.th, d2) / R(3);
 }
 
+// Strain derivative of a multipole's reciprocal energy through the
+// reciprocal vectors at fixed Cartesian multipoles: entry (a, b) of
+// d1_a mu_b + (2/3) sum_c d2_ac Theta_cb (its negative adds to dE/d eps_ab;
+// the Ewald structure factor's k-dependence of mu.k and k.Theta.k)
+template <typename R>
+__device__ inline R mp_strain(const Mp<R> &m, const Derivs<R> &D, int k) {
+    const int a = k / 3, b = k % 3;
+    const R th[6] = {m.th.xx, m.th.yy, m.th.zz, m.th.xy, m.th.xz, m.th.yz};
+    const R mu[3] = {m.mu.x, m.mu.y, m.mu.z};
+    R t = R(0);
+    for (int c = 0; c < 3; ++c) t += sym_at(D.d2, a, c) * sym_at(th, c, b);
+    return D.d1[a] * mu[b] + R(2.0 / 3.0) * t;
+}
+
 constexpr int GW = 8;   // warps (points) per block of the gather kernels
 
 // Permanent pass: one warp per point (7 per molecule).  Sites: energy,
@@ -341,6 +446,10 @@ __global__ void __launch_bounds__(32 * GW) k_gather_perm(KParams p, DevState<R> 
             if (pt < 3) d.d2rec[m * 18 + pt * 6 + lane - 3] = (double)D.d2[lane - 3];
         } else if (lane == 9) {
             atomicAdd(&d.epart[m * NTERM + T_ELEC], 0.5 * (double)mp_energy(mp, D));
+        }
+        if (p.vir) {
+            if (lane >= 10 && lane < 19) atomicAdd(&d.vir[m * 9 + lane - 10], -(double)mp_strain(mp, D, lane - 10));
+            else if (lane >= 19 && lane < 22 && pt < 3) d.vphi[m * 9 + pt * 3 + lane - 19] = D.d1[lane - 19];
         }
     } else {
         warp_gather<R, 1>(p, d, d.grid, m, pt, lane, buf[w], D);
@@ -448,6 +557,13 @@ __global__ void __launch_bounds__(32 * GW) k_gather_polforce(KParams p, DevState
         d.gmu[(m * NS + pt) * 3 + lane] += (double)S.d1[lane];
     } else if (lane < 9) {
         d.gth[(m * NS + pt) * 6 + lane - 3] += (double)S.d2[lane - 3] / 3.0;
+    } else if (p.vir && lane >= 10 && lane < 19) {
+        // permanent multipoles in the induced + lambda potential; induced
+        // dipole in the permanent + induced potential
+        const int k = lane - 10, a = k / 3, b = k % 3;
+        double c = (double)mp_strain(mp, S, k);
+        if (pt < 3) c += ((double)d.vphi[m * 9 + pt * 3 + a] + (double)A.d1[a]) * d.mu[m * 9 + pt * 3 + b];
+        atomicAdd(&d.vir[m * 9 + k], -c);
     }
 }
 
@@ -464,7 +580,8 @@ void launch_gather_polforce(const KParams &p, DevState<R> &d, Launch L) {
     template void launch_influence_copy<R>(const KParams &, DevState<R> &, Launch);                      \
     template void launch_gather_perm<R>(const KParams &, DevState<R> &, Launch);                         \
     template void launch_gather_field<R>(const KParams &, DevState<R> &, double *, Launch);              \
-    template void launch_gather_polforce<R>(const KParams &, DevState<R> &, Launch);
+    template void launch_gather_polforce<R>(const KParams &, DevState<R> &, Launch);                     \
+    template void launch_convolve_vir<R>(const KParams &, DevState<R> &, int, Launch);
 INST(float)
 INST(double)
 

@@ -19,6 +19,7 @@ constexpr int MAXN = 384;      // neighbour slots per molecule
 constexpr int NTERM = 7;       // elec pen rep disp xdisp pol ct
 enum { T_ELEC = 0, T_PEN, T_REP, T_DISP, T_XDISP, T_POL, T_CT };
 constexpr int ORDER = 5;       // B-spline order of the SPME
+constexpr int VK_BLOCKS = 304;  // blocks of the virial convolution (fixed, so its partial sums have a fixed layout)
 
 // error flags (bitwise, device side)
 enum { F_CUTOFF = 1, F_NEIGHBOR = 2, F_CTDEN = 4, F_NAN = 8, F_NOCONV = 16 };
@@ -44,6 +45,7 @@ struct KParams {
     int periodic;
     int n_cl;              // clusters (1: one system)
     int tls;               // T-pair list slots per polarizable atom: 3 x the most neighbours a molecule can have
+    int vir;               // 1: this evaluation also accumulates the virial
     double box[3];
     double ibox[3];        // 1 / box
     double rc, rc2;
@@ -169,6 +171,13 @@ struct DevState {
     double *lam;        // M*2 dE_ct/dV_lp
     double *kap;        // M*3 dE_ct/dV_int
     double *epart;      // M*NTERM per-molecule energy partials
+    // Virial: per-molecule dE/d eps (row-major 3x3) for the affine strain
+    // x -> (I + eps) x of atoms and cell, and the reciprocal-space parts
+    double *vir;        // M*9
+    double *vir_r;      // M*9 (reciprocal chain)
+    double *virk;       // 2 passes x VK_BLOCKS x 8: k-space sums per convolution block
+    void *qhat_p;       // K0*K1*(K2/2+1) complex: spectrum of the permanent grid (kept for the force pass)
+    R *vphi;            // M*9 gradient of the reciprocal permanent potential at O, H1, H2
     // Accumulators of the reciprocal-space chain (SPME and intramolecular
     // Ewald corrections), which runs on a second stream concurrently with the
     // real-space kernels; same layouts as the arrays above, merged where used.
@@ -252,6 +261,18 @@ __device__ inline V3<R> symv(const Sym<R> &t, V3<R> v) {
 template <typename R>
 __device__ inline R symdd(const Sym<R> &a, const Sym<R> &b) {
     return a.xx * b.xx + a.yy * b.yy + a.zz * b.zz + R(2) * (a.xy * b.xy + a.xz * b.xz + a.yz * b.yz);
+}
+
+// Virial accumulation: W[3a + b] += c g_a x_b (g a gradient, x a displacement)
+template <typename R>
+__device__ inline void vir_add(R (&W)[9], V3<R> g, V3<R> x, R c) {
+    const R ga[3] = {c * g.x, c * g.y, c * g.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        W[3 * a] += ga[a] * x.x;
+        W[3 * a + 1] += ga[a] * x.y;
+        W[3 * a + 2] += ga[a] * x.z;
+    }
 }
 
 // A point multipole: charge, dipole, traceless quadrupole (1/3 convention:
@@ -557,6 +578,27 @@ __device__ inline R warp_transpose_sum(const R (&v)[NV], R *buf, int lane) {
     return s0 + s1;
 }
 
+// Virial epilogue of the molecule-pair kernels (translation-invariance form):
+// lanes 0-14 hold the warp-reduced gradients g of i's points O, H1, H2, LP1,
+// LP2 (offsets P from O_i); adds sum_p G_p (x) off_p and the warp sum of the
+// per-lane W to vir[i].
+template <typename R>
+__device__ inline void vir_points_out(const DevState<R> &d, int i, const V3<R> (&P)[5], R g, const R (&W)[9],
+                                      R *buf, int lane) {
+    __syncwarp();
+    if (lane < 15) buf[lane] = g;
+    __syncwarp();
+    R wo = R(0);
+    if (lane < 9) {
+        const int a = lane / 3, b = lane % 3;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) wo += buf[k * 3 + a] * (b == 0 ? P[k].x : (b == 1 ? P[k].y : P[k].z));
+    }
+    __syncwarp();
+    const R wv = warp_transpose_sum<R, 9>(W, buf, lane);
+    if (lane < 9) d.vir[i * 9 + lane] += double(wo) + double(wv);
+}
+
 // position of point k of molecule m relative to its O (points: 5 sites, 2 lone pairs)
 template <typename R>
 __device__ inline V3<R> my_pt(const DevState<R> &d, int i, int pt) {
@@ -761,6 +803,7 @@ inline DevState<R> rec_view(const DevState<R> &d) {
     r.vlp = d.vlp_r;
     r.dvlp = d.dvlp_r;
     r.epart = d.epart_r;
+    r.vir = d.vir_r;
     return r;
 }
 
@@ -782,6 +825,10 @@ template <typename R> void launch_pcg_first(const KParams &p, DevState<R> &d, La
 template <typename R> void launch_pcg_step(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_pol_energy(const KParams &p, DevState<R> &d, Launch L);
 void launch_energy_reduce(int M, const double *epart, const double *epart_r, double *out, Launch L);
+// k-space virial sums of one convolution pass (0: permanent, 1: force pass) fused with the convolution
+template <typename R> void launch_convolve_vir(const KParams &p, DevState<R> &d, int pass, Launch L);
+// out[9] = -dE/d eps summed over molecules, both chains and the k-space partials
+template <typename R> void launch_virial_total(const KParams &p, DevState<R> &d, double *out, Launch L);
 template <typename R> void launch_cluster_energy(const KParams &p, DevState<R> &d, double *out, Launch L);
 void launch_begin(double *scal, int *flags, double tol_D, Launch L);
 void launch_pcg_check(const double *scal, int *flags, Launch L);

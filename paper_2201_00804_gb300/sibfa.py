@@ -194,13 +194,20 @@ def sibfa_create(params: dict, mp_local: np.ndarray, *, periodic: bool, box=None
     return out
 
 
-def sibfa_energy_forces(ctx, pos, forces=None, box=None):
+def sibfa_energy_forces(ctx, pos, forces=None, box=None, virial=None):
     """One evaluation; returns a dict of energy terms (kcal/mol).  forces (same
-    shape as pos) is filled in place when given."""
+    shape as pos) is filled in place when given; virial (a host float64 array
+    of 9) receives W_ab = -dE/d eps_ab (row-major) when given."""
     lib = load_library()
     e = sibfa_energy_terms()
-    st = lib.sibfa_energy_forces(ctx, _ptr(pos), _ptr(box), C.byref(e), _ptr(forces), None)
+    vir = None
+    if virial is not None:
+        vir = (C.c_double * 9)()
+    st = lib.sibfa_energy_forces(ctx, _ptr(pos), _ptr(box), C.byref(e), _ptr(forces),
+                                 C.addressof(vir) if vir is not None else None)
     _check(lib, ctx, st)
+    if virial is not None:
+        virial[...] = np.frombuffer(vir, dtype=np.float64).reshape(np.shape(virial))
     return {n: getattr(e, n) for n in TERMS}
 
 
