@@ -577,23 +577,42 @@ void launch_finalize(const KParams &p, DevState<R> &d, double *forces_out, Launc
 }
 
 // energy totals: out[k] = sum_m epart[m*NTERM + k], out[NTERM] = total (fixed order)
-__global__ void k_energy_reduce(int M, const double *epart, const double *epart_r, double *out) {
-    __shared__ double sh[32];
-    double tot = 0;
+// One pass: every thread sums all terms of its molecules (independent
+// chains), then one shared-memory tree per term; the order is fixed.
+__global__ void __launch_bounds__(1024) k_energy_reduce(int M, const double *epart, const double *epart_r,
+                                                        double *out) {
+    __shared__ double sh[32][NTERM];
+    double v[NTERM];
+#pragma unroll
+    for (int k = 0; k < NTERM; ++k) v[k] = 0.0;
+    for (int m = threadIdx.x; m < M; m += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NTERM; ++k) v[k] += epart[m * NTERM + k] + epart_r[m * NTERM + k];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
     for (int k = 0; k < NTERM; ++k) {
-        double v = 0;
-        for (int m = threadIdx.x; m < M; m += blockDim.x) v += epart[m * NTERM + k] + epart_r[m * NTERM + k];
-        v = block_sum(v, sh);
-        if (threadIdx.x == 0) {
-            out[k] = v;
-            tot += v;
-        }
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (l == 0) sh[w][k] = x;
     }
-    if (threadIdx.x == 0) out[NTERM] = tot;
+    __syncthreads();
+    if (threadIdx.x < NTERM) {
+        double x = 0.0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) x += sh[j][threadIdx.x];
+        out[threadIdx.x] = x;
+        sh[0][threadIdx.x] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < NTERM; ++k) tot += sh[0][k];
+        out[NTERM] = tot;
+    }
 }
 
 void launch_energy_reduce(int M, const double *epart, const double *epart_r, double *out, Launch L) {
-    k_energy_reduce<<<1, 512, 0, L.s>>>(M, epart, epart_r, out);
+    k_energy_reduce<<<1, 1024, 0, L.s>>>(M, epart, epart_r, out);
     count(L);
 }
 
