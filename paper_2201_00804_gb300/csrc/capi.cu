@@ -26,6 +26,12 @@ struct sibfa_ctx {
     cudaStream_t s = nullptr;    // the library's own work stream (non-blocking)
     cudaStream_t s2 = nullptr;   // reciprocal-space chain, forked from s and joined back
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // short-range kernels (lowest priority), forked after the neighbour list
+    // and joined before the chain rule: they fill the SMs that the permanent
+    // pass's tail and the latency-bound polarization solve leave idle
+    cudaStream_t s3 = nullptr;
+    cudaEvent_t ev_fork3 = nullptr, ev_join3 = nullptr;
+    bool short_pending = false;
     cudaStream_t us = nullptr;   // the caller's stream (ordering only)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     // polarization iterations as one CUDA graph with a device-side while loop
@@ -172,6 +178,7 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.vir_r, M * 9);
     AL(d.vphi, M * 9);
     AL(d.gpt_r, M * NP * 3);
+    AL(d.gpt_s, M * NP * 3);
     AL(d.gmu_r, M * NS * 3);
     AL(d.gth_r, M * NS * 6);
     AL(d.efield_r, M * 9);
@@ -344,6 +351,19 @@ sibfa_status fork_rec(sibfa_ctx *ctx) {
     CK(cudaStreamWaitEvent(ctx->s2, ctx->ev_fork, 0));
     return SIBFA_OK;
 }
+sibfa_status fork_short(sibfa_ctx *ctx) {
+    CK(cudaEventRecord(ctx->ev_fork3, ctx->s));
+    CK(cudaStreamWaitEvent(ctx->s3, ctx->ev_fork3, 0));
+    return SIBFA_OK;
+}
+sibfa_status join_short(sibfa_ctx *ctx) {
+    if (!ctx->short_pending) return SIBFA_OK;
+    ctx->short_pending = false;
+    CK(cudaEventRecord(ctx->ev_join3, ctx->s3));
+    CK(cudaStreamWaitEvent(ctx->s, ctx->ev_join3, 0));
+    return SIBFA_OK;
+}
+
 sibfa_status join_rec(sibfa_ctx *ctx) {
     CK(cudaEventRecord(ctx->ev_join, ctx->s2));
     CK(cudaStreamWaitEvent(ctx->s, ctx->ev_join, 0));
@@ -504,7 +524,18 @@ sibfa_status solve(sibfa_ctx *ctx, DevState<R> &d, double tol, Launch L) {
 
 // One evaluation on the positions already in d.pos.
 template <typename R>
+sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, double tol);
+
+// One evaluation; the short-range stream is joined back on every path.
+template <typename R>
 sibfa_status evaluate(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, double tol) {
+    const sibfa_status st = evaluate_impl<R>(ctx, want_forces, dipoles_only, tol);
+    const sibfa_status sj = join_short(ctx);
+    return st ? st : sj;
+}
+
+template <typename R>
+sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, double tol) {
     DevState<R> &d = state<R>(ctx);
     DevState<R> dr = rec_view(d);   // accumulators of the reciprocal chain
     const KParams &p = ctx->kp;
@@ -529,8 +560,21 @@ sibfa_status evaluate(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, doubl
         launch_intra_perm(p, dr, L2);
     }
     { Phase ph(ctx, "neighbors");  launch_neighbors(p, d, ctx->ncell, L); }
+    // Short-range terms on the third, lowest-priority stream beside the
+    // permanent pass and the solve (which is latency-bound and leaves SMs
+    // idle): their short blocks fill in behind the other streams' work.  They
+    // write their own gradient array and are joined before the chain rule.
+    // The virial variant runs in order on the main stream.
+    const bool bg_short = !dipoles_only && !p.vir;
+    if (bg_short) {
+        if ((st = fork_short(ctx))) return st;
+        ctx->short_pending = true;
+        Phase ph(ctx, "short", ctx->s3);
+        DevState<R> ds = short_view(d);
+        launch_short(p, ds, Launch{ctx->s3, &ctx->launches});
+    }
     { Phase ph(ctx, "real_perm");  launch_real_perm(p, d, L); }
-    if (!dipoles_only) { Phase ph(ctx, "short");  launch_short(p, d, L); }
+    if (!dipoles_only && !bg_short) { Phase ph(ctx, "short");  launch_short(p, d, L); }
     if (p.periodic) {
         if ((st = join_rec(ctx))) return st;
         launch_merge_rec(p, d, L);
@@ -566,8 +610,10 @@ sibfa_status evaluate(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, doubl
             sibfa_status sj = join_rec(ctx);
             if (sj) return sj;
         }
+        if ((st = join_short(ctx))) return st;
         { Phase ph(ctx, "finalize");  launch_finalize(p, d, ctx->d_forces, L); }
     }
+    if ((st = join_short(ctx))) return st;
     if (p.n_cl > 1) launch_cluster_energy(p, d, ctx->d_energy, L);
     else launch_energy_reduce(p.M, d.epart, d.epart_r, ctx->d_energy, L);
     return st_solve;
@@ -829,10 +875,15 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
     int prio_lo = 0, prio_hi = 0;
     cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
     // the reciprocal chain is a sequence of small latency-bound kernels: it
-    // gets the higher priority so that its blocks start ahead of the large
-    // real-space grids that run beside it
-    if (cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking) != cudaSuccess ||
+    // gets the highest priority so that its blocks start ahead of the large
+    // real-space grids that run beside it; the short-range kernels the
+    // lowest, so that they only take what the other two streams leave
+    const int prio_mid = prio_hi < prio_lo ? prio_hi + 1 : prio_hi;
+    if (cudaStreamCreateWithPriority(&ctx->s, cudaStreamNonBlocking, prio_mid) != cudaSuccess ||
         cudaStreamCreateWithPriority(&ctx->s2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ctx->s3, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork3, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join3, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -1038,7 +1089,10 @@ void sibfa_destroy(sibfa_ctx *ctx) {
     if (!ctx) return;
     if (ctx->s) cudaStreamSynchronize(ctx->s);
     if (ctx->s2) cudaStreamSynchronize(ctx->s2);
+    if (ctx->s3) cudaStreamSynchronize(ctx->s3);
     if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+    if (ctx->ev_fork3) cudaEventDestroy(ctx->ev_fork3);
+    if (ctx->ev_join3) cudaEventDestroy(ctx->ev_join3);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -1060,6 +1114,7 @@ void sibfa_destroy(sibfa_ctx *ctx) {
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     if (ctx->s) cudaStreamDestroy(ctx->s);
     if (ctx->s2) cudaStreamDestroy(ctx->s2);
+    if (ctx->s3) cudaStreamDestroy(ctx->s3);
     delete ctx;
 }
 

@@ -318,7 +318,8 @@ __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1
     const Scal<R> &S = sc<R>(p);
     const R cs = S.cs_lp, cp = S.cp_lp, t = S.ct_t, mm = S.ct_m, n = S.nlp;
     const V3<R> v1 = a1 - c, v2 = a2 - c, u = lp - c;
-    const R r1 = sqrt_(dot(v1, v1)), r2 = sqrt_(dot(v2, v2));
+    const R q1 = dot(v1, v1), q2 = dot(v2, v2);
+    const R ir1 = rsqrt_(q1), ir2 = rsqrt_(q2), r1 = q1 * ir1, r2 = q2 * ir2;
     V3<R> du1, dv1, du2, dv2;
     const R ca = cosv(u, v1, du1, dv1);
     const R cb = cosv(u, v2, du2, dv2);
@@ -329,7 +330,7 @@ __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1
     const R D = e1 - e2;
     const R dE = S.ct_ae + V - S.ct_ah;
     if (!(dE > R(0))) atomicOr(flags, F_CTDEN);
-    const R idE = R(1) / dE;
+    const R idE = rcp_(dE);
     o.E = -n * D * D * idE;
     const R gD = R(-2) * n * D * idE;
     o.dV = gD * (-E1 * K1 + E2 * K2) + n * D * D * idE * idE;
@@ -337,7 +338,7 @@ __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1
     o.dVi2 = -gD * E2 * K2;
     const R dr1 = gD * (-ek1 * e1), dr2 = gD * (ek2 * e2);
     const R dca = gD * E1 * (Vi1 - V) * cp * mm, dcb = -gD * E2 * (Vi2 - V) * cp * mm;
-    const V3<R> n1 = (R(1) / r1) * v1, n2 = (R(1) / r2) * v2;
+    const V3<R> n1 = ir1 * v1, n2 = ir2 * v2;
     o.glp = dca * du1 + dcb * du2;
     o.ga1 = dr1 * n1 + dca * dv1;
     o.ga2 = dr2 * n2 + dcb * dv2;

@@ -318,7 +318,9 @@ void launch_pcg_step(const KParams &p, DevState<R> &d, Launch L) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_pcg_step<R>, PB, 0);
         if (ps < 1) ps = 1;
     }
-    const unsigned grid = (unsigned)std::min<long long>(nblk(p.M * 9), (long long)ps * n_sm);
+    // at most two blocks per SM: the grid must be co-resident while the
+    // short-range kernels occupy part of every SM on their own stream
+    const unsigned grid = (unsigned)std::min<long long>(nblk(p.M * 9), (long long)std::min(ps, 2) * n_sm);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(PB);
@@ -399,7 +401,11 @@ __global__ void __launch_bounds__(128) k_finalize(KParams p, DevState<R> d, doub
         auto sum2 = [&](const double *a, const double *b, int o) {
             return mk(R(a[o] + b[o]), R(a[o + 1] + b[o + 1]), R(a[o + 2] + b[o + 2]));
         };
-        auto gpt = [&](int k) { return sum2(d.gpt, d.gpt_r, (m * NP + k) * 3); };
+        auto gpt = [&](int k) {
+            const int o = (m * NP + k) * 3;
+            return mk(R(d.gpt[o] + d.gpt_r[o] + d.gpt_s[o]), R(d.gpt[o + 1] + d.gpt_r[o + 1] + d.gpt_s[o + 1]),
+                      R(d.gpt[o + 2] + d.gpt_r[o + 2] + d.gpt_s[o + 2]));
+        };
         // lone-pair point gradient including the charge-transfer dependence through its potential
         auto glp = [&](int l) {
             return gpt(5 + l) + R(d.lam[m * 2 + l]) * sum2(d.dvlp, d.dvlp_r, (m * 2 + l) * 3);

@@ -39,7 +39,13 @@ template <typename R>
 struct RepAtom {
     R cs, cp, g, cf;
     int kind;   // 0 = O, 1 = H, 2 = lone pair (selects the pair-type exponent coefficients)
+    R sg;       // sqrt(g cf): the pair prefactor sqrt(g_a g_b cf_a cf_b) is sg_a sg_b
 };
+
+template <typename R>
+__device__ inline RepAtom<R> rep_atom(R cs, R cp, R g, R cf, int kind) {
+    return {cs, cp, g, cf, kind, sqrt_(g * cf)};
+}
 
 // Pair-type coefficient tables copied to shared memory: items of one round
 // mix pair types, and divergent indices into the parameter bank serialise.
@@ -56,23 +62,23 @@ __device__ inline void rep_pair_term(V3<R> x, V3<R> xp, const RepAtom<R> &ai, V3
     V3<R> gx, gxp;
     const R O = overlap_i(x, xp, y, uy, ai.cs * aj.cs, aj.cs * ai.cp * f, ai.cs * aj.cp * f, pp * ai.cp * aj.cp, gx, gxp);
     const V3<R> v = x - y;
-    const R rr = sqrt_(dot(v, v));
+    const R vv = dot(v, v), irr = rsqrt_(vv), rr = vv * irr;
     const KParams::Coef &k1 = T.rep_k1[ai.kind][aj.kind], &k2 = T.rep_k2[ai.kind][aj.kind];
-    const R M = sqrt_(ai.g * aj.g * ai.cf * aj.cf);
+    const R M = ai.sg * aj.sg;
     const R S1 = M * exp_(-mulc(rr, k1)), S2 = M * exp_(-mulc(rr, k2));
     O1 += O * S1;
     O2 += O * S2;
-    const V3<R> drdx = (R(1) / rr) * v;
+    const V3<R> drdx = irr * v;
     g1x = S1 * gx + (O * S1 * (-cval<R>(k1))) * drdx;
     g2x = S2 * gx + (O * S2 * (-cval<R>(k2))) * drdx;
     g1xp = S1 * gxp;
     g2xp = S2 * gxp;
 }
 
-// E = pref (C1 O1^2 / r + C2 O2^2 / r^2): returns E and dE/dO1, dE/dO2, dE/dr.
+// E = pref (C1 O1^2 / r + C2 O2^2 / r^2) from ri = 1/r: returns E and dE/dO1,
+// dE/dO2, dE/dr.
 template <typename R>
-__device__ inline R rep_energy(R pref, R C1, R C2, R O1, R O2, R r, R &e1, R &e2, R &er) {
-    const R ri = R(1) / r;
+__device__ inline R rep_energy(R pref, R C1, R C2, R O1, R O2, R ri, R &e1, R &e2, R &er) {
     e1 = pref * C1 * R(2) * O1 * ri;
     e2 = pref * C2 * R(2) * O2 * ri * ri;
     er = pref * (-C1 * O1 * O1 * ri * ri - R(2) * C2 * O2 * O2 * ri * ri * ri);
@@ -129,8 +135,8 @@ __device__ inline R qcharge(const DevState<R> &d, int j, int k) { return d.gmp[(
 template <typename R>
 __device__ inline RepAtom<R> atom_j(const Scal<R> &S, const DevState<R> &d, int j, int k) {
     const R q = qcharge(d, j, k);
-    if (k == 0) return {S.cs_o, S.cp_o, S.g_o, R(1) - q * S.inv_nval_o, 0};
-    return {S.cs_h, S.cp_h, S.g_h, R(1) - q * S.inv_nval_h, 1};
+    if (k == 0) return rep_atom(S.cs_o, S.cp_o, S.g_o, R(1) - q * S.inv_nval_o, 0);
+    return rep_atom(S.cs_h, S.cp_h, S.g_h, R(1) - q * S.inv_nval_h, 1);
 }
 
 template <typename R>
@@ -155,7 +161,7 @@ __device__ void item_bb(const Scal<R> &S, const ShortTables &T, const DevState<R
     const V3<R> Q0 = dO, Qc = qpt(d, j, dO, kc);
     const RepAtom<R> AjO = atom_j(S, d, j, 0), Ajc = atom_j(S, d, j, kc);
     const V3<R> dm = R(0.5) * (P0 + Pb) - R(0.5) * (Q0 + Qc);
-    const R rm = sqrt_(dot(dm, dm));
+    const R irm = rsqrt_(dot(dm, dm));
     R O1 = 0, O2 = 0;
     const V3<R> z = mk(R(0), R(0), R(0));
     V3<R> g1a = z, g1b = z, g2a = z, g2b = z;   // gradients at O_i (a) and H_kb (b)
@@ -169,8 +175,8 @@ __device__ void item_bb(const Scal<R> &S, const ShortTables &T, const DevState<R
         else { g1b = g1b + t1x; g2b = g2b + t2x; g1a = g1a + t1xp; g2a = g2a + t2xp; }
     }
     R e1, e2, er;
-    a.Erep.add(R(0.5) * rep_energy(S.occ * S.occ, S.rep_c1, S.rep_c2, O1, O2, rm, e1, e2, er));
-    const V3<R> drm = (R(0.5) / rm) * dm;
+    a.Erep.add(R(0.5) * rep_energy(S.occ * S.occ, S.rep_c1, S.rep_c2, O1, O2, irm, e1, e2, er));
+    const V3<R> drm = (R(0.5) * irm) * dm;
     const V3<R> ga = e1 * g1a + e2 * g2a + er * drm, gb = e1 * g1b + e2 * g2b + er * drm;
     a.G[0] = a.G[0] + ga;
     addG(a, kb, gb);
@@ -188,9 +194,9 @@ __device__ void item_bl(const Scal<R> &S, const ShortTables &T, const DevState<R
     const V3<R> P0 = I.P[0], Pb = kb == 1 ? I.P[1] : I.P[2];
     const RepAtom<R> Ab = kb == 1 ? I.A[1] : I.A[2];
     const V3<R> Ql = qpt(d, j, dO, 3 + l);
-    const RepAtom<R> Alp = {S.cs_lp, S.cp_lp, S.g_o, R(1) - S.nlp * S.inv_nval_o, 2};
+    const RepAtom<R> Alp = rep_atom(S.cs_lp, S.cp_lp, S.g_o, R(1) - S.nlp * S.inv_nval_o, 2);
     const V3<R> dm = R(0.5) * (P0 + Pb) - Ql;
-    const R rr = sqrt_(dot(dm, dm));
+    const R irr = rsqrt_(dot(dm, dm));
     R O1 = 0, O2 = 0;
     const V3<R> z = mk(R(0), R(0), R(0));
     V3<R> g1a = z, g1b = z, g2a = z, g2b = z;
@@ -203,8 +209,8 @@ __device__ void item_bl(const Scal<R> &S, const ShortTables &T, const DevState<R
         else { g1b = g1b + t1x; g2b = g2b + t2x; g1a = g1a + t1xp; g2a = g2a + t2xp; }
     }
     R e1, e2, er;
-    a.Erep.add(R(0.5) * rep_energy(S.occ * S.nlp, S.rep_c1, S.rep_c2, O1, O2, rr, e1, e2, er));
-    const V3<R> drm = (R(0.5) / rr) * dm;
+    a.Erep.add(R(0.5) * rep_energy(S.occ * S.nlp, S.rep_c1, S.rep_c2, O1, O2, irr, e1, e2, er));
+    const V3<R> drm = (R(0.5) * irr) * dm;
     const V3<R> ga = e1 * g1a + e2 * g2a + er * drm, gb = e1 * g1b + e2 * g2b + er * drm;
     a.G[0] = a.G[0] + ga;
     addG(a, kb, gb);
@@ -223,9 +229,9 @@ __device__ void item_lb(const Scal<R> &S, const ShortTables &T, const DevState<R
     const V3<R> P0 = I.P[0], Pl = l ? I.P[4] : I.P[3];
     const V3<R> Q0 = dO, Qc = qpt(d, j, dO, kc);
     const RepAtom<R> AjO = atom_j(S, d, j, 0), Ajc = atom_j(S, d, j, kc);
-    const RepAtom<R> Alp = {S.cs_lp, S.cp_lp, S.g_o, R(1) - S.nlp * S.inv_nval_o, 2};
+    const RepAtom<R> Alp = rep_atom(S.cs_lp, S.cp_lp, S.g_o, R(1) - S.nlp * S.inv_nval_o, 2);
     const V3<R> dm = Pl - R(0.5) * (Q0 + Qc);
-    const R rr = sqrt_(dot(dm, dm));
+    const R irr = rsqrt_(dot(dm, dm));
     R O1 = 0, O2 = 0;
     const V3<R> z = mk(R(0), R(0), R(0));
     V3<R> g1c = z, g1l = z, g2c = z, g2l = z;
@@ -237,8 +243,8 @@ __device__ void item_lb(const Scal<R> &S, const ShortTables &T, const DevState<R
         g1c = g1c + t1x; g2c = g2c + t2x; g1l = g1l + t1xp; g2l = g2l + t2xp;
     }
     R e1, e2, er;
-    a.Erep.add(R(0.5) * rep_energy(S.occ * S.nlp, S.rep_c1, S.rep_c2, O1, O2, rr, e1, e2, er));
-    const V3<R> gc = e1 * g1c + e2 * g2c, gl = e1 * g1l + e2 * g2l + (er / rr) * dm;
+    a.Erep.add(R(0.5) * rep_energy(S.occ * S.nlp, S.rep_c1, S.rep_c2, O1, O2, irr, e1, e2, er));
+    const V3<R> gc = e1 * g1c + e2 * g2c, gl = e1 * g1l + e2 * g2l + (er * irr) * dm;
     a.G[0] = a.G[0] + gc;
     addG(a, 3 + l, gl);
     if (VIR) vir_add(a.W, gc + gl, dO, R(-0.5));
@@ -256,7 +262,7 @@ __device__ void item_ll(const Scal<R> &S, const ShortTables &T, const DevState<R
     const V3<R> P0 = I.P[0], Ip = l1 ? I.P[4] : I.P[3];
     const V3<R> Jp = qpt(d, j, dO, 3 + l2);
     const V3<R> dIJ = Ip - Jp;
-    const R rr = sqrt_(dot(dIJ, dIJ));
+    const R irr = rsqrt_(dot(dIJ, dIJ));
     V3<R> dui, dvi, duj, dvj;
     const R ci = cosv(Ip - P0, Jp - P0, dui, dvi);   // depends on I and A
     const R cj = cosv(Jp - dO, Ip - dO, duj, dvj);   // depends on I
@@ -266,16 +272,16 @@ __device__ void item_ll(const Scal<R> &S, const ShortTables &T, const DevState<R
     const V3<R> dOdI = dci * dui + dcj * dvj;
     const V3<R> dOdA = R(-1) * dci * (dui + dvi);
     const V3<R> dAB = P0 - dO;
-    const R rab = sqrt_(dot(dAB, dAB));
+    const R ab2 = dot(dAB, dAB), irab = rsqrt_(ab2), rab = ab2 * irab;
     const R M = S.g_o * (R(1) - S.nlp * S.inv_nval_o);
     const R S1 = M * exp_(-mulc(rab, T.rep_k1[2][2])), S2 = M * exp_(-mulc(rab, T.rep_k2[2][2]));
     const R O1 = O * S1, O2 = O * S2;
     R e1, e2, er;
-    a.Erep.add(R(0.5) * rep_energy(S.nlp * S.nlp, S.rep_c1, S.rep_c2, O1, O2, rr, e1, e2, er));
-    const V3<R> drab = (R(1) / rab) * dAB;
+    a.Erep.add(R(0.5) * rep_energy(S.nlp * S.nlp, S.rep_c1, S.rep_c2, O1, O2, irr, e1, e2, er));
+    const V3<R> drab = irab * dAB;
     const V3<R> go = (e1 * S1 + e2 * S2) * dOdA +
                      (e1 * O1 * (-cval<R>(T.rep_k1[2][2])) + e2 * O2 * (-cval<R>(T.rep_k2[2][2]))) * drab;
-    const V3<R> gl = (e1 * S1 + e2 * S2) * dOdI + (er / rr) * dIJ;
+    const V3<R> gl = (e1 * S1 + e2 * S2) * dOdI + (er * irr) * dIJ;
     a.G[0] = a.G[0] + go;
     addG(a, 3 + l1, gl);
     if (VIR) vir_add(a.W, go + gl, dO, R(-0.5));
@@ -294,7 +300,7 @@ __device__ void item_d(const KParams &p, const Scal<R> &S, const ShortTables &T,
     const R r2 = dot(dv, dv);
     const R ri = rsqrt_(r2), r = r2 * ri;
     const int ku = u == 0 ? 0 : (u < 3 ? 1 : 2), kv = v == 0 ? 0 : (v < 3 ? 1 : 2);
-    const R m = mulc(r, T.disp_km[ku][kv]), mi = R(1) / m;
+    const R m = mulc(r, T.disp_km[ku][kv]), mi = rcp_(m);
     // exp(-gamma_n d) with d = S/r - 1: argument gamma_n - (gamma_n S)/r
     const R a6 = mulc(ri, T.disp_gS[0][ku][kv]), a8 = mulc(ri, T.disp_gS[1][ku][kv]),
             a10 = mulc(ri, T.disp_gS[2][ku][kv]);
@@ -351,137 +357,141 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
     }
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = blockIdx.x * 4 + w;
-    if (i >= p.M) return;
     int *q = qbuf[w];
     const Scal<R> &S = sc<R>(p);
-    const R rc2 = S.rc2;
-    ShortI<R> I;
-    for (int k = 0; k < 3; ++k) I.P[k] = my_pt(d, i, k);
-    I.P[3] = my_pt(d, i, 5);
-    I.P[4] = my_pt(d, i, 6);
-    {
-        const R q0 = d.gmp[(i * NS) * GMP], q1 = d.gmp[(i * NS + 1) * GMP], q2 = d.gmp[(i * NS + 2) * GMP];
-        I.A[0] = {S.cs_o, S.cp_o, S.g_o, R(1) - q0 * S.inv_nval_o, 0};
-        I.A[1] = {S.cs_h, S.cp_h, S.g_h, R(1) - q1 * S.inv_nval_h, 1};
-        I.A[2] = {S.cs_h, S.cp_h, S.g_h, R(1) - q2 * S.inv_nval_h, 1};
-        I.cf[0] = I.A[0].cf;
-        I.cf[1] = I.A[1].cf;
-        I.cf[2] = I.A[2].cf;
-        I.cf[3] = I.A[0].cf;
-        I.cf[4] = I.A[0].cf;
-    }
-    ShortAcc<R> acc;
-    for (int k = 0; k < 5; ++k) acc.G[k] = mk(R(0), R(0), R(0));
-#pragma unroll
-    for (int k = 0; k < 9; ++k) acc.W[k] = R(0);
-    int h[5] = {0, 0, 0, 0, 0}, t[5] = {0, 0, 0, 0, 0};   // heads and tails: BB, BL, LB, LL, D
-    const int nn = d.nnbr[i];
-    for (int base = 0;; base += 32) {
-        const bool flush = base >= nn;
-        const int slot = base + lane;
-        const bool live = slot < nn;
-        int j = 0;
-        V3<R> dO = mk(R(0), R(0), R(0));
-        if (live) neighbour(d, i, slot, j, dO);
-        // PART 0, stage 0: repulsion items; PART 1, stages 1-5: dispersion items of point u = stage - 1
-        const int s0 = PART == 0 ? 0 : 1, s1 = PART == 0 ? 1 : 6;
-        for (int stage = s0; stage < s1; ++stage) {
-            if (PART == 0) {
-                unsigned bb = 0, bl = 0, lb = 0, ll = 0;
-                if (live) {
-                    const V3<R> Q1 = qpt(d, j, dO, 1), Q2 = qpt(d, j, dO, 2);
-                    const V3<R> L1 = qpt(d, j, dO, 3), L2 = qpt(d, j, dO, 4);
-                    const V3<R> mi1 = R(0.5) * (I.P[0] + I.P[1]), mi2 = R(0.5) * (I.P[0] + I.P[2]);
-                    const V3<R> mj1 = R(0.5) * (dO + Q1), mj2 = R(0.5) * (dO + Q2);
-                    auto in = [&](V3<R> x) { return !PER || dot(x, x) < rc2; };
-                    bb = in(mi1 - mj1) | in(mi1 - mj2) << 1 | in(mi2 - mj1) << 2 | in(mi2 - mj2) << 3;
-                    bl = in(mi1 - L1) | in(mi1 - L2) << 1 | in(mi2 - L1) << 2 | in(mi2 - L2) << 3;
-                    lb = in(I.P[3] - mj1) | in(I.P[3] - mj2) << 1 | in(I.P[4] - mj1) << 2 | in(I.P[4] - mj2) << 3;
-                    ll = in(I.P[3] - L1) | in(I.P[3] - L2) << 1 | in(I.P[4] - L1) << 2 | in(I.P[4] - L2) << 3;
-                }
-                const unsigned bits[4] = {bb, bl, lb, ll};
-                const int off[4] = {SQ_BB, SQ_BL, SQ_LB, SQ_LL};
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    int n;
-                    int pos = warp_excl_scan(__popc(bits[c]), lane, n);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if ((bits[c] >> k) & 1u) q[off[c] + (t[c] + pos++) % SQ_CAP] = slot * 32 + k;
-                    t[c] += n;
-                }
-            } else {
-                const int u = stage - 1;
-                unsigned bits = 0;
-                if (live) {
-                    const V3<R> Pu = selP(I, u);
-#pragma unroll
-                    for (int v = 0; v < 5; ++v) {
-                        const V3<R> x = Pu - qpt(d, j, dO, v);
-                        if (!PER || dot(x, x) < rc2) bits |= 1u << v;
+    // molecules i = 4 block + w, then strided by the grid (a persistent launch
+    // with a capped grid leaves room for the kernels of the other streams)
+    for (int i = blockIdx.x * 4 + w; i < p.M; i += gridDim.x * 4) {
+        const R rc2 = S.rc2;
+        ShortI<R> I;
+        for (int k = 0; k < 3; ++k) I.P[k] = my_pt(d, i, k);
+        I.P[3] = my_pt(d, i, 5);
+        I.P[4] = my_pt(d, i, 6);
+        {
+            const R q0 = d.gmp[(i * NS) * GMP], q1 = d.gmp[(i * NS + 1) * GMP], q2 = d.gmp[(i * NS + 2) * GMP];
+            I.A[0] = rep_atom(S.cs_o, S.cp_o, S.g_o, R(1) - q0 * S.inv_nval_o, 0);
+            I.A[1] = rep_atom(S.cs_h, S.cp_h, S.g_h, R(1) - q1 * S.inv_nval_h, 1);
+            I.A[2] = rep_atom(S.cs_h, S.cp_h, S.g_h, R(1) - q2 * S.inv_nval_h, 1);
+            I.cf[0] = I.A[0].cf;
+            I.cf[1] = I.A[1].cf;
+            I.cf[2] = I.A[2].cf;
+            I.cf[3] = I.A[0].cf;
+            I.cf[4] = I.A[0].cf;
+        }
+        ShortAcc<R> acc;
+        for (int k = 0; k < 5; ++k) acc.G[k] = mk(R(0), R(0), R(0));
+    #pragma unroll
+        for (int k = 0; k < 9; ++k) acc.W[k] = R(0);
+        int h[5] = {0, 0, 0, 0, 0}, t[5] = {0, 0, 0, 0, 0};   // heads and tails: BB, BL, LB, LL, D
+        const int nn = d.nnbr[i];
+        for (int base = 0;; base += 32) {
+            const bool flush = base >= nn;
+            const int slot = base + lane;
+            const bool live = slot < nn;
+            int j = 0;
+            V3<R> dO = mk(R(0), R(0), R(0));
+            if (live) neighbour(d, i, slot, j, dO);
+            // PART 0, stage 0: repulsion items; PART 1, stages 1-5: dispersion items of point u = stage - 1
+            const int s0 = PART == 0 ? 0 : 1, s1 = PART == 0 ? 1 : 6;
+            for (int stage = s0; stage < s1; ++stage) {
+                if (PART == 0) {
+                    unsigned bb = 0, bl = 0, lb = 0, ll = 0;
+                    if (live) {
+                        const V3<R> Q1 = qpt(d, j, dO, 1), Q2 = qpt(d, j, dO, 2);
+                        const V3<R> L1 = qpt(d, j, dO, 3), L2 = qpt(d, j, dO, 4);
+                        const V3<R> mi1 = R(0.5) * (I.P[0] + I.P[1]), mi2 = R(0.5) * (I.P[0] + I.P[2]);
+                        const V3<R> mj1 = R(0.5) * (dO + Q1), mj2 = R(0.5) * (dO + Q2);
+                        auto in = [&](V3<R> x) { return !PER || dot(x, x) < rc2; };
+                        bb = in(mi1 - mj1) | in(mi1 - mj2) << 1 | in(mi2 - mj1) << 2 | in(mi2 - mj2) << 3;
+                        bl = in(mi1 - L1) | in(mi1 - L2) << 1 | in(mi2 - L1) << 2 | in(mi2 - L2) << 3;
+                        lb = in(I.P[3] - mj1) | in(I.P[3] - mj2) << 1 | in(I.P[4] - mj1) << 2 | in(I.P[4] - mj2) << 3;
+                        ll = in(I.P[3] - L1) | in(I.P[3] - L2) << 1 | in(I.P[4] - L1) << 2 | in(I.P[4] - L2) << 3;
                     }
-                }
-                int n;
-                int pos = warp_excl_scan(__popc(bits), lane, n);
-#pragma unroll
-                for (int v = 0; v < 5; ++v)
-                    if ((bits >> v) & 1u) q[SQ_D + (t[4] + pos++) % SQ_CAPD] = slot * 32 + u * 5 + v;
-                t[4] += n;
-            }
-            __syncwarp();
-            const bool last = flush && stage == s1 - 1;
-            if (PART == 1) {
-                while (t[4] - h[4] >= 32 || (last && t[4] > h[4])) {
-                    if (lane < t[4] - h[4]) item_d<R, VIR>(p, S, T, d, I, i, q[SQ_D + (h[4] + lane) % SQ_CAPD], acc);
-                    h[4] += min(32, t[4] - h[4]);
+                    const unsigned bits[4] = {bb, bl, lb, ll};
+                    const int off[4] = {SQ_BB, SQ_BL, SQ_LB, SQ_LL};
+    #pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        int n;
+                        int pos = warp_excl_scan(__popc(bits[c]), lane, n);
+    #pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if ((bits[c] >> k) & 1u) q[off[c] + (t[c] + pos++) % SQ_CAP] = slot * 32 + k;
+                        t[c] += n;
+                    }
+                } else {
+                    const int u = stage - 1;
+                    unsigned bits = 0;
+                    if (live) {
+                        const V3<R> Pu = selP(I, u);
+    #pragma unroll
+                        for (int v = 0; v < 5; ++v) {
+                            const V3<R> x = Pu - qpt(d, j, dO, v);
+                            if (!PER || dot(x, x) < rc2) bits |= 1u << v;
+                        }
+                    }
+                    int n;
+                    int pos = warp_excl_scan(__popc(bits), lane, n);
+    #pragma unroll
+                    for (int v = 0; v < 5; ++v)
+                        if ((bits >> v) & 1u) q[SQ_D + (t[4] + pos++) % SQ_CAPD] = slot * 32 + u * 5 + v;
+                    t[4] += n;
                 }
                 __syncwarp();
-                continue;
+                const bool last = flush && stage == s1 - 1;
+                if (PART == 1) {
+                    while (t[4] - h[4] >= 32 || (last && t[4] > h[4])) {
+                        if (lane < t[4] - h[4]) item_d<R, VIR>(p, S, T, d, I, i, q[SQ_D + (h[4] + lane) % SQ_CAPD], acc);
+                        h[4] += min(32, t[4] - h[4]);
+                    }
+                    __syncwarp();
+                    continue;
+                }
+                while (t[0] - h[0] >= 32 || (last && t[0] > h[0])) {
+                    if (lane < t[0] - h[0]) item_bb<R, VIR>(S, T, d, I, i, q[SQ_BB + (h[0] + lane) % SQ_CAP], acc);
+                    h[0] += min(32, t[0] - h[0]);
+                }
+                while (t[1] - h[1] >= 32 || (last && t[1] > h[1])) {
+                    if (lane < t[1] - h[1]) item_bl<R, VIR>(S, T, d, I, i, q[SQ_BL + (h[1] + lane) % SQ_CAP], acc);
+                    h[1] += min(32, t[1] - h[1]);
+                }
+                while (t[2] - h[2] >= 32 || (last && t[2] > h[2])) {
+                    if (lane < t[2] - h[2]) item_lb<R, VIR>(S, T, d, I, i, q[SQ_LB + (h[2] + lane) % SQ_CAP], acc);
+                    h[2] += min(32, t[2] - h[2]);
+                }
+                while (t[3] - h[3] >= 32 || (last && t[3] > h[3])) {
+                    if (lane < t[3] - h[3]) item_ll<R, VIR>(S, T, d, I, i, q[SQ_LL + (h[3] + lane) % SQ_CAP], acc);
+                    h[3] += min(32, t[3] - h[3]);
+                }
+                __syncwarp();
             }
-            while (t[0] - h[0] >= 32 || (last && t[0] > h[0])) {
-                if (lane < t[0] - h[0]) item_bb<R, VIR>(S, T, d, I, i, q[SQ_BB + (h[0] + lane) % SQ_CAP], acc);
-                h[0] += min(32, t[0] - h[0]);
-            }
-            while (t[1] - h[1] >= 32 || (last && t[1] > h[1])) {
-                if (lane < t[1] - h[1]) item_bl<R, VIR>(S, T, d, I, i, q[SQ_BL + (h[1] + lane) % SQ_CAP], acc);
-                h[1] += min(32, t[1] - h[1]);
-            }
-            while (t[2] - h[2] >= 32 || (last && t[2] > h[2])) {
-                if (lane < t[2] - h[2]) item_lb<R, VIR>(S, T, d, I, i, q[SQ_LB + (h[2] + lane) % SQ_CAP], acc);
-                h[2] += min(32, t[2] - h[2]);
-            }
-            while (t[3] - h[3] >= 32 || (last && t[3] > h[3])) {
-                if (lane < t[3] - h[3]) item_ll<R, VIR>(S, T, d, I, i, q[SQ_LL + (h[3] + lane) % SQ_CAP], acc);
-                h[3] += min(32, t[3] - h[3]);
-            }
-            __syncwarp();
+            if (flush) break;
         }
-        if (flush) break;
-    }
-    // lane reduction; points 3, 4 are the lone pairs (point slots 5, 6)
-    const R vals[15] = {acc.G[0].x, acc.G[0].y, acc.G[0].z, acc.G[1].x, acc.G[1].y, acc.G[1].z,
-                        acc.G[2].x, acc.G[2].y, acc.G[2].z, acc.G[3].x, acc.G[3].y, acc.G[3].z,
-                        acc.G[4].x, acc.G[4].y, acc.G[4].z};
-    const R s = warp_transpose_sum<R, 15>(vals, reinterpret_cast<R *>(q), lane);
-    const int pt = lane / 3;
-    if (lane < 15) d.gpt[(i * NP + (pt < 3 ? pt : pt + 2)) * 3 + lane % 3] += double(s);
-    if (VIR) vir_points_out(d, i, I.P, s, acc.W, reinterpret_cast<R *>(q), lane);
-    if (PART == 0) {
-        const double er_ = warp_sum_acc(acc.Erep);
-        if (lane == 0) d.epart[i * NTERM + T_REP] += er_;
-    } else {
-        const double ed_ = warp_sum_acc(acc.Ed), ex_ = warp_sum_acc(acc.Ex);
-        if (lane == 0) {
-            d.epart[i * NTERM + T_DISP] += ed_;
-            d.epart[i * NTERM + T_XDISP] += ex_;
+        // lane reduction; points 3, 4 are the lone pairs (point slots 5, 6)
+        const R vals[15] = {acc.G[0].x, acc.G[0].y, acc.G[0].z, acc.G[1].x, acc.G[1].y, acc.G[1].z,
+                            acc.G[2].x, acc.G[2].y, acc.G[2].z, acc.G[3].x, acc.G[3].y, acc.G[3].z,
+                            acc.G[4].x, acc.G[4].y, acc.G[4].z};
+        const R s = warp_transpose_sum<R, 15>(vals, reinterpret_cast<R *>(q), lane);
+        const int pt = lane / 3;
+        if (lane < 15) d.gpt[(i * NP + (pt < 3 ? pt : pt + 2)) * 3 + lane % 3] += double(s);
+        if (VIR) vir_points_out(d, i, I.P, s, acc.W, reinterpret_cast<R *>(q), lane);
+        if (PART == 0) {
+            const double er_ = warp_sum_acc(acc.Erep);
+            if (lane == 0) d.epart[i * NTERM + T_REP] += er_;
+        } else {
+            const double ed_ = warp_sum_acc(acc.Ed), ex_ = warp_sum_acc(acc.Ex);
+            if (lane == 0) {
+                d.epart[i * NTERM + T_DISP] += ed_;
+                d.epart[i * NTERM + T_XDISP] += ex_;
+            }
         }
     }
 }
 
+// max_blocks > 0 caps the grid (each block then walks several molecules per warp)
 template <typename R>
-void launch_short(const KParams &p, DevState<R> &d, Launch L) {
-    const unsigned nb = (p.M + 3) / 4;
+void launch_short(const KParams &p, DevState<R> &d, Launch L, int max_blocks) {
+    unsigned nb = (p.M + 3) / 4;
+    if (max_blocks > 0 && nb > (unsigned)max_blocks) nb = (unsigned)max_blocks;
     if (p.vir) {
         if (p.periodic) {
             k_short<R, true, 0, true><<<nb, 128, 0, L.s>>>(p, d);
@@ -500,7 +510,7 @@ void launch_short(const KParams &p, DevState<R> &d, Launch L) {
     count(L, 2);
 }
 
-template void launch_short<float>(const KParams &, DevState<float> &, Launch);
-template void launch_short<double>(const KParams &, DevState<double> &, Launch);
+template void launch_short<float>(const KParams &, DevState<float> &, Launch, int);
+template void launch_short<double>(const KParams &, DevState<double> &, Launch, int);
 
 }  // namespace sibfa

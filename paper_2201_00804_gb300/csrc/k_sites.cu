@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(128) k_sites(KParams p, DevState<R> d) {
             }
         }
         // clear the per-molecule accumulators of this evaluation
-        for (int k = t; k < NP * 3; k += 8) d.gpt[m * NP * 3 + k] = 0.0, d.gpt_r[m * NP * 3 + k] = 0.0;
+        for (int k = t; k < NP * 3; k += 8)
+            d.gpt[m * NP * 3 + k] = 0.0, d.gpt_r[m * NP * 3 + k] = 0.0, d.gpt_s[m * NP * 3 + k] = 0.0;
         for (int k = t; k < NS * 3; k += 8) d.gmu[m * NS * 3 + k] = 0.0, d.gmu_r[m * NS * 3 + k] = 0.0;
         for (int k = t; k < NS * 6; k += 8) d.gth[m * NS * 6 + k] = 0.0, d.gth_r[m * NS * 6 + k] = 0.0;
         for (int k = t; k < 9; k += 8) d.efield[m * 9 + k] = 0.0, d.efield_r[m * 9 + k] = 0.0;

@@ -182,6 +182,9 @@ struct DevState {
     // Ewald corrections), which runs on a second stream concurrently with the
     // real-space kernels; same layouts as the arrays above, merged where used.
     double *gpt_r, *gmu_r, *gth_r, *efield_r, *vlp_r, *dvlp_r, *epart_r, *efp_r;
+    // point gradients of the short-range kernels, which run on a third stream
+    // concurrently with the permanent pass and the polarization solve
+    double *gpt_s;
     // polarization solve
     double *mu, *res, *zv, *pv, *ap, *efp;   // M*9 each
     R *vecR;            // M*9 the vector of the current T product in the working precision
@@ -238,6 +241,15 @@ template <> __device__ inline float rsqrt_<float>(float x) {
     return fmaf(y, h, y);
 }
 template <> __device__ inline double rsqrt_<double>(double x) { return rsqrt(x); }
+// Reciprocal.  FP32: the hardware approximation refined by one Newton step
+// (y <- y + y (1 - x y)), in place of the IEEE division sequence and its
+// slow-path branch; FP64: the plain division.
+template <typename R> __device__ inline R rcp_(R x);
+template <> __device__ inline float rcp_<float>(float x) {
+    const float y = __fdividef(1.0f, x);
+    return fmaf(y, fmaf(-x, y, 1.0f), y);
+}
+template <> __device__ inline double rcp_<double>(double x) { return 1.0 / x; }
 template <typename R> __device__ inline R exp_(R x);
 template <> __device__ inline float exp_<float>(float x) { return expf(x); }
 template <> __device__ inline double exp_<double>(double x) { return exp(x); }
@@ -301,7 +313,7 @@ template <typename R, int N>
 __device__ inline void g_erfc(R r, R rinv, R alpha, R *g) {
     const R r2i = rinv * rinv;
     const R ar = alpha * r;
-    const R ex = exp_(-ar * ar) * (R(0.56418958354775628695) / alpha);   // 1/(a sqrt(pi))
+    const R ex = exp_(-ar * ar) * (R(0.56418958354775628695) * rcp_(alpha));   // 1/(a sqrt(pi))
     R b = erfc_(ar) * rinv;
     g[0] = b;
     R tw = R(2) * alpha * alpha, p = tw;
@@ -612,8 +624,8 @@ __device__ inline R cosv(V3<R> u, V3<R> v, V3<R> &du, V3<R> &dv) {
     const R uu = dot(u, u), vv = dot(v, v);
     const R iu = rsqrt_(uu), iv = rsqrt_(vv);
     const R c = dot(u, v) * iu * iv;
-    du = (iu * iv) * v - (c / uu) * u;
-    dv = (iu * iv) * u - (c / vv) * v;
+    du = (iu * iv) * v - (c * iu * iu) * u;
+    dv = (iu * iv) * u - (c * iv * iv) * v;
     return c;
 }
 
@@ -782,7 +794,7 @@ struct Launch {
 template <typename R> void launch_sites(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_neighbors(const KParams &p, DevState<R> &d, int ncell[3], Launch L);
 template <typename R> void launch_real_perm(const KParams &p, DevState<R> &d, Launch L);
-template <typename R> void launch_short(const KParams &p, DevState<R> &d, Launch L);
+template <typename R> void launch_short(const KParams &p, DevState<R> &d, Launch L, int max_blocks = 0);
 template <typename R> void launch_ct(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_intra_perm(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_real_tmu(const KParams &p, DevState<R> &d, double *out,
@@ -804,6 +816,13 @@ inline DevState<R> rec_view(const DevState<R> &d) {
     r.dvlp = d.dvlp_r;
     r.epart = d.epart_r;
     r.vir = d.vir_r;
+    return r;
+}
+// the short-range kernels' view: their own point-gradient array
+template <typename R>
+inline DevState<R> short_view(const DevState<R> &d) {
+    DevState<R> r = d;
+    r.gpt = d.gpt_s;
     return r;
 }
 
