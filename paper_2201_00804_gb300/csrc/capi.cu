@@ -32,6 +32,11 @@ struct sibfa_ctx {
     cudaStream_t s3 = nullptr;
     cudaEvent_t ev_fork3 = nullptr, ev_join3 = nullptr;
     bool short_pending = false;
+    // charge transfer (lowest priority), forked after the permanent pass and
+    // joined before the force pass: it runs beside the polarization solve
+    cudaStream_t s4 = nullptr;
+    cudaEvent_t ev_fork4 = nullptr, ev_join4 = nullptr;
+    bool ct_pending = false;
     cudaStream_t us = nullptr;   // the caller's stream (ordering only)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     // polarization iterations as one CUDA graph with a device-side while loop
@@ -363,6 +368,18 @@ sibfa_status join_short(sibfa_ctx *ctx) {
     CK(cudaStreamWaitEvent(ctx->s, ctx->ev_join3, 0));
     return SIBFA_OK;
 }
+sibfa_status fork_ct(sibfa_ctx *ctx) {
+    CK(cudaEventRecord(ctx->ev_fork4, ctx->s));
+    CK(cudaStreamWaitEvent(ctx->s4, ctx->ev_fork4, 0));
+    return SIBFA_OK;
+}
+sibfa_status join_ct(sibfa_ctx *ctx) {
+    if (!ctx->ct_pending) return SIBFA_OK;
+    ctx->ct_pending = false;
+    CK(cudaEventRecord(ctx->ev_join4, ctx->s4));
+    CK(cudaStreamWaitEvent(ctx->s, ctx->ev_join4, 0));
+    return SIBFA_OK;
+}
 
 sibfa_status join_rec(sibfa_ctx *ctx) {
     CK(cudaEventRecord(ctx->ev_join, ctx->s2));
@@ -531,7 +548,8 @@ template <typename R>
 sibfa_status evaluate(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, double tol) {
     const sibfa_status st = evaluate_impl<R>(ctx, want_forces, dipoles_only, tol);
     const sibfa_status sj = join_short(ctx);
-    return st ? st : sj;
+    const sibfa_status sc = join_ct(ctx);
+    return st ? st : (sj ? sj : sc);
 }
 
 template <typename R>
@@ -579,7 +597,17 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
         if ((st = join_rec(ctx))) return st;
         launch_merge_rec(p, d, L);
     }
-    if (!dipoles_only) { Phase ph(ctx, "ct");  launch_ct(p, d, L); }
+    if (!dipoles_only) {
+        if (p.vir) {
+            Phase ph(ctx, "ct");
+            launch_ct(p, d, L);
+        } else {   // beside the solve, which does not read its results
+            if ((st = fork_ct(ctx))) return st;
+            ctx->ct_pending = true;
+            Phase ph(ctx, "ct", ctx->s4);
+            launch_ct(p, d, Launch{ctx->s4, &ctx->launches});
+        }
+    }
     {
         Phase ph(ctx, "pcg");
         st = solve(ctx, d, tol, L);
@@ -587,6 +615,8 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
     if (st == SIBFA_E_CUDA) return st;
     sibfa_status st_solve = st;
     if (dipoles_only) return st_solve;
+    // the lambdas of the charge transfer feed k_pol_energy's working-precision copy
+    if ((st = join_ct(ctx))) return st;
     launch_pol_energy(p, d, L);
     if (want_forces) {
         if (p.periodic) {
@@ -882,6 +912,9 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
     if (cudaStreamCreateWithPriority(&ctx->s, cudaStreamNonBlocking, prio_mid) != cudaSuccess ||
         cudaStreamCreateWithPriority(&ctx->s2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaStreamCreateWithPriority(&ctx->s3, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ctx->s4, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork4, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join4, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork3, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join3, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
@@ -1090,7 +1123,10 @@ void sibfa_destroy(sibfa_ctx *ctx) {
     if (ctx->s) cudaStreamSynchronize(ctx->s);
     if (ctx->s2) cudaStreamSynchronize(ctx->s2);
     if (ctx->s3) cudaStreamSynchronize(ctx->s3);
+    if (ctx->s4) cudaStreamSynchronize(ctx->s4);
     if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+    if (ctx->ev_fork4) cudaEventDestroy(ctx->ev_fork4);
+    if (ctx->ev_join4) cudaEventDestroy(ctx->ev_join4);
     if (ctx->ev_fork3) cudaEventDestroy(ctx->ev_fork3);
     if (ctx->ev_join3) cudaEventDestroy(ctx->ev_join3);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
@@ -1115,6 +1151,7 @@ void sibfa_destroy(sibfa_ctx *ctx) {
     if (ctx->s) cudaStreamDestroy(ctx->s);
     if (ctx->s2) cudaStreamDestroy(ctx->s2);
     if (ctx->s3) cudaStreamDestroy(ctx->s3);
+    if (ctx->s4) cudaStreamDestroy(ctx->s4);
     delete ctx;
 }
 
