@@ -32,8 +32,9 @@ struct sibfa_ctx {
     cudaStream_t s3 = nullptr;
     cudaEvent_t ev_fork3 = nullptr, ev_join3 = nullptr;
     bool short_pending = false;
-    // charge transfer (lowest priority), forked after the permanent pass and
-    // joined before the force pass: it runs beside the polarization solve
+    // lone-pair potentials and charge transfer, forked after the neighbour
+    // list and joined before the polarization energy: they run beside the
+    // permanent pass and the polarization solve
     cudaStream_t s4 = nullptr;
     cudaEvent_t ev_fork4 = nullptr, ev_join4 = nullptr;
     bool ct_pending = false;
@@ -179,6 +180,7 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.lam, M * 2);
     AL(d.kap, M * 3);
     AL(d.epart, M * NTERM);
+    AL(d.epw, M * NS * 2);
     AL(d.vir, M * 9);
     AL(d.vir_r, M * 9);
     AL(d.vphi, M * 9);
@@ -591,6 +593,15 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
         DevState<R> ds = short_view(d);
         launch_short(p, ds, Launch{ctx->s3, &ctx->launches});
     }
+    // Lone-pair potentials and then the charge transfer on the fourth stream
+    // (the transfer after the reciprocal chain); joined before the
+    // polarization energy, which copies the lambdas.
+    const bool bg_ct = !dipoles_only && !p.vir;
+    if (bg_ct) {
+        if ((st = fork_ct(ctx))) return st;
+        ctx->ct_pending = true;
+        launch_lp_potential(p, d, Launch{ctx->s4, &ctx->launches});
+    }
     { Phase ph(ctx, "real_perm");  launch_real_perm(p, d, L); }
     if (!dipoles_only && !bg_short) { Phase ph(ctx, "short");  launch_short(p, d, L); }
     if (p.periodic) {
@@ -598,12 +609,14 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
         launch_merge_rec(p, d, L);
     }
     if (!dipoles_only) {
-        if (p.vir) {
+        if (!bg_ct) {
+            launch_lp_potential(p, d, L);
             Phase ph(ctx, "ct");
             launch_ct(p, d, L);
         } else {   // beside the solve, which does not read its results
+            // after the permanent pass on this stream (both add into the
+            // point gradients) and the reciprocal chain (lone-pair potentials)
             if ((st = fork_ct(ctx))) return st;
-            ctx->ct_pending = true;
             Phase ph(ctx, "ct", ctx->s4);
             launch_ct(p, d, Launch{ctx->s4, &ctx->launches});
         }
@@ -912,7 +925,7 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
     if (cudaStreamCreateWithPriority(&ctx->s, cudaStreamNonBlocking, prio_mid) != cudaSuccess ||
         cudaStreamCreateWithPriority(&ctx->s2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
         cudaStreamCreateWithPriority(&ctx->s3, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&ctx->s4, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ctx->s4, cudaStreamNonBlocking, prio_mid) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork4, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join4, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork3, cudaEventDisableTiming) != cudaSuccess ||

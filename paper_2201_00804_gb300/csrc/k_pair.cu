@@ -164,16 +164,20 @@ __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d
     }
 }
 
-template <typename R, bool PER, bool VIR>
-__global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) {
-    __shared__ double s_e[7][2];
-    __shared__ double s_w[VIR ? NS : 1][9];
-    __shared__ PairQueue<R> qs[7];
+// Two launches per molecule set: LPS = false, one block of 5 warps per
+// molecule (target sites; each warp stores its energies, so the blocks need
+// no barrier outside the virial variant); LPS = true, one block of 2 warps
+// (target lone pairs: potential and gradient), which runs on another stream.
+template <typename R, bool PER, bool VIR, bool LPS>
+__global__ void __launch_bounds__(LPS ? 64 : 160, LPS ? 8 : 3) k_real_perm(KParams p, DevState<R> d) {
+    __shared__ double s_w[VIR && !LPS ? NS : 1][9];
+    __shared__ PairQueue<R> qs[LPS ? 2 : NS];
     static_assert(sizeof(PairQueue<R>) >= 15 * 33 * sizeof(R), "reduction buffer aliases the queue");
     const int i = blockIdx.x;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool is_lp = w >= NS;
-    PairQueue<R> &q = qs[w];
+    const int wq = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = LPS ? NS + wq : wq;   // target point
+    constexpr bool is_lp = LPS;
+    PairQueue<R> &q = qs[wq];
     const V3<R> ot = my_pt(d, i, w);
     Mp<R> mt{};
     if (!is_lp) mt = load_mp(d.gmp + (i * NS + w) * GMP);
@@ -269,35 +273,40 @@ __global__ void __launch_bounds__(224, 2) k_real_perm(KParams p, DevState<R> d) 
             const R wv = warp_transpose_sum<R, 9>(A.W, buf, lane);
             if (lane < 9) s_w[w][lane] = double(wv);
         }
+        // per-warp energies (summed over the five sites in a fixed order by k_pol_energy)
         const double e0 = warp_sum_acc(A.Ue), e1 = warp_sum_acc(A.Up);
         if (lane == 0) {
-            s_e[w][0] = e0;
-            s_e[w][1] = e1;
+            d.epw[(i * NS + w) * 2] = ke * e0;
+            d.epw[(i * NS + w) * 2 + 1] = ke * e1;
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0, b = 0;
-        for (int k = 0; k < NS; ++k) a += s_e[k][0], b += s_e[k][1];
-        d.epart[i * NTERM + T_ELEC] += ke * a;
-        d.epart[i * NTERM + T_PEN] += ke * b;
-    }
-    if (VIR && threadIdx.x < 9) {   // the site warps' virials in a fixed order
-        double v = 0;
-        for (int k = 0; k < NS; ++k) v += s_w[k][threadIdx.x];
-        d.vir[i * 9 + threadIdx.x] += ke * v;
+    if (VIR && !LPS) {   // the site warps' virials in a fixed order
+        __syncthreads();
+        if (threadIdx.x < 9) {
+            double v = 0;
+            for (int k = 0; k < NS; ++k) v += s_w[k][threadIdx.x];
+            d.vir[i * 9 + threadIdx.x] += ke * v;
+        }
     }
 }
 
 template <typename R>
 void launch_real_perm(const KParams &p, DevState<R> &d, Launch L) {
     if (p.vir) {
-        if (p.periodic) k_real_perm<R, true, true><<<p.M, 224, 0, L.s>>>(p, d);
-        else k_real_perm<R, false, true><<<p.M, 224, 0, L.s>>>(p, d);
+        if (p.periodic) k_real_perm<R, true, true, false><<<p.M, 160, 0, L.s>>>(p, d);
+        else k_real_perm<R, false, true, false><<<p.M, 160, 0, L.s>>>(p, d);
     } else {
-        if (p.periodic) k_real_perm<R, true, false><<<p.M, 224, 0, L.s>>>(p, d);
-        else k_real_perm<R, false, false><<<p.M, 224, 0, L.s>>>(p, d);
+        if (p.periodic) k_real_perm<R, true, false, false><<<p.M, 160, 0, L.s>>>(p, d);
+        else k_real_perm<R, false, false, false><<<p.M, 160, 0, L.s>>>(p, d);
     }
+    count(L);
+}
+
+// potential and field of the permanent multipoles at the lone pairs (real space)
+template <typename R>
+void launch_lp_potential(const KParams &p, DevState<R> &d, Launch L) {
+    if (p.periodic) k_real_perm<R, true, false, true><<<p.M, 64, 0, L.s>>>(p, d);
+    else k_real_perm<R, false, false, true><<<p.M, 64, 0, L.s>>>(p, d);
     count(L);
 }
 
@@ -362,7 +371,8 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
     for (int k = 0; k < 3; ++k) P[k] = my_pt(d, i, k);
     P[3] = my_pt(d, i, 5);
     P[4] = my_pt(d, i, 6);
-    const R Vi[2] = {R(d.vlp[i * 2]), R(d.vlp[i * 2 + 1])};
+    // lone-pair potentials: real space + reciprocal chain
+    const R Vi[2] = {R(d.vlp[i * 2] + d.vlp_r[i * 2]), R(d.vlp[i * 2 + 1] + d.vlp_r[i * 2 + 1])};
     const R Vint_i[3] = {R(d.vint[i * 3]), R(d.vint[i * 3 + 1]), R(d.vint[i * 3 + 2])};
     V3<R> G[5];
     for (int k = 0; k < 5; ++k) G[k] = mk(R(0), R(0), R(0));
@@ -383,7 +393,7 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
         Q[2] = dO + my_pt(d, j, 2);
         Q[3] = dO + my_pt(d, j, 5);
         Q[4] = dO + my_pt(d, j, 6);
-        const R Vj[2] = {R(d.vlp[j * 2]), R(d.vlp[j * 2 + 1])};
+        const R Vj[2] = {R(d.vlp[j * 2] + d.vlp_r[j * 2]), R(d.vlp[j * 2 + 1] + d.vlp_r[j * 2 + 1])};
         const R Vint_j[3] = {R(d.vint[j * 3]), R(d.vint[j * 3 + 1]), R(d.vint[j * 3 + 2])};
         V3<R> Gj = mk(R(0), R(0), R(0));   // gradient on i's points from j (virial)
         for (int l = 0; l < 2; ++l)
@@ -678,6 +688,7 @@ void launch_real_polforce(const KParams &p, DevState<R> &d, Launch L) {
 
 #define INST(R)                                                                                    \
     template void launch_real_perm<R>(const KParams &, DevState<R> &, Launch);                     \
+    template void launch_lp_potential<R>(const KParams &, DevState<R> &, Launch);                  \
     template void launch_ct<R>(const KParams &, DevState<R> &, Launch);                            \
     template void launch_real_tmu<R>(const KParams &, DevState<R> &, double *, Launch);             \
     template void launch_real_polforce<R>(const KParams &, DevState<R> &, Launch);

@@ -348,6 +348,11 @@ __global__ void k_pol_energy(KParams p, DevState<R> d) {
     d.lamR[m * 2] = R(d.lam[m * 2]);
     d.lamR[m * 2 + 1] = R(d.lam[m * 2 + 1]);
     d.epart[m * NTERM + T_POL] = -0.5 * p.ke * e;
+    // real-space multipole and penetration energies of the five target sites
+    double el = 0, pe = 0;
+    for (int w = 0; w < NS; ++w) el += d.epw[(m * NS + w) * 2], pe += d.epw[(m * NS + w) * 2 + 1];
+    d.epart[m * NTERM + T_ELEC] += el;
+    d.epart[m * NTERM + T_PEN] += pe;
 }
 template <typename R>
 void launch_pol_energy(const KParams &p, DevState<R> &d, Launch L) {
@@ -561,13 +566,13 @@ void launch_virial_total(const KParams &p, DevState<R> &d, double *out, Launch L
     count(L);
 }
 
-// Join of the reciprocal chain into the arrays read by the charge transfer
-// and the polarization solve: permanent field and lone-pair potentials.
+// Join of the reciprocal chain into the permanent field that the
+// polarization solve reads (the charge transfer reads both lone-pair
+// potential arrays itself).
 template <typename R>
 __global__ void k_merge_rec(int M, DevState<R> d) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < M * 9) d.efield[k] += d.efield_r[k];
-    if (k < M * 2) d.vlp[k] += d.vlp_r[k];
 }
 template <typename R>
 void launch_merge_rec(const KParams &p, DevState<R> &d, Launch L) {

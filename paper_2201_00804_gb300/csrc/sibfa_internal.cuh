@@ -171,6 +171,7 @@ struct DevState {
     double *lam;        // M*2 dE_ct/dV_lp
     double *kap;        // M*3 dE_ct/dV_int
     double *epart;      // M*NTERM per-molecule energy partials
+    double *epw;        // M*NS*2 multipole and penetration energy of each target site (k_real_perm)
     // Virial: per-molecule dE/d eps (row-major 3x3) for the affine strain
     // x -> (I + eps) x of atoms and cell, and the reciprocal-space parts
     double *vir;        // M*9
@@ -794,6 +795,7 @@ struct Launch {
 template <typename R> void launch_sites(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_neighbors(const KParams &p, DevState<R> &d, int ncell[3], Launch L);
 template <typename R> void launch_real_perm(const KParams &p, DevState<R> &d, Launch L);
+template <typename R> void launch_lp_potential(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_short(const KParams &p, DevState<R> &d, Launch L, int max_blocks = 0);
 template <typename R> void launch_ct(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_intra_perm(const KParams &p, DevState<R> &d, Launch L);
