@@ -491,23 +491,25 @@ __global__ void __launch_bounds__(32 * GW) k_gather_field(KParams p, DevState<R>
         vals[0] = -v[1] * S.ike;
         vals[1] = -v[2] * S.ike;
         vals[2] = -v[3] * S.ike;
-    } else if (lane == 25) {
+    } else if (lane < 28) {
+        // lane 25: self term of the atom's own dipole; lanes 26, 27: the
+        // erf part of the field of each of the other two atoms' dipoles
         const R al = S.alpha;
-        const R cself = R(4.0 / 3.0) * al * al * al * R(0.56418958354775628695);
         const R *v = d.vecR + m * 9;
-        const V3<R> Xa = my_pt(d, m, a);
-        V3<R> E = cself * mk(v[a * 3], v[a * 3 + 1], v[a * 3 + 2]);
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            if (b == a) continue;
-            const V3<R> xv = Xa - my_pt(d, m, b);
+        V3<R> E;
+        if (lane == 25) {
+            const R cself = R(4.0 / 3.0) * al * al * al * R(0.56418958354775628695);
+            E = cself * mk(v[a * 3], v[a * 3 + 1], v[a * 3 + 2]);
+        } else {
+            const int b = (a + lane - 25) % 3;   // the two atoms b != a
+            const V3<R> xv = my_pt(d, m, a) - my_pt(d, m, b);
             R g[4];
             g_erf_s<R, 3>(dot(xv, xv), al, g);
             Mp<R> s{};
             s.mu = mk(v[b * 3], v[b * 3 + 1], v[b * 3 + 2]);
             FieldTerms<R> f;
             source_field<R, 1>(s, xv, g, f);
-            E = E + f.d1;
+            E = f.d1;
         }
         vals[0] = E.x;
         vals[1] = E.y;
