@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the FP64 GPU path")
-    ap.add_argument("--workload", default="water4096", choices=["water4096", "clusters4096", "served"])
+    ap.add_argument("--workload", default="water4096", choices=["water4096", "water32000", "clusters4096", "served"])
     ap.add_argument("--rates", default="20,50,100", help="served: arrival rates (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="served: arrival window per rate (s)")
     return ap.parse_args()
@@ -271,6 +271,9 @@ def run_reference(args, dist, rank, ws):
 
 WORKLOADS = {
     "water4096": WORKLOAD,
+    "water32000": ("water32000: 32,000 rigid-geometry waters (96,000 atoms; 32^3 lattice, 768 seeded removals), cubic "
+                   "box 98.6 A, rc 9 A, SPME 108^3 order 5, alpha 0.4/A, PCG 1e-6 D warm start, velocity-Verlet NVE "
+                   "0.5 fs from 300 K"),
     "clusters4096": ("clusters4096: 4096 independent gas-phase water clusters, sizes uniform in 2-32 (70,240 waters, "
                      "210,720 atoms), all pairs within each cluster, no cutoff or Ewald, one context and one launch "
                      "per kernel, PCG 1e-6 D per cluster with warm start, velocity-Verlet NVE 0.5 fs from 300 K"),
@@ -280,15 +283,15 @@ WORKLOADS = {
 def setup(name, pkg, synth, precision, stream):
     """Context, device arrays and unit counts of a workload."""
     import torch
-    if name == "water4096":
-        s, o = synth.make_config("water4096")
+    if name in ("water4096", "water32000"):
+        s, o = synth.make_config(name)
         ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
                                ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"], precision=precision,
                                warm_start=True, stream=stream)
         make_api = lambda: pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"],  # noqa: E731
                                             grid=o["grid"], ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"],
                                             precision=precision, warm_start=True, stream=stream)
-        seed = 2
+        seed = 2 if name == "water4096" else 3
     else:
         s, start, _ = synth.make_cluster_batch(4096, seed=4)
         o = {"rc": None, "cluster_start": start}
@@ -495,7 +498,7 @@ def main():
     # roofline of the real-space permanent kernel (one launch per step)
     P = synth.PARAMS
     pos_h = pos.cpu().numpy().reshape(M, 3, 3)
-    if args.workload == "water4096":
+    if args.workload in ("water4096", "water32000"):
         units = count_units(pos_h, s.box, o["rc"], points_from_pos(pos_h, P))
     else:
         units = count_units_clusters(o["cluster_start"], M)
@@ -503,7 +506,7 @@ def main():
     rp_ms = phases["real_perm"]["ms_per_step"]
     achieved = flops / (rp_ms * 1e-3) / 1e12
     peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    kname = "k_real_perm<float, 1, 0, 0>" if args.workload == "water4096" else "k_real_perm<float, 0, 0, 0>"
+    kname = "k_real_perm<float, 0, 0, 0>" if args.workload == "clusters4096" else "k_real_perm<float, 1, 0, 0>"
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": measured_traffic() if args.workload == "water4096" else None,
