@@ -204,12 +204,14 @@ def points_from_pos(pos, P):
 
 
 def dist_setup():
+    """Process group of a torchrun launch (NCCL on GPUs; gloo without CUDA,
+    for the host-side tests of the multi-rank logic)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
-        dist.init_process_group(backend)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         return dist, rank, ws
     return None, 0, 1
 
@@ -220,12 +222,20 @@ def barrier(dist):
 
 
 def max_over_ranks(dist, v):
+    """The slowest rank's time (the job's time)."""
     if dist is None:
         return v
     import torch
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_value(ws, atoms_per_rank, step_ms):
+    """Whole-job atom-steps/s: every rank advances its own replica of
+    atoms_per_rank atoms by one step in step_ms (the slowest rank's time)."""
+    return ws * atoms_per_rank / (step_ms / 1000.0)
 
 
 def sample_system():
@@ -493,7 +503,7 @@ def main():
         phases[name] = {"ms_per_step": ms / args.steps, "launches": n}
     pkg.sibfa_set_profiling(ctx, False)
     step_ms = max_over_ranks(dist, total_ms) / args.steps
-    value = ws * 3 * M / (step_ms / 1000.0)
+    value = weak_value(ws, 3 * M, step_ms)
 
     # roofline of the real-space permanent kernel (one launch per step)
     P = synth.PARAMS
