@@ -516,7 +516,7 @@ def main():
     rp_ms = phases["real_perm"]["ms_per_step"]
     achieved = flops / (rp_ms * 1e-3) / 1e12
     peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    kname = "k_real_perm<float, 0, 0, 0>" if args.workload == "clusters4096" else "k_real_perm<float, 1, 0, 0>"
+    kname = "k_real_perm<float, 0, 0, 0, 5>" if args.workload == "clusters4096" else "k_real_perm<float, 1, 0, 0, 5>"
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": measured_traffic() if args.workload == "water4096" else None,

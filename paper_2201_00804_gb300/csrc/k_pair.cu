@@ -164,19 +164,20 @@ __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d
     }
 }
 
-// Two launches per molecule set: LPS = false, one block of 5 warps per
-// molecule (target sites; each warp stores its energies, so the blocks need
-// no barrier outside the virial variant); LPS = true, one block of 2 warps
-// (target lone pairs: potential and gradient), which runs on another stream.
-template <typename R, bool PER, bool VIR, bool LPS>
-__global__ void __launch_bounds__(LPS ? 64 : 160, LPS ? 8 : 3) k_real_perm(KParams p, DevState<R> d) {
-    __shared__ double s_w[VIR && !LPS ? NS : 1][9];
-    __shared__ PairQueue<R> qs[LPS ? 2 : NS];
+// One block per molecule whose NW warps take the target points W0 ..
+// W0 + NW - 1: the five sites (W0 = 0) and, in a second launch on another
+// stream, the lone pairs (W0 = 5: potential and gradient).  Each warp stores
+// its energies, so the blocks need no barrier; the virial variant sums the
+// site warps' virials in a fixed order.
+template <typename R, bool PER, bool VIR, int W0, int NW>
+__global__ void __launch_bounds__(32 * NW, NW == 5 ? 3 : (NW == 3 ? 5 : 8)) k_real_perm(KParams p, DevState<R> d) {
+    __shared__ double s_w[VIR ? NW : 1][9];
+    __shared__ PairQueue<R> qs[NW];
     static_assert(sizeof(PairQueue<R>) >= 15 * 33 * sizeof(R), "reduction buffer aliases the queue");
     const int i = blockIdx.x;
     const int wq = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int w = LPS ? NS + wq : wq;   // target point
-    constexpr bool is_lp = LPS;
+    const int w = W0 + wq;   // target point
+    constexpr bool is_lp = W0 >= NS;
     PairQueue<R> &q = qs[wq];
     const V3<R> ot = my_pt(d, i, w);
     Mp<R> mt{};
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(LPS ? 64 : 160, LPS ? 8 : 3) k_real_perm(KPara
         if (dst) *dst += (lane < 12 ? ke : 1.0) * double(t);
         if (VIR) {
             const R wv = warp_transpose_sum<R, 9>(A.W, buf, lane);
-            if (lane < 9) s_w[w][lane] = double(wv);
+            if (lane < 9) s_w[wq][lane] = double(wv);
         }
         // per-warp energies (summed over the five sites in a fixed order by k_pol_energy)
         const double e0 = warp_sum_acc(A.Ue), e1 = warp_sum_acc(A.Up);
@@ -280,11 +281,11 @@ __global__ void __launch_bounds__(LPS ? 64 : 160, LPS ? 8 : 3) k_real_perm(KPara
             d.epw[(i * NS + w) * 2 + 1] = ke * e1;
         }
     }
-    if (VIR && !LPS) {   // the site warps' virials in a fixed order
+    if (VIR) {   // the site warps' virials in a fixed order
         __syncthreads();
         if (threadIdx.x < 9) {
             double v = 0;
-            for (int k = 0; k < NS; ++k) v += s_w[k][threadIdx.x];
+            for (int k = 0; k < NW; ++k) v += s_w[k][threadIdx.x];
             d.vir[i * 9 + threadIdx.x] += ke * v;
         }
     }
@@ -293,20 +294,23 @@ __global__ void __launch_bounds__(LPS ? 64 : 160, LPS ? 8 : 3) k_real_perm(KPara
 template <typename R>
 void launch_real_perm(const KParams &p, DevState<R> &d, Launch L) {
     if (p.vir) {
-        if (p.periodic) k_real_perm<R, true, true, false><<<p.M, 160, 0, L.s>>>(p, d);
-        else k_real_perm<R, false, true, false><<<p.M, 160, 0, L.s>>>(p, d);
-    } else {
-        if (p.periodic) k_real_perm<R, true, false, false><<<p.M, 160, 0, L.s>>>(p, d);
-        else k_real_perm<R, false, false, false><<<p.M, 160, 0, L.s>>>(p, d);
+        if (p.periodic) k_real_perm<R, true, true, 0, NS><<<p.M, 32 * NS, 0, L.s>>>(p, d);
+        else k_real_perm<R, false, true, 0, NS><<<p.M, 32 * NS, 0, L.s>>>(p, d);
+        count(L);
+        return;
     }
+    // the five sites in one block: as two launches (atoms, midpoints) the
+    // second launch's tail cost more than the uneven warps of one block
+    if (p.periodic) k_real_perm<R, true, false, 0, NS><<<p.M, 32 * NS, 0, L.s>>>(p, d);
+    else k_real_perm<R, false, false, 0, NS><<<p.M, 32 * NS, 0, L.s>>>(p, d);
     count(L);
 }
 
 // potential and field of the permanent multipoles at the lone pairs (real space)
 template <typename R>
 void launch_lp_potential(const KParams &p, DevState<R> &d, Launch L) {
-    if (p.periodic) k_real_perm<R, true, false, true><<<p.M, 64, 0, L.s>>>(p, d);
-    else k_real_perm<R, false, false, true><<<p.M, 64, 0, L.s>>>(p, d);
+    if (p.periodic) k_real_perm<R, true, false, NS, 2><<<p.M, 64, 0, L.s>>>(p, d);
+    else k_real_perm<R, false, false, NS, 2><<<p.M, 64, 0, L.s>>>(p, d);
     count(L);
 }
 
@@ -573,13 +577,17 @@ __device__ __forceinline__ void polf_pair(const KParams &p, const DevState<R> &d
     if (VIR) vir_add(A.W, gv, x, R(0.5));
 }
 
-template <typename R, bool PER, bool VIR>
-__global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d) {
-    __shared__ PairQueue<R, PQ_A + PQ_M + PQ_L> qs[5];
+// Target sites W0 .. W0 + NW - 1 of one molecule per block: the atoms and
+// the midpoints in two launches (the virial variant: all five in one block).
+template <typename R, bool PER, bool VIR, int W0, int NW>
+__global__ void __launch_bounds__(32 * NW, NW == 5 ? 3 : (NW == 3 ? 5 : 8)) k_real_polforce(KParams p,
+                                                                                          DevState<R> d) {
+    __shared__ PairQueue<R, PQ_A + PQ_M + PQ_L> qs[NW];
     static_assert(sizeof(PairQueue<R, PQ_A + PQ_M + PQ_L>) >= 12 * 33 * sizeof(R), "reduction buffer");
     const int i = blockIdx.x;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    PairQueue<R, PQ_A + PQ_M + PQ_L> &q = qs[w];
+    const int wq = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = W0 + wq;   // target site
+    PairQueue<R, PQ_A + PQ_M + PQ_L> &q = qs[wq];
     const V3<R> ot = my_pt(d, i, w);
     const Mp<R> mt = load_mp(d.gmp + (i * NS + w) * GMP);
     V3<R> mui = mk(R(0), R(0), R(0));
@@ -661,14 +669,14 @@ __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d)
     else if (lane < 6) dst = d.gmu + (i * NS + w) * 3 + lane - 3;
     else if (lane < 12) dst = d.gth + (i * NS + w) * 6 + lane - 6;
     if (dst) *dst += ke * double(s);
-    if (VIR) {   // the five warps' virials summed in a fixed order
-        __shared__ double s_w[NS][9];
+    if (VIR) {   // the warps' virials summed in a fixed order
+        __shared__ double s_w[NW][9];
         const R wv = warp_transpose_sum<R, 9>(A.W, reinterpret_cast<R *>(&q), lane);
-        if (lane < 9) s_w[w][lane] = double(wv);
+        if (lane < 9) s_w[wq][lane] = double(wv);
         __syncthreads();
         if (threadIdx.x < 9) {
             double v = 0;
-            for (int k = 0; k < NS; ++k) v += s_w[k][threadIdx.x];
+            for (int k = 0; k < NW; ++k) v += s_w[k][threadIdx.x];
             d.vir[i * 9 + threadIdx.x] += ke * v;
         }
     }
@@ -677,13 +685,19 @@ __global__ void __launch_bounds__(160) k_real_polforce(KParams p, DevState<R> d)
 template <typename R>
 void launch_real_polforce(const KParams &p, DevState<R> &d, Launch L) {
     if (p.vir) {
-        if (p.periodic) k_real_polforce<R, true, true><<<p.M, 160, 0, L.s>>>(p, d);
-        else k_real_polforce<R, false, true><<<p.M, 160, 0, L.s>>>(p, d);
-    } else {
-        if (p.periodic) k_real_polforce<R, true, false><<<p.M, 160, 0, L.s>>>(p, d);
-        else k_real_polforce<R, false, false><<<p.M, 160, 0, L.s>>>(p, d);
+        if (p.periodic) k_real_polforce<R, true, true, 0, NS><<<p.M, 32 * NS, 0, L.s>>>(p, d);
+        else k_real_polforce<R, false, true, 0, NS><<<p.M, 32 * NS, 0, L.s>>>(p, d);
+        count(L);
+        return;
     }
-    count(L);
+    if (p.periodic) {
+        k_real_polforce<R, true, false, 0, 3><<<p.M, 96, 0, L.s>>>(p, d);
+        k_real_polforce<R, true, false, 3, 2><<<p.M, 64, 0, L.s>>>(p, d);
+    } else {
+        k_real_polforce<R, false, false, 0, 3><<<p.M, 96, 0, L.s>>>(p, d);
+        k_real_polforce<R, false, false, 3, 2><<<p.M, 64, 0, L.s>>>(p, d);
+    }
+    count(L, 2);
 }
 
 #define INST(R)                                                                                    \
