@@ -57,7 +57,8 @@ __device__ inline void line_weight(const Axis<R, NDER> &A, int i, int &g, R (&w)
 // kind DIP: 3 polarizable atoms with the induced dipoles (d.muR);
 // kind DIP_PCG: the same from the working-precision PCG vector;
 // kind LAMBDA: 2 lone pairs with the charge-transfer lambdas (d.lamR).
-template <typename R>
+// NDER: derivative order the multipoles need (2: quadrupoles, 1: dipoles, 0: charges).
+template <typename R, int NDER>
 __global__ void __launch_bounds__(256) k_spread(KParams p, DevState<R> d, int kind, const double *vec, R *grid) {
     const bool pcg = kind == SPREAD_DIP_PCG;
     if (pcg) {
@@ -75,30 +76,44 @@ __global__ void __launch_bounds__(256) k_spread(KParams p, DevState<R> d, int ki
         const R *v = pcg ? d.vecR : d.muR;
         mp.mu = mk(v[m * 9 + a * 3], v[m * 9 + a * 3 + 1], v[m * 9 + a * 3 + 2]);
     } else mp.q = d.lamR[m * 2 + a];
-    Axis<R, 2> X, Y, Z;
-    axis_weights<R, 2>(p, d, m, pt, 0, X);
-    axis_weights<R, 2>(p, d, m, pt, 1, Y);
-    axis_weights<R, 2>(p, d, m, pt, 2, Z);
+    Axis<R, NDER> X, Y, Z;
+    axis_weights<R, NDER>(p, d, m, pt, 0, X);
+    axis_weights<R, NDER>(p, d, m, pt, 1, Y);
+    axis_weights<R, NDER>(p, d, m, pt, 2, Z);
     int gx, gy;
-    R wx[3], wy[3];
-    line_weight<R, 2>(X, lane / 5, gx, wx);
-    line_weight<R, 2>(Y, lane % 5, gy, wy);
+    R wx[NDER + 1], wy[NDER + 1];
+    line_weight<R, NDER>(X, lane / 5, gx, wx);
+    line_weight<R, NDER>(Y, lane % 5, gy, wy);
     const R third = R(1) / R(3);
     // coefficients of the z weights (0th, 1st, 2nd derivative)
-    const R c0 = mp.q * wx[0] * wy[0] + mp.mu.x * wx[1] * wy[0] + mp.mu.y * wx[0] * wy[1] +
-                 third * (mp.th.xx * wx[2] * wy[0] + mp.th.yy * wx[0] * wy[2] + R(2) * mp.th.xy * wx[1] * wy[1]);
-    const R c1 = mp.mu.z * wx[0] * wy[0] + third * R(2) * (mp.th.xz * wx[1] * wy[0] + mp.th.yz * wx[0] * wy[1]);
-    const R c2 = third * mp.th.zz * wx[0] * wy[0];
+    R c0 = mp.q * wx[0] * wy[0], c1 = R(0), c2 = R(0);
+    if constexpr (NDER >= 1) {
+        c0 += mp.mu.x * wx[1] * wy[0] + mp.mu.y * wx[0] * wy[1];
+        c1 = mp.mu.z * wx[0] * wy[0];
+    }
+    if constexpr (NDER >= 2) {
+        c0 += third * (mp.th.xx * wx[2] * wy[0] + mp.th.yy * wx[0] * wy[2] + R(2) * mp.th.xy * wx[1] * wy[1]);
+        c1 += third * R(2) * (mp.th.xz * wx[1] * wy[0] + mp.th.yz * wx[0] * wy[1]);
+        c2 = third * mp.th.zz * wx[0] * wy[0];
+    }
     const size_t row = ((size_t)gx * p.K[1] + gy) * p.K[2];
 #pragma unroll
-    for (int k = 0; k < ORDER; ++k) atomicAdd(&grid[row + Z.g[k]], c0 * Z.w[0][k] + c1 * Z.w[1][k] + c2 * Z.w[2][k]);
+    for (int k = 0; k < ORDER; ++k) {
+        R v = c0 * Z.w[0][k];
+        if constexpr (NDER >= 1) v += c1 * Z.w[1][k];
+        if constexpr (NDER >= 2) v += c2 * Z.w[2][k];
+        atomicAdd(&grid[row + Z.g[k]], v);
+    }
 }
 
 template <typename R>
 void launch_spread(const KParams &p, DevState<R> &d, int kind, const double *vec, R *grid, Launch L) {
     const int per = kind == SPREAD_PERM ? NS : ((kind == SPREAD_DIP || kind == SPREAD_DIP_PCG) ? 3 : 2);
     const long long threads = (long long)p.M * per * 32;
-    k_spread<R><<<(unsigned)((threads + 255) / 256), 256, 0, L.s>>>(p, d, kind, vec, grid);
+    const unsigned nb = (unsigned)((threads + 255) / 256);
+    if (kind == SPREAD_PERM) k_spread<R, 2><<<nb, 256, 0, L.s>>>(p, d, kind, vec, grid);
+    else if (kind == SPREAD_LAMBDA) k_spread<R, 0><<<nb, 256, 0, L.s>>>(p, d, kind, vec, grid);
+    else k_spread<R, 1><<<nb, 256, 0, L.s>>>(p, d, kind, vec, grid);
     count(L);
 }
 
