@@ -591,7 +591,10 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
         ctx->short_pending = true;
         Phase ph(ctx, "short", ctx->s3);
         DevState<R> ds = short_view(d);
-        launch_short(p, ds, Launch{ctx->s3, &ctx->launches});
+        // periodic: at most 3 blocks per SM, so that the solve's many small
+        // SPME kernels find room on every SM; cluster batches: uncapped (their
+        // short-range work is larger than their solve)
+        launch_short(p, ds, Launch{ctx->s3, &ctx->launches}, 0, p.periodic ? 3 : 0);
     }
     // Lone-pair potentials and then the charge transfer on the fourth stream
     // (the transfer after the reciprocal chain); joined before the

@@ -487,30 +487,50 @@ __global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
     }
 }
 
-// max_blocks > 0 caps the grid (each block then walks several molecules per warp)
+// max_blocks > 0 caps the grid (each block then walks several molecules per
+// warp); max_per_sm > 0 caps the blocks resident per SM by reserving unused
+// dynamic shared memory, which leaves registers on every SM for the kernels
+// of the other streams.
 template <typename R>
-void launch_short(const KParams &p, DevState<R> &d, Launch L, int max_blocks) {
+void launch_short(const KParams &p, DevState<R> &d, Launch L, int max_blocks, int max_per_sm) {
     unsigned nb = (p.M + 3) / 4;
     if (max_blocks > 0 && nb > (unsigned)max_blocks) nb = (unsigned)max_blocks;
+    size_t sm = 0;
+    if (max_per_sm > 0 && !p.vir) {
+        auto k0 = p.periodic ? k_short<R, true, 0, false> : k_short<R, false, 0, false>;
+        auto k1 = p.periodic ? k_short<R, true, 1, false> : k_short<R, false, 1, false>;
+        int dev = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaFuncAttributes fa;
+        cudaFuncGetAttributes(&fa, k0);
+        // one byte more per block than a (max_per_sm + 1)-th block would leave room for
+        const long long need = per_sm / (max_per_sm + 1) + 1 - (long long)fa.sharedSizeBytes;
+        if (need > 0) {
+            sm = (size_t)need;
+            cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        }
+    }
     if (p.vir) {
         if (p.periodic) {
-            k_short<R, true, 0, true><<<nb, 128, 0, L.s>>>(p, d);
-            k_short<R, true, 1, true><<<nb, 128, 0, L.s>>>(p, d);
+            k_short<R, true, 0, true><<<nb, 128, sm, L.s>>>(p, d);
+            k_short<R, true, 1, true><<<nb, 128, sm, L.s>>>(p, d);
         } else {
-            k_short<R, false, 0, true><<<nb, 128, 0, L.s>>>(p, d);
-            k_short<R, false, 1, true><<<nb, 128, 0, L.s>>>(p, d);
+            k_short<R, false, 0, true><<<nb, 128, sm, L.s>>>(p, d);
+            k_short<R, false, 1, true><<<nb, 128, sm, L.s>>>(p, d);
         }
     } else if (p.periodic) {
-        k_short<R, true, 0, false><<<nb, 128, 0, L.s>>>(p, d);
-        k_short<R, true, 1, false><<<nb, 128, 0, L.s>>>(p, d);
+        k_short<R, true, 0, false><<<nb, 128, sm, L.s>>>(p, d);
+        k_short<R, true, 1, false><<<nb, 128, sm, L.s>>>(p, d);
     } else {
-        k_short<R, false, 0, false><<<nb, 128, 0, L.s>>>(p, d);
-        k_short<R, false, 1, false><<<nb, 128, 0, L.s>>>(p, d);
+        k_short<R, false, 0, false><<<nb, 128, sm, L.s>>>(p, d);
+        k_short<R, false, 1, false><<<nb, 128, sm, L.s>>>(p, d);
     }
     count(L, 2);
 }
 
-template void launch_short<float>(const KParams &, DevState<float> &, Launch, int);
-template void launch_short<double>(const KParams &, DevState<double> &, Launch, int);
+template void launch_short<float>(const KParams &, DevState<float> &, Launch, int, int);
+template void launch_short<double>(const KParams &, DevState<double> &, Launch, int, int);
 
 }  // namespace sibfa

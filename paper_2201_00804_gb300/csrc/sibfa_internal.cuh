@@ -796,7 +796,8 @@ template <typename R> void launch_sites(const KParams &p, DevState<R> &d, Launch
 template <typename R> void launch_neighbors(const KParams &p, DevState<R> &d, int ncell[3], Launch L);
 template <typename R> void launch_real_perm(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_lp_potential(const KParams &p, DevState<R> &d, Launch L);
-template <typename R> void launch_short(const KParams &p, DevState<R> &d, Launch L, int max_blocks = 0);
+template <typename R> void launch_short(const KParams &p, DevState<R> &d, Launch L, int max_blocks = 0,
+                                         int max_per_sm = 0);
 template <typename R> void launch_ct(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_intra_perm(const KParams &p, DevState<R> &d, Launch L);
 template <typename R> void launch_real_tmu(const KParams &p, DevState<R> &d, double *out,
