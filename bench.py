@@ -496,6 +496,7 @@ def main():
     torch.cuda.synchronize()
     barrier(dist)
     launches = pkg.sibfa_kernel_launches(ctx) - l0
+    tb, tdone = pkg.sibfa_tuned_shape(ctx)
     phases = {}
     for name in ("sites", "neighbors", "real_perm", "short", "spme_perm", "ct", "pcg", "real_tmu", "real_polforce",
                  "spme_polforce", "finalize"):
@@ -572,6 +573,7 @@ def main():
                    "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{ws}"},
         "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
         "cpu_baseline": cpu, "fp64_gpu_path": fp64, "pcg_iters_mean": float(np.mean(iters)), "phases_ms": phases,
+        "tuned": {"short_blocks_per_sm": tb, "fixed": tdone},
     }
     print(json.dumps(line), flush=True)
 

@@ -132,7 +132,10 @@ typedef struct sibfa_ctx sibfa_ctx;
  * with a conditional while-node; with the environment variable
  * SIBFA_PCG_HOST_LOOP=1 at creation it is driven from the host instead (one
  * launch per kernel and iteration, same arithmetic), which kernel profilers
- * can follow. */
+ * can follow.  The context tunes the launch shape of its short-range kernels
+ * (resident blocks per SM) over its first full evaluations by timing them
+ * and then keeps the fastest; the choice affects scheduling only, never the
+ * results.  SIBFA_TUNE=0 at creation turns the tuning off (fixed shape). */
 sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo,
                           const sibfa_run_opts *opts, sibfa_ctx **out);
 
@@ -183,6 +186,12 @@ sibfa_status sibfa_cluster_terms(sibfa_ctx *ctx, sibfa_energy_terms *terms);
 /* Number of the library's own kernel launches since the context was created
  * (cuFFT executions are not counted). */
 uint64_t sibfa_kernel_launches(const sibfa_ctx *ctx);
+
+/* Launch shape of the short-range kernels chosen by the context's tuning:
+ * *blocks_per_sm = resident blocks per SM (0 = uncapped), *done = 1 once the
+ * tuning has fixed it (0 while candidates are still being timed).  Either
+ * pointer may be NULL.  Returns SIBFA_E_INVALID for a NULL context. */
+sibfa_status sibfa_tuned_shape(const sibfa_ctx *ctx, int *blocks_per_sm, int *done);
 
 /* Optional phase timing with CUDA events recorded on the context stream
  * around each phase of an evaluation: "sites", "neighbors", "real_perm"

@@ -32,6 +32,21 @@ struct sibfa_ctx {
     cudaStream_t s3 = nullptr;
     cudaEvent_t ev_fork3 = nullptr, ev_join3 = nullptr;
     bool short_pending = false;
+    // Autotuner of the short-range launch shape (resident blocks per SM, 0 =
+    // uncapped): the first evaluations after two warm-up ones each run one
+    // candidate and are timed whole on the main stream (two per candidate,
+    // the faster kept); then the fastest candidate is fixed.  The choice
+    // changes only the scheduling, never the arithmetic.
+    struct ShortTuner {
+        bool on = true;
+        int seen = 0;            // evaluations with forces seen
+        int cand = 0;            // candidate being timed
+        int reps = 0;
+        int choice = -1;         // fixed candidate, -1 while tuning
+        float tmin[3] = {1e30f, 1e30f, 1e30f};
+        bool pending = false;    // events of the last timed evaluation not read yet
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+    } tune;
     // lone-pair potentials and charge transfer, forked after the neighbour
     // list and joined before the polarization energy: they run beside the
     // permanent pass and the polarization solve
@@ -383,6 +398,39 @@ sibfa_status join_ct(sibfa_ctx *ctx) {
     return SIBFA_OK;
 }
 
+// Short-range launch shape candidates: resident blocks per SM (0 = uncapped).
+constexpr int kShortCaps[3] = {3, 0, 2};
+constexpr int kTuneWarm = 2, kTuneReps = 2;
+
+int short_cap(const sibfa_ctx *ctx) {
+    const auto &T = ctx->tune;
+    if (!T.on) return ctx->kp.periodic ? 3 : 0;
+    return kShortCaps[T.choice >= 0 ? T.choice : T.cand];
+}
+
+// Reads the last timed evaluation (waiting for it, only while tuning) and
+// advances the candidate; after the last candidate, fixes the fastest.
+void tune_account(sibfa_ctx *ctx) {
+    auto &T = ctx->tune;
+    if (!T.pending) return;
+    T.pending = false;
+    float ms = 0;
+    if (cudaEventSynchronize(T.e1) != cudaSuccess || cudaEventElapsedTime(&ms, T.e0, T.e1) != cudaSuccess) {
+        cudaGetLastError();
+        T.on = false;   // no timing: keep the fixed default shape
+        return;
+    }
+    if (T.seen++ < kTuneWarm) return;
+    T.tmin[T.cand] = std::min(T.tmin[T.cand], ms);
+    if (++T.reps < kTuneReps) return;
+    T.reps = 0;
+    if (++T.cand < 3) return;
+    int best = 0;
+    for (int c = 1; c < 3; ++c)
+        if (T.tmin[c] < T.tmin[best]) best = c;
+    T.choice = best;
+}
+
 sibfa_status join_rec(sibfa_ctx *ctx) {
     CK(cudaEventRecord(ctx->ev_join, ctx->s2));
     CK(cudaStreamWaitEvent(ctx->s, ctx->ev_join, 0));
@@ -546,11 +594,23 @@ template <typename R>
 sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, double tol);
 
 // One evaluation; the short-range stream is joined back on every path.
+// Full evaluations (not the dipole-only solve nor the virial variant) feed
+// the short-range autotuner.
 template <typename R>
 sibfa_status evaluate(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, double tol) {
+    auto &T = ctx->tune;
+    const bool timed = T.on && T.choice < 0 && !dipoles_only && !ctx->kp.vir && !ctx->capturing;
+    if (timed) {
+        tune_account(ctx);
+        if (T.choice < 0) CK(cudaEventRecord(T.e0, ctx->s));
+    }
     const sibfa_status st = evaluate_impl<R>(ctx, want_forces, dipoles_only, tol);
     const sibfa_status sj = join_short(ctx);
     const sibfa_status sc = join_ct(ctx);
+    if (timed && T.choice < 0) {
+        CK(cudaEventRecord(T.e1, ctx->s));
+        T.pending = true;
+    }
     return st ? st : (sj ? sj : sc);
 }
 
@@ -591,10 +651,9 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
         ctx->short_pending = true;
         Phase ph(ctx, "short", ctx->s3);
         DevState<R> ds = short_view(d);
-        // periodic: at most 3 blocks per SM, so that the solve's many small
-        // SPME kernels find room on every SM; cluster batches: uncapped (their
-        // short-range work is larger than their solve)
-        launch_short(p, ds, Launch{ctx->s3, &ctx->launches}, 0, p.periodic ? 3 : 0);
+        // resident blocks per SM (0: uncapped), chosen by the autotuner: a cap
+        // leaves every SM registers for the solve's small kernels
+        launch_short(p, ds, Launch{ctx->s3, &ctx->launches}, 0, short_cap(ctx));
     }
     // Lone-pair potentials and then the charge transfer on the fourth stream
     // (the transfer after the reciprocal chain); joined before the
@@ -930,6 +989,7 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
         cudaStreamCreateWithPriority(&ctx->s3, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
         cudaStreamCreateWithPriority(&ctx->s4, cudaStreamNonBlocking, prio_mid) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork4, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&ctx->tune.e0) != cudaSuccess || cudaEventCreate(&ctx->tune.e1) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join4, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork3, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join3, cudaEventDisableTiming) != cudaSuccess ||
@@ -961,6 +1021,8 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
     {
         const char *e = getenv("SIBFA_PCG_HOST_LOOP");
         if (e && e[0] == '1') ctx->pcg_graph_state = -1;
+        const char *t = getenv("SIBFA_TUNE");
+        if (t && t[0] == '0') ctx->tune.on = false;
     }
     if (opts->periodic) {
         const double cell = opts->rc + 2.6;   // rc + 2 * maximum site extent (1.3 A)
@@ -1134,6 +1196,13 @@ void sibfa_profile_clear(sibfa_ctx *ctx) {
 
 uint64_t sibfa_kernel_launches(const sibfa_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+sibfa_status sibfa_tuned_shape(const sibfa_ctx *ctx, int *blocks_per_sm, int *done) {
+    if (!ctx) return SIBFA_E_INVALID;
+    if (blocks_per_sm) *blocks_per_sm = short_cap(ctx);
+    if (done) *done = (!ctx->tune.on || ctx->tune.choice >= 0) ? 1 : 0;
+    return SIBFA_OK;
+}
+
 void sibfa_destroy(sibfa_ctx *ctx) {
     if (!ctx) return;
     if (ctx->s) cudaStreamSynchronize(ctx->s);
@@ -1142,6 +1211,8 @@ void sibfa_destroy(sibfa_ctx *ctx) {
     if (ctx->s4) cudaStreamSynchronize(ctx->s4);
     if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
     if (ctx->ev_fork4) cudaEventDestroy(ctx->ev_fork4);
+    if (ctx->tune.e0) cudaEventDestroy(ctx->tune.e0);
+    if (ctx->tune.e1) cudaEventDestroy(ctx->tune.e1);
     if (ctx->ev_join4) cudaEventDestroy(ctx->ev_join4);
     if (ctx->ev_fork3) cudaEventDestroy(ctx->ev_fork3);
     if (ctx->ev_join3) cudaEventDestroy(ctx->ev_join3);

@@ -114,6 +114,8 @@ def load_library(path: str = LIB_PATH):
     lib.sibfa_server_destroy.restype = None
     lib.sibfa_kernel_launches.argtypes = [C.c_void_p]
     lib.sibfa_kernel_launches.restype = C.c_uint64
+    lib.sibfa_tuned_shape.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    lib.sibfa_tuned_shape.restype = C.c_int
     lib.sibfa_set_profiling.argtypes = [C.c_void_p, C.c_int]
     lib.sibfa_set_profiling.restype = None
     lib.sibfa_profile_get.argtypes = [C.c_void_p, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int)]
@@ -271,6 +273,15 @@ def sibfa_last_stats(ctx):
 
 def sibfa_kernel_launches(ctx) -> int:
     return int(load_library().sibfa_kernel_launches(ctx))
+
+
+def sibfa_tuned_shape(ctx):
+    """(short-range resident blocks per SM, 0 = uncapped; True once tuning fixed it)."""
+    lib = load_library()
+    b, dn = C.c_int(), C.c_int()
+    st = lib.sibfa_tuned_shape(ctx, C.byref(b), C.byref(dn))
+    _check(lib, ctx, st)
+    return b.value, bool(dn.value)
 
 
 def sibfa_set_profiling(ctx, on: bool):
