@@ -503,12 +503,6 @@ sibfa_status matvec(sibfa_ctx *ctx, DevState<R> &d, const double *vec, Launch L)
     return SIBFA_OK;
 }
 
-// Continue the device-side PCG loop while not converged and below maxit.
-__global__ void k_pcg_cond(cudaGraphConditionalHandle h, const double *scal, int maxit) {
-    const bool more = scal[SC_DONE] == 0.0 && scal[SC_IT] < (double)maxit;
-    cudaGraphSetConditional(h, more ? 1u : 0u);
-}
-
 // One PCG iteration (T p product, step, residual, direction update) captured
 // as the body of a graph while-node; the loop runs on the device and the host
 // waits once per solve.
@@ -536,8 +530,7 @@ sibfa_status build_pcg_graph(sibfa_ctx *ctx, DevState<R> &d, int maxit) {
         ctx->capturing = true;
         Launch L{ctx->s, &ctx->launches};
         sibfa_status sm = matvec(ctx, d, d.pv, L);
-        launch_pcg_step(ctx->kp, d, L);
-        k_pcg_cond<<<1, 1, 0, ctx->s>>>(h, d.scal, maxit);
+        launch_pcg_step(ctx->kp, d, L, h, maxit);   // also sets the loop condition
         ctx->capturing = false;
         const cudaError_t ec = cudaStreamEndCapture(ctx->s, &out);
         if (sm != SIBFA_OK || ec != cudaSuccess) break;
@@ -545,7 +538,7 @@ sibfa_status build_pcg_graph(sibfa_ctx *ctx, DevState<R> &d, int maxit) {
         st = SIBFA_OK;
     } while (0);
     ctx->capturing = false;
-    ctx->pcg_iter_launches = ctx->launches - before + 1;
+    ctx->pcg_iter_launches = ctx->launches - before;
     ctx->launches = before;     // counted per executed iteration instead
     cudaGraphDestroy(g);
     cudaGetLastError();

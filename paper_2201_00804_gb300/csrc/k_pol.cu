@@ -180,12 +180,18 @@ __device__ inline double sum_partials(const double *part, int nb, int stride, do
 //       residual check
 //   (c) p = z + beta p, working-precision copy of p, clear the field
 //       accumulators and the SPME grid for the next product.
+// Inside the solver graph (maxit > 0) it also sets the while-node's
+// condition: another iteration while not converged and below maxit.
 template <typename R>
-__global__ void __launch_bounds__(PB) k_pcg_step(KParams p, DevState<R> d) {
+__global__ void __launch_bounds__(PB) k_pcg_step(KParams p, DevState<R> d, cudaGraphConditionalHandle loop,
+                                                 int maxit) {
     namespace cg = cooperative_groups;
     cg::grid_group grid = cg::this_grid();
     __shared__ double sh[32];
-    if (d.flags[1]) return;   // converged before this launch: uniform over the grid
+    if (d.flags[1]) {   // converged before this launch: uniform over the grid
+        if (maxit > 0 && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(loop, 0u);
+        return;
+    }
     const int n = p.M * 9;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     const int nb = gridDim.x;
@@ -257,6 +263,7 @@ __global__ void __launch_bounds__(PB) k_pcg_step(KParams p, DevState<R> d) {
             d.scal[S_DONE] = 1.0;
             d.flags[1] = 1;
         }
+        if (maxit > 0) cudaGraphSetConditional(loop, (!done && d.scal[S_IT] < (double)maxit) ? 1u : 0u);
     }
     if (done) return;   // uniform: every block computed the same residual
     for (int k = tid; k < n; k += nth) {
@@ -308,7 +315,7 @@ void launch_pcg_first(const KParams &p, DevState<R> &d, Launch L) {
 // Cooperative launch of the PCG step: a grid-stride kernel with as many
 // blocks as can be resident at once (at most one per 256 vector entries).
 template <typename R>
-void launch_pcg_step(const KParams &p, DevState<R> &d, Launch L) {
+void launch_pcg_step(const KParams &p, DevState<R> &d, Launch L, cudaGraphConditionalHandle loop, int maxit) {
     static int per_sm[2] = {0, 0}, n_sm = 0;
     int &ps = per_sm[sizeof(R) == 8];
     if (ps == 0) {
@@ -330,7 +337,7 @@ void launch_pcg_step(const KParams &p, DevState<R> &d, Launch L) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_pcg_step<R>, p, d);
+    cudaLaunchKernelEx(&cfg, k_pcg_step<R>, p, d, loop, maxit);
     count(L);
 }
 
@@ -735,7 +742,7 @@ void launch_md_kick(int M, double *pos, double *vel, const double *inv_mass, con
 #define INST(R)                                                                                        \
     template void launch_pcg_init<R>(const KParams &, DevState<R> &, int, Launch);                     \
     template void launch_pcg_first<R>(const KParams &, DevState<R> &, Launch);                         \
-    template void launch_pcg_step<R>(const KParams &, DevState<R> &, Launch);                          \
+    template void launch_pcg_step<R>(const KParams &, DevState<R> &, Launch, cudaGraphConditionalHandle, int); \
     template void launch_pol_energy<R>(const KParams &, DevState<R> &, Launch);                        \
     template void launch_finalize<R>(const KParams &, DevState<R> &, double *, Launch);                \
     template void launch_merge_rec<R>(const KParams &, DevState<R> &, Launch);                         \

@@ -844,7 +844,9 @@ template <typename R> void launch_influence_copy(const KParams &p, DevState<R> &
 // PCG
 template <typename R> void launch_pcg_init(const KParams &p, DevState<R> &d, int warm, Launch L);
 template <typename R> void launch_pcg_first(const KParams &p, DevState<R> &d, Launch L);
-template <typename R> void launch_pcg_step(const KParams &p, DevState<R> &d, Launch L);
+// maxit > 0: inside the solver graph, also set the loop condition through `loop`
+template <typename R> void launch_pcg_step(const KParams &p, DevState<R> &d, Launch L,
+                                           cudaGraphConditionalHandle loop = 0, int maxit = 0);
 template <typename R> void launch_pol_energy(const KParams &p, DevState<R> &d, Launch L);
 void launch_energy_reduce(int M, const double *epart, const double *epart_r, double *out, Launch L);
 // k-space virial sums of one convolution pass (0: permanent, 1: force pass) fused with the convolution
