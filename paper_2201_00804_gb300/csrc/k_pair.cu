@@ -169,8 +169,11 @@ __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d
 // stream, the lone pairs (W0 = 5: potential and gradient).  Each warp stores
 // its energies, so the blocks need no barrier; the virial variant sums the
 // site warps' virials in a fixed order.
+// Site blocks: 3 resident per SM in periodic systems, 4 in the gas phase
+// (96 registers; measured faster there, slower with the Ewald kernels).
 template <typename R, bool PER, bool VIR, int W0, int NW>
-__global__ void __launch_bounds__(32 * NW, NW == 5 ? 3 : (NW == 3 ? 5 : 8)) k_real_perm(KParams p, DevState<R> d) {
+__global__ void __launch_bounds__(32 * NW, NW == 5 ? (PER ? 3 : 4) : (NW == 3 ? 5 : 8))
+    k_real_perm(KParams p, DevState<R> d) {
     __shared__ double s_w[VIR ? NW : 1][9];
     __shared__ PairQueue<R> qs[NW];
     static_assert(sizeof(PairQueue<R>) >= 15 * 33 * sizeof(R), "reduction buffer aliases the queue");
@@ -579,8 +582,10 @@ __device__ __forceinline__ void polf_pair(const KParams &p, const DevState<R> &d
 
 // Target sites W0 .. W0 + NW - 1 of one molecule per block: the atoms and
 // the midpoints in two launches (the virial variant: all five in one block).
+// The gas-phase launches keep more blocks resident (fewer registers), which
+// measured faster there.
 template <typename R, bool PER, bool VIR, int W0, int NW>
-__global__ void __launch_bounds__(32 * NW, NW == 5 ? 3 : (NW == 3 ? 5 : 8)) k_real_polforce(KParams p,
+__global__ void __launch_bounds__(32 * NW, NW == 5 ? 3 : (NW == 3 ? (PER ? 5 : 6) : (PER ? 8 : 10))) k_real_polforce(KParams p,
                                                                                           DevState<R> d) {
     __shared__ PairQueue<R, PQ_A + PQ_M + PQ_L> qs[NW];
     static_assert(sizeof(PairQueue<R, PQ_A + PQ_M + PQ_L>) >= 12 * 33 * sizeof(R), "reduction buffer");

@@ -339,8 +339,10 @@ __device__ void item_d(const KParams &p, const Scal<R> &S, const ShortTables &T,
 // VIR: also the virial, in the translation-invariance form of the pair
 // kernels (see vir_points_out): per item -1/2 (gradient on i's points) (x)
 // dO_ij, plus sum_p G_p (x) off_p at the end.
+// Resident blocks per SM: periodic 4 (repulsion) and 6 (dispersion), the
+// registers those need; gas phase 5 (measured faster for cluster batches).
 template <typename R, bool PER, int PART, bool VIR>
-__global__ void __launch_bounds__(128) k_short(KParams p, DevState<R> d) {
+__global__ void __launch_bounds__(128, PER ? (PART == 0 ? 4 : 6) : 5) k_short(KParams p, DevState<R> d) {
     __shared__ ShortTables T;
     __shared__ int qbuf[4][SQ_WORDS];
     static_assert(SQ_D + SQ_CAPD <= SQ_WORDS && 15 * 33 * sizeof(R) <= SQ_WORDS * sizeof(int), "queue layout");
