@@ -11,8 +11,6 @@
 
 namespace sibfa {
 
-constexpr int TILE = 32;
-
 template <typename R>
 __device__ inline void symadd(Sym<R> &a, const Sym<R> &b, R s) {
     a.xx += s * b.xx; a.yy += s * b.yy; a.zz += s * b.zz;

@@ -756,34 +756,6 @@ __device__ inline void frame_axes(V3<W> zv, V3<W> xv, V3<W> &ex, V3<W> &ey, V3<W
 // frame carrying site s: O -> 0, H1 and the O-H1 midpoint -> 1, H2 and the O-H2 midpoint -> 2
 __device__ inline int site_frame(int s) { return s == 0 ? 0 : (s == 1 || s == 3 ? 1 : 2); }
 
-template <typename R>
-__device__ inline Mp<double> mp_d(const DevState<R> &d, int m, int s) {
-    const R *g = d.gmp + (m * NS + s) * GMP;
-    Mp<double> o;
-    o.q = g[0];
-    o.mu = mk((double)g[1], (double)g[2], (double)g[3]);
-    o.th = Sym<double>{g[4], g[5], g[6], g[7], g[8], g[9]};
-    return o;
-}
-
-// erf(alpha r)/r weights g_0..g_5 (1/r minus the Ewald real-space kernel)
-__device__ inline void g_erf_d(double r, double alpha, double *g) {
-    double gb[6], ge[6];
-    g_bare<double, 5>(1.0 / r, gb);
-    g_erfc<double, 5>(r, 1.0 / r, alpha, ge);
-    for (int n = 0; n < 6; ++n) g[n] = gb[n] - ge[n];
-}
-
-__device__ inline void addv(double *dst, V3<double> v, double s) {
-    dst[0] += s * v.x;
-    dst[1] += s * v.y;
-    dst[2] += s * v.z;
-}
-__device__ inline void adds(double *dst, const Sym<double> &v, double s) {
-    dst[0] += s * v.xx; dst[1] += s * v.yy; dst[2] += s * v.zz;
-    dst[3] += s * v.xy; dst[4] += s * v.xz; dst[5] += s * v.yz;
-}
-
 // ---------------------------------------------------------------------------
 // Host-side launchers (explicitly instantiated for float and double)
 // ---------------------------------------------------------------------------
