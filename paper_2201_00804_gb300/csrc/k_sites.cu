@@ -19,10 +19,22 @@ __global__ void __launch_bounds__(128) k_sites(KParams p, DevState<R> d) {
     const int m = g >> 3, t = g & 7;
     const bool live = m < p.M;
     float ext = 0.f;
+    // bond vectors r1 = H1 - O, r2 = H2 - O: lane t < 6 takes one FP64
+    // difference (rounded once to R) and the molecule's 8 lanes share them
+    R bc = R(0);
+    if (live && t < 6) {
+        const double *x = d.pos + m * 9;
+        bc = R(x[3 + t] - x[t % 3]);
+    }
+    V3<R> r1, r2;
+    r1.x = __shfl_sync(0xffffffffu, bc, 0, 8);
+    r1.y = __shfl_sync(0xffffffffu, bc, 1, 8);
+    r1.z = __shfl_sync(0xffffffffu, bc, 2, 8);
+    r2.x = __shfl_sync(0xffffffffu, bc, 3, 8);
+    r2.y = __shfl_sync(0xffffffffu, bc, 4, 8);
+    r2.z = __shfl_sync(0xffffffffu, bc, 5, 8);
     if (live) {
         const double *x = d.pos + m * 9;
-        V3<R> r1, r2;
-        bond_vectors(x, r1, r2);
         const R s1 = rsqrt_<R>(dot(r1, r1)), s2 = rsqrt_<R>(dot(r2, r2));
         const int f = t < NS ? site_frame(t) : 0;
         V3<R> zv, xv, ex, ey, ez;
