@@ -103,8 +103,12 @@ enum { SIBFA_PREC_FP64 = 0, SIBFA_PREC_MIXED = 1 };
  * precision: SIBFA_PREC_FP64 (all FP64) or SIBFA_PREC_MIXED (FP32 pair and
  * grid arithmetic, FP64 accumulation across pairs, FP64 PCG scalars,
  * energies and influence function).  stream: a cudaStream_t or NULL for the
- * legacy default stream.  warm_start: reuse the previous call's dipoles as
- * the PCG initial guess. */
+ * legacy default stream; each call is ordered after the work queued on it
+ * and the work queued on it afterwards waits for the call's results.  Inside,
+ * the context runs four streams of its own (main; reciprocal space, highest
+ * priority; short-range terms, lowest; lone-pair potentials and charge
+ * transfer), forked from and joined back into the main one within the call.
+ * warm_start: reuse the previous call's dipoles as the PCG initial guess. */
 typedef struct {
     int periodic;
     double box[3];
