@@ -264,30 +264,40 @@ __global__ void k_cell_count(KParams p, DevState<R> d, int nc0, int nc1, int nc2
     atomicAdd(&d.cell_cursor[c], 1);
 }
 
-// exclusive scan of the cell counts (one block)
+// exclusive scan of the cell counts (one block of 1024 threads): every thread
+// sums a contiguous chunk, the chunk sums are scanned with warp shuffles and
+// one pass over the warp totals, and each thread writes its chunk's starts
 template <typename R>
-__global__ void k_cell_scan(DevState<R> d, int ncell) {
-    __shared__ int part[1024];
-    const int t = threadIdx.x;
+__global__ void __launch_bounds__(1024) k_cell_scan(DevState<R> d, int ncell) {
+    __shared__ int wsum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int per = (ncell + blockDim.x - 1) / blockDim.x;
     const int a = t * per, b = min(ncell, a + per);
     int s = 0;
     for (int k = a; k < b; ++k) s += d.cell_cursor[k];
-    part[t] = s;
+    int incl = s;   // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[w] = incl;
     __syncthreads();
-    if (t == 0) {
-        int acc = 0;
-        for (int k = 0; k < (int)blockDim.x; ++k) {
-            int v = part[k];
-            part[k] = acc;
-            acc += v;
+    if (w == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        int v = lane < nw ? wsum[lane] : 0, iv = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, iv, o);
+            if (lane >= o) iv += u;
         }
-        d.cell_start[ncell] = acc;
+        if (lane < nw) wsum[lane] = iv - v;   // exclusive warp offsets
+        if (lane == nw - 1) d.cell_start[ncell] = iv;
     }
     __syncthreads();
-    int acc = part[t];
+    int acc = wsum[w] + incl - s;
     for (int k = a; k < b; ++k) {
-        int v = d.cell_cursor[k];
+        const int v = d.cell_cursor[k];
         d.cell_start[k] = acc;
         acc += v;
         d.cell_cursor[k] = 0;
