@@ -3,8 +3,10 @@
 
 Workload: the 4096-water box (12,288 atoms, 49.66 A, rc 9 A, SPME 64^3 order
 5, alpha 0.4 A^-1), mixed precision (FP32 pair and grid arithmetic, FP64
-accumulation and solver scalars), PCG tolerance 1e-6 D with warm start,
-velocity-Verlet NVE at 0.5 fs from 300 K Maxwell velocities.  A step is one
+accumulation and solver scalars), PCG tolerance 1e-6 D with warm start
+(by default the initial guess extrapolates the dipoles of the last four
+steps; --warm-start 1 takes the previous step's), velocity-Verlet NVE at
+0.5 fs from 300 K Maxwell velocities.  A step is one
 velocity-Verlet step: one full energy + force evaluation (sites, neighbour
 list, real-space pair terms, SPME, charge transfer, polarization solve,
 forces) plus the two half kicks.  Metric: atom-steps/s.
@@ -62,6 +64,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the FP64 GPU path")
+    ap.add_argument("--warm-start", type=int, default=4, choices=[1, 2, 3, 4],
+                    help="PCG initial guess along the trajectory: 1 previous dipoles, 2-4 extrapolation through "
+                         "the last 2-4 steps' dipoles")
     ap.add_argument("--workload", default="water4096", choices=["water4096", "water32000", "clusters4096", "served"])
     ap.add_argument("--rates", default="20,50,100", help="served: arrival rates (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="served: arrival window per rate (s)")
@@ -290,25 +295,30 @@ WORKLOADS = {
 }
 
 
-def setup(name, pkg, synth, precision, stream):
+GUESS = {1: "previous step's dipoles", 2: "linear extrapolation of the last 2 steps' dipoles",
+         3: "quadratic extrapolation of the last 3 steps' dipoles",
+         4: "cubic extrapolation of the last 4 steps' dipoles"}
+
+
+def setup(name, pkg, synth, precision, stream, warm=1):
     """Context, device arrays and unit counts of a workload."""
     import torch
     if name in ("water4096", "water32000"):
         s, o = synth.make_config(name)
         ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
                                ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"], precision=precision,
-                               warm_start=True, stream=stream)
+                               warm_start=warm, stream=stream)
         make_api = lambda: pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"],  # noqa: E731
                                             grid=o["grid"], ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"],
-                                            precision=precision, warm_start=True, stream=stream)
+                                            precision=precision, warm_start=warm, stream=stream)
         seed = 2 if name == "water4096" else 3
     else:
         s, start, _ = synth.make_cluster_batch(4096, seed=4)
         o = {"rc": None, "cluster_start": start}
         ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=False, pcg_tol_D=1e-6, precision=precision,
-                               warm_start=True, stream=stream, cluster_start=start)
+                               warm_start=warm, stream=stream, cluster_start=start)
         make_api = lambda: pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=False, pcg_tol_D=1e-6,  # noqa: E731
-                                            precision=precision, warm_start=True, stream=stream,
+                                            precision=precision, warm_start=warm, stream=stream,
                                             cluster_start=start)
         seed = 4
     pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
@@ -476,7 +486,7 @@ def main():
     torch.cuda.set_device(local)
     build.build()
     stream = torch.cuda.current_stream()
-    s, o, ctx, make_api, pos, vel, masses = setup(args.workload, pkg, synth, pkg.PREC_MIXED, stream)
+    s, o, ctx, make_api, pos, vel, masses = setup(args.workload, pkg, synth, pkg.PREC_MIXED, stream, args.warm_start)
     M = s.n_mol
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     # The random starting structures are far from equilibrium (close
@@ -547,7 +557,7 @@ def main():
     # comparison the metric names): a few steps, same timing method.
     fp64 = None
     if not args.no_fp64_path:
-        _, _, c64, _, p64, v64, m64 = setup(args.workload, pkg, synth, pkg.PREC_FP64, stream)
+        _, _, c64, _, p64, v64, m64 = setup(args.workload, pkg, synth, pkg.PREC_FP64, stream, args.warm_start)
         p64.copy_(pos0)
         v64.copy_(vel0)
         for _ in range(2):
@@ -570,7 +580,8 @@ def main():
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "precision": "FP32 pair/grid arithmetic, FP64 accumulation",
-                   "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{ws}"},
+                   "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{ws}",
+                   "pcg_initial_guess": GUESS[args.warm_start]},
         "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
         "cpu_baseline": cpu, "fp64_gpu_path": fp64, "pcg_iters_mean": float(np.mean(iters)), "phases_ms": phases,
         "tuned": {"short_blocks_per_sm": tb, "fixed": tdone},

@@ -12,6 +12,7 @@
 #include <cstdlib>
 
 #include "sibfa_internal.cuh"
+#include "pcg_guess.cuh"
 #include "server_internal.h"
 
 using namespace sibfa;
@@ -79,6 +80,10 @@ struct sibfa_ctx {
     int last_iters = 0;
     double last_resid = 0;
     bool have_mu = false;
+    // converged dipoles of the last full evaluations (warm_start >= 2): four
+    // slots of capacity * 9 doubles, the newest at hist_head - 1
+    double *mu_hist = nullptr;
+    int hist_n = 0, hist_head = 0;
     bool md_forces_valid = false;
     // optional per-phase timing with CUDA events on the context stream
     bool profiling = false;
@@ -545,11 +550,41 @@ sibfa_status build_pcg_graph(sibfa_ctx *ctx, DevState<R> &d, int maxit) {
     return st;
 }
 
+// Initial guess from the stored solutions of full evaluations: the
+// polynomial through the last n of them (times -1..-n) taken at time 0,
+// coefficients (-1)^(j+1) C(n, j) for the j-th newest.
+MuGuess mu_guess(const sibfa_ctx *ctx, bool full) {
+    MuGuess g{};
+    const int want = ctx->opts.warm_start;
+    if (!full || want < 2 || ctx->hist_n < 1) return g;
+    static const double C[5][4] = {{0, 0, 0, 0}, {1, 0, 0, 0}, {2, -1, 0, 0}, {3, -3, 1, 0}, {4, -6, 4, -1}};
+    g.n = std::min(want, ctx->hist_n);
+    const size_t stride = (size_t)ctx->capacity * 9;
+    for (int j = 0; j < g.n; ++j) {
+        g.h[j] = ctx->mu_hist + (size_t)((ctx->hist_head - 1 - j + 8) % 4) * stride;
+        g.c[j] = C[g.n][j];
+    }
+    return g;
+}
+
+// Store the converged dipoles of a full evaluation (stream-ordered after the solve).
+sibfa_status push_mu(sibfa_ctx *ctx, const double *mu, bool full) {
+    if (!full || ctx->opts.warm_start < 2) return SIBFA_OK;
+    const size_t stride = (size_t)ctx->capacity * 9;
+    CK(cudaMemcpyAsync(ctx->mu_hist + (size_t)ctx->hist_head * stride, mu, (size_t)ctx->M * 9 * sizeof(double),
+                       cudaMemcpyDeviceToDevice, ctx->s));
+    ctx->hist_head = (ctx->hist_head + 1) % 4;
+    ctx->hist_n = std::min(ctx->hist_n + 1, 4);
+    return SIBFA_OK;
+}
+
 template <typename R>
-sibfa_status solve(sibfa_ctx *ctx, DevState<R> &d, double tol, Launch L) {
+sibfa_status solve(sibfa_ctx *ctx, DevState<R> &d, double tol, Launch L, bool full) {
     const KParams &p = ctx->kp;
     const int warm = (ctx->opts.warm_start && ctx->have_mu) ? 1 : 0;
-    launch_pcg_init(p, d, warm, L);
+    const MuGuess g = mu_guess(ctx, full);
+    if (g.n > 0) launch_pcg_init_guess(p, d, g, L);
+    else launch_pcg_init(p, d, warm, L);
     sibfa_status st = matvec(ctx, d, d.mu, L);
     if (st) return st;
     launch_pcg_first(p, d, L);
@@ -565,7 +600,7 @@ sibfa_status solve(sibfa_ctx *ctx, DevState<R> &d, double tol, Launch L) {
         CK(cudaMemcpyAsync(ctx->h_scal, d.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
         ctx->pcg_graph_solves += 1;
         ctx->have_mu = true;
-        return SIBFA_OK;
+        return push_mu(ctx, d.mu, full);
     }
     for (;;) {
         CK(cudaMemcpyAsync(h, d.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
@@ -579,7 +614,7 @@ sibfa_status solve(sibfa_ctx *ctx, DevState<R> &d, double tol, Launch L) {
     std::memcpy(ctx->h_scal, h, 16 * sizeof(double));
     ctx->have_mu = true;
     launch_pcg_check(d.scal, d.flags, L);
-    return SIBFA_OK;
+    return push_mu(ctx, d.mu, full);
 }
 
 // One evaluation on the positions already in d.pos.
@@ -678,7 +713,7 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
     }
     {
         Phase ph(ctx, "pcg");
-        st = solve(ctx, d, tol, L);
+        st = solve(ctx, d, tol, L, !dipoles_only);
     }
     if (st == SIBFA_E_CUDA) return st;
     sibfa_status st_solve = st;
@@ -944,6 +979,10 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
         g_create_error = "sibfa_create: unknown precision";
         return SIBFA_E_INVALID;
     }
+    if (opts->warm_start < 0 || opts->warm_start > 4) {
+        g_create_error = "sibfa_create: warm_start must be 0..4";
+        return SIBFA_E_INVALID;
+    }
     if (opts->periodic) {
         if (opts->order != 5 && opts->order != 0) {
             g_create_error = "sibfa_create: only B-spline order 5 is implemented";
@@ -1027,6 +1066,10 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
         if (st) break;
         st = dalloc(ctx, &ctx->d_energy, 32);
         if (st) break;
+        if (opts->warm_start >= 2) {
+            st = dalloc(ctx, &ctx->mu_hist, (size_t)4 * ctx->capacity * 9);
+            if (st) break;
+        }
         if (cudaMallocHost((void **)&ctx->h_pin, ((size_t)ctx->M * 9 * 2 + 64) * sizeof(double)) != cudaSuccess ||
             cudaMallocHost((void **)&ctx->h_scal, 16 * sizeof(double)) != cudaSuccess) {
             ctx->err = "cudaMallocHost failed";
@@ -1273,6 +1316,7 @@ sibfa_status ctx_set_batch(sibfa_ctx *ctx, int M, int n_cl, const int *cluster_s
     ctx->kp.M = M;
     ctx->kp.n_cl = n_cl;
     ctx->md_forces_valid = false;
+    ctx->hist_n = 0;   // stored dipoles belong to the previous batch
     // the device-side PCG loop is captured for one size: drive the loop from the host
     if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
     ctx->pcg_exec = nullptr;

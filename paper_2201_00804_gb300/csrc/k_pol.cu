@@ -7,6 +7,7 @@
 #include <algorithm>
 
 #include "sibfa_internal.cuh"
+#include "pcg_guess.cuh"
 
 namespace sibfa {
 
@@ -76,12 +77,18 @@ __device__ inline void zero_grid(const KParams &p, const DevState<R> &d, size_t 
 }
 
 template <typename R>
-__global__ void k_pcg_init(KParams p, DevState<R> d, int warm) {
+__global__ void k_pcg_init(KParams p, DevState<R> d, int warm, MuGuess g) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     zero_grid(p, d, k, (size_t)gridDim.x * blockDim.x);
     if (p.n_cl > 1 && k < p.n_cl) d.cl_rr[k] = 0.0;
     if (k >= p.M * 9) return;
-    if (!warm) d.mu[k] = apol(p, k) * d.efield[k];
+    if (g.n > 0) {
+        double m = 0;
+        for (int j = 0; j < g.n; ++j) m += g.c[j] * g.h[j][k];
+        d.mu[k] = m;
+    } else if (!warm) {
+        d.mu[k] = apol(p, k) * d.efield[k];
+    }
     d.vecR[k] = R(d.mu[k]);
     d.efp[k] = 0.0;
     d.efp_r[k] = 0.0;
@@ -304,7 +311,12 @@ void launch_begin(double *scal, int *flags, double tol_D, Launch L) {
 
 template <typename R>
 void launch_pcg_init(const KParams &p, DevState<R> &d, int warm, Launch L) {
-    k_pcg_init<R><<<nblk(p.M * 9), PB, 0, L.s>>>(p, d, warm);
+    k_pcg_init<R><<<nblk(p.M * 9), PB, 0, L.s>>>(p, d, warm, MuGuess{});
+    count(L);
+}
+template <typename R>
+void launch_pcg_init_guess(const KParams &p, DevState<R> &d, MuGuess g, Launch L) {
+    k_pcg_init<R><<<nblk(p.M * 9), PB, 0, L.s>>>(p, d, 1, g);
     count(L);
 }
 template <typename R>
@@ -741,6 +753,7 @@ void launch_md_kick(int M, double *pos, double *vel, const double *inv_mass, con
 
 #define INST(R)                                                                                        \
     template void launch_pcg_init<R>(const KParams &, DevState<R> &, int, Launch);                     \
+    template void launch_pcg_init_guess<R>(const KParams &, DevState<R> &, MuGuess, Launch);           \
     template void launch_pcg_first<R>(const KParams &, DevState<R> &, Launch);                         \
     template void launch_pcg_step<R>(const KParams &, DevState<R> &, Launch, cudaGraphConditionalHandle, int); \
     template void launch_pol_energy<R>(const KParams &, DevState<R> &, Launch);                        \

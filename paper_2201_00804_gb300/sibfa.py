@@ -163,7 +163,9 @@ def sibfa_create(params: dict, mp_local: np.ndarray, *, periodic: bool, box=None
     """Create a context.  mp_local: (n_mol, 5, 10) float64 host array.
     stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None.
     cluster_start: optional (n_clusters + 1) ints splitting a gas-phase batch
-    into independent clusters of consecutive molecules."""
+    into independent clusters of consecutive molecules.
+    warm_start: PCG initial guess, False/0 direct field, True/1 previous
+    dipoles, 2..4 extrapolation through the last 2..4 full evaluations."""
     lib = load_library()
     P = sibfa_params(*[float(params[n]) for n in PARAM_FIELDS])
     mp = np.ascontiguousarray(mp_local, dtype=np.float64)
@@ -186,7 +188,7 @@ def sibfa_create(params: dict, mp_local: np.ndarray, *, periodic: bool, box=None
     o.pcg_tol_D = float(pcg_tol_D)
     o.pcg_max_iter = int(pcg_max_iter)
     o.precision = int(precision)
-    o.warm_start = 1 if warm_start else 0
+    o.warm_start = int(warm_start)
     if stream is not None:
         o.stream = int(getattr(stream, "cuda_stream", stream))
     o.md_k_bond, o.md_r0, o.md_k_angle, o.md_theta0_deg = md_k_bond, md_r0, md_k_angle, md_theta0_deg

@@ -14,7 +14,9 @@ from .water import (  # noqa: F401
     make_box,
     make_cluster,
     make_cluster_batch,
+    make_cluster_sizes,
     make_dimer,
+    make_ortho_box,
     make_config,
     maxwell_velocities,
     random_rotation,

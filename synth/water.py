@@ -272,6 +272,40 @@ def make_box(n_side: int, box_len: float, seed: int, n_remove: int = 0,
                   meta={"kind": "box", "n_side": n_side, "seed": seed})
 
 
+def make_ortho_box(n_sides, box_lens, seed: int, jitter: float = 0.4, min_oo: float = 2.5) -> System:
+    """Waters on a jittered nx x ny x nz lattice in an orthorhombic periodic
+    box of edges box_lens (a non-cubic cell for the per-axis paths)."""
+    rng = np.random.default_rng(seed)
+    n = np.asarray(n_sides, dtype=np.int64)
+    box = np.asarray(box_lens, dtype=np.float64)
+    a = box / n
+    idx = np.stack(np.meshgrid(np.arange(n[0]), np.arange(n[1]), np.arange(n[2]), indexing="ij"),
+                   -1).reshape(-1, 3)
+    centers = (idx + 0.5) * a
+
+    def propose(k):
+        return centers[k] + (rng.uniform(-jitter, jitter, size=3) if jitter > 0 else 0.0)
+
+    pos = _place_molecules(rng, propose, centers.shape[0], box, min_oo)
+    mp = _random_multipoles(rng, pos.shape[0])
+    return System(pos=pos, mp_local=mp, box=box,
+                  meta={"kind": "ortho_box", "n_sides": tuple(int(v) for v in n), "seed": seed})
+
+
+def make_cluster_sizes(sizes, seed: int):
+    """A gas-phase batch with the given cluster sizes (in order); each cluster
+    is make_cluster with its own seed drawn from `seed`.  Returns the same
+    triple as make_cluster_batch."""
+    rng = np.random.default_rng(seed)
+    seeds = rng.integers(0, 2**31 - 1, size=len(sizes))
+    parts = [make_cluster(int(n), seed=int(s)) for n, s in zip(sizes, seeds)]
+    start = np.zeros(len(sizes) + 1, dtype=np.int32)
+    start[1:] = np.cumsum(sizes)
+    allsys = System(pos=np.concatenate([c.pos for c in parts]), mp_local=np.concatenate([c.mp_local for c in parts]),
+                    box=None, meta={"kind": "cluster_batch", "n_clusters": len(sizes), "seed": seed})
+    return allsys, start, parts
+
+
 def make_cluster(n_mol: int, seed: int, min_oo: float = 2.5) -> System:
     """Gas-phase cluster: O uniform in a sphere of radius 3 n^(1/3) A."""
     rng = np.random.default_rng(seed)

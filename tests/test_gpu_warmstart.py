@@ -1,0 +1,76 @@
+"""PCG initial guesses along an MD trajectory (216-water box, FP64 path,
+tolerance 1e-10 D): the direct-field guess (0), the previous dipoles (1)
+and the cubic extrapolation through the last four full evaluations (4) all
+converge to the same energies, forces and dipoles; the extrapolation needs
+no more iterations than the previous dipoles once its history is full; a
+dipole-only solve in between does not enter that history."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import TERMS
+
+pytestmark = pytest.mark.gpu
+
+N_STEPS = 10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_00804_gb300 import build
+    build.build()
+
+
+def _ctx(pkg, s, o, warm):
+    return pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
+                            ewald_alpha=o["ewald"], pcg_tol_D=1e-10, precision=pkg.PREC_FP64, warm_start=warm)
+
+
+def test_guesses_converge_to_the_same_solution():
+    import torch
+    import paper_2201_00804_gb300 as pkg
+    s, o = synth.make_config("water216")
+    # a short NVE trajectory (0.5 fs steps) from a context of its own
+    pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
+    vel = torch.tensor(synth.maxwell_velocities(s, 300.0, seed=7).reshape(-1), dtype=torch.float64, device="cuda")
+    masses = torch.tensor(s.masses().reshape(-1), dtype=torch.float64, device="cuda")
+    md = _ctx(pkg, s, o, 1)
+    snaps = []
+    try:
+        for _ in range(N_STEPS):
+            pkg.sibfa_md_steps(md, pos, vel, masses, 0.5, 1)
+            snaps.append(pos.clone())
+    finally:
+        pkg.sibfa_destroy(md)
+    res = {}
+    for warm in (0, 1, 4):
+        ctx = _ctx(pkg, s, o, warm)
+        out = []
+        try:
+            for k, x in enumerate(snaps):
+                F = torch.zeros_like(x)
+                e = pkg.sibfa_energy_forces(ctx, x, F)
+                it = pkg.sibfa_last_stats(ctx)[0]
+                if k == N_STEPS // 2:
+                    # a dipole-only solve at other positions between two steps
+                    mu = torch.zeros_like(x)
+                    pkg.sibfa_solve_dipoles(ctx, snaps[0], mu, 1e-10)
+                torch.cuda.synchronize()
+                out.append((e, F.cpu().numpy(), it))
+        finally:
+            pkg.sibfa_destroy(ctx)
+        res[warm] = out
+    for k in range(N_STEPS):
+        e0, F0, _ = res[0][k]
+        mag = sum(abs(e0[t]) for t in TERMS)
+        for warm in (1, 4):
+            e, F, _ = res[warm][k]
+            for t in TERMS:
+                assert abs(e[t] - e0[t]) <= 1e-9 * mag, (warm, k, t, e[t], e0[t])
+            assert np.abs(F - F0).max() <= 1e-7 * np.abs(F0).max(), (warm, k)
+    it1 = sum(r[2] for r in res[1][4:])
+    it4 = sum(r[2] for r in res[4][4:])
+    assert it4 <= it1, ([r[2] for r in res[1]], [r[2] for r in res[4]])
