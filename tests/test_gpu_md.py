@@ -1,0 +1,105 @@
+"""The device velocity-Verlet driver (sibfa_md_steps) against a host
+integration of the same trajectory: two 0.5 fs steps of the 216-water box,
+FP64 path.  The host side takes the intermolecular forces from
+sibfa_energy_forces on a second context and the intramolecular support
+forces as central finite differences of the energy the header defines
+(k_bond (r - r0)^2 per O-H bond + k_angle (theta - theta0)^2 per angle), and
+converts (kcal/mol/A)/amu to A/fs^2 from the unit definitions.  Positions,
+velocities and the reported energy terms of the last step must agree."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import TERMS
+
+pytestmark = pytest.mark.gpu
+
+KB, R0, KA, TH0_DEG = 529.6, 0.9572, 34.05, 104.52
+DT_FS = 0.5
+# 1 kcal/mol/A per amu: 4184 J/mol / (1e-3 kg/mol) / 1e-10 m, in A/fs^2
+ACC = 4184.0 / 1e-3 / 1e-10 * 1e10 * 1e-30
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_00804_gb300 import build
+    build.build()
+
+
+def intra_energy(x):
+    """Per-molecule support energy; x (M, 3, 3)."""
+    a, b = x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]
+    ra, rb = np.linalg.norm(a, axis=-1), np.linalg.norm(b, axis=-1)
+    th = np.arccos(np.clip((a * b).sum(-1) / (ra * rb), -1.0, 1.0))
+    return KB * ((ra - R0) ** 2 + (rb - R0) ** 2) + KA * (th - math.radians(TH0_DEG)) ** 2
+
+
+def intra_forces(x, h=1e-5):
+    """-dE/dx by central differences; molecules are independent, so one
+    coordinate is displaced in every molecule at once."""
+    F = np.zeros_like(x)
+    for k in range(3):
+        for c in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[:, k, c] += h
+            xm[:, k, c] -= h
+            F[:, k, c] = -(intra_energy(xp) - intra_energy(xm)) / (2 * h)
+    return F
+
+
+def _ctx(pkg, s, o):
+    return pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
+                            ewald_alpha=o["ewald"], pcg_tol_D=1e-11, precision=pkg.PREC_FP64, warm_start=0,
+                            md_k_bond=KB, md_r0=R0, md_k_angle=KA, md_theta0_deg=TH0_DEG)
+
+
+def test_velocity_verlet_matches_host_integration():
+    import torch
+    import paper_2201_00804_gb300 as pkg
+    s, o = synth.make_config("water216")
+    M = s.n_mol
+    m = s.masses()                                     # (M, 3) amu
+    v0 = synth.maxwell_velocities(s, 300.0, seed=11)   # (M, 3, 3) A/fs
+    ctx_f = _ctx(pkg, s, o)
+    try:
+        def inter(x):
+            xd = torch.tensor(x.reshape(-1), dtype=torch.float64, device="cuda")
+            F = torch.zeros_like(xd)
+            e = pkg.sibfa_energy_forces(ctx_f, xd, F)
+            torch.cuda.synchronize()
+            return F.cpu().numpy().reshape(M, 3, 3), e
+
+        x, v = s.pos.copy(), v0.copy()
+        F = inter(x)[0] + intra_forces(x)
+        for _ in range(2):
+            v = v + 0.5 * DT_FS * ACC * F / m[:, :, None]
+            x = x + DT_FS * v
+            Fi, e_host = inter(x)
+            F = Fi + intra_forces(x)
+            v = v + 0.5 * DT_FS * ACC * F / m[:, :, None]
+    finally:
+        pkg.sibfa_destroy(ctx_f)
+
+    pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
+    vel = torch.tensor(v0.reshape(-1), dtype=torch.float64, device="cuda")
+    masses = torch.tensor(m.reshape(-1), dtype=torch.float64, device="cuda")
+    ctx = _ctx(pkg, s, o)
+    try:
+        e_dev = pkg.sibfa_md_steps(ctx, pos, vel, masses, DT_FS, 2)
+        torch.cuda.synchronize()
+    finally:
+        pkg.sibfa_destroy(ctx)
+    xd = pos.cpu().numpy().reshape(M, 3, 3)
+    vd = vel.cpu().numpy().reshape(M, 3, 3)
+    moved = np.abs(x - s.pos).max()
+    assert moved > 1e-3                                 # the step did move the atoms
+    assert np.abs(xd - x).max() < 1e-9, np.abs(xd - x).max()
+    assert np.abs(vd - v).max() < 1e-7 * np.abs(v).max(), np.abs(vd - v).max()
+    mag = sum(abs(e_host[k]) for k in TERMS)
+    for k in TERMS:
+        assert abs(e_dev[k] - e_host[k]) <= 1e-9 * mag, (k, e_dev[k], e_host[k])
