@@ -1,6 +1,6 @@
 """Oracle pins for the short-range terms: penetration limits, charge-transfer
-sign, scaling and decay, repulsion sign and decay, and the C6 tail of the
-dispersion."""
+sign, scaling and decay, repulsion sign and decay, the C6 tail of the
+dispersion and its asymptotic coefficient in closed form."""
 import numpy as np
 
 import oracle
@@ -66,3 +66,27 @@ def test_dispersion_c6_tail():
     assert abs(e2 / e1 * 64.0 - 1.0) < 0.01
     x = _terms(_dimer_at(1.0))["xdisp"]
     assert x > 0
+
+
+def test_dispersion_asymptotic_coefficient():
+    """Far apart every damping ratio d -> -1 and every reduced distance
+    m -> R / (2 sqrt(rv rv)), so R^6 E_disp tends to
+    64 C6 e^(gamma6) sum_pairs pref (rv_i rv_j)^3 with the pair prefactors
+    -beta_i beta_j (atom-atom), -n^2/4 (lone pair-lone pair) and -delta/2
+    (atom-lone pair, both ways).  R^6 E is extrapolated to 1/R -> 0 from
+    R = 2000 and 4000 A (its leading correction is linear in 1/R)."""
+    P = PARAMS
+    ra = np.array([P["rvdw_disp_o"], P["rvdw_disp_h"], P["rvdw_disp_h"]])
+    ba = np.array([P["beta_o"], P["beta_h"], P["beta_h"]])
+    rl = np.array([P["rvdw_disp_lp"]] * 2)
+    s_at = float((ba * ra ** 3).sum())
+    s_r = float((ra ** 3).sum())
+    s_lp = float((rl ** 3).sum())
+    pair_sum = -s_at ** 2 - P["n_lp"] ** 2 / 4.0 * s_lp ** 2 - P["disp_delta"] * s_r * s_lp
+    ref = 64.0 * P["c6"] * np.exp(P["gamma6"]) * pair_sum
+
+    def r6e(R):
+        return _terms(_dimer_at(R / 2.91))["disp"] * R ** 6
+
+    lim = 2.0 * r6e(4000.0) - r6e(2000.0)
+    assert abs(lim / ref - 1.0) < 1e-4, (lim, ref)
