@@ -113,7 +113,8 @@ enum { SIBFA_PREC_FP64 = 0, SIBFA_PREC_MIXED = 1 };
  * converged dipoles of the last warm_start full evaluations (energy and
  * forces, equally spaced in time as in an MD run), extrapolated one step
  * ahead (linear, quadratic, cubic); with fewer stored it uses as many as it
- * has; a dipole-only solve neither uses nor feeds that history.  Every
+ * has; a dipole-only solve neither uses nor feeds that history, and
+ * sibfa_minimize clears it when it returns.  Every
  * choice converges to the same tolerance; only the iteration count differs.
  * Other values: SIBFA_E_INVALID. */
 typedef struct {

@@ -1137,6 +1137,7 @@ static sibfa_status minimize_impl(sibfa_ctx *ctx, double *pos, int n, double cap
     if (st_e) return st_e;
     CK(cudaStreamSynchronize(ctx->s));
     ctx->md_forces_valid = false;
+    ctx->hist_n = 0;   // relaxation steps are not a trajectory to extrapolate along
     solve_stats(ctx);
     {
         sibfa_status fl = check_flags(ctx, *(int *)(h + 16));
