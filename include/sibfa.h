@@ -221,23 +221,29 @@ void sibfa_profile_clear(sibfa_ctx *ctx);
  * counterpart: this entry point exists for callers that cannot allocate.)
  *
  * Some callers must not allocate device memory during a step: code running
- * under a memory pool or arena that owns all device memory, plugins of host
- * MD engines that forbid cudaMalloc/cudaFree inside their force callback
- * (an allocation can synchronize the device and stall other streams), and
- * code that records its launches into a CUDA graph.  This call computes, on
- * `stream`, the same multipole (elec) and penetration (pen) energies that
- * sibfa_energy_forces reports for a gas-phase cluster, using only a fixed
- * file-scope device array as scratch (about 270 KB, held by every GPU that
- * loads the library until the process exits).
+ * under a memory pool or arena that owns all device memory, and plugins of
+ * host MD engines that forbid cudaMalloc/cudaFree inside their force
+ * callback (an allocation can synchronize the device and stall other
+ * streams).  This call computes, on `stream`, the same multipole (elec) and
+ * penetration (pen) energies that sibfa_energy_forces reports for a
+ * gas-phase cluster, using only a fixed file-scope device array as scratch
+ * (about 270 KB, held by every GPU that loads the library until the process
+ * exits).
  *
  * n_mol: 1..512 waters (larger clusters are rejected with SIBFA_E_INVALID).
  * pos: DEVICE pointer, n_mol*9 doubles (O, H1, H2).  mp_local: DEVICE
  * pointer, n_mol*5*10 doubles (local-frame multipoles as in sibfa_topology).
  * elec_pen: DEVICE pointer to 2 doubles receiving elec and pen (kcal/mol).
+ * The three must be device or managed memory of the current device
+ * (checked with cudaPointerGetAttributes, which allocates nothing; anything
+ * else returns SIBFA_E_INVALID before any launch); their lengths cannot be
+ * checked through plain pointers and are the caller's responsibility.
  * params: host struct.  The call is asynchronous on `stream` and does not
  * synchronize.  The first call on each device looks up the scratch array's
- * device address with that device current; make that first call before any
- * stream capture.  All calls on a device share the scratch array: calls whose
+ * device address with that device current and keeps it until the process
+ * exits; make that first call before any stream capture, and do not use the
+ * call after cudaDeviceReset on that device (the kept address would be
+ * stale).  All calls on a device share the scratch array: calls whose
  * kernels overlap on the GPU (different streams, no ordering) race.  Errors
  * are described by sibfa_noalloc_last_error(). */
 sibfa_status sibfa_cluster_elec_noalloc(const sibfa_params *params, int n_mol, const double *pos,

@@ -925,13 +925,20 @@ static sibfa_status md_impl(sibfa_ctx *ctx, double *pos, double *vel, const doub
     sibfa_status st = SIBFA_OK;
     if (!ctx->md_forces_valid) {
         st = evaluate<R>(ctx, true, false, tol);
-        if (st) return st;
+        if (st) {
+            leave(ctx);   // keep the caller's stream ordered after what was queued
+            return st;
+        }
         launch_water_intra(M, d.pos, ctx->d_forces, o.md_k_bond, o.md_r0, o.md_k_angle, th0, L);
     }
     for (int k = 0; k < n; ++k) {
         launch_md_kick(M, d.pos, vel, ctx->d_invm, ctx->d_forces, dt, 1, L);
         st = evaluate<R>(ctx, true, false, tol);
-        if (st) return st;
+        if (st) {
+            ctx->md_forces_valid = false;
+            leave(ctx);
+            return st;
+        }
         launch_water_intra(M, d.pos, ctx->d_forces, o.md_k_bond, o.md_r0, o.md_k_angle, th0, L);
         launch_md_kick(M, d.pos, vel, ctx->d_invm, ctx->d_forces, dt, 0, L);
     }
@@ -1121,11 +1128,23 @@ static sibfa_status minimize_impl(sibfa_ctx *ctx, double *pos, int n, double cap
     const double th0 = o.md_theta0_deg * M_PI / 180.0;
     sibfa_status st_e = enter(ctx);
     if (st_e) return st_e;
+    // Relaxation steps are not a trajectory to extrapolate along: the stored
+    // dipole history is cleared on every exit from here on, error or not.
+    struct ClearHistory {
+        sibfa_ctx *c;
+        ~ClearHistory() {
+            c->hist_n = 0;
+            c->md_forces_valid = false;
+        }
+    } clear_history{ctx};
     CK(cudaMemsetAsync(d.flags, 0, sizeof(int), ctx->s));
     CK(cudaMemcpyAsync(d.pos, pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
     for (int k = 0; k < n; ++k) {
         sibfa_status st = evaluate<R>(ctx, true, false, tol);
-        if (st) return st;
+        if (st) {
+            leave(ctx);   // keep the caller's stream ordered after what was queued
+            return st;
+        }
         launch_water_intra(M, d.pos, ctx->d_forces, o.md_k_bond, o.md_r0, o.md_k_angle, th0, L);
         launch_sd_step(M, d.pos, ctx->d_forces, 1e-4, cap, L);
     }
@@ -1136,8 +1155,6 @@ static sibfa_status minimize_impl(sibfa_ctx *ctx, double *pos, int n, double cap
     st_e = leave(ctx);
     if (st_e) return st_e;
     CK(cudaStreamSynchronize(ctx->s));
-    ctx->md_forces_valid = false;
-    ctx->hist_n = 0;   // relaxation steps are not a trajectory to extrapolate along
     solve_stats(ctx);
     {
         sibfa_status fl = check_flags(ctx, *(int *)(h + 16));

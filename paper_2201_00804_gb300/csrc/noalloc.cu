@@ -175,15 +175,44 @@ __global__ void k_na_reduce(int M, double ke, const double *scr, double *out) {
     }
 }
 
-// Device address of the scratch array for the current device (looked up once
-// per device, with that device current).
-sibfa_status na_scratch(double **ptr) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= NA_MAX_DEV) {
+// The current device, or an error.
+sibfa_status na_device(int *dev) {
+    cudaError_t e = cudaGetDevice(dev);
+    if (e != cudaSuccess || *dev < 0 || *dev >= NA_MAX_DEV) {
         g_na_error = std::string("sibfa_cluster_elec_noalloc: no usable current device: ") + cudaGetErrorString(e);
         return SIBFA_E_CUDA;
     }
+    return SIBFA_OK;
+}
+
+// A caller buffer must be device (or managed) memory of the current device:
+// a host address handed to the kernels would be read as a device address.
+// cudaPointerGetAttributes allocates nothing.
+sibfa_status na_check_ptr(const void *p, int dev, const char *name) {
+    cudaPointerAttributes a;
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_na_error = std::string("sibfa_cluster_elec_noalloc: ") + name + " is not a CUDA pointer: " +
+                     cudaGetErrorString(e);
+        return SIBFA_E_INVALID;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
+        g_na_error = std::string("sibfa_cluster_elec_noalloc: ") + name + " must be device or managed memory";
+        return SIBFA_E_INVALID;
+    }
+    if (a.type == cudaMemoryTypeDevice && a.device != dev) {
+        g_na_error = std::string("sibfa_cluster_elec_noalloc: ") + name + " lives on device " +
+                     std::to_string(a.device) + ", not on the current device " + std::to_string(dev);
+        return SIBFA_E_INVALID;
+    }
+    return SIBFA_OK;
+}
+
+// Device address of the scratch array on device `dev` (looked up once per
+// device, with that device current, and kept until the process exits).
+sibfa_status na_scratch(int dev, double **ptr) {
+    cudaError_t e = cudaSuccess;
     std::lock_guard<std::mutex> lock(g_na_mutex);
     if (!g_na_ptr[dev]) {
         void *p = nullptr;
@@ -214,9 +243,14 @@ sibfa_status sibfa_cluster_elec_noalloc(const sibfa_params *params, int n_mol, c
                      std::to_string(NA_MAX_MOL) + " molecules of the static scratch array";
         return SIBFA_E_INVALID;
     }
-    double *scr = nullptr;
-    sibfa_status st = na_scratch(&scr);
+    int dev = 0;
+    sibfa_status st = na_device(&dev);
     if (st) return st;
+    if ((st = na_check_ptr(pos, dev, "pos")) || (st = na_check_ptr(mp_local, dev, "mp_local")) ||
+        (st = na_check_ptr(elec_pen, dev, "elec_pen")))
+        return st;
+    double *scr = nullptr;
+    if ((st = na_scratch(dev, &scr))) return st;
     KParams p{};
     p.z[0] = params->z_o;
     p.z[1] = p.z[2] = params->z_h;

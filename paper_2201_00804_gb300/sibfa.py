@@ -248,9 +248,18 @@ def sibfa_cluster_elec_noalloc(params: dict, pos, mp_local, elec_pen, stream=Non
     (n_mol*50) and elec_pen (2) are float64 CUDA tensors.  Asynchronous on
     `stream` (a torch.cuda.Stream, raw handle, or None for the legacy default
     stream)."""
+    import torch
+    for name, t in (("pos", pos), ("mp_local", mp_local), ("elec_pen", elec_pen)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda):
+            raise TypeError(f"sibfa_cluster_elec_noalloc: {name} must be a CUDA tensor")
+    if len({t.device for t in (pos, mp_local, elec_pen)}) != 1:
+        raise ValueError("sibfa_cluster_elec_noalloc: pos, mp_local and elec_pen must be on one device")
+    n_mol = int(pos.numel() // 9)
+    if pos.numel() % 9 or mp_local.numel() != n_mol * 50 or elec_pen.numel() < 2:
+        raise ValueError("sibfa_cluster_elec_noalloc: need pos of n_mol*9, mp_local of n_mol*50 and elec_pen "
+                         f"of >= 2 doubles (got {pos.numel()}, {mp_local.numel()}, {elec_pen.numel()})")
     lib = load_library()
     P = sibfa_params(*[float(params[n]) for n in PARAM_FIELDS])
-    n_mol = int(pos.numel() // 9)
     s = None if stream is None else int(getattr(stream, "cuda_stream", stream))
     st = lib.sibfa_cluster_elec_noalloc(C.byref(P), n_mol, _ptr(pos), _ptr(mp_local), _ptr(elec_pen), s)
     if st != SIBFA_OK:

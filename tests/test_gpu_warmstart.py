@@ -74,3 +74,43 @@ def test_guesses_converge_to_the_same_solution():
     it1 = sum(r[2] for r in res[1][4:])
     it4 = sum(r[2] for r in res[4][4:])
     assert it4 <= it1, ([r[2] for r in res[1]], [r[2] for r in res[4]])
+
+
+def test_minimize_then_md_matches_a_fresh_context():
+    """sibfa_minimize leaves no dipoles in the extrapolation history: MD steps
+    after a relaxation take the same PCG iterations and give the same energies
+    and positions as a fresh context started from the relaxed positions.  (The
+    first evaluation of each MD call sequence differs only in its guess, the
+    relaxation's last dipoles or the direct field, and is not counted: the
+    iterations compared are those of each call's last evaluation.)"""
+    import torch
+    import paper_2201_00804_gb300 as pkg
+    s, o = synth.make_config("water216")
+    pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
+    v0 = torch.tensor(synth.maxwell_velocities(s, 300.0, seed=9).reshape(-1), dtype=torch.float64, device="cuda")
+    masses = torch.tensor(s.masses().reshape(-1), dtype=torch.float64, device="cuda")
+    a = _ctx(pkg, s, o, 4)
+    try:
+        pkg.sibfa_minimize(a, pos, 5, 0.01)
+        relaxed = pos.clone()
+        pa, va = relaxed.clone(), v0.clone()
+        ea, ita = [], []
+        for _ in range(3):
+            ea.append(pkg.sibfa_md_steps(a, pa, va, masses, 0.5, 1))
+            ita.append(pkg.sibfa_last_stats(a)[0])
+    finally:
+        pkg.sibfa_destroy(a)
+    b = _ctx(pkg, s, o, 4)
+    try:
+        pb, vb = relaxed.clone(), v0.clone()
+        eb, itb = [], []
+        for _ in range(3):
+            eb.append(pkg.sibfa_md_steps(b, pb, vb, masses, 0.5, 1))
+            itb.append(pkg.sibfa_last_stats(b)[0])
+    finally:
+        pkg.sibfa_destroy(b)
+    assert ita == itb, (ita, itb)
+    for x, y in zip(ea, eb):
+        for t in TERMS:
+            assert abs(x[t] - y[t]) <= 1e-9 * max(1.0, abs(y[t])), (t, x[t], y[t])
+    assert float((pa - pb).abs().max()) <= 1e-10
