@@ -10,8 +10,14 @@ and translation invariance and zero net force/torque in the gas phase,
 textbook two-site closed forms, Thole and kernel recurrences, Ewald alpha
 independence and agreement with an exact k-space sum and a direct lattice sum,
 B-spline partition of unity, symmetry of T, PCG against a dense solve, the
-polarization-energy identity at the solution, a hand-computed charge-transfer
-pair, and the penetration b -> infinity limit.
+polarization-energy identity at the solution, the penetration b -> infinity
+limit, and hand evaluations of the paper's formulas on laid-out geometries:
+lone-pair and frame geometry, the rotated multipoles' potential, bond-bond,
+bond-lone pair and lone pair-lone pair repulsion, one pair of each
+dispersion/exchange-dispersion kind, a donor-acceptor charge-transfer case
+and V_int; the gas-phase lone-pair potential against the textbook multipole
+potential; and alpha independence of the periodic lone-pair potential,
+permanent field, induced dipoles and polarization energy.
 
 Parity with the paper's printed energies (Tables 1-2) is unpinned: the
 parameters, lone-pair positions and geometries they need are not in the

@@ -20,4 +20,6 @@ from .water import (  # noqa: F401
     make_config,
     maxwell_velocities,
     random_rotation,
+    general_multipoles,
+    with_general_multipoles,
 )

@@ -187,6 +187,36 @@ def _random_multipoles(rng: np.random.Generator, n_mol: int) -> np.ndarray:
     return mp
 
 
+def general_multipoles(rng: np.random.Generator, n_mol: int) -> np.ndarray:
+    """Per-molecule draws with no symmetry in the local frames, for parity
+    tests of the full rotation (all dipole components, off-diagonal
+    quadrupoles): charges as in the workloads (q_O uniform in [-0.85, -0.75],
+    -q_O/4 on the other four sites); on every site a dipole of uniformly random
+    direction with |mu| uniform in [0, 0.3] e.A, and a quadrupole whose six
+    independent entries are uniform in [-0.5, 0.5] e.A^2 before the trace is
+    removed from the diagonal."""
+    mp = np.zeros((n_mol, N_SITES, N_MP))
+    q_o = rng.uniform(-0.85, -0.75, size=n_mol)
+    mp[:, 0, 0] = q_o
+    mp[:, 1:, 0] = (-q_o / 4.0)[:, None]
+    d = rng.normal(size=(n_mol, N_SITES, 3))
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    mp[:, :, 1:4] = d * rng.uniform(0.0, 0.3, size=(n_mol, N_SITES, 1))
+    th = rng.uniform(-0.5, 0.5, size=(n_mol, N_SITES, 6))
+    th[..., 0:3] -= th[..., 0:3].mean(axis=-1, keepdims=True)
+    mp[:, :, 4:10] = th
+    return mp
+
+
+def with_general_multipoles(system: "System", seed: int) -> "System":
+    """The same geometry with general_multipoles drawn from `seed`."""
+    rng = np.random.default_rng(seed)
+    meta = dict(system.meta)
+    meta["multipoles"] = ("general", seed)
+    return System(pos=system.pos.copy(), mp_local=general_multipoles(rng, system.n_mol),
+                  box=None if system.box is None else system.box.copy(), meta=meta)
+
+
 MIN_ATOM_DIST = 1.7   # A, minimum intermolecular atom-atom distance of a starting structure
 
 

@@ -38,6 +38,11 @@ def _cases():
         "water216": synth.make_config("water216"),
         # 512 waters with rc 5.5: three cells per side, exercises the cell list
         "water512": (synth.make_box(8, 24.83, seed=33), {"rc": 5.5, "grid": 32, "order": 5, "ewald": 0.55}),
+        # dipoles of any direction and quadrupoles with off-diagonal entries in
+        # every local frame: the full rotation and its torques
+        "cluster8_general": (synth.with_general_multipoles(synth.make_cluster(8, seed=31), seed=34), None),
+        "water216_general": (synth.with_general_multipoles(synth.make_config("water216")[0], seed=35),
+                             synth.make_config("water216")[1]),
     }
 
 

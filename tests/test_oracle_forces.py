@@ -64,3 +64,12 @@ def test_gas_invariance_and_net_force_torque():
     X = s.pos.reshape(-1, 3)
     assert np.abs(F.sum(0)).max() < 1e-9
     assert np.abs(np.cross(X, F).sum(0)).max() < 1e-8
+
+
+def test_fd_forces_gas_cluster_general_multipoles():
+    """Dipoles of any direction and quadrupoles with off-diagonal entries in
+    the local frames: forces through the rotated multipoles (torques)."""
+    s = synth.with_general_multipoles(synth.make_cluster(3, seed=12), seed=13)
+    rng = np.random.default_rng(2)
+    coords = [(int(rng.integers(3)), int(rng.integers(3)), int(rng.integers(3))) for _ in range(6)]
+    _check(s, None, coords, 2e-6)
