@@ -39,21 +39,15 @@ WORKLOAD = ("water4096: 4096 rigid-geometry waters (12,288 atoms), cubic box 49.
             "alpha 0.4/A, PCG 1e-6 D warm start, velocity-Verlet NVE 0.5 fs from 300 K")
 SAMPLE = ("oracle sample: 512 waters (1,536 atoms) at the same density, rc 9 A, SPME 32^3 (1.29 points/A, as 64^3 "
           "on 49.66 A) order 5, alpha 0.4, PCG 1e-6 D; one full energy + force evaluation per step")
-FP32_LANES_PER_SM = 128
-N_SM = 152
-SM_MAX_MHZ = 2070.0
-
-# Algorithmic FP32 operations per unit of the real-space permanent kernel,
-# counted by hand from its formulas (fused multiply-add = 2, each
-# transcendental or reciprocal square root = 1).
-FLOPS_PERM_SITE_PAIR = 364      # multipole pair: erfc kernel g0..g5, field to d2, energy, gradient with d3, sensitivities
-FLOPS_PEN_ATOM_ATOM = 236       # penetration, both sites atoms (charge-charge*, both dipole/quadrupole* sides)
-FLOPS_PEN_ATOM_MID = 129        # penetration, atom target and midpoint source
-FLOPS_PEN_MID_ATOM = 156        # penetration, midpoint target and atom source (incl. sensitivity terms)
-FLOPS_THOLE_PAIR = 119          # Thole-damped field of a site at a polarizable atom
-FLOPS_LP_PAIR = 101             # potential and gradient of a site at a lone pair (separate launch, not in the roofline)
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_real_perm_traffic.json")
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_2201_00804_gb300", "csrc", f) for f in ("k_pair.cu", "sibfa_internal.cuh")]
+# Algorithmic FP32 work per unit (fused multiply-add = 2): the midpoints of
+# the per-unit estimates of the hot-path scope table (multipole site pair with
+# Ewald kernel, energy, gradient, torque, field and penetration 250-350;
+# repulsion orbital pair 150-250; dispersion + exchange-dispersion point pair
+# 60-80; charge-transfer donor-acceptor pair ~100).
+FLOPS_PERM_SITE_PAIR = 300
+FLOPS_REP_ITEM = 200
+FLOPS_DISP_ITEM = 70
+FLOPS_CT_ITEM = 100
 
 
 def parse():
@@ -127,68 +121,137 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def count_units(pos, box, rc, mp_points):
-    """Pairs evaluated by the real-space permanent kernel: intermolecular
-    (site, site) pairs within rc split by which side carries a valence
-    (penetration), (polarizable atom, site) pairs and (lone pair, site)
-    pairs within rc."""
-    M = pos.shape[0]
-    sites = mp_points[:, :5]
-    lps = mp_points[:, 5:7]
+def unordered_pairs(O, box, cut):
+    """Unordered molecule pairs (i < j) whose minimum-image O-O distance is
+    below `cut`, with the image shift to add to molecule j's points."""
+    from scipy.spatial import cKDTree
+    L = np.asarray(box, dtype=np.float64)
+    Ow = np.mod(O, L)
+    pr = cKDTree(Ow, boxsize=L).query_pairs(cut, output_type="ndarray")
+    if pr.size == 0:
+        return np.zeros((0,), np.int64), np.zeros((0,), np.int64), np.zeros((0, 3))
+    i, j = pr[:, 0], pr[:, 1]
+    d = O[j] - O[i]
+    sh = -L * np.round(d / L)
+    return i, j, sh
+
+
+def count_units(pos, box, rc, pts):
+    """Algorithmic units of one evaluation's real-space kernels, with each
+    kernel's cutoff semantics (per point pair, on the distance of the term's
+    radial factor):
+      site_pairs  ordered (target site, source site) pairs within rc: the
+                  permanent kernel evaluates every pair from both sides
+                  (target-site formulation: energy, gradient, torque and
+                  field of the target);
+      lp_pairs    ordered (lone pair, source site) pairs within rc;
+      rep_items   unordered repulsion orbital pairs: bond-bond (bond
+                  midpoints), bond-lone pair and lone pair-bond (midpoint to
+                  lone pair), lone pair-lone pair, within rc;
+      disp_items  unordered (point, point) dispersion pairs within rc over
+                  O, H1, H2, LP1, LP2;
+      ct_items    unordered donor-acceptor pairs: 8 per molecule pair whose
+                  O-O distance is below rc.
+    pts: (M, 7, 3) absolute O, H1, H2, M1, M2, LP1, LP2."""
     O = pos[:, 0]
-    n = dict(site_pairs=0, pen_atom_atom=0, pen_atom_mid=0, pen_mid_atom=0, thole_pairs=0, lp_pairs=0)
-    L = np.asarray(box)
-    atom = np.array([1, 1, 1, 0, 0], bool)
-    aa = atom[:, None, None] & atom[None, None, :]
-    am = atom[:, None, None] & ~atom[None, None, :]
-    ma = ~atom[:, None, None] & atom[None, None, :]
-    for i0 in range(0, M, 128):
-        i1 = min(M, i0 + 128)
-        d = O[None, :, :] - O[i0:i1, None, :]
-        d -= L * np.round(d / L)
-        near = np.einsum("ijk,ijk->ij", d, d) < (rc + 2.6) ** 2
-        for a in range(i1 - i0):
-            i = i0 + a
-            js = np.nonzero(near[a])[0]
-            js = js[js != i]
-            sh = (d[a, js] - (O[js] - O[i]))[:, None, :]
-            sj = sites[js] + sh                                   # (n,5,3)
-            r = np.linalg.norm(sites[i][:, None, None, :] - sj[None], axis=-1)   # (5,n,5)
-            inr = r < rc
-            n["site_pairs"] += int(inr.sum())
-            n["pen_atom_atom"] += int((inr & aa).sum())
-            n["pen_atom_mid"] += int((inr & am).sum())
-            n["pen_mid_atom"] += int((inr & ma).sum())
-            n["thole_pairs"] += int(inr[:3].sum())
-            rl = np.linalg.norm(lps[i][:, None, None, :] - sj[None], axis=-1)
-            n["lp_pairs"] += int((rl < rc).sum())
+    i, j, sh = unordered_pairs(O, box, rc + 2.6)
+    n = dict(site_pairs=0, lp_pairs=0, rep_items=0, disp_items=0, ct_items=0)
+    rc2 = rc * rc
+    for a in range(0, i.size, 65536):
+        ii, jj, ss = i[a:a + 65536], j[a:a + 65536], sh[a:a + 65536]
+        Pi, Pj = pts[ii], pts[jj] + ss[:, None, :]
+
+        def within(A, B):
+            d = A[:, :, None, :] - B[:, None, :, :]
+            return np.einsum("nabk,nabk->nab", d, d) < rc2
+
+        ss_ = within(Pi[:, :5], Pj[:, :5])
+        n["site_pairs"] += 2 * int(ss_.sum())
+        n["lp_pairs"] += int(within(Pi[:, 5:7], Pj[:, :5]).sum() + within(Pj[:, 5:7], Pi[:, :5]).sum())
+        mi = 0.5 * (Pi[:, 0:1] + Pi[:, 1:3])            # bond midpoints (n, 2, 3)
+        mj = 0.5 * (Pj[:, 0:1] + Pj[:, 1:3])
+        li, lj = Pi[:, 5:7], Pj[:, 5:7]
+        n["rep_items"] += int(within(mi, mj).sum() + within(mi, lj).sum() + within(li, mj).sum()
+                              + within(li, lj).sum())
+        qi = np.concatenate([Pi[:, :3], li], 1)
+        qj = np.concatenate([Pj[:, :3], lj], 1)
+        n["disp_items"] += int(within(qi, qj).sum())
+        dO = Pj[:, 0] - Pi[:, 0]
+        n["ct_items"] += 8 * int((np.einsum("nk,nk->n", dO, dO) < rc2).sum())
     return n
 
 
-def unit_flops(n):
-    """Algorithmic flops of one k_real_perm launch (site targets); the
-    lone-pair targets run in a separate launch and are not counted."""
-    return (n["site_pairs"] * FLOPS_PERM_SITE_PAIR + n["pen_atom_atom"] * FLOPS_PEN_ATOM_ATOM
-            + n["pen_atom_mid"] * FLOPS_PEN_ATOM_MID + n["pen_mid_atom"] * FLOPS_PEN_MID_ATOM
-            + n["thole_pairs"] * FLOPS_THOLE_PAIR)
+def count_units_clusters(start, M):
+    """The same units for a batch of gas-phase clusters (all pairs inside each
+    cluster, no cutoff)."""
+    n = np.diff(np.asarray(start, dtype=np.int64))
+    pairs = int((n * (n - 1) // 2).sum())           # unordered molecule pairs
+    return dict(site_pairs=2 * 25 * pairs, lp_pairs=2 * 10 * pairs, rep_items=16 * pairs, disp_items=25 * pairs,
+                ct_items=8 * pairs)
 
 
-def measured_traffic():
-    """DRAM bytes per launch of k_real_perm from the committed ncu summary,
-    or None when the kernel source changed after those counters were taken."""
+def kernel_flops(n):
+    """Algorithmic FP32 flops per launch set, from the per-unit figures above."""
+    return {"real_perm": n["site_pairs"] * FLOPS_PERM_SITE_PAIR,
+            "short": n["rep_items"] * FLOPS_REP_ITEM + n["disp_items"] * FLOPS_DISP_ITEM,
+            "ct": n["ct_items"] * FLOPS_CT_ITEM}
+
+
+def spme_pass_bytes(K, n_sites):
+    """Algorithmic bytes of one SPME pass over a grid of G = K0 K1 K2 points:
+    spread write 4G, forward FFT read + write ~12G, convolution read + write
+    16G, influence function read 4G (FP64 on the half spectrum), inverse FFT
+    ~12G, gather read 4G (56 G in all), plus 64 B read and 80 B written per
+    site (multipole in, potential derivatives out)."""
+    G = int(np.prod(K))
+    return 56 * G + 144 * n_sites
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+
+
+def measured_traffic(kernel_key, workload):
+    """DRAM bytes (read + write) per step of a kernel from the committed ncu
+    summary, or None when its source changed after the counters were taken or
+    none were taken for this workload."""
     import hashlib
     try:
         with open(TRAFFIC_FILE) as f:
-            rec = json.load(f)
-    except (OSError, ValueError):
+            rec = json.load(f)[workload][kernel_key]
+    except (OSError, ValueError, KeyError):
         return None
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
-        with open(p, "rb") as f:
+    for p in rec.get("sources", []):
+        with open(os.path.join(ROOT, p), "rb") as f:
             h.update(f.read())
     if rec.get("source_sha256") != h.hexdigest():
         return None
-    return rec.get("dram_bytes_per_launch_scaled", rec.get("dram_bytes_per_launch"))
+    return rec.get("dram_bytes_per_step")
+
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
+def measure_fp32_peak(pkg, local):
+    """FP32 FMA rate of this GPU: a kernel of independent FMA chains on every
+    SM (8 blocks of 256 threads per SM, ~20 ms per launch), best of five,
+    with the SM clock sampled meanwhile.  The number of SMs is the device's."""
+    import torch
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    best = 0.0
+    with Clocks(local) as clk:
+        for _ in range(5):
+            fl, ms = pkg.sibfa_alu_peak(False, 16384, 8 * nsm)
+            best = max(best, fl / (ms * 1e-3) / 1e12)
+    c = clk.summary()
+    return {"tflops": best, "sms": nsm, "sm_mhz": c["sm_mhz"], "sm_max_mhz": c["sm_max_mhz"],
+            "basis": ("measured: FP32 FMA-chain kernel on all %d SMs, best of 5 launches (%.1f TFLOP/s at a median "
+                      "%s MHz SM clock)" % (nsm, best, c["sm_mhz"]))}
 
 
 def points_from_pos(pos, P):
@@ -325,14 +388,6 @@ def setup(name, pkg, synth, precision, stream, warm=1):
     vel = torch.tensor(synth.maxwell_velocities(s, 300.0, seed=seed).reshape(-1), dtype=torch.float64, device="cuda")
     masses = torch.tensor(s.masses().reshape(-1), dtype=torch.float64, device="cuda")
     return s, o, ctx, make_api, pos, vel, masses
-
-
-def count_units_clusters(start, M):
-    """Unit counts of the permanent kernel for all intramolecular-free pairs inside clusters."""
-    n = np.diff(np.asarray(start, dtype=np.int64))
-    pairs = int((n * (n - 1)).sum())          # ordered molecule pairs (full list)
-    return dict(site_pairs=25 * pairs, pen_atom_atom=9 * pairs, pen_atom_mid=6 * pairs, pen_mid_atom=6 * pairs,
-                thole_pairs=15 * pairs, lp_pairs=10 * pairs)
 
 
 def timed_steps(pkg, ctx, pos, vel, masses, steps, stream, flush, dt_fs=0.5, keep=False):
@@ -513,27 +568,61 @@ def main():
         ms, n = pkg.sibfa_profile_get(ctx, name)
         phases[name] = {"ms_per_step": ms / args.steps, "launches": n}
     pkg.sibfa_set_profiling(ctx, False)
+    peak = measure_fp32_peak(pkg, local)
     step_ms = max_over_ranks(dist, total_ms) / args.steps
     value = weak_value(ws, 3 * M, step_ms)
 
-    # roofline of the real-space permanent kernel (one launch per step)
+    # Rooflines.  Pair kernels: algorithmic FP32 flops per step (unit counts
+    # x per-unit figures) over the kernel's live CUDA-event time on its own
+    # stream, against the FP32 FMA rate measured on this device; SPME: the
+    # permanent pass's algorithmic bytes over its event time, against the
+    # measured HBM copy bandwidth.
     P = synth.PARAMS
     pos_h = pos.cpu().numpy().reshape(M, 3, 3)
     if args.workload in ("water4096", "water32000"):
         units = count_units(pos_h, s.box, o["rc"], points_from_pos(pos_h, P))
     else:
         units = count_units_clusters(o["cluster_start"], M)
-    flops = unit_flops(units)
-    rp_ms = phases["real_perm"]["ms_per_step"]
-    achieved = flops / (rp_ms * 1e-3) / 1e12
-    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    kname = "k_real_perm<float, 0, 0, 0, 5>" if args.workload == "clusters4096" else "k_real_perm<float, 1, 0, 0, 5>"
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak,
-                "traffic": measured_traffic() if args.workload == "water4096" else None,
-                "flops_per_launch": flops, "units": units,
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived from unit counts and max clock)"}
-
+    kfl = kernel_flops(units)
+    kernels = {"real_perm": ("k_real_perm<float, %d, 0, 0, 5>" % int(args.workload != "clusters4096"),
+                             "site targets: multipole + penetration energy, gradient, torque sensitivities, "
+                             "Thole field; 1 launch per step"),
+               "short": ("k_short<float, %d, 0, 0|1>" % int(args.workload != "clusters4096"),
+                         "repulsion (part 0) and dispersion + exchange-dispersion (part 1); 2 launches per step, "
+                         "timed together on the short-range stream"),
+               "ct": ("k_ct<float, %d, 0>" % int(args.workload != "clusters4096"),
+                      "reduced charge transfer; 1 launch per step on the charge-transfer stream")}
+    lines = {}
+    for key, (kname, what) in kernels.items():
+        ms = phases[key]["ms_per_step"]
+        if ms <= 0:
+            continue
+        ach = kfl[key] / (ms * 1e-3) / 1e12
+        lines[key] = {"bound": "alu", "kernel": kname, "what": what, "achieved": ach, "peak": peak["tflops"],
+                      "unit": "TFLOP/s", "frac": ach / peak["tflops"], "flops_per_step": kfl[key],
+                      "ms_per_step": ms, "traffic": measured_traffic(key, args.workload)}
+    if args.workload != "clusters4096":
+        K = o["grid"] if not np.isscalar(o["grid"]) else (o["grid"],) * 3
+        nbytes = spme_pass_bytes(K, 5 * M)
+        ms = phases["spme_perm"]["ms_per_step"]
+        hbm = measured_hbm_peak()
+        lines["spme_perm"] = {"bound": "hbm", "kernel": "spme permanent pass (spread, cuFFT r2c, convolution, "
+                              "cuFFT c2r, gather to 3rd derivatives, intramolecular corrections)",
+                              "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                              "frac": nbytes / (ms * 1e-3) / 1e9 / hbm, "bytes_per_pass": nbytes, "ms_per_step": ms,
+                              "traffic": None, "peak_basis": "hbm_gbs of MEASURED_PEAKS.json (copy bandwidth)"}
+        it = float(np.mean(iters))
+        pcg_ms = phases["pcg"]["ms_per_step"]
+        lines["pcg_iteration"] = {"bound": "hbm", "kernel": "one PCG iteration (real-space T.p from the pair list, "
+                                  "SPME of the direction, cooperative vector step)",
+                                  "achieved": nbytes / (pcg_ms / (it + 1) * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                  "frac": nbytes / (pcg_ms / (it + 1) * 1e-3) / 1e9 / hbm,
+                                  "ms_per_iteration": pcg_ms / (it + 1), "iterations_per_step": it,
+                                  "bytes_per_iteration_spme": nbytes, "traffic": None}
+    dom = max(("real_perm", "short"), key=lambda k: lines[k]["ms_per_step"] if k in lines else -1)
+    roofline = dict(lines[dom])
+    roofline["peak_basis"] = peak["basis"]
+    roofline["units"] = units
     # End to end through the C ABI with host buffers: a second context
     # evaluates, from host memory, the positions of the trajectory that the
     # first context advances on the device (untimed); each timed call copies
@@ -583,6 +672,7 @@ def main():
                    "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{ws}",
                    "pcg_initial_guess": GUESS[args.warm_start]},
         "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+        "rooflines": lines, "fp32_peak": peak,
         "cpu_baseline": cpu, "fp64_gpu_path": fp64, "pcg_iters_mean": float(np.mean(iters)), "phases_ms": phases,
         "tuned": {"short_blocks_per_sm": tb, "fixed": tdone},
     }

@@ -250,6 +250,18 @@ sibfa_status sibfa_cluster_elec_noalloc(const sibfa_params *params, int n_mol, c
                                         const double *mp_local, double *elec_pen, void *stream);
 const char *sibfa_noalloc_last_error(void);
 
+/* CUDA-core arithmetic peak of the current device (a measurement utility;
+ * the paper has no counterpart).  Runs `blocks` blocks of 256 threads, each
+ * thread `iters` x 128 fused multiply-adds on 8 independent chains, FP32
+ * (fp64 = 0) or FP64 (fp64 = 1), on the legacy default stream after one
+ * shorter warm-up launch, and returns the CUDA-event time of the timed
+ * launch (*ms) and its flop count (*flops, an FMA counted as 2).  The ratio
+ * is the device's FMA rate at the clock it ran at; the pair kernels' roofline
+ * is measured against it.  Allocates and frees a small device buffer;
+ * synchronizes the device.  Errors: sibfa_alu_peak_error(). */
+sibfa_status sibfa_alu_peak(int fp64, int iters, int blocks, double *ms, double *flops);
+const char *sibfa_alu_peak_error(void);
+
 void sibfa_destroy(sibfa_ctx *ctx);
 
 /* ---------------------------------------------------------------------------

@@ -10,6 +10,7 @@ from .sibfa import (  # noqa: F401
     Server,
     SibfaError,
     load_library,
+    sibfa_alu_peak,
     sibfa_cluster_terms,
     sibfa_create,
     sibfa_destroy,

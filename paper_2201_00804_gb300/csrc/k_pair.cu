@@ -59,13 +59,33 @@ struct PermAcc {
 // VIR: also accumulate the pair virial 1/2 g (x) x of the target's gradient g
 // (both molecules of a pair see it, so each adds half); the lone-pair
 // potential's share is taken with the lambda charges in the force pass.
+//
+// Periodic systems: rv is the source position relative to O_i (O-O
+// displacement plus the source's offset).  Gas phase: rv is the O-O
+// displacement D = O_j - O_i itself and the pair displacement is formed as
+// x = (target offset - source offset) - D.  The charge-charge energy is then
+// taken as q_t q_s (1/r - 1/R), R = |D| the same for all site pairs of the
+// molecule pair, from 1/r - 1/R = (R^2 - r^2) / (r R (r + R)) with
+// R^2 - r^2 = 2 sv.D - sv.sv (sv = target - source offsets): a small,
+// cancellation-free term per site pair; the missing sum_ts q_t q_s / R =
+// Q_i Q_j / R is added once per molecule pair (zero for neutral molecules).
+// In FP32 this keeps the multipole energy of a gas-phase cluster, whose
+// site-pair charge terms of ~10 kcal/mol cancel to the molecular
+// interaction, about 15x closer to FP64 than q_t q_s / r summed directly.
 template <typename R, bool PER, bool ATOM_SRC, bool VIR>
 __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d, int w, bool is_lp, V3<R> ot,
-                                          const Mp<R> &mt, R Nt_, int js, V3<R> rs, size_t te, PermAcc<R> &A) {
+                                          const Mp<R> &mt, R Nt_, int js, V3<R> rv, size_t te, PermAcc<R> &A) {
     const Scal<R> &S = sc<R>(p);
     const R third = R(1) / R(3);
     const int j = js >> 3, s = js & 7;
-    const V3<R> x = ot - rs;
+    V3<R> x, sv;
+    if (PER) {
+        x = ot - rv;
+    } else {
+        const R *os = d.off + (j * NP + s) * 3;
+        sv = ot - mk(__ldg(os), __ldg(os + 1), __ldg(os + 2));
+        x = sv - rv;
+    }
     const R r2 = dot(x, x);
     const R rinv = rsqrt_(r2);
     const R r = r2 * rinv;
@@ -82,7 +102,15 @@ __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d
     }
     FieldTerms<R> f;
     source_field<R, 3>(ms, x, g, f);
-    const R U = mt.q * f.phi + dot(mt.mu, f.d1) + third * symdd(mt.th, f.d2);
+    R qphi;
+    if (PER) {
+        qphi = mt.q * f.phi;
+    } else {
+        const R RR = dot(rv, rv), Rinv = rsqrt_(RR);
+        const R dinv = (R(2) * dot(sv, rv) - dot(sv, sv)) * rinv * Rinv / (r + RR * Rinv);   // 1/r - 1/R
+        qphi = mt.q * (f.phi_mp + ms.q * dinv);
+    }
+    const R U = qphi + dot(mt.mu, f.d1) + third * symdd(mt.th, f.d2);
     A.Ue.add(R(0.5) * U);
     const V3<R> gel = target_grad(mt, ms, x, g, f);
     A.gr = A.gr + gel;
@@ -196,6 +224,11 @@ __global__ void __launch_bounds__(32 * NW, NW == 5 ? (PER ? 3 : 4) : (NW == 3 ? 
 #pragma unroll
     for (int k = 0; k < 9; ++k) A.W[k] = R(0);
     int ha = 0, ta = 0, hm = 0, tm = 0;   // queue heads and tails (warp-uniform, monotone)
+    // gas phase: charge of molecule i (the molecule-pair term of the shifted
+    // charge-charge energy, taken by the O-site warp)
+    R Qi = R(0);
+    if (!PER && !is_lp && w == 0)
+        for (int s = 0; s < NS; ++s) Qi += d.gmp[(i * NS + s) * GMP];
     const int nn = d.nnbr[i];
     for (int base = 0;; base += 32) {
         const bool flush = base >= nn;   // list exhausted: evaluate what is left in the queues
@@ -213,6 +246,13 @@ __global__ void __launch_bounds__(32 * NW, NW == 5 ? (PER ? 3 : 4) : (NW == 3 ? 
                 rs[s] = dO + mk(__ldg(offj + s * 3), __ldg(offj + s * 3 + 1), __ldg(offj + s * 3 + 2));
                 const V3<R> x = ot - rs[s];
                 if (!PER || dot(x, x) < rc2) bits |= 1u << s;
+                if (!PER) rs[s] = dO;   // queued: the O-O displacement (see perm_pair)
+            }
+            if (!PER && !is_lp && w == 0) {
+                R Qj = R(0);
+                for (int s = 0; s < NS; ++s) Qj += d.gmp[(j * NS + s) * GMP];
+                const R RR = dot(dO, dO);
+                A.Ue.add(R(0.5) * Qi * Qj * rsqrt_(RR));
             }
         }
         int na, nm;

@@ -453,6 +453,7 @@ __device__ inline void g_thole(R r, R rinv, R Ainv3, R a, bool periodic, R alpha
 template <typename R>
 struct FieldTerms {
     R phi;
+    R phi_mp;   // the dipole and quadrupole part of phi (phi - q g0)
     V3<R> d1;
     Sym<R> d2;
     // intermediates for the third-derivative contraction
@@ -466,7 +467,8 @@ __device__ inline void source_field(const Mp<R> &s, V3<R> x, const R *g, FieldTe
     const V3<R> v = symv(s.th, x);
     const R w = dot(x, v);
     const R third = R(1) / R(3), twoth = R(2) / R(3);
-    f.phi = s.q * g[0] - sx * g[1] + third * w * g[2];
+    f.phi_mp = third * w * g[2] - sx * g[1];
+    f.phi = s.q * g[0] + f.phi_mp;
     if constexpr (NDER >= 1) {
         const R P = s.q * g[1] - sx * g[2] + third * w * g[3];
         const V3<R> Q = R(-g[1]) * s.mu + (twoth * g[2]) * v;

@@ -127,6 +127,10 @@ def load_library(path: str = LIB_PATH):
     lib.sibfa_cluster_elec_noalloc.restype = C.c_int
     lib.sibfa_noalloc_last_error.argtypes = []
     lib.sibfa_noalloc_last_error.restype = C.c_char_p
+    lib.sibfa_alu_peak.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.sibfa_alu_peak.restype = C.c_int
+    lib.sibfa_alu_peak_error.argtypes = []
+    lib.sibfa_alu_peak_error.restype = C.c_char_p
     lib.sibfa_destroy.argtypes = [C.c_void_p]
     lib.sibfa_destroy.restype = None
     lib.sibfa_last_error.argtypes = [C.c_void_p]
@@ -264,6 +268,20 @@ def sibfa_cluster_elec_noalloc(params: dict, pos, mp_local, elec_pen, stream=Non
     st = lib.sibfa_cluster_elec_noalloc(C.byref(P), n_mol, _ptr(pos), _ptr(mp_local), _ptr(elec_pen), s)
     if st != SIBFA_OK:
         raise SibfaError(st, lib.sibfa_noalloc_last_error().decode())
+
+
+def sibfa_alu_peak(fp64: bool = False, iters: int = 4096, blocks: int = 0):
+    """FMA-chain rate of the current device: returns (flops, milliseconds).
+    blocks = 0 launches 8 blocks of 256 threads per SM."""
+    lib = load_library()
+    if blocks <= 0:
+        import torch
+        blocks = 8 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    ms, fl = C.c_double(), C.c_double()
+    st = lib.sibfa_alu_peak(1 if fp64 else 0, int(iters), int(blocks), C.byref(ms), C.byref(fl))
+    if st != SIBFA_OK:
+        raise SibfaError(st, lib.sibfa_alu_peak_error().decode())
+    return fl.value, ms.value
 
 
 def sibfa_cluster_terms(ctx, n_clusters: int):

@@ -1,8 +1,9 @@
-"""Unit counting behind the bench's roofline line: bench.count_units (a
-molecule-list walk with the O-O minimum image, as the kernel does) equals a
-brute-force count over every ordered molecule pair and every point pair
-with the minimum image taken on the point-point displacement itself, on the
-216-water box at rc 7 A; and the per-launch flops are the per-unit figures
+"""Unit counting behind the bench's roofline lines: bench.count_units (a
+k-d-tree molecule-pair walk with the O-O minimum image, as the kernels'
+neighbour list) equals a brute-force count over every ordered molecule pair
+and every point pair with the minimum image taken on the point-point
+displacement itself, on the 216-water box at rc 7 A; the cluster counts are
+all pairs of each cluster; the per-kernel flops are the per-unit figures
 times those counts."""
 import os
 import sys
@@ -17,24 +18,29 @@ import synth  # noqa: E402
 
 
 def brute_force(pts, box, rc):
+    """pts: (M, 7, 3) O, H1, H2, M1, M2, LP1, LP2."""
     M = pts.shape[0]
     L = np.asarray(box)
-    atom = np.array([1, 1, 1, 0, 0], bool)
-    n = dict(site_pairs=0, pen_atom_atom=0, pen_atom_mid=0, pen_mid_atom=0, thole_pairs=0, lp_pairs=0)
-    sites, lps = pts[:, :5], pts[:, 5:7]
-    for i in range(M):
-        others = np.arange(M) != i
-        d = sites[others][None, :, :, :] - sites[i][:, None, None, :]      # (5, M-1, 5, 3)
+    n = dict(site_pairs=0, lp_pairs=0, rep_items=0, disp_items=0, ct_items=0)
+
+    def cnt(A, B):
+        d = A[:, None, :] - B[None, :, :]
         d -= L * np.round(d / L)
-        inr = np.sqrt((d * d).sum(-1)) < rc
-        n["site_pairs"] += int(inr.sum())
-        n["pen_atom_atom"] += int(inr[atom][:, :, atom].sum())
-        n["pen_atom_mid"] += int(inr[atom][:, :, ~atom].sum())
-        n["pen_mid_atom"] += int(inr[~atom][:, :, atom].sum())
-        n["thole_pairs"] += int(inr[:3].sum())
-        dl = sites[others][None, :, :, :] - lps[i][:, None, None, :]
-        dl -= L * np.round(dl / L)
-        n["lp_pairs"] += int((np.sqrt((dl * dl).sum(-1)) < rc).sum())
+        return int((np.sqrt((d * d).sum(-1)) < rc).sum())
+
+    mids = 0.5 * (pts[:, 0:1] + pts[:, 1:3])
+    for i in range(M):
+        for j in range(M):
+            if i == j:
+                continue
+            n["site_pairs"] += cnt(pts[i, :5], pts[j, :5])
+            n["lp_pairs"] += cnt(pts[i, 5:7], pts[j, :5])
+            if j > i:
+                n["rep_items"] += (cnt(mids[i], mids[j]) + cnt(mids[i], pts[j, 5:7]) + cnt(pts[i, 5:7], mids[j])
+                                   + cnt(pts[i, 5:7], pts[j, 5:7]))
+                q = [0, 1, 2, 5, 6]
+                n["disp_items"] += cnt(pts[i, q], pts[j, q])
+                n["ct_items"] += 8 * cnt(pts[i, 0:1], pts[j, 0:1])
     return n
 
 
@@ -44,15 +50,20 @@ def test_count_units_equals_brute_force():
     got = bench.count_units(s.pos, s.box, o["rc"], pts)
     ref = brute_force(pts, s.box, o["rc"])
     assert got == ref
-    assert ref["site_pairs"] > 0 and ref["pen_mid_atom"] == ref["pen_atom_mid"]
-    flops = bench.unit_flops(got)
-    assert flops == (got["site_pairs"] * bench.FLOPS_PERM_SITE_PAIR + got["pen_atom_atom"] * bench.FLOPS_PEN_ATOM_ATOM
-                     + got["pen_atom_mid"] * bench.FLOPS_PEN_ATOM_MID + got["pen_mid_atom"] * bench.FLOPS_PEN_MID_ATOM
-                     + got["thole_pairs"] * bench.FLOPS_THOLE_PAIR)
+    assert ref["site_pairs"] > 0 and ref["rep_items"] > 0 and ref["ct_items"] > 0
+    fl = bench.kernel_flops(got)
+    assert fl["real_perm"] == got["site_pairs"] * bench.FLOPS_PERM_SITE_PAIR
+    assert fl["short"] == got["rep_items"] * bench.FLOPS_REP_ITEM + got["disp_items"] * bench.FLOPS_DISP_ITEM
+    assert fl["ct"] == got["ct_items"] * bench.FLOPS_CT_ITEM
 
 
-def test_cluster_counts_are_all_ordered_pairs():
+def test_cluster_counts_are_all_pairs():
     start = np.array([0, 2, 5, 9])
     n = bench.count_units_clusters(start, 9)
-    pairs = 2 * 1 + 3 * 2 + 4 * 3
-    assert n["site_pairs"] == 25 * pairs and n["thole_pairs"] == 15 * pairs and n["lp_pairs"] == 10 * pairs
+    pairs = 1 + 3 + 6                       # unordered molecule pairs of clusters of 2, 3, 4
+    assert n == dict(site_pairs=2 * 25 * pairs, lp_pairs=2 * 10 * pairs, rep_items=16 * pairs,
+                     disp_items=25 * pairs, ct_items=8 * pairs)
+
+
+def test_spme_pass_bytes():
+    assert bench.spme_pass_bytes((64, 64, 64), 20480) == 56 * 64 ** 3 + 144 * 20480

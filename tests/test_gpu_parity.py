@@ -58,15 +58,13 @@ def test_fp64_path_matches_oracle(name):
     compare(gpu, ref, FP64_E_REL, FP64_F_RMS_REL, FP64_MU_RMS_D)
 
 
-# The two-molecule cluster is FP64-only: its elec term is a sum of 25 site
-# pairs of ~50 kcal/mol cancelling to a few kcal/mol, below FP32 resolution.
-@pytest.mark.parametrize("name", [n for n in CASES if n != "cluster2"])
+@pytest.mark.parametrize("name", list(CASES))
 def test_mixed_path_matches_oracle(name):
     import paper_2201_00804_gb300 as pkg
     s, o = CASES[name]
     ref = _ref(name, s, o)
     gpu = run_gpu(s, o, pkg.PREC_MIXED, 1e-8)
-    compare(gpu, ref, MIXED_E_REL, MIXED_F_RMS_REL, MIXED_MU_RMS_D, total_vs_terms=True)
+    compare(gpu, ref, MIXED_E_REL, MIXED_F_RMS_REL, MIXED_MU_RMS_D)
 
 
 def test_host_and_device_pointers_agree():

@@ -114,3 +114,41 @@ def test_minimize_then_md_matches_a_fresh_context():
         for t in TERMS:
             assert abs(x[t] - y[t]) <= 1e-9 * max(1.0, abs(y[t])), (t, x[t], y[t])
     assert float((pa - pb).abs().max()) <= 1e-10
+
+
+def test_mixed_path_with_extrapolated_guess_matches_oracle_along_trajectory():
+    """The mixed path as the MD workloads run it (cubic extrapolation of the
+    last four solutions as the PCG start) meets the mixed-precision bounds
+    against the oracle at later points of a trajectory, where the guess
+    comes from the history and not from the direct field."""
+    import torch
+    import oracle
+    import paper_2201_00804_gb300 as pkg
+    from gpu_util import MIXED_E_REL, MIXED_F_RMS_REL, compare
+    s, o = synth.make_config("water216")
+    pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
+    vel = torch.tensor(synth.maxwell_velocities(s, 300.0, seed=11).reshape(-1), dtype=torch.float64, device="cuda")
+    masses = torch.tensor(s.masses().reshape(-1), dtype=torch.float64, device="cuda")
+    ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
+                           ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"], precision=pkg.PREC_MIXED, warm_start=4)
+    try:
+        for step in range(1, 9):
+            pkg.sibfa_md_steps(ctx, pos, vel, masses, 0.5, 1)
+            if step in (6, 8):
+                # the same positions through the same context: its guess is the
+                # extrapolation of the trajectory's last four solutions
+                x = pos.clone()
+                F = torch.zeros_like(x)
+                mu = torch.zeros_like(x)
+                e = pkg.sibfa_energy_forces(ctx, x, F)
+                it = pkg.sibfa_last_stats(ctx)[0]
+                pkg.sibfa_solve_dipoles(ctx, x, mu, o["pcg_tol"])
+                torch.cuda.synchronize()
+                snap = synth.System(pos=x.cpu().numpy().reshape(-1, 3, 3), mp_local=s.mp_local, box=s.box)
+                ref = oracle.evaluate(snap, o, tol_D=1e-11)
+                gpu = {"terms": e, "forces": F.cpu().numpy().reshape(-1, 3, 3), "mu": mu.cpu().numpy().reshape(-1, 3, 3)}
+                # the workload's dipole tolerance (1e-8 D here) bounds the dipole error
+                compare(gpu, ref, MIXED_E_REL, MIXED_F_RMS_REL, 1e-6)
+                assert it < 30, it
+    finally:
+        pkg.sibfa_destroy(ctx)
