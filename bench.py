@@ -1,12 +1,15 @@
 #!/usr/bin/env python
 """SIBFA energy + force benchmark on one GB300 (or N independent replicas).
 
-Workload: the 4096-water box (12,288 atoms, 49.66 A, rc 9 A, SPME 64^3 order
-5, alpha 0.4 A^-1), mixed precision (FP32 pair and grid arithmetic, FP64
-accumulation and solver scalars), PCG tolerance 1e-6 D with warm start
-(by default the initial guess extrapolates the dipoles of the last four
-steps; --warm-start 1 takes the previous step's), velocity-Verlet NVE at
-0.5 fs from 300 K Maxwell velocities.  A step is one
+Default workload: the 32,000-water box (96,000 atoms, 98.6 A, rc 9 A, SPME
+108^3 order 5, alpha 0.4 A^-1), mixed precision (FP32 pair and grid
+arithmetic, FP64 accumulation and solver scalars), PCG tolerance 1e-6 D
+with warm start (by default the initial guess extrapolates the dipoles of
+the last four steps; --warm-start 1 takes the previous step's),
+velocity-Verlet NVE at 0.5 fs from 300 K after an untimed relaxation and
+velocity-rescaled equilibration; the plain FP64 GPU path is timed on the
+same workload.  --workload water4096 (4096 waters, 49.66 A, SPME 64^3),
+clusters4096 and served select the other workloads.  A step is one
 velocity-Verlet step: one full energy + force evaluation (sites, neighbour
 list, real-space pair terms, SPME, charge transfer, polarization solve,
 forces) plus the two half kicks.  Metric: atom-steps/s.
@@ -61,7 +64,9 @@ def parse():
     ap.add_argument("--warm-start", type=int, default=4, choices=[1, 2, 3, 4],
                     help="PCG initial guess along the trajectory: 1 previous dipoles, 2-4 extrapolation through "
                          "the last 2-4 steps' dipoles")
-    ap.add_argument("--workload", default="water4096", choices=["water4096", "water32000", "clusters4096", "served"])
+    ap.add_argument("--workload", default="water32000", choices=["water4096", "water32000", "clusters4096", "served"])
+    ap.add_argument("--equil-steps", type=int, default=200,
+                    help="untimed velocity-rescaled MD steps (300 K) after the relaxation, before the NVE steps")
     ap.add_argument("--rates", default="20,50,100", help="served: arrival rates (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="served: arrival window per rate (s)")
     return ap.parse_args()
@@ -340,7 +345,7 @@ def run_reference(args, dist, rank, ws):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": SAMPLE},
+            "config": {"workload": WORKLOADS.get(args.workload, WORKLOAD), "sample": SAMPLE},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
                              "sample": SAMPLE},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -390,24 +395,66 @@ def setup(name, pkg, synth, precision, stream, warm=1):
     return s, o, ctx, make_api, pos, vel, masses
 
 
-def timed_steps(pkg, ctx, pos, vel, masses, steps, stream, flush, dt_fs=0.5, keep=False):
-    """steps velocity-Verlet steps, each timed with CUDA events on the
-    caller's stream after an L2 flush; returns (ms total, iterations, snapshots)."""
+KB_KCAL = 0.0019872041          # kcal/(mol K)
+AMU_A2_FS2 = 4.184e-4           # kcal/mol per amu A^2/fs^2
+
+
+def kinetic(vel, masses3):
+    """Kinetic energy (kcal/mol) of device velocities (A/fs)."""
+    return 0.5 * float((masses3 * vel * vel).sum()) / AMU_A2_FS2
+
+
+def intra_energy(pos, k_bond=529.6, r0=0.9572, k_angle=34.05, theta0_deg=104.52):
+    """The MD driver's intramolecular support potential (kcal/mol) at device
+    positions: k_bond (r - r0)^2 per O-H bond + k_angle (theta - theta0)^2 per
+    H-O-H angle (the same definition as the run options)."""
     import torch
-    total, iters, snaps = 0.0, [], []
+    x = pos.view(-1, 3, 3)
+    b1, b2 = x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]
+    r1, r2 = b1.norm(dim=-1), b2.norm(dim=-1)
+    th = torch.acos(((b1 * b2).sum(-1) / (r1 * r2)).clamp(-1.0, 1.0))
+    return float((k_bond * ((r1 - r0) ** 2 + (r2 - r0) ** 2) + k_angle * (th - math.radians(theta0_deg)) ** 2).sum())
+
+
+def equilibrate(pkg, ctx, pos, vel, masses, n_min=20, n_thermo=200, temp=300.0, every=5, dt_fs=0.5):
+    """Untimed preparation of an MD workload from its random starting
+    structure: capped steepest descent, then velocity-Verlet steps with the
+    velocities rescaled to `temp` every `every` steps, which removes the heat
+    that the relaxation of the lattice releases."""
+    m3 = masses.repeat_interleave(3)
+    ndof = vel.numel() - 3
+    pkg.sibfa_minimize(ctx, pos, n_min, 0.01)
+    for _ in range(n_thermo // every):
+        pkg.sibfa_md_steps(ctx, pos, vel, masses, dt_fs, every)
+        T = 2.0 * kinetic(vel, m3) / (ndof * KB_KCAL)
+        vel.mul_(math.sqrt(temp / T))
+    return 2.0 * kinetic(vel, m3) / (ndof * KB_KCAL)
+
+
+def timed_steps(pkg, ctx, pos, vel, masses, steps, stream, flush, dt_fs=0.5, keep=False, energy=False):
+    """steps velocity-Verlet steps, each timed with CUDA events on the
+    caller's stream after an L2 flush; returns (ms total, iterations,
+    snapshots, total energies).  With energy=True the total energy (kinetic +
+    intermolecular + intramolecular support) after each step is recorded,
+    outside the timed span."""
+    import torch
+    m3 = masses.repeat_interleave(3)
+    total, iters, snaps, etot = 0.0, [], [], []
     for _ in range(steps):
         flush.zero_()                       # evict L2 (512 MB > 129 MB) before every timed step
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        pkg.sibfa_md_steps(ctx, pos, vel, masses, dt_fs, 1)
+        e = pkg.sibfa_md_steps(ctx, pos, vel, masses, dt_fs, 1)
         b.record(stream)
         b.synchronize()
         total += a.elapsed_time(b)
         iters.append(pkg.sibfa_last_stats(ctx)[0])
         if keep:
             snaps.append(pos.clone())
-    return total, iters, snaps
+        if energy:
+            etot.append(kinetic(vel, m3) + e["total"] + intra_energy(pos))
+    return total, iters, snaps, etot
 
 
 def smooth235(n):
@@ -544,9 +591,9 @@ def main():
     s, o, ctx, make_api, pos, vel, masses = setup(args.workload, pkg, synth, pkg.PREC_MIXED, stream, args.warm_start)
     M = s.n_mol
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    # The random starting structures are far from equilibrium (close
-    # hydrogens): relax them first (untimed), then warm up.
-    pkg.sibfa_minimize(ctx, pos, 20, 0.01)
+    # The random starting structures are far from equilibrium: relax them and
+    # equilibrate at 300 K first (untimed), then warm up in NVE.
+    t_equil = equilibrate(pkg, ctx, pos, vel, masses, n_min=20, n_thermo=args.equil_steps)
     pos0, vel0 = pos.clone(), vel.clone()
     for _ in range(max(3, args.warmup)):
         pkg.sibfa_md_steps(ctx, pos, vel, masses, 0.5, 1)
@@ -557,7 +604,8 @@ def main():
     barrier(dist)
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        total_ms, iters, snapshots = timed_steps(pkg, ctx, pos, vel, masses, args.steps, stream, flush, keep=True)
+        total_ms, iters, snapshots, etot = timed_steps(pkg, ctx, pos, vel, masses, args.steps, stream, flush,
+                                                       keep=True, energy=True)
     torch.cuda.synchronize()
     barrier(dist)
     launches = pkg.sibfa_kernel_launches(ctx) - l0
@@ -652,8 +700,8 @@ def main():
         for _ in range(2):
             pkg.sibfa_md_steps(c64, p64, v64, m64, 0.5, 1)
         torch.cuda.synchronize()
-        n64 = 3
-        ms64, it64, _ = timed_steps(pkg, c64, p64, v64, m64, n64, stream, flush)
+        n64 = 10
+        ms64, it64, _, _ = timed_steps(pkg, c64, p64, v64, m64, n64, stream, flush)
         ms64 = max_over_ranks(dist, ms64) / n64
         pkg.sibfa_destroy(c64)
         fp64 = {"value": ws * 3 * M / (ms64 / 1000.0), "unit": UNIT, "ms_per_step": ms64, "steps": n64,
@@ -662,7 +710,7 @@ def main():
     if rank != 0:
         return
     cpu = None
-    if ws == 1 and not args.no_cpu_baseline and args.workload == "water4096":
+    if ws == 1 and not args.no_cpu_baseline and args.workload in ("water4096", "water32000"):
         cpu = cpu_baseline()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -674,6 +722,11 @@ def main():
         "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
         "rooflines": lines, "fp32_peak": peak,
         "cpu_baseline": cpu, "fp64_gpu_path": fp64, "pcg_iters_mean": float(np.mean(iters)), "phases_ms": phases,
+        "nve": {"equilibration": f"20 capped steepest-descent steps, {args.equil_steps} velocity-rescaled steps at "
+                                 f"300 K (T after: {t_equil:.1f} K), {max(3, args.warmup)} NVE warm-up steps",
+                "total_energy_first": etot[0], "total_energy_last": etot[-1],
+                "drift_kcal_per_mol_atom_per_ps": (etot[-1] - etot[0]) / (3 * M) / (0.5e-3 * max(1, len(etot) - 1)),
+                "temperature_end_K": 2.0 * kinetic(vel, masses.repeat_interleave(3)) / ((vel.numel() - 3) * KB_KCAL)},
         "tuned": {"short_blocks_per_sm": tb, "fixed": tdone},
     }
     print(json.dumps(line), flush=True)

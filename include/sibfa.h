@@ -262,6 +262,20 @@ const char *sibfa_noalloc_last_error(void);
 sibfa_status sibfa_alu_peak(int fp64, int iters, int blocks, double *ms, double *flops);
 const char *sibfa_alu_peak_error(void);
 
+/* The library's FP32 elementary kernels beside CUDA's functions, for tests
+ * that hold them to an error bound (test support; the paper has no
+ * counterpart).  x, out: DEVICE float arrays; asynchronous on `stream`.
+ *   fn 0: out[2k] = the Newton-refined reciprocal square root of x[k] used by
+ *         the pair kernels, out[2k+1] = rsqrtf(x[k]);
+ *   fn 1: out[2k] = the Newton-refined reciprocal of x[k], out[2k+1] =
+ *         1.0f / x[k] (IEEE division);
+ *   fn 2: x[k] = r; out[5k..5k+3] = the radial kernels g_0..g_3 of
+ *         erf(alpha r)/r (g_{n+1} = (1/r) dg_n/dr) used by the intramolecular
+ *         Ewald exclusions, out[5k+4] = erff(alpha r) / r.
+ * out holds 2n (fn 0, 1) or 5n (fn 2) floats.  SIBFA_E_INVALID for another
+ * fn or null arrays. */
+sibfa_status sibfa_math_selftest(int fn, int n, const float *x, float alpha, float *out, void *stream);
+
 void sibfa_destroy(sibfa_ctx *ctx);
 
 /* ---------------------------------------------------------------------------

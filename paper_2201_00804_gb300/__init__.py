@@ -12,6 +12,7 @@ from .sibfa import (  # noqa: F401
     load_library,
     sibfa_alu_peak,
     sibfa_cluster_terms,
+    sibfa_math_selftest,
     sibfa_create,
     sibfa_destroy,
     sibfa_energy_forces,

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libsibfa.so")
 OBJDIR = os.path.join(HERE, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["k_sites.cu", "k_pair.cu", "k_short.cu", "k_spme.cu", "k_pol.cu", "k_intra.cu", "capi.cu", "noalloc.cu", "server.cu", "peak.cu"]
+SOURCES = ["k_sites.cu", "k_pair.cu", "k_short.cu", "k_spme.cu", "k_pol.cu", "k_intra.cu", "capi.cu", "noalloc.cu", "server.cu", "peak.cu", "selftest.cu"]
 
 
 def _nvcc():

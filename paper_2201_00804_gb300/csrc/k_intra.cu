@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(128) k_intra_perm(KParams p, DevState<R> d) {
         e -= self * al * spi;
     }
     const double ke = p.ke;
-    const double esum = warp_sum(double(e));
+    // FP32 path: the energy comes from k_intra_energy64
+    const double esum = sizeof(R) == 8 ? warp_sum(double(e)) : 0.0;
     // lanes 22-26 carry lone pair 0, lanes 27-31 lone pair 1
     const double v0 = warp_sum(lane < 27 ? double(vl) : 0.0);
     const double v1 = warp_sum(lane >= 27 ? double(vl) : 0.0);
@@ -160,10 +161,84 @@ __global__ void __launch_bounds__(128) k_intra_perm(KParams p, DevState<R> d) {
     if (p.vir) vir_warp_out(d, m, W, ke, lane);
 }
 
+// Global multipole and offset from O of site s of molecule m, in FP64 from
+// the FP64 positions and local multipoles (frames as in the site kernel).
+__device__ inline void site64(const double *x, const double *ml, int s, Mp<double> &M, V3<double> &off) {
+    const V3<double> r1 = mk(x[3] - x[0], x[4] - x[1], x[5] - x[2]);
+    const V3<double> r2 = mk(x[6] - x[0], x[7] - x[1], x[8] - x[2]);
+    const double s1 = rsqrt(dot(r1, r1)), s2 = rsqrt(dot(r2, r2));
+    V3<double> zv, xv, ex, ey, ez;
+    frame_generators(site_frame(s), r1, r2, s1, s2, zv, xv);
+    frame_axes(zv, xv, ex, ey, ez);
+    const V3<double> so[NS] = {mk(0.0, 0.0, 0.0), r1, r2, 0.5 * r1, 0.5 * r2};
+    off = so[s];
+    const double *l = ml + s * NMP;
+    M.q = l[0];
+    M.mu = l[1] * ex + l[2] * ey + l[3] * ez;
+    const double tl[3][3] = {{l[4], l[7], l[8]}, {l[7], l[5], l[9]}, {l[8], l[9], l[6]}};
+    const V3<double> e[3] = {ex, ey, ez};
+    double T[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const V3<double> A = tl[a][b] * e[b];
+            const double ea[3] = {e[a].x, e[a].y, e[a].z}, Ab[3] = {A.x, A.y, A.z};
+            for (int u = 0; u < 3; ++u)
+                for (int v = 0; v < 3; ++v) T[u][v] += ea[u] * Ab[v];
+        }
+    M.th.xx = T[0][0]; M.th.yy = T[1][1]; M.th.zz = T[2][2];
+    M.th.xy = T[0][1]; M.th.xz = T[0][2]; M.th.yz = T[1][2];
+}
+
+// Mixed path: the intramolecular Ewald energy (erf part of the 10 site pairs
+// of each molecule and the five Gaussian self terms) in FP64.  These terms
+// are ~50 kcal/mol per molecule and cancel against the reciprocal sum; the
+// same geometry repeats in every rigid molecule, so FP32 rounding of them
+// adds up coherently over the box (about 1e-6 of the total energy at a few
+// hundred waters).  Sixteen lanes per molecule: lanes 0-9 the pairs, lanes
+// 10-14 the self terms; FP64 throughout.
+__global__ void __launch_bounds__(128) k_intra_energy64(KParams p, const double *pos, const double *mp_local,
+                                                        double *epart) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = g >> 4, t = g & 15;
+    const bool live = m < p.M;
+    const double al = p.alpha, spi = 0.56418958354775628695;
+    double e = 0.0;
+    if (live) {
+        const double *x = pos + m * 9, *ml = mp_local + m * NS * NMP;
+        if (t < 10) {
+            const int a = c_pair10[t][0], b = c_pair10[t][1];
+            Mp<double> Ma, Mb;
+            V3<double> oa, ob;
+            site64(x, ml, a, Ma, oa);
+            site64(x, ml, b, Mb, ob);
+            const V3<double> xv = oa - ob;
+            double gg[4];
+            g_erf_s<double, 3>(dot(xv, xv), al, gg);
+            FieldTerms<double> f;
+            source_field<double, 2>(Mb, xv, gg, f);
+            e = -(Ma.q * f.phi + dot(Ma.mu, f.d1) + symdd(Ma.th, f.d2) * (1.0 / 3.0));
+        } else if (t < 10 + NS) {
+            Mp<double> M;
+            V3<double> o;
+            site64(x, ml, t - 10, M, o);
+            const double self = M.q * M.q + (2.0 / 3.0) * al * al * dot(M.mu, M.mu) +
+                                (8.0 / 45.0) * al * al * al * al * symdd(M.th, M.th);
+            e = -self * al * spi;
+        }
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o, 16);
+    if (live && t == 0) epart[m * NTERM + T_ELEC] += p.ke * e;
+}
+
 template <typename R>
 void launch_intra_perm(const KParams &p, DevState<R> &d, Launch L) {
     k_intra_perm<R><<<(p.M + IW - 1) / IW, 32 * IW, 0, L.s>>>(p, d);
     count(L);
+    if (sizeof(R) == 4) {
+        k_intra_energy64<<<(p.M * 16 + 127) / 128, 128, 0, L.s>>>(p, d.pos, d.mp_local, d.epart);
+        count(L);
+    }
 }
 
 __constant__ int c_pair3[3][2] = {{0, 1}, {0, 2}, {1, 2}};

@@ -63,27 +63,40 @@ struct PermAcc {
 // Periodic systems: rv is the source position relative to O_i (O-O
 // displacement plus the source's offset).  Gas phase: rv is the O-O
 // displacement D = O_j - O_i itself and the pair displacement is formed as
-// x = (target offset - source offset) - D.  The charge-charge energy is then
-// taken as q_t q_s (1/r - 1/R), R = |D| the same for all site pairs of the
-// molecule pair, from 1/r - 1/R = (R^2 - r^2) / (r R (r + R)) with
-// R^2 - r^2 = 2 sv.D - sv.sv (sv = target - source offsets): a small,
-// cancellation-free term per site pair; the missing sum_ts q_t q_s / R =
-// Q_i Q_j / R is added once per molecule pair (zero for neutral molecules).
-// In FP32 this keeps the multipole energy of a gas-phase cluster, whose
-// site-pair charge terms of ~10 kcal/mol cancel to the molecular
-// interaction, about 15x closer to FP64 than q_t q_s / r summed directly.
+// x = (target offset - source offset) - D.  The energy terms that involve a
+// charge are taken as differences from reference points, because over a
+// neutral molecule they cancel to the molecular interaction (site-pair
+// terms of ~10 kcal/mol for a total of a few) and FP32 would keep only their
+// rounding: with a = 1/|x|, b = 1/|y| for a reference vector y and
+// d = |y|^2 - |x|^2 computed from the offsets without cancellation,
+//   a - b = d a b / (|x| + |y|),  a^3 - b^3 = (a - b)(a^2 + ab + b^2),
+//   a^5 - b^5 = (a - b)(a^4 + a^3 b + a^2 b^2 + a b^3 + b^4).
+//   charge-charge:        y0 = -D (O_i - O_j):  q_t q_s (a - b0);
+//   target charge in the source dipole/quadrupole potential, y1 = O_i - x_s:
+//     q_t [mu_s.o_t a^3 + mu_s.y1 (a^3 - b1^3) + (o_t Th_s o_t + 2 y1 Th_s o_t) a^5
+//          + y1 Th_s y1 (a^5 - b1^5)]   (x = y1 + o_t);
+//   source charge in the target dipole/quadrupole, y2 = x_t - O_j:
+//     q_s [mu_t.o_s a^3 - mu_t.y2 (a^3 - b2^3) + (o_s Th_t o_s - 2 y2 Th_t o_s) a^5
+//          + y2 Th_t y2 (a^5 - b2^5)]   (x = y2 - o_s).
+// The remainders (the reference values times the molecule's total charge,
+// zero for neutral molecules) are added once per molecule pair (Q_i Q_j / R),
+// per target site and neighbour, and per source site on the O target's warp.
+// For gas-phase clusters this brings the FP32 multipole energy some 30x
+// closer to FP64 than summing the site-pair energies directly.
 template <typename R, bool PER, bool ATOM_SRC, bool VIR>
 __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d, int w, bool is_lp, V3<R> ot,
-                                          const Mp<R> &mt, R Nt_, int js, V3<R> rv, size_t te, PermAcc<R> &A) {
+                                          const Mp<R> &mt, R Nt_, R Qi, int js, V3<R> rv, size_t te,
+                                          PermAcc<R> &A) {
     const Scal<R> &S = sc<R>(p);
     const R third = R(1) / R(3);
     const int j = js >> 3, s = js & 7;
-    V3<R> x, sv;
+    V3<R> x, sv, osrc;
     if (PER) {
         x = ot - rv;
     } else {
         const R *os = d.off + (j * NP + s) * 3;
-        sv = ot - mk(__ldg(os), __ldg(os + 1), __ldg(os + 2));
+        osrc = mk(__ldg(os), __ldg(os + 1), __ldg(os + 2));
+        sv = ot - osrc;
         x = sv - rv;
     }
     const R r2 = dot(x, x);
@@ -102,15 +115,37 @@ __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d
     }
     FieldTerms<R> f;
     source_field<R, 3>(ms, x, g, f);
-    R qphi;
+    R U;
     if (PER) {
-        qphi = mt.q * f.phi;
+        U = mt.q * f.phi + dot(mt.mu, f.d1) + third * symdd(mt.th, f.d2);
     } else {
-        const R RR = dot(rv, rv), Rinv = rsqrt_(RR);
-        const R dinv = (R(2) * dot(sv, rv) - dot(sv, sv)) * rinv * Rinv / (r + RR * Rinv);   // 1/r - 1/R
-        qphi = mt.q * (f.phi_mp + ms.q * dinv);
+        const R a = rinv, a3 = a * a * a, a5 = a3 * a * a;
+        // charge-charge, reference -D
+        const R RR = dot(rv, rv), b0 = rsqrt_(RR);
+        U = mt.q * ms.q * ((R(2) * dot(sv, rv) - dot(sv, sv)) * a * b0 / (r + RR * b0));
+        // target charge, reference O_i - x_s
+        const V3<R> y1 = R(-1) * (rv + osrc);
+        const R y1y1 = dot(y1, y1), b1 = rsqrt_(y1y1);
+        R B3, B5;
+        ref_diff35(-(R(2) * dot(y1, ot) + dot(ot, ot)), a, b1, r, y1y1 * b1, B3, B5);
+        const V3<R> Tso = symv(ms.th, ot), Tsy = symv(ms.th, y1);
+        const R mu_y1 = dot(ms.mu, y1), y1Ty1 = dot(y1, Tsy);
+        U += mt.q * (dot(ms.mu, ot) * a3 + mu_y1 * B3 + (dot(ot, Tso) + R(2) * dot(y1, Tso)) * a5 + y1Ty1 * B5);
+        if (w == 0) {   // sum over the target sites of q_t times the reference value: Q_i phi_s(y1)
+            const R b13 = b1 * b1 * b1;
+            U += Qi * (mu_y1 * b13 + y1Ty1 * b13 * b1 * b1);
+        }
+        // source charge, reference x_t - O_j
+        const V3<R> y2 = ot - rv;
+        const R y2y2 = dot(y2, y2), b2 = rsqrt_(y2y2);
+        R C3, C5;
+        ref_diff35(R(2) * dot(y2, osrc) - dot(osrc, osrc), a, b2, r, y2y2 * b2, C3, C5);
+        const V3<R> Tto = symv(mt.th, osrc), Tty = symv(mt.th, y2);
+        U += ms.q * (dot(mt.mu, osrc) * a3 - dot(mt.mu, y2) * C3 + (dot(osrc, Tto) - R(2) * dot(y2, Tto)) * a5 +
+                     dot(y2, Tty) * C5);
+        // target dipole and quadrupole in the source dipole and quadrupole field
+        U += dot(mt.mu, f.d1_mp) + third * symdd(mt.th, f.d2_mp);
     }
-    const R U = qphi + dot(mt.mu, f.d1) + third * symdd(mt.th, f.d2);
     A.Ue.add(R(0.5) * U);
     const V3<R> gel = target_grad(mt, ms, x, g, f);
     A.gr = A.gr + gel;
@@ -224,10 +259,10 @@ __global__ void __launch_bounds__(32 * NW, NW == 5 ? (PER ? 3 : 4) : (NW == 3 ? 
 #pragma unroll
     for (int k = 0; k < 9; ++k) A.W[k] = R(0);
     int ha = 0, ta = 0, hm = 0, tm = 0;   // queue heads and tails (warp-uniform, monotone)
-    // gas phase: charge of molecule i (the molecule-pair term of the shifted
-    // charge-charge energy, taken by the O-site warp)
+    // gas phase: charge of molecule i (remainders of the reference-difference
+    // energy terms, see perm_pair)
     R Qi = R(0);
-    if (!PER && !is_lp && w == 0)
+    if (!PER && !is_lp)
         for (int s = 0; s < NS; ++s) Qi += d.gmp[(i * NS + s) * GMP];
     const int nn = d.nnbr[i];
     for (int base = 0;; base += 32) {
@@ -248,11 +283,16 @@ __global__ void __launch_bounds__(32 * NW, NW == 5 ? (PER ? 3 : 4) : (NW == 3 ? 
                 if (!PER || dot(x, x) < rc2) bits |= 1u << s;
                 if (!PER) rs[s] = dO;   // queued: the O-O displacement (see perm_pair)
             }
-            if (!PER && !is_lp && w == 0) {
+            if (!PER && !is_lp) {
                 R Qj = R(0);
                 for (int s = 0; s < NS; ++s) Qj += d.gmp[(j * NS + s) * GMP];
-                const R RR = dot(dO, dO);
-                A.Ue.add(R(0.5) * Qi * Qj * rsqrt_(RR));
+                // Q_j times the reference value of the target's terms: the
+                // charge-charge one (O target only) and the dipole/quadrupole ones
+                const V3<R> y2 = ot - dO;
+                const R b2 = rsqrt_(dot(y2, y2)), b23 = b2 * b2 * b2;
+                R rem = -dot(mt.mu, y2) * b23 + dot(y2, symv(mt.th, y2)) * b23 * b2 * b2;
+                if (w == 0) rem += Qi * rsqrt_(dot(dO, dO));
+                A.Ue.add(R(0.5) * Qj * rem);
             }
         }
         int na, nm;
@@ -275,14 +315,15 @@ __global__ void __launch_bounds__(32 * NW, NW == 5 ? (PER ? 3 : 4) : (NW == 3 ? 
         while (ta - ha >= 32 || (flush && ta > ha)) {
             if (lane < ta - ha) {
                 const int e = (ha + lane) % QCAP_A;
-                perm_pair<R, PER, true, VIR>(p, d, w, is_lp, ot, mt, Nt_, q.js[e], q.at(e), tbase + ha + lane, A);
+                perm_pair<R, PER, true, VIR>(p, d, w, is_lp, ot, mt, Nt_, Qi, q.js[e], q.at(e), tbase + ha + lane,
+                                             A);
             }
             ha += min(32, ta - ha);
         }
         while (tm - hm >= 32 || (flush && tm > hm)) {
             if (lane < tm - hm) {
                 const int e = QCAP_A + (hm + lane) % QCAP_M;
-                perm_pair<R, PER, false, VIR>(p, d, w, is_lp, ot, mt, Nt_, q.js[e], q.at(e), 0, A);
+                perm_pair<R, PER, false, VIR>(p, d, w, is_lp, ot, mt, Nt_, Qi, q.js[e], q.at(e), 0, A);
             }
             hm += min(32, tm - hm);
         }

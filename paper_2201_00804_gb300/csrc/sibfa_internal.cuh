@@ -456,6 +456,8 @@ struct FieldTerms {
     R phi_mp;   // the dipole and quadrupole part of phi (phi - q g0)
     V3<R> d1;
     Sym<R> d2;
+    V3<R> d1_mp;   // the dipole and quadrupole parts of d1, d2 (without the charge)
+    Sym<R> d2_mp;
     // intermediates for the third-derivative contraction
     R Rs, S;
     V3<R> U, W, v;
@@ -473,6 +475,8 @@ __device__ inline void source_field(const Mp<R> &s, V3<R> x, const R *g, FieldTe
         const R P = s.q * g[1] - sx * g[2] + third * w * g[3];
         const V3<R> Q = R(-g[1]) * s.mu + (twoth * g[2]) * v;
         f.d1 = P * x + Q;
+        const R Pm = third * w * g[3] - sx * g[2];
+        f.d1_mp = Pm * x + Q;
         if constexpr (NDER >= 2) {
             const R Rr = s.q * g[2] - sx * g[3] + third * w * g[4];
             const V3<R> U = R(-g[2]) * s.mu + (twoth * g[3]) * v;
@@ -483,6 +487,13 @@ __device__ inline void source_field(const Mp<R> &s, V3<R> x, const R *g, FieldTe
             f.d2.xy = x.x * x.y * Rr + x.x * U.y + x.y * U.x + t2 * s.th.xy;
             f.d2.xz = x.x * x.z * Rr + x.x * U.z + x.z * U.x + t2 * s.th.xz;
             f.d2.yz = x.y * x.z * Rr + x.y * U.z + x.z * U.y + t2 * s.th.yz;
+            const R Rm = third * w * g[4] - sx * g[3];
+            f.d2_mp.xx = Pm + x.x * x.x * Rm + R(2) * x.x * U.x + t2 * s.th.xx;
+            f.d2_mp.yy = Pm + x.y * x.y * Rm + R(2) * x.y * U.y + t2 * s.th.yy;
+            f.d2_mp.zz = Pm + x.z * x.z * Rm + R(2) * x.z * U.z + t2 * s.th.zz;
+            f.d2_mp.xy = x.x * x.y * Rm + x.x * U.y + x.y * U.x + t2 * s.th.xy;
+            f.d2_mp.xz = x.x * x.z * Rm + x.x * U.z + x.z * U.x + t2 * s.th.xz;
+            f.d2_mp.yz = x.y * x.z * Rm + x.y * U.z + x.z * U.y + t2 * s.th.yz;
             f.Rs = Rr;
             f.U = U;
             if constexpr (NDER >= 3) {
@@ -492,6 +503,17 @@ __device__ inline void source_field(const Mp<R> &s, V3<R> x, const R *g, FieldTe
             }
         }
     }
+}
+
+// a^3 - b^3 and a^5 - b^5 for a = 1/|x|, b = 1/|y| from dd = |y|^2 - |x|^2
+// and the lengths rx = |x|, ry = |y|, without the cancellation of the direct
+// differences (a - b = dd a b / (rx + ry)).
+template <typename R>
+__device__ inline void ref_diff35(R dd, R a, R b, R rx, R ry, R &d3, R &d5) {
+    const R d1 = dd * a * b / (rx + ry);
+    const R a2 = a * a, b2 = b * b, ab = a * b;
+    d3 = d1 * (a2 + ab + b2);
+    d5 = d1 * (a2 * a2 + ab * (a2 + b2) + ab * ab + b2 * b2);
 }
 
 // Target contraction.  Energy U = q phi + mu.d1 + (1/3) Th:d2; gradient of U

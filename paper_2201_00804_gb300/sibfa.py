@@ -131,6 +131,8 @@ def load_library(path: str = LIB_PATH):
     lib.sibfa_alu_peak.restype = C.c_int
     lib.sibfa_alu_peak_error.argtypes = []
     lib.sibfa_alu_peak_error.restype = C.c_char_p
+    lib.sibfa_math_selftest.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_float, C.c_void_p, C.c_void_p]
+    lib.sibfa_math_selftest.restype = C.c_int
     lib.sibfa_destroy.argtypes = [C.c_void_p]
     lib.sibfa_destroy.restype = None
     lib.sibfa_last_error.argtypes = [C.c_void_p]
@@ -282,6 +284,23 @@ def sibfa_alu_peak(fp64: bool = False, iters: int = 4096, blocks: int = 0):
     if st != SIBFA_OK:
         raise SibfaError(st, lib.sibfa_alu_peak_error().decode())
     return fl.value, ms.value
+
+
+def sibfa_math_selftest(fn: int, x, alpha: float = 0.0):
+    """The library's FP32 elementary kernels beside CUDA's on a float32 CUDA
+    tensor x: returns a float32 CUDA tensor of shape (n, 2) (fn 0, 1) or
+    (n, 5) (fn 2), see include/sibfa.h."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+        raise TypeError("x must be a contiguous float32 CUDA tensor")
+    lib = load_library()
+    w = 5 if fn == 2 else 2
+    out = torch.empty((x.numel(), w), dtype=torch.float32, device=x.device)
+    st = lib.sibfa_math_selftest(int(fn), x.numel(), x.data_ptr(), float(alpha), out.data_ptr(),
+                                 torch.cuda.current_stream().cuda_stream)
+    if st != SIBFA_OK:
+        raise SibfaError(st, "sibfa_math_selftest failed")
+    return out
 
 
 def sibfa_cluster_terms(ctx, n_clusters: int):
