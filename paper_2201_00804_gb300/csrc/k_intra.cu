@@ -212,8 +212,8 @@ __global__ void __launch_bounds__(128) k_intra_energy64(KParams p, const double 
             site64(x, ml, a, Ma, oa);
             site64(x, ml, b, Mb, ob);
             const V3<double> xv = oa - ob;
-            double gg[4];
-            g_erf_s<double, 3>(dot(xv, xv), al, gg);
+            double gg[5];   // source_field to second derivatives reads g_0..g_4
+            g_erf_s<double, 4>(dot(xv, xv), al, gg);
             FieldTerms<double> f;
             source_field<double, 2>(Mb, xv, gg, f);
             e = -(Ma.q * f.phi + dot(Ma.mu, f.d1) + symdd(Ma.th, f.d2) * (1.0 / 3.0));

@@ -1,9 +1,10 @@
-"""Write synth_water4096.json: fingerprints of the seeded 4096-water inputs
-that water4096_oracle.npz was computed from (a few molecules' positions and
-local multipoles, and column sums), so that a change of the generator shows
-up on the host before the stored oracle results go stale.  Calls only synth/.
+"""Write synth_<config>.json: fingerprints of the seeded water-box inputs
+that <config>_oracle.npz was computed from (a few molecules' positions and
+local multipoles, column sums, and the parameter table), so that a change of
+the generator or of the parameters shows up on the host before the stored
+oracle results go stale.  Calls only synth/.
 
-    python tests/golden/make_synth_fixture.py
+    python tests/golden/make_synth_fixture.py [water4096 water32000]
 """
 import json
 import os
@@ -22,15 +23,17 @@ def fingerprint(name="water4096"):
     idx = [0, s.n_mol // 3, 2 * s.n_mol // 3, s.n_mol - 1]
     return {"config": name, "n_mol": s.n_mol, "box": s.box.tolist(), "molecules": idx,
             "pos": s.pos[idx].tolist(), "mp_local": s.mp_local[idx].tolist(),
-            "pos_sum": s.pos.sum(axis=(0, 1)).tolist(), "mp_sum": s.mp_local.sum(axis=0).tolist()}
+            "pos_sum": s.pos.sum(axis=(0, 1)).tolist(), "mp_sum": s.mp_local.sum(axis=0).tolist(),
+            "params": dict(synth.PARAMS)}
 
 
-def main():
-    out = os.path.join(HERE, "synth_water4096.json")
-    with open(out, "w") as f:
-        json.dump(fingerprint(), f, indent=1)
-    print(out)
+def main(names=("water4096", "water32000")):
+    for name in names:
+        out = os.path.join(HERE, f"synth_{name}.json")
+        with open(out, "w") as f:
+            json.dump(fingerprint(name), f, indent=1)
+        print(out)
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1:] or ("water4096", "water32000"))

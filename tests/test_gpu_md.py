@@ -103,3 +103,44 @@ def test_velocity_verlet_matches_host_integration():
     mag = sum(abs(e_host[k]) for k in TERMS)
     for k in TERMS:
         assert abs(e_dev[k] - e_host[k]) <= 1e-9 * mag, (k, e_dev[k], e_host[k])
+
+
+def test_nve_stays_stable_with_bounded_drift():
+    """The 216-water box as the MD workloads run it (mixed precision, PCG
+    1e-6 D, cubic-extrapolation start): 20 capped relaxation steps, 100
+    velocity-rescaled steps at 300 K, then 240 NVE steps of 0.5 fs: no error
+    status (in particular no charge-transfer denominator reaching zero), the
+    temperature stays near 300 K and the total energy (kinetic +
+    intermolecular + support) drifts by less than 0.02 kcal/mol per atom."""
+    import torch
+    import paper_2201_00804_gb300 as pkg
+    s, o = synth.make_config("water216")
+    ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
+                           ewald_alpha=o["ewald"], pcg_tol_D=1e-6, precision=pkg.PREC_MIXED, warm_start=4,
+                           md_k_bond=KB, md_r0=R0, md_k_angle=KA, md_theta0_deg=TH0_DEG)
+    pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
+    vel = torch.tensor(synth.maxwell_velocities(s, 300.0, seed=21).reshape(-1), dtype=torch.float64, device="cuda")
+    masses = torch.tensor(s.masses().reshape(-1), dtype=torch.float64, device="cuda")
+    m3 = masses.repeat_interleave(3)
+    ndof = vel.numel() - 3
+    kb, conv = 0.0019872041, 4.184e-4
+
+    def kinetic():
+        return 0.5 * float((m3 * vel * vel).sum()) / conv
+
+    try:
+        pkg.sibfa_minimize(ctx, pos, 20, 0.01)
+        for _ in range(20):
+            pkg.sibfa_md_steps(ctx, pos, vel, masses, DT_FS, 5)
+            vel.mul_(math.sqrt(300.0 / (2.0 * kinetic() / (ndof * kb))))
+        totals, temps = [], []
+        for _ in range(24):
+            e = pkg.sibfa_md_steps(ctx, pos, vel, masses, DT_FS, 10)
+            x = pos.cpu().numpy().reshape(-1, 3, 3)
+            totals.append(kinetic() + e["total"] + float(intra_energy(x).sum()))
+            temps.append(2.0 * kinetic() / (ndof * kb))
+    finally:
+        pkg.sibfa_destroy(ctx)
+    drift = abs(totals[-1] - totals[0]) / s.n_atoms
+    assert drift < 0.02, (drift, totals[0], totals[-1])
+    assert 200.0 < min(temps) and max(temps) < 450.0, temps
