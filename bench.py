@@ -65,7 +65,7 @@ def parse():
                     help="PCG initial guess along the trajectory: 1 previous dipoles, 2-4 extrapolation through "
                          "the last 2-4 steps' dipoles")
     ap.add_argument("--workload", default="water32000", choices=["water4096", "water32000", "clusters4096", "served"])
-    ap.add_argument("--equil-steps", type=int, default=200,
+    ap.add_argument("--equil-steps", type=int, default=600,
                     help="untimed velocity-rescaled MD steps (300 K) after the relaxation, before the NVE steps")
     ap.add_argument("--rates", default="20,50,100", help="served: arrival rates (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="served: arrival window per rate (s)")

@@ -134,6 +134,14 @@ typedef struct {
      * per O-H bond + k_angle (theta - theta0)^2 per H-O-H angle
      * (kcal/mol, A, rad; theta0 in degrees).  k = 0 switches a term off. */
     double md_k_bond, md_r0, md_k_angle, md_theta0_deg;
+    /* Long-range dispersion (periodic only; 0 = off): 1 adds the dispersion
+     * beyond rc for a homogeneous fluid (pair distribution 1 past the
+     * cutoff; the C6/C8/C10 pair function of the Technical Appendix
+     * integrated from rc to infinity, 2 pi M (M-1)/V times the sum over the
+     * point types) to the dispersion energy and total of every call, and
+     * E_tail on the diagonal of the virial (it scales as 1/V).  Forces do
+     * not change: the term depends on the volume only. */
+    int disp_tail;
 } sibfa_run_opts;
 
 typedef struct sibfa_ctx sibfa_ctx;

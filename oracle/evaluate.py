@@ -125,6 +125,13 @@ def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=20
             for e, nm in ((e_el, "elec"), (e_pen, "pen"), (e_rep, "rep"), (e_d, "disp"), (e_xd, "xdisp")):
                 add_grad(e, nm, retain=True)
 
+    # ---- dispersion beyond the cutoff (homogeneous-fluid tail), if asked ------
+    if st.periodic and opts.get("disp_tail"):
+        cell = st.box if ew.is_cell(st.box) else torch.diag(st.box)
+        e_tail = tm.disp_tail(M, 1.0, st.rc, P) / torch.linalg.det(cell)
+        acc(e_tail, "disp")
+        add_grad(e_tail, "disp")
+
     # ---- reciprocal, self and intramolecular corrections --------------------
     Psi_perm = None
     if st.periodic:

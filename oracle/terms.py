@@ -396,6 +396,39 @@ def disp_pairs(S, i, j, sh, P, rc):
     return e_disp, e_xd
 
 
+def disp_tail(n_mol, volume, rc, P):
+    """Dispersion beyond the cutoff for a homogeneous fluid (pair distribution
+    1 past rc): 2 pi N (N-1) / V sum over the point types u, v of one molecule
+    (O, H1, H2, LP1, LP2) of the integral from rc to infinity of r^2 e_uv(r),
+    with e_uv the damped C6/C8/C10 pair function of the Technical Appendix
+    (prefactors as in disp_pairs).  Each C_n term integrates in closed form:
+    with d = c/r - 1 (c = (rv_u + rv_v) alpha_disp) and m = r/k
+    (k = 2 sqrt(rv_u rv_v)),
+      int_rc^inf r^2 C_n e^{-g d} (k/r)^n dr
+        = C_n e^{g} k^n (g c)^{3-n} Gamma(n-3) P(n-3, g c / rc),
+    P the regularized lower incomplete gamma function (t = 1/r).  The
+    exchange-dispersion, exponential in r, is negligible past the cutoff."""
+    from scipy.special import gamma as Gf, gammainc
+    n = P["n_lp"]
+    rv = [P["rvdw_disp_o"], P["rvdw_disp_h"], P["rvdw_disp_h"], P["rvdw_disp_lp"], P["rvdw_disp_lp"]]
+    beta = [P["beta_o"], P["beta_h"], P["beta_h"]]
+    total = 0.0
+    for u in range(5):
+        for v in range(5):
+            if u < 3 and v < 3:
+                pref = -beta[u] * beta[v]
+            elif u >= 3 and v >= 3:
+                pref = -n * n / 4.0
+            else:
+                pref = -P["disp_delta"] / 2.0
+            c = (rv[u] + rv[v]) * P["disp_alpha"]
+            k = 2.0 * math.sqrt(rv[u] * rv[v])
+            for order, C, g in ((6, P["c6"], P["gamma6"]), (8, P["c8"], P["gamma8"]), (10, P["c10"], P["gamma10"])):
+                s = order - 3
+                total += pref * C * math.exp(g) * k ** order * (g * c) ** (-s) * Gf(s) * gammainc(s, g * c / rc)
+    return 2.0 * math.pi * n_mol * (n_mol - 1) / volume * total
+
+
 # ---------------------------------------------------------------------------
 # Polarization functionals (Technical Appendix: E_pol = 1/2 mu^T T mu - mu^T E)
 # Induced dipoles live on O, H1, H2 (mu: (M, 3, 3)).

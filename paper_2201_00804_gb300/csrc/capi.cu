@@ -79,6 +79,7 @@ struct sibfa_ctx {
     size_t dev_bytes = 0;         // device memory allocated by the context
     int last_iters = 0;
     double last_resid = 0;
+    double e_tail = 0;            // dispersion beyond rc (homogeneous fluid), added to disp and the virial
     bool have_mu = false;
     // converged dipoles of the last full evaluations (warm_start >= 2): four
     // slots of capacity * 9 doubles, the newest at hist_head - 1
@@ -276,6 +277,39 @@ void fill_scal(Scal<R> &s, const KParams &k) {
     s.ct_t = R(k.ct_t); s.ct_m = R(k.ct_m); s.ct_ae = R(k.ct_ae); s.ct_ah = R(k.ct_ah);
     for (int c = 0; c < 3; ++c) s.kl[c] = k.box[c] > 0 ? R((double)k.K[c] / k.box[c]) : R(0);
     s.ike = R(1.0 / k.ke);
+}
+
+// Dispersion beyond the cutoff for a homogeneous fluid (pair distribution 1
+// past rc): 2 pi M (M-1) / V times, over the point types u, v of a water (O,
+// H1, H2 and the two lone pairs), the integral from rc to infinity of r^2
+// times the damped C6/C8/C10 pair function.  With t = 1/r each C_n term
+// becomes pref C_n e^{g} k^n int_0^{1/rc} t^(n-4) e^{-g c t} dt
+// (c = (rv_u + rv_v) alpha_disp, k = 2 sqrt(rv_u rv_v)), a smooth integrand
+// taken by composite Simpson quadrature on 4096 intervals.  The
+// exchange-dispersion, exponential in r, is negligible past the cutoff.
+double disp_tail_energy(const sibfa_params &P, int M, double volume, double rc) {
+    const double rv[5] = {P.rvdw_disp_o, P.rvdw_disp_h, P.rvdw_disp_h, P.rvdw_disp_lp, P.rvdw_disp_lp};
+    const double beta[3] = {P.beta_o, P.beta_h, P.beta_h};
+    const double Cn[3] = {P.c6, P.c8, P.c10}, gn[3] = {P.gamma6, P.gamma8, P.gamma10};
+    const int order[3] = {6, 8, 10};
+    const int NI = 4096;
+    double total = 0;
+    for (int u = 0; u < 5; ++u)
+        for (int v = 0; v < 5; ++v) {
+            const double pref = (u < 3 && v < 3) ? -beta[u] * beta[v]
+                                                 : ((u >= 3 && v >= 3) ? -0.25 * P.n_lp * P.n_lp : -0.5 * P.disp_delta);
+            const double c = (rv[u] + rv[v]) * P.disp_alpha, k = 2.0 * std::sqrt(rv[u] * rv[v]);
+            for (int o = 0; o < 3; ++o) {
+                const double h = (1.0 / rc) / NI, b = gn[o] * c;
+                double sum = 0;
+                for (int q = 0; q <= NI; ++q) {
+                    const double t = q * h, w = (q == 0 || q == NI) ? 1.0 : (q % 2 ? 4.0 : 2.0);
+                    sum += w * std::pow(t, order[o] - 4) * std::exp(-b * t);
+                }
+                total += pref * Cn[o] * std::exp(gn[o]) * std::pow(k, order[o]) * sum * h / 3.0;
+            }
+        }
+    return 2.0 * M_PI * (double)M * (double)(M - 1) / volume * total;
 }
 
 void fill_params(KParams &k, const sibfa_params &P, const sibfa_run_opts &o, int M) {
@@ -829,7 +863,13 @@ sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_ene
     CK(cudaStreamSynchronize(ctx->s));
     CK(cudaGetLastError());
     if (forces && !is_device_ptr(forces)) std::memcpy(forces, h + 32, nb);
-    if (virial) std::memcpy(virial, h + 20, 9 * sizeof(double));
+    if (virial) {
+        std::memcpy(virial, h + 20, 9 * sizeof(double));
+        // the tail scales as 1/V at fixed cutoff: W = -dE/d eps = E_tail on the diagonal
+        virial[0] += ctx->e_tail;
+        virial[4] += ctx->e_tail;
+        virial[8] += ctx->e_tail;
+    }
     if (mu_out && !is_device_ptr(mu_out)) std::memcpy(mu_out, h + 32, nb);
     solve_stats(ctx);
     sibfa_status fl = check_flags(ctx, *(int *)(h + 16));
@@ -839,11 +879,11 @@ sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_ene
         e->elec = h[T_ELEC];
         e->pen = h[T_PEN];
         e->rep = h[T_REP];
-        e->disp = h[T_DISP];
+        e->disp = h[T_DISP] + ctx->e_tail;
         e->xdisp = h[T_XDISP];
         e->pol = h[T_POL];
         e->ct = h[T_CT];
-        e->total = h[NTERM];
+        e->total = h[NTERM] + ctx->e_tail;
     }
     if (iters) *iters = ctx->last_iters;
     if (resid) *resid = ctx->last_resid;
@@ -954,8 +994,8 @@ static sibfa_status md_impl(sibfa_ctx *ctx, double *pos, double *vel, const doub
     sibfa_status fl = check_flags(ctx, *(int *)(h + 16));
     if (fl) return fl;
     if (e) {
-        e->elec = h[T_ELEC]; e->pen = h[T_PEN]; e->rep = h[T_REP]; e->disp = h[T_DISP];
-        e->xdisp = h[T_XDISP]; e->pol = h[T_POL]; e->ct = h[T_CT]; e->total = h[NTERM];
+        e->elec = h[T_ELEC]; e->pen = h[T_PEN]; e->rep = h[T_REP]; e->disp = h[T_DISP] + ctx->e_tail;
+        e->xdisp = h[T_XDISP]; e->pol = h[T_POL]; e->ct = h[T_CT]; e->total = h[NTERM] + ctx->e_tail;
     }
     return SIBFA_OK;
 }
@@ -1041,6 +1081,8 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
         return SIBFA_E_CUDA;
     }
     fill_params(ctx->kp, *params, *opts, ctx->M);
+    if (opts->periodic && opts->disp_tail)
+        ctx->e_tail = disp_tail_energy(*params, ctx->M, opts->box[0] * opts->box[1] * opts->box[2], opts->rc);
     ctx->kp.n_cl = topo->n_clusters > 1 ? topo->n_clusters : 1;
     {
         // the most neighbours a molecule can have: the list capacity in a box,
@@ -1161,8 +1203,8 @@ static sibfa_status minimize_impl(sibfa_ctx *ctx, double *pos, int n, double cap
         if (fl) return fl;
     }
     if (e) {
-        e->elec = h[T_ELEC]; e->pen = h[T_PEN]; e->rep = h[T_REP]; e->disp = h[T_DISP];
-        e->xdisp = h[T_XDISP]; e->pol = h[T_POL]; e->ct = h[T_CT]; e->total = h[NTERM];
+        e->elec = h[T_ELEC]; e->pen = h[T_PEN]; e->rep = h[T_REP]; e->disp = h[T_DISP] + ctx->e_tail;
+        e->xdisp = h[T_XDISP]; e->pol = h[T_POL]; e->ct = h[T_CT]; e->total = h[NTERM] + ctx->e_tail;
     }
     return SIBFA_OK;
 }
