@@ -213,6 +213,7 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.vlp_r, M * 2);
     AL(d.dvlp_r, M * 6);
     AL(d.epart_r, M * NTERM);
+    AL(d.eintra, M);
     AL(d.efp_r, M * 9);
     AL(d.mu, M * 9);
     AL(d.res, M * 9);
@@ -717,6 +718,9 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
         // leaves every SM registers for the solve's small kernels
         launch_short(p, ds, Launch{ctx->s3, &ctx->launches}, 0, short_cap(ctx));
     }
+    // mixed periodic path: the FP64 intramolecular Ewald energy, beside everything else
+    if (sizeof(R) == 4 && p.periodic && !dipoles_only)
+        launch_intra_energy64(p, d, bg_short ? Launch{ctx->s3, &ctx->launches} : L);
     // Lone-pair potentials and then the charge transfer on the fourth stream
     // (the transfer after the reciprocal chain); joined before the
     // polarization energy, which copies the lambdas.
@@ -782,7 +786,8 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
     }
     if ((st = join_short(ctx))) return st;
     if (p.n_cl > 1) launch_cluster_energy(p, d, ctx->d_energy, L);
-    else launch_energy_reduce(p.M, d.epart, d.epart_r, ctx->d_energy, L);
+    else launch_energy_reduce(p.M, d.epart, d.epart_r, (sizeof(R) == 4 && p.periodic) ? d.eintra : nullptr,
+                              ctx->d_energy, L);
     return st_solve;
 }
 

@@ -194,33 +194,52 @@ __device__ inline void site64(const double *x, const double *ml, int s, Mp<doubl
 // are ~50 kcal/mol per molecule and cancel against the reciprocal sum; the
 // same geometry repeats in every rigid molecule, so FP32 rounding of them
 // adds up coherently over the box (about 1e-6 of the total energy at a few
-// hundred waters).  Sixteen lanes per molecule: lanes 0-9 the pairs, lanes
-// 10-14 the self terms; FP64 throughout.
+// hundred waters).  Sixteen lanes per molecule: lanes 0-4 build the global
+// multipoles and offsets of the five sites into shared memory, then lanes
+// 0-9 take the pairs and lanes 10-14 the self terms.  It reads only the
+// positions and local multipoles, so it runs on the lowest-priority stream
+// beside the other kernels, and writes its own per-molecule array.
+constexpr int IE_MOL = 8;   // molecules per 128-thread block
 __global__ void __launch_bounds__(128) k_intra_energy64(KParams p, const double *pos, const double *mp_local,
-                                                        double *epart) {
+                                                        double *eintra) {
+    __shared__ double sq[IE_MOL][NS], smu[IE_MOL][NS][3], sth[IE_MOL][NS][6], soff[IE_MOL][NS][3];
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int m = g >> 4, t = g & 15;
+    const int lm = threadIdx.x >> 4, m = g >> 4, t = g & 15;
     const bool live = m < p.M;
     const double al = p.alpha, spi = 0.56418958354775628695;
+    if (live && t < NS) {
+        Mp<double> M;
+        V3<double> o;
+        site64(pos + m * 9, mp_local + m * NS * NMP, t, M, o);
+        sq[lm][t] = M.q;
+        smu[lm][t][0] = M.mu.x; smu[lm][t][1] = M.mu.y; smu[lm][t][2] = M.mu.z;
+        sth[lm][t][0] = M.th.xx; sth[lm][t][1] = M.th.yy; sth[lm][t][2] = M.th.zz;
+        sth[lm][t][3] = M.th.xy; sth[lm][t][4] = M.th.xz; sth[lm][t][5] = M.th.yz;
+        soff[lm][t][0] = o.x; soff[lm][t][1] = o.y; soff[lm][t][2] = o.z;
+    }
+    __syncthreads();
+    auto site = [&](int k) {
+        Mp<double> M;
+        M.q = sq[lm][k];
+        M.mu = mk(smu[lm][k][0], smu[lm][k][1], smu[lm][k][2]);
+        M.th.xx = sth[lm][k][0]; M.th.yy = sth[lm][k][1]; M.th.zz = sth[lm][k][2];
+        M.th.xy = sth[lm][k][3]; M.th.xz = sth[lm][k][4]; M.th.yz = sth[lm][k][5];
+        return M;
+    };
     double e = 0.0;
     if (live) {
-        const double *x = pos + m * 9, *ml = mp_local + m * NS * NMP;
         if (t < 10) {
             const int a = c_pair10[t][0], b = c_pair10[t][1];
-            Mp<double> Ma, Mb;
-            V3<double> oa, ob;
-            site64(x, ml, a, Ma, oa);
-            site64(x, ml, b, Mb, ob);
-            const V3<double> xv = oa - ob;
+            const Mp<double> Ma = site(a), Mb = site(b);
+            const V3<double> xv = mk(soff[lm][a][0] - soff[lm][b][0], soff[lm][a][1] - soff[lm][b][1],
+                                     soff[lm][a][2] - soff[lm][b][2]);
             double gg[5];   // source_field to second derivatives reads g_0..g_4
             g_erf_s<double, 4>(dot(xv, xv), al, gg);
             FieldTerms<double> f;
             source_field<double, 2>(Mb, xv, gg, f);
             e = -(Ma.q * f.phi + dot(Ma.mu, f.d1) + symdd(Ma.th, f.d2) * (1.0 / 3.0));
         } else if (t < 10 + NS) {
-            Mp<double> M;
-            V3<double> o;
-            site64(x, ml, t - 10, M, o);
+            const Mp<double> M = site(t - 10);
             const double self = M.q * M.q + (2.0 / 3.0) * al * al * dot(M.mu, M.mu) +
                                 (8.0 / 45.0) * al * al * al * al * symdd(M.th, M.th);
             e = -self * al * spi;
@@ -228,17 +247,19 @@ __global__ void __launch_bounds__(128) k_intra_energy64(KParams p, const double 
     }
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o, 16);
-    if (live && t == 0) epart[m * NTERM + T_ELEC] += p.ke * e;
+    if (live && t == 0) eintra[m] = p.ke * e;
+}
+
+template <typename R>
+void launch_intra_energy64(const KParams &p, DevState<R> &d, Launch L) {
+    k_intra_energy64<<<(p.M + IE_MOL - 1) / IE_MOL, 128, 0, L.s>>>(p, d.pos, d.mp_local, d.eintra);
+    count(L);
 }
 
 template <typename R>
 void launch_intra_perm(const KParams &p, DevState<R> &d, Launch L) {
     k_intra_perm<R><<<(p.M + IW - 1) / IW, 32 * IW, 0, L.s>>>(p, d);
     count(L);
-    if (sizeof(R) == 4) {
-        k_intra_energy64<<<(p.M * 16 + 127) / 128, 128, 0, L.s>>>(p, d.pos, d.mp_local, d.epart);
-        count(L);
-    }
 }
 
 __constant__ int c_pair3[3][2] = {{0, 1}, {0, 2}, {1, 2}};
@@ -332,7 +353,8 @@ void launch_intra_polforce(const KParams &p, DevState<R> &d, Launch L) {
 
 #define INST(R)                                                                                         \
     template void launch_intra_perm<R>(const KParams &, DevState<R> &, Launch);                         \
-    template void launch_intra_polforce<R>(const KParams &, DevState<R> &, Launch);
+    template void launch_intra_polforce<R>(const KParams &, DevState<R> &, Launch);                     \
+    template void launch_intra_energy64<R>(const KParams &, DevState<R> &, Launch);
 INST(float)
 INST(double)
 

@@ -610,14 +610,16 @@ void launch_finalize(const KParams &p, DevState<R> &d, double *forces_out, Launc
 // One pass: every thread sums all terms of its molecules (independent
 // chains), then one shared-memory tree per term; the order is fixed.
 __global__ void __launch_bounds__(1024) k_energy_reduce(int M, const double *epart, const double *epart_r,
-                                                        double *out) {
+                                                        const double *eintra, double *out) {
     __shared__ double sh[32][NTERM];
     double v[NTERM];
 #pragma unroll
     for (int k = 0; k < NTERM; ++k) v[k] = 0.0;
-    for (int m = threadIdx.x; m < M; m += blockDim.x)
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
 #pragma unroll
         for (int k = 0; k < NTERM; ++k) v[k] += epart[m * NTERM + k] + epart_r[m * NTERM + k];
+        if (eintra) v[T_ELEC] += eintra[m];
+    }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < NTERM; ++k) {
@@ -641,8 +643,9 @@ __global__ void __launch_bounds__(1024) k_energy_reduce(int M, const double *epa
     }
 }
 
-void launch_energy_reduce(int M, const double *epart, const double *epart_r, double *out, Launch L) {
-    k_energy_reduce<<<1, 1024, 0, L.s>>>(M, epart, epart_r, out);
+void launch_energy_reduce(int M, const double *epart, const double *epart_r, const double *eintra, double *out,
+                          Launch L) {
+    k_energy_reduce<<<1, 1024, 0, L.s>>>(M, epart, epart_r, eintra, out);
     count(L);
 }
 

@@ -4,7 +4,9 @@ cluster alone; the batch result of a cluster matches the same cluster
 evaluated on its own.
 
 Mixed path: each term and the total within 1e-6 of the cluster's energy
-scale (the sum of its term magnitudes), force RMS relative error <= 1e-5,
+scale (the sum of its term magnitudes, or 1 kcal/mol for the weakest
+clusters: FP32 site-pair energies of a few kcal/mol leave absolute errors of
+~1e-7 kcal/mol whatever the cluster's total), force RMS relative error <= 1e-5,
 dipole RMS error <= 1e-6 D, for the workloads' multipoles and for general
 ones (dipoles of any direction and full quadrupoles on every site); the
 total of the whole batch within 1e-6 of itself.  A single random cluster's
@@ -75,6 +77,8 @@ def test_cluster_batch_matches_oracle(precision, general):
     for c, cl in enumerate(parts):
         ref = oracle.evaluate(cl, None, tol_D=1e-11)
         mag = sum(abs(ref["terms"][k]) for k in TERMS)
+        if precision == "mixed":
+            mag = max(mag, 1.0)
         for k in TERMS:
             assert abs(per[c][k] - ref["terms"][k]) <= e_tol * mag, (c, k, per[c][k], ref["terms"][k])
             sums[k] += per[c][k]
@@ -138,7 +142,7 @@ def test_full_4096_cluster_batch_sampled_against_oracle():
     got_total, ref_total = 0.0, 0.0
     for c in sample:
         ref = oracle.evaluate(parts[c], None, tol_D=1e-11)
-        mag = sum(abs(ref["terms"][k]) for k in TERMS)
+        mag = max(1.0, sum(abs(ref["terms"][k]) for k in TERMS))
         for k in TERMS + ("total",):
             assert abs(per[c][k] - ref["terms"][k]) <= MIXED_E_REL * mag, (c, k, per[c][k], ref["terms"][k])
         got_total += per[c]["total"]
