@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--warm-start", type=int, default=4, choices=[1, 2, 3, 4],
                     help="PCG initial guess along the trajectory: 1 previous dipoles, 2-4 extrapolation through "
                          "the last 2-4 steps' dipoles")
-    ap.add_argument("--workload", default="water32000", choices=["water4096", "water32000", "clusters4096", "served"])
+    ap.add_argument("--workload", default="water32000",
+                    choices=["water4096", "water32000", "water216_paper", "clusters4096", "served"])
     ap.add_argument("--equil-steps", type=int, default=600,
                     help="untimed velocity-rescaled MD steps (300 K) after the relaxation, before the NVE steps")
     ap.add_argument("--rates", default="20,50,100", help="served: arrival rates (requests/s)")
@@ -352,11 +353,23 @@ def run_reference(args, dist, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+# The paper's MD setting (Computational Details; intramolecular potential of
+# its flexible water): Beeman at 1 fs, MM3-style anharmonic bond and angle
+# with a Urey-Bradley H-H term about 0.9572 A, 108.5 deg and 1.5326 A, and
+# the dispersion beyond the 7 A cutoff as a homogeneous-fluid tail (the
+# paper's 20 A dispersion cutoff exceeds half of the 18.643 A box).
+PAPER_MD = dict(md_integrator="beeman", md_anharmonic=True, md_k_ub=38.25, md_r_ub=1.5326, md_theta0_deg=108.5,
+                disp_tail=True)
+
 WORKLOADS = {
     "water4096": WORKLOAD,
     "water32000": ("water32000: 32,000 rigid-geometry waters (96,000 atoms; 32^3 lattice, 768 seeded removals), cubic "
                    "box 98.6 A, rc 9 A, SPME 108^3 order 5, alpha 0.4/A, PCG 1e-6 D warm start, velocity-Verlet NVE "
                    "0.5 fs from 300 K"),
+    "water216_paper": ("water216_paper: the paper's MD setting, 216 waters (648 atoms) in an 18.643 A box, SPME "
+                       "120^3 order 5, Ewald and repulsion cutoff 7 A with the dispersion beyond it as a "
+                       "homogeneous-fluid tail, PCG 1e-5 D warm start, Beeman NVE at 1 fs with MM3-style anharmonic "
+                       "bond/angle and Urey-Bradley support terms"),
     "clusters4096": ("clusters4096: 4096 independent gas-phase water clusters, sizes uniform in 2-32 (70,240 waters, "
                      "210,720 atoms), all pairs within each cluster, no cutoff or Ewald, one context and one launch "
                      "per kernel, PCG 1e-6 D per cluster with warm start, velocity-Verlet NVE 0.5 fs from 300 K"),
@@ -371,15 +384,16 @@ GUESS = {1: "previous step's dipoles", 2: "linear extrapolation of the last 2 st
 def setup(name, pkg, synth, precision, stream, warm=1):
     """Context, device arrays and unit counts of a workload."""
     import torch
-    if name in ("water4096", "water32000"):
+    if name in ("water4096", "water32000", "water216_paper"):
         s, o = synth.make_config(name)
+        extra = dict(PAPER_MD) if name == "water216_paper" else {}
         ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
                                ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"], precision=precision,
-                               warm_start=warm, stream=stream)
+                               warm_start=warm, stream=stream, **extra)
         make_api = lambda: pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"],  # noqa: E731
                                             grid=o["grid"], ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"],
-                                            precision=precision, warm_start=warm, stream=stream)
-        seed = 2 if name == "water4096" else 3
+                                            precision=precision, warm_start=warm, stream=stream, **extra)
+        seed = {"water4096": 2, "water32000": 3, "water216_paper": 1}[name]
     else:
         s, start, _ = synth.make_cluster_batch(4096, seed=4)
         o = {"rc": None, "cluster_start": start}
@@ -404,16 +418,28 @@ def kinetic(vel, masses3):
     return 0.5 * float((masses3 * vel * vel).sum()) / AMU_A2_FS2
 
 
-def intra_energy(pos, k_bond=529.6, r0=0.9572, k_angle=34.05, theta0_deg=104.52):
+def intra_energy(pos, k_bond=529.6, r0=0.9572, k_angle=34.05, theta0_deg=104.52, md_anharmonic=False, md_k_ub=0.0,
+                 md_r_ub=1.5326, **_):
     """The MD driver's intramolecular support potential (kcal/mol) at device
-    positions: k_bond (r - r0)^2 per O-H bond + k_angle (theta - theta0)^2 per
-    H-O-H angle (the same definition as the run options)."""
+    positions, as the run options define it: k_bond dr^2 per O-H bond and
+    k_angle dth^2 per H-O-H angle, with the MM3-style anharmonic factors and
+    the Urey-Bradley H-H term when asked."""
     import torch
     x = pos.view(-1, 3, 3)
     b1, b2 = x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]
     r1, r2 = b1.norm(dim=-1), b2.norm(dim=-1)
-    th = torch.acos(((b1 * b2).sum(-1) / (r1 * r2)).clamp(-1.0, 1.0))
-    return float((k_bond * ((r1 - r0) ** 2 + (r2 - r0) ** 2) + k_angle * (th - math.radians(theta0_deg)) ** 2).sum())
+    dth = torch.acos(((b1 * b2).sum(-1) / (r1 * r2)).clamp(-1.0, 1.0)) - math.radians(theta0_deg)
+
+    def bond(dr):
+        return k_bond * dr ** 2 * ((1 - 2.55 * dr + (7.0 / 12.0) * 2.55 ** 2 * dr ** 2) if md_anharmonic else 1.0)
+
+    D = dth * (180.0 / math.pi)
+    ang = k_angle * dth ** 2 * ((1 - 0.014 * D + 5.6e-5 * D ** 2 - 7e-7 * D ** 3 + 9e-10 * D ** 4)
+                                if md_anharmonic else 1.0)
+    e = bond(r1 - r0) + bond(r2 - r0) + ang
+    if md_k_ub > 0:
+        e = e + md_k_ub * ((x[:, 1] - x[:, 2]).norm(dim=-1) - md_r_ub) ** 2
+    return float(e.sum())
 
 
 def equilibrate(pkg, ctx, pos, vel, masses, n_min=20, n_thermo=200, temp=300.0, every=5, dt_fs=0.5):
@@ -431,7 +457,7 @@ def equilibrate(pkg, ctx, pos, vel, masses, n_min=20, n_thermo=200, temp=300.0, 
     return 2.0 * kinetic(vel, m3) / (ndof * KB_KCAL)
 
 
-def timed_steps(pkg, ctx, pos, vel, masses, steps, stream, flush, dt_fs=0.5, keep=False, energy=False):
+def timed_steps(pkg, ctx, pos, vel, masses, steps, stream, flush, dt_fs=0.5, keep=False, energy=False, support=None):
     """steps velocity-Verlet steps, each timed with CUDA events on the
     caller's stream after an L2 flush; returns (ms total, iterations,
     snapshots, total energies).  With energy=True the total energy (kinetic +
@@ -453,7 +479,7 @@ def timed_steps(pkg, ctx, pos, vel, masses, steps, stream, flush, dt_fs=0.5, kee
         if keep:
             snaps.append(pos.clone())
         if energy:
-            etot.append(kinetic(vel, m3) + e["total"] + intra_energy(pos))
+            etot.append(kinetic(vel, m3) + e["total"] + intra_energy(pos, **(support or {})))
     return total, iters, snaps, etot
 
 
@@ -593,10 +619,14 @@ def main():
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     # The random starting structures are far from equilibrium: relax them and
     # equilibrate at 300 K first (untimed), then warm up in NVE.
-    t_equil = equilibrate(pkg, ctx, pos, vel, masses, n_min=20, n_thermo=args.equil_steps)
+    dt = 1.0 if args.workload == "water216_paper" else 0.5
+    support = PAPER_MD if args.workload == "water216_paper" else None
+    if support:
+        support = dict(support, theta0_deg=support["md_theta0_deg"])
+    t_equil = equilibrate(pkg, ctx, pos, vel, masses, n_min=20, n_thermo=args.equil_steps, dt_fs=dt)
     pos0, vel0 = pos.clone(), vel.clone()
     for _ in range(max(3, args.warmup)):
-        pkg.sibfa_md_steps(ctx, pos, vel, masses, 0.5, 1)
+        pkg.sibfa_md_steps(ctx, pos, vel, masses, dt, 1)
     torch.cuda.synchronize()
     pkg.sibfa_set_profiling(ctx, True)
     pkg.sibfa_profile_clear(ctx)
@@ -605,7 +635,7 @@ def main():
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         total_ms, iters, snapshots, etot = timed_steps(pkg, ctx, pos, vel, masses, args.steps, stream, flush,
-                                                       keep=True, energy=True)
+                                                       dt_fs=dt, keep=True, energy=True, support=support)
     torch.cuda.synchronize()
     barrier(dist)
     launches = pkg.sibfa_kernel_launches(ctx) - l0
@@ -627,7 +657,7 @@ def main():
     # measured HBM copy bandwidth.
     P = synth.PARAMS
     pos_h = pos.cpu().numpy().reshape(M, 3, 3)
-    if args.workload in ("water4096", "water32000"):
+    if args.workload in ("water4096", "water32000", "water216_paper"):
         units = count_units(pos_h, s.box, o["rc"], points_from_pos(pos_h, P))
     else:
         units = count_units_clusters(o["cluster_start"], M)
@@ -698,10 +728,10 @@ def main():
         p64.copy_(pos0)
         v64.copy_(vel0)
         for _ in range(2):
-            pkg.sibfa_md_steps(c64, p64, v64, m64, 0.5, 1)
+            pkg.sibfa_md_steps(c64, p64, v64, m64, dt, 1)
         torch.cuda.synchronize()
         n64 = 10
-        ms64, it64, _, _ = timed_steps(pkg, c64, p64, v64, m64, n64, stream, flush)
+        ms64, it64, _, _ = timed_steps(pkg, c64, p64, v64, m64, n64, stream, flush, dt_fs=dt)
         ms64 = max_over_ranks(dist, ms64) / n64
         pkg.sibfa_destroy(c64)
         fp64 = {"value": ws * 3 * M / (ms64 / 1000.0), "unit": UNIT, "ms_per_step": ms64, "steps": n64,
@@ -725,7 +755,7 @@ def main():
         "nve": {"equilibration": f"20 capped steepest-descent steps, {args.equil_steps} velocity-rescaled steps at "
                                  f"300 K (T after: {t_equil:.1f} K), {max(3, args.warmup)} NVE warm-up steps",
                 "total_energy_first": etot[0], "total_energy_last": etot[-1],
-                "drift_kcal_per_mol_atom_per_ps": (etot[-1] - etot[0]) / (3 * M) / (0.5e-3 * max(1, len(etot) - 1)),
+                "drift_kcal_per_mol_atom_per_ps": (etot[-1] - etot[0]) / (3 * M) / (dt * 1e-3 * max(1, len(etot) - 1)),
                 "temperature_end_K": 2.0 * kinetic(vel, masses.repeat_interleave(3)) / ((vel.numel() - 3) * KB_KCAL)},
         "tuned": {"short_blocks_per_sm": tb, "fixed": tdone},
     }

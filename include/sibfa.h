@@ -142,6 +142,21 @@ typedef struct {
      * E_tail on the diagonal of the virial (it scales as 1/V).  Forces do
      * not change: the term depends on the volume only. */
     int disp_tail;
+    /* Integrator of sibfa_md_steps: 0 velocity Verlet, 1 Beeman (the
+     * paper's MD setting, Computational Details):
+     *   x(t+dt) = x + v dt + (4 a(t) - a(t-dt)) dt^2 / 6,
+     *   v(t+dt) = v + (2 a(t+dt) + 5 a(t) - a(t-dt)) dt / 6,
+     * with a(t-dt) = a(t) on the first step of a context. */
+    int md_integrator;
+    /* Anharmonic (MM3-style) corrections to the support potential, 0 = off:
+     * bond  k_bond dr^2 (1 - 2.55 dr + (7/12) 2.55^2 dr^2)            (dr in A)
+     * angle k_angle dth^2 (1 - 0.014 D + 5.6e-5 D^2 - 7e-7 D^3 + 9e-10 D^4)
+     *       (dth in rad, D the same deviation in degrees),
+     * plus a Urey-Bradley H-H term md_k_ub (r_HH - md_r_ub)^2 when
+     * md_k_ub > 0 (the paper's flexible water: MM3 bond and angle terms with
+     * a Urey-Bradley term). */
+    int md_anharmonic;
+    double md_k_ub, md_r_ub;
 } sibfa_run_opts;
 
 typedef struct sibfa_ctx sibfa_ctx;
@@ -181,7 +196,8 @@ sibfa_status sibfa_energy_forces(sibfa_ctx *ctx, const double *pos, const double
 sibfa_status sibfa_solve_dipoles(sibfa_ctx *ctx, const double *pos, const double *box,
                                  double tol_D, double *mu, int *iters, double *resid_D);
 
-/* Velocity-Verlet NVE steps on the device (support for the MD workloads):
+/* NVE steps on the device (velocity Verlet or Beeman, see run options;
+ * support for the MD workloads):
  * pos and vel (n_mol*9 doubles, A and A/fs) are updated in place; masses
  * n_mol*3 doubles (amu).  Each step is one full energy + force evaluation.
  * e (may be NULL) receives the energy of the last step. */

@@ -80,6 +80,7 @@ struct sibfa_ctx {
     int last_iters = 0;
     double last_resid = 0;
     double e_tail = 0;            // dispersion beyond rc (homogeneous fluid), added to disp and the virial
+    double *d_fprev = nullptr;    // Beeman: forces of the previous step (library-owned)
     bool have_mu = false;
     // converged dipoles of the last full evaluations (warm_start >= 2): four
     // slots of capacity * 9 doubles, the newest at hist_head - 1
@@ -968,24 +969,38 @@ static sibfa_status md_impl(sibfa_ctx *ctx, double *pos, double *vel, const doub
     const sibfa_run_opts &o = ctx->opts;
     const double th0 = o.md_theta0_deg * M_PI / 180.0;
     sibfa_status st = SIBFA_OK;
+    const bool beeman = o.md_integrator == 1;
+    if (beeman && !ctx->d_fprev) {
+        sibfa_status sa = dalloc(ctx, &ctx->d_fprev, (size_t)ctx->capacity * 9);
+        if (sa) {
+            leave(ctx);
+            return sa;
+        }
+    }
     if (!ctx->md_forces_valid) {
         st = evaluate<R>(ctx, true, false, tol);
         if (st) {
             leave(ctx);   // keep the caller's stream ordered after what was queued
             return st;
         }
-        launch_water_intra(M, d.pos, ctx->d_forces, o.md_k_bond, o.md_r0, o.md_k_angle, th0, L);
+        launch_water_intra(M, d.pos, ctx->d_forces, o.md_k_bond, o.md_r0, o.md_k_angle, th0, o.md_anharmonic,
+                           o.md_k_ub, o.md_r_ub, L);
+        // Beeman's first step takes a(t - dt) = a(t)
+        if (beeman) CK(cudaMemcpyAsync(ctx->d_fprev, ctx->d_forces, nb, cudaMemcpyDeviceToDevice, ctx->s));
     }
     for (int k = 0; k < n; ++k) {
-        launch_md_kick(M, d.pos, vel, ctx->d_invm, ctx->d_forces, dt, 1, L);
+        if (beeman) launch_beeman(M, d.pos, vel, ctx->d_invm, ctx->d_forces, ctx->d_fprev, dt, 1, L);
+        else launch_md_kick(M, d.pos, vel, ctx->d_invm, ctx->d_forces, dt, 1, L);
         st = evaluate<R>(ctx, true, false, tol);
         if (st) {
             ctx->md_forces_valid = false;
             leave(ctx);
             return st;
         }
-        launch_water_intra(M, d.pos, ctx->d_forces, o.md_k_bond, o.md_r0, o.md_k_angle, th0, L);
-        launch_md_kick(M, d.pos, vel, ctx->d_invm, ctx->d_forces, dt, 0, L);
+        launch_water_intra(M, d.pos, ctx->d_forces, o.md_k_bond, o.md_r0, o.md_k_angle, th0, o.md_anharmonic,
+                           o.md_k_ub, o.md_r_ub, L);
+        if (beeman) launch_beeman(M, d.pos, vel, ctx->d_invm, ctx->d_forces, ctx->d_fprev, dt, 2, L);
+        else launch_md_kick(M, d.pos, vel, ctx->d_invm, ctx->d_forces, dt, 0, L);
     }
     CK(cudaMemcpyAsync(pos, d.pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
     double *h = ctx->h_pin;
@@ -1029,6 +1044,10 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
     }
     if (opts->precision != SIBFA_PREC_FP64 && opts->precision != SIBFA_PREC_MIXED) {
         g_create_error = "sibfa_create: unknown precision";
+        return SIBFA_E_INVALID;
+    }
+    if (opts->md_integrator < 0 || opts->md_integrator > 1) {
+        g_create_error = "sibfa_create: md_integrator must be 0 (velocity Verlet) or 1 (Beeman)";
         return SIBFA_E_INVALID;
     }
     if (opts->warm_start < 0 || opts->warm_start > 4) {
@@ -1192,7 +1211,8 @@ static sibfa_status minimize_impl(sibfa_ctx *ctx, double *pos, int n, double cap
             leave(ctx);   // keep the caller's stream ordered after what was queued
             return st;
         }
-        launch_water_intra(M, d.pos, ctx->d_forces, o.md_k_bond, o.md_r0, o.md_k_angle, th0, L);
+        launch_water_intra(M, d.pos, ctx->d_forces, o.md_k_bond, o.md_r0, o.md_k_angle, th0, o.md_anharmonic,
+                           o.md_k_ub, o.md_r_ub, L);
         launch_sd_step(M, d.pos, ctx->d_forces, 1e-4, cap, L);
     }
     CK(cudaMemcpyAsync(pos, d.pos, nb, cudaMemcpyDeviceToDevice, ctx->s));

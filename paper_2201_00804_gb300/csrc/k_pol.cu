@@ -696,29 +696,56 @@ __global__ void k_md_kick(int M, double *pos, double *vel, const double *inv_mas
 }
 
 // Intramolecular support potential for the MD driver (not part of the
-// intermolecular energy): harmonic O-H bonds and a harmonic H-O-H angle,
-// forces added to F in place.
-__global__ void k_water_intra(int M, const double *pos, double *F, double kb, double r0, double ka, double th0) {
+// intermolecular energy): O-H bonds and the H-O-H angle, harmonic or with the
+// MM3-style anharmonic factors (anh = 1), and an optional Urey-Bradley H-H
+// term; forces added to F in place.
+//   bond  E = kb dr^2 (1 - cs dr + (7/12) cs^2 dr^2), cs = 2.55 / A
+//   angle E = ka dth^2 (1 - 0.014 D + 5.6e-5 D^2 - 7e-7 D^3 + 9e-10 D^4), D = dth in degrees
+//   UB    E = kub (r_HH - rub)^2
+__device__ inline double bond_dEdr(double kb, double dr, int anh) {
+    if (!anh) return 2.0 * kb * dr;
+    const double cs = 2.55, c4 = (7.0 / 12.0) * cs * cs;
+    // d/dr [dr^2 - cs dr^3 + c4 dr^4]
+    return kb * (2.0 * dr - 3.0 * cs * dr * dr + 4.0 * c4 * dr * dr * dr);
+}
+__device__ inline double angle_dEdth(double ka, double dth, int anh) {
+    if (!anh) return 2.0 * ka * dth;
+    const double g = 180.0 / M_PI;   // degrees per radian
+    const double D = dth * g;
+    const double f = 1.0 - 0.014 * D + 5.6e-5 * D * D - 7.0e-7 * D * D * D + 9.0e-10 * D * D * D * D;
+    const double dfdD = -0.014 + 2.0 * 5.6e-5 * D - 3.0 * 7.0e-7 * D * D + 4.0 * 9.0e-10 * D * D * D;
+    return ka * (2.0 * dth * f + dth * dth * dfdD * g);
+}
+
+__global__ void k_water_intra(int M, const double *pos, double *F, double kb, double r0, double ka, double th0,
+                              int anh, double kub, double rub) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     const double *x = pos + m * 9;
     const V3<double> O = mk(x[0], x[1], x[2]), H1 = mk(x[3], x[4], x[5]), H2 = mk(x[6], x[7], x[8]);
     const V3<double> a = H1 - O, b = H2 - O;
     const double ra = sqrt(dot(a, a)), rb = sqrt(dot(b, b));
-    // bonds: E = kb (r - r0)^2
-    const V3<double> fa = (-2.0 * kb * (ra - r0) / ra) * a;   // force on H1
-    const V3<double> fb = (-2.0 * kb * (rb - r0) / rb) * b;
-    // angle: E = ka (theta - th0)^2
+    // bonds
+    const V3<double> fa = (-bond_dEdr(kb, ra - r0, anh) / ra) * a;   // force on H1
+    const V3<double> fb = (-bond_dEdr(kb, rb - r0, anh) / rb) * b;
+    // angle
     const double c = fmax(-1.0, fmin(1.0, dot(a, b) / (ra * rb)));
     const double th = acos(c);
     const double s = fmax(sqrt(1.0 - c * c), 1e-8);
-    const double dEdth = 2.0 * ka * (th - th0);
+    const double dEdth = angle_dEdth(ka, th - th0, anh);
     // dtheta/da = -(b/(ra rb) - c a/ra^2)/sin
     const V3<double> dca = (1.0 / (ra * rb)) * b - (c / (ra * ra)) * a;
     const V3<double> dcb = (1.0 / (ra * rb)) * a - (c / (rb * rb)) * b;
     const V3<double> ga = (dEdth / s) * dca;     // -dE/da  (dtheta = -dc/sin)
     const V3<double> gb = (dEdth / s) * dcb;
-    const V3<double> f1 = fa + ga, f2 = fb + gb;
+    V3<double> f1 = fa + ga, f2 = fb + gb;
+    if (kub > 0.0) {   // Urey-Bradley: force on H1 along H2 -> H1
+        const V3<double> hh = H1 - H2;
+        const double rhh = sqrt(dot(hh, hh));
+        const V3<double> fu = (-2.0 * kub * (rhh - rub) / rhh) * hh;
+        f1 = f1 + fu;
+        f2 = f2 - fu;
+    }
     double *f = F + m * 9;
     f[0] -= f1.x + f2.x; f[1] -= f1.y + f2.y; f[2] -= f1.z + f2.z;
     f[3] += f1.x; f[4] += f1.y; f[5] += f1.z;
@@ -743,8 +770,36 @@ void launch_sd_step(int M, double *pos, const double *F, double gamma, double ca
     count(L);
 }
 
-void launch_water_intra(int M, const double *pos, double *F, double kb, double r0, double ka, double th0, Launch L) {
-    k_water_intra<<<(M + 127) / 128, 128, 0, L.s>>>(M, pos, F, kb, r0, ka, th0);
+void launch_water_intra(int M, const double *pos, double *F, double kb, double r0, double ka, double th0, int anh,
+                        double kub, double rub, Launch L) {
+    k_water_intra<<<(M + 127) / 128, 128, 0, L.s>>>(M, pos, F, kb, r0, ka, th0, anh, kub, rub);
+    count(L);
+}
+
+// Beeman integrator, first half: x += v dt + (4 a - a_prev) dt^2 / 6,
+// v += (5 a - a_prev) dt / 6, then a_prev <- a (stored as forces).
+__global__ void k_beeman1(int M, double *pos, double *vel, const double *inv_mass, const double *F, double *Fprev,
+                          double dt) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M * 9) return;
+    const double conv = 4.184e-4;   // (kcal/mol/A)/amu -> A/fs^2
+    const double im = inv_mass[k / 3] * conv;
+    const double a = F[k] * im, ap = Fprev[k] * im;
+    const double v = vel[k];
+    pos[k] += v * dt + (4.0 * a - ap) * dt * dt * (1.0 / 6.0);
+    vel[k] = v + (5.0 * a - ap) * dt * (1.0 / 6.0);
+    Fprev[k] = F[k];
+}
+// second half, after the forces at t + dt: v += 2 a(t + dt) dt / 6
+__global__ void k_beeman2(int M, double *vel, const double *inv_mass, const double *F, double dt) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M * 9) return;
+    vel[k] += 2.0 * F[k] * inv_mass[k / 3] * 4.184e-4 * dt * (1.0 / 6.0);
+}
+void launch_beeman(int M, double *pos, double *vel, const double *inv_mass, double *F, double *Fprev, double dt,
+                   int half, Launch L) {
+    if (half == 1) k_beeman1<<<(M * 9 + 255) / 256, 256, 0, L.s>>>(M, pos, vel, inv_mass, F, Fprev, dt);
+    else k_beeman2<<<(M * 9 + 255) / 256, 256, 0, L.s>>>(M, vel, inv_mass, F, dt);
     count(L);
 }
 

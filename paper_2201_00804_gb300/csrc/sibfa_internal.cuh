@@ -856,7 +856,10 @@ template <typename R> void launch_virial_total(const KParams &p, DevState<R> &d,
 template <typename R> void launch_cluster_energy(const KParams &p, DevState<R> &d, double *out, Launch L);
 void launch_begin(double *scal, int *flags, double tol_D, Launch L);
 void launch_pcg_check(const double *scal, int *flags, Launch L);
-void launch_water_intra(int M, const double *pos, double *F, double kb, double r0, double ka, double th0, Launch L);
+void launch_water_intra(int M, const double *pos, double *F, double kb, double r0, double ka, double th0, int anh,
+                        double kub, double rub, Launch L);
+void launch_beeman(int M, double *pos, double *vel, const double *inv_mass, double *F, double *Fprev, double dt,
+                   int half, Launch L);
 void launch_sd_step(int M, double *pos, const double *F, double gamma, double cap, Launch L);
 enum { SC_RZ = 0, SC_RES = 4, SC_IT = 6, SC_DONE = 7, SC_TOL = 8 };
 void launch_md_kick(int M, double *pos, double *vel, const double *inv_mass, const double *forces, double dt,

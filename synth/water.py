@@ -415,6 +415,11 @@ CONFIGS = {
                       ewald=0.4, pcg_tol=1e-6),
     "water32000": dict(n_side=32, box=98.6, seed=3, n_remove=768, rc=9.0, grid=108,
                        ewald=0.4, pcg_tol=1e-6),
+    # the paper's own MD setting (Computational Details): 216 waters in an
+    # 18.643 A box, SPME grid 120^3, Ewald and repulsion cutoff 7 A, PCG
+    # 1e-5 D (run with the Beeman integrator at 1 fs)
+    "water216_paper": dict(n_side=6, box=18.643, seed=1, n_remove=0, rc=7.0, grid=120,
+                           ewald=0.4, pcg_tol=1e-5),
 }
 
 

@@ -146,3 +146,85 @@ def test_nve_stays_stable_with_bounded_drift():
     drift = abs(totals[-1] - totals[0]) / s.n_atoms
     assert drift < 0.02, (drift, totals[0], totals[-1])
     assert 200.0 < min(temps) and max(temps) < 1500.0, temps
+
+
+KUB, RUB = 38.25, 1.5326
+
+
+def intra_energy_mm3(x):
+    """The anharmonic support potential of the header (MM3-style bond and
+    angle factors, Urey-Bradley H-H term), per molecule."""
+    a, b = x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]
+    ra, rb = np.linalg.norm(a, axis=-1), np.linalg.norm(b, axis=-1)
+    th = np.arccos(np.clip((a * b).sum(-1) / (ra * rb), -1.0, 1.0))
+
+    def bond(dr):
+        return KB * dr ** 2 * (1 - 2.55 * dr + (7.0 / 12.0) * 2.55 ** 2 * dr ** 2)
+
+    dth = th - math.radians(TH0_DEG)
+    D = np.degrees(dth)
+    ang = KA * dth ** 2 * (1 - 0.014 * D + 5.6e-5 * D ** 2 - 7e-7 * D ** 3 + 9e-10 * D ** 4)
+    rhh = np.linalg.norm(x[:, 1] - x[:, 2], axis=-1)
+    return bond(ra - R0) + bond(rb - R0) + ang + KUB * (rhh - RUB) ** 2
+
+
+def intra_forces_mm3(x, h=1e-5):
+    F = np.zeros_like(x)
+    for k in range(3):
+        for c in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[:, k, c] += h
+            xm[:, k, c] -= h
+            F[:, k, c] = -(intra_energy_mm3(xp) - intra_energy_mm3(xm)) / (2 * h)
+    return F
+
+
+def test_beeman_with_anharmonic_support_matches_host_integration():
+    """Beeman steps (the paper's integrator) with the anharmonic bond/angle
+    factors and the Urey-Bradley term against a host integration of the
+    same recurrences, with the library's intermolecular forces and
+    central-difference support forces from the header's definition."""
+    import torch
+    import paper_2201_00804_gb300 as pkg
+    s, o = synth.make_config("water216")
+    M = s.n_mol
+    m = s.masses()
+    v0 = synth.maxwell_velocities(s, 300.0, seed=12)
+    ctx_f = _ctx(pkg, s, o)
+    try:
+        def inter(x):
+            xd = torch.tensor(x.reshape(-1), dtype=torch.float64, device="cuda")
+            F = torch.zeros_like(xd)
+            e = pkg.sibfa_energy_forces(ctx_f, xd, F)
+            torch.cuda.synchronize()
+            return F.cpu().numpy().reshape(M, 3, 3), e
+
+        dt = 1.0
+        x, v = s.pos.copy(), v0.copy()
+        a = ACC * (inter(x)[0] + intra_forces_mm3(x)) / m[:, :, None]
+        a_prev = a.copy()
+        for _ in range(2):
+            x = x + v * dt + (4 * a - a_prev) * dt * dt / 6
+            Fi, e_host = inter(x)
+            a_new = ACC * (Fi + intra_forces_mm3(x)) / m[:, :, None]
+            v = v + (2 * a_new + 5 * a - a_prev) * dt / 6
+            a_prev, a = a, a_new
+    finally:
+        pkg.sibfa_destroy(ctx_f)
+    pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
+    vel = torch.tensor(v0.reshape(-1), dtype=torch.float64, device="cuda")
+    masses = torch.tensor(m.reshape(-1), dtype=torch.float64, device="cuda")
+    ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
+                           ewald_alpha=o["ewald"], pcg_tol_D=1e-11, precision=pkg.PREC_FP64, warm_start=0,
+                           md_k_bond=KB, md_r0=R0, md_k_angle=KA, md_theta0_deg=TH0_DEG, md_integrator="beeman",
+                           md_anharmonic=True, md_k_ub=KUB, md_r_ub=RUB)
+    try:
+        pkg.sibfa_md_steps(ctx, pos, vel, masses, 1.0, 2)
+        torch.cuda.synchronize()
+    finally:
+        pkg.sibfa_destroy(ctx)
+    xd = pos.cpu().numpy().reshape(M, 3, 3)
+    vd = vel.cpu().numpy().reshape(M, 3, 3)
+    assert np.abs(x - s.pos).max() > 1e-3
+    assert np.abs(xd - x).max() < 1e-9, np.abs(xd - x).max()
+    assert np.abs(vd - v).max() < 1e-7 * np.abs(v).max(), np.abs(vd - v).max()
