@@ -45,7 +45,9 @@ typedef enum {
     SIBFA_E_NOT_CONVERGED = -3,  /* PCG hit max_iter above the tolerance        */
     SIBFA_E_CUTOFF = -4,         /* rc + 2 * site extent exceeds half the box   */
     SIBFA_E_CT_DENOM = -5,       /* a charge-transfer denominator dE <= 0       */
-    SIBFA_E_TIMEOUT = -6,        /* a bounded device wait gave up               */
+    SIBFA_E_TIMEOUT = -6,        /* reserved: no kernel of this library waits on
+                                    another (grid-wide steps use cooperative
+                                    launches), so no call returns it             */
     SIBFA_E_CUDA = -7,           /* a CUDA / cuFFT call failed                  */
     SIBFA_E_BUSY = -8,           /* admission refused (serving)                 */
     SIBFA_E_NEIGHBOR = -9        /* neighbour list overflow                     */

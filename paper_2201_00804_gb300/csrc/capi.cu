@@ -215,6 +215,7 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.dvlp_r, M * 6);
     AL(d.epart_r, M * NTERM);
     AL(d.eintra, M);
+    AL(d.epartial, 128 * NTERM);
     AL(d.efp_r, M * 9);
     AL(d.mu, M * 9);
     AL(d.res, M * 9);
@@ -788,7 +789,7 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
     if ((st = join_short(ctx))) return st;
     if (p.n_cl > 1) launch_cluster_energy(p, d, ctx->d_energy, L);
     else launch_energy_reduce(p.M, d.epart, d.epart_r, (sizeof(R) == 4 && p.periodic) ? d.eintra : nullptr,
-                              ctx->d_energy, L);
+                              d.epartial, ctx->d_energy, L);
     return st_solve;
 }
 

@@ -606,16 +606,20 @@ void launch_finalize(const KParams &p, DevState<R> &d, double *forces_out, Launc
     count(L);
 }
 
-// energy totals: out[k] = sum_m epart[m*NTERM + k], out[NTERM] = total (fixed order)
-// One pass: every thread sums all terms of its molecules (independent
-// chains), then one shared-memory tree per term; the order is fixed.
-__global__ void __launch_bounds__(1024) k_energy_reduce(int M, const double *epart, const double *epart_r,
-                                                        const double *eintra, double *out) {
-    __shared__ double sh[32][NTERM];
+// energy totals: out[k] = sum_m epart[m*NTERM + k], out[NTERM] = total, in a
+// fixed order: ER_BLOCKS blocks each sum a contiguous slice of molecules
+// (threads take independent chains, then a shared-memory tree per term) into
+// partials; one small block sums the partials in block order.
+constexpr int ER_BLOCKS = 128, ER_THREADS = 256;
+__global__ void __launch_bounds__(ER_THREADS) k_energy_partial(int M, const double *epart, const double *epart_r,
+                                                              const double *eintra, double *partial) {
+    __shared__ double sh[ER_THREADS / 32][NTERM];
+    const int per = (M + ER_BLOCKS - 1) / ER_BLOCKS;
+    const int m0 = blockIdx.x * per, m1 = min(M, m0 + per);
     double v[NTERM];
 #pragma unroll
     for (int k = 0; k < NTERM; ++k) v[k] = 0.0;
-    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+    for (int m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
 #pragma unroll
         for (int k = 0; k < NTERM; ++k) v[k] += epart[m * NTERM + k] + epart_r[m * NTERM + k];
         if (eintra) v[T_ELEC] += eintra[m];
@@ -631,22 +635,31 @@ __global__ void __launch_bounds__(1024) k_energy_reduce(int M, const double *epa
     __syncthreads();
     if (threadIdx.x < NTERM) {
         double x = 0.0;
-        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) x += sh[j][threadIdx.x];
+        for (int j = 0; j < ER_THREADS / 32; ++j) x += sh[j][threadIdx.x];
+        partial[blockIdx.x * NTERM + threadIdx.x] = x;
+    }
+}
+__global__ void k_energy_final(const double *partial, double *out) {
+    __shared__ double sh[NTERM];
+    if (threadIdx.x < NTERM) {
+        double x = 0.0;
+        for (int b = 0; b < ER_BLOCKS; ++b) x += partial[b * NTERM + threadIdx.x];
         out[threadIdx.x] = x;
-        sh[0][threadIdx.x] = x;
+        sh[threadIdx.x] = x;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot = 0.0;
-        for (int k = 0; k < NTERM; ++k) tot += sh[0][k];
+        for (int k = 0; k < NTERM; ++k) tot += sh[k];
         out[NTERM] = tot;
     }
 }
 
-void launch_energy_reduce(int M, const double *epart, const double *epart_r, const double *eintra, double *out,
-                          Launch L) {
-    k_energy_reduce<<<1, 1024, 0, L.s>>>(M, epart, epart_r, eintra, out);
-    count(L);
+void launch_energy_reduce(int M, const double *epart, const double *epart_r, const double *eintra, double *partial,
+                          double *out, Launch L) {
+    k_energy_partial<<<ER_BLOCKS, ER_THREADS, 0, L.s>>>(M, epart, epart_r, eintra, partial);
+    k_energy_final<<<1, 32, 0, L.s>>>(partial, out);
+    count(L, 2);
 }
 
 // Cluster batches: terms per cluster (one block per cluster, fixed order),

@@ -172,6 +172,7 @@ struct DevState {
     double *kap;        // M*3 dE_ct/dV_int
     double *epart;      // M*NTERM per-molecule energy partials
     double *eintra;     // M  mixed periodic path: FP64 intramolecular Ewald energy per molecule
+    double *epartial;   // 128*NTERM per-block partial energy sums
     double *epw;        // M*NS*2 multipole and penetration energy of each target site (k_real_perm)
     // Virial: per-molecule dE/d eps (row-major 3x3) for the affine strain
     // x -> (I + eps) x of atoms and cell, and the reciprocal-space parts
@@ -845,8 +846,8 @@ template <typename R> void launch_pcg_first(const KParams &p, DevState<R> &d, La
 template <typename R> void launch_pcg_step(const KParams &p, DevState<R> &d, Launch L,
                                            cudaGraphConditionalHandle loop = 0, int maxit = 0);
 template <typename R> void launch_pol_energy(const KParams &p, DevState<R> &d, Launch L);
-void launch_energy_reduce(int M, const double *epart, const double *epart_r, const double *eintra, double *out,
-                          Launch L);
+void launch_energy_reduce(int M, const double *epart, const double *epart_r, const double *eintra, double *partial,
+                          double *out, Launch L);
 // mixed periodic path: the intramolecular Ewald energy of every molecule in FP64 into eintra
 template <typename R> void launch_intra_energy64(const KParams &p, DevState<R> &d, Launch L);
 // k-space virial sums of one convolution pass (0: permanent, 1: force pass) fused with the convolution
