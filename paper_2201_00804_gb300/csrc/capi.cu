@@ -239,6 +239,9 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.counter, 4);
     AL(d.flags, 4);
     AL(d.ext, 4);
+    AL(d.oref, M * 3);
+    AL(d.lst, 4);
+    AL(d.lflag, 2);
     if (ctx->opts.periodic) {
         const size_t ng = (size_t)ctx->kp.K[0] * ctx->kp.K[1] * ctx->kp.K[2];
         const size_t nh = (size_t)ctx->kp.K[0] * ctx->kp.K[1] * (ctx->kp.K[2] / 2 + 1);
@@ -324,6 +327,7 @@ void fill_params(KParams &k, const sibfa_params &P, const sibfa_run_opts &o, int
     }
     k.rc = o.rc;
     k.rc2 = o.rc * o.rc;
+    k.skin = o.periodic ? LIST_SKIN : 0.0;
     k.alpha = o.ewald_alpha;
     for (int i = 0; i < 3; ++i) k.K[i] = o.grid[i];
     k.ke = P.ke;
@@ -1131,7 +1135,7 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
         if (t && t[0] == '0') ctx->tune.on = false;
     }
     if (opts->periodic) {
-        const double cell = opts->rc + 2.6;   // rc + 2 * maximum site extent (1.3 A)
+        const double cell = opts->rc + 2.6 + LIST_SKIN;   // rc + 2 * maximum site extent (1.3 A) + skin
         for (int k = 0; k < 3; ++k) ctx->ncell[k] = (int)floor(opts->box[k] / cell);
     }
     sibfa_status st = SIBFA_OK;

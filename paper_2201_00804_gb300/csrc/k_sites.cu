@@ -169,6 +169,45 @@ void launch_sites(const KParams &p, DevState<R> &d, Launch L) {
 __device__ inline double list_cut(const KParams &p, const float *ext) {
     return p.periodic ? p.rc + 2.0 * (double)(*ext) : 1e300;
 }
+// the radius of a build: rc + 2 ext + the skin chosen at that build
+template <typename R>
+__device__ inline double build_cut(const KParams &p, const DevState<R> &d) {
+    return p.periodic ? p.rc + 2.0 * (double)d.lst[0] + (double)d.lst[1] : 1e300;
+}
+
+// Verlet skin (periodic systems).  The largest O displacement since the last
+// build (squared, as float bits: non-negative floats order like their bits).
+template <typename R>
+__global__ void k_skin_disp(KParams p, DevState<R> d) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= p.M) return;
+    double d2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double v = d.pos[m * 9 + k] - d.oref[m * 3 + k];
+        d2 += v * v;
+    }
+    atomicMax((int *)(d.lst + 2), __float_as_int((float)fmin(d2, 1e30)));
+}
+// Rebuild when no list exists yet, when the skin is zero, or when twice the
+// largest move plus twice the growth of the site extent reaches the skin (a
+// pair can then have come from outside the listed radius to inside rc +
+// 2 ext).  A rebuild takes the current extent and the largest skin that keeps
+// the list radius below half the box (minimum image).
+template <typename R>
+__global__ void k_skin_decide(KParams p, DevState<R> d) {
+    const float ext = *d.ext;
+    const float md = sqrtf(__int_as_float(*(const int *)(d.lst + 2)));
+    const bool rebuild = d.lflag[1] == 0 || d.lst[1] <= 0.f || 2.f * md + 2.f * fmaxf(0.f, ext - d.lst[0]) >= d.lst[1];
+    if (rebuild) {
+        const double half = 0.5 * fmin(p.box[0], fmin(p.box[1], p.box[2]));
+        d.lst[0] = ext;
+        d.lst[1] = (float)fmax(0.0, fmin(p.skin, half - p.rc - 2.0 * (double)ext - 1e-3));
+        d.lflag[1] = 1;
+    }
+    d.lflag[0] = rebuild ? 1 : 0;
+    *(int *)(d.lst + 2) = 0;
+}
+
 
 template <typename R>
 __global__ void k_check_ext(KParams p, DevState<R> d) {
@@ -221,12 +260,25 @@ __device__ inline void store_entry(const KParams &p, DevState<R> &d, int i, int 
     o[2] = R(dz);
 }
 
+// Without a rebuild: the listed pairs' displacements at the current positions.
 template <typename R>
-__global__ void k_nbr_all(KParams p, DevState<R> d) {
+__global__ void k_nbr_refresh(KParams p, DevState<R> d) {
+    if (d.lflag[0]) return;
     const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (i >= p.M) return;
-    const double cut = list_cut(p, d.ext) + 1e-3;
+    const int nn = d.nnbr[i];
+    for (int slot = lane; slot < nn; slot += 32) store_entry(p, d, i, slot, d.nbr[i * MAXN + slot]);
+}
+
+template <typename R>
+__global__ void k_nbr_all(KParams p, DevState<R> d) {
+    if (!d.lflag[0]) return;
+    const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (i >= p.M) return;
+    if (lane < 3) d.oref[i * 3 + lane] = d.pos[i * 9 + lane];
+    const double cut = build_cut(p, d) + 1e-3;
     const float cut2f = p.periodic ? (float)(cut * cut) : 3.0e38f;
     // partners: the molecules of i's own cluster (the whole system when n_cl = 1)
     const int c = d.cl_of[i], j_lo = d.cl_start[c], j_hi = d.cl_start[c + 1];
@@ -256,6 +308,7 @@ __device__ inline int cell_index(const KParams &p, const int nc[3], float x, flo
 
 template <typename R>
 __global__ void k_cell_count(KParams p, DevState<R> d, int nc0, int nc1, int nc2) {
+    if (!d.lflag[0]) return;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= p.M) return;
     const int nc[3] = {nc0, nc1, nc2};
@@ -270,6 +323,7 @@ __global__ void k_cell_count(KParams p, DevState<R> d, int nc0, int nc1, int nc2
 template <typename R>
 __global__ void __launch_bounds__(1024) k_cell_scan(DevState<R> d, int ncell) {
     __shared__ int wsum[32];
+    if (!d.lflag[0]) return;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int per = (ncell + blockDim.x - 1) / blockDim.x;
     const int a = t * per, b = min(ncell, a + per);
@@ -306,6 +360,7 @@ __global__ void __launch_bounds__(1024) k_cell_scan(DevState<R> d, int ncell) {
 
 template <typename R>
 __global__ void k_cell_fill(KParams p, DevState<R> d) {
+    if (!d.lflag[0]) return;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= p.M) return;
     int c = d.cell_of[m];
@@ -319,6 +374,7 @@ constexpr int SORT_CAP = 256;
 template <typename R>
 __global__ void k_cell_sort(DevState<R> d, int ncell) {
     __shared__ int buf[4][SORT_CAP];
+    if (!d.lflag[0]) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x * 4 + w;
     if (c >= ncell) return;
@@ -346,10 +402,12 @@ __global__ void k_cell_sort(DevState<R> d, int ncell) {
 
 template <typename R>
 __global__ void k_nbr_cell(KParams p, DevState<R> d, int nc0, int nc1, int nc2) {
+    if (!d.lflag[0]) return;
     const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (i >= p.M) return;
-    const double cut = list_cut(p, d.ext) + 1e-3;
+    if (lane < 3) d.oref[i * 3 + lane] = d.pos[i * 9 + lane];
+    const double cut = build_cut(p, d) + 1e-3;
     const float cut2f = (float)(cut * cut);
     const int ci = d.cell_of[i];
     const int cz = ci % nc2, cy = (ci / nc2) % nc1, cx = ci / (nc1 * nc2);
@@ -380,8 +438,13 @@ __global__ void k_nbr_cell(KParams p, DevState<R> d, int nc0, int nc1, int nc2) 
 template <typename R>
 void launch_neighbors(const KParams &p, DevState<R> &d, int nc[3], Launch L) {
     k_check_ext<R><<<1, 1, 0, L.s>>>(p, d);
-    count(L);
+    k_skin_disp<R><<<(p.M + 255) / 256, 256, 0, L.s>>>(p, d);
+    k_skin_decide<R><<<1, 1, 0, L.s>>>(p, d);
+    count(L, 3);
     const int wpb = 4;
+    // either the refresh or the build kernels do work, as the decision says
+    k_nbr_refresh<R><<<(p.M + wpb - 1) / wpb, 32 * wpb, 0, L.s>>>(p, d);
+    count(L);
     if (!p.periodic || nc[0] < 3 || nc[1] < 3 || nc[2] < 3) {
         k_nbr_all<R><<<(p.M + wpb - 1) / wpb, 32 * wpb, 0, L.s>>>(p, d);
         count(L);

@@ -40,6 +40,11 @@ struct Scal {
 // ---------------------------------------------------------------------------
 // Kernel parameters (by value).
 // ---------------------------------------------------------------------------
+// Verlet skin of the periodic neighbour list (A): the list keeps the pairs
+// within rc + 2 * site extent + skin of its build and is rebuilt once an O
+// has moved by half the skin (less any growth of the extent) since then.
+constexpr double LIST_SKIN = 0.4;
+
 struct KParams {
     int M;
     int periodic;
@@ -49,6 +54,7 @@ struct KParams {
     double box[3];
     double ibox[3];        // 1 / box
     double rc, rc2;
+    double skin;           // Verlet skin of the periodic neighbour list (0: rebuilt every evaluation)
     double alpha;          // Ewald
     int K[3];
     double ke;
@@ -203,6 +209,9 @@ struct DevState {
     unsigned int *counter;
     int *flags;         // [0] error flags, [1] PCG converged
     float *ext;         // maximum point distance from own O (float bits, atomicMax)
+    double *oref;       // M*3 O positions at the last neighbour-list build
+    float *lst;         // list state: [0] extent at the build, [1] skin of the build, [2] max squared O move (bits)
+    int *lflag;         // [0] rebuild the list this evaluation, [1] a list has been built
     // grids
     R *grid;            // 2 * K0*K1*K2 (two real grids for the force pass)
     void *cgrid;        // 2 * K0*K1*(K2/2+1) complex

@@ -228,3 +228,57 @@ def test_beeman_with_anharmonic_support_matches_host_integration():
     assert np.abs(x - s.pos).max() > 1e-3
     assert np.abs(xd - x).max() < 1e-9, np.abs(xd - x).max()
     assert np.abs(vd - v).max() < 1e-7 * np.abs(v).max(), np.abs(vd - v).max()
+
+
+@pytest.mark.parametrize("case", ["water512_cells", "water216_all_pairs"])
+def test_neighbour_list_reuse_matches_a_fresh_build(case):
+    """Along 40 MD steps the periodic neighbour list is rebuilt only when an
+    O has moved by half the list skin; in between its entries are refreshed.
+    Energies, forces and dipoles at the final positions equal those of a
+    fresh context, which builds its list from scratch (FP64, rounding only):
+    the cell-list path (512 waters, three cells per side) and the all-pairs
+    path (216 waters)."""
+    import torch
+    import paper_2201_00804_gb300 as pkg
+    if case == "water512_cells":
+        s = synth.make_box(8, 24.83, seed=33)
+        o = {"rc": 5.0, "grid": 32, "order": 5, "ewald": 0.6}
+    else:
+        s, o = synth.make_config("water216")
+
+    def ctx_():
+        return pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
+                                ewald_alpha=o["ewald"], pcg_tol_D=1e-11, precision=pkg.PREC_FP64, warm_start=0,
+                                md_k_bond=KB, md_r0=R0, md_k_angle=KA, md_theta0_deg=TH0_DEG)
+
+    pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
+    vel = torch.tensor(synth.maxwell_velocities(s, 600.0, seed=13).reshape(-1), dtype=torch.float64, device="cuda")
+    masses = torch.tensor(s.masses().reshape(-1), dtype=torch.float64, device="cuda")
+    res = []
+    a = ctx_()
+    try:
+        pkg.sibfa_md_steps(a, pos, vel, masses, 0.5, 40)
+        F = torch.zeros_like(pos)
+        mu = torch.zeros_like(pos)
+        res.append((pkg.sibfa_energy_forces(a, pos, F), F.clone()))
+        pkg.sibfa_solve_dipoles(a, pos, mu, 1e-11)
+        res[-1] += (mu.clone(),)
+    finally:
+        pkg.sibfa_destroy(a)
+    b = ctx_()
+    try:
+        F = torch.zeros_like(pos)
+        mu = torch.zeros_like(pos)
+        res.append((pkg.sibfa_energy_forces(b, pos, F), F.clone()))
+        pkg.sibfa_solve_dipoles(b, pos, mu, 1e-11)
+        res[-1] += (mu.clone(),)
+    finally:
+        pkg.sibfa_destroy(b)
+    torch.cuda.synchronize()
+    (ea, Fa, ma), (eb, Fb, mb) = res
+    assert float((pos.view(-1, 3, 3)[:, 0] - torch.tensor(s.pos[:, 0], device="cuda")).norm(dim=-1).max()) > 0.05
+    mag = sum(abs(eb[k]) for k in TERMS)
+    for k in TERMS:
+        assert abs(ea[k] - eb[k]) <= 1e-10 * mag, (k, ea[k], eb[k])
+    assert float((Fa - Fb).abs().max()) <= 1e-8 * float(Fb.abs().max())
+    assert float((ma - mb).abs().max()) <= 1e-9

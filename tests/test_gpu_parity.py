@@ -36,8 +36,9 @@ def _cases():
         "cluster8": (synth.make_cluster(8, seed=31), None),
         "cluster2": (synth.make_cluster(2, seed=32), None),
         "water216": synth.make_config("water216"),
-        # 512 waters with rc 5.5: three cells per side, exercises the cell list
-        "water512": (synth.make_box(8, 24.83, seed=33), {"rc": 5.5, "grid": 32, "order": 5, "ewald": 0.55}),
+        # 512 waters with rc 5 A: three cells per side (cells of rc + 2.6 A of
+        # site extents + 0.4 A of list skin), exercises the cell list
+        "water512": (synth.make_box(8, 24.83, seed=33), {"rc": 5.0, "grid": 32, "order": 5, "ewald": 0.6}),
         # dipoles of any direction and quadrupoles with off-diagonal entries in
         # every local frame: the full rotation and its torques
         "cluster8_general": (synth.with_general_multipoles(synth.make_cluster(8, seed=31), seed=34), None),
