@@ -63,10 +63,6 @@ class _Setup:
     strain = None   # (I + eps) in virial mode: image shifts are lattice vectors and deform with the cell
 
 
-def _grad(e, wrt, retain=False):
-    return torch.autograd.grad(e, wrt, allow_unused=True, retain_graph=retain)
-
-
 def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=2048,
              P=None, mu_guess=None, pcg_log=None, per_term=False, keep_operators=False, virial=False):
     """Energies (kcal/mol) per term, forces (kcal/mol/A) on O, H1, H2, induced
@@ -179,28 +175,48 @@ def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=20
                 lam += gv
     E["ct"] = e_ct
     if forces and float(lam.abs().sum()) > 0:
-        add_grad((lam.detach() * lp_potential(x)).sum(), "ct")
+        # d/dx of sum lam . V_lp(x), one chunk of pairs at a time (the
+        # gradient of the sum is the sum of the chunks' gradients)
+        lamd = lam.detach()
+        S = build_sites(x, st.mp, P)
+        for i, j, sh in st.chunks(chunk):
+            add_grad((lamd * tm.lp_potential_pairs(S, i, j, sh, P, st.rc, st.alpha)).sum(), "ct", retain=True)
+        if st.periodic:
+            Qp = ew.spread(S["x"].reshape(-1, 3), S["q"].reshape(-1), S["mu"].reshape(-1, 3),
+                           S["th"].reshape(-1, 3, 3), st.box, st.K, st.order)
+            add_grad((lamd * tm.lp_potential_periodic(S, P, st.alpha, ew.convolve(Qp, st.G), st.box, st.K,
+                                                      st.order)).sum(), "ct", retain=True)
+        del S
 
     # ---- polarization ---------------------------------------------------------
     a_pol = tm.site_tables(P)["alpha_pol"]
 
-    def linear(xx, mu):
+    # The polarization functional's linear (-mu.E_perm) and quadratic
+    # (1/2 mu.T.mu) parts as a sequence of terms, one chunk of pairs each:
+    # gradients are taken term by term, so only one chunk's graph is held.
+    def linear_parts(xx, mu):
         S = build_sites(xx, st.mp, P)
-        e = 0.0
         for i, j, sh in st.chunks(chunk):
-            e = e + tm.pol_linear_pairs(S, mu, i, j, sh, P, st.rc, st.alpha)
+            yield tm.pol_linear_pairs(S, mu, i, j, sh, P, st.rc, st.alpha)
         if st.periodic:
-            e = e + tm.pol_periodic_linear(S, mu, P, st.alpha, Psi_perm_of(xx), st.box, st.K, st.order)
-        return e
+            yield tm.pol_periodic_linear(S, mu, P, st.alpha, Psi_perm_of(xx), st.box, st.K, st.order)
 
-    def quadratic(xx, mu):
+    def quadratic_parts(xx, mu):
         S = build_sites(xx, st.mp, P)
-        e = tm.pol_diag(mu, P)
+        yield tm.pol_diag(mu, P)
         for i, j, sh in st.chunks(chunk):
-            e = e + tm.pol_quadratic_pairs(S, mu, i, j, sh, P, st.rc, st.alpha)
+            yield tm.pol_quadratic_pairs(S, mu, i, j, sh, P, st.rc, st.alpha)
         if st.periodic:
-            e = e + tm.pol_periodic_quadratic(S, mu, P, st.alpha, st.G, st.box, st.K, st.order)
-        return e
+            yield tm.pol_periodic_quadratic(S, mu, P, st.alpha, st.G, st.box, st.K, st.order)
+
+    def grad_mu(parts, mu):
+        g = torch.zeros_like(mu)
+        for e in parts:
+            if torch.is_tensor(e) and e.requires_grad:
+                ge, = torch.autograd.grad(e, [mu], allow_unused=True, retain_graph=True)
+                if ge is not None:
+                    g = g + ge
+        return g
 
     def Psi_perm_of(xx):
         if not xx.requires_grad:
@@ -213,11 +229,11 @@ def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=20
     xd = x.detach()
     # E_perm = -d(-mu.E)/dmu ; T p = d(1/2 p.T.p)/dp   (both divided by ke below)
     mu0 = torch.zeros((M, 3, 3), dtype=DT, requires_grad=True)
-    Efield = -_grad(linear(xd, mu0), [mu0], virial)[0] / P["ke"]
+    Efield = -grad_mu(linear_parts(xd, mu0), mu0) / P["ke"]
 
     def matvec(p):
         pp = p.detach().clone().requires_grad_(True)
-        return _grad(quadratic(xd, pp), [pp], virial)[0] / P["ke"]
+        return grad_mu(quadratic_parts(xd, pp), pp) / P["ke"]
 
     debye = P["debye"]
     mu = (a_pol[None, :, None] * Efield) if mu_guess is None else torch.as_tensor(mu_guess, dtype=DT).clone()
@@ -247,7 +263,10 @@ def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=20
     E["pol"] = -0.5 * P["ke"] * float((mu * Efield).sum())
     if forces:
         mud = mu.detach()
-        add_grad(quadratic(x, mud) + linear(x, mud), "pol")
+        for e in quadratic_parts(x, mud):
+            add_grad(e, "pol", retain=True)
+        for e in linear_parts(x, mud):
+            add_grad(e, "pol", retain=True)
 
     E["total"] = sum(E[k] for k in TERMS)
     return {
@@ -262,7 +281,8 @@ def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=20
         "resid_D": res,
         "min_ct_denominator": min_de,
         "pol_ops": ({"matvec": matvec, "alpha": a_pol,
-                     "functional": lambda m: float(quadratic(xd, m) + linear(xd, m)) / P["ke"]}
+                     "functional": lambda m: (sum(float(e) for e in quadratic_parts(xd, m)) +
+                                              sum(float(e) for e in linear_parts(xd, m))) / P["ke"]}
                     if keep_operators else None),
     }
 
