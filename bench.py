@@ -42,13 +42,21 @@ WORKLOAD = ("water4096: 4096 rigid-geometry waters (12,288 atoms), cubic box 49.
             "alpha 0.4/A, PCG 1e-6 D warm start, velocity-Verlet NVE 0.5 fs from 300 K")
 SAMPLE = ("oracle sample: 512 waters (1,536 atoms) at the same density, rc 9 A, SPME 32^3 (1.29 points/A, as 64^3 "
           "on 49.66 A) order 5, alpha 0.4, PCG 1e-6 D; one full energy + force evaluation per step")
-# Algorithmic FP32 work per unit (fused multiply-add = 2): the midpoints of
-# the per-unit estimates of the hot-path scope table (multipole site pair with
-# Ewald kernel, energy, gradient, torque, field and penetration 250-350;
-# repulsion orbital pair 150-250; dispersion + exchange-dispersion point pair
-# 60-80; charge-transfer donor-acceptor pair ~100).
+# Algorithmic FP32 work per unit (fused multiply-add = 2, a transcendental or
+# reciprocal square root = 1), energy and full gradient of one unordered unit:
+# multipole site pair with Ewald kernel, energy, gradient, torque, field and
+# penetration 300 (the middle of the 250-350 estimate); charge-transfer
+# donor-acceptor pair 100.  Repulsion and dispersion are counted from their
+# formulas (Technical Appendix): one atom pair of an overlap (two cosines,
+# the s/p overlap, two exponentials, and their gradients at the four points)
+# is 63 + 125 flops; a bond-bond item has four atom pairs plus the midpoint
+# distance, the S^2/R and S^2/R^2 energy and the gradient assembly (850);
+# bond-lone pair and lone pair-bond items two atom pairs (455); lone
+# pair-lone pair one overlap with two cosines (220); a dispersion point pair
+# the C6/C8/C10 damped terms and exchange-dispersion with their radial
+# derivative (70).
 FLOPS_PERM_SITE_PAIR = 300
-FLOPS_REP_ITEM = 200
+FLOPS_REP = {"rep_bb": 850, "rep_bl": 455, "rep_lb": 455, "rep_ll": 220}
 FLOPS_DISP_ITEM = 70
 FLOPS_CT_ITEM = 100
 
@@ -151,9 +159,10 @@ def count_units(pos, box, rc, pts):
                   (target-site formulation: energy, gradient, torque and
                   field of the target);
       lp_pairs    ordered (lone pair, source site) pairs within rc;
-      rep_items   unordered repulsion orbital pairs: bond-bond (bond
-                  midpoints), bond-lone pair and lone pair-bond (midpoint to
-                  lone pair), lone pair-lone pair, within rc;
+      rep_items   unordered repulsion orbital pairs within rc, and by class:
+                  rep_bb bond-bond (bond midpoints), rep_bl and rep_lb
+                  bond-lone pair and lone pair-bond (midpoint to lone pair),
+                  rep_ll lone pair-lone pair;
       disp_items  unordered (point, point) dispersion pairs within rc over
                   O, H1, H2, LP1, LP2;
       ct_items    unordered donor-acceptor pairs: 8 per molecule pair whose
@@ -161,7 +170,8 @@ def count_units(pos, box, rc, pts):
     pts: (M, 7, 3) absolute O, H1, H2, M1, M2, LP1, LP2."""
     O = pos[:, 0]
     i, j, sh = unordered_pairs(O, box, rc + 2.6)
-    n = dict(site_pairs=0, lp_pairs=0, rep_items=0, disp_items=0, ct_items=0)
+    n = dict(site_pairs=0, lp_pairs=0, rep_items=0, rep_bb=0, rep_bl=0, rep_lb=0, rep_ll=0, disp_items=0,
+             ct_items=0)
     rc2 = rc * rc
     for a in range(0, i.size, 65536):
         ii, jj, ss = i[a:a + 65536], j[a:a + 65536], sh[a:a + 65536]
@@ -177,8 +187,11 @@ def count_units(pos, box, rc, pts):
         mi = 0.5 * (Pi[:, 0:1] + Pi[:, 1:3])            # bond midpoints (n, 2, 3)
         mj = 0.5 * (Pj[:, 0:1] + Pj[:, 1:3])
         li, lj = Pi[:, 5:7], Pj[:, 5:7]
-        n["rep_items"] += int(within(mi, mj).sum() + within(mi, lj).sum() + within(li, mj).sum()
-                              + within(li, lj).sum())
+        cls = {"rep_bb": int(within(mi, mj).sum()), "rep_bl": int(within(mi, lj).sum()),
+               "rep_lb": int(within(li, mj).sum()), "rep_ll": int(within(li, lj).sum())}
+        for k, v in cls.items():
+            n[k] += v
+        n["rep_items"] += sum(cls.values())
         qi = np.concatenate([Pi[:, :3], li], 1)
         qj = np.concatenate([Pj[:, :3], lj], 1)
         n["disp_items"] += int(within(qi, qj).sum())
@@ -192,14 +205,14 @@ def count_units_clusters(start, M):
     cluster, no cutoff)."""
     n = np.diff(np.asarray(start, dtype=np.int64))
     pairs = int((n * (n - 1) // 2).sum())           # unordered molecule pairs
-    return dict(site_pairs=2 * 25 * pairs, lp_pairs=2 * 10 * pairs, rep_items=16 * pairs, disp_items=25 * pairs,
-                ct_items=8 * pairs)
+    return dict(site_pairs=2 * 25 * pairs, lp_pairs=2 * 10 * pairs, rep_items=16 * pairs, rep_bb=4 * pairs,
+                rep_bl=4 * pairs, rep_lb=4 * pairs, rep_ll=4 * pairs, disp_items=25 * pairs, ct_items=8 * pairs)
 
 
 def kernel_flops(n):
     """Algorithmic FP32 flops per launch set, from the per-unit figures above."""
     return {"real_perm": n["site_pairs"] * FLOPS_PERM_SITE_PAIR,
-            "short": n["rep_items"] * FLOPS_REP_ITEM + n["disp_items"] * FLOPS_DISP_ITEM,
+            "short": sum(n[k] * f for k, f in FLOPS_REP.items()) + n["disp_items"] * FLOPS_DISP_ITEM,
             "ct": n["ct_items"] * FLOPS_CT_ITEM}
 
 
@@ -457,6 +470,18 @@ def equilibrate(pkg, ctx, pos, vel, masses, n_min=20, n_thermo=200, temp=300.0, 
     return 2.0 * kinetic(vel, m3) / (ndof * KB_KCAL)
 
 
+PHASES = ("sites", "neighbors", "real_perm", "short", "spme_perm", "ct", "pcg", "real_tmu", "real_polforce",
+          "spme_polforce", "finalize")
+
+
+def read_phases(pkg, ctx, steps):
+    out = {}
+    for name in PHASES:
+        ms, n = pkg.sibfa_profile_get(ctx, name)
+        out[name] = {"ms_per_step": ms / steps, "launches": n}
+    return out
+
+
 def timed_steps(pkg, ctx, pos, vel, masses, steps, stream, flush, dt_fs=0.5, keep=False, energy=False, support=None):
     """steps velocity-Verlet steps, each timed with CUDA events on the
     caller's stream after an L2 flush; returns (ms total, iterations,
@@ -640,21 +665,28 @@ def main():
     barrier(dist)
     launches = pkg.sibfa_kernel_launches(ctx) - l0
     tb, tdone = pkg.sibfa_tuned_shape(ctx)
-    phases = {}
-    for name in ("sites", "neighbors", "real_perm", "short", "spme_perm", "ct", "pcg", "real_tmu", "real_polforce",
-                 "spme_polforce", "finalize"):
-        ms, n = pkg.sibfa_profile_get(ctx, name)
-        phases[name] = {"ms_per_step": ms / args.steps, "launches": n}
+    phases = read_phases(pkg, ctx, args.steps)
+    # Serial pass (after the timed region, same trajectory): every phase alone
+    # on the GPU, so a phase's span is its kernels' own duration.  In the
+    # timed steps the short-range and charge-transfer kernels share the SMs
+    # with the solve from lower-priority streams and their spans include the
+    # waits.
+    n_serial = 3
+    pkg.sibfa_set_profiling(ctx, 2)
+    pkg.sibfa_profile_clear(ctx)
+    _, iters_serial, _, _ = timed_steps(pkg, ctx, pos, vel, masses, n_serial, stream, flush, dt_fs=dt)
+    phases_serial = read_phases(pkg, ctx, n_serial)
     pkg.sibfa_set_profiling(ctx, False)
     peak = measure_fp32_peak(pkg, local)
     step_ms = max_over_ranks(dist, total_ms) / args.steps
     value = weak_value(ws, 3 * M, step_ms)
 
     # Rooflines.  Pair kernels: algorithmic FP32 flops per step (unit counts
-    # x per-unit figures) over the kernel's live CUDA-event time on its own
-    # stream, against the FP32 FMA rate measured on this device; SPME: the
-    # permanent pass's algorithmic bytes over its event time, against the
-    # measured HBM copy bandwidth.
+    # x per-unit figures) over the kernel's CUDA-event time on the stream it
+    # runs on in the serial pass, against the FP32 FMA rate measured on this
+    # device; the same over its span in the timed steps is reported as
+    # achieved_live.  SPME: the permanent pass's algorithmic bytes over its
+    # serial event time, against the measured HBM copy bandwidth.
     P = synth.PARAMS
     pos_h = pos.cpu().numpy().reshape(M, 3, 3)
     if args.workload in ("water4096", "water32000", "water216_paper"):
@@ -667,36 +699,41 @@ def main():
                              "Thole field; 1 launch per step"),
                "short": ("k_short<float, %d, 0, 0|1>" % int(args.workload != "clusters4096"),
                          "repulsion (part 0) and dispersion + exchange-dispersion (part 1); 2 launches per step, "
-                         "timed together on the short-range stream"),
+                         "timed together"),
                "ct": ("k_ct<float, %d, 0>" % int(args.workload != "clusters4096"),
-                      "reduced charge transfer; 1 launch per step on the charge-transfer stream")}
+                      "reduced charge transfer; 1 launch per step")}
     lines = {}
     for key, (kname, what) in kernels.items():
-        ms = phases[key]["ms_per_step"]
+        ms, ms_live = phases_serial[key]["ms_per_step"], phases[key]["ms_per_step"]
         if ms <= 0:
             continue
         ach = kfl[key] / (ms * 1e-3) / 1e12
+        ach_live = kfl[key] / (ms_live * 1e-3) / 1e12 if ms_live > 0 else None
         lines[key] = {"bound": "alu", "kernel": kname, "what": what, "achieved": ach, "peak": peak["tflops"],
                       "unit": "TFLOP/s", "frac": ach / peak["tflops"], "flops_per_step": kfl[key],
-                      "ms_per_step": ms, "traffic": measured_traffic(key, args.workload)}
+                      "ms_per_step": ms, "timing": "serial pass, kernel alone on the GPU",
+                      "achieved_live": ach_live, "frac_live": ach_live / peak["tflops"] if ach_live else None,
+                      "ms_per_step_live": ms_live, "traffic": measured_traffic(key, args.workload)}
     if args.workload != "clusters4096":
         K = o["grid"] if not np.isscalar(o["grid"]) else (o["grid"],) * 3
         nbytes = spme_pass_bytes(K, 5 * M)
-        ms = phases["spme_perm"]["ms_per_step"]
+        ms = phases_serial["spme_perm"]["ms_per_step"]
         hbm = measured_hbm_peak()
         lines["spme_perm"] = {"bound": "hbm", "kernel": "spme permanent pass (spread, cuFFT r2c, convolution, "
                               "cuFFT c2r, gather to 3rd derivatives, intramolecular corrections)",
                               "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                               "frac": nbytes / (ms * 1e-3) / 1e9 / hbm, "bytes_per_pass": nbytes, "ms_per_step": ms,
+                              "timing": "serial pass", "ms_per_step_live": phases["spme_perm"]["ms_per_step"],
                               "traffic": None, "peak_basis": "hbm_gbs of MEASURED_PEAKS.json (copy bandwidth)"}
-        it = float(np.mean(iters))
-        pcg_ms = phases["pcg"]["ms_per_step"]
+        it = float(np.mean(iters_serial))
+        pcg_ms = phases_serial["pcg"]["ms_per_step"]
         lines["pcg_iteration"] = {"bound": "hbm", "kernel": "one PCG iteration (real-space T.p from the pair list, "
                                   "SPME of the direction, cooperative vector step)",
                                   "achieved": nbytes / (pcg_ms / (it + 1) * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                                   "frac": nbytes / (pcg_ms / (it + 1) * 1e-3) / 1e9 / hbm,
                                   "ms_per_iteration": pcg_ms / (it + 1), "iterations_per_step": it,
-                                  "bytes_per_iteration_spme": nbytes, "traffic": None}
+                                  "bytes_per_iteration_spme": nbytes, "timing": "serial pass (device loop, the solve alone on the GPU)",
+                                  "traffic": None}
     dom = max(("real_perm", "short"), key=lambda k: lines[k]["ms_per_step"] if k in lines else -1)
     roofline = dict(lines[dom])
     roofline["peak_basis"] = peak["basis"]
@@ -752,6 +789,7 @@ def main():
         "clocks": clk.summary(), "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
         "rooflines": lines, "fp32_peak": peak,
         "cpu_baseline": cpu, "fp64_gpu_path": fp64, "pcg_iters_mean": float(np.mean(iters)), "phases_ms": phases,
+        "phases_ms_serial": phases_serial,
         "nve": {"equilibration": f"20 capped steepest-descent steps, {args.equil_steps} velocity-rescaled steps at "
                                  f"300 K (T after: {t_equil:.1f} K), {max(3, args.warmup)} NVE warm-up steps",
                 "total_energy_first": etot[0], "total_energy_last": etot[-1],

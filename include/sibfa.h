@@ -238,7 +238,16 @@ sibfa_status sibfa_tuned_shape(const sibfa_ctx *ctx, int *blocks_per_sm, int *do
  * (whole solve), "real_tmu" (real-space part of each T.mu product),
  * "real_polforce", "spme_polforce", "finalize".  sibfa_profile_get returns
  * the summed milliseconds and the number of spans of one phase recorded
- * since the last get/clear of that phase, and synchronizes the stream. */
+ * since the last get/clear of that phase, and synchronizes the stream.
+ * on = 1: the phases keep their usual overlap on the context's streams, so a
+ * span on a low-priority stream includes the time it waited for SMs.
+ * on = 2: serial profiling: every phase runs alone on the GPU (the streams
+ * join after each reciprocal-space chain, and the short-range and
+ * charge-transfer kernels run in order on the main stream), so each span is
+ * the duration of that phase's kernels alone.  The solve keeps its device
+ * loop (real and reciprocal parts of each product concurrent, as captured);
+ * "real_tmu" then times the first product's real-space part alone.  Results agree
+ * with on = 0 or 1 up to the order of floating-point sums.  on = 0: off. */
 void sibfa_set_profiling(sibfa_ctx *ctx, int on);
 sibfa_status sibfa_profile_get(sibfa_ctx *ctx, const char *name, double *ms, int *count);
 void sibfa_profile_clear(sibfa_ctx *ctx);

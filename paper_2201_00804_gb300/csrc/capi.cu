@@ -89,6 +89,7 @@ struct sibfa_ctx {
     bool md_forces_valid = false;
     // optional per-phase timing with CUDA events on the context stream
     bool profiling = false;
+    bool serial = false;   // profiling with every phase alone on the GPU (no stream overlap)
     struct Span {
         std::string name;
         cudaEvent_t a, b;
@@ -543,6 +544,8 @@ sibfa_status matvec(sibfa_ctx *ctx, DevState<R> &d, const double *vec, Launch L)
         st = fft(ctx, d, false, 1);
         if (st) return st;
         launch_gather_field(p, d, d.efp_r, L2);   // includes the intramolecular part
+        // serial profiling, outside the captured loop: the real-space product alone
+        if (ctx->serial && !ctx->capturing && (st = join_rec(ctx))) return st;
     }
     { Phase ph(ctx, "real_tmu");  launch_real_tmu(p, d, d.efp, L); }
     if (p.periodic) return join_rec(ctx);
@@ -707,6 +710,7 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
         if ((st = fft(ctx, d, false, 1))) return st;
         launch_gather_perm(p, dr, L2);
         launch_intra_perm(p, dr, L2);
+        if (ctx->serial && (st = join_rec(ctx))) return st;
     }
     { Phase ph(ctx, "neighbors");  launch_neighbors(p, d, ctx->ncell, L); }
     // Short-range terms on the third, lowest-priority stream beside the
@@ -714,7 +718,7 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
     // idle): their short blocks fill in behind the other streams' work.  They
     // write their own gradient array and are joined before the chain rule.
     // The virial variant runs in order on the main stream.
-    const bool bg_short = !dipoles_only && !p.vir;
+    const bool bg_short = !dipoles_only && !p.vir && !ctx->serial;
     if (bg_short) {
         if ((st = fork_short(ctx))) return st;
         ctx->short_pending = true;
@@ -730,7 +734,7 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
     // Lone-pair potentials and then the charge transfer on the fourth stream
     // (the transfer after the reciprocal chain); joined before the
     // polarization energy, which copies the lambdas.
-    const bool bg_ct = !dipoles_only && !p.vir;
+    const bool bg_ct = !dipoles_only && !p.vir && !ctx->serial;
     if (bg_ct) {
         if ((st = fork_ct(ctx))) return st;
         ctx->ct_pending = true;
@@ -781,6 +785,7 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
             if ((sf = fft(ctx, d, false, 2))) return sf;
             launch_gather_polforce(p, dr, L2);
             launch_intra_polforce(p, dr, L2);
+            if (ctx->serial && (sf = join_rec(ctx))) return sf;
         }
         { Phase ph(ctx, "real_polforce");  launch_real_polforce(p, d, L); }
         if (p.periodic) {
@@ -1281,6 +1286,7 @@ sibfa_status sibfa_last_stats(const sibfa_ctx *ctx, int *pcg_iters, double *pcg_
 void sibfa_set_profiling(sibfa_ctx *ctx, int on) {
     if (!ctx) return;
     ctx->profiling = on != 0;
+    ctx->serial = on == 2;
 }
 
 /* Sum of the recorded phase durations (ms) and their count for `name`; the

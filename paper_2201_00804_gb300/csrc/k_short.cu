@@ -8,11 +8,14 @@
 //   BL  bond of i with lone pair l of j                 4
 //   LB  lone pair l of i with bond of j                 4
 //   LL  lone pair of i with lone pair of j              4
-//   D   point u of i with point v of j                 25   (O, H1, H2, LP1, LP2)
-// Items inside the cutoff (per item, on the distance of its radial factor)
-// are appended to one ring queue per class in shared memory and evaluated in
-// full 32-lane rounds, so all lanes of a round do the same work.  Dispersion
-// items are pushed per point u of i to bound the queue.  Gradients go to i's
+//   D   point u of i with the points v of j            5    (u, v: O, H1, H2, LP1, LP2)
+// Repulsion items inside the cutoff (per item, on the distance of its radial
+// factor) are appended to one ring queue per class in shared memory and
+// evaluated in full 32-lane rounds, so all lanes of a round do the same work.
+// A dispersion item is a point u of i with every point v of j, queued when
+// at least one of the five point pairs is inside the cutoff and carrying the
+// mask of those that are; the lane runs the five v unrolled, so the
+// partner's data and u's factors are read once per item.  Gradients go to i's
 // points only (the full list visits each pair from both sides).
 #include <cstddef>
 
@@ -88,7 +91,7 @@ __device__ inline R rep_energy(R pref, R C1, R C2, R O1, R O2, R ri, R &e1, R &e
 // Queue layout (words: slot * 32 + item code)
 constexpr int SQ_BB = 0, SQ_BL = 160, SQ_LB = 320, SQ_LL = 480, SQ_D = 640;
 constexpr int SQ_CAP = 160;    // >= 31 carried + 32 lanes x 4 items
-constexpr int SQ_CAPD = 192;   // >= 31 carried + 32 lanes x 5 items (one point u of i)
+constexpr int SQ_CAPD = 192;   // >= 31 carried + 32 lanes x 5 items (points u of i)
 constexpr int SQ_WORDS = 1024; // also holds the FP64 reduction buffer (15 x 33 doubles)
 
 // i-side state of one warp
@@ -287,47 +290,60 @@ __device__ void item_ll(const Scal<R> &S, const ShortTables &T, const DevState<R
     if (VIR) vir_add(a.W, go + gl, dO, R(-0.5));
 }
 
-// dispersion and exchange-dispersion of point u of i with point v of j
+// dispersion and exchange-dispersion of point u of i with the points v of j
+// whose bits are set in vmask (v = 0..4 unrolled: the partner's point, kind
+// and prefactors are compile-time per v; the neighbour's data and u's are
+// read once per item)
 template <typename R, bool VIR>
-__device__ void item_d(const KParams &p, const Scal<R> &S, const ShortTables &T, const DevState<R> &d,
-                       const ShortI<R> &I, int i, int word, ShortAcc<R> &a) {
-    const int slot = word >> 5, c = word & 31;
-    const int u = c / 5, v = c % 5;
+__device__ void item_du(const KParams &p, const Scal<R> &S, const ShortTables &T, const DevState<R> &d,
+                        const ShortI<R> &I, int i, int word, ShortAcc<R> &a) {
+    const int slot = word >> 8, u = (word >> 5) & 7, vmask = word & 31;
     int j;
     V3<R> dO;
     neighbour(d, i, slot, j, dO);
-    const V3<R> dv = selP(I, u) - qpt(d, j, dO, v);
-    const R r2 = dot(dv, dv);
-    const R ri = rsqrt_(r2), r = r2 * ri;
-    const int ku = u == 0 ? 0 : (u < 3 ? 1 : 2), kv = v == 0 ? 0 : (v < 3 ? 1 : 2);
-    const R m = mulc(r, T.disp_km[ku][kv]), mi = rcp_(m);
-    // exp(-gamma_n d) with d = S/r - 1: argument gamma_n - (gamma_n S)/r
-    const R a6 = mulc(ri, T.disp_gS[0][ku][kv]), a8 = mulc(ri, T.disp_gS[1][ku][kv]),
-            a10 = mulc(ri, T.disp_gS[2][ku][kv]);
-    const R m2i = mi * mi, m6i = m2i * m2i * m2i, m8i = m6i * m2i, m10i = m8i * m2i;
-    const R e6 = S.c6 * exp_(S.g6 - a6) * m6i;
-    const R e8 = S.c8 * exp_(S.g8 - a8) * m8i;
-    const R e10 = S.c10 * exp_(S.g10 - a10) * m10i;
-    const R fsum = e6 + e8 + e10;
-    const R dfdr = e6 * ((a6 - R(6)) * ri) + e8 * ((a8 - R(8)) * ri) + e10 * ((a10 - R(10)) * ri);
-    const bool lu = u >= 3, lv = v >= 3;
-    const R bu = betap<R>(p, u), bv = betap<R>(p, v);
-    const R nlp = S.nlp;
-    R pref, xc;
-    if (!lu && !lv) { pref = -bu * bv; xc = S.xd_c1; }
-    else if (lu && lv) { pref = -nlp * nlp * R(0.25); xc = nlp * nlp * R(0.25) * S.xd_c2; }
-    else { pref = -S.delta * R(0.5); xc = nlp * R(0.5) * S.xd_c3; }
-    const R cfj = R(1) - qcharge(d, j, v < 3 ? v : 0) * (v == 1 || v == 2 ? S.inv_nval_h : S.inv_nval_o);
+    const V3<R> Pu = selP(I, u);
+    const int ku = u == 0 ? 0 : (u < 3 ? 1 : 2);
+    const bool lu = u >= 3;
+    const R bu = betap<R>(p, u), nlp = S.nlp;
     R cfi = I.cf[0];
 #pragma unroll
     for (int t = 1; t < 5; ++t)
         if (t == u) cfi = I.cf[t];
-    const R K = bu * bv * cfi * cfj;
-    const R ex = xc * K * exp_(-mulc(r, T.xd_k[ku][kv]));
-    a.Ed.add(R(0.5) * pref * fsum);
-    a.Ex.add(R(0.5) * ex);
-    const R dEdr = pref * dfdr - cval<R>(T.xd_k[ku][kv]) * ex;
-    const V3<R> gu = (dEdr * ri) * dv;
+    const R *offj = d.off + j * NP * 3;
+    const R qO = qcharge(d, j, 0);
+    V3<R> gu = mk(R(0), R(0), R(0));
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        if (!((vmask >> v) & 1)) continue;
+        const int s = v < 3 ? v : v + 2;
+        const V3<R> dv = Pu - (dO + mk(offj[s * 3], offj[s * 3 + 1], offj[s * 3 + 2]));
+        const R r2 = dot(dv, dv);
+        const R ri = rsqrt_(r2), r = r2 * ri;
+        const int kv = v == 0 ? 0 : (v < 3 ? 1 : 2);
+        const R m = mulc(r, T.disp_km[ku][kv]), mi = rcp_(m);
+        const R a6 = mulc(ri, T.disp_gS[0][ku][kv]), a8 = mulc(ri, T.disp_gS[1][ku][kv]),
+                a10 = mulc(ri, T.disp_gS[2][ku][kv]);
+        const R m2i = mi * mi, m6i = m2i * m2i * m2i, m8i = m6i * m2i, m10i = m8i * m2i;
+        const R e6 = S.c6 * exp_(S.g6 - a6) * m6i;
+        const R e8 = S.c8 * exp_(S.g8 - a8) * m8i;
+        const R e10 = S.c10 * exp_(S.g10 - a10) * m10i;
+        const R fsum = e6 + e8 + e10;
+        const R dfdr = e6 * ((a6 - R(6)) * ri) + e8 * ((a8 - R(8)) * ri) + e10 * ((a10 - R(10)) * ri);
+        const bool lv = v >= 3;
+        const R bv = betap<R>(p, v);
+        R pref, xc;
+        if (!lu && !lv) { pref = -bu * bv; xc = S.xd_c1; }
+        else if (lu && lv) { pref = -nlp * nlp * R(0.25); xc = nlp * nlp * R(0.25) * S.xd_c2; }
+        else { pref = -S.delta * R(0.5); xc = nlp * R(0.5) * S.xd_c3; }
+        const R qv = v < 3 ? qcharge(d, j, v) : qO;
+        const R cfj = R(1) - qv * (v == 1 || v == 2 ? S.inv_nval_h : S.inv_nval_o);
+        const R K = bu * bv * cfi * cfj;
+        const R ex = xc * K * exp_(-mulc(r, T.xd_k[ku][kv]));
+        a.Ed.add(R(0.5) * pref * fsum);
+        a.Ex.add(R(0.5) * ex);
+        const R dEdr = pref * dfdr - cval<R>(T.xd_k[ku][kv]) * ex;
+        gu = gu + (dEdr * ri) * dv;
+    }
     addG(a, u, gu);
     if (VIR) vir_add(a.W, gu, dO, R(-0.5));
 }
@@ -393,8 +409,8 @@ __global__ void __launch_bounds__(128, PER ? (PART == 0 ? 4 : 6) : 5) k_short(KP
             int j = 0;
             V3<R> dO = mk(R(0), R(0), R(0));
             if (live) neighbour(d, i, slot, j, dO);
-            // PART 0, stage 0: repulsion items; PART 1, stages 1-5: dispersion items of point u = stage - 1
-            const int s0 = PART == 0 ? 0 : 1, s1 = PART == 0 ? 1 : 6;
+            // PART 0, stage 0: repulsion items; PART 1, stage 1: dispersion items
+            const int s0 = PART == 0 ? 0 : 1, s1 = PART == 0 ? 1 : 2;
             for (int stage = s0; stage < s1; ++stage) {
                 if (PART == 0) {
                     unsigned bb = 0, bl = 0, lb = 0, ll = 0;
@@ -421,28 +437,35 @@ __global__ void __launch_bounds__(128, PER ? (PART == 0 ? 4 : 6) : 5) k_short(KP
                         t[c] += n;
                     }
                 } else {
-                    const int u = stage - 1;
-                    unsigned bits = 0;
+                    // one item per point u of i with at least one point v of j inside the cutoff
+                    unsigned vm[5] = {0, 0, 0, 0, 0};
                     if (live) {
-                        const V3<R> Pu = selP(I, u);
+                        V3<R> Q[5];
     #pragma unroll
-                        for (int v = 0; v < 5; ++v) {
-                            const V3<R> x = Pu - qpt(d, j, dO, v);
-                            if (!PER || dot(x, x) < rc2) bits |= 1u << v;
-                        }
+                        for (int v = 0; v < 5; ++v) Q[v] = qpt(d, j, dO, v);
+    #pragma unroll
+                        for (int u = 0; u < 5; ++u)
+    #pragma unroll
+                            for (int v = 0; v < 5; ++v) {
+                                const V3<R> x = I.P[u] - Q[v];
+                                if (!PER || dot(x, x) < rc2) vm[u] |= 1u << v;
+                            }
                     }
-                    int n;
-                    int pos = warp_excl_scan(__popc(bits), lane, n);
+                    int cnt = 0;
     #pragma unroll
-                    for (int v = 0; v < 5; ++v)
-                        if ((bits >> v) & 1u) q[SQ_D + (t[4] + pos++) % SQ_CAPD] = slot * 32 + u * 5 + v;
+                    for (int u = 0; u < 5; ++u) cnt += vm[u] != 0;
+                    int n;
+                    int pos = warp_excl_scan(cnt, lane, n);
+    #pragma unroll
+                    for (int u = 0; u < 5; ++u)
+                        if (vm[u]) q[SQ_D + (t[4] + pos++) % SQ_CAPD] = (slot << 8) | (u << 5) | (int)vm[u];
                     t[4] += n;
                 }
                 __syncwarp();
                 const bool last = flush && stage == s1 - 1;
                 if (PART == 1) {
                     while (t[4] - h[4] >= 32 || (last && t[4] > h[4])) {
-                        if (lane < t[4] - h[4]) item_d<R, VIR>(p, S, T, d, I, i, q[SQ_D + (h[4] + lane) % SQ_CAPD], acc);
+                        if (lane < t[4] - h[4]) item_du<R, VIR>(p, S, T, d, I, i, q[SQ_D + (h[4] + lane) % SQ_CAPD], acc);
                         h[4] += min(32, t[4] - h[4]);
                     }
                     __syncwarp();

@@ -50,9 +50,42 @@ __device__ inline void line_weight(const Axis<R, NDER> &A, int i, int &g, R (&w)
         }
 }
 
-// Spread one point per warp: lanes 0-24 own the stencil rows (i, j) and add
-// the multipole operator q + mu.grad + (1/3) Theta:grad grad applied to the
-// B-spline weights at the 5 grid points of their row.
+// Spread and PCG-gather layout: a group of PG = 8 lanes per point (4 points
+// per warp).  Lanes 0-4 of a group own the x-lines i = 0..4 of the 5x5x5
+// stencil (25 grid points each); lanes 5-7 take per-point work that does
+// not touch the grid.  The lanes of a group reduce with shuffles.
+constexpr int PG = 8;
+
+// Adds v[k] at the grid points row + zg[k] (k = 0..4, zg[k] = b - k modulo
+// K2).  In FP32, when the row length is a multiple of 4 and the five points
+// do not wrap, the values go as two aligned 4-wide vector reductions over the
+// 8 points from the 4-aligned index at or below b - 4 (the three free slots
+// add zero): 2 atomic operations instead of 5.
+template <typename R>
+__device__ inline void add_zline(R *grid, size_t row, int K2, const int (&zg)[ORDER], const R (&v)[ORDER]) {
+    if constexpr (sizeof(R) == 4) {
+        if ((K2 & 3) == 0 && zg[0] >= ORDER - 1) {
+            const int zlo = zg[0] - (ORDER - 1), a0 = zlo & ~3, r = zlo - a0;
+            // u: values at increasing z from zlo, then shifted up by r (0..3)
+            float u[8] = {v[4], v[3], v[2], v[1], v[0], 0.f, 0.f, 0.f};
+            float t[8];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) t[o] = (r & 1) ? (o >= 1 ? u[o - 1] : 0.f) : u[o];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) u[o] = (r & 2) ? (o >= 2 ? t[o - 2] : 0.f) : t[o];
+            float4 *g4 = reinterpret_cast<float4 *>(grid + row + a0);
+            atomicAdd(g4, make_float4(u[0], u[1], u[2], u[3]));
+            atomicAdd(g4 + 1, make_float4(u[4], u[5], u[6], u[7]));
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < ORDER; ++k) atomicAdd(&grid[row + zg[k]], v[k]);
+}
+
+// Spread: lane i < 5 of a point's group adds the multipole operator
+// q + mu.grad + (1/3) Theta:grad grad applied to the B-spline weights at the
+// 25 grid points of x-line i.
 // kind PERM: 5 sites per molecule with their multipoles;
 // kind DIP: 3 polarizable atoms with the induced dipoles (d.muR);
 // kind DIP_PCG: the same from the working-precision PCG vector;
@@ -66,8 +99,9 @@ __global__ void __launch_bounds__(256) k_spread(KParams p, DevState<R> d, int ki
         kind = SPREAD_DIP;
     }
     const int per = kind == SPREAD_PERM ? NS : (kind == SPREAD_DIP ? 3 : 2);
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (t >= p.M * per || lane >= 25) return;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = gt / PG, xi = gt % PG;
+    if (t >= p.M * per || xi >= ORDER) return;
     const int m = t / per, a = t % per;
     const int pt = kind == SPREAD_LAMBDA ? 5 + a : a;
     Mp<R> mp{};
@@ -80,36 +114,41 @@ __global__ void __launch_bounds__(256) k_spread(KParams p, DevState<R> d, int ki
     axis_weights<R, NDER>(p, d, m, pt, 0, X);
     axis_weights<R, NDER>(p, d, m, pt, 1, Y);
     axis_weights<R, NDER>(p, d, m, pt, 2, Z);
-    int gx, gy;
-    R wx[NDER + 1], wy[NDER + 1];
-    line_weight<R, NDER>(X, lane / 5, gx, wx);
-    line_weight<R, NDER>(Y, lane % 5, gy, wy);
+    int gx;
+    R wx[NDER + 1];
+    line_weight<R, NDER>(X, xi, gx, wx);
     const R third = R(1) / R(3);
-    // coefficients of the z weights (0th, 1st, 2nd derivative)
-    R c0 = mp.q * wx[0] * wy[0], c1 = R(0), c2 = R(0);
-    if constexpr (NDER >= 1) {
-        c0 += mp.mu.x * wx[1] * wy[0] + mp.mu.y * wx[0] * wy[1];
-        c1 = mp.mu.z * wx[0] * wy[0];
-    }
-    if constexpr (NDER >= 2) {
-        c0 += third * (mp.th.xx * wx[2] * wy[0] + mp.th.yy * wx[0] * wy[2] + R(2) * mp.th.xy * wx[1] * wy[1]);
-        c1 += third * R(2) * (mp.th.xz * wx[1] * wy[0] + mp.th.yz * wx[0] * wy[1]);
-        c2 = third * mp.th.zz * wx[0] * wy[0];
-    }
-    const size_t row = ((size_t)gx * p.K[1] + gy) * p.K[2];
 #pragma unroll
-    for (int k = 0; k < ORDER; ++k) {
-        R v = c0 * Z.w[0][k];
-        if constexpr (NDER >= 1) v += c1 * Z.w[1][k];
-        if constexpr (NDER >= 2) v += c2 * Z.w[2][k];
-        atomicAdd(&grid[row + Z.g[k]], v);
+    for (int jy = 0; jy < ORDER; ++jy) {
+        R wy[NDER + 1];
+#pragma unroll
+        for (int n = 0; n <= NDER; ++n) wy[n] = Y.w[n][jy];
+        // coefficients of the z weights (0th, 1st, 2nd derivative)
+        R c0 = mp.q * wx[0] * wy[0], c1 = R(0), c2 = R(0);
+        if constexpr (NDER >= 1) {
+            c0 += mp.mu.x * wx[1] * wy[0] + mp.mu.y * wx[0] * wy[1];
+            c1 = mp.mu.z * wx[0] * wy[0];
+        }
+        if constexpr (NDER >= 2) {
+            c0 += third * (mp.th.xx * wx[2] * wy[0] + mp.th.yy * wx[0] * wy[2] + R(2) * mp.th.xy * wx[1] * wy[1]);
+            c1 += third * R(2) * (mp.th.xz * wx[1] * wy[0] + mp.th.yz * wx[0] * wy[1]);
+            c2 = third * mp.th.zz * wx[0] * wy[0];
+        }
+        R v[ORDER];
+#pragma unroll
+        for (int k = 0; k < ORDER; ++k) {
+            v[k] = c0 * Z.w[0][k];
+            if constexpr (NDER >= 1) v[k] += c1 * Z.w[1][k];
+            if constexpr (NDER >= 2) v[k] += c2 * Z.w[2][k];
+        }
+        add_zline<R>(grid, ((size_t)gx * p.K[1] + Y.g[jy]) * p.K[2], p.K[2], Z.g, v);
     }
 }
 
 template <typename R>
 void launch_spread(const KParams &p, DevState<R> &d, int kind, const double *vec, R *grid, Launch L) {
     const int per = kind == SPREAD_PERM ? NS : ((kind == SPREAD_DIP || kind == SPREAD_DIP_PCG) ? 3 : 2);
-    const long long threads = (long long)p.M * per * 32;
+    const long long threads = (long long)p.M * per * PG;
     const unsigned nb = (unsigned)((threads + 255) / 256);
     if (kind == SPREAD_PERM) k_spread<R, 2><<<nb, 256, 0, L.s>>>(p, d, kind, vec, grid);
     else if (kind == SPREAD_LAMBDA) k_spread<R, 0><<<nb, 256, 0, L.s>>>(p, d, kind, vec, grid);
@@ -352,30 +391,37 @@ __device__ inline void gather_row(const KParams &p, const R *grid, const Axis<R,
     }
 }
 
-// Warp gather of one point: returns the derivatives in shared memory (buf,
-// ND_VALS * 33 elements of this warp), valid in all lanes after the call.
+// Group gather of one point (PG lanes; lanes 0-4 sum x-lines 0-4 of the
+// stencil): the derivatives up to NDER, complete in every lane of the group
+// after a shuffle reduction.  All 32 lanes of the warp must call it; a group
+// with live = false returns zeros.
 template <typename R, int NDER>
-__device__ inline void warp_gather(const KParams &p, const DevState<R> &d, const R *grid, int m, int pt, int lane,
-                                   R *buf, Derivs<R> &D) {
+__device__ inline void group_gather(const KParams &p, const DevState<R> &d, const R *grid, int m, int pt, int sub,
+                                    bool live, Derivs<R> &D) {
     constexpr int NV = NDER >= 3 ? 20 : (NDER == 2 ? 10 : (NDER == 1 ? 4 : 1));
-    Axis<R, NDER> X, Y, Z;
-    axis_weights<R, NDER>(p, d, m, pt, 0, X);
-    axis_weights<R, NDER>(p, d, m, pt, 1, Y);
-    axis_weights<R, NDER>(p, d, m, pt, 2, Z);
     R v[ND_VALS];
 #pragma unroll
     for (int k = 0; k < ND_VALS; ++k) v[k] = R(0);
-    if (lane < 25) gather_row<R, NDER>(p, grid, X, Y, Z, lane, v);
-    R vv[NV];
+    if (live && sub < ORDER) {
+        Axis<R, NDER> X, Y, Z;
+        axis_weights<R, NDER>(p, d, m, pt, 0, X);
+        axis_weights<R, NDER>(p, d, m, pt, 1, Y);
+        axis_weights<R, NDER>(p, d, m, pt, 2, Z);
 #pragma unroll
-    for (int k = 0; k < NV; ++k) vv[k] = v[k];
-    const R s = warp_transpose_sum<R, NV>(vv, buf, lane);
-    if (lane < NV) buf[lane] = s;
-    __syncwarp();
-    R *o = reinterpret_cast<R *>(&D);
+        for (int jy = 0; jy < ORDER; ++jy) {
+            R u[ND_VALS];
+            gather_row<R, NDER>(p, grid, X, Y, Z, sub * ORDER + jy, u);
 #pragma unroll
-    for (int k = 0; k < ND_VALS; ++k) o[k] = k < NV ? buf[k] : R(0);
-    __syncwarp();
+            for (int k = 0; k < NV; ++k) v[k] += u[k];
+        }
+    }
+#pragma unroll
+    for (int o = PG / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    R *out = reinterpret_cast<R *>(&D);
+#pragma unroll
+    for (int k = 0; k < ND_VALS; ++k) out[k] = k < NV ? v[k] : R(0);
 }
 
 // full third-derivative tensor entry (a, b, c) from the 10 unique components
@@ -436,87 +482,108 @@ __device__ inline R mp_strain(const Mp<R> &m, const Derivs<R> &D, int k) {
     return D.d1[a] * mu[b] + R(2.0 / 3.0) * t;
 }
 
-constexpr int GW = 8;   // warps (points) per block of the gather kernels
-
-// Permanent pass: one warp per point (7 per molecule).  Sites: energy,
+// Permanent pass: a group of PG lanes per point, the 5 sites of every
+// molecule first (points t < 5 M), then the 2 lone pairs.  Sites: energy,
 // gradient, multipole sensitivities; O/H1/H2 also their field and Hessian;
-// lone pairs: potential and its gradient.
+// lone pairs: potential and its gradient.  The group's lanes then share the
+// outputs.
 template <typename R>
-__global__ void __launch_bounds__(32 * GW) k_gather_perm(KParams p, DevState<R> d) {
-    __shared__ R buf[GW][ND_VALS * 33];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * GW + w;
-    if (t >= p.M * NP) return;
-    const int m = t / NP, pt = t % NP;
+__global__ void __launch_bounds__(256, 2) k_gather_perm(KParams p, DevState<R> d) {
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = gt / PG, sub = gt % PG;
+    const int nsite = p.M * NS;
+    const bool live = t < p.M * NP;
+    const bool site = t < nsite;
+    const int m = site ? t / NS : (t - nsite) / 2;
+    const int pt = site ? t % NS : NS + (t - nsite) % 2;
     Derivs<R> D;
-    if (pt < NS) {
-        warp_gather<R, 3>(p, d, d.grid, m, pt, lane, buf[w], D);
+    // groups of one warp are all sites except in one warp
+    const bool any_site = __any_sync(0xffffffffu, live && site), any_lp = __any_sync(0xffffffffu, live && !site);
+    if (any_site) group_gather<R, 3>(p, d, d.grid, m, pt, sub, live && site, D);
+    if (any_lp) {
+        Derivs<R> Dl;
+        group_gather<R, 1>(p, d, d.grid, m, pt, sub, live && !site, Dl);
+        if (!site) D = Dl;
+    }
+    if (!live) return;
+    if (site) {
         const Mp<R> mp = load_mp(d.gmp + (m * NS + pt) * GMP);
-        if (lane < 3) {
-            d.gpt[(m * NP + pt) * 3 + lane] += (double)mp_grad(mp, D, lane);
-            d.gmu[(m * NS + pt) * 3 + lane] += (double)D.d1[lane];
-            if (pt < 3) d.efield[m * 9 + pt * 3 + lane] -= (double)D.d1[lane] / p.ke;
-        } else if (lane < 9) {
-            d.gth[(m * NS + pt) * 6 + lane - 3] += (double)D.d2[lane - 3] / 3.0;
-            if (pt < 3) d.d2rec[m * 18 + pt * 6 + lane - 3] = (double)D.d2[lane - 3];
-        } else if (lane == 9) {
-            atomicAdd(&d.epart[m * NTERM + T_ELEC], 0.5 * (double)mp_energy(mp, D));
-        }
-        if (p.vir) {
-            if (lane >= 10 && lane < 19) atomicAdd(&d.vir[m * 9 + lane - 10], -(double)mp_strain(mp, D, lane - 10));
-            else if (lane >= 19 && lane < 22 && pt < 3) d.vphi[m * 9 + pt * 3 + lane - 19] = D.d1[lane - 19];
+        for (int o = sub; o < 22; o += PG) {
+            if (o < 3) {
+                d.gpt[(m * NP + pt) * 3 + o] += (double)mp_grad(mp, D, o);
+                d.gmu[(m * NS + pt) * 3 + o] += (double)D.d1[o];
+                if (pt < 3) d.efield[m * 9 + pt * 3 + o] -= (double)D.d1[o] / p.ke;
+            } else if (o < 9) {
+                d.gth[(m * NS + pt) * 6 + o - 3] += (double)D.d2[o - 3] / 3.0;
+                if (pt < 3) d.d2rec[m * 18 + pt * 6 + o - 3] = (double)D.d2[o - 3];
+            } else if (o == 9) {
+                atomicAdd(&d.epart[m * NTERM + T_ELEC], 0.5 * (double)mp_energy(mp, D));
+            } else if (p.vir) {
+                if (o < 19) atomicAdd(&d.vir[m * 9 + o - 10], -(double)mp_strain(mp, D, o - 10));
+                else if (pt < 3) d.vphi[m * 9 + pt * 3 + o - 19] = D.d1[o - 19];
+            }
         }
     } else {
-        warp_gather<R, 1>(p, d, d.grid, m, pt, lane, buf[w], D);
         const int l = pt - NS;
-        if (lane < 3) d.dvlp[(m * 2 + l) * 3 + lane] += (double)D.d1[lane];
-        else if (lane == 3) d.vlp[m * 2 + l] += (double)D.phi;
+        if (sub < 3) d.dvlp[(m * 2 + l) * 3 + sub] += (double)D.d1[sub];
+        else if (sub == 3) d.vlp[m * 2 + l] += (double)D.phi;
     }
 }
 
 template <typename R>
 void launch_gather_perm(const KParams &p, DevState<R> &d, Launch L) {
-    const int n = p.M * NP;
-    k_gather_perm<R><<<(n + GW - 1) / GW, 32 * GW, 0, L.s>>>(p, d);
+    const long long threads = (long long)p.M * NP * PG;
+    k_gather_perm<R><<<(unsigned)((threads + 255) / 256), 256, 0, L.s>>>(p, d);
     count(L);
 }
 
 // PCG product, reciprocal and intramolecular part at each polarizable atom:
-// out += -grad phi / ke from the dipole grid (lanes 0-24, one stencil row
-// each) plus, from lane 25, the self term of the atom's own dipole minus the
-// erf part of the field of the other two atoms' dipoles (dipoles: the
-// working-precision PCG vector).
+// out += -grad phi / ke from the dipole grid plus the self term of the atom's
+// own dipole minus the erf part of the field of the other two atoms' dipoles
+// (dipoles: the working-precision PCG vector).  A group of PG lanes per atom:
+// lanes 0-4 sum the 25 grid points of their x-line, lane 5 the self term,
+// lanes 6 and 7 the erf field of one other atom each.
 template <typename R>
-__global__ void __launch_bounds__(32 * GW) k_gather_field(KParams p, DevState<R> d, double *out) {
-    __shared__ R buf[GW][4 * 33];
+__global__ void __launch_bounds__(256) k_gather_field(KParams p, DevState<R> d, double *out) {
     if (d.flags[1]) return;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * GW + w;
-    if (t >= p.M * 3) return;
-    const int m = t / 3, a = t % 3;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = gt / PG, sub = gt % PG;
+    const bool live = t < p.M * 3;   // the whole group is live or not
+    const int m = live ? t / 3 : 0, a = live ? t % 3 : 0;
     const Scal<R> &S = sc<R>(p);
-    Axis<R, 1> X, Y, Z;
-    axis_weights<R, 1>(p, d, m, a, 0, X);
-    axis_weights<R, 1>(p, d, m, a, 1, Y);
-    axis_weights<R, 1>(p, d, m, a, 2, Z);
-    R vals[3] = {R(0), R(0), R(0)};
-    if (lane < 25) {
-        R v[4];
-        gather_row<R, 1>(p, d.grid, X, Y, Z, lane, v);
-        vals[0] = -v[1] * S.ike;
-        vals[1] = -v[2] * S.ike;
-        vals[2] = -v[3] * S.ike;
-    } else if (lane < 28) {
-        // lane 25: self term of the atom's own dipole; lanes 26, 27: the
-        // erf part of the field of each of the other two atoms' dipoles
+    V3<R> E = mk(R(0), R(0), R(0));
+    if (live && sub < ORDER) {
+        Axis<R, 1> X, Y, Z;
+        axis_weights<R, 1>(p, d, m, a, 0, X);
+        axis_weights<R, 1>(p, d, m, a, 1, Y);
+        axis_weights<R, 1>(p, d, m, a, 2, Z);
+        int gx;
+        R wx[2];
+        line_weight<R, 1>(X, sub, gx, wx);
+        R v1 = R(0), v2 = R(0), v3 = R(0);
+#pragma unroll
+        for (int jy = 0; jy < ORDER; ++jy) {
+            const R *row = d.grid + ((size_t)gx * p.K[1] + Y.g[jy]) * p.K[2];
+            R t0 = R(0), t1 = R(0);
+#pragma unroll
+            for (int k = 0; k < ORDER; ++k) {
+                const R g = row[Z.g[k]];
+                t0 += g * Z.w[0][k];
+                t1 += g * Z.w[1][k];
+            }
+            v1 += wx[1] * Y.w[0][jy] * t0;
+            v2 += wx[0] * Y.w[1][jy] * t0;
+            v3 += wx[0] * Y.w[0][jy] * t1;
+        }
+        E = mk(-v1 * S.ike, -v2 * S.ike, -v3 * S.ike);
+    } else if (live) {
         const R al = S.alpha;
         const R *v = d.vecR + m * 9;
-        V3<R> E;
-        if (lane == 25) {
+        if (sub == ORDER) {
             const R cself = R(4.0 / 3.0) * al * al * al * R(0.56418958354775628695);
             E = cself * mk(v[a * 3], v[a * 3 + 1], v[a * 3 + 2]);
         } else {
-            const int b = (a + lane - 25) % 3;   // the two atoms b != a
+            const int b = (a + sub - ORDER) % 3;   // the two atoms b != a
             const V3<R> xv = my_pt(d, m, a) - my_pt(d, m, b);
             R g[4];
             g_erf_s<R, 3>(dot(xv, xv), al, g);
@@ -526,18 +593,20 @@ __global__ void __launch_bounds__(32 * GW) k_gather_field(KParams p, DevState<R>
             source_field<R, 1>(s, xv, g, f);
             E = f.d1;
         }
-        vals[0] = E.x;
-        vals[1] = E.y;
-        vals[2] = E.z;
     }
-    const R s = warp_transpose_sum<R, 3>(vals, buf[w], lane);
-    if (lane < 3) out[m * 9 + a * 3 + lane] += (double)s;
+#pragma unroll
+    for (int o = PG / 2; o > 0; o >>= 1) {
+        E.x += __shfl_xor_sync(0xffffffffu, E.x, o);
+        E.y += __shfl_xor_sync(0xffffffffu, E.y, o);
+        E.z += __shfl_xor_sync(0xffffffffu, E.z, o);
+    }
+    if (live && sub < 3) out[m * 9 + a * 3 + sub] += (double)(sub == 0 ? E.x : (sub == 1 ? E.y : E.z));
 }
 
 template <typename R>
 void launch_gather_field(const KParams &p, DevState<R> &d, double *out, Launch L) {
-    const int n = p.M * 3;
-    k_gather_field<R><<<(n + GW - 1) / GW, 32 * GW, 0, L.s>>>(p, d, out);
+    const long long threads = (long long)p.M * 3 * PG;
+    k_gather_field<R><<<(unsigned)((threads + 255) / 256), 256, 0, L.s>>>(p, d, out);
     count(L);
 }
 
@@ -546,48 +615,50 @@ void launch_gather_field(const KParams &p, DevState<R> &d, double *out, Launch L
 // both potentials.  O/H1/H2: gradient of the induced dipole in the induced
 // (grid 0) and permanent (stored Hessian) reciprocal potentials.
 template <typename R>
-__global__ void __launch_bounds__(32 * GW) k_gather_polforce(KParams p, DevState<R> d) {
-    __shared__ R buf[GW][ND_VALS * 33];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * GW + w;
-    if (t >= p.M * NS) return;
-    const int m = t / NS, pt = t % NS;
+__global__ void __launch_bounds__(256, 2) k_gather_polforce(KParams p, DevState<R> d) {
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = gt / PG, sub = gt % PG;
+    const bool live = t < p.M * NS;
+    const int m = live ? t / NS : 0, pt = live ? t % NS : 0;
     const size_t ng = (size_t)p.K[0] * p.K[1] * p.K[2];
     Derivs<R> A, B;
-    warp_gather<R, 3>(p, d, d.grid, m, pt, lane, buf[w], A);
-    warp_gather<R, 3>(p, d, d.grid + ng, m, pt, lane, buf[w], B);
+    group_gather<R, 3>(p, d, d.grid, m, pt, sub, live, A);
+    group_gather<R, 3>(p, d, d.grid + ng, m, pt, sub, live, B);
+    if (!live) return;
     Derivs<R> S;
     S.phi = A.phi + B.phi;
     for (int k = 0; k < 3; ++k) S.d1[k] = A.d1[k] + B.d1[k];
     for (int k = 0; k < 6; ++k) S.d2[k] = A.d2[k] + B.d2[k];
     for (int k = 0; k < 10; ++k) S.d3[k] = A.d3[k] + B.d3[k];
     const Mp<R> mp = load_mp(d.gmp + (m * NS + pt) * GMP);
-    if (lane < 3) {
-        double g = (double)mp_grad(mp, S, lane);
-        if (pt < 3) {
-            // induced dipole in the induced (grid 0) and permanent (stored Hessian) potentials
-            const double *mu = d.mu + m * 9 + pt * 3;
-            const double *h = d.d2rec + m * 18 + pt * 6;
-            for (int b = 0; b < 3; ++b) g += ((double)sym_at(A.d2, lane, b) + sym_at(h, lane, b)) * mu[b];
+    for (int o = sub; o < 19; o += PG) {
+        if (o < 3) {
+            double g = (double)mp_grad(mp, S, o);
+            if (pt < 3) {
+                // induced dipole in the induced (grid 0) and permanent (stored Hessian) potentials
+                const double *mu = d.mu + m * 9 + pt * 3;
+                const double *h = d.d2rec + m * 18 + pt * 6;
+                for (int b = 0; b < 3; ++b) g += ((double)sym_at(A.d2, o, b) + sym_at(h, o, b)) * mu[b];
+            }
+            d.gpt[(m * NP + pt) * 3 + o] += g;
+            d.gmu[(m * NS + pt) * 3 + o] += (double)S.d1[o];
+        } else if (o < 9) {
+            d.gth[(m * NS + pt) * 6 + o - 3] += (double)S.d2[o - 3] / 3.0;
+        } else if (p.vir && o >= 10) {
+            // permanent multipoles in the induced + lambda potential; induced
+            // dipole in the permanent + induced potential
+            const int k = o - 10, a = k / 3, b = k % 3;
+            double c = (double)mp_strain(mp, S, k);
+            if (pt < 3) c += ((double)d.vphi[m * 9 + pt * 3 + a] + (double)A.d1[a]) * d.mu[m * 9 + pt * 3 + b];
+            atomicAdd(&d.vir[m * 9 + k], -c);
         }
-        d.gpt[(m * NP + pt) * 3 + lane] += g;
-        d.gmu[(m * NS + pt) * 3 + lane] += (double)S.d1[lane];
-    } else if (lane < 9) {
-        d.gth[(m * NS + pt) * 6 + lane - 3] += (double)S.d2[lane - 3] / 3.0;
-    } else if (p.vir && lane >= 10 && lane < 19) {
-        // permanent multipoles in the induced + lambda potential; induced
-        // dipole in the permanent + induced potential
-        const int k = lane - 10, a = k / 3, b = k % 3;
-        double c = (double)mp_strain(mp, S, k);
-        if (pt < 3) c += ((double)d.vphi[m * 9 + pt * 3 + a] + (double)A.d1[a]) * d.mu[m * 9 + pt * 3 + b];
-        atomicAdd(&d.vir[m * 9 + k], -c);
     }
 }
 
 template <typename R>
 void launch_gather_polforce(const KParams &p, DevState<R> &d, Launch L) {
-    const int n = p.M * NS;
-    k_gather_polforce<R><<<(n + GW - 1) / GW, 32 * GW, 0, L.s>>>(p, d);
+    const long long threads = (long long)p.M * NS * PG;
+    k_gather_polforce<R><<<(unsigned)((threads + 255) / 256), 256, 0, L.s>>>(p, d);
     count(L);
 }
 

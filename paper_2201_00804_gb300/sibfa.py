@@ -339,8 +339,10 @@ def sibfa_tuned_shape(ctx):
     return b.value, bool(dn.value)
 
 
-def sibfa_set_profiling(ctx, on: bool):
-    load_library().sibfa_set_profiling(ctx, 1 if on else 0)
+def sibfa_set_profiling(ctx, on):
+    """on: False/0 off, True/1 phase spans with the usual stream overlap,
+    2 serial (every phase alone on the GPU)."""
+    load_library().sibfa_set_profiling(ctx, int(on))
 
 
 def sibfa_profile_get(ctx, name: str):
