@@ -73,11 +73,17 @@ def parse():
                     help="PCG initial guess along the trajectory: 1 previous dipoles, 2-4 extrapolation through "
                          "the last 2-4 steps' dipoles")
     ap.add_argument("--workload", default="water32000",
-                    choices=["water4096", "water32000", "water216_paper", "clusters4096", "served"])
+                    choices=["water216", "water4096", "water32000", "water216_paper", "clusters4096", "served"])
     ap.add_argument("--equil-steps", type=int, default=600,
                     help="untimed velocity-rescaled MD steps (300 K) after the relaxation, before the NVE steps")
     ap.add_argument("--rates", default="20,50,100", help="served: arrival rates (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="served: arrival window per rate (s)")
+    ap.add_argument("--npt-steps", type=int, default=2000,
+                    help="water216_paper: untimed constant-pressure steps after the timed ones (0: none)")
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="reference arm: host threads for the oracle (0: PyTorch's default, all cores)")
+    ap.add_argument("--served-fp64", action="store_true",
+                    help="served: also run the same mix through the FP64 path at the highest rate")
     return ap.parse_args()
 
 
@@ -331,16 +337,23 @@ def sample_system():
     return s, {"rc": 9.0, "grid": 32, "order": 5, "ewald": 0.4}
 
 
-def cpu_baseline(steps=1):
+def cpu_baseline(steps=1, workload=None):
+    """The oracle on the host cores: the whole 216-water box (one evaluation
+    at its PCG tolerance), else the 512-water sample of the large boxes."""
     import torch
     import oracle
-    s, o = sample_system()
+    if workload == "water216":
+        import synth
+        s, o = synth.make_config("water216")
+        tol, sample = o["pcg_tol"], "the whole 216-water box; one full energy + force evaluation per step"
+    else:
+        (s, o), tol, sample = sample_system(), 1e-6, SAMPLE
     t = time.perf_counter()
     for _ in range(steps):
-        oracle.evaluate(s, o, tol_D=1e-6)
+        oracle.evaluate(s, o, tol_D=tol)
     dt = time.perf_counter() - t
     return {"value": s.n_atoms * steps / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": SAMPLE, "seconds": dt}
+            "sample": sample, "seconds": dt}
 
 
 def run_reference(args, dist, rank, ws):
@@ -348,6 +361,8 @@ def run_reference(args, dist, rank, ws):
         return
     import torch
     import oracle
+    if args.cpu_threads > 0:
+        torch.set_num_threads(args.cpu_threads)
     s, o = sample_system()
     for _ in range(args.warmup):
         oracle.evaluate(s, o, tol_D=1e-6)
@@ -379,6 +394,8 @@ WORKLOADS = {
     "water32000": ("water32000: 32,000 rigid-geometry waters (96,000 atoms; 32^3 lattice, 768 seeded removals), cubic "
                    "box 98.6 A, rc 9 A, SPME 108^3 order 5, alpha 0.4/A, PCG 1e-6 D warm start, velocity-Verlet NVE "
                    "0.5 fs from 300 K"),
+    "water216": ("water216: 216 rigid-geometry waters (648 atoms), cubic box 18.62 A, rc 7 A, SPME 24^3 order 5, "
+                 "alpha 0.4/A, PCG 1e-8 D warm start, velocity-Verlet NVE 0.5 fs from 300 K"),
     "water216_paper": ("water216_paper: the paper's MD setting, 216 waters (648 atoms) in an 18.643 A box, SPME "
                        "120^3 order 5, Ewald and repulsion cutoff 7 A with the dispersion beyond it as a "
                        "homogeneous-fluid tail, PCG 1e-5 D warm start, Beeman NVE at 1 fs with MM3-style anharmonic "
@@ -397,7 +414,7 @@ GUESS = {1: "previous step's dipoles", 2: "linear extrapolation of the last 2 st
 def setup(name, pkg, synth, precision, stream, warm=1):
     """Context, device arrays and unit counts of a workload."""
     import torch
-    if name in ("water4096", "water32000", "water216_paper"):
+    if name in ("water216", "water4096", "water32000", "water216_paper"):
         s, o = synth.make_config(name)
         extra = dict(PAPER_MD) if name == "water216_paper" else {}
         ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
@@ -406,7 +423,7 @@ def setup(name, pkg, synth, precision, stream, warm=1):
         make_api = lambda: pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"],  # noqa: E731
                                             grid=o["grid"], ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"],
                                             precision=precision, warm_start=warm, stream=stream, **extra)
-        seed = {"water4096": 2, "water32000": 3, "water216_paper": 1}[name]
+        seed = {"water216": 1, "water4096": 2, "water32000": 3, "water216_paper": 1}[name]
     else:
         s, start, _ = synth.make_cluster_batch(4096, seed=4)
         o = {"rc": None, "cluster_start": start}
@@ -431,14 +448,18 @@ def kinetic(vel, masses3):
     return 0.5 * float((masses3 * vel * vel).sum()) / AMU_A2_FS2
 
 
-def intra_energy(pos, k_bond=529.6, r0=0.9572, k_angle=34.05, theta0_deg=104.52, md_anharmonic=False, md_k_ub=0.0,
-                 md_r_ub=1.5326, **_):
+def intra_energy(pos, **support):
+    return float(intra_energy_t(pos, **support))
+
+
+def intra_energy_t(pos, k_bond=529.6, r0=0.9572, k_angle=34.05, theta0_deg=104.52, md_anharmonic=False,
+                   md_k_ub=0.0, md_r_ub=1.5326, **_):
     """The MD driver's intramolecular support potential (kcal/mol) at device
     positions, as the run options define it: k_bond dr^2 per O-H bond and
     k_angle dth^2 per H-O-H angle, with the MM3-style anharmonic factors and
     the Urey-Bradley H-H term when asked."""
     import torch
-    x = pos.view(-1, 3, 3)
+    x = pos.reshape(-1, 3, 3)
     b1, b2 = x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]
     r1, r2 = b1.norm(dim=-1), b2.norm(dim=-1)
     dth = torch.acos(((b1 * b2).sum(-1) / (r1 * r2)).clamp(-1.0, 1.0)) - math.radians(theta0_deg)
@@ -452,7 +473,52 @@ def intra_energy(pos, k_bond=529.6, r0=0.9572, k_angle=34.05, theta0_deg=104.52,
     e = bond(r1 - r0) + bond(r2 - r0) + ang
     if md_k_ub > 0:
         e = e + md_k_ub * ((x[:, 1] - x[:, 2]).norm(dim=-1) - md_r_ub) ** 2
-    return float(e.sum())
+    return e.sum()
+
+
+BAR_PER_KCAL_MOL_A3 = 69476.95    # 1 kcal/mol/A^3 in bar
+
+
+def intra_virial(pos, **support):
+    """W_ab = -dE/d eps_ab of the support potential under x -> (I + eps) x."""
+    import torch
+    eps = torch.zeros((3, 3), dtype=torch.float64, device=pos.device, requires_grad=True)
+    x = pos.detach().reshape(-1, 3) @ (torch.eye(3, dtype=torch.float64, device=pos.device) + eps).T
+    g, = torch.autograd.grad(intra_energy_t(x, **support), [eps])
+    return -g.cpu().numpy()
+
+
+def berendsen_npt(pkg, ctx, pos, vel, masses, box, n_steps, every=10, dt_fs=1.0, p_bar=1.0, tau_ps=1.0,
+                  kappa_per_bar=4.5e-5, support=None):
+    """Constant pressure by Berendsen's weak coupling: MD steps in chunks of
+    `every`; after each chunk the pressure P = (2 K + tr W) / (3 V) from the
+    kinetic energy, the library's virial (with the dispersion tail) and the
+    support potential's virial, then all atoms and the box scaled by
+    mu = [1 - kappa (every dt / tau) (p_bar - P)]^(1/3) (clamped to 1 +/- 1%);
+    the scaled box reaches the context through a dipole solve at the scaled
+    positions before the next chunk.  Returns the box, the volumes and the
+    pressures after each chunk."""
+    import torch
+    support = support or {}
+    m3 = masses.repeat_interleave(3)
+    box = np.asarray(box, dtype=np.float64).copy()
+    F = torch.zeros_like(pos)
+    vols, press = [], []
+    for _ in range(n_steps // every):
+        pkg.sibfa_md_steps(ctx, pos, vel, masses, dt_fs, every)
+        W = np.zeros((3, 3))
+        pkg.sibfa_energy_forces(ctx, pos, F, box=box, virial=W)
+        W = W + intra_virial(pos, **support)
+        V = float(np.prod(box))
+        P = (2.0 * kinetic(vel, m3) + np.trace(W)) / (3.0 * V) * BAR_PER_KCAL_MOL_A3
+        mu = (1.0 - kappa_per_bar * (every * dt_fs * 1e-3 / tau_ps) * (p_bar - P)) ** (1.0 / 3.0)
+        mu = min(1.01, max(0.99, mu))
+        box *= mu
+        pos.mul_(mu)
+        pkg.sibfa_solve_dipoles(ctx, pos, None, 0.0, box=box)
+        vols.append(float(np.prod(box)))
+        press.append(P)
+    return {"box": box, "volumes": vols, "pressure_bar": np.array(press)}
 
 
 def equilibrate(pkg, ctx, pos, vel, masses, n_min=20, n_thermo=200, temp=300.0, every=5, dt_fs=0.5):
@@ -537,18 +603,22 @@ def served_pool(synth, rng):
     return clusters, boxes
 
 
-def run_served(args, pkg, synth):
+def run_served(args, pkg, synth, precision=None, rates=None):
     """Poisson arrivals at each rate for a fixed window; 70% clusters, 30%
-    boxes, 1-50 MD steps per job; latency = completion - arrival."""
+    boxes, 1-50 MD steps per job; latency = completion - arrival.  A rate the
+    server cannot keep up with is drained for at most 20 s after the window;
+    jobs still running then are reported as unfinished and their work is not
+    counted."""
     import torch
     rng = np.random.default_rng(5)
     clusters, boxes = served_pool(synth, rng)
     vel_c = [synth.maxwell_velocities(c, 300.0, seed=k) for k, c in enumerate(clusters)]
     vel_b = [synth.maxwell_velocities(b[0], 300.0, seed=k) for k, b in enumerate(boxes)]
     out = []
-    for rate in [float(r) for r in args.rates.split(",")]:
+    precision = pkg.PREC_MIXED if precision is None else precision
+    for rate in rates or [float(r) for r in args.rates.split(",")]:
         srv = pkg.Server(synth.PARAMS, slots=3, device_mem_bytes=64 << 30, max_pending=100000, batch_waters=16384,
-                         precision=pkg.PREC_MIXED, pcg_tol_D=1e-6)
+                         precision=precision, pcg_tol_D=1e-6)
         # warm the server: one job of every box shape and one cluster, untimed
         warm = [srv.submit(b[0].pos, b[0].mp_local, periodic=True, box=b[0].box, rc=b[1]["rc"], grid=b[1]["grid"],
                            ewald_alpha=b[1]["ewald"], n_steps=1) for b in boxes]
@@ -565,7 +635,7 @@ def run_served(args, pkg, synth):
         t0 = time.perf_counter()
         live, lat, atom_steps, busy, nxt = {}, [], 0, 0, 0
         last_done = t0
-        deadline = args.serve_seconds + 180.0    # a stream that cannot drain is reported, not waited for
+        deadline = args.serve_seconds + 20.0     # a stream that cannot drain is reported, not waited for
         while (nxt < arrivals.size or live) and time.perf_counter() - t0 < deadline:
             now = time.perf_counter() - t0
             while nxt < arrivals.size and arrivals[nxt] <= now:
@@ -598,7 +668,8 @@ def run_served(args, pkg, synth):
         wall = last_done - t0
         srv.close()
         lat = np.array(lat)
-        out.append({"rate_per_s": rate, "jobs": int(lat.size), "busy_refused": busy, "unfinished": len(live),
+        out.append({"rate_per_s": rate, "precision": "fp64" if precision == pkg.PREC_FP64 else "mixed",
+                    "jobs": int(lat.size), "busy_refused": busy, "unfinished": len(live),
                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                     "atom_steps_per_s": atom_steps / wall, "wall_s": wall})
         print(json.dumps({"served_rate": out[-1]}), file=sys.stderr, flush=True)
@@ -618,6 +689,9 @@ def main():
         from paper_2201_00804_gb300 import build
         build.build()
         res = run_served(args, pkg, synth)
+        # the same mix through the plain FP64 path, at the highest rate (saturated)
+        res64 = run_served(args, pkg, synth, precision=pkg.PREC_FP64,
+                           rates=[max(float(r) for r in args.rates.split(","))]) if args.served_fp64 else None
         best = max(res, key=lambda r: r["atom_steps_per_s"])
         line = {"metric": METRIC, "value": best["atom_steps_per_s"], "unit": UNIT, "n_gpus": 1,
                 "steps": int(sum(r["jobs"] for r in res)), "warmup": 1, "higher_is_better": True, "scaling": "weak",
@@ -626,7 +700,7 @@ def main():
                                        "periodic boxes (216-8192 waters, 1.3 grid points/A), 1-50 velocity-Verlet "
                                        "steps per job, mixed precision, PCG 1e-6 D",
                            "window_s_per_rate": args.serve_seconds},
-                "served": res}
+                "served": res, "served_fp64_path": res64}
         print(json.dumps(line), flush=True)
         return
     import torch
@@ -689,7 +763,7 @@ def main():
     # serial event time, against the measured HBM copy bandwidth.
     P = synth.PARAMS
     pos_h = pos.cpu().numpy().reshape(M, 3, 3)
-    if args.workload in ("water4096", "water32000", "water216_paper"):
+    if args.workload in ("water216", "water4096", "water32000", "water216_paper"):
         units = count_units(pos_h, s.box, o["rc"], points_from_pos(pos_h, P))
     else:
         units = count_units_clusters(o["cluster_start"], M)
@@ -755,6 +829,21 @@ def main():
     e2e = {"value": ws * 3 * M * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(pos_host.nbytes),
            "d2h_bytes_per_step": int(F_host.nbytes + 8 * 8 + 4)}
     pkg.sibfa_destroy(api)
+    # The paper's setting runs at constant pressure: an untimed Berendsen
+    # stretch (1 bar, tau 1 ps, water's compressibility, pressure every 10
+    # steps) after the timed steps, reported as the density it reaches.
+    npt = None
+    if args.workload == "water216_paper" and args.npt_steps > 0:
+        out = berendsen_npt(pkg, ctx, pos, vel, masses, s.box, n_steps=args.npt_steps, every=10, dt_fs=dt,
+                            support=support)
+        vols, pr = np.array(out["volumes"]), out["pressure_bar"]
+        grams = M * 18.01528 / 0.602214076          # g per mol of waters / (A^3 -> cm^3 * N_A)
+        half = len(vols) // 2
+        npt = {"steps": args.npt_steps, "barostat": "Berendsen, 1 bar, tau 1 ps, kappa 4.5e-5/bar, every 10 steps",
+               "density_start_g_cm3": grams / float(np.prod(s.box)), "density_end_g_cm3": grams / vols[-1],
+               "density_mean_second_half_g_cm3": float(np.mean(grams / vols[half:])),
+               "pressure_mean_second_half_bar": float(np.mean(pr[half:])),
+               "box_end_A": [float(b) for b in out["box"]]}
     pkg.sibfa_destroy(ctx)
 
     # The plain FP64 GPU path on the same workload and starting state (the
@@ -777,8 +866,8 @@ def main():
     if rank != 0:
         return
     cpu = None
-    if ws == 1 and not args.no_cpu_baseline and args.workload in ("water4096", "water32000"):
-        cpu = cpu_baseline()
+    if ws == 1 and not args.no_cpu_baseline and args.workload in ("water216", "water4096", "water32000"):
+        cpu = cpu_baseline(workload=args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -795,7 +884,7 @@ def main():
                 "total_energy_first": etot[0], "total_energy_last": etot[-1],
                 "drift_kcal_per_mol_atom_per_ps": (etot[-1] - etot[0]) / (3 * M) / (dt * 1e-3 * max(1, len(etot) - 1)),
                 "temperature_end_K": 2.0 * kinetic(vel, masses.repeat_interleave(3)) / ((vel.numel() - 3) * KB_KCAL)},
-        "tuned": {"short_blocks_per_sm": tb, "fixed": tdone},
+        "tuned": {"short_blocks_per_sm": tb, "fixed": tdone}, "npt": npt,
     }
     print(json.dumps(line), flush=True)
 

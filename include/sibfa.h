@@ -177,7 +177,15 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
                           const sibfa_run_opts *opts, sibfa_ctx **out);
 
 /* One energy + force evaluation.  pos: n_mol*9 doubles (O, H1, H2 xyz per
- * molecule, Angstrom).  box: 3 doubles or NULL to keep the current box.
+ * molecule, Angstrom).  box: 3 doubles (host) or NULL to keep the current
+ * box.  A box that differs from the context's current one changes it, for
+ * this and every later call (constant-pressure MD; periodic contexts only,
+ * SIBFA_E_INVALID for a gas-phase context): the influence function is
+ * recomputed, the neighbour list rebuilt and the dispersion tail rescaled.
+ * Returns SIBFA_E_INVALID for a non-positive edge or when the new box needs
+ * more cells than the context allocated at create (a box much larger than
+ * the first), SIBFA_E_CUTOFF when rc + 2 * O-H distance exceeds half the
+ * new box; the box is then unchanged.
  * e: host struct, filled on success (may be NULL).  forces: n_mol*9 doubles
  * (kcal/mol/A, = -dE/dx) or NULL.  virial: 9 host doubles (row-major 3x3,
  * kcal/mol) or NULL: W_ab = -dE/d eps_ab for the affine strain x -> (I + eps) x

@@ -150,29 +150,54 @@ def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=20
             V = V + tm.lp_potential_periodic(S2, P, st.alpha, ew.convolve(Qp, st.G), st.box, st.K, st.order)
         return V
 
+    # the original many-body charge transfer (opts["ct_original"]) also
+    # needs the potential at the acceptor atoms O, H1, H2
+    ct_orig = bool(opts.get("ct_original"))
+
+    def atom_potential(xx):
+        S = build_sites(xx, st.mp, P)
+        V = torch.zeros((M, 3), dtype=DT)
+        for i, j, sh in st.chunks(chunk):
+            V = V + tm.atom_potential_pairs(S, i, j, sh, P, st.rc, st.alpha)
+        if st.periodic:
+            Qp = ew.spread(S["x"].reshape(-1, 3), S["q"].reshape(-1), S["mu"].reshape(-1, 3),
+                           S["th"].reshape(-1, 3, 3), st.box, st.K, st.order)
+            V = V + tm.atom_potential_periodic(S, P, st.alpha, ew.convolve(Qp, st.G), st.box, st.K, st.order)
+        return V
+
     with torch.no_grad():
         V_lp = lp_potential(x.detach())
+        V_at = atom_potential(x.detach()) if ct_orig else None
     Vleaf = V_lp.clone().requires_grad_(True)
+    leaves = [Vleaf]
+    if ct_orig:
+        Valeaf = V_at.clone().requires_grad_(True)
+        leaves.append(Valeaf)
     e_ct = 0.0
     min_de = math.inf
     lam = torch.zeros_like(V_lp)
+    lam_a = torch.zeros_like(V_at) if ct_orig else None
     for i, j, sh in st.chunks(chunk):
         S = build_sites(x, st.mp, P)
         Vint = tm.v_int(S, P)
-        e, mde = tm.ct_pairs(S, Vleaf, Vint, i, j, sh, P, st.rc)
+        if ct_orig:
+            e, mde = tm.ct_pairs_original(S, Vleaf, Valeaf, Vint, i, j, sh, P, st.rc)
+        else:
+            e, mde = tm.ct_pairs(S, Vleaf, Vint, i, j, sh, P, st.rc)
         min_de = min(min_de, mde)
         e_ct += float(e.detach())
         if e.requires_grad:
+            g = torch.autograd.grad(e, ([wrt] if forces else []) + leaves, allow_unused=True, retain_graph=virial)
             if forces:
-                gx, gv = torch.autograd.grad(e, [wrt, Vleaf], allow_unused=True, retain_graph=virial)
+                gx, g = g[0], g[1:]
                 if gx is not None:
                     F.sub_(gx)
                     if FT is not None:
                         FT["ct"].sub_(gx)
-            else:
-                gv, = torch.autograd.grad(e, [Vleaf], allow_unused=True, retain_graph=virial)
-            if gv is not None:
-                lam += gv
+            if g[0] is not None:
+                lam += g[0]
+            if ct_orig and g[1] is not None:
+                lam_a += g[1]
     E["ct"] = e_ct
     if forces and float(lam.abs().sum()) > 0:
         # d/dx of sum lam . V_lp(x), one chunk of pairs at a time (the
@@ -186,6 +211,18 @@ def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=20
                            S["th"].reshape(-1, 3, 3), st.box, st.K, st.order)
             add_grad((lamd * tm.lp_potential_periodic(S, P, st.alpha, ew.convolve(Qp, st.G), st.box, st.K,
                                                       st.order)).sum(), "ct", retain=True)
+        del S
+    if forces and ct_orig and float(lam_a.abs().sum()) > 0:
+        # the same for sum lam_a . V(a)(x) over the acceptor atoms
+        lamd = lam_a.detach()
+        S = build_sites(x, st.mp, P)
+        for i, j, sh in st.chunks(chunk):
+            add_grad((lamd * tm.atom_potential_pairs(S, i, j, sh, P, st.rc, st.alpha)).sum(), "ct", retain=True)
+        if st.periodic:
+            Qp = ew.spread(S["x"].reshape(-1, 3), S["q"].reshape(-1), S["mu"].reshape(-1, 3),
+                           S["th"].reshape(-1, 3, 3), st.box, st.K, st.order)
+            add_grad((lamd * tm.atom_potential_periodic(S, P, st.alpha, ew.convolve(Qp, st.G), st.box, st.K,
+                                                        st.order)).sum(), "ct", retain=True)
         del S
 
     # ---- polarization ---------------------------------------------------------
@@ -277,6 +314,7 @@ def evaluate(system, opts=None, forces=True, tol_D=1e-10, max_iter=500, chunk=20
         "mu": mu.detach().numpy(),
         "efield": Efield.detach().numpy(),
         "v_lp": V_lp.detach().numpy(),
+        "v_atoms": V_at.detach().numpy() if ct_orig else None,
         "iters": it,
         "resid_D": res,
         "min_ct_denominator": min_de,

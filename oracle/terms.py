@@ -196,6 +196,45 @@ def lp_potential_periodic(S, P, alpha, Psi, box, K, order):
     return phi - P["ke"] * own
 
 
+def atom_potential_pairs(S, i, j, sh, P, rc, alpha):
+    """Real-space / gas-phase potential at O, H1, H2 from the permanent
+    multipoles of the other molecule of every pair, (M, 3): the acceptor
+    potentials V_a of the original charge transfer (CT section; same kernel
+    and per-site-pair cutoff as the lone-pair potential)."""
+    M = S["q"].shape[0]
+    A, B = _take(S, i), _take(S, j, sh)
+
+    def one(at, src):
+        r = at[:, :, None, :] - src["x"][:, None, :, :]
+        rn = _norm(r)
+        g = g_erfc(rn, alpha, 2) if alpha is not None else g_bare(rn, 2)
+        T = tensors(r, g, 2)
+        phi = mp_potential(T, src["q"][:, None, :], src["mu"][:, None, :, :], src["th"][:, None, :, :, :])
+        return (phi * _mask(rn, rc)).sum(-1) * P["ke"]
+
+    V = torch.zeros((M, 3), dtype=DT)
+    V = V.index_add(0, torch.as_tensor(i), one(A["x"][:, :3], B))
+    V = V.index_add(0, torch.as_tensor(j), one(B["x"][:, :3], A))
+    return V
+
+
+def atom_potential_periodic(S, P, alpha, Psi, box, K, order):
+    """Reciprocal potential at O, H1, H2 minus the own molecule's part: the erf
+    part of its other four sites and the Gaussian self potential of the atom's
+    own charge, 2 alpha / sqrt(pi) q (its own dipole and traceless quadrupole
+    have none at their centre)."""
+    M = S["q"].shape[0]
+    phi = ew.potential_derivs(S["x"][:, :3].reshape(-1, 3), Psi, box, K, order, 0)["phi"].reshape(M, 3)
+    out = []
+    for a in range(3):
+        others = [t for t in range(5) if t != a]
+        r = S["x"][:, a:a + 1, :] - S["x"][:, others, :]
+        T = tensors(r, g_erf(_norm(r), alpha, 2), 2)
+        own = mp_potential(T, S["q"][:, others], S["mu"][:, others], S["th"][:, others]).sum(-1)
+        out.append(own + 2.0 * alpha / math.sqrt(math.pi) * S["q"][:, a])
+    return phi - P["ke"] * torch.stack(out, -1)
+
+
 # ---------------------------------------------------------------------------
 # Charge transfer, reduced form (Eqs. 13-16)
 # ---------------------------------------------------------------------------
@@ -258,6 +297,59 @@ def ct_pairs(S, V, Vint, i, j, sh, P, rc):
     ia, ja = torch.as_tensor(i), torch.as_tensor(j)
     e_ab, d1 = direction(A, B, V[ia], Vint[ja])
     e_ba, d2 = direction(B, A, V[ja], Vint[ia])
+    min_de = min(float(d1.detach().min()) if d1.numel() else 1.0,
+                 float(d2.detach().min()) if d2.numel() else 1.0)
+    return e_ab + e_ba, min_de
+
+
+def ct_pairs_original(S, V, Vat, Vint, i, j, sh, P, rc):
+    """The original many-body charge transfer (CT section, before its
+    reduction): as ct_pairs, with the acceptor potentials kept,
+    e1 = exp(-eta rho1) (Vint(a1) + V*(a1) - V_l)(Cs t + Cp m cos alpha),
+    e2 = exp(-eta rho2) (Vint(a2) + V*(a2) - V_l)(Cs t + Cp m cos beta),
+    dE = ae + V_l - (ah + V(a1)),
+    where V(a) = Vat is the potential at acceptor atom a from every molecule
+    but its own, and V*(a) = V(a) minus the potential at a of the donor's
+    molecule (its five multipole sites, bare, at the pair's image)."""
+    n = P["n_lp"]
+    cs, cp = P["cs_lp"], P["cp_lp"]
+    t, mm = P["ct_t"], P["ct_m"]
+    eta = P["ct_eta"]
+    rvo, rvh = P["rvdw_ct_o"], P["rvdw_ct_h"]
+
+    def donor_potential(D, at):
+        """Bare potential of the donor's sites at the acceptor atoms (C, 3)."""
+        r = at[:, :, None, :] - D["x"][:, None, :, :]
+        T = tensors(r, g_bare(_norm(r), 2), 2)
+        return P["ke"] * mp_potential(T, D["q"][:, None, :], D["mu"][:, None, :, :],
+                                      D["th"][:, None, :, :, :]).sum(-1)
+
+    def direction(D, Ad, VD, VintA, VatA):
+        c = D["x"][:, 0]
+        lp = D["lp"]
+        a1 = Ad["x"][:, 0]
+        a2 = Ad["x"][:, 1:3]
+        r1 = _norm(a1 - c)
+        m = _mask(r1, rc)
+        rho1 = r1 / (2.0 * math.sqrt(rvo * rvo))
+        rho2 = _norm(a2 - c[:, None]) / (2.0 * math.sqrt(rvo * rvh))
+        u = lp - c[:, None]
+        cos_a = _cos(u, (a1 - c)[:, None, :])
+        cos_b = _cos(u[:, :, None, :], (a2 - c[:, None])[:, None, :, :])
+        Vl = VD[:, :, None]
+        Vs = VatA - donor_potential(D, Ad["x"][:, :3])       # V*(a) for O, H1, H2 of the acceptor
+        e1 = (torch.exp(-eta * rho1)[:, None, None] * (VintA[:, 0][:, None, None] + Vs[:, 0][:, None, None] - Vl)
+              * (cs * t + cp * mm * cos_a[:, :, None]))
+        e2 = (torch.exp(-eta * rho2)[:, None, :] * (VintA[:, 1:3][:, None, :] + Vs[:, None, 1:3] - Vl)
+              * (cs * t + cp * mm * cos_b))
+        dE = P["ct_ae"] + Vl - (P["ct_ah"] + VatA[:, 0][:, None, None])
+        e = -n * (e1 - e2) ** 2 / dE
+        return (e.sum((1, 2)) * m).sum(), dE
+
+    A, B = _take(S, i), _take(S, j, sh)
+    ia, ja = torch.as_tensor(i), torch.as_tensor(j)
+    e_ab, d1 = direction(A, B, V[ia], Vint[ja], Vat[ja])
+    e_ba, d2 = direction(B, A, V[ja], Vint[ia], Vat[ia])
     min_de = min(float(d1.detach().min()) if d1.numel() else 1.0,
                  float(d2.detach().min()) if d2.numel() else 1.0)
     return e_ab + e_ba, min_de

@@ -68,6 +68,7 @@ struct sibfa_ctx {
     cufftHandle r2c1 = 0, c2r1 = 0, r2c2 = 0, c2r2 = 0;
     bool have_fft = false;
     int ncell[3] = {0, 0, 0};
+    int ncell_cap = 0;            // cells the cell-list arrays hold (set at create)
     double *d_forces = nullptr;   // M*9
     double *d_energy = nullptr;   // NTERM+1 energies; [16, 25) the virial
     double *d_vel = nullptr, *d_invm = nullptr;
@@ -189,6 +190,7 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.cl_rr, M);
     AL(d.cl_energy, (size_t)M * (NTERM + 1));
     int ncell = std::max(1, ctx->ncell[0] * ctx->ncell[1] * ctx->ncell[2]);
+    ctx->ncell_cap = ncell;
     AL(d.cell_of, M);
     AL(d.cell_start, ncell + 1);
     AL(d.cell_cursor, ncell);
@@ -822,21 +824,73 @@ sibfa_status check_flags(sibfa_ctx *ctx, int flags) {
     return SIBFA_OK;
 }
 
+// A new orthorhombic box for a periodic context (constant-pressure MD):
+// the box-dependent parameters (box, inverse box, fixed-point scale, SPME
+// grid points per length), the influence function, the cell grid (within
+// the cells allocated at create), the dispersion tail (proportional to
+// 1/V), a neighbour-list rebuild at the next evaluation, and the captured
+// solve loop (its kernels hold the parameters by value) rebuilt on first
+// use.  Called on the work stream after enter().
+template <typename R>
+sibfa_status set_box(sibfa_ctx *ctx, DevState<R> &d, const double *box) {
+    for (int k = 0; k < 3; ++k)
+        if (!(box[k] > 0)) {
+            ctx->err = "box lengths must be > 0";
+            return SIBFA_E_INVALID;
+        }
+    const double half = 0.5 * std::min(box[0], std::min(box[1], box[2]));
+    if (ctx->opts.rc + 2.0 * 0.9572 > half) {
+        ctx->err = "rc + 2 * O-H distance exceeds half the new box";
+        return SIBFA_E_CUTOFF;
+    }
+    const double cell = ctx->opts.rc + 2.6 + LIST_SKIN;
+    int nc[3];
+    for (int k = 0; k < 3; ++k) nc[k] = (int)floor(box[k] / cell);
+    if (nc[0] >= 3 && nc[1] >= 3 && nc[2] >= 3 && nc[0] * nc[1] * nc[2] > ctx->ncell_cap) {
+        ctx->err = "the new box needs more cells than the context allocated at create";
+        return SIBFA_E_INVALID;
+    }
+    const double v_old = ctx->kp.box[0] * ctx->kp.box[1] * ctx->kp.box[2];
+    KParams &k = ctx->kp;
+    for (int i = 0; i < 3; ++i) {
+        ctx->opts.box[i] = box[i];
+        k.box[i] = box[i];
+        k.ibox[i] = 1.0 / box[i];
+        k.fxs[i] = (float)(box[i] / 4294967296.0);
+        ctx->ncell[i] = nc[i];
+    }
+    fill_scal(k.sd, k);
+    fill_scal(k.sf, k);
+    ctx->e_tail *= v_old / (box[0] * box[1] * box[2]);
+    Launch L{ctx->s, &ctx->launches};
+    launch_influence(k, d.infl, L);
+    launch_influence_copy(k, d, L);
+    CK(cudaMemsetAsync(d.lflag + 1, 0, sizeof(int), ctx->s));   // no list yet: rebuild
+    if (ctx->pcg_graph_state == 1) {
+        cudaGraphExecDestroy(ctx->pcg_exec);
+        ctx->pcg_exec = nullptr;
+        ctx->pcg_graph_state = 0;
+    }
+    return SIBFA_OK;
+}
+
 template <typename R>
 sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_energy_terms *e, double *forces,
                  bool dipoles_only, double tol, double *mu_out, int *iters, double *resid, double *virial = nullptr) {
     DevState<R> &d = state<R>(ctx);
     const int M = ctx->M;
     const size_t nb = (size_t)M * 9 * sizeof(double);
+    bool new_box = false;
     if (box) {
-        for (int k = 0; k < 3; ++k)
-            if (box[k] != ctx->kp.box[k]) {
-                ctx->err = "changing the box after create is not supported";
-                return SIBFA_E_INVALID;
-            }
+        for (int k = 0; k < 3; ++k) new_box = new_box || box[k] != ctx->kp.box[k];
+        if (new_box && !ctx->opts.periodic) {
+            ctx->err = "a gas-phase context has no box";
+            return SIBFA_E_INVALID;
+        }
     }
     sibfa_status st0 = enter(ctx);
     if (st0) return st0;
+    if (new_box && (st0 = set_box<R>(ctx, d, box))) return leave(ctx) ? SIBFA_E_CUDA : st0;
     CK(cudaMemsetAsync(d.flags, 0, sizeof(int), ctx->s));
     if (pos) {
         if (is_device_ptr(pos)) {

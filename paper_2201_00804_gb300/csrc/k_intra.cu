@@ -161,61 +161,37 @@ __global__ void __launch_bounds__(128) k_intra_perm(KParams p, DevState<R> d) {
     if (p.vir) vir_warp_out(d, m, W, ke, lane);
 }
 
-// Global multipole and offset from O of site s of molecule m, in FP64 from
-// the FP64 positions and local multipoles (frames as in the site kernel).
-__device__ inline void site64(const double *x, const double *ml, int s, Mp<double> &M, V3<double> &off) {
-    const V3<double> r1 = mk(x[3] - x[0], x[4] - x[1], x[5] - x[2]);
-    const V3<double> r2 = mk(x[6] - x[0], x[7] - x[1], x[8] - x[2]);
-    const double s1 = rsqrt(dot(r1, r1)), s2 = rsqrt(dot(r2, r2));
-    V3<double> zv, xv, ex, ey, ez;
-    frame_generators(site_frame(s), r1, r2, s1, s2, zv, xv);
-    frame_axes(zv, xv, ex, ey, ez);
-    const V3<double> so[NS] = {mk(0.0, 0.0, 0.0), r1, r2, 0.5 * r1, 0.5 * r2};
-    off = so[s];
-    const double *l = ml + s * NMP;
-    M.q = l[0];
-    M.mu = l[1] * ex + l[2] * ey + l[3] * ez;
-    const double tl[3][3] = {{l[4], l[7], l[8]}, {l[7], l[5], l[9]}, {l[8], l[9], l[6]}};
-    const V3<double> e[3] = {ex, ey, ez};
-    double T[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-            const V3<double> A = tl[a][b] * e[b];
-            const double ea[3] = {e[a].x, e[a].y, e[a].z}, Ab[3] = {A.x, A.y, A.z};
-            for (int u = 0; u < 3; ++u)
-                for (int v = 0; v < 3; ++v) T[u][v] += ea[u] * Ab[v];
-        }
-    M.th.xx = T[0][0]; M.th.yy = T[1][1]; M.th.zz = T[2][2];
-    M.th.xy = T[0][1]; M.th.xz = T[0][2]; M.th.yz = T[1][2];
-}
-
 // Mixed path: the intramolecular Ewald energy (erf part of the 10 site pairs
 // of each molecule and the five Gaussian self terms) in FP64.  These terms
 // are ~50 kcal/mol per molecule and cancel against the reciprocal sum; the
 // same geometry repeats in every rigid molecule, so FP32 rounding of them
 // adds up coherently over the box (about 1e-6 of the total energy at a few
-// hundred waters).  Sixteen lanes per molecule: lanes 0-4 build the global
-// multipoles and offsets of the five sites into shared memory, then lanes
-// 0-9 take the pairs and lanes 10-14 the self terms.  It reads only the
-// positions and local multipoles, so it runs on the lowest-priority stream
-// beside the other kernels, and writes its own per-molecule array.
+// hundred waters).  The multipoles are the working-precision global ones the
+// reciprocal grid was spread from (converted exactly to FP64), the site
+// offsets FP64 differences of the positions; the radial kernels, products
+// and sums are FP64 (the FP64 pipe bounds this kernel).  Sixteen lanes per
+// molecule: lanes 0-4 stage the five sites in shared memory, then lanes 0-9
+// take the pairs and lanes 10-14 the self terms.  It reads only positions
+// and multipoles, so it runs on the lowest-priority stream beside the other
+// kernels, and writes its own per-molecule array.
 constexpr int IE_MOL = 8;   // molecules per 128-thread block
-__global__ void __launch_bounds__(128) k_intra_energy64(KParams p, const double *pos, const double *mp_local,
-                                                        double *eintra) {
+template <typename R>
+__global__ void __launch_bounds__(128) k_intra_energy64(KParams p, const double *pos, const R *gmp, double *eintra) {
     __shared__ double sq[IE_MOL][NS], smu[IE_MOL][NS][3], sth[IE_MOL][NS][6], soff[IE_MOL][NS][3];
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int lm = threadIdx.x >> 4, m = g >> 4, t = g & 15;
     const bool live = m < p.M;
     const double al = p.alpha, spi = 0.56418958354775628695;
     if (live && t < NS) {
-        Mp<double> M;
-        V3<double> o;
-        site64(pos + m * 9, mp_local + m * NS * NMP, t, M, o);
-        sq[lm][t] = M.q;
-        smu[lm][t][0] = M.mu.x; smu[lm][t][1] = M.mu.y; smu[lm][t][2] = M.mu.z;
-        sth[lm][t][0] = M.th.xx; sth[lm][t][1] = M.th.yy; sth[lm][t][2] = M.th.zz;
-        sth[lm][t][3] = M.th.xy; sth[lm][t][4] = M.th.xz; sth[lm][t][5] = M.th.yz;
-        soff[lm][t][0] = o.x; soff[lm][t][1] = o.y; soff[lm][t][2] = o.z;
+        const R *gm = gmp + (m * NS + t) * GMP;
+        sq[lm][t] = double(gm[0]);
+        for (int k = 0; k < 3; ++k) smu[lm][t][k] = double(gm[1 + k]);
+        for (int k = 0; k < 6; ++k) sth[lm][t][k] = double(gm[4 + k]);   // xx yy zz xy xz yz
+        const double *x = pos + m * 9;
+        // offsets from O: O, H1, H2, and the O-H midpoints
+        const int h = t == 0 ? 0 : (t == 1 || t == 3 ? 1 : 2);
+        const double f = t >= 3 ? 0.5 : 1.0;
+        for (int k = 0; k < 3; ++k) soff[lm][t][k] = h ? f * (x[3 * h + k] - x[k]) : 0.0;
     }
     __syncthreads();
     auto site = [&](int k) {
@@ -252,7 +228,7 @@ __global__ void __launch_bounds__(128) k_intra_energy64(KParams p, const double 
 
 template <typename R>
 void launch_intra_energy64(const KParams &p, DevState<R> &d, Launch L) {
-    k_intra_energy64<<<(p.M + IE_MOL - 1) / IE_MOL, 128, 0, L.s>>>(p, d.pos, d.mp_local, d.eintra);
+    k_intra_energy64<R><<<(p.M + IE_MOL - 1) / IE_MOL, 128, 0, L.s>>>(p, d.pos, d.gmp, d.eintra);
     count(L);
 }
 

@@ -312,6 +312,7 @@ __device__ void item_du(const KParams &p, const Scal<R> &S, const ShortTables &T
     const R *offj = d.off + j * NP * 3;
     const R qO = qcharge(d, j, 0);
     V3<R> gu = mk(R(0), R(0), R(0));
+    R ed = R(0), ex_sum = R(0);   // this item's few terms, then one compensated add each
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
         if (!((vmask >> v) & 1)) continue;
@@ -339,11 +340,13 @@ __device__ void item_du(const KParams &p, const Scal<R> &S, const ShortTables &T
         const R cfj = R(1) - qv * (v == 1 || v == 2 ? S.inv_nval_h : S.inv_nval_o);
         const R K = bu * bv * cfi * cfj;
         const R ex = xc * K * exp_(-mulc(r, T.xd_k[ku][kv]));
-        a.Ed.add(R(0.5) * pref * fsum);
-        a.Ex.add(R(0.5) * ex);
+        ed += pref * fsum;
+        ex_sum += ex;
         const R dEdr = pref * dfdr - cval<R>(T.xd_k[ku][kv]) * ex;
         gu = gu + (dEdr * ri) * dv;
     }
+    a.Ed.add(R(0.5) * ed);
+    a.Ex.add(R(0.5) * ex_sum);
     addG(a, u, gu);
     if (VIR) vir_add(a.W, gu, dO, R(-0.5));
 }

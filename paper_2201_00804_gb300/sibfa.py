@@ -211,11 +211,26 @@ def sibfa_create(params: dict, mp_local: np.ndarray, *, periodic: bool, box=None
     return out
 
 
+def _host_box(box):
+    """The box as 3 host doubles (the C ABI reads it on the host)."""
+    if box is None:
+        return None
+    if hasattr(box, "detach"):
+        box = box.detach().cpu().numpy()
+    b = np.ascontiguousarray(box, dtype=np.float64).reshape(-1)
+    if b.size != 3:
+        raise ValueError("box must have 3 edges")
+    return b
+
+
 def sibfa_energy_forces(ctx, pos, forces=None, box=None, virial=None):
     """One evaluation; returns a dict of energy terms (kcal/mol).  forces (same
     shape as pos) is filled in place when given; virial (a host float64 array
-    of 9) receives W_ab = -dE/d eps_ab (row-major) when given."""
+    of 9) receives W_ab = -dE/d eps_ab (row-major) when given.  box (3 edges)
+    different from the context's current box changes it (periodic contexts;
+    constant-pressure MD)."""
     lib = load_library()
+    box = _host_box(box)
     e = sibfa_energy_terms()
     vir = None
     if virial is not None:
@@ -231,6 +246,7 @@ def sibfa_energy_forces(ctx, pos, forces=None, box=None, virial=None):
 def sibfa_solve_dipoles(ctx, pos, mu=None, tol_D=0.0, box=None):
     """Solve T mu = E only; returns (iterations, residual in D)."""
     lib = load_library()
+    box = _host_box(box)
     it = C.c_int()
     res = C.c_double()
     st = lib.sibfa_solve_dipoles(ctx, _ptr(pos), _ptr(box), float(tol_D), _ptr(mu), C.byref(it), C.byref(res))
