@@ -159,6 +159,20 @@ typedef struct {
      * a Urey-Bradley term). */
     int md_anharmonic;
     double md_k_ub, md_r_ub;
+    /* Charge transfer form, 0 = the reduced one of Eqs. 13-16.  1 = the
+     * original many-body form (CT section, before its reduction): the
+     * acceptor atoms' potentials are kept,
+     *   e1 = exp(-eta rho1) (V_int(a1) + V*(a1) - V_lp)(Cs t + Cp m cos alpha),
+     *   e2 = exp(-eta rho2) (V_int(a2) + V*(a2) - V_lp)(Cs t + Cp m cos beta),
+     *   dE = ae + V_lp - (ah + V(a1)),
+     * with V(a) the potential of the permanent multipoles of every molecule
+     * but a's own at acceptor atom a (undamped, full Ewald in a box) and
+     * V*(a) = V(a) minus the donor molecule's part (its five sites, bare,
+     * at the pair's image).  Forces include the dependence through V(a)
+     * (point charges dE/dV(a) on the acceptor atoms) and through the
+     * donor's multipoles in V*.  The virial is not available with it
+     * (SIBFA_E_INVALID when requested). */
+    int ct_original;
 } sibfa_run_opts;
 
 typedef struct sibfa_ctx sibfa_ctx;

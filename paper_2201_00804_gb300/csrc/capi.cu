@@ -204,6 +204,17 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.dvlp, M * 6);
     AL(d.lam, M * 2);
     AL(d.kap, M * 3);
+    {
+        // original charge transfer (allocated small when off)
+        const bool cto = ctx->opts.ct_original != 0;
+        AL(d.va, cto ? M * 3 : 1);
+        AL(d.va_r, cto ? M * 3 : 1);
+        AL(d.dva, cto ? M * 9 : 1);
+        AL(d.dva_r, cto ? M * 9 : 1);
+        AL(d.lama, cto ? M * 3 : 1);
+        AL(d.lamaR, cto ? M * 3 : 1);
+        AL(d.cvs, cto ? (size_t)M * MAXN * 6 : 1);
+    }
     AL(d.epart, M * NTERM);
     AL(d.epw, M * NS * 2);
     AL(d.vir, M * 9);
@@ -331,6 +342,7 @@ void fill_params(KParams &k, const sibfa_params &P, const sibfa_run_opts &o, int
     k.rc = o.rc;
     k.rc2 = o.rc * o.rc;
     k.skin = o.periodic ? LIST_SKIN : 0.0;
+    k.ct_orig = o.ct_original ? 1 : 0;
     k.alpha = o.ewald_alpha;
     for (int i = 0; i < 3; ++i) k.K[i] = o.grid[i];
     k.ke = P.ke;
@@ -880,6 +892,10 @@ sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_ene
     DevState<R> &d = state<R>(ctx);
     const int M = ctx->M;
     const size_t nb = (size_t)M * 9 * sizeof(double);
+    if (virial && ctx->kp.ct_orig) {
+        ctx->err = "the virial is not available with the original charge transfer";
+        return SIBFA_E_INVALID;
+    }
     bool new_box = false;
     if (box) {
         for (int k = 0; k < 3; ++k) new_box = new_box || box[k] != ctx->kp.box[k];
@@ -1108,6 +1124,10 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
     }
     if (opts->precision != SIBFA_PREC_FP64 && opts->precision != SIBFA_PREC_MIXED) {
         g_create_error = "sibfa_create: unknown precision";
+        return SIBFA_E_INVALID;
+    }
+    if (opts->ct_original < 0 || opts->ct_original > 1) {
+        g_create_error = "sibfa_create: ct_original must be 0 (reduced) or 1 (original)";
         return SIBFA_E_INVALID;
     }
     if (opts->md_integrator < 0 || opts->md_integrator > 1) {

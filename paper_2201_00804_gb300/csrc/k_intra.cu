@@ -19,6 +19,7 @@ struct IntraAcc {
     R gth[NS][6];
     R ef[3][3];
     R dvlp[2][3];
+    R va[3], dva[3][3];   // original charge transfer: potential and gradient at O, H1, H2
 };
 
 template <typename R>
@@ -74,8 +75,12 @@ __constant__ int c_pair10[10][2] = {{0, 1}, {0, 2}, {0, 3}, {0, 4}, {1, 2}, {1, 
 
 // Permanent pass.  Lanes 0-9: the 10 site pairs (energy, gradients and
 // sensitivities of both sites); lanes 10-21: field on O/H1/H2 from the other
-// 4 sites; lanes 22-31: lone-pair potential from the 5 sites.  Lanes 0-4 add
-// the Gaussian self energy of their site, lanes 10/14/18 the self field.
+// 4 sites (with the original charge transfer also the potential and its
+// gradient there, removed from the acceptor potentials together with the
+// atom's own Gaussian self terms: the charge's potential 2 alpha / sqrt(pi)
+// q and the dipole's potential gradient (4/3) alpha^3 / sqrt(pi) mu); lanes 22-31:
+// lone-pair potential from the 5 sites.  Lanes 0-4 add the Gaussian self
+// energy of their site, lanes 10/14/18 the self field.
 template <typename R>
 __global__ void __launch_bounds__(128) k_intra_perm(KParams p, DevState<R> d) {
     __shared__ IntraAcc<R> acc[IW];
@@ -118,11 +123,20 @@ __global__ void __launch_bounds__(128) k_intra_perm(KParams p, DevState<R> d) {
         FieldTerms<R> f;
         source_field<R, 1>(Ms, x, g, f);
         V3<R> E = f.d1;
+        R va = -f.phi;
+        V3<R> dva = R(-1) * f.d1;
         if (k == 0) {
             const Mp<R> Ma = load_mp(d.gmp + (m * NS + a) * GMP);
             E = E + cself * Ma.mu;
+            va -= R(2) * al * spi * Ma.q;
+            // the own Gaussian dipole's potential gradient at its centre, cself mu
+            dva = dva - cself * Ma.mu;
         }
         sadd3(A.ef[a], E, R(1));
+        if (p.ct_orig) {
+            atomicAdd(&A.va[a], va);
+            sadd3(A.dva[a], dva, R(1));
+        }
     } else {
         const int l = (lane - 22) / 5, s = (lane - 22) % 5;
         const Mp<R> Ms = load_mp(d.gmp + (m * NS + s) * GMP);
@@ -152,6 +166,10 @@ __global__ void __launch_bounds__(128) k_intra_perm(KParams p, DevState<R> d) {
     for (int k = lane; k < NS * 6; k += 32) d.gth[m * NS * 6 + k] += ke * double((&A.gth[0][0])[k]);
     if (lane < 9) d.efield[m * 9 + lane] += double((&A.ef[0][0])[lane]);
     if (lane < 6) d.dvlp[m * 6 + lane] += ke * double((&A.dvlp[0][0])[lane]);
+    if (p.ct_orig) {
+        if (lane < 3) d.va[m * 3 + lane] += ke * double(A.va[lane]);
+        if (lane < 9) d.dva[m * 9 + lane] += ke * double((&A.dva[0][0])[lane]);
+    }
     if (lane == 0) {
         d.vlp[m * 2] += ke * v0;
         d.vlp[m * 2 + 1] += ke * v1;
@@ -312,6 +330,35 @@ __global__ void __launch_bounds__(128) k_intra_polforce(KParams p, DevState<R> d
         const int a = lane - 25;
         const R cself = R(4.0 / 3.0) * al * al * al * R(0.56418958354775628695);
         sadd3(A.gmu[a], mu_of(a), -cself);
+    }
+    // original charge transfer: the charges dE/dV(a) on O, H1, H2 were spread
+    // with the lone-pair lambdas; remove their erf part at the molecule's
+    // other four sites, and at the atom's own site the gradient d2 . mu that
+    // the charge's own Gaussian (field gradient -(4/3) alpha^3 / sqrt(pi) I at
+    // its centre) gives its dipole
+    if (p.ct_orig && lane >= 25 && lane < 28) {
+        const int a = lane - 25;
+        const R cself = R(4.0 / 3.0) * al * al * al * R(0.56418958354775628695);
+        const Mp<R> Ma = load_mp(d.gmp + (m * NS + a) * GMP);
+        sadd3(A.gpt[a], Ma.mu, cself * R(d.lama[m * 3 + a]));
+    }
+    if (p.ct_orig && lane < 12) {
+        const int a = lane / 4, k = lane % 4;
+        const int s = k < a ? k : k + 1;
+        const double lq = d.lama[m * 3 + a];
+        if (lq != 0.0) {
+            const Mp<R> Ms = load_mp(d.gmp + (m * NS + s) * GMP);
+            const V3<R> x = opt(d, m, s) - opt(d, m, a);
+            R g[6];
+            g_erf_s<R, 5>(dot(x, x), al, g);
+            Mp<R> c{};
+            c.q = R(lq);
+            FieldTerms<R> f;
+            source_field<R, 3>(c, x, g, f);
+            sadd3(A.gpt[s], target_grad(Ms, c, x, g, f), R(-1));
+            sadd3(A.gmu[s], f.d1, R(-1));
+            sadd6(A.gth[s], f.d2, R(-1.0 / 3.0));
+        }
     }
     const double ke = p.ke;
     __syncwarp();

@@ -227,12 +227,14 @@ __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d
 
 // One block per molecule whose NW warps take the target points W0 ..
 // W0 + NW - 1: the five sites (W0 = 0) and, in a second launch on another
-// stream, the lone pairs (W0 = 5: potential and gradient).  Each warp stores
+// stream, the lone pairs (W0 = 5: potential and gradient).  POT: the atoms
+// O, H1, H2 as potential-only targets (potential and gradient, the acceptor
+// potentials of the original charge transfer).  Each warp stores
 // its energies, so the blocks need no barrier; the virial variant sums the
 // site warps' virials in a fixed order.
 // Site blocks: 3 resident per SM in periodic systems, 4 in the gas phase
 // (96 registers; measured faster there, slower with the Ewald kernels).
-template <typename R, bool PER, bool VIR, int W0, int NW>
+template <typename R, bool PER, bool VIR, int W0, int NW, bool POT = false>
 __global__ void __launch_bounds__(32 * NW, NW == 5 ? (PER ? 3 : 4) : (NW == 3 ? 5 : 8))
     k_real_perm(KParams p, DevState<R> d) {
     __shared__ double s_w[VIR ? NW : 1][9];
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(32 * NW, NW == 5 ? (PER ? 3 : 4) : (NW == 3 ? 
     const int i = blockIdx.x;
     const int wq = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w = W0 + wq;   // target point
-    constexpr bool is_lp = W0 >= NS;
+    constexpr bool is_lp = W0 >= NS || POT;   // potential-only targets
     PairQueue<R> &q = qs[wq];
     const V3<R> ot = my_pt(d, i, w);
     Mp<R> mt{};
@@ -331,10 +333,16 @@ __global__ void __launch_bounds__(32 * NW, NW == 5 ? (PER ? 3 : 4) : (NW == 3 ? 
         if (flush) break;
     }
 
-    if (w < 3 && lane == 0) d.tl_n[i * 3 + w] = ta;
+    if (!POT && w < 3 && lane == 0) d.tl_n[i * 3 + w] = ta;
     const double ke = p.ke;
     R *buf = reinterpret_cast<R *>(&q);
-    if (is_lp) {
+    if (POT) {
+        const double v = warp_sum_acc(A.Vl);
+        const R vals[3] = {A.gr.x, A.gr.y, A.gr.z};
+        const R t = warp_transpose_sum<R, 3>(vals, buf, lane);
+        if (lane < 3) d.dva[(i * 3 + w) * 3 + lane] += ke * double(t);
+        if (lane == 0) d.va[i * 3 + w] += ke * v;
+    } else if (is_lp) {
         const int l = w - NS;
         const double v = warp_sum_acc(A.Vl);
         const R vals[3] = {A.gr.x, A.gr.y, A.gr.z};
@@ -388,12 +396,18 @@ void launch_real_perm(const KParams &p, DevState<R> &d, Launch L) {
     count(L);
 }
 
-// potential and field of the permanent multipoles at the lone pairs (real space)
+// potential and field of the permanent multipoles at the lone pairs (real
+// space); with the original charge transfer also at the atoms O, H1, H2
 template <typename R>
 void launch_lp_potential(const KParams &p, DevState<R> &d, Launch L) {
     if (p.periodic) k_real_perm<R, true, false, NS, 2><<<p.M, 64, 0, L.s>>>(p, d);
     else k_real_perm<R, false, false, NS, 2><<<p.M, 64, 0, L.s>>>(p, d);
     count(L);
+    if (p.ct_orig) {
+        if (p.periodic) k_real_perm<R, true, false, 0, 3, true><<<p.M, 96, 0, L.s>>>(p, d);
+        else k_real_perm<R, false, false, 0, 3, true><<<p.M, 96, 0, L.s>>>(p, d);
+        count(L);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -402,13 +416,16 @@ void launch_lp_potential(const KParams &p, DevState<R> &d, Launch L) {
 // ---------------------------------------------------------------------------
 template <typename R>
 struct CtOut {
-    R E, dV, dVi1, dVi2;
+    R E, dV, dVi1, dVi2, dsh;
     V3<R> gc, glp, ga1, ga2;
 };
 
+// Vi1, Vi2: the acceptor atoms' potentials in e1, e2 (V_int; the original
+// form adds V*); shift: subtracted from the denominator (the original form's
+// V(a1)); dsh = dE/dshift.
 template <typename R>
 __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1, V3<R> a2, R V, R Vi1, R Vi2,
-                                   int *flags) {
+                                   int *flags, R shift = R(0)) {
     CtOut<R> o;
     const Scal<R> &S = sc<R>(p);
     const R cs = S.cs_lp, cp = S.cp_lp, t = S.ct_t, mm = S.ct_m, n = S.nlp;
@@ -423,7 +440,7 @@ __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1
     const R K1 = cs * t + cp * mm * ca, K2 = cs * t + cp * mm * cb;
     const R e1 = E1 * (Vi1 - V) * K1, e2 = E2 * (Vi2 - V) * K2;
     const R D = e1 - e2;
-    const R dE = S.ct_ae + V - S.ct_ah;
+    const R dE = S.ct_ae + V - S.ct_ah - shift;
     if (!(dE > R(0))) atomicOr(flags, F_CTDEN);
     const R idE = rcp_(dE);
     o.E = -n * D * D * idE;
@@ -431,6 +448,7 @@ __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1
     o.dV = gD * (-E1 * K1 + E2 * K2) + n * D * D * idE * idE;
     o.dVi1 = gD * E1 * K1;
     o.dVi2 = -gD * E2 * K2;
+    o.dsh = -n * D * D * idE * idE;
     const R dr1 = gD * (-ek1 * e1), dr2 = gD * (ek2 * e2);
     const R dca = gD * E1 * (Vi1 - V) * cp * mm, dcb = -gD * E2 * (Vi2 - V) * cp * mm;
     const V3<R> n1 = ir1 * v1, n2 = ir2 * v2;
@@ -441,6 +459,25 @@ __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1
     return o;
 }
 
+// Bare potential (times ke) of the five multipole sites of molecule m at a
+// point y given relative to m's O: the donor's part of an acceptor atom's
+// potential in the original charge transfer.
+template <typename R>
+__device__ inline R mol_phi(const KParams &p, const DevState<R> &d, int m, V3<R> y) {
+    R phi = R(0);
+#pragma unroll 1
+    for (int s = 0; s < NS; ++s) {
+        const Mp<R> M = load_mp_g(d.gmp + (m * NS + s) * GMP);
+        const V3<R> x = y - my_pt(d, m, s);
+        R g[3];
+        g_bare<R, 2>(rsqrt_(dot(x, x)), g);
+        FieldTerms<R> f;
+        source_field<R, 0>(M, x, g, f);
+        phi += f.phi;
+    }
+    return R(p.ke) * phi;
+}
+
 // VIR: the virial of the pair terms by translation invariance: with X_p =
 // O_i + off_p, sum over a molecule pair of g_p (x) X_p = sum_{p of i} g_p (x)
 // off_p + sum_{p of j} g_p (x) off_p - G_{i<-j} (x) dO_ij, where G_{i<-j} is
@@ -448,7 +485,7 @@ __device__ inline CtOut<R> ct_pair(const KParams &p, V3<R> c, V3<R> lp, V3<R> a1
 // its own offsets term and half of the last one.
 template <typename R, bool PER, bool VIR>
 __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
-    __shared__ R red[4][20 * 33];
+    __shared__ R red[4][23 * 33];
     const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= p.M) return;
@@ -463,6 +500,11 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
     V3<R> G[5];
     for (int k = 0; k < 5; ++k) G[k] = mk(R(0), R(0), R(0));
     R lam[2] = {R(0), R(0)}, kap[3] = {R(0), R(0), R(0)};
+    // original form: the acceptor potentials V(a) of i's atoms and dE/dV(a)
+    const bool orig = p.ct_orig != 0;
+    R Va_i[3] = {R(0), R(0), R(0)}, lama[3] = {R(0), R(0), R(0)};
+    if (orig)
+        for (int a = 0; a < 3; ++a) Va_i[a] = R(d.va[i * 3 + a] + d.va_r[i * 3 + a]);
     R W[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) W[k] = R(0);
@@ -472,7 +514,12 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
         const int j = d.nbr[i * MAXN + slot];
         const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
         const V3<R> dO = mk(dp_[0], dp_[1], dp_[2]);
-        if (PER && dot(dO, dO) >= rc2) continue;
+        R *cv = orig ? d.cvs + ((size_t)i * MAXN + slot) * 6 : nullptr;
+        if (PER && dot(dO, dO) >= rc2) {
+            if (orig)
+                for (int k = 0; k < 6; ++k) cv[k] = R(0);
+            continue;
+        }
         V3<R> Q[5];
         Q[0] = dO;
         Q[1] = dO + my_pt(d, j, 1);
@@ -481,38 +528,140 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
         Q[4] = dO + my_pt(d, j, 6);
         const R Vj[2] = {R(d.vlp[j * 2] + d.vlp_r[j * 2]), R(d.vlp[j * 2 + 1] + d.vlp_r[j * 2 + 1])};
         const R Vint_j[3] = {R(d.vint[j * 3]), R(d.vint[j * 3 + 1]), R(d.vint[j * 3 + 2])};
+        // original form: W = V_int + V* in e1, e2 and V(a1) in the denominator,
+        // V*(a) = V(a) minus the donor molecule's bare potential at a
+        R Wj[3] = {Vint_j[0], Vint_j[1], Vint_j[2]}, Wi[3] = {Vint_i[0], Vint_i[1], Vint_i[2]};
+        R sh_j = R(0), sh_i = R(0);
+        R cd[3] = {R(0), R(0), R(0)}, ca[3] = {R(0), R(0), R(0)};
+        if (orig) {
+            for (int a = 0; a < 3; ++a) {
+                const R Va_j = R(d.va[j * 3 + a] + d.va_r[j * 3 + a]);
+                Wj[a] += Va_j - mol_phi(p, d, i, Q[a]);            // i's sites at j's atom a
+                Wi[a] += Va_i[a] - mol_phi(p, d, j, P[a] - dO);    // j's sites at i's atom a
+                if (a == 0) sh_j = Va_j;
+            }
+            sh_i = Va_i[0];
+        }
         V3<R> Gj = mk(R(0), R(0), R(0));   // gradient on i's points from j (virial)
         for (int l = 0; l < 2; ++l)
             for (int k = 1; k <= 2; ++k) {
                 // i donor (lone pair l of i), j acceptor (bond O-H_k of j)
-                CtOut<R> o = ct_pair(p, P[0], P[3 + l], Q[0], Q[k], Vi[l], Vint_j[0], Vint_j[k], d.flags);
+                CtOut<R> o = ct_pair(p, P[0], P[3 + l], Q[0], Q[k], Vi[l], Wj[0], Wj[k], d.flags, sh_j);
                 Ect.add(R(0.5) * o.E);
                 G[0] = G[0] + o.gc;
                 G[3 + l] = G[3 + l] + o.glp;
                 lam[l] += o.dV;
+                cd[0] += o.dVi1;
+                cd[k] += o.dVi2;
                 // j donor (lone pair l of j), i acceptor (bond O-H_k of i)
-                CtOut<R> q = ct_pair(p, Q[0], Q[3 + l], P[0], P[k], Vj[l], Vint_i[0], Vint_i[k], d.flags);
+                CtOut<R> q = ct_pair(p, Q[0], Q[3 + l], P[0], P[k], Vj[l], Wi[0], Wi[k], d.flags, sh_i);
                 Ect.add(R(0.5) * q.E);
                 G[0] = G[0] + q.ga1;
                 G[k] = G[k] + q.ga2;
                 kap[0] += q.dVi1;
                 kap[k] += q.dVi2;
+                ca[0] += q.dVi1;
+                ca[k] += q.dVi2;
+                lama[0] += q.dVi1 + q.dsh;
+                lama[k] += q.dVi2;
                 if (VIR) Gj = Gj + o.gc + o.glp + q.ga1 + q.ga2;
             }
+        if (orig) {
+            for (int a = 0; a < 3; ++a) cv[a] = cd[a], cv[3 + a] = ca[a];
+        }
         if (VIR) vir_add(W, Gj, dO, R(-0.5));
     }
-    const R vals[20] = {G[0].x, G[0].y, G[0].z, G[1].x, G[1].y, G[1].z, G[2].x, G[2].y, G[2].z,
-                        G[3].x, G[3].y, G[3].z, G[4].x, G[4].y, G[4].z, lam[0], lam[1], kap[0], kap[1], kap[2]};
-    const R t = warp_transpose_sum<R, 20>(vals, red[threadIdx.x >> 5], lane);
+    const R vals[23] = {G[0].x, G[0].y, G[0].z, G[1].x, G[1].y, G[1].z, G[2].x, G[2].y, G[2].z,
+                        G[3].x, G[3].y, G[3].z, G[4].x, G[4].y, G[4].z, lam[0], lam[1], kap[0], kap[1], kap[2],
+                        lama[0], lama[1], lama[2]};
+    const R t = warp_transpose_sum<R, 23>(vals, red[threadIdx.x >> 5], lane);
     const int pt = lane / 3;
     double *dst = nullptr;
     if (lane < 15) dst = d.gpt + (i * NP + (pt < 3 ? pt : pt + 2)) * 3 + lane % 3;
     else if (lane < 17) dst = d.lam + i * 2 + lane - 15;
     else if (lane < 20) dst = d.kap + i * 3 + lane - 17;
+    else if (lane < 23 && orig) dst = d.lama + i * 3 + lane - 20;
     if (dst) *dst += double(t);
     if (VIR) vir_points_out(d, i, P, t, W, red[threadIdx.x >> 5], lane);
     const double e = warp_sum_acc(Ect);
     if (lane == 0) d.epart[i * NTERM + T_CT] += e;
+}
+
+// Original charge transfer, the dependence through V*(a) = V(a) - phi_D(a)
+// (phi_D: the donor molecule's bare potential at the acceptor atom a) and
+// through V(a).  With c = dE/dV*(a) per neighbour slot (k_ct: 0-2 at the
+// partner's atoms for i donating, 3-5 at i's atoms for the partner
+// donating) the energy varies as -sum c phi_D(a).  Warps 0-4: site s of i as
+// the donor's source, point charges -c at the partners' atoms acting on its
+// multipole (gradient at the site and multipole sensitivities); warps 5-7:
+// atom a of i as the acceptor, the gradient of -c phi_j at the atom, plus
+// the atom's own share of dE/dV(a) times the gradient of V(a) (the partners'
+// share, charges dE/dV(a) on the atoms in the potential of every site, is
+// taken in the force pass).
+template <typename R>
+__global__ void __launch_bounds__(256) k_ct_vstar(KParams p, DevState<R> d) {
+    __shared__ R red[8][12 * 33];
+    const int i = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nn = d.nnbr[i];
+    const R third = R(1) / R(3);
+    V3<R> gr = mk(R(0), R(0), R(0)), gm = gr;
+    Sym<R> gt{};
+    if (w < NS) {
+        const Mp<R> mt = load_mp(d.gmp + (i * NS + w) * GMP);
+        const V3<R> ot = my_pt(d, i, w);
+        for (int slot = lane; slot < nn; slot += 32) {
+            const R *c = d.cvs + ((size_t)i * MAXN + slot) * 6;
+            if (c[0] == R(0) && c[1] == R(0) && c[2] == R(0)) continue;
+            const int j = d.nbr[i * MAXN + slot];
+            const R *dp = d.ndo + ((size_t)i * MAXN + slot) * 3;
+            const V3<R> dO = mk(dp[0], dp[1], dp[2]);
+            for (int a = 0; a < 3; ++a) {
+                Mp<R> ms{};
+                ms.q = -c[a];
+                const V3<R> x = ot - (dO + my_pt(d, j, a));
+                R g[6];   // source_field to third derivatives reads g_0..g_5
+                g_bare<R, 5>(rsqrt_(dot(x, x)), g);
+                FieldTerms<R> f;
+                source_field<R, 3>(ms, x, g, f);
+                gr = gr + target_grad(mt, ms, x, g, f);
+                gm = gm + f.d1;
+                symadd(gt, f.d2, third);
+            }
+        }
+    } else {
+        const int a = w - NS;
+        const V3<R> ot = my_pt(d, i, a);
+        for (int slot = lane; slot < nn; slot += 32) {
+            const R c = d.cvs[((size_t)i * MAXN + slot) * 6 + 3 + a];
+            if (c == R(0)) continue;
+            const int j = d.nbr[i * MAXN + slot];
+            const R *dp = d.ndo + ((size_t)i * MAXN + slot) * 3;
+            const V3<R> dO = mk(dp[0], dp[1], dp[2]);
+            for (int s = 0; s < NS; ++s) {
+                const Mp<R> ms = load_mp_g(d.gmp + (j * NS + s) * GMP);
+                const V3<R> x = ot - (dO + my_pt(d, j, s));
+                R g[4];
+                g_bare<R, 3>(rsqrt_(dot(x, x)), g);
+                FieldTerms<R> f;
+                source_field<R, 1>(ms, x, g, f);
+                gr = gr - c * f.d1;
+            }
+        }
+    }
+    const R vals[12] = {gr.x, gr.y, gr.z, gm.x, gm.y, gm.z, gt.xx, gt.yy, gt.zz, gt.xy, gt.xz, gt.yz};
+    const R t = warp_transpose_sum<R, 12>(vals, red[w], lane);
+    const double ke = p.ke;
+    // warps w < 3 (sites O, H1, H2) and 5 + w (the same atoms) both add to
+    // the atom's point gradient: atomically
+    if (w < NS) {
+        if (lane < 3) atomicAdd(d.gpt + (i * NP + w) * 3 + lane, ke * double(t));
+        else if (lane < 6) d.gmu[(i * NS + w) * 3 + lane - 3] += ke * double(t);
+        else if (lane < 12) d.gth[(i * NS + w) * 6 + lane - 6] += ke * double(t);
+    } else if (lane < 3) {
+        const int a = w - NS;
+        const double gv = d.dva[(i * 3 + a) * 3 + lane] + d.dva_r[(i * 3 + a) * 3 + lane];
+        atomicAdd(d.gpt + (i * NP + a) * 3 + lane, ke * double(t) + d.lama[i * 3 + a] * gv);
+    }
 }
 
 template <typename R>
@@ -526,6 +675,10 @@ void launch_ct(const KParams &p, DevState<R> &d, Launch L) {
         else k_ct<R, false, false><<<nb, 128, 0, L.s>>>(p, d);
     }
     count(L);
+    if (p.ct_orig) {
+        k_ct_vstar<R><<<p.M, 256, 0, L.s>>>(p, d);
+        count(L);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -639,6 +792,16 @@ __device__ __forceinline__ void polf_pair(const KParams &p, const DevState<R> &d
         A.gr = A.gr + gm;
         A.gm = A.gm + f.d1;
         symadd(A.gt, f.d2, third);
+        if (p.ct_orig) {   // original charge transfer: dE/dV(a) as a charge on atom s of j, undamped
+            Mp<R> ml{};
+            ml.q = d.lamaR[j * 3 + s];
+            const R gl[6] = {gb[0], gb[1], gb[2], gb[3], gb[4], R(0)};
+            FieldTerms<R> fl;
+            source_field<R, 3>(ml, x, gl, fl);
+            A.gr = A.gr + target_grad(mt, ml, x, gl, fl);
+            A.gm = A.gm + fl.d1;
+            symadd(A.gt, fl.d2, third);
+        }
         if (VIR) gv = gm;
         // induced-induced, d/dr_a of mu_a . grad phi_b: for w < 3 the site
         // damping polarizability is the atom's, so f is the atom-atom field

@@ -366,6 +366,8 @@ __global__ void k_pol_energy(KParams p, DevState<R> d) {
     }
     d.lamR[m * 2] = R(d.lam[m * 2]);
     d.lamR[m * 2 + 1] = R(d.lam[m * 2 + 1]);
+    if (p.ct_orig)
+        for (int a = 0; a < 3; ++a) d.lamaR[m * 3 + a] = R(d.lama[m * 3 + a]);
     d.epart[m * NTERM + T_POL] = -0.5 * p.ke * e;
     // real-space multipole and penetration energies of the five target sites
     double el = 0, pe = 0;

@@ -140,6 +140,10 @@ __global__ void __launch_bounds__(128) k_sites(KParams p, DevState<R> d) {
         if (t < 2) d.vlp[m * 2 + t] = 0.0, d.vlp_r[m * 2 + t] = 0.0, d.lam[m * 2 + t] = 0.0;
         if (t < 6) d.dvlp[m * 6 + t] = 0.0, d.dvlp_r[m * 6 + t] = 0.0;
         if (t < 3) d.kap[m * 3 + t] = 0.0;
+        if (p.ct_orig) {
+            if (t < 3) d.va[m * 3 + t] = 0.0, d.va_r[m * 3 + t] = 0.0, d.lama[m * 3 + t] = 0.0;
+            for (int k = t; k < 9; k += 8) d.dva[m * 9 + k] = 0.0, d.dva_r[m * 9 + k] = 0.0;
+        }
         if (t < NTERM) d.epart[m * NTERM + t] = 0.0, d.epart_r[m * NTERM + t] = 0.0;
         if (p.vir)
             for (int k = t; k < 9; k += 8) d.vir[m * 9 + k] = 0.0, d.vir_r[m * 9 + k] = 0.0;

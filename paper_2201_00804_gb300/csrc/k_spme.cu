@@ -89,7 +89,8 @@ __device__ inline void add_zline(R *grid, size_t row, int K2, const int (&zg)[OR
 // kind PERM: 5 sites per molecule with their multipoles;
 // kind DIP: 3 polarizable atoms with the induced dipoles (d.muR);
 // kind DIP_PCG: the same from the working-precision PCG vector;
-// kind LAMBDA: 2 lone pairs with the charge-transfer lambdas (d.lamR).
+// kind LAMBDA: 2 lone pairs with the charge-transfer lambdas (d.lamR), and
+// with the original charge transfer also O, H1, H2 with dE/dV(a) (d.lamaR).
 // NDER: derivative order the multipoles need (2: quadrupoles, 1: dipoles, 0: charges).
 template <typename R, int NDER>
 __global__ void __launch_bounds__(256) k_spread(KParams p, DevState<R> d, int kind, const double *vec, R *grid) {
@@ -98,18 +99,18 @@ __global__ void __launch_bounds__(256) k_spread(KParams p, DevState<R> d, int ki
         if (d.flags[1]) return;   // solver already converged
         kind = SPREAD_DIP;
     }
-    const int per = kind == SPREAD_PERM ? NS : (kind == SPREAD_DIP ? 3 : 2);
+    const int per = kind == SPREAD_PERM ? NS : (kind == SPREAD_DIP ? 3 : (p.ct_orig ? 5 : 2));
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int t = gt / PG, xi = gt % PG;
     if (t >= p.M * per || xi >= ORDER) return;
     const int m = t / per, a = t % per;
-    const int pt = kind == SPREAD_LAMBDA ? 5 + a : a;
+    const int pt = kind == SPREAD_LAMBDA ? (a < 2 ? 5 + a : a - 2) : a;
     Mp<R> mp{};
     if (kind == SPREAD_PERM) mp = load_mp(d.gmp + (m * NS + a) * GMP);
     else if (kind == SPREAD_DIP) {
         const R *v = pcg ? d.vecR : d.muR;
         mp.mu = mk(v[m * 9 + a * 3], v[m * 9 + a * 3 + 1], v[m * 9 + a * 3 + 2]);
-    } else mp.q = d.lamR[m * 2 + a];
+    } else mp.q = a < 2 ? d.lamR[m * 2 + a] : d.lamaR[m * 3 + a - 2];
     Axis<R, NDER> X, Y, Z;
     axis_weights<R, NDER>(p, d, m, pt, 0, X);
     axis_weights<R, NDER>(p, d, m, pt, 1, Y);
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(256) k_spread(KParams p, DevState<R> d, int ki
 
 template <typename R>
 void launch_spread(const KParams &p, DevState<R> &d, int kind, const double *vec, R *grid, Launch L) {
-    const int per = kind == SPREAD_PERM ? NS : ((kind == SPREAD_DIP || kind == SPREAD_DIP_PCG) ? 3 : 2);
+    const int per = kind == SPREAD_PERM ? NS : ((kind == SPREAD_DIP || kind == SPREAD_DIP_PCG) ? 3 : (p.ct_orig ? 5 : 2));
     const long long threads = (long long)p.M * per * PG;
     const unsigned nb = (unsigned)((threads + 255) / 256);
     if (kind == SPREAD_PERM) k_spread<R, 2><<<nb, 256, 0, L.s>>>(p, d, kind, vec, grid);
@@ -508,7 +509,9 @@ __global__ void __launch_bounds__(256, 2) k_gather_perm(KParams p, DevState<R> d
     if (!live) return;
     if (site) {
         const Mp<R> mp = load_mp(d.gmp + (m * NS + pt) * GMP);
-        for (int o = sub; o < 22; o += PG) {
+        // original charge transfer: also the potential and its gradient at the atoms
+        const int nout = (p.ct_orig && pt < 3) ? 26 : 22;
+        for (int o = sub; o < nout; o += PG) {
             if (o < 3) {
                 d.gpt[(m * NP + pt) * 3 + o] += (double)mp_grad(mp, D, o);
                 d.gmu[(m * NS + pt) * 3 + o] += (double)D.d1[o];
@@ -518,9 +521,15 @@ __global__ void __launch_bounds__(256, 2) k_gather_perm(KParams p, DevState<R> d
                 if (pt < 3) d.d2rec[m * 18 + pt * 6 + o - 3] = (double)D.d2[o - 3];
             } else if (o == 9) {
                 atomicAdd(&d.epart[m * NTERM + T_ELEC], 0.5 * (double)mp_energy(mp, D));
-            } else if (p.vir) {
-                if (o < 19) atomicAdd(&d.vir[m * 9 + o - 10], -(double)mp_strain(mp, D, o - 10));
-                else if (pt < 3) d.vphi[m * 9 + pt * 3 + o - 19] = D.d1[o - 19];
+            } else if (o < 22) {
+                if (p.vir) {
+                    if (o < 19) atomicAdd(&d.vir[m * 9 + o - 10], -(double)mp_strain(mp, D, o - 10));
+                    else if (pt < 3) d.vphi[m * 9 + pt * 3 + o - 19] = D.d1[o - 19];
+                }
+            } else if (o == 22) {
+                d.va[m * 3 + pt] += (double)D.phi;
+            } else {
+                d.dva[(m * 3 + pt) * 3 + o - 23] += (double)D.d1[o - 23];
             }
         }
     } else {

@@ -51,6 +51,7 @@ struct KParams {
     int n_cl;              // clusters (1: one system)
     int tls;               // T-pair list slots per polarizable atom: 3 x the most neighbours a molecule can have
     int vir;               // 1: this evaluation also accumulates the virial
+    int ct_orig;           // 1: the original many-body charge transfer (acceptor potentials kept)
     double box[3];
     double ibox[3];        // 1 / box
     double rc, rc2;
@@ -202,6 +203,13 @@ struct DevState {
     // t = 3 m + a, entries [t*tls, t*tls + tl_n[t]) hold the partner atom
     // (3 j + b), the displacement x = r_t - r_jb and the Thole-damped kernel
     // weights g1, g2 of the dipole field (E = g2 (mu.x) x + g1 mu).
+    // original charge transfer: potential and its gradient at O, H1, H2 from
+    // the other molecules (real space / reciprocal chain), dE/dV(a) of the
+    // acceptor atoms (FP64 and working-precision copy), and per neighbour
+    // slot the sensitivities dE/dV*(a) at the partner's atoms (i donor, 0-2)
+    // and at the molecule's own atoms (j donor, 3-5)
+    double *va, *va_r, *dva, *dva_r, *lama;
+    R *lamaR, *cvs;
     int *tl_n, *tl_j;
     R *tl_x, *tl_y, *tl_z, *tl_g1, *tl_g2;
     double *partial;    // reduction partials
@@ -830,6 +838,8 @@ inline DevState<R> rec_view(const DevState<R> &d) {
     r.efield = d.efield_r;
     r.vlp = d.vlp_r;
     r.dvlp = d.dvlp_r;
+    r.va = d.va_r;
+    r.dva = d.dva_r;
     r.epart = d.epart_r;
     r.vir = d.vir_r;
     return r;

@@ -45,7 +45,7 @@ class sibfa_run_opts(C.Structure):
                 ("stream", C.c_void_p), ("md_k_bond", C.c_double), ("md_r0", C.c_double),
                 ("md_k_angle", C.c_double), ("md_theta0_deg", C.c_double), ("disp_tail", C.c_int),
                 ("md_integrator", C.c_int), ("md_anharmonic", C.c_int), ("md_k_ub", C.c_double),
-                ("md_r_ub", C.c_double)]
+                ("md_r_ub", C.c_double), ("ct_original", C.c_int)]
 
 
 class sibfa_energy_terms(C.Structure):
@@ -168,7 +168,7 @@ def sibfa_create(params: dict, mp_local: np.ndarray, *, periodic: bool, box=None
                  ewald_alpha=0.4, pcg_tol_D=1e-6, pcg_max_iter=200, precision=PREC_MIXED, warm_start=True,
                  stream=None, md_k_bond=529.6, md_r0=0.9572, md_k_angle=34.05, md_theta0_deg=104.52,
                  cluster_start=None, disp_tail=False, md_integrator="verlet", md_anharmonic=False, md_k_ub=0.0,
-                 md_r_ub=1.5326):
+                 md_r_ub=1.5326, ct_original=False):
     """Create a context.  mp_local: (n_mol, 5, 10) float64 host array.
     stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None.
     cluster_start: optional (n_clusters + 1) ints splitting a gas-phase batch
@@ -205,6 +205,7 @@ def sibfa_create(params: dict, mp_local: np.ndarray, *, periodic: bool, box=None
     o.md_integrator = {"verlet": 0, "beeman": 1}[md_integrator]
     o.md_anharmonic = 1 if md_anharmonic else 0
     o.md_k_ub, o.md_r_ub = float(md_k_ub), float(md_r_ub)
+    o.ct_original = 1 if ct_original else 0
     out = C.c_void_p()
     st = lib.sibfa_create(C.byref(P), C.byref(topo), C.byref(o), C.byref(out))
     _check(lib, None, st)

@@ -21,7 +21,7 @@ FP64_MU_RMS_D = 1e-8
 TERMS = ("elec", "pen", "rep", "disp", "xdisp", "pol", "ct")
 
 
-def run_gpu(system, opts, precision, tol_D, device=True, params=None, max_iter=300):
+def run_gpu(system, opts, precision, tol_D, device=True, params=None, max_iter=300, **create_kw):
     import torch
     import paper_2201_00804_gb300 as pkg
 
@@ -31,7 +31,7 @@ def run_gpu(system, opts, precision, tol_D, device=True, params=None, max_iter=3
     if periodic:
         kw = dict(box=system.box, rc=opts["rc"], grid=opts["grid"], ewald_alpha=opts["ewald"])
     ctx = pkg.sibfa_create(P, system.mp_local, periodic=periodic, pcg_tol_D=tol_D, precision=precision,
-                           pcg_max_iter=max_iter, warm_start=False, **kw)
+                           pcg_max_iter=max_iter, warm_start=False, **kw, **create_kw)
     try:
         if device:
             pos = torch.tensor(system.pos.reshape(-1), dtype=torch.float64, device="cuda")

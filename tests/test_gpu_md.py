@@ -148,6 +148,49 @@ def test_nve_stays_stable_with_bounded_drift():
     assert 200.0 < min(temps) and max(temps) < 1500.0, temps
 
 
+@pytest.mark.parametrize("name,n_nve", [("water4096", 1000), ("water32000", 500)])
+def test_workload_nve_runs_reach_their_lengths(name, n_nve):
+    """The MD workloads' own lengths at 0.5 fs (1000 NVE steps of the
+    4096-water box, 500 of the 32,000-water box) after the bench's
+    preparation shortened (20 capped relaxation steps, 200 velocity-rescaled
+    steps at 300 K): every chunk returns without an error status, the total
+    energy drifts by less than 0.02 kcal/mol per atom and the temperature
+    stays bounded."""
+    import torch
+    import paper_2201_00804_gb300 as pkg
+    s, o = synth.make_config(name)
+    ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
+                           ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"], precision=pkg.PREC_MIXED, warm_start=4,
+                           md_k_bond=KB, md_r0=R0, md_k_angle=KA, md_theta0_deg=TH0_DEG)
+    pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
+    vel = torch.tensor(synth.maxwell_velocities(s, 300.0, seed=22).reshape(-1), dtype=torch.float64, device="cuda")
+    masses = torch.tensor(s.masses().reshape(-1), dtype=torch.float64, device="cuda")
+    m3 = masses.repeat_interleave(3)
+    ndof = vel.numel() - 3
+    kb, conv = 0.0019872041, 4.184e-4
+
+    def kinetic():
+        return 0.5 * float((m3 * vel * vel).sum()) / conv
+
+    try:
+        pkg.sibfa_minimize(ctx, pos, 20, 0.01)
+        for _ in range(40):
+            pkg.sibfa_md_steps(ctx, pos, vel, masses, DT_FS, 5)
+            vel.mul_(math.sqrt(300.0 / (2.0 * kinetic() / (ndof * kb))))
+        totals, temps = [], []
+        for _ in range(n_nve // 50):
+            e = pkg.sibfa_md_steps(ctx, pos, vel, masses, DT_FS, 50)
+            x = pos.cpu().numpy().reshape(-1, 3, 3)
+            totals.append(kinetic() + e["total"] + float(intra_energy(x).sum()))
+            temps.append(2.0 * kinetic() / (ndof * kb))
+    finally:
+        pkg.sibfa_destroy(ctx)
+    assert len(totals) * 50 == n_nve
+    drift = abs(totals[-1] - totals[0]) / s.n_atoms
+    assert drift < 0.02, (drift, totals[0], totals[-1])
+    assert 200.0 < min(temps) and max(temps) < 1500.0, temps
+
+
 KUB, RUB = 38.25, 1.5326
 
 
