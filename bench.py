@@ -780,7 +780,7 @@ def main():
     else:
         units = count_units_clusters(o["cluster_start"], M)
     kfl = kernel_flops(units)
-    kernels = {"real_perm": ("k_real_perm<float, %d, 0, 0, 5>" % int(args.workload != "clusters4096"),
+    kernels = {"real_perm": ("k_real_perm<float, %d, 0, 0, 5, 0>" % int(args.workload != "clusters4096"),
                              "site targets: multipole + penetration energy, gradient, torque sensitivities, "
                              "Thole field; 1 launch per step"),
                "short": ("k_short<float, %d, 0, 0|1>" % int(args.workload != "clusters4096"),
