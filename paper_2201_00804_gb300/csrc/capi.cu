@@ -215,6 +215,7 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
         AL(d.lamaR, cto ? M * 3 : 1);
         AL(d.cvs, cto ? (size_t)M * MAXN * 6 : 1);
     }
+    AL(d.ctin, M * 8);
     AL(d.epart, M * NTERM);
     AL(d.epw, M * NS * 2);
     AL(d.vir, M * 9);

@@ -478,15 +478,38 @@ __device__ inline R mol_phi(const KParams &p, const DevState<R> &d, int m, V3<R>
     return R(p.ke) * phi;
 }
 
+// Working-precision per-molecule inputs of the charge transfer, so the pair
+// loop reads no FP64: the lone-pair potentials (real space + reciprocal
+// chain), V_int of O, H1, H2 and, for the original form, V(a) of O, H1, H2.
+constexpr int CT_IN = 8;
+template <typename R>
+__global__ void k_ct_prep(int M, int orig, DevState<R> d) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    R *o = d.ctin + m * CT_IN;
+    o[0] = R(d.vlp[m * 2] + d.vlp_r[m * 2]);
+    o[1] = R(d.vlp[m * 2 + 1] + d.vlp_r[m * 2 + 1]);
+    for (int a = 0; a < 3; ++a) {
+        o[2 + a] = R(d.vint[m * 3 + a]);
+        o[5 + a] = orig ? R(d.va[m * 3 + a] + d.va_r[m * 3 + a]) : R(0);
+    }
+}
+
 // VIR: the virial of the pair terms by translation invariance: with X_p =
 // O_i + off_p, sum over a molecule pair of g_p (x) X_p = sum_{p of i} g_p (x)
 // off_p + sum_{p of j} g_p (x) off_p - G_{i<-j} (x) dO_ij, where G_{i<-j} is
 // the total gradient on i's points and dO_ij = O_j - O_i; each side adds
 // its own offsets term and half of the last one.
+// One warp per molecule i.  The neighbour list is read 32 slots at a time;
+// the slots inside the cutoff (carrier-carrier distance) are queued in
+// shared memory and taken in full 32-lane rounds, each lane one molecule
+// pair with its 8 donor-acceptor items (i donating to j and j to i).
 template <typename R, bool PER, bool VIR>
 __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
     __shared__ R red[4][23 * 33];
-    const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
+    __shared__ int sq[4][64];
+    const int wq = threadIdx.x >> 5;
+    const int i = blockIdx.x * 4 + wq;
     const int lane = threadIdx.x & 31;
     if (i >= p.M) return;
     const R rc2 = sc<R>(p).rc2;
@@ -494,52 +517,43 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
     for (int k = 0; k < 3; ++k) P[k] = my_pt(d, i, k);
     P[3] = my_pt(d, i, 5);
     P[4] = my_pt(d, i, 6);
-    // lone-pair potentials: real space + reciprocal chain
-    const R Vi[2] = {R(d.vlp[i * 2] + d.vlp_r[i * 2]), R(d.vlp[i * 2 + 1] + d.vlp_r[i * 2 + 1])};
-    const R Vint_i[3] = {R(d.vint[i * 3]), R(d.vint[i * 3 + 1]), R(d.vint[i * 3 + 2])};
+    const R *in_i = d.ctin + i * CT_IN;
+    const R Vi[2] = {in_i[0], in_i[1]};
+    const R Vint_i[3] = {in_i[2], in_i[3], in_i[4]};
     V3<R> G[5];
     for (int k = 0; k < 5; ++k) G[k] = mk(R(0), R(0), R(0));
     R lam[2] = {R(0), R(0)}, kap[3] = {R(0), R(0), R(0)};
     // original form: the acceptor potentials V(a) of i's atoms and dE/dV(a)
     const bool orig = p.ct_orig != 0;
-    R Va_i[3] = {R(0), R(0), R(0)}, lama[3] = {R(0), R(0), R(0)};
-    if (orig)
-        for (int a = 0; a < 3; ++a) Va_i[a] = R(d.va[i * 3 + a] + d.va_r[i * 3 + a]);
+    const R Va_i[3] = {in_i[5], in_i[6], in_i[7]};
+    R lama[3] = {R(0), R(0), R(0)};
     R W[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) W[k] = R(0);
     Acc<R> Ect;
-    const int nn = d.nnbr[i];
-    for (int slot = lane; slot < nn; slot += 32) {
+    auto pair = [&](int slot) {
         const int j = d.nbr[i * MAXN + slot];
         const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
         const V3<R> dO = mk(dp_[0], dp_[1], dp_[2]);
-        R *cv = orig ? d.cvs + ((size_t)i * MAXN + slot) * 6 : nullptr;
-        if (PER && dot(dO, dO) >= rc2) {
-            if (orig)
-                for (int k = 0; k < 6; ++k) cv[k] = R(0);
-            continue;
-        }
         V3<R> Q[5];
         Q[0] = dO;
         Q[1] = dO + my_pt(d, j, 1);
         Q[2] = dO + my_pt(d, j, 2);
         Q[3] = dO + my_pt(d, j, 5);
         Q[4] = dO + my_pt(d, j, 6);
-        const R Vj[2] = {R(d.vlp[j * 2] + d.vlp_r[j * 2]), R(d.vlp[j * 2 + 1] + d.vlp_r[j * 2 + 1])};
-        const R Vint_j[3] = {R(d.vint[j * 3]), R(d.vint[j * 3 + 1]), R(d.vint[j * 3 + 2])};
+        const R *in_j = d.ctin + j * CT_IN;
+        const R Vj[2] = {in_j[0], in_j[1]};
         // original form: W = V_int + V* in e1, e2 and V(a1) in the denominator,
         // V*(a) = V(a) minus the donor molecule's bare potential at a
-        R Wj[3] = {Vint_j[0], Vint_j[1], Vint_j[2]}, Wi[3] = {Vint_i[0], Vint_i[1], Vint_i[2]};
+        R Wj[3] = {in_j[2], in_j[3], in_j[4]}, Wi[3] = {Vint_i[0], Vint_i[1], Vint_i[2]};
         R sh_j = R(0), sh_i = R(0);
         R cd[3] = {R(0), R(0), R(0)}, ca[3] = {R(0), R(0), R(0)};
         if (orig) {
             for (int a = 0; a < 3; ++a) {
-                const R Va_j = R(d.va[j * 3 + a] + d.va_r[j * 3 + a]);
-                Wj[a] += Va_j - mol_phi(p, d, i, Q[a]);            // i's sites at j's atom a
-                Wi[a] += Va_i[a] - mol_phi(p, d, j, P[a] - dO);    // j's sites at i's atom a
-                if (a == 0) sh_j = Va_j;
+                Wj[a] += in_j[5 + a] - mol_phi(p, d, i, Q[a]);      // i's sites at j's atom a
+                Wi[a] += Va_i[a] - mol_phi(p, d, j, P[a] - dO);      // j's sites at i's atom a
             }
+            sh_j = in_j[5];
             sh_i = Va_i[0];
         }
         V3<R> Gj = mk(R(0), R(0), R(0));   // gradient on i's points from j (virial)
@@ -567,14 +581,48 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
                 if (VIR) Gj = Gj + o.gc + o.glp + q.ga1 + q.ga2;
             }
         if (orig) {
+            R *cv = d.cvs + ((size_t)i * MAXN + slot) * 6;
             for (int a = 0; a < 3; ++a) cv[a] = cd[a], cv[3 + a] = ca[a];
         }
         if (VIR) vir_add(W, Gj, dO, R(-0.5));
+    };
+    int *q = sq[wq];
+    int cnt = 0, base = 0;   // queued slots and next list slot (warp-uniform)
+    const int nn = d.nnbr[i];
+    for (;;) {
+        while (cnt < 32 && base < nn) {
+            const int slot = base + lane;
+            bool in = false;
+            if (slot < nn) {
+                in = true;
+                if (PER) {
+                    const R *dp_ = d.ndo + ((size_t)i * MAXN + slot) * 3;
+                    const R x = dp_[0], y = dp_[1], z = dp_[2];
+                    in = x * x + y * y + z * z < rc2;
+                }
+                if (!in && orig) {   // no transfer: zero sensitivities for k_ct_vstar
+                    R *cv = d.cvs + ((size_t)i * MAXN + slot) * 6;
+                    for (int k = 0; k < 6; ++k) cv[k] = R(0);
+                }
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, in);
+            if (in) q[cnt + __popc(b & ((1u << lane) - 1u))] = slot;
+            cnt += __popc(b);
+            base += 32;
+            __syncwarp();
+        }
+        if (cnt == 0) break;
+        const int take = cnt < 32 ? cnt : 32;
+        if (lane < take) pair(q[lane]);
+        __syncwarp();
+        if (lane < cnt - take) q[lane] = q[take + lane];
+        cnt -= take;
+        __syncwarp();
     }
     const R vals[23] = {G[0].x, G[0].y, G[0].z, G[1].x, G[1].y, G[1].z, G[2].x, G[2].y, G[2].z,
                         G[3].x, G[3].y, G[3].z, G[4].x, G[4].y, G[4].z, lam[0], lam[1], kap[0], kap[1], kap[2],
                         lama[0], lama[1], lama[2]};
-    const R t = warp_transpose_sum<R, 23>(vals, red[threadIdx.x >> 5], lane);
+    const R t = warp_transpose_sum<R, 23>(vals, red[wq], lane);
     const int pt = lane / 3;
     double *dst = nullptr;
     if (lane < 15) dst = d.gpt + (i * NP + (pt < 3 ? pt : pt + 2)) * 3 + lane % 3;
@@ -582,7 +630,7 @@ __global__ void __launch_bounds__(128) k_ct(KParams p, DevState<R> d) {
     else if (lane < 20) dst = d.kap + i * 3 + lane - 17;
     else if (lane < 23 && orig) dst = d.lama + i * 3 + lane - 20;
     if (dst) *dst += double(t);
-    if (VIR) vir_points_out(d, i, P, t, W, red[threadIdx.x >> 5], lane);
+    if (VIR) vir_points_out(d, i, P, t, W, red[wq], lane);
     const double e = warp_sum_acc(Ect);
     if (lane == 0) d.epart[i * NTERM + T_CT] += e;
 }
@@ -666,6 +714,8 @@ __global__ void __launch_bounds__(256) k_ct_vstar(KParams p, DevState<R> d) {
 
 template <typename R>
 void launch_ct(const KParams &p, DevState<R> &d, Launch L) {
+    k_ct_prep<R><<<(p.M + 127) / 128, 128, 0, L.s>>>(p.M, p.ct_orig, d);
+    count(L);
     const unsigned nb = (p.M + 3) / 4;
     if (p.vir) {
         if (p.periodic) k_ct<R, true, true><<<nb, 128, 0, L.s>>>(p, d);

@@ -210,6 +210,7 @@ struct DevState {
     // and at the molecule's own atoms (j donor, 3-5)
     double *va, *va_r, *dva, *dva_r, *lama;
     R *lamaR, *cvs;
+    R *ctin;            // M*8 working-precision charge-transfer inputs (V_lp, V_int, V(a))
     int *tl_n, *tl_j;
     R *tl_x, *tl_y, *tl_z, *tl_g1, *tl_g2;
     double *partial;    // reduction partials
