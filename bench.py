@@ -5,7 +5,7 @@ Default workload: the 32,000-water box (96,000 atoms, 98.6 A, rc 9 A, SPME
 108^3 order 5, alpha 0.4 A^-1), mixed precision (FP32 pair and grid
 arithmetic, FP64 accumulation and solver scalars), PCG tolerance 1e-6 D
 with warm start (by default the initial guess extrapolates the dipoles of
-the last four steps; --warm-start 1 takes the previous step's),
+the last five steps, a quartic; --warm-start 1 takes the previous step's),
 velocity-Verlet NVE at 0.5 fs from 300 K after an untimed relaxation and
 velocity-rescaled equilibration; the plain FP64 GPU path is timed on the
 same workload.  --workload water4096 (4096 waters, 49.66 A, SPME 64^3),
@@ -69,9 +69,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the FP64 GPU path")
-    ap.add_argument("--warm-start", type=int, default=4, choices=[1, 2, 3, 4],
-                    help="PCG initial guess along the trajectory: 1 previous dipoles, 2-4 extrapolation through "
-                         "the last 2-4 steps' dipoles")
+    ap.add_argument("--warm-start", type=int, default=5, choices=[1, 2, 3, 4, 5, 6],
+                    help="PCG initial guess along the trajectory: 1 previous dipoles, 2-6 extrapolation through "
+                         "the last 2-6 steps' dipoles")
     ap.add_argument("--workload", default="water32000",
                     choices=["water216", "water4096", "water32000", "water216_paper", "clusters4096", "served"])
     ap.add_argument("--equil-steps", type=int, default=600,
@@ -410,7 +410,9 @@ WORKLOADS = {
 
 GUESS = {1: "previous step's dipoles", 2: "linear extrapolation of the last 2 steps' dipoles",
          3: "quadratic extrapolation of the last 3 steps' dipoles",
-         4: "cubic extrapolation of the last 4 steps' dipoles"}
+         4: "cubic extrapolation of the last 4 steps' dipoles",
+         5: "quartic extrapolation of the last 5 steps' dipoles",
+         6: "quintic extrapolation of the last 6 steps' dipoles"}
 
 
 def setup(name, pkg, synth, precision, stream, warm=1, ct_original=False):

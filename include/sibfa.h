@@ -111,10 +111,11 @@ enum { SIBFA_PREC_FP64 = 0, SIBFA_PREC_MIXED = 1 };
  * priority; short-range terms, lowest; lone-pair potentials and charge
  * transfer), forked from and joined back into the main one within the call.
  * warm_start: the PCG initial guess.  0: the direct-field dipoles alpha E.
- * 1: the dipoles of the previous solve.  2..4: the polynomial through the
+ * 1: the dipoles of the previous solve.  2..6: the polynomial through the
  * converged dipoles of the last warm_start full evaluations (energy and
  * forces, equally spaced in time as in an MD run), extrapolated one step
- * ahead (linear, quadratic, cubic); with fewer stored it uses as many as it
+ * ahead (linear, quadratic, cubic, quartic, quintic: coefficients
+ * (-1)^(j+1) C(n, j) for the j-th newest of n); with fewer stored it uses as many as it
  * has; a dipole-only solve neither uses nor feeds that history, and
  * sibfa_minimize clears it when it returns.  Every
  * choice converges to the same tolerance; only the iteration count differs.

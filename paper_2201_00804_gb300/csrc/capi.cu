@@ -83,8 +83,8 @@ struct sibfa_ctx {
     double e_tail = 0;            // dispersion beyond rc (homogeneous fluid), added to disp and the virial
     double *d_fprev = nullptr;    // Beeman: forces of the previous step (library-owned)
     bool have_mu = false;
-    // converged dipoles of the last full evaluations (warm_start >= 2): four
-    // slots of capacity * 9 doubles, the newest at hist_head - 1
+    // converged dipoles of the last full evaluations (warm_start >= 2):
+    // warm_start slots of capacity * 9 doubles, the newest at hist_head - 1
     double *mu_hist = nullptr;
     int hist_n = 0, hist_head = 0;
     bool md_forces_valid = false;
@@ -616,11 +616,14 @@ MuGuess mu_guess(const sibfa_ctx *ctx, bool full) {
     MuGuess g{};
     const int want = ctx->opts.warm_start;
     if (!full || want < 2 || ctx->hist_n < 1) return g;
-    static const double C[5][4] = {{0, 0, 0, 0}, {1, 0, 0, 0}, {2, -1, 0, 0}, {3, -3, 1, 0}, {4, -6, 4, -1}};
+    static const double C[MU_HIST + 1][MU_HIST] = {{0, 0, 0, 0, 0, 0},      {1, 0, 0, 0, 0, 0},
+                                                  {2, -1, 0, 0, 0, 0},     {3, -3, 1, 0, 0, 0},
+                                                  {4, -6, 4, -1, 0, 0},    {5, -10, 10, -5, 1, 0},
+                                                  {6, -15, 20, -15, 6, -1}};
     g.n = std::min(want, ctx->hist_n);
     const size_t stride = (size_t)ctx->capacity * 9;
     for (int j = 0; j < g.n; ++j) {
-        g.h[j] = ctx->mu_hist + (size_t)((ctx->hist_head - 1 - j + 8) % 4) * stride;
+        g.h[j] = ctx->mu_hist + (size_t)((ctx->hist_head - 1 - j + 2 * want) % want) * stride;
         g.c[j] = C[g.n][j];
     }
     return g;
@@ -632,8 +635,8 @@ sibfa_status push_mu(sibfa_ctx *ctx, const double *mu, bool full) {
     const size_t stride = (size_t)ctx->capacity * 9;
     CK(cudaMemcpyAsync(ctx->mu_hist + (size_t)ctx->hist_head * stride, mu, (size_t)ctx->M * 9 * sizeof(double),
                        cudaMemcpyDeviceToDevice, ctx->s));
-    ctx->hist_head = (ctx->hist_head + 1) % 4;
-    ctx->hist_n = std::min(ctx->hist_n + 1, 4);
+    ctx->hist_head = (ctx->hist_head + 1) % ctx->opts.warm_start;
+    ctx->hist_n = std::min(ctx->hist_n + 1, ctx->opts.warm_start);
     return SIBFA_OK;
 }
 
@@ -1135,8 +1138,8 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
         g_create_error = "sibfa_create: md_integrator must be 0 (velocity Verlet) or 1 (Beeman)";
         return SIBFA_E_INVALID;
     }
-    if (opts->warm_start < 0 || opts->warm_start > 4) {
-        g_create_error = "sibfa_create: warm_start must be 0..4";
+    if (opts->warm_start < 0 || opts->warm_start > MU_HIST) {
+        g_create_error = "sibfa_create: warm_start must be 0..6";
         return SIBFA_E_INVALID;
     }
     if (opts->periodic) {
@@ -1225,7 +1228,7 @@ sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo
         st = dalloc(ctx, &ctx->d_energy, 32);
         if (st) break;
         if (opts->warm_start >= 2) {
-            st = dalloc(ctx, &ctx->mu_hist, (size_t)4 * ctx->capacity * 9);
+            st = dalloc(ctx, &ctx->mu_hist, (size_t)opts->warm_start * ctx->capacity * 9);
             if (st) break;
         }
         if (cudaMallocHost((void **)&ctx->h_pin, ((size_t)ctx->M * 9 * 2 + 64) * sizeof(double)) != cudaSuccess ||

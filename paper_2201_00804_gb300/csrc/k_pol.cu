@@ -165,6 +165,54 @@ __device__ inline void cluster_rr_add(const DevState<R> &d, int k, bool valid, d
     }
 }
 
+// Block sums of two values at once (valid in thread 0): the two FP64 add
+// chains interleave, and the second stage runs over the 8 warp totals only.
+__device__ inline void block_sum2(double a, double b, double *sh, double &ra, double &rb) {
+    static_assert(PB == 256, "8 warps per block");
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) {
+        sh[w] = a;
+        sh[16 + w] = b;
+    }
+    __syncthreads();
+    ra = rb = 0;
+    if (w == 0) {
+        double x = l < 8 ? sh[l] : 0.0, y = l < 8 ? sh[16 + l] : 0.0;
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        }
+        ra = x;
+        rb = y;
+    }
+}
+
+// Sums of nb pairs of block partials (part[2b], part[2b + 1]) in a fixed
+// order, both in one pass: every block obtains bit-identical totals.
+__device__ inline void sum_partials2(const double *part, int nb, double *sh, double &ta, double &tb) {
+    if (threadIdx.x < 32) {
+        double a = 0, b = 0;
+        for (int k = threadIdx.x; k < nb; k += 32) {
+            a += __ldcg(part + 2 * k);
+            b += __ldcg(part + 2 * k + 1);
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        if (threadIdx.x == 0) {
+            sh[0] = a;
+            sh[1] = b;
+        }
+    }
+    __syncthreads();
+    ta = sh[0];
+    tb = sh[1];
+    __syncthreads();
+}
+
 // Sum of the nb block partials at part[0], part[stride], ... in a fixed
 // order (lane l takes l, l+32, ...; then a fixed tree): every block obtains
 // the bit-identical total.
@@ -235,15 +283,15 @@ __global__ void __launch_bounds__(PB) k_pcg_step(KParams p, DevState<R> d, cudaG
         }
         if (p.n_cl > 1) cluster_rr_add(d, k, k < n, q);
     }
-    rz = block_sum(rz, sh);
-    rr = block_sum(rr, sh);
+    double brz, brr;
+    block_sum2(rz, rr, sh, brz, brr);
     if (threadIdx.x == 0) {
-        d.partial[nb + 2 * blockIdx.x] = rz;
-        d.partial[nb + 2 * blockIdx.x + 1] = rr;
+        d.partial[nb + 2 * blockIdx.x] = brz;
+        d.partial[nb + 2 * blockIdx.x + 1] = brr;
     }
     grid.sync();
-    const double trz = sum_partials(d.partial + nb, nb, 2, sh);
-    const double trr = sum_partials(d.partial + nb + 1, nb, 2, sh);
+    double trz, trr;
+    sum_partials2(d.partial + nb, nb, sh, trz, trr);
     const double beta = trz / rz_old;
     double res = sqrt(trr / (p.M * 3)) * 4.80321;
     if (p.n_cl > 1) {

@@ -5,9 +5,10 @@
 namespace sibfa {
 
 // sum_j c[j] h[j] over n stored dipole vectors (n = 0: no stored guess)
+constexpr int MU_HIST = 6;   // stored solutions at most (quintic extrapolation)
 struct MuGuess {
-    const double *h[4];
-    double c[4];
+    const double *h[MU_HIST];
+    double c[MU_HIST];
     int n;
 };
 

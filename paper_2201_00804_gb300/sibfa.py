@@ -174,7 +174,7 @@ def sibfa_create(params: dict, mp_local: np.ndarray, *, periodic: bool, box=None
     cluster_start: optional (n_clusters + 1) ints splitting a gas-phase batch
     into independent clusters of consecutive molecules.
     warm_start: PCG initial guess, False/0 direct field, True/1 previous
-    dipoles, 2..4 extrapolation through the last 2..4 full evaluations."""
+    dipoles, 2..6 extrapolation through the last 2..6 full evaluations."""
     lib = load_library()
     P = sibfa_params(*[float(params[n]) for n in PARAM_FIELDS])
     mp = np.ascontiguousarray(mp_local, dtype=np.float64)

@@ -55,7 +55,7 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
 def test_create_rejects_bad_arguments_on_the_host(lib_path):
     """sibfa_create checks its arguments before its first CUDA call, so each
     bad argument returns its status here without a GPU: no molecules, an
-    unknown precision, a warm-start mode outside 0..4, an unsupported spline order, a grid below 8 points,
+    unknown precision, a warm-start mode outside 0..6, an unsupported spline order, a grid below 8 points,
     a non-positive cutoff or Ewald exponent, a cutoff plus twice the O-H
     extent above half the box (CUTOFF), and malformed cluster batches
     (periodic, not ending at n_mol, decreasing, an empty cluster, a cluster
@@ -70,7 +70,7 @@ def test_create_rejects_bad_arguments_on_the_host(lib_path):
     cases = [
         (dict(mp_local=mp[:0], periodic=False), -1),
         (dict(mp_local=mp, periodic=False, precision=7), -1),
-        (dict(mp_local=mp, periodic=False, warm_start=5), -1),
+        (dict(mp_local=mp, periodic=False, warm_start=7), -1),
         (dict(mp_local=mp, periodic=False, warm_start=-1), -1),
         (dict(per, order=4), -1),
         (dict(per, grid=(16, 16, 4)), -1),

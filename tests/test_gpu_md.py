@@ -107,7 +107,7 @@ def test_velocity_verlet_matches_host_integration():
 
 def test_nve_stays_stable_with_bounded_drift():
     """The 216-water box as the MD workloads run it (mixed precision, PCG
-    1e-6 D, cubic-extrapolation start): 20 capped relaxation steps, 100
+    1e-6 D, quartic-extrapolation start): 20 capped relaxation steps, 100
     velocity-rescaled steps at 300 K, then 240 NVE steps of 0.5 fs: no error
     status (in particular no charge-transfer denominator reaching zero, no
     atom leaving its molecule), the total energy (kinetic + intermolecular +
@@ -118,7 +118,7 @@ def test_nve_stays_stable_with_bounded_drift():
     import paper_2201_00804_gb300 as pkg
     s, o = synth.make_config("water216")
     ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
-                           ewald_alpha=o["ewald"], pcg_tol_D=1e-6, precision=pkg.PREC_MIXED, warm_start=4,
+                           ewald_alpha=o["ewald"], pcg_tol_D=1e-6, precision=pkg.PREC_MIXED, warm_start=5,
                            md_k_bond=KB, md_r0=R0, md_k_angle=KA, md_theta0_deg=TH0_DEG)
     pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
     vel = torch.tensor(synth.maxwell_velocities(s, 300.0, seed=21).reshape(-1), dtype=torch.float64, device="cuda")
@@ -160,7 +160,7 @@ def test_workload_nve_runs_reach_their_lengths(name, n_nve):
     import paper_2201_00804_gb300 as pkg
     s, o = synth.make_config(name)
     ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
-                           ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"], precision=pkg.PREC_MIXED, warm_start=4,
+                           ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"], precision=pkg.PREC_MIXED, warm_start=5,
                            md_k_bond=KB, md_r0=R0, md_k_angle=KA, md_theta0_deg=TH0_DEG)
     pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
     vel = torch.tensor(synth.maxwell_velocities(s, 300.0, seed=22).reshape(-1), dtype=torch.float64, device="cuda")

@@ -1,9 +1,10 @@
 """PCG initial guesses along an MD trajectory (216-water box, FP64 path,
 tolerance 1e-10 D): the direct-field guess (0), the previous dipoles (1)
-and the cubic extrapolation through the last four full evaluations (4) all
-converge to the same energies, forces and dipoles; the extrapolation needs
-no more iterations than the previous dipoles once its history is full; a
-dipole-only solve in between does not enter that history."""
+and the cubic, quartic and quintic extrapolations through the last four,
+five and six full evaluations (4, 5, 6) all converge to the same energies,
+forces and dipoles; the extrapolations need no more iterations than the
+previous dipoles once their history is full; a dipole-only solve in
+between does not enter that history."""
 import numpy as np
 import pytest
 
@@ -12,7 +13,7 @@ from gpu_util import TERMS
 
 pytestmark = pytest.mark.gpu
 
-N_STEPS = 10
+N_STEPS = 12
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -46,7 +47,7 @@ def test_guesses_converge_to_the_same_solution():
     finally:
         pkg.sibfa_destroy(md)
     res = {}
-    for warm in (0, 1, 4):
+    for warm in (0, 1, 4, 5, 6):
         ctx = _ctx(pkg, s, o, warm)
         out = []
         try:
@@ -66,14 +67,15 @@ def test_guesses_converge_to_the_same_solution():
     for k in range(N_STEPS):
         e0, F0, _ = res[0][k]
         mag = sum(abs(e0[t]) for t in TERMS)
-        for warm in (1, 4):
+        for warm in (1, 4, 5, 6):
             e, F, _ = res[warm][k]
             for t in TERMS:
                 assert abs(e[t] - e0[t]) <= 1e-9 * mag, (warm, k, t, e[t], e0[t])
             assert np.abs(F - F0).max() <= 1e-7 * np.abs(F0).max(), (warm, k)
-    it1 = sum(r[2] for r in res[1][4:])
-    it4 = sum(r[2] for r in res[4][4:])
-    assert it4 <= it1, ([r[2] for r in res[1]], [r[2] for r in res[4]])
+    it1 = sum(r[2] for r in res[1][6:])
+    for warm in (4, 5, 6):
+        itw = sum(r[2] for r in res[warm][6:])
+        assert itw <= it1, (warm, [r[2] for r in res[1]], [r[2] for r in res[warm]])
 
 
 def test_minimize_then_md_matches_a_fresh_context():
@@ -117,8 +119,8 @@ def test_minimize_then_md_matches_a_fresh_context():
 
 
 def test_mixed_path_with_extrapolated_guess_matches_oracle_along_trajectory():
-    """The mixed path as the MD workloads run it (cubic extrapolation of the
-    last four solutions as the PCG start) meets the mixed-precision bounds
+    """The mixed path as the MD workloads run it (quartic extrapolation of the
+    last five solutions as the PCG start) meets the mixed-precision bounds
     against the oracle at later points of a trajectory, where the guess
     comes from the history and not from the direct field."""
     import torch
@@ -130,13 +132,13 @@ def test_mixed_path_with_extrapolated_guess_matches_oracle_along_trajectory():
     vel = torch.tensor(synth.maxwell_velocities(s, 300.0, seed=11).reshape(-1), dtype=torch.float64, device="cuda")
     masses = torch.tensor(s.masses().reshape(-1), dtype=torch.float64, device="cuda")
     ctx = pkg.sibfa_create(synth.PARAMS, s.mp_local, periodic=True, box=s.box, rc=o["rc"], grid=o["grid"],
-                           ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"], precision=pkg.PREC_MIXED, warm_start=4)
+                           ewald_alpha=o["ewald"], pcg_tol_D=o["pcg_tol"], precision=pkg.PREC_MIXED, warm_start=5)
     try:
         for step in range(1, 9):
             pkg.sibfa_md_steps(ctx, pos, vel, masses, 0.5, 1)
             if step in (6, 8):
                 # the same positions through the same context: its guess is the
-                # extrapolation of the trajectory's last four solutions
+                # extrapolation of the trajectory's last five solutions
                 x = pos.clone()
                 F = torch.zeros_like(x)
                 mu = torch.zeros_like(x)
