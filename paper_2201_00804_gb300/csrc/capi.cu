@@ -216,6 +216,7 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
         AL(d.cvs, cto ? (size_t)M * MAXN * 6 : 1);
     }
     AL(d.ctin, M * 8);
+    AL(d.spk, M * 20);
     AL(d.epart, M * NTERM);
     AL(d.epw, M * NS * 2);
     AL(d.vir, M * 9);

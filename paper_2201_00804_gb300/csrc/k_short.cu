@@ -124,22 +124,62 @@ __device__ inline V3<R> selP(const ShortI<R> &I, int k) {
     return r;
 }
 
-// point k (0 O, 1 H1, 2 H2, 3 LP1, 4 LP2) of neighbour j relative to O_i
+// Per-molecule data of the short-range items, packed so that an item reads
+// one aligned 4-vector per point of its neighbour: for the points O, H1, H2,
+// LP1, LP2 the offset from O and the valence factor 1 - q/N_val of the
+// point's atom (O's for the lone pairs).  Written each evaluation before the
+// short-range launches, from the site offsets and the global charges.
+constexpr int SPK = 5 * 4;
 template <typename R>
-__device__ inline V3<R> qpt(const DevState<R> &d, int j, V3<R> dO, int k) {
-    const int s = k < 3 ? k : k + 2;
-    const R *o = d.off + (j * NP + s) * 3;
-    return dO + mk(o[0], o[1], o[2]);
+__global__ void k_short_pack(KParams p, DevState<R> d) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.M * 5) return;
+    const Scal<R> &S = sc<R>(p);
+    const int m = t / 5, k = t % 5;
+    const int s = k < 3 ? k : k + 2, a = k < 3 ? k : 0;
+    const R *o = d.off + (m * NP + s) * 3;
+    const R q = d.gmp[(m * NS + a) * GMP];
+    R *w = d.spk + (size_t)t * 4;
+    w[0] = o[0];
+    w[1] = o[1];
+    w[2] = o[2];
+    w[3] = R(1) - q * (a == 0 ? S.inv_nval_o : S.inv_nval_h);
 }
 
 template <typename R>
-__device__ inline R qcharge(const DevState<R> &d, int j, int k) { return d.gmp[(j * NS + k) * GMP]; }
+__device__ inline void ld4(const R *w, R &a, R &b, R &c, R &e);
+template <>
+__device__ inline void ld4<float>(const float *w, float &a, float &b, float &c, float &e) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(w));
+    a = v.x, b = v.y, c = v.z, e = v.w;
+}
+template <>
+__device__ inline void ld4<double>(const double *w, double &a, double &b, double &c, double &e) {
+    const double2 v0 = __ldg(reinterpret_cast<const double2 *>(w)), v1 = __ldg(reinterpret_cast<const double2 *>(w) + 1);
+    a = v0.x, b = v0.y, c = v1.x, e = v1.y;
+}
+
+// point k (0 O, 1 H1, 2 H2, 3 LP1, 4 LP2) of neighbour j relative to O_i,
+// and the valence factor of its atom
+template <typename R>
+__device__ inline V3<R> qpt(const DevState<R> &d, int j, V3<R> dO, int k, R &cf) {
+    R a, b, c;
+    ld4(d.spk + ((size_t)j * 5 + k) * 4, a, b, c, cf);
+    return dO + mk(a, b, c);
+}
+template <typename R>
+__device__ inline V3<R> qpt(const DevState<R> &d, int j, V3<R> dO, int k) {
+    R cf;
+    return qpt(d, j, dO, k, cf);
+}
+// valence factor of atom k (0 O, 1 H1, 2 H2) of molecule j
+template <typename R>
+__device__ inline R qcf(const DevState<R> &d, int j, int k) { return d.spk[((size_t)j * 5 + k) * 4 + 3]; }
 
 template <typename R>
-__device__ inline RepAtom<R> atom_j(const Scal<R> &S, const DevState<R> &d, int j, int k) {
-    const R q = qcharge(d, j, k);
-    if (k == 0) return rep_atom(S.cs_o, S.cp_o, S.g_o, R(1) - q * S.inv_nval_o, 0);
-    return rep_atom(S.cs_h, S.cp_h, S.g_h, R(1) - q * S.inv_nval_h, 1);
+__device__ inline RepAtom<R> atom_j(const Scal<R> &S, R cf, int k) {
+    if (k == 0) return rep_atom(S.cs_o, S.cp_o, S.g_o, cf, 0);
+    return rep_atom(S.cs_h, S.cp_h, S.g_h, cf, 1);
 }
 
 template <typename R>
@@ -161,8 +201,9 @@ __device__ void item_bb(const Scal<R> &S, const ShortTables &T, const DevState<R
     neighbour(d, i, slot, j, dO);
     const V3<R> P0 = I.P[0], Pb = kb == 1 ? I.P[1] : I.P[2];
     const RepAtom<R> Ab = kb == 1 ? I.A[1] : I.A[2];
-    const V3<R> Q0 = dO, Qc = qpt(d, j, dO, kc);
-    const RepAtom<R> AjO = atom_j(S, d, j, 0), Ajc = atom_j(S, d, j, kc);
+    R cfc;
+    const V3<R> Q0 = dO, Qc = qpt(d, j, dO, kc, cfc);
+    const RepAtom<R> AjO = atom_j(S, qcf(d, j, 0), 0), Ajc = atom_j(S, cfc, kc);
     const V3<R> dm = R(0.5) * (P0 + Pb) - R(0.5) * (Q0 + Qc);
     const R irm = rsqrt_(dot(dm, dm));
     R O1 = 0, O2 = 0;
@@ -230,8 +271,9 @@ __device__ void item_lb(const Scal<R> &S, const ShortTables &T, const DevState<R
     V3<R> dO;
     neighbour(d, i, slot, j, dO);
     const V3<R> P0 = I.P[0], Pl = l ? I.P[4] : I.P[3];
-    const V3<R> Q0 = dO, Qc = qpt(d, j, dO, kc);
-    const RepAtom<R> AjO = atom_j(S, d, j, 0), Ajc = atom_j(S, d, j, kc);
+    R cfc;
+    const V3<R> Q0 = dO, Qc = qpt(d, j, dO, kc, cfc);
+    const RepAtom<R> AjO = atom_j(S, qcf(d, j, 0), 0), Ajc = atom_j(S, cfc, kc);
     const RepAtom<R> Alp = rep_atom(S.cs_lp, S.cp_lp, S.g_o, R(1) - S.nlp * S.inv_nval_o, 2);
     const V3<R> dm = Pl - R(0.5) * (Q0 + Qc);
     const R irr = rsqrt_(dot(dm, dm));
@@ -309,15 +351,13 @@ __device__ void item_du(const KParams &p, const Scal<R> &S, const ShortTables &T
 #pragma unroll
     for (int t = 1; t < 5; ++t)
         if (t == u) cfi = I.cf[t];
-    const R *offj = d.off + j * NP * 3;
-    const R qO = qcharge(d, j, 0);
     V3<R> gu = mk(R(0), R(0), R(0));
     R ed = R(0), ex_sum = R(0);   // this item's few terms, then one compensated add each
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
         if (!((vmask >> v) & 1)) continue;
-        const int s = v < 3 ? v : v + 2;
-        const V3<R> dv = Pu - (dO + mk(offj[s * 3], offj[s * 3 + 1], offj[s * 3 + 2]));
+        R cfj;
+        const V3<R> dv = Pu - qpt(d, j, dO, v, cfj);
         const R r2 = dot(dv, dv);
         const R ri = rsqrt_(r2), r = r2 * ri;
         const int kv = v == 0 ? 0 : (v < 3 ? 1 : 2);
@@ -336,8 +376,6 @@ __device__ void item_du(const KParams &p, const Scal<R> &S, const ShortTables &T
         if (!lu && !lv) { pref = -bu * bv; xc = S.xd_c1; }
         else if (lu && lv) { pref = -nlp * nlp * R(0.25); xc = nlp * nlp * R(0.25) * S.xd_c2; }
         else { pref = -S.delta * R(0.5); xc = nlp * R(0.5) * S.xd_c3; }
-        const R qv = v < 3 ? qcharge(d, j, v) : qO;
-        const R cfj = R(1) - qv * (v == 1 || v == 2 ? S.inv_nval_h : S.inv_nval_o);
         const R K = bu * bv * cfi * cfj;
         const R ex = xc * K * exp_(-mulc(r, T.xd_k[ku][kv]));
         ed += pref * fsum;
@@ -540,6 +578,8 @@ void launch_short(const KParams &p, DevState<R> &d, Launch L, int max_blocks, in
             cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         }
     }
+    k_short_pack<R><<<(p.M * 5 + 255) / 256, 256, 0, L.s>>>(p, d);
+    count(L);
     if (p.vir) {
         if (p.periodic) {
             k_short<R, true, 0, true><<<nb, 128, sm, L.s>>>(p, d);

@@ -211,6 +211,7 @@ struct DevState {
     double *va, *va_r, *dva, *dva_r, *lama;
     R *lamaR, *cvs;
     R *ctin;            // M*8 working-precision charge-transfer inputs (V_lp, V_int, V(a))
+    R *spk;             // M*20 short-range point data (offset from O, valence factor) x 5 points
     int *tl_n, *tl_j;
     R *tl_x, *tl_y, *tl_z, *tl_g1, *tl_g2;
     double *partial;    // reduction partials
