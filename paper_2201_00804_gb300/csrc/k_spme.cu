@@ -515,9 +515,9 @@ __global__ void __launch_bounds__(256, 2) k_gather_perm(KParams p, DevState<R> d
             if (o < 3) {
                 d.gpt[(m * NP + pt) * 3 + o] += (double)mp_grad(mp, D, o);
                 d.gmu[(m * NS + pt) * 3 + o] += (double)D.d1[o];
-                if (pt < 3) d.efield[m * 9 + pt * 3 + o] -= (double)D.d1[o] / p.ke;
+                if (pt < 3) d.efield[m * 9 + pt * 3 + o] -= (double)D.d1[o] * p.sd.ike;
             } else if (o < 9) {
-                d.gth[(m * NS + pt) * 6 + o - 3] += (double)D.d2[o - 3] / 3.0;
+                d.gth[(m * NS + pt) * 6 + o - 3] += (double)D.d2[o - 3] * (1.0 / 3.0);
                 if (pt < 3) d.d2rec[m * 18 + pt * 6 + o - 3] = (double)D.d2[o - 3];
             } else if (o == 9) {
                 atomicAdd(&d.epart[m * NTERM + T_ELEC], 0.5 * (double)mp_energy(mp, D));
@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(256, 2) k_gather_polforce(KParams p, DevState<
             d.gpt[(m * NP + pt) * 3 + o] += g;
             d.gmu[(m * NS + pt) * 3 + o] += (double)S.d1[o];
         } else if (o < 9) {
-            d.gth[(m * NS + pt) * 6 + o - 3] += (double)S.d2[o - 3] / 3.0;
+            d.gth[(m * NS + pt) * 6 + o - 3] += (double)S.d2[o - 3] * (1.0 / 3.0);
         } else if (p.vir && o >= 10) {
             // permanent multipoles in the induced + lambda potential; induced
             // dipole in the permanent + induced potential
