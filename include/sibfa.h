@@ -341,8 +341,8 @@ void sibfa_destroy(sibfa_ctx *ctx);
  *
  * Jobs are MD runs (n_steps velocity-Verlet steps; n_steps = 0 is one energy
  * and force evaluation) of a periodic water box or a gas-phase cluster.
- * Box jobs run in `slots` concurrent workers, each with its own stream and a
- * context kept between jobs of the same shape.  Gas-phase clusters of at most
+ * Box jobs run in `slots` concurrent workers, each with its own stream and up
+ * to four contexts of distinct shapes kept between jobs of those shapes.  Gas-phase clusters of at most
  * `batch_max_cluster` waters are batched continuously: one resident batch
  * context advances every admitted cluster by one step per tick, finished jobs
  * leave and newly arrived ones join at the next tick, and each cluster keeps

@@ -1,10 +1,11 @@
 // Request server: energy/force jobs (MD runs of periodic water boxes and of
 // gas-phase clusters) that arrive over time.
 //
-// * Box jobs run in `slots` worker threads, each with its own stream and a
-//   context kept for the next job of the same shape (positions, velocities and
-//   multipoles are replaced; the previous induced dipoles serve as the first
-//   warm start).  Work of different slots overlaps on the device.
+// * Box jobs run in `slots` worker threads, each with its own stream and up
+//   to four contexts of distinct shapes kept for later jobs of those shapes
+//   (positions, velocities and multipoles are replaced; the previous induced
+//   dipoles serve as the first warm start); a slot prefers queued jobs of a
+//   shape it holds.  Work of different slots overlaps on the device.
 // * Gas-phase clusters are batched continuously: one resident batch context
 //   (a cluster batch, see sibfa_topology) advances all admitted clusters by one
 //   velocity-Verlet step per tick; jobs that reach their step count leave and
@@ -110,7 +111,7 @@ struct sibfa_server {
     std::deque<Job *> queue;
     std::unordered_map<uint64_t, Job *> jobs;
     uint64_t next_id = 1;
-    std::vector<size_t> resident;   // device bytes held by each slot's cached context
+    std::vector<size_t> resident;   // device bytes held by each slot's cached contexts
     size_t batch_bytes = 0;
     size_t running_bytes = 0;       // estimates of slot jobs whose context is being built
     bool stop = false;
@@ -152,33 +153,96 @@ sibfa_run_opts run_opts_for(const sibfa_server &S, const sibfa_job &j, cudaStrea
     return r;
 }
 
-// Box jobs (and clusters that do not join the batch) in slot k.
+// A context a slot keeps for later jobs of the same shape, with its device
+// arrays (positions, velocities, masses, forces).
+struct SlotCtx {
+    Shape shape;
+    sibfa_ctx *ctx = nullptr;
+    double *dpos = nullptr, *dvel = nullptr, *dmass = nullptr, *dF = nullptr;
+    size_t bytes = 0;     // device bytes: the context and the four arrays
+    uint64_t last = 0;    // use stamp; the least recently used is evicted first
+};
+constexpr int SLOT_CACHE = 4;   // contexts (distinct shapes) a slot keeps
+constexpr int SLOT_LOOK = 8;    // queued slot jobs a slot looks through for a shape it holds
+constexpr int SLOT_WAIT_MS = 250;   // the oldest slot job waiting longer is taken first
+
+void release(SlotCtx &c) {
+    if (c.ctx) sibfa_destroy(c.ctx);
+    cudaFree(c.dpos), cudaFree(c.dvel), cudaFree(c.dmass), cudaFree(c.dF);
+    c = SlotCtx{};
+}
+
+int find_shape(const std::vector<SlotCtx> &cache, const Shape &s) {
+    for (size_t c = 0; c < cache.size(); ++c)
+        if (cache[c].shape == s) return (int)c;
+    return -1;
+}
+
+// Box jobs (and clusters that do not join the batch) in slot k.  The slot
+// keeps up to SLOT_CACHE contexts of distinct shapes.  It takes the oldest of
+// the first SLOT_LOOK queued slot jobs whose shape it holds (no context to
+// build: allocations, FFT plans, solver graph and launch-shape tuning are
+// done once per shape and slot), unless the oldest slot job has waited
+// longer than SLOT_WAIT_MS; otherwise the oldest job whose context fits under
+// the memory cap, evicting the slot's least recently used contexts as needed.
 void slot_worker(sibfa_server *S, int k) {
     cudaSetDevice(S->device);
     cudaStream_t st;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    sibfa_ctx *ctx = nullptr;
-    Shape shape;
-    double *dpos = nullptr, *dvel = nullptr, *dmass = nullptr, *dF = nullptr;
+    std::vector<SlotCtx> cache;
+    uint64_t stamp = 0;
     std::vector<double> hmass;
     for (;;) {
         Job *j = nullptr;
-        bool reuse = false;
+        int hit = -1;
+        std::vector<int> evict;   // cache entries to release before building the job's context
         {
             std::unique_lock<std::mutex> lk(S->m);
             for (;;) {
                 if (S->stop) break;
-                for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
-                    Job *c = *it;
-                    if (c->batch) continue;
-                    const bool r = ctx && shape == shape_of(c->spec);
-                    const size_t need = r ? S->resident[k] : c->mem;
-                    if (S->used() - S->resident[k] + need <= S->o.device_mem_bytes) {
-                        j = c;
-                        reuse = r;
+                int seen = 0;
+                Job *head = nullptr;
+                for (Job *c : S->queue)
+                    if (!c->batch) {
+                        head = c;
+                        break;
+                    }
+                if (head && Clock::now() - head->t_submit > std::chrono::milliseconds(SLOT_WAIT_MS))
+                    seen = SLOT_LOOK;   // no reordering: the oldest job goes next
+                for (auto it = S->queue.begin(); it != S->queue.end() && seen < SLOT_LOOK; ++it) {
+                    if ((*it)->batch) continue;
+                    ++seen;
+                    const int c = find_shape(cache, shape_of((*it)->spec));
+                    if (c >= 0) {
+                        j = *it;
+                        hit = c;
                         S->queue.erase(it);
                         break;
                     }
+                }
+                if (!j) {
+                    std::vector<int> order(cache.size());
+                    for (size_t c = 0; c < cache.size(); ++c) order[c] = (int)c;
+                    std::sort(order.begin(), order.end(), [&](int a, int b) { return cache[a].last < cache[b].last; });
+                    const size_t used = S->used();
+                    for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+                        Job *c = *it;
+                        if (c->batch) continue;
+                        evict.clear();
+                        size_t freed = 0;
+                        const size_t must = cache.size() >= (size_t)SLOT_CACHE ? 1 : 0;
+                        for (int e : order) {
+                            if (evict.size() >= must && used - freed + c->mem <= S->o.device_mem_bytes) break;
+                            evict.push_back(e);
+                            freed += cache[e].bytes;
+                        }
+                        if (evict.size() >= must && used - freed + c->mem <= S->o.device_mem_bytes) {
+                            j = c;
+                            S->queue.erase(it);
+                            break;
+                        }
+                    }
+                    if (!j) evict.clear();
                 }
                 if (j) break;
                 S->cv.wait(lk);
@@ -186,61 +250,67 @@ void slot_worker(sibfa_server *S, int k) {
             if (!j) break;
             j->state = 1;
             j->t_start = Clock::now();
-            if (!reuse) {
-                S->resident[k] = 0;   // the cached context is replaced
+            if (hit < 0) {
+                for (int e : evict) S->resident[k] -= cache[e].bytes;
                 S->running_bytes += j->mem;
             }
         }
         const sibfa_job &J = j->spec;
         const size_t nb = (size_t)J.n_mol * 9 * sizeof(double);
         int status = SIBFA_OK;
-        if (!reuse) {
-            if (ctx) sibfa_destroy(ctx);
-            cudaFree(dpos), cudaFree(dvel), cudaFree(dmass), cudaFree(dF);
-            dpos = dvel = dmass = dF = nullptr;
-            ctx = nullptr;
+        if (hit < 0) {
+            std::sort(evict.begin(), evict.end(), [](int a, int b) { return a > b; });
+            for (int e : evict) {
+                release(cache[e]);
+                cache.erase(cache.begin() + e);
+            }
+            SlotCtx c;
             sibfa_topology topo{};
             topo.n_mol = J.n_mol;
             topo.mp_local = j->mp.data();
             const sibfa_run_opts ro = run_opts_for(*S, J, st);
-            status = sibfa_create(&S->params, &topo, &ro, &ctx);
+            status = sibfa_create(&S->params, &topo, &ro, &c.ctx);
             if (status == SIBFA_OK) {
-                if (cudaMalloc(&dpos, nb) != cudaSuccess || cudaMalloc(&dvel, nb) != cudaSuccess ||
-                    cudaMalloc(&dmass, nb) != cudaSuccess || cudaMalloc(&dF, nb) != cudaSuccess)
+                if (cudaMalloc(&c.dpos, nb) != cudaSuccess || cudaMalloc(&c.dvel, nb) != cudaSuccess ||
+                    cudaMalloc(&c.dmass, nb) != cudaSuccess || cudaMalloc(&c.dF, nb) != cudaSuccess)
                     status = SIBFA_E_OOM;
                 fill_masses(hmass, J.n_mol);
                 if (status == SIBFA_OK)
-                    cudaMemcpyAsync(dmass, hmass.data(), hmass.size() * sizeof(double), cudaMemcpyHostToDevice, st);
-                shape = shape_of(J);
+                    cudaMemcpyAsync(c.dmass, hmass.data(), hmass.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+                c.shape = shape_of(J);
+                c.bytes = c.ctx ? sibfa::ctx_device_bytes(c.ctx) + 4 * nb : 0;
             }
-            if (status != SIBFA_OK) {
-                if (ctx) sibfa_destroy(ctx);
-                ctx = nullptr;
-            }
+            if (status != SIBFA_OK) release(c);
             std::lock_guard<std::mutex> lk(S->m);
             S->running_bytes -= j->mem;
-            S->resident[k] = ctx ? sibfa::ctx_device_bytes(ctx) + 4 * nb : 0;
+            if (status == SIBFA_OK) {
+                S->resident[k] += c.bytes;
+                cache.push_back(c);
+                hit = (int)cache.size() - 1;
+            }
         } else {
             // same shape: new multipoles; the previous dipoles are the first warm start
-            const sibfa::BatchArrays b = sibfa::ctx_batch_arrays(ctx);
+            const sibfa::BatchArrays b = sibfa::ctx_batch_arrays(cache[hit].ctx);
             cudaMemcpyAsync(b.mp_local, j->mp.data(), (size_t)J.n_mol * 50 * sizeof(double), cudaMemcpyHostToDevice,
-                            sibfa::ctx_stream(ctx));
-            cudaStreamSynchronize(sibfa::ctx_stream(ctx));
+                            sibfa::ctx_stream(cache[hit].ctx));
+            cudaStreamSynchronize(sibfa::ctx_stream(cache[hit].ctx));
         }
         if (status == SIBFA_OK) {
-            cudaMemcpyAsync(dpos, j->pos.data(), nb, cudaMemcpyHostToDevice, st);
-            cudaMemcpyAsync(dvel, j->vel.data(), nb, cudaMemcpyHostToDevice, st);
+            SlotCtx &c = cache[hit];
+            c.last = ++stamp;
+            cudaMemcpyAsync(c.dpos, j->pos.data(), nb, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(c.dvel, j->vel.data(), nb, cudaMemcpyHostToDevice, st);
             cudaStreamSynchronize(st);
-            if (J.n_steps <= 0) status = sibfa_energy_forces(ctx, dpos, nullptr, &j->terms, dF, nullptr);
-            else status = sibfa_md_steps(ctx, dpos, dvel, dmass, J.dt_fs, J.n_steps, &j->terms);
+            if (J.n_steps <= 0) status = sibfa_energy_forces(c.ctx, c.dpos, nullptr, &j->terms, c.dF, nullptr);
+            else status = sibfa_md_steps(c.ctx, c.dpos, c.dvel, c.dmass, J.dt_fs, J.n_steps, &j->terms);
             j->forces.resize((size_t)J.n_mol * 9);
             j->pos_out.resize((size_t)J.n_mol * 9);
-            const double *fsrc = J.n_steps <= 0 ? dF : sibfa::ctx_batch_arrays(ctx).forces;
+            const double *fsrc = J.n_steps <= 0 ? c.dF : sibfa::ctx_batch_arrays(c.ctx).forces;
             cudaMemcpyAsync(j->forces.data(), fsrc, nb, cudaMemcpyDeviceToHost, st);
-            cudaMemcpyAsync(j->pos_out.data(), dpos, nb, cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(j->pos_out.data(), c.dpos, nb, cudaMemcpyDeviceToHost, st);
             cudaStreamSynchronize(st);
             double res = 0;
-            sibfa_last_stats(ctx, &j->iters, &res);
+            sibfa_last_stats(c.ctx, &j->iters, &res);
         }
         {
             std::lock_guard<std::mutex> lk(S->m);
@@ -249,8 +319,7 @@ void slot_worker(sibfa_server *S, int k) {
         }
         S->cv.notify_all();
     }
-    if (ctx) sibfa_destroy(ctx);
-    cudaFree(dpos), cudaFree(dvel), cudaFree(dmass), cudaFree(dF);
+    for (SlotCtx &c : cache) release(c);
     cudaStreamDestroy(st);
 }
 
