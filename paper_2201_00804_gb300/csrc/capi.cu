@@ -521,6 +521,18 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Page-locked host memory (cudaMallocHost, cudaHostRegister): the copy
+// engines read and write it directly, so it needs no staging copy.
+bool is_pinned_host_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 template <typename R>
 DevState<R> &state(sibfa_ctx *ctx);
 template <>
@@ -916,6 +928,8 @@ sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_ene
     if (pos) {
         if (is_device_ptr(pos)) {
             CK(cudaMemcpyAsync(d.pos, pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
+        } else if (is_pinned_host_ptr(pos)) {
+            CK(cudaMemcpyAsync(d.pos, pos, nb, cudaMemcpyHostToDevice, ctx->s));
         } else {
             CK(cudaStreamSynchronize(ctx->s));
             std::memcpy(ctx->h_pin, pos, nb);
@@ -938,22 +952,23 @@ sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_ene
     // results: energies + flags (+ dipoles) to pinned memory
     CK(cudaMemcpyAsync(h, ctx->d_energy, (NTERM + 1) * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
     CK(cudaMemcpyAsync((int *)(h + 16), d.flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    // outputs: device memory device to device, page-locked host memory
+    // directly, pageable host memory through the pinned staging buffer
+    const bool f_dev = is_device_ptr(forces), f_pin = !f_dev && is_pinned_host_ptr(forces);
+    const bool m_dev = is_device_ptr(mu_out), m_pin = !m_dev && is_pinned_host_ptr(mu_out);
     if (forces) {
-        if (is_device_ptr(forces)) {
-            CK(cudaMemcpyAsync(forces, ctx->d_forces, nb, cudaMemcpyDeviceToDevice, ctx->s));
-        } else {
-            CK(cudaMemcpyAsync(h + 32, ctx->d_forces, nb, cudaMemcpyDeviceToHost, ctx->s));
-        }
+        if (f_dev) CK(cudaMemcpyAsync(forces, ctx->d_forces, nb, cudaMemcpyDeviceToDevice, ctx->s));
+        else CK(cudaMemcpyAsync(f_pin ? forces : h + 32, ctx->d_forces, nb, cudaMemcpyDeviceToHost, ctx->s));
     }
     if (mu_out) {
-        if (is_device_ptr(mu_out)) CK(cudaMemcpyAsync(mu_out, d.mu, nb, cudaMemcpyDeviceToDevice, ctx->s));
-        else CK(cudaMemcpyAsync(h + 32, d.mu, nb, cudaMemcpyDeviceToHost, ctx->s));
+        if (m_dev) CK(cudaMemcpyAsync(mu_out, d.mu, nb, cudaMemcpyDeviceToDevice, ctx->s));
+        else CK(cudaMemcpyAsync(m_pin ? mu_out : h + 32, d.mu, nb, cudaMemcpyDeviceToHost, ctx->s));
     }
     st0 = leave(ctx);
     if (st0) return st0;
     CK(cudaStreamSynchronize(ctx->s));
     CK(cudaGetLastError());
-    if (forces && !is_device_ptr(forces)) std::memcpy(forces, h + 32, nb);
+    if (forces && !f_dev && !f_pin) std::memcpy(forces, h + 32, nb);
     if (virial) {
         std::memcpy(virial, h + 20, 9 * sizeof(double));
         // the tail scales as 1/V at fixed cutoff: W = -dE/d eps = E_tail on the diagonal
@@ -961,7 +976,7 @@ sibfa_status run(sibfa_ctx *ctx, const double *pos, const double *box, sibfa_ene
         virial[4] += ctx->e_tail;
         virial[8] += ctx->e_tail;
     }
-    if (mu_out && !is_device_ptr(mu_out)) std::memcpy(mu_out, h + 32, nb);
+    if (mu_out && !m_dev && !m_pin) std::memcpy(mu_out, h + 32, nb);
     solve_stats(ctx);
     sibfa_status fl = check_flags(ctx, *(int *)(h + 16));
     if (fl && fl != SIBFA_E_NOT_CONVERGED) return fl;

@@ -33,7 +33,11 @@ def run_gpu(system, opts, precision, tol_D, device=True, params=None, max_iter=3
     ctx = pkg.sibfa_create(P, system.mp_local, periodic=periodic, pcg_tol_D=tol_D, precision=precision,
                            pcg_max_iter=max_iter, warm_start=False, **kw, **create_kw)
     try:
-        if device:
+        if device == "pinned":   # page-locked host memory, copied without staging
+            pos = torch.tensor(system.pos.reshape(-1), dtype=torch.float64).pin_memory()
+            F = torch.zeros_like(pos).pin_memory()
+            mu = torch.zeros_like(pos).pin_memory()
+        elif device:
             pos = torch.tensor(system.pos.reshape(-1), dtype=torch.float64, device="cuda")
             F = torch.zeros_like(pos)
             mu = torch.zeros_like(pos)

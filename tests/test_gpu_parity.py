@@ -73,9 +73,11 @@ def test_host_and_device_pointers_agree():
     s, o = CASES["water216"]
     # FP64 path: only the order of the grid atomics can differ between runs
     a = run_gpu(s, o, pkg.PREC_FP64, 1e-10, device=True)
-    b = run_gpu(s, o, pkg.PREC_FP64, 1e-10, device=False)
-    assert a["terms"]["total"] == pytest.approx(b["terms"]["total"], rel=1e-11)
-    np.testing.assert_allclose(a["forces"], b["forces"], rtol=0, atol=1e-8)
+    for host in (False, "pinned"):   # pageable (staged) and page-locked host buffers
+        b = run_gpu(s, o, pkg.PREC_FP64, 1e-10, device=host)
+        assert a["terms"]["total"] == pytest.approx(b["terms"]["total"], rel=1e-11)
+        np.testing.assert_allclose(a["forces"], b["forces"], rtol=0, atol=1e-8)
+        np.testing.assert_allclose(a["mu"], b["mu"], rtol=0, atol=1e-9)
 
 
 def test_single_molecule_has_no_intermolecular_energy():
