@@ -23,9 +23,10 @@
  * Memory and errors.  The library owns the context and every device buffer
  * it allocates at sibfa_create.  The caller owns all input and output
  * arrays; they may be host or device pointers (detected per call).  Device
- * pointers are read and written on the context's stream; host pointers are
- * staged through the context's pinned buffers and the call returns after the
- * results are in host memory.  No call throws; every call returns a status
+ * pointers are read and written on the context's stream; page-locked host
+ * memory (cudaMallocHost, cudaHostRegister) is copied to and from directly,
+ * pageable host memory is staged through the context's pinned buffers, and
+ * the call returns after the results are in host memory.  No call throws; every call returns a status
  * and sibfa_last_error() gives a one-line reason for the last failure.
  */
 #ifndef SIBFA_H
