@@ -185,10 +185,12 @@ typedef struct sibfa_ctx sibfa_ctx;
  * with a conditional while-node; with the environment variable
  * SIBFA_PCG_HOST_LOOP=1 at creation it is driven from the host instead (one
  * launch per kernel and iteration, same arithmetic), which kernel profilers
- * can follow.  The context tunes the launch shape of its short-range kernels
- * (resident blocks per SM) over its first full evaluations by timing them
- * and then keeps the fastest; the choice affects scheduling only, never the
- * results.  SIBFA_TUNE=0 at creation turns the tuning off (fixed shape). */
+ * can follow.  The context tunes the schedule of its short-range kernels
+ * (resident blocks per SM, and whether they finish before the polarization
+ * solve; see sibfa_tuned_schedule) over its first full evaluations outside
+ * sibfa_minimize by timing them and then keeps the fastest; the choice
+ * affects scheduling only, never the results.  SIBFA_TUNE=0 at creation
+ * turns the tuning off (fixed shape). */
 sibfa_status sibfa_create(const sibfa_params *params, const sibfa_topology *topo,
                           const sibfa_run_opts *opts, sibfa_ctx **out);
 
@@ -254,6 +256,19 @@ uint64_t sibfa_kernel_launches(const sibfa_ctx *ctx);
  * tuning has fixed it (0 while candidates are still being timed).  Either
  * pointer may be NULL.  Returns SIBFA_E_INVALID for a NULL context. */
 sibfa_status sibfa_tuned_shape(const sibfa_ctx *ctx, int *blocks_per_sm, int *done);
+
+/* The whole short-range schedule chosen by the tuning.  The candidates, in
+ * order: (blocks per SM, joined before the solve) = (3, no), (0, no),
+ * (2, no), (0, yes), (3, yes); "joined before the solve" means the
+ * short-range kernels finish before the polarization solve starts (the
+ * solve's latency-bound kernels then have the SMs to themselves), otherwise
+ * they run beside it until the chain rule.  *blocks_per_sm, *join_before_solve
+ * (0/1) and *done as for sibfa_tuned_shape; cand_ms (HOST, n_cand entries,
+ * may be NULL) receives each candidate's fastest timed evaluation in ms (0
+ * for a candidate not timed, or beyond the 5 candidates).  Any output may be
+ * NULL.  Returns SIBFA_E_INVALID for a NULL context or n_cand < 0. */
+sibfa_status sibfa_tuned_schedule(const sibfa_ctx *ctx, int *blocks_per_sm, int *join_before_solve, int *done,
+                                  double *cand_ms, int n_cand);
 
 /* Optional phase timing with CUDA events recorded on the context stream
  * around each phase of an evaluation: "sites", "neighbors", "real_perm"

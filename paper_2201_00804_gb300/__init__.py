@@ -17,6 +17,7 @@ from .sibfa import (  # noqa: F401
     sibfa_destroy,
     sibfa_energy_forces,
     sibfa_kernel_launches,
+    sibfa_tuned_schedule,
     sibfa_tuned_shape,
     sibfa_last_error,
     sibfa_last_stats,

@@ -33,18 +33,21 @@ struct sibfa_ctx {
     cudaStream_t s3 = nullptr;
     cudaEvent_t ev_fork3 = nullptr, ev_join3 = nullptr;
     bool short_pending = false;
-    // Autotuner of the short-range launch shape (resident blocks per SM, 0 =
-    // uncapped): the first evaluations after two warm-up ones each run one
-    // candidate and are timed whole on the main stream (two per candidate,
-    // the faster kept); then the fastest candidate is fixed.  The choice
-    // changes only the scheduling, never the arithmetic.
+    // Autotuner of the short-range schedule: resident blocks per SM (0 =
+    // uncapped) and whether the short-range stream is joined before the
+    // polarization solve (the solve then has the SMs to itself) or only
+    // before the chain rule.  The first evaluations outside sibfa_minimize
+    // after two warm-up ones
+    // each run one candidate and are timed whole on the main stream (two per
+    // candidate, the faster kept); then the fastest candidate is fixed.  The
+    // choice changes only the scheduling, never the arithmetic.
     struct ShortTuner {
         bool on = true;
         int seen = 0;            // evaluations with forces seen
         int cand = 0;            // candidate being timed
         int reps = 0;
         int choice = -1;         // fixed candidate, -1 while tuning
-        float tmin[3] = {1e30f, 1e30f, 1e30f};
+        float tmin[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
         bool pending = false;    // events of the last timed evaluation not read yet
         cudaEvent_t e0 = nullptr, e1 = nullptr;
     } tune;
@@ -88,6 +91,7 @@ struct sibfa_ctx {
     double *mu_hist = nullptr;
     int hist_n = 0, hist_head = 0;
     bool md_forces_valid = false;
+    bool minimizing = false;   // inside sibfa_minimize: its evaluations do not feed the tuner
     // optional per-phase timing with CUDA events on the context stream
     bool profiling = false;
     bool serial = false;   // profiling with every phase alone on the GPU (no stream overlap)
@@ -461,15 +465,22 @@ sibfa_status join_ct(sibfa_ctx *ctx) {
     return SIBFA_OK;
 }
 
-// Short-range launch shape candidates: resident blocks per SM (0 = uncapped).
-constexpr int kShortCaps[3] = {3, 0, 2};
+// Short-range schedule candidates: resident blocks per SM (0 = uncapped) and
+// the join of the short-range stream before the solve.
+struct ShortSched {
+    int cap;
+    bool join_before_solve;
+};
+constexpr int kNSched = 5;
+constexpr ShortSched kSched[kNSched] = {{3, false}, {0, false}, {2, false}, {0, true}, {3, true}};
 constexpr int kTuneWarm = 2, kTuneReps = 2;
 
-int short_cap(const sibfa_ctx *ctx) {
+ShortSched short_sched(const sibfa_ctx *ctx) {
     const auto &T = ctx->tune;
-    if (!T.on) return ctx->kp.periodic ? 3 : 0;
-    return kShortCaps[T.choice >= 0 ? T.choice : T.cand];
+    if (!T.on) return {ctx->kp.periodic ? 3 : 0, false};
+    return kSched[T.choice >= 0 ? T.choice : T.cand];
 }
+int short_cap(const sibfa_ctx *ctx) { return short_sched(ctx).cap; }
 
 // Reads the last timed evaluation (waiting for it, only while tuning) and
 // advances the candidate; after the last candidate, fixes the fastest.
@@ -487,9 +498,9 @@ void tune_account(sibfa_ctx *ctx) {
     T.tmin[T.cand] = std::min(T.tmin[T.cand], ms);
     if (++T.reps < kTuneReps) return;
     T.reps = 0;
-    if (++T.cand < 3) return;
+    if (++T.cand < kNSched) return;
     int best = 0;
-    for (int c = 1; c < 3; ++c)
+    for (int c = 1; c < kNSched; ++c)
         if (T.tmin[c] < T.tmin[best]) best = c;
     T.choice = best;
 }
@@ -702,7 +713,9 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
 template <typename R>
 sibfa_status evaluate(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, double tol) {
     auto &T = ctx->tune;
-    const bool timed = T.on && T.choice < 0 && !dipoles_only && !ctx->kp.vir && !ctx->capturing;
+    // relaxation steps start each solve far from its answer (many more PCG
+    // iterations than along a trajectory), so they are not timed
+    const bool timed = T.on && T.choice < 0 && !dipoles_only && !ctx->kp.vir && !ctx->capturing && !ctx->minimizing;
     if (timed) {
         tune_account(ctx);
         if (T.choice < 0) CK(cudaEventRecord(T.e0, ctx->s));
@@ -790,6 +803,8 @@ sibfa_status evaluate_impl(sibfa_ctx *ctx, bool want_forces, bool dipoles_only, 
             launch_ct(p, d, Launch{ctx->s4, &ctx->launches});
         }
     }
+    // schedule choice: the short-range kernels finish before the solve
+    if (bg_short && short_sched(ctx).join_before_solve && (st = join_short(ctx))) return st;
     {
         Phase ph(ctx, "pcg");
         st = solve(ctx, d, tol, L, !dipoles_only);
@@ -1305,8 +1320,10 @@ static sibfa_status minimize_impl(sibfa_ctx *ctx, double *pos, int n, double cap
         ~ClearHistory() {
             c->hist_n = 0;
             c->md_forces_valid = false;
+            c->minimizing = false;
         }
     } clear_history{ctx};
+    ctx->minimizing = true;
     CK(cudaMemsetAsync(d.flags, 0, sizeof(int), ctx->s));
     CK(cudaMemcpyAsync(d.pos, pos, nb, cudaMemcpyDeviceToDevice, ctx->s));
     for (int k = 0; k < n; ++k) {
@@ -1426,6 +1443,19 @@ sibfa_status sibfa_tuned_shape(const sibfa_ctx *ctx, int *blocks_per_sm, int *do
     if (!ctx) return SIBFA_E_INVALID;
     if (blocks_per_sm) *blocks_per_sm = short_cap(ctx);
     if (done) *done = (!ctx->tune.on || ctx->tune.choice >= 0) ? 1 : 0;
+    return SIBFA_OK;
+}
+
+sibfa_status sibfa_tuned_schedule(const sibfa_ctx *ctx, int *blocks_per_sm, int *join_before_solve, int *done,
+                                  double *cand_ms, int n_cand) {
+    if (!ctx || n_cand < 0) return SIBFA_E_INVALID;
+    const ShortSched s = short_sched(ctx);
+    if (blocks_per_sm) *blocks_per_sm = s.cap;
+    if (join_before_solve) *join_before_solve = s.join_before_solve ? 1 : 0;
+    if (done) *done = (!ctx->tune.on || ctx->tune.choice >= 0) ? 1 : 0;
+    if (cand_ms)
+        for (int c = 0; c < n_cand; ++c)
+            cand_ms[c] = (c < kNSched && ctx->tune.tmin[c] < 1e29f) ? (double)ctx->tune.tmin[c] : 0.0;
     return SIBFA_OK;
 }
 

@@ -118,6 +118,9 @@ def load_library(path: str = LIB_PATH):
     lib.sibfa_kernel_launches.restype = C.c_uint64
     lib.sibfa_tuned_shape.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.sibfa_tuned_shape.restype = C.c_int
+    lib.sibfa_tuned_schedule.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                         C.POINTER(C.c_double), C.c_int]
+    lib.sibfa_tuned_schedule.restype = C.c_int
     lib.sibfa_set_profiling.argtypes = [C.c_void_p, C.c_int]
     lib.sibfa_set_profiling.restype = None
     lib.sibfa_profile_get.argtypes = [C.c_void_p, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int)]
@@ -345,6 +348,17 @@ def sibfa_last_stats(ctx):
 
 def sibfa_kernel_launches(ctx) -> int:
     return int(load_library().sibfa_kernel_launches(ctx))
+
+
+def sibfa_tuned_schedule(ctx):
+    """(short-range blocks per SM, joined before the solve, True once tuning
+    fixed it, the five candidates' fastest timed evaluations in ms)."""
+    lib = load_library()
+    b, j, dn = C.c_int(), C.c_int(), C.c_int()
+    ms = (C.c_double * 5)()
+    st = lib.sibfa_tuned_schedule(ctx, C.byref(b), C.byref(j), C.byref(dn), ms, 5)
+    _check(lib, ctx, st)
+    return b.value, bool(j.value), bool(dn.value), list(ms)
 
 
 def sibfa_tuned_shape(ctx):

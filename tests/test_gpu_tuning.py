@@ -1,7 +1,8 @@
-"""The short-range launch-shape tuning: after its warm-up and timed
-evaluations a context has fixed one of the candidate shapes, and the shape
-changes the scheduling only: energies and forces equal those of a context
-with the tuning off."""
+"""The short-range schedule tuning (resident blocks per SM, and whether the
+short-range kernels finish before the polarization solve): after its
+warm-up and timed evaluations a context has fixed one of the candidates,
+every candidate was timed, and the choice changes the scheduling only:
+energies and forces equal those of a context with the tuning off."""
 import os
 
 import numpy as np
@@ -42,10 +43,14 @@ def test_tuning_fixes_a_shape_and_leaves_results_unchanged():
     a, b = _ctx(pkg, s, o, True), _ctx(pkg, s, o, False)
     try:
         Fa, Fb = torch.zeros_like(pos), torch.zeros_like(pos)
-        for _ in range(10):
+        for _ in range(14):   # 2 warm-up + 5 candidates x 2 timed, each read at the next call
             ea = pkg.sibfa_energy_forces(a, pos, Fa)
         blocks, done = pkg.sibfa_tuned_shape(a)
         assert done and blocks in (0, 2, 3)
+        b2, join, done2, ms = pkg.sibfa_tuned_schedule(a)
+        assert (b2, done2) == (blocks, done) and join in (False, True)
+        assert all(t > 0 for t in ms)                       # every candidate was timed
+        assert pkg.sibfa_tuned_schedule(b)[:3] == (3, False, True)
         eb = pkg.sibfa_energy_forces(b, pos, Fb)
         assert pkg.sibfa_tuned_shape(b) == (3, True)      # tuning off: the fixed periodic shape
         torch.cuda.synchronize()
