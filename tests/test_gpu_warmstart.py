@@ -154,3 +154,26 @@ def test_mixed_path_with_extrapolated_guess_matches_oracle_along_trajectory():
                 assert it < 30, it
     finally:
         pkg.sibfa_destroy(ctx)
+
+
+@pytest.mark.parametrize("warm", [2, 3, 4, 5, 6])
+def test_extrapolation_of_a_constant_history_is_the_solution(warm):
+    """At fixed positions every stored solution is the same vector, and the
+    extrapolation coefficients (-1)^(j+1) C(n, j) of each order sum to one:
+    once the history holds n solutions, the initial guess is the converged
+    solution itself and the solve stops before its first iteration."""
+    import torch
+    import paper_2201_00804_gb300 as pkg
+    s, o = synth.make_config("water216")
+    ctx = _ctx(pkg, s, o, warm)
+    try:
+        pos = torch.tensor(s.pos.reshape(-1), dtype=torch.float64, device="cuda")
+        F = torch.zeros_like(pos)
+        its = []
+        for _ in range(warm + 2):
+            pkg.sibfa_energy_forces(ctx, pos, F)
+            its.append(pkg.sibfa_last_stats(ctx)[0])
+    finally:
+        pkg.sibfa_destroy(ctx)
+    assert its[0] > 5, its                 # the first solve starts from the direct field
+    assert its[warm + 1] == 0, its          # history full: the guess is the answer
