@@ -100,6 +100,42 @@ def test_results_alone_equal_in_the_mix():
         assert r["latency_ms"] >= r["queue_ms"] >= 0.0
 
 
+def test_slot_context_cache_with_eviction():
+    """One box slot and five box shapes (the same 216 waters on five grid
+    sizes), submitted as 1, 2, 3, 1, 4, 5, 1: the slot keeps four contexts,
+    so shape 1 comes back from its cache once and, after shapes 4 and 5, is
+    rebuilt once its context has been evicted as the least recently used;
+    every result equals the job run alone."""
+    import paper_2201_00804_gb300 as pkg
+    s, o = synth.make_config("water216")
+    grids = (24, 25, 27, 30, 32)
+    order = (0, 1, 2, 0, 3, 4, 0)
+    jobs = []
+    for k, g in enumerate(order):
+        sk = synth.System(pos=s.pos + 0.01 * k, mp_local=s.mp_local, box=s.box)
+        jobs.append(dict(sys=sk, periodic=True, rc=o["rc"], grid=grids[g], alpha=o["ewald"], n_steps=k % 2 * 2,
+                         vel=synth.maxwell_velocities(sk, 300.0, seed=40 + k)))
+    srv = pkg.Server(synth.PARAMS, slots=1, batch_waters=0, precision=pkg.PREC_MIXED)
+    try:
+        tickets, res = [], {}
+        for j in jobs:
+            sk = j["sys"]
+            t = srv.submit(sk.pos, sk.mp_local, periodic=True, n_steps=j["n_steps"], vel=j["vel"], dt_fs=0.5,
+                           box=sk.box, rc=j["rc"], grid=j["grid"], ewald_alpha=j["alpha"])
+            tickets.append(t)
+            res.update(_wait(srv, [t]))    # one at a time: the submission order is the run order
+    finally:
+        srv.close()
+    for j, t in zip(jobs, tickets):
+        r = res[t]
+        assert r["status"] == 0
+        terms, pos = _alone(j)
+        mag = sum(abs(terms[k]) for k in TERMS)
+        for k in TERMS:
+            assert abs(r["terms"][k] - terms[k]) <= 1e-6 * mag, (k, r["terms"][k], terms[k])
+        assert np.abs(r["pos"] - pos).max() <= 1e-6
+
+
 def test_full_queue_answers_busy():
     import paper_2201_00804_gb300 as pkg
     s, o = synth.make_config("water216")
