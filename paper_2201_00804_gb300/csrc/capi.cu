@@ -253,7 +253,6 @@ sibfa_status alloc_state(sibfa_ctx *ctx, DevState<R> &d) {
     AL(d.tl_y, nt);
     AL(d.tl_z, nt);
     AL(d.tl_g1, nt);
-    AL(d.tl_g2, nt);
     AL(d.partial, 4 * ((M * 9 + 255) / 256) + 64);
     AL(d.scal, 32);
     AL(d.counter, 4);

@@ -215,12 +215,14 @@ __device__ __forceinline__ void perm_pair(const KParams &p, const DevState<R> &d
         source_field<R, 1>(ms, x, gtol, f4);
         A.ef = A.ef - f4.d1;
         if (ATOM_SRC) {   // the same atom pair in the polarization matrix T
-            d.tl_j[te] = j * 3 + s;
-            d.tl_x[te] = x.x;
-            d.tl_y[te] = x.y;
-            d.tl_z[te] = x.z;
+            // the field of a dipole mu at x is g2 (mu.x) x + g1 mu = sgn(g2) (mu.y) y + g1 mu
+            // with y = sqrt|g2| x: four values and the sign of g2 in the index's top bit
+            const R sq = sqrt_(fabs(gtol[2]));
+            d.tl_j[te] = (j * 3 + s) | (gtol[2] < R(0) ? int(0x80000000u) : 0);
+            d.tl_x[te] = sq * x.x;
+            d.tl_y[te] = sq * x.y;
+            d.tl_z[te] = sq * x.z;
             d.tl_g1[te] = gtol[1];
-            d.tl_g2[te] = gtol[2];
         }
     }
 }
@@ -740,12 +742,14 @@ void launch_ct(const KParams &p, DevState<R> &d, Launch L) {
 // ---------------------------------------------------------------------------
 constexpr int TW = 8;   // warps per block
 
+// entry: partner atom index (the sign of g2 in its top bit), y = sqrt|g2| x, g1
 template <typename R>
-__device__ inline void tmu_entry(const DevState<R> &d, size_t k, int jb, V3<R> &ef) {
-    const R *mv = d.vecR + jb * 3;
+__device__ inline void tmu_entry(const DevState<R> &d, size_t k, int jraw, V3<R> &ef) {
+    const R *mv = d.vecR + (jraw & 0x7fffffff) * 3;
     const V3<R> mu = mk(mv[0], mv[1], mv[2]);
-    const V3<R> x = mk(d.tl_x[k], d.tl_y[k], d.tl_z[k]);
-    ef = ef + (d.tl_g2[k] * dot(mu, x)) * x + d.tl_g1[k] * mu;
+    const V3<R> y = mk(d.tl_x[k], d.tl_y[k], d.tl_z[k]);
+    const R my = dot(mu, y);
+    ef = ef + (jraw < 0 ? -my : my) * y + d.tl_g1[k] * mu;
 }
 
 template <typename R>

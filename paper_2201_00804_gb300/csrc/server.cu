@@ -77,7 +77,7 @@ Shape shape_of(const sibfa_job &j) {
 // a fixed allowance for the context and cuFFT.  An estimate with margin.
 size_t estimate_bytes(const sibfa_job &j, int precision) {
     const int nb = j.periodic ? 384 : std::max(1, std::min(384, j.n_mol - 1));
-    const size_t entry = precision == SIBFA_PREC_FP64 ? 44 : 24;
+    const size_t entry = precision == SIBFA_PREC_FP64 ? 36 : 20;
     const size_t per_mol =
         (size_t)3 * 3 * nb * entry + (size_t)nb * (precision == SIBFA_PREC_FP64 ? 28 : 16) + 6144;
     size_t b = (size_t)j.n_mol * per_mol;

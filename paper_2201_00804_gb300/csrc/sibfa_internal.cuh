@@ -212,8 +212,8 @@ struct DevState {
     R *lamaR, *cvs;
     R *ctin;            // M*8 working-precision charge-transfer inputs (V_lp, V_int, V(a))
     R *spk;             // M*20 short-range point data (offset from O, valence factor) x 5 points
-    int *tl_n, *tl_j;
-    R *tl_x, *tl_y, *tl_z, *tl_g1, *tl_g2;
+    int *tl_n, *tl_j;                   // polarization pair list: count per atom; partner | sgn(g2) << 31
+    R *tl_x, *tl_y, *tl_z, *tl_g1;      // sqrt|g2| x (x the pair displacement) and g1
     double *partial;    // reduction partials
     double *scal;       // device scalars (see pcg kernels)
     unsigned int *counter;
